@@ -1,0 +1,278 @@
+"""ctypes wrapper of the FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import
+this module.  It marshals numpy arrays into the C oracle (lxw_oracle.c) and
+holds none of the method's arithmetic.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+PERIODIC, REFLECT, TRANSPARENT = 0, 1, 2
+QUAD, TRI = 0, 1
+DIAG_KEYS = ["s", "dt", "min_rho", "min_p", "mass", "momx", "momy", "energy",
+             "n_mom", "n_edge", "n_sc", "status"]
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip) if a is not None else None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_gauss_legendre.argtypes = [C.c_int, _dp, _dp]
+        L.orc_num_modes.argtypes = [C.c_int, C.c_int]
+        L.orc_basis_eval.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
+        L.orc_interior_rule.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
+        for f in (L.orc_flux_d1, L.orc_flux_d2):
+            f.argtypes = [C.c_double, _dp, _dp, _dp, _dp]
+        L.orc_flux.argtypes = [C.c_double, _dp, _dp, _dp]
+        L.orc_mesh_cartesian.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _ip]
+        L.orc_mesh_cartesian.restype = C.c_void_p
+        L.orc_mesh_triangles.argtypes = [C.c_int, _dp, C.c_int, _ip, _ip]
+        L.orc_mesh_triangles.restype = C.c_void_p
+        L.orc_mesh_free.argtypes = [C.c_void_p]
+        for f in (L.orc_mesh_num_elements, L.orc_mesh_num_edges, L.orc_mesh_edges_per_element):
+            f.argtypes = [C.c_void_p]
+        L.orc_mesh_geometry.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
+        L.orc_solver_new.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.orc_solver_new.restype = C.c_void_p
+        L.orc_solver_free.argtypes = [C.c_void_p]
+        L.orc_solver_set_params.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int]
+        for f in (L.orc_solver_num_modes, L.orc_solver_num_points, L.orc_projection_num_points):
+            f.argtypes = [C.c_void_p]
+        L.orc_projection_points.argtypes = [C.c_void_p, _dp]
+        L.orc_projection_weights.argtypes = [C.c_void_p, _dp]
+        L.orc_project.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_eval_projection_points.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_eval_limiter_points.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_limiter_points.argtypes = [C.c_void_p, _dp]
+        L.orc_last_fluxes.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_last_fluxes.restype = C.c_double
+        L.orc_moment_limit.argtypes = [C.c_void_p, _dp, _dp, _ip]
+        L.orc_moment_limit.restype = C.c_double
+        L.orc_wave_speed.argtypes = [C.c_void_p, _dp]
+        L.orc_wave_speed.restype = C.c_double
+        L.orc_ck_element.argtypes = [C.c_void_p, _dp, C.c_int, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_mu_solve.argtypes = [C.c_double, C.c_double, _dp, _dp]
+        L.orc_mu_solve.restype = C.c_double
+        L.orc_flux_limit_cell.argtypes = [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
+        L.orc_shock_limit.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_step.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
+        L.orc_num_threads.argtypes = []
+        _lib = L
+    return _lib
+
+
+def gauss_legendre(n):
+    x = np.zeros(n); w = np.zeros(n)
+    lib().orc_gauss_legendre(n, _d(x), _d(w))
+    return x, w
+
+
+def interior_rule(kind, n):
+    xi = np.zeros(n * n); eta = np.zeros(n * n); w = np.zeros(n * n)
+    k = lib().orc_interior_rule(kind, n, _d(xi), _d(eta), _d(w))
+    return xi[:k], eta[:k], w[:k]
+
+
+def num_modes(kind, deg):
+    return lib().orc_num_modes(kind, deg)
+
+
+def basis_eval(kind, deg, xi, eta):
+    xi = np.ascontiguousarray(xi, dtype=np.float64); eta = np.ascontiguousarray(eta, dtype=np.float64)
+    ML = num_modes(kind, deg)
+    phi = np.zeros((len(xi), ML)); dx = np.zeros_like(phi); dy = np.zeros_like(phi)
+    lib().orc_basis_eval(kind, deg, len(xi), _d(xi), _d(eta), _d(phi), _d(dx), _d(dy))
+    return phi, dx, dy
+
+
+def flux(gamma, q):
+    q = np.ascontiguousarray(q, dtype=np.float64); F = np.zeros(4); G = np.zeros(4)
+    lib().orc_flux(gamma, _d(q), _d(F), _d(G))
+    return F, G
+
+
+def flux_d1(gamma, q, w):
+    q = np.ascontiguousarray(q, dtype=np.float64); w = np.ascontiguousarray(w, dtype=np.float64)
+    F = np.zeros(4); G = np.zeros(4)
+    lib().orc_flux_d1(gamma, _d(q), _d(w), _d(F), _d(G))
+    return F, G
+
+
+def flux_d2(gamma, q, w):
+    q = np.ascontiguousarray(q, dtype=np.float64); w = np.ascontiguousarray(w, dtype=np.float64)
+    F = np.zeros(4); G = np.zeros(4)
+    lib().orc_flux_d2(gamma, _d(q), _d(w), _d(F), _d(G))
+    return F, G
+
+
+def mu_solve(gamma, eps0, qlxf, qc):
+    a = np.ascontiguousarray(qlxf, dtype=np.float64); b = np.ascontiguousarray(qc, dtype=np.float64)
+    return lib().orc_mu_solve(gamma, eps0, _d(a), _d(b))
+
+
+def flux_limit_cell(gamma, eps0, area, dt, qbar, fW, fF):
+    """Steps 4-5 of the flux limiter on one element; returns (proposals, cfl_bad)."""
+    qbar = np.ascontiguousarray(qbar, dtype=np.float64)
+    fW = np.ascontiguousarray(fW, dtype=np.float64); fF = np.ascontiguousarray(fF, dtype=np.float64)
+    prop = np.zeros(fW.shape[0])
+    bad = lib().orc_flux_limit_cell(gamma, eps0, fW.shape[0], area, dt, _d(qbar), _d(fW), _d(fF), _d(prop))
+    return prop, bad
+
+
+def num_threads():
+    return lib().orc_num_threads()
+
+
+class Mesh:
+    def __init__(self, ptr):
+        if not ptr:
+            raise ValueError("oracle mesh construction failed")
+        self.ptr = ptr
+        L = lib()
+        self.N = L.orc_mesh_num_elements(ptr)
+        self.E = L.orc_mesh_edges_per_element(ptr)
+        self.nedges = L.orc_mesh_num_edges(ptr)
+
+    @classmethod
+    def cartesian(cls, nx, ny, box=(0.0, 1.0, 0.0, 1.0), bc=(PERIODIC,) * 4):
+        b = np.array(bc, dtype=np.int32)
+        return cls(lib().orc_mesh_cartesian(nx, ny, box[0], box[1], box[2], box[3], _i(b)))
+
+    @classmethod
+    def triangles(cls, xy, tv, ebc=None):
+        xy = np.ascontiguousarray(xy, dtype=np.float64); tv = np.ascontiguousarray(tv, dtype=np.int32)
+        e = None if ebc is None else np.ascontiguousarray(ebc, dtype=np.int32)
+        return cls(lib().orc_mesh_triangles(len(xy), _d(xy), len(tv), _i(tv), _i(e)))
+
+    def geometry(self):
+        a = np.zeros(self.N); p = np.zeros(self.N); cx = np.zeros(self.N); cy = np.zeros(self.N)
+        lib().orc_mesh_geometry(self.ptr, _d(a), _d(p), _d(cx), _d(cy))
+        return a, p, cx, cy
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.orc_mesh_free(self.ptr)
+            self.ptr = None
+
+
+class Solver:
+    def __init__(self, mesh, deg, gamma=1.4, eps0=1e-12, alpha0=500.0, shock_limiter=True):
+        self.mesh = mesh  # keep alive
+        self.ptr = lib().orc_solver_new(mesh.ptr, deg, gamma)
+        if not self.ptr:
+            raise ValueError("oracle solver construction failed")
+        lib().orc_solver_set_params(self.ptr, eps0, alpha0, int(bool(shock_limiter)))
+        self.gamma = gamma
+        self.N, self.E = mesh.N, mesh.E
+        self.ML = lib().orc_solver_num_modes(self.ptr)
+        self.npts = lib().orc_solver_num_points(self.ptr)
+        self.nproj = lib().orc_projection_num_points(self.ptr)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.orc_solver_free(self.ptr)
+            self.ptr = None
+
+    def new_state(self):
+        return np.zeros((self.N, 4, self.ML))
+
+    def projection_points(self):
+        xy = np.zeros((self.N, self.nproj, 2))
+        lib().orc_projection_points(self.ptr, _d(xy))
+        return xy
+
+    def projection_weights(self):
+        w = np.zeros(self.nproj)
+        lib().orc_projection_weights(self.ptr, _d(w))
+        return w
+
+    def project(self, prim):
+        prim = np.ascontiguousarray(prim, dtype=np.float64)
+        assert prim.shape == (self.N, self.nproj, 4)
+        Q = self.new_state()
+        lib().orc_project(self.ptr, _d(prim), _d(Q))
+        return Q
+
+    def project_fn(self, fn):
+        """Project a primitive-variable function fn(x, y) -> (rho, u, v, p)."""
+        xy = self.projection_points()
+        r, u, v, p = fn(xy[..., 0], xy[..., 1])
+        prim = np.stack(np.broadcast_arrays(r, u, v, p), axis=-1)
+        return self.project(prim)
+
+    def eval_projection_points(self, Q):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        q = np.zeros((self.N, self.nproj, 4))
+        lib().orc_eval_projection_points(self.ptr, _d(Q), _d(q))
+        return q
+
+    def eval_limiter_points(self, Q):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        q = np.zeros((self.N, self.npts, 4))
+        lib().orc_eval_limiter_points(self.ptr, _d(Q), _d(q))
+        return q
+
+    def limiter_points(self):
+        xy = np.zeros((self.N, self.npts, 2))
+        lib().orc_limiter_points(self.ptr, _d(xy))
+        return xy
+
+    def last_fluxes(self):
+        """Outward f^LxW, f^LxF per element edge [N][E][4] and dt of the last step."""
+        fw = np.zeros((self.N, self.E, 4)); ff = np.zeros((self.N, self.E, 4))
+        dt = lib().orc_last_fluxes(self.ptr, _d(fw), _d(ff))
+        return fw, ff, dt
+
+    def moment_limit(self, Q):
+        """In place; returns theta per element and the status bits."""
+        th = np.zeros(self.N); st = C.c_int(0)
+        lib().orc_moment_limit(self.ptr, _d(Q), _d(th), C.byref(st))
+        return th, st.value
+
+    def wave_speed(self, Q):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        return lib().orc_wave_speed(self.ptr, _d(Q))
+
+    def ck_element(self, Q, i, dt):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        out = [np.zeros((self.npts, 4)) for _ in range(5)]
+        V = np.zeros((self.ML, 4))
+        lib().orc_ck_element(self.ptr, _d(Q), i, dt, *[_d(o) for o in out], _d(V))
+        return dict(q=out[0], qt=out[1], qtt=out[2], FT=out[3], GT=out[4], V=V)
+
+    def shock_limit(self, Q):
+        th = np.zeros(self.N)
+        lib().orc_shock_limit(self.ptr, _d(Q), _d(th))
+        return th
+
+    def step(self, Q, dt=0.0, cfl=0.1, want_theta=False):
+        """Advance Q (in place) one step; returns the diagnostics dict."""
+        assert Q.dtype == np.float64 and Q.flags.c_contiguous and Q.shape == (self.N, 4, self.ML)
+        diag = np.zeros(16)
+        tm = ts = te = None
+        if want_theta:
+            tm = np.zeros(self.N); ts = np.zeros(self.N); te = np.zeros((self.N, self.E))
+        lib().orc_step(self.ptr, _d(Q), dt, cfl, _d(diag), _d(tm), _d(ts), _d(te))
+        d = {k: diag[i] for i, k in enumerate(DIAG_KEYS)}
+        d["status"] = int(d["status"])
+        if want_theta:
+            d.update(theta_mom=tm, theta_sc=ts, theta_edge=te)
+        return d

@@ -1,0 +1,161 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the
+benchmark.
+
+This module holds problem data only -- meshes (vertex coordinates and
+connectivity), initial conditions as primitive-variable point functions, and
+seeded random states -- and none of the method's arithmetic (no basis,
+quadrature, flux, limiter or geometry).  Each side (the CPU oracle and the
+GPU library) builds its own geometry, tables and projections from these.
+
+Workloads (the paper's Sec. 4 problems and the scaled synthetic cases built
+from them):
+  smooth   32x32 periodic [0,1]^2, rho = 1 + 0.2 sin 2pi(x+y), u = (1,1), p = 1
+  rarefy   224x224x2 jittered triangles on [0,1]^2, rho = 1, p = 0.4,
+           u = -2 (x < 0.5) / +2 (x > 0.5), transparent boundaries
+  blast    1024x1024 on [-1.1,1.1]^2, rho = 1, u = 0, p = 1e-12 except the 4
+           centre cells with E = 0.244816 / cell area, reflective walls
+  paper_smooth  the Table 1 problem rho = 1 - 0.9999 sin 2pi x sin 2pi y,
+           u = (1,0), p = 1, periodic
+"""
+import numpy as np
+
+PERIODIC, REFLECT, TRANSPARENT = 0, 1, 2
+GAMMA = 1.4
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """n outputs of the SplitMix64 generator (Steele, Lea & Flood 2014)."""
+    out = np.empty(n, dtype=np.uint64)
+    x = seed & MASK64
+    for i in range(n):
+        x = (x + 0x9E3779B97F4A7C15) & MASK64
+        z = x
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        out[i] = z ^ (z >> 31)
+    return out
+
+
+def uniform01(seed: int, n: int) -> np.ndarray:
+    """n doubles in [0,1) from the top 53 bits of SplitMix64."""
+    return (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+def structured_triangles(n: int, jitter: float = 0.2, seed: int = 20160129,
+                         box=(0.0, 1.0, 0.0, 1.0)):
+    """n x n squares, each split by its '/' diagonal into two CCW triangles.
+
+    Interior vertices move by U[-jitter, jitter] * h in each coordinate;
+    boundary vertices move only along their side; corners stay fixed.
+    Returns (xy[nv,2], tv[nt,3]).
+    """
+    x0, x1, y0, y1 = box
+    hx, hy = (x1 - x0) / n, (y1 - y0) / n
+    I, J = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="xy")
+    X = x0 + I * hx
+    Y = y0 + J * hy
+    if jitter > 0.0:
+        r = uniform01(seed, 2 * (n + 1) * (n + 1)).reshape(2, n + 1, n + 1)
+        dx = (2.0 * r[0] - 1.0) * jitter * hx
+        dy = (2.0 * r[1] - 1.0) * jitter * hy
+        onx = (I == 0) | (I == n)     # on a vertical side: x fixed
+        ony = (J == 0) | (J == n)     # on a horizontal side: y fixed
+        X = X + np.where(onx, 0.0, dx)
+        Y = Y + np.where(ony, 0.0, dy)
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1)
+    vid = lambda i, j: j * (n + 1) + i
+    i, j = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    i = i.ravel(); j = j.ravel()
+    a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+    t1 = np.stack([a, b, c], axis=1)
+    t2 = np.stack([a, c, d], axis=1)
+    tv = np.empty((2 * n * n, 3), dtype=np.int32)
+    tv[0::2] = t1
+    tv[1::2] = t2
+    return xy, tv
+
+
+# ---------------------------------------------------------------- initial data
+def ic_smooth(x, y):
+    return 1.0 + 0.2 * np.sin(2 * np.pi * (x + y)), np.ones_like(x), np.ones_like(x), np.ones_like(x)
+
+
+def exact_smooth_density(x, y, t):
+    return 1.0 + 0.2 * np.sin(2 * np.pi * (x + y - 2.0 * t))
+
+
+def ic_paper_smooth(x, y):
+    rho = 1.0 - 0.9999 * np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y)
+    return rho, np.ones_like(x), np.zeros_like(x), np.ones_like(x)
+
+
+def exact_paper_smooth_density(x, y, t):
+    return 1.0 - 0.9999 * np.sin(2 * np.pi * (x - t)) * np.sin(2 * np.pi * y)
+
+
+def ic_rarefy(x, y):
+    u = np.where(x < 0.5, -2.0, 2.0)
+    return np.ones_like(x), u, np.zeros_like(x), 0.4 * np.ones_like(x)
+
+
+def ic_uniform(rho=1.3, u=0.3, v=-0.2, p=0.8):
+    def f(x, y):
+        one = np.ones_like(x)
+        return rho * one, u * one, v * one, p * one
+    return f
+
+
+def ic_blast(n: int, half_width: float = 1.1, gamma: float = GAMMA, e_total: float = 0.979264):
+    """Point-energy blast on an n x n grid of [-w,w]^2 (n even): the 4 cells
+    touching the origin share e_total; elsewhere p = 1e-12."""
+    h = 2.0 * half_width / n
+    p_in = (gamma - 1.0) * (e_total / 4.0) / (h * h)
+
+    def f(x, y):
+        inside = (np.abs(x) < h) & (np.abs(y) < h)
+        return np.ones_like(x), np.zeros_like(x), np.zeros_like(x), np.where(inside, p_in, 1e-12)
+    return f
+
+
+def ic_quadrants(seed: int):
+    """Four-quadrant Riemann data on [0,1]^2 drawn from a per-problem seed:
+    rho ~ U[0.1,2], p ~ U[0.01,2], u, v ~ U[-1,1] in each quadrant."""
+    r = uniform01(seed, 16).reshape(4, 4)
+    rho = 0.1 + 1.9 * r[:, 0]
+    p = 0.01 + 1.99 * r[:, 1]
+    u = -1.0 + 2.0 * r[:, 2]
+    v = -1.0 + 2.0 * r[:, 3]
+
+    def f(x, y):
+        qd = (x >= 0.5).astype(np.int64) + 2 * (y >= 0.5).astype(np.int64)
+        return rho[qd], u[qd], v[qd], p[qd]
+    return f
+
+
+def ensemble_sizes(count: int = 256, lo: int = 32, hi: int = 256, seed: int = 4242):
+    """Per-problem grid sizes n_p ~ U{lo..hi} (n_p x n_p cells each)."""
+    r = uniform01(seed, count)
+    return (lo + np.floor(r * (hi - lo + 1))).astype(np.int64).clip(lo, hi)
+
+
+def random_modal_state(N: int, ML: int, seed: int, amp: float = 0.3, gamma: float = GAMMA,
+                       rho_range=(0.5, 2.0), p_range=(0.2, 2.0)):
+    """Random modal coefficients Q[N][4][ML] with positive averages.
+
+    Averages come from random primitive data (rho, u, v, p); every higher
+    coefficient is U[-amp, amp] times the magnitude of its variable's
+    average, so large amp drives point values negative and wakes the
+    limiters."""
+    r = uniform01(seed, N * (4 + 4 * ML)).reshape(N, 4 + 4 * ML)
+    rho = rho_range[0] + (rho_range[1] - rho_range[0]) * r[:, 0]
+    u = -1.0 + 2.0 * r[:, 1]
+    v = -1.0 + 2.0 * r[:, 2]
+    p = p_range[0] + (p_range[1] - p_range[0]) * r[:, 3]
+    avg = np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)], axis=1)
+    Q = np.zeros((N, 4, ML))
+    Q[:, :, 0] = avg
+    scale = np.abs(avg) + 0.1 * np.abs(avg[:, :1])
+    hi = (2.0 * r[:, 4:].reshape(N, 4, ML) - 1.0) * amp
+    Q[:, :, 1:] = hi[:, :, 1:] * scale[:, :, None]
+    return Q

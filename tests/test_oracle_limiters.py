@@ -1,0 +1,143 @@
+"""Pins of the oracle's positivity machinery (Sec. 3) by brute force on small
+random inputs: the moment limiter (Sec. 3.1), the mu quadratic (Sec. 3.3
+Step 5b), the positivity of every state in the final theta box (Steps 4-6)
+and the invariants of the shock-capturing limiter (Sec. 4.1)."""
+import numpy as np
+import pytest
+
+import synth
+
+G = 1.4
+
+
+def pressure(q):
+    return (G - 1) * (q[..., 3] - 0.5 * (q[..., 1] ** 2 + q[..., 2] ** 2) / q[..., 0])
+
+
+def small_meshes(orc):
+    yield orc.Mesh.cartesian(5, 4, (0.0, 1.0, 0.0, 0.8))
+    xy, tv = synth.structured_triangles(3, jitter=0.2, seed=5)
+    yield orc.Mesh.triangles(xy, tv)
+
+
+@pytest.mark.parametrize("deg", [2, 3])
+def test_moment_limiter_positivity_and_feasibility(orc, deg):
+    for mesh in small_meshes(orc):
+        sol = orc.Solver(mesh, deg, gamma=G)
+        Q0 = synth.random_modal_state(mesh.N, sol.ML, seed=100 + deg, amp=1.2)
+        Q0[::2, :, 1:] *= 0.02 * np.arange(1, mesh.N + 1, 2)[:, None, None] / mesh.N
+        Q = Q0.copy()
+        th, st = sol.moment_limit(Q)
+        assert st == 0
+        assert np.array_equal(Q[:, :, 0], Q0[:, :, 0])               # averages untouched
+        assert np.all((th >= 0) & (th <= 1)) and np.any(th < 1) and np.any(th == 1)
+        assert np.allclose(Q[:, :, 1:], th[:, None, None] * Q0[:, :, 1:], rtol=1e-15, atol=0)
+        q = sol.eval_limiter_points(Q)
+        rbar = Q0[:, 0, 0]; pbar = pressure(Q0[:, :, 0])
+        eps_r = np.minimum(1e-12, rbar / 2); eps_p = np.minimum(1e-12, pbar / 2)
+        scale = np.abs(Q0[:, :, 0]).max(axis=1)
+        assert np.all(q[..., 0] >= eps_r[:, None] - 1e-14 * scale[:, None])
+        assert np.all(pressure(q) >= eps_p[:, None] - 1e-13 * scale[:, None])
+        # brute force: every theta' <= theta is feasible, and theta is not
+        # larger than the largest feasible value found on a dense grid
+        qu = sol.eval_limiter_points(Q0)
+        qb = Q0[:, :, 0][:, None, :]
+        grid = np.linspace(0.0, 1.0, 2001)
+        for i in range(mesh.N):
+            qs = qb[i] + grid[:, None, None] * (qu[i] - qb[i])[None]
+            ok = np.all(qs[..., 0] >= eps_r[i] * (1 - 1e-9), axis=1) & np.all(pressure(qs) >= eps_p[i] * (1 - 1e-9), axis=1)
+            star = grid[np.argmin(ok)] if not ok.all() else 1.0
+            assert th[i] <= star + 1e-12
+            assert ok[grid <= th[i] - 1e-12].all()
+
+
+def test_mu_solve_matches_bisection(orc):
+    rng = np.random.default_rng(3)
+    hits = 0
+    for _ in range(400):
+        ql = synth.random_modal_state(1, 1, seed=int(rng.integers(1 << 30)))[0, :, 0]
+        qc = ql + rng.normal(size=4) * np.abs(ql) * rng.uniform(0.1, 3)
+        qc[0] = abs(qc[0]) + 1e-3                        # corner densities are positive
+        mu = orc.mu_solve(G, 1e-12, ql, qc)
+        eps_p = min(1e-12, 0.5 * pressure(ql))
+        f = lambda m: pressure(ql + m * (qc - ql)) - eps_p
+        if f(1.0) >= 0:
+            assert mu == 1.0
+            continue
+        lo, hi = 0.0, 1.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if f(mid) >= 0 else (lo, mid)
+        assert abs(mu - lo) < 1e-12
+        assert f(mu) >= -1e-12 * abs(ql[3])
+        hits += 1
+    assert hits > 50
+
+
+@pytest.mark.parametrize("E", [3, 4])
+def test_flux_limiter_box_positivity_brute_force(orc, E):
+    """Steps 4-5 on random cells: every state of the box [0, Lambda'] has
+    rho >= 0 and p > 0 (sampled densely, corners included)."""
+    rng = np.random.default_rng(E)
+    limited = 0
+    for trial in range(300):
+        qbar = synth.random_modal_state(1, 1, seed=1000 * E + trial, rho_range=(0.01, 2.0), p_range=(1e-3, 2.0))[0, :, 0]
+        T, dt = rng.uniform(0.5, 2.0), rng.uniform(0.05, 0.3)
+        # a positive low-order state q^LxF fixes sum_k f^LxF_k
+        qlxf = synth.random_modal_state(1, 1, seed=7000 * E + trial, rho_range=(1e-4, 1.0), p_range=(1e-5, 1.0))[0, :, 0]
+        fF = rng.normal(size=(E, 4))
+        fF += ((qbar - qlxf) * T / dt - fF.sum(0)) / E
+        fW = fF + rng.normal(size=(E, 4)) * np.abs(qbar) * T / dt * rng.uniform(0.05, 1.0)
+        prop, bad = orc.flux_limit_cell(G, 1e-12, T, dt, qbar, fW, fF)
+        assert bad == 0 and np.all((prop >= 0) & (prop <= 1))
+        limited += np.any(prop < 1)
+        samp = rng.uniform(0, 1, (400, E)) * prop[None, :]
+        corners = np.array([[(c >> k) & 1 for k in range(E)] for c in range(1 << E)]) * prop[None, :]
+        samp = np.vstack([samp, corners])
+        qn = qbar[None, :] - dt / T * (samp @ fW + (1 - samp) @ fF)
+        assert np.all(qn[:, 0] >= 0)
+        assert np.all(pressure(qn) > 0)
+    assert limited > 100
+
+
+def test_step_uses_edge_min_of_proposals(orc):
+    """Through a full step: the new averages equal the blended update at
+    theta_e, and theta_e keeps every state of the box positive."""
+    mesh = orc.Mesh.cartesian(10, 10, bc=(2, 2, 2, 2))
+    sol = orc.Solver(mesh, 2, gamma=G, shock_limiter=False)
+    Q = synth.random_modal_state(mesh.N, sol.ML, seed=78, amp=0.3, rho_range=(0.01, 3.0), p_range=(0.001, 3.0))
+    Qlim = Q.copy(); sol.moment_limit(Qlim)
+    d = sol.step(Q, cfl=0.9, want_theta=True)
+    assert d["status"] == 0 and d["n_edge"] > 0
+    fw, ff, dt = sol.last_fluxes()
+    area = mesh.geometry()[0]
+    rng = np.random.default_rng(0)
+    for i in range(mesh.N):
+        th = d["theta_edge"][i]
+        samp = np.vstack([rng.uniform(0, 1, (300, mesh.E)) * th[None, :], th[None, :]])
+        qn = Qlim[i, :, 0][None, :] - dt / area[i] * (samp @ fw[i] + (1 - samp) @ ff[i])
+        assert np.all(qn[:, 0] >= 0) and np.all(pressure(qn) > 0)
+        assert np.allclose(qn[-1], Q[i, :, 0], rtol=1e-13, atol=1e-14)
+
+
+def test_shock_limiter_invariants(orc):
+    n = 8
+    mesh = orc.Mesh.cartesian(n, n)
+    sol = orc.Solver(mesh, 2, gamma=G, alpha0=5.0)
+    Q0 = synth.random_modal_state(mesh.N, sol.ML, seed=21, amp=0.6)
+    Q = Q0.copy()
+    th = sol.shock_limit(Q)
+    assert np.array_equal(Q[:, :, 0], Q0[:, :, 0])
+    assert np.all((th >= 0) & (th <= 1)) and np.any(th < 1)
+    assert np.allclose(Q[:, :, 1:], th[:, None, None] * Q0[:, :, 1:], rtol=1e-15, atol=0)
+    # density is linear in Q: its limited point values lie in [m_i, M_i]
+    alpha = 5.0 * (1.0 / n) ** 1.5
+    rb = Q0[:, 0, 0].reshape(n, n)
+    nb = np.stack([np.roll(rb, 1, 0), np.roll(rb, -1, 0), np.roll(rb, 1, 1), np.roll(rb, -1, 1)])
+    Mx = np.maximum(rb + alpha, nb.max(0)).ravel(); Mn = np.minimum(rb - alpha, nb.min(0)).ravel()
+    r = sol.eval_limiter_points(Q)[..., 0]
+    assert np.all(r <= Mx[:, None] + 1e-13) and np.all(r >= Mn[:, None] - 1e-13)
+    # smooth, well-resolved data is left alone
+    sm = orc.Solver(orc.Mesh.cartesian(32, 32), 2, gamma=G)
+    Qs = sm.project_fn(synth.ic_smooth)
+    assert np.all(sm.shock_limit(Qs.copy()) == 1.0)
