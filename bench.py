@@ -1,0 +1,284 @@
+#!/usr/bin/env python
+"""Throughput of the LxW-DG time step on the GPU, in DOF-updates/s.
+
+A step is one pass of the whole hot path (moment limiter, wave speed, CK
+time-averaged flux and volume integral, edge fluxes, flux limiter, blended
+update, shock limiter) over the workload.  Default workload: 224x224 squares
+split into 100,352 jittered triangles (seeded +-20% vertex jitter), P2
+(24 DOF per element), two-rarefaction near-vacuum data, transparent
+boundaries, CFL 0.1 -- the unstructured-triangle configuration the metric is
+quoted on.  Inputs are synthetic and resident in HBM before timing; the L2
+is flushed (256 MB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica of the workload
+(the problems are independent; no collective on the data path) and the
+slowest rank's time counts.  --impl reference times the FP64 CPU oracle,
+the slow plain reference of this repository, on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "DOF-updates/s, LxW-DG Euler P2: mixed+learned vs plain FP64 GPU at equal L1 error"
+UNIT = "DOF-updates/s"
+
+WORKLOADS = {
+    "rarefy": dict(kind="tri", n=224, deg=2, cfl=0.1, ic=synth.ic_rarefy,
+                   desc="rarefaction: 224x224x2 = 100,352 jittered triangles, P2, rho=1 p=0.4 u=-+2, transparent"),
+    "blast": dict(kind="quad", n=1024, deg=2, cfl=0.1, ic=None, bc=(1, 1, 1, 1), box=(-1.1, 1.1, -1.1, 1.1),
+                  desc="blast: 1024x1024 Cartesian, P2, point energy 0.979264 in the 4 centre cells, reflective"),
+    "smooth": dict(kind="quad", n=32, deg=2, cfl=0.1, ic=synth.ic_smooth,
+                   desc="smooth: 32x32 periodic Cartesian, P2, advected density wave"),
+}
+
+# Algorithmic FP64 work per element of the CK kernel (P2): the modal <->
+# point contractions (q at 21 points 1008, two projections 1728, q_t and q_tt
+# at 21 points 2016 each, volume integral 864) plus the pointwise flux,
+# Jacobian and Hessian products and F_T assembly (~250 flop at each of 21
+# points).  Triangles (9 interior + 9 edge points) scale the point terms.
+def ck_flops_per_element(kind, deg):
+    ML = (deg + 1) * (deg + 2) // 2
+    NQ = (deg + 1) ** 2
+    NE = (4 if kind == "quad" else 3) * (deg + 1)
+    npt = NQ + NE
+    contract = 2 * 4 * ML * npt + 2 * 2 * 2 * 4 * ML * NQ + 2 * (2 * 2 * 4 * ML * npt) + 2 * 2 * 4 * ML * NQ
+    return contract + 250 * npt
+
+
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64 (derived, and the measured probe)
+# DRAM bytes per k_ck launch from the ncu capture summarised in profiles/ (None until captured
+# for the current kernel version)
+CK_TRAFFIC_BYTES = None
+
+
+def build_workload(L, name, stream):
+    w = WORKLOADS[name]
+    if w["kind"] == "tri":
+        xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
+        mesh = L.lxw_mesh_triangles(xy, tv)
+    else:
+        mesh = L.lxw_mesh_cartesian(w["n"], w["n"], w.get("box", (0.0, 1.0, 0.0, 1.0)), w.get("bc", (0, 0, 0, 0)))
+    sol = L.lxw_solver_create(mesh, w["deg"], stream=stream)
+    return w, sol
+
+
+def project(L, sol, w):
+    import torch
+    ic = w["ic"] or synth.ic_blast(w["n"])
+    xy = L.lxw_projection_points(sol)
+    r, u, v, p = ic(xy[..., 0], xy[..., 1])
+    prim = torch.from_numpy(np.stack(np.broadcast_arrays(r, u, v, p), axis=-1).copy()).cuda()
+    Q = torch.empty(sol.state_shape, dtype=torch.float64, device="cuda")
+    L.lxw_project(sol, prim, Q)
+    return Q
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.lines, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=lambda: [self.lines.append(l) for l in self.proc.stdout], daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(name, budget_s=10.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload."""
+    from oracle import oracle as O
+    w = WORKLOADS[name]
+    if w["kind"] == "tri":
+        xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
+        m = O.Mesh.triangles(xy, tv)
+    else:
+        m = O.Mesh.cartesian(w["n"], w["n"], w.get("box", (0.0, 1.0, 0.0, 1.0)), w.get("bc", (0, 0, 0, 0)))
+    s = O.Solver(m, w["deg"])
+    Q = s.project_fn(w["ic"] or synth.ic_blast(w["n"]))
+    s.step(Q, cfl=w["cfl"])          # untimed first step (page-in)
+    t0 = time.perf_counter(); k = 0
+    while k < 3 or (time.perf_counter() - t0 < budget_s and k < 400):
+        s.step(Q, cfl=w["cfl"]); k += 1
+    dt = time.perf_counter() - t0
+    dof = s.N * 4 * s.ML
+    return {"value": dof * k / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{k} full steps of the {name} workload ({s.N} elements) from its initial data, {dt:.1f} s"}, k, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    w = WORKLOADS[args.workload]
+    if w["kind"] == "tri":
+        xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
+        m = O.Mesh.triangles(xy, tv)
+    else:
+        m = O.Mesh.cartesian(w["n"], w["n"], w.get("box", (0.0, 1.0, 0.0, 1.0)), w.get("bc", (0, 0, 0, 0)))
+    s = O.Solver(m, w["deg"])
+    Q = s.project_fn(w["ic"] or synth.ic_blast(w["n"]))
+    for _ in range(args.warmup):
+        s.step(Q, cfl=w["cfl"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(Q, cfl=w["cfl"])
+    dt = time.perf_counter() - t0
+    val = s.N * 4 * s.ML * args.steps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w["desc"], "elements": s.N, "degree": w["deg"], "form": "FP64 CPU oracle"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                            "sample": f"{args.steps} full steps after {args.warmup} warm-up steps"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rarefy", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1601_08145_gb300 import build, lxw as L
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    w, sol = build_workload(L, args.workload, stream)
+    Q = project(L, sol, w)
+    dof = sol.N * 4 * sol.ML
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    for _ in range(max(args.warmup, 3)):
+        L.lxw_profile_step(sol, Q, w["cfl"])
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    phases = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        phases.append(L.lxw_profile_step(sol, Q, w["cfl"]))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [sum(p.values()) for p in phases]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    value = world * dof * args.steps / (total_ms / 1e3)
+    mean_phase = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+    dom = max(mean_phase, key=mean_phase.get)
+    flops = ck_flops_per_element(w["kind"], w["deg"]) * sol.N
+    ck_ms = mean_phase["ck"]
+    achieved = flops / (ck_ms / 1e3) / 1e12
+    roofline = {"kernel": "k_ck", "dominant_kernel": dom, "bound": "alu", "pipe": "fp64",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": CK_TRAFFIC_BYTES,
+                "algorithmic_flops_per_launch": flops, "launch_ms": ck_ms}
+
+    # end to end through the public C ABI on HOST memory: H2D of the state,
+    # one step, D2H of the result, every step
+    Qh = torch.empty(sol.state_shape, dtype=torch.float64).pin_memory()
+    Qh.copy_(Q.cpu())
+    L.lxw_run_host(sol, Qh, 1, w["cfl"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.lxw_run_host(sol, Qh, 1, w["cfl"])
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * dof * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": dof * 8,
+           "d2h_bytes_per_step": dof * 8}
+    if world > 1:
+        dist.barrier()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w["desc"], "elements": sol.N, "degree": w["deg"], "dof_per_step": dof,
+                      "form": "plain FP64 GPU", "cfl": w["cfl"],
+                      "l2": "flushed between timed steps (256 MB write)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "roofline": roofline,
+           "e2e": e2e,
+           "gpu_launches": args.steps * L.lxw_step_launches(sol),
+           "clocks": clk,
+           "phases_ms": mean_phase}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"], _, _ = cpu_baseline(args.workload)
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * lxw.h -- C ABI of the GB300 (sm_103a) library for one time step of the
+ * positivity-preserving Lax-Wendroff discontinuous Galerkin (LxW-DG) method
+ * for the 2D compressible Euler equations (Moe, Rossmanith & Seal,
+ * arXiv:1601.08145), on axis-aligned Cartesian and unstructured triangle
+ * meshes, polynomial degree 2 or 3.
+ *
+ * Every call returns lxw_status (LXW_OK = 0); no C++ exception crosses the
+ * boundary.  On failure lxw_last_error() returns a thread-local message.
+ * Pointers named *_dev are CUDA device pointers owned by the caller; *_host
+ * pointers are host memory owned by the caller.  Meshes and solvers are
+ * opaque, owned by the library and released by their destroy calls.
+ *
+ * State layout (Sec. 1.2, modal expansion q^h = sum_l Q^(l) phi^(l)):
+ *   Q[N][4][ML] doubles, element-major; variables (rho, rho u, rho v, E);
+ *   mode l = 0 is the cell average (phi^(1) = 1).  ML = 6 (P2) or 10 (P3).
+ *   Quadrilateral modes (reference square [-1,1]^2, normalised Legendre
+ *   L_n with (1/2) Int L_n^2 = 1): 1, L1(x), L1(y), L1(x)L1(y), L2(x),
+ *   L2(y) [, L3(x), L2(x)L1(y), L1(x)L2(y), L3(y)].  Triangle modes
+ *   (reference {x,y >= 0, x+y <= 1}): Gram-Schmidt of 1, x, y, x^2, xy,
+ *   y^2 [, x^3, x^2y, xy^2, y^3] under (1/|T0|) Int, positive leading term.
+ *
+ * Boundary codes: LXW_BC_PERIODIC (Cartesian, paired sides),
+ * LXW_BC_REFLECT (solid wall) and LXW_BC_TRANSPARENT (outflow), Sec. 2.4.
+ */
+#ifndef LXW_H
+#define LXW_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LXW_OK = 0,
+  LXW_ERR_ARG = 1,          /* invalid argument (message says which)              */
+  LXW_ERR_CUDA = 2,         /* a CUDA runtime call failed                          */
+  LXW_ERR_NONPOSITIVE = 3,  /* an input cell average had rho <= 0 or p <= 0        */
+  LXW_ERR_CFL = 4,          /* Gamma^rho < 0: dt above the low-order CFL bound      */
+  LXW_ERR_NAN = 5,          /* a non-finite value appeared in the state            */
+  LXW_ERR_BOUNDS = 6,       /* mesh connectivity out of range                      */
+  LXW_ERR_TIMEOUT = 7,      /* reserved: a bounded device wait gave up             */
+  LXW_ERR_NOMEM = 8         /* device or host allocation failed                    */
+} lxw_status;
+
+enum { LXW_BC_PERIODIC = 0, LXW_BC_REFLECT = 1, LXW_BC_TRANSPARENT = 2 };
+enum { LXW_KIND_QUAD = 0, LXW_KIND_TRI = 1 };
+enum { LXW_PREC_FP64 = 0 };
+
+/* device status bits (returned in lxw_diag.status) */
+enum { LXW_ST_NONPOSITIVE = 1, LXW_ST_CFL = 2, LXW_ST_NAN = 4 };
+
+typedef struct lxw_mesh lxw_mesh;
+typedef struct lxw_solver lxw_solver;
+
+/* Physics and method parameters.  Defaults (lxw_options_default):
+ * gamma 1.4 (Eq. eos), eps0 1e-12 (Sec. 3.1 Step 0), alpha0 500 (shock
+ * limiter alpha = alpha0 * dx^1.5, Sec. 4.1), shock limiter on, FP64. */
+typedef struct {
+  double gamma;
+  double eps0;
+  double alpha0;
+  int shock_limiter;
+  int precision;
+  int block_threads;        /* threads per CTA of the element kernels (0 = 128)   */
+  int reserved[9];
+} lxw_options;
+
+/* Per-step diagnostics (filled when a non-NULL pointer is passed). */
+typedef struct {
+  double s;                 /* global wave speed of the step (Eq. LLF)             */
+  double dt;                /* time step used                                       */
+  double min_rho, min_p;    /* minimum cell-average density / pressure after step  */
+  double mass, momx, momy, energy;  /* sum_i |T_i| Q^(1)_i after the step          */
+  double n_mom;             /* cells with moment-limiter theta < 1 (Sec. 3.1)       */
+  double n_edge;            /* edges with flux-limiter theta_e < 1 (Sec. 3.3)       */
+  double n_sc;              /* cells with shock-limiter theta < 1 (Sec. 4.1)        */
+  int status;               /* LXW_ST_* bits seen on the device during the step     */
+  int reserved;
+} lxw_diag;
+
+const char* lxw_last_error(void);
+lxw_status lxw_options_default(lxw_options* opt);
+
+/* --- meshes (Sec. 1.2: non-overlapping elements; Sec. 3.3: edge normals n_e
+ * with |n_e| = edge length, eps_ik, owner i_e = lower element index) ----- */
+
+/* nx*ny axis-aligned cells on [x0,x1]x[y0,y1]; element id = iy*nx + ix.
+ * bc[4] = codes of the (left, right, bottom, top) sides; periodic sides
+ * must be paired.  Errors: LXW_ERR_ARG. */
+lxw_status lxw_mesh_cartesian(int nx, int ny, double x0, double x1, double y0, double y1,
+                              const int bc[4], lxw_mesh** out);
+
+/* Triangles tv[nt][3] (counter-clockwise vertex ids into xy_host[nv][2]).
+ * ebc_host[nt][3] (nullable; default transparent) gives the boundary code
+ * of triangle-local edge k (vertex k -> k+1), read only on boundary edges.
+ * Errors: LXW_ERR_BOUNDS (vertex id), LXW_ERR_ARG (non-positive area,
+ * an edge shared by more than two triangles). */
+lxw_status lxw_mesh_triangles(int nv, const double* xy_host, int nt, const int* tv_host,
+                              const int* ebc_host, lxw_mesh** out);
+void lxw_mesh_destroy(lxw_mesh* mesh);
+int lxw_mesh_num_elements(const lxw_mesh* mesh);
+
+/* --- solver: tables, geometry and workspace on the device --------------- */
+
+/* degree 2 or 3.  stream: cudaStream_t (NULL = legacy default stream) on
+ * which every later call of this solver is enqueued.  Allocates all device
+ * memory the solver needs; later calls allocate nothing. */
+lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options* opt,
+                             void* stream, lxw_solver** out);
+void lxw_solver_destroy(lxw_solver* s);
+lxw_status lxw_solver_set_stream(lxw_solver* s, void* stream);
+/* N elements, E edges per element, ML modes, npts limiter points per element
+ * (interior + edge quadrature points), nproj projection points. */
+lxw_status lxw_solver_info(const lxw_solver* s, int* N, int* E, int* ML, int* npts, int* nproj);
+
+/* Physical coordinates of the initial-condition projection points
+ * xy_host[N][nproj][2] (Gauss rule with degree+3 points per direction). */
+lxw_status lxw_projection_points(const lxw_solver* s, double* xy_host);
+/* L2 projection Q^(l) = (1/|T0|) Int q phi^(l) (Sec. 1.2) of primitive values
+ * prim_dev[N][nproj][4] = (rho, u, v, p) at the projection points into
+ * Q_dev[N][4][ML]; the energy follows Eq. eos.  Asynchronous on the stream. */
+lxw_status lxw_project(lxw_solver* s, const double* prim_dev, double* Q_dev);
+
+/* --- the hot path --------------------------------------------------------- */
+
+/* One LxW-DG time step, in place on Q_dev[N][4][ML] (Sec. 3.3 Steps 1-6 and
+ * the shock-capturing limiter, outline Step 5):
+ *   moment limiter (Sec. 3.1) -> global wave speed s -> CK time-averaged flux
+ *   and volume integral (Sec. 2.2-2.3) -> LLF edge flux, f^LxW, f^LxF (Step 3)
+ *   -> flux limiter (Steps 4-5) -> blended update (Step 6) -> shock limiter.
+ * dt > 0 is used as given; dt <= 0 selects dt = cfl * min_i(2|T_i|/P_i) / s.
+ * theta_cell_dev (nullable) receives [2][N] = (moment theta, shock theta);
+ * theta_edge_dev (nullable) receives [N][E] theta_e seen from each element.
+ * diag_host (nullable) synchronises the stream and fills the diagnostics;
+ * with diag_host NULL the call is asynchronous and graph-capturable.
+ * Returns LXW_ERR_NONPOSITIVE / LXW_ERR_CFL / LXW_ERR_NAN only when diag_host
+ * is given and the device flagged the condition (the step still completes). */
+lxw_status lxw_step(lxw_solver* s, double* Q_dev, double dt, double cfl, lxw_diag* diag_host,
+                    double* theta_cell_dev, double* theta_edge_dev);
+
+/* nsteps steps with dt from cfl, replayed from a CUDA graph of one step
+ * captured on first use (the graph is rebuilt when Q_dev changes).  diag_host
+ * (nullable) receives the last step's diagnostics. */
+lxw_status lxw_run(lxw_solver* s, double* Q_dev, int nsteps, double cfl, lxw_diag* diag_host);
+
+/* End-to-end form of lxw_run on HOST memory: copies Q_host (pinned or
+ * pageable, [N][4][ML]) to the solver's device state, runs nsteps and copies
+ * the result back, synchronously. */
+lxw_status lxw_run_host(lxw_solver* s, double* Q_host, int nsteps, double cfl, lxw_diag* diag_host);
+
+/* Single phases of the step, for per-phase checks (same kernels as lxw_step):
+ * moment limiter on Q_dev in place (Sec. 3.1) with theta_dev[N] (nullable)
+ * and the global wave speed written to s_dev[0] (device double). */
+lxw_status lxw_moment_limit(lxw_solver* s, double* Q_dev, double* theta_dev, double* s_dev);
+/* shock-capturing limiter (Sec. 4.1) on Q_dev in place, theta_dev[N] nullable */
+lxw_status lxw_shock_limit(lxw_solver* s, double* Q_dev, double* theta_dev);
+
+/* Number of kernel launches one lxw_step enqueues (diag_host NULL). */
+int lxw_step_launches(const lxw_solver* s);
+
+/* lxw_step (dt from cfl, no diagnostics) with a CUDA event recorded on the
+ * solver's stream around each kernel; synchronises and writes the duration
+ * in milliseconds of each launch to ms_host[lxw_step_launches(s)] in launch
+ * order (reset, moment, ck, edge, update[, shock]).  Tracing aid: the events
+ * are created with the solver. */
+lxw_status lxw_profile_step(lxw_solver* s, double* Q_dev, double cfl, float* ms_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,596 @@
+// lxw_host.cpp -- host side of the library: quadrature and modal basis
+// tables, mesh connectivity and geometry, device memory of a solver, CUDA
+// graph replay, and the extern "C" entry points declared in include/lxw.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "lxw_internal.h"
+
+namespace lxw {
+void decode_diag(const double* raw, double out[9]);
+size_t diag_bytes();
+}  // namespace lxw
+
+using namespace lxw;
+
+namespace {
+
+thread_local std::string g_err;
+
+lxw_status fail(lxw_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define LXW_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(LXW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ------------------------------------------------------------- quadrature
+// Gauss-Legendre nodes on [-1,1]: Newton iteration on P_n from Tricomi's
+// asymptotic initial guesses, in long double; weights 2/((1-x^2) P_n'(x)^2).
+// The lower half is computed and mirrored, so x[n-1-i] = -x[i] exactly.
+void legendre_eval(int n, long double x, long double& p, long double& dp) {
+  long double a = 1.0L, b = x;
+  if (n == 0) { p = 1.0L; dp = 0.0L; return; }
+  for (int k = 1; k < n; ++k) {
+    long double c = ((2 * k + 1) * x * b - k * a) / (k + 1);
+    a = b; b = c;
+  }
+  p = b;
+  dp = n * (a - x * b) / (1.0L - x * x);
+}
+
+void gauss_legendre(int n, double* x, double* w) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < n / 2 + n % 2; ++i) {
+    long double th = pi * (4 * (i + 1) - 1) / (4 * n + 2);
+    long double z = (1.0L - (n - 1.0L) / (8.0L * n * n * n)) * cosl(th);
+    for (int it = 0; it < 50; ++it) {
+      long double p, dp;
+      legendre_eval(n, z, p, dp);
+      long double step = p / dp;
+      z -= step;
+      if (fabsl(step) < 1e-30L) break;
+    }
+    long double p, dp;
+    legendre_eval(n, z, p, dp);
+    long double wi = 2.0L / ((1.0L - z * z) * dp * dp);
+    x[i] = (double)(-z); x[n - 1 - i] = (double)z;
+    w[i] = (double)wi; w[n - 1 - i] = (double)wi;
+  }
+  if (n % 2) x[n / 2] = 0.0;
+}
+
+// normalised Legendre value/derivative, (1/2) Int_{-1}^{1} L_n^2 = 1
+void legendre_norm(int n, double x, double& v, double& d) {
+  long double p, dp;
+  legendre_eval(n, x, p, dp);
+  if (n == 0) dp = 0.0L;
+  // derivative at |x| = 1 would divide by zero; the tables never sample there
+  long double s = sqrtl(2.0L * n + 1.0L);
+  v = (double)(s * p);
+  d = (double)(s * dp);
+}
+
+// interior rule with n points per direction, weights summing to 1
+int interior_rule(int kind, int n, double* xi, double* eta, double* w) {
+  double g[8], gw[8];
+  gauss_legendre(n, g, gw);
+  int c = 0;
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b, ++c) {
+      if (kind == LXW_KIND_QUAD) {
+        xi[c] = g[a]; eta[c] = g[b]; w[c] = 0.25 * gw[a] * gw[b];
+      } else {
+        // collapsed coordinates x = u, y = v (1 - u) on the reference triangle
+        double u = 0.5 + 0.5 * g[a], v = 0.5 + 0.5 * g[b];
+        xi[c] = u; eta[c] = v * (1.0 - u);
+        w[c] = 0.5 * gw[a] * gw[b] * (1.0 - u);
+      }
+    }
+  return c;
+}
+
+// ------------------------------------------------------------ modal basis
+// Quadrilateral: products of normalised Legendre polynomials, ordered by
+// total degree: (0,0),(1,0),(0,1),(1,1),(2,0),(0,2),(3,0),(2,1),(1,2),(0,3).
+// Triangle: the monomials 1,x,y,x^2,xy,y^2,x^3,x^2y,xy^2,y^3 orthonormalised
+// in that order under (1/|T0|) Int_T0 (the Cholesky factor of their exact
+// Gram matrix, 2 a! b!/(a+b+2)!), computed in long double.
+const int kQA[10] = {0, 1, 0, 1, 2, 0, 3, 2, 1, 0};
+const int kQB[10] = {0, 0, 1, 1, 0, 2, 0, 1, 2, 3};
+const int kMA[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+const int kMB[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+
+struct TriBasis { double c[kMaxML][kMaxML]; };  // phi_l = sum_j c[l][j] m_j
+
+TriBasis triangle_basis(int ML) {
+  long double G[kMaxML][kMaxML], L[kMaxML][kMaxML] = {};
+  auto fac = [](int n) { long double f = 1.0L; for (int k = 2; k <= n; ++k) f *= k; return f; };
+  for (int a = 0; a < ML; ++a)
+    for (int b = 0; b < ML; ++b) {
+      int p = kMA[a] + kMA[b], q = kMB[a] + kMB[b];
+      G[a][b] = 2.0L * fac(p) * fac(q) / fac(p + q + 2);
+    }
+  // G = L L^T
+  for (int r = 0; r < ML; ++r)
+    for (int col = 0; col <= r; ++col) {
+      long double s = G[r][col];
+      for (int k = 0; k < col; ++k) s -= L[r][k] * L[col][k];
+      L[r][col] = (r == col) ? sqrtl(s) : s / L[col][col];
+    }
+  // rows of L^{-1} are the coefficients of the orthonormal polynomials
+  long double Li[kMaxML][kMaxML] = {};
+  for (int col = 0; col < ML; ++col) {
+    for (int r = 0; r < ML; ++r) {
+      long double s = (r == col) ? 1.0L : 0.0L;
+      for (int k = 0; k < r; ++k) s -= L[r][k] * Li[k][col];
+      Li[r][col] = s / L[r][r];
+    }
+  }
+  TriBasis tb{};
+  for (int l = 0; l < ML; ++l)
+    for (int j = 0; j < ML; ++j) tb.c[l][j] = (double)Li[l][j];
+  return tb;
+}
+
+void basis_at(int kind, int ML, const TriBasis& tb, double x, double y, double* phi, double* dx, double* dy) {
+  for (int l = 0; l < ML; ++l) {
+    if (kind == LXW_KIND_QUAD) {
+      double a, da, b, db;
+      legendre_norm(kQA[l], x, a, da);
+      legendre_norm(kQB[l], y, b, db);
+      phi[l] = a * b; if (dx) dx[l] = da * b; if (dy) dy[l] = a * db;
+    } else {
+      double v = 0.0, vx = 0.0, vy = 0.0;
+      for (int j = 0; j < ML; ++j) {
+        int pa = kMA[j], pb = kMB[j];
+        double xa = 1.0, yb = 1.0, xa1 = 0.0, yb1 = 0.0;
+        for (int k = 0; k < pa; ++k) { xa1 = (k == pa - 1) ? xa * pa : xa1; xa *= x; }
+        for (int k = 0; k < pb; ++k) { yb1 = (k == pb - 1) ? yb * pb : yb1; yb *= y; }
+        v += tb.c[l][j] * xa * yb;
+        vx += tb.c[l][j] * xa1 * yb;
+        vy += tb.c[l][j] * xa * yb1;
+      }
+      phi[l] = v; if (dx) dx[l] = vx; if (dy) dy[l] = vy;
+    }
+  }
+}
+
+const double kQuadV[4][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}};
+const double kTriV[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+
+void build_tables(int kind, int deg, Tables& t, ProjTables& pt) {
+  std::memset(&t, 0, sizeof(t));
+  std::memset(&pt, 0, sizeof(pt));
+  const int ML = (deg + 1) * (deg + 2) / 2, n = deg + 1;
+  const int E = kind == LXW_KIND_QUAD ? 4 : 3;
+  TriBasis tb = kind == LXW_KIND_TRI ? triangle_basis(ML) : TriBasis{};
+  t.ML = ML; t.E = E; t.MQ = n;
+  double xi[kMaxPts], eta[kMaxPts], w[kMaxQ];
+  t.NQ = interior_rule(kind, n, xi, eta, w);
+  for (int k = 0; k < t.NQ; ++k) t.w[k] = w[k];
+  double g[8], gw[8];
+  gauss_legendre(n, g, gw);
+  for (int p = 0; p < n; ++p) t.ew[p] = gw[p];
+  const double(*V)[2] = kind == LXW_KIND_QUAD ? kQuadV : kTriV;
+  for (int k = 0; k < E; ++k)
+    for (int p = 0; p < n; ++p) {
+      double s = 0.5 * (g[p] + 1.0);
+      int idx = t.NQ + k * n + p;
+      xi[idx] = V[k][0] + s * (V[(k + 1) % E][0] - V[k][0]);
+      eta[idx] = V[k][1] + s * (V[(k + 1) % E][1] - V[k][1]);
+    }
+  t.NPT = t.NQ + E * n;
+  for (int p = 0; p < t.NPT; ++p) basis_at(kind, ML, tb, xi[p], eta[p], t.phi[p], t.dxi[p], t.deta[p]);
+  // projection rule: deg + 3 points per direction
+  double pxi[kMaxProj], peta[kMaxProj], pw[kMaxProj];
+  pt.ML = ML;
+  pt.NPJ = interior_rule(kind, deg + 3, pxi, peta, pw);
+  t.NPJ = pt.NPJ;
+  for (int p = 0; p < pt.NPJ; ++p) {
+    pt.w[p] = pw[p];
+    basis_at(kind, ML, tb, pxi[p], peta[p], pt.phi[p], nullptr, nullptr);
+  }
+}
+
+void projection_reference_points(int kind, int deg, std::vector<double>& xi, std::vector<double>& eta) {
+  double a[kMaxProj], b[kMaxProj], w[kMaxProj];
+  int n = interior_rule(kind, deg + 3, a, b, w);
+  xi.assign(a, a + n); eta.assign(b, b + n);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ mesh
+struct lxw_mesh {
+  int kind, N, E;
+  std::vector<double> vx;   // [N][E][2]
+  std::vector<int> nbr;     // [N][E]: neighbour or -1 - bc
+  std::vector<int> nbk;     // [N][E]
+};
+
+struct lxw_solver {
+  int kind, deg, N, E, ML;
+  lxw_options opt;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  Tables tab;
+  ProjTables ptab;
+  DevMesh dm{};
+  DevWork dw{};
+  std::vector<void*> allocs;
+  double* Qdev = nullptr;        // state buffer of lxw_run_host
+  double* host_diag = nullptr;   // pinned
+  std::vector<double> xproj;     // [N][NPJ][2]
+  cudaGraphExec_t graph = nullptr;
+  double* graph_Q = nullptr;
+  double graph_cfl = 0.0;
+  void* events[8] = {};          // cudaEvent_t of lxw_profile_step
+  ~lxw_solver() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (void* e : events) if (e) cudaEventDestroy((cudaEvent_t)e);
+    for (void* p : allocs) cudaFree(p);
+    if (host_diag) cudaFreeHost(host_diag);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+};
+
+extern "C" {
+
+const char* lxw_last_error(void) { return g_err.c_str(); }
+
+lxw_status lxw_options_default(lxw_options* opt) {
+  if (!opt) return fail(LXW_ERR_ARG, "lxw_options_default: null");
+  std::memset(opt, 0, sizeof(*opt));
+  opt->gamma = 1.4;
+  opt->eps0 = 1e-12;
+  opt->alpha0 = 500.0;
+  opt->shock_limiter = 1;
+  opt->precision = LXW_PREC_FP64;
+  opt->block_threads = 128;
+  return LXW_OK;
+}
+
+lxw_status lxw_mesh_cartesian(int nx, int ny, double x0, double x1, double y0, double y1, const int bc[4],
+                              lxw_mesh** out) {
+  if (!out || !bc) return fail(LXW_ERR_ARG, "lxw_mesh_cartesian: null argument");
+  if (nx < 1 || ny < 1 || !(x1 > x0) || !(y1 > y0)) return fail(LXW_ERR_ARG, "lxw_mesh_cartesian: bad size or box");
+  for (int k = 0; k < 4; ++k)
+    if (bc[k] < 0 || bc[k] > 2) return fail(LXW_ERR_ARG, "lxw_mesh_cartesian: bad boundary code");
+  if ((bc[0] == LXW_BC_PERIODIC) != (bc[1] == LXW_BC_PERIODIC) || (bc[2] == LXW_BC_PERIODIC) != (bc[3] == LXW_BC_PERIODIC))
+    return fail(LXW_ERR_ARG, "lxw_mesh_cartesian: periodic sides must be paired");
+  lxw_mesh* m = new (std::nothrow) lxw_mesh;
+  if (!m) return fail(LXW_ERR_NOMEM, "lxw_mesh_cartesian: out of memory");
+  m->kind = LXW_KIND_QUAD; m->N = nx * ny; m->E = 4;
+  m->vx.resize((size_t)m->N * 8); m->nbr.resize((size_t)m->N * 4); m->nbk.resize((size_t)m->N * 4);
+  std::vector<double> X(nx + 1), Y(ny + 1);
+  for (int a = 0; a <= nx; ++a) X[a] = x0 + (x1 - x0) * a / nx;
+  for (int b = 0; b <= ny; ++b) Y[b] = y0 + (y1 - y0) * b / ny;
+  // local edges counter-clockwise from the lower-left vertex: bottom, right, top, left
+  const int side_bc[4] = {bc[2], bc[1], bc[3], bc[0]};
+  const int opposite[4] = {2, 3, 0, 1};
+  for (int iy = 0; iy < ny; ++iy)
+    for (int ix = 0; ix < nx; ++ix) {
+      const int e = iy * nx + ix;
+      double* v = &m->vx[(size_t)e * 8];
+      v[0] = X[ix]; v[1] = Y[iy]; v[2] = X[ix + 1]; v[3] = Y[iy]; v[4] = X[ix + 1]; v[5] = Y[iy + 1]; v[6] = X[ix]; v[7] = Y[iy + 1];
+      int jx[4] = {ix, ix + 1, ix, ix - 1}, jy[4] = {iy - 1, iy, iy + 1, iy};
+      for (int k = 0; k < 4; ++k) {
+        int a = jx[k], b = jy[k];
+        bool inside = a >= 0 && a < nx && b >= 0 && b < ny;
+        if (!inside && side_bc[k] == LXW_BC_PERIODIC) { a = (a + nx) % nx; b = (b + ny) % ny; inside = true; }
+        m->nbr[(size_t)e * 4 + k] = inside ? b * nx + a : -1 - side_bc[k];
+        m->nbk[(size_t)e * 4 + k] = inside ? opposite[k] : -1;
+      }
+    }
+  *out = m;
+  return LXW_OK;
+}
+
+lxw_status lxw_mesh_triangles(int nv, const double* xy, int nt, const int* tv, const int* ebc, lxw_mesh** out) {
+  if (!out || !xy || !tv || nv < 3 || nt < 1) return fail(LXW_ERR_ARG, "lxw_mesh_triangles: bad argument");
+  lxw_mesh* m = new (std::nothrow) lxw_mesh;
+  if (!m) return fail(LXW_ERR_NOMEM, "lxw_mesh_triangles: out of memory");
+  m->kind = LXW_KIND_TRI; m->N = nt; m->E = 3;
+  m->vx.resize((size_t)nt * 6); m->nbr.assign((size_t)nt * 3, 0); m->nbk.assign((size_t)nt * 3, -1);
+  std::unordered_map<uint64_t, int> open;   // undirected edge -> first (element*3 + k)
+  open.reserve((size_t)nt * 2);
+  for (int e = 0; e < nt; ++e) {
+    for (int k = 0; k < 3; ++k) {
+      int a = tv[3 * e + k];
+      if (a < 0 || a >= nv) { delete m; return fail(LXW_ERR_BOUNDS, "lxw_mesh_triangles: vertex id out of range"); }
+      m->vx[(size_t)e * 6 + 2 * k] = xy[2 * a];
+      m->vx[(size_t)e * 6 + 2 * k + 1] = xy[2 * a + 1];
+    }
+    const double* v = &m->vx[(size_t)e * 6];
+    double det = (v[2] - v[0]) * (v[5] - v[1]) - (v[4] - v[0]) * (v[3] - v[1]);
+    if (!(det > 0.0)) { delete m; return fail(LXW_ERR_ARG, "lxw_mesh_triangles: triangle " + std::to_string(e) + " is not counter-clockwise"); }
+    for (int k = 0; k < 3; ++k) {
+      uint32_t a = (uint32_t)tv[3 * e + k], b = (uint32_t)tv[3 * e + (k + 1) % 3];
+      uint64_t key = a < b ? ((uint64_t)a << 32 | b) : ((uint64_t)b << 32 | a);
+      auto it = open.find(key);
+      if (it == open.end()) {
+        open.emplace(key, e * 3 + k);
+      } else {
+        int o = it->second;
+        if (o < 0) { delete m; return fail(LXW_ERR_ARG, "lxw_mesh_triangles: edge shared by more than two triangles"); }
+        int oe = o / 3, ok = o % 3;
+        m->nbr[(size_t)e * 3 + k] = oe; m->nbk[(size_t)e * 3 + k] = ok;
+        m->nbr[(size_t)oe * 3 + ok] = e; m->nbk[(size_t)oe * 3 + ok] = k;
+        it->second = -1;
+      }
+    }
+  }
+  for (auto& kv : open)
+    if (kv.second >= 0) {
+      int e = kv.second / 3, k = kv.second % 3;
+      int code = ebc ? ebc[kv.second] : LXW_BC_TRANSPARENT;
+      if (code != LXW_BC_REFLECT && code != LXW_BC_TRANSPARENT) { delete m; return fail(LXW_ERR_ARG, "lxw_mesh_triangles: boundary edges need a reflective or transparent code"); }
+      m->nbr[(size_t)e * 3 + k] = -1 - code;
+      m->nbk[(size_t)e * 3 + k] = -1;
+    }
+  *out = m;
+  return LXW_OK;
+}
+
+void lxw_mesh_destroy(lxw_mesh* m) { delete m; }
+int lxw_mesh_num_elements(const lxw_mesh* m) { return m ? m->N : 0; }
+
+lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options* optp, void* stream, lxw_solver** out) {
+  if (!mesh || !out) return fail(LXW_ERR_ARG, "lxw_solver_create: null argument");
+  if (degree != 2 && degree != 3) return fail(LXW_ERR_ARG, "lxw_solver_create: degree must be 2 or 3");
+  lxw_options opt;
+  if (optp) opt = *optp; else lxw_options_default(&opt);
+  if (!(opt.gamma > 1.0)) return fail(LXW_ERR_ARG, "lxw_solver_create: gamma must exceed 1");
+  if (opt.precision != LXW_PREC_FP64) return fail(LXW_ERR_ARG, "lxw_solver_create: unsupported precision");
+  if (opt.block_threads <= 0) opt.block_threads = 128;
+  if (opt.block_threads % 32 || opt.block_threads > 1024) return fail(LXW_ERR_ARG, "lxw_solver_create: block_threads must be a multiple of 32 <= 1024");
+  lxw_solver* s = new (std::nothrow) lxw_solver;
+  if (!s) return fail(LXW_ERR_NOMEM, "lxw_solver_create: out of memory");
+  s->kind = mesh->kind; s->deg = degree; s->N = mesh->N; s->E = mesh->E; s->opt = opt;
+  s->stream = (cudaStream_t)stream;
+  build_tables(mesh->kind, degree, s->tab, s->ptab);
+  s->ML = s->tab.ML;
+  const int N = s->N, E = s->E, MQ = s->tab.MQ;
+
+  // geometry (affine map of the reference element) on the host
+  std::vector<double> area(N), jinv((size_t)4 * N), nrm((size_t)E * 2 * N), sdx(N);
+  std::vector<int> nbr((size_t)E * N), nbk((size_t)E * N);
+  double hmin = 1e300;
+  s->xproj.resize((size_t)N * s->ptab.NPJ * 2);
+  std::vector<double> pxi, peta;
+  projection_reference_points(mesh->kind, degree, pxi, peta);
+  for (int e = 0; e < N; ++e) {
+    const double* v = &mesh->vx[(size_t)e * E * 2];
+    double o[2], J[4];
+    if (mesh->kind == LXW_KIND_QUAD) {
+      // x = centre + diag(hx/2, hy/2) xi on [-1,1]^2
+      o[0] = 0.5 * (v[0] + v[2]); o[1] = 0.5 * (v[1] + v[7]);
+      J[0] = 0.5 * (v[2] - v[0]); J[1] = 0.0; J[2] = 0.0; J[3] = 0.5 * (v[7] - v[1]);
+    } else {
+      o[0] = v[0]; o[1] = v[1];
+      J[0] = v[2] - v[0]; J[1] = v[4] - v[0]; J[2] = v[3] - v[1]; J[3] = v[5] - v[1];
+    }
+    const double det = J[0] * J[3] - J[1] * J[2];
+    jinv[e] = J[3] / det; jinv[N + e] = -J[1] / det; jinv[2 * (size_t)N + e] = -J[2] / det; jinv[3 * (size_t)N + e] = J[0] / det;
+    area[e] = (mesh->kind == LXW_KIND_QUAD ? 4.0 : 0.5) * det;
+    double P = 0.0;
+    for (int k = 0; k < E; ++k) {
+      const int k1 = (k + 1) % E;
+      const double nx = v[2 * k1 + 1] - v[2 * k + 1], ny = -(v[2 * k1] - v[2 * k]);
+      nrm[(size_t)(2 * k) * N + e] = nx; nrm[(size_t)(2 * k + 1) * N + e] = ny;
+      P += std::sqrt(nx * nx + ny * ny);
+      nbr[(size_t)k * N + e] = mesh->nbr[(size_t)e * E + k];
+      nbk[(size_t)k * N + e] = mesh->nbk[(size_t)e * E + k];
+    }
+    hmin = std::fmin(hmin, 2.0 * area[e] / P);
+    sdx[e] = mesh->kind == LXW_KIND_QUAD ? 2.0 * J[0] : std::sqrt(2.0 * area[e]);
+    for (int p = 0; p < s->ptab.NPJ; ++p) {
+      s->xproj[((size_t)e * s->ptab.NPJ + p) * 2] = o[0] + J[0] * pxi[p] + J[1] * peta[p];
+      s->xproj[((size_t)e * s->ptab.NPJ + p) * 2 + 1] = o[1] + J[2] * pxi[p] + J[3] * peta[p];
+    }
+  }
+  auto dalloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    s->allocs.push_back(p);
+    return p;
+  };
+  double* d_area = (double*)dalloc(sizeof(double) * N);
+  double* d_jinv = (double*)dalloc(sizeof(double) * 4 * N);
+  double* d_nrm = (double*)dalloc(sizeof(double) * E * 2 * N);
+  double* d_sdx = (double*)dalloc(sizeof(double) * N);
+  int* d_nbr = (int*)dalloc(sizeof(int) * E * N);
+  int* d_nbk = (int*)dalloc(sizeof(int) * E * N);
+  s->dw.trace = (double*)dalloc(sizeof(double) * (size_t)E * MQ * 8 * N);
+  s->dw.flux = (double*)dalloc(sizeof(double) * (size_t)E * 8 * N);
+  s->dw.prop = (double*)dalloc(sizeof(double) * (size_t)E * N);
+  s->dw.smax = (unsigned long long*)dalloc(sizeof(unsigned long long));
+  s->dw.status = (unsigned int*)dalloc(sizeof(unsigned int));
+  s->dw.diag = (double*)dalloc(diag_bytes());
+  s->Qdev = (double*)dalloc(sizeof(double) * (size_t)N * 4 * s->ML);
+  if (!d_area || !d_jinv || !d_nrm || !d_sdx || !d_nbr || !d_nbk || !s->dw.trace || !s->dw.flux || !s->dw.prop ||
+      !s->dw.smax || !s->dw.status || !s->dw.diag || !s->Qdev) {
+    delete s;
+    return fail(LXW_ERR_NOMEM, "lxw_solver_create: device allocation failed");
+  }
+  if (cudaMallocHost(&s->host_diag, 64 * sizeof(double)) != cudaSuccess) {
+    s->host_diag = nullptr; delete s;
+    return fail(LXW_ERR_NOMEM, "lxw_solver_create: pinned allocation failed");
+  }
+  for (auto& e : s->events) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) { delete s; return fail(LXW_ERR_CUDA, "lxw_solver_create: event creation failed"); }
+    e = ev;
+  }
+  if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    s->cap_stream = nullptr; delete s;
+    return fail(LXW_ERR_CUDA, "lxw_solver_create: stream creation failed");
+  }
+  cudaError_t e1 = cudaMemcpy(d_area, area.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
+  cudaError_t e2 = cudaMemcpy(d_jinv, jinv.data(), sizeof(double) * 4 * N, cudaMemcpyHostToDevice);
+  cudaError_t e3 = cudaMemcpy(d_nrm, nrm.data(), sizeof(double) * E * 2 * N, cudaMemcpyHostToDevice);
+  cudaError_t e4 = cudaMemcpy(d_sdx, sdx.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
+  cudaError_t e5 = cudaMemcpy(d_nbr, nbr.data(), sizeof(int) * E * N, cudaMemcpyHostToDevice);
+  cudaError_t e6 = cudaMemcpy(d_nbk, nbk.data(), sizeof(int) * E * N, cudaMemcpyHostToDevice);
+  if (e1 || e2 || e3 || e4 || e5 || e6 || upload_tables(s->kind, degree, s->tab)) {
+    delete s;
+    return fail(LXW_ERR_CUDA, "lxw_solver_create: upload failed");
+  }
+  s->dm.N = N; s->dm.E = E; s->dm.area = d_area; s->dm.jinv = d_jinv; s->dm.nrm = d_nrm; s->dm.sdx = d_sdx;
+  s->dm.nbr = d_nbr; s->dm.nbk = d_nbk; s->dm.hmin = hmin;
+  *out = s;
+  return LXW_OK;
+}
+
+void lxw_solver_destroy(lxw_solver* s) { delete s; }
+
+lxw_status lxw_solver_set_stream(lxw_solver* s, void* stream) {
+  if (!s) return fail(LXW_ERR_ARG, "lxw_solver_set_stream: null solver");
+  s->stream = (cudaStream_t)stream;
+  return LXW_OK;
+}
+
+lxw_status lxw_solver_info(const lxw_solver* s, int* N, int* E, int* ML, int* npts, int* nproj) {
+  if (!s) return fail(LXW_ERR_ARG, "lxw_solver_info: null solver");
+  if (N) *N = s->N;
+  if (E) *E = s->E;
+  if (ML) *ML = s->ML;
+  if (npts) *npts = s->tab.NPT;
+  if (nproj) *nproj = s->ptab.NPJ;
+  return LXW_OK;
+}
+
+lxw_status lxw_projection_points(const lxw_solver* s, double* xy) {
+  if (!s || !xy) return fail(LXW_ERR_ARG, "lxw_projection_points: null argument");
+  std::memcpy(xy, s->xproj.data(), sizeof(double) * s->xproj.size());
+  return LXW_OK;
+}
+
+lxw_status lxw_project(lxw_solver* s, const double* prim, double* Q) {
+  if (!s || !prim || !Q) return fail(LXW_ERR_ARG, "lxw_project: null argument");
+  if (launch_project(s->ptab, s->N, s->opt.gamma, prim, Q, s->stream)) return fail(LXW_ERR_CUDA, "lxw_project: launch failed");
+  return LXW_OK;
+}
+
+static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_diag, double* tc, double* te) {
+  StepArgs a{};
+  a.dt_in = dt; a.cfl = cfl; a.gamma = s->opt.gamma; a.eps0 = s->opt.eps0; a.alpha0 = s->opt.alpha0;
+  a.shock_limiter = s->opt.shock_limiter; a.want_diag = want_diag; a.theta_cell = tc; a.theta_edge = te;
+  return a;
+}
+
+static lxw_status read_diag(lxw_solver* s, double dt, double cfl, lxw_diag* d) {
+  double* h = s->host_diag;
+  LXW_CUDA(cudaMemcpyAsync(h, s->dw.diag, diag_bytes(), cudaMemcpyDeviceToHost, s->stream));
+  LXW_CUDA(cudaMemcpyAsync(h + 32, s->dw.smax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream));
+  LXW_CUDA(cudaMemcpyAsync(h + 33, s->dw.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s->stream));
+  LXW_CUDA(cudaStreamSynchronize(s->stream));
+  double v[9];
+  decode_diag(h, v);
+  std::memset(d, 0, sizeof(*d));
+  double sp;
+  std::memcpy(&sp, h + 32, sizeof(double));
+  unsigned int st;
+  std::memcpy(&st, h + 33, sizeof(unsigned int));
+  d->s = sp;
+  d->dt = dt > 0.0 ? dt : cfl * s->dm.hmin / sp;
+  d->mass = v[0]; d->momx = v[1]; d->momy = v[2]; d->energy = v[3];
+  d->min_rho = v[4]; d->min_p = v[5];
+  d->n_mom = v[6]; d->n_edge = v[7]; d->n_sc = v[8];
+  d->status = (int)st;
+  if (st & LXW_ST_NONPOSITIVE) return fail(LXW_ERR_NONPOSITIVE, "lxw_step: non-positive cell average at step start");
+  if (st & LXW_ST_CFL) return fail(LXW_ERR_CFL, "lxw_step: Gamma^rho < 0 (dt above the low-order CFL bound)");
+  if (st & LXW_ST_NAN) return fail(LXW_ERR_NAN, "lxw_step: non-finite state");
+  return LXW_OK;
+}
+
+lxw_status lxw_step(lxw_solver* s, double* Q, double dt, double cfl, lxw_diag* diag, double* theta_cell,
+                    double* theta_edge) {
+  if (!s || !Q) return fail(LXW_ERR_ARG, "lxw_step: null argument");
+  if (!(dt > 0.0) && !(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_step: need dt > 0 or cfl > 0");
+  StepArgs a = make_args(s, dt, cfl, diag != nullptr, theta_cell, theta_edge);
+  if (launch_step(s->kind, s->deg, s->dm, s->dw, Q, a, s->stream, s->opt.block_threads))
+    return fail(LXW_ERR_CUDA, std::string("lxw_step: launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+  if (diag) return read_diag(s, dt, cfl, diag);
+  return LXW_OK;
+}
+
+lxw_status lxw_run(lxw_solver* s, double* Q, int nsteps, double cfl, lxw_diag* diag) {
+  if (!s || !Q || nsteps < 0) return fail(LXW_ERR_ARG, "lxw_run: bad argument");
+  if (!(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_run: cfl must be positive");
+  if (nsteps == 0) return LXW_OK;
+  int body = diag ? nsteps - 1 : nsteps;
+  if (body > 0) {
+    if (!s->graph || s->graph_Q != Q || s->graph_cfl != cfl) {
+      if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+      StepArgs a = make_args(s, 0.0, cfl, 0, nullptr, nullptr);
+      cudaGraph_t g = nullptr;
+      LXW_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+      int rc = launch_step(s->kind, s->deg, s->dm, s->dw, Q, a, s->cap_stream, s->opt.block_threads);
+      cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
+      if (rc || ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail(LXW_ERR_CUDA, "lxw_run: graph capture failed"); }
+      cudaError_t ie = cudaGraphInstantiate(&s->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) { s->graph = nullptr; return fail(LXW_ERR_CUDA, "lxw_run: graph instantiation failed"); }
+      s->graph_Q = Q; s->graph_cfl = cfl;
+    }
+    for (int k = 0; k < body; ++k) LXW_CUDA(cudaGraphLaunch(s->graph, s->stream));
+  }
+  if (diag) return lxw_step(s, Q, 0.0, cfl, diag, nullptr, nullptr);
+  return LXW_OK;
+}
+
+lxw_status lxw_run_host(lxw_solver* s, double* Qh, int nsteps, double cfl, lxw_diag* diag) {
+  if (!s || !Qh) return fail(LXW_ERR_ARG, "lxw_run_host: null argument");
+  const size_t bytes = sizeof(double) * (size_t)s->N * 4 * s->ML;
+  LXW_CUDA(cudaMemcpyAsync(s->Qdev, Qh, bytes, cudaMemcpyHostToDevice, s->stream));
+  lxw_status st = lxw_run(s, s->Qdev, nsteps, cfl, diag);
+  if (st != LXW_OK && st != LXW_ERR_NONPOSITIVE && st != LXW_ERR_CFL && st != LXW_ERR_NAN) return st;
+  LXW_CUDA(cudaMemcpyAsync(Qh, s->Qdev, bytes, cudaMemcpyDeviceToHost, s->stream));
+  LXW_CUDA(cudaStreamSynchronize(s->stream));
+  return st;
+}
+
+lxw_status lxw_moment_limit(lxw_solver* s, double* Q, double* theta, double* s_dev) {
+  if (!s || !Q) return fail(LXW_ERR_ARG, "lxw_moment_limit: null argument");
+  StepArgs a = make_args(s, 0.0, 0.0, 0, nullptr, nullptr);
+  if (launch_moment_limit(s->kind, s->deg, s->dm, s->dw, Q, a, theta, s->stream, s->opt.block_threads))
+    return fail(LXW_ERR_CUDA, "lxw_moment_limit: launch failed");
+  if (s_dev && launch_copy_speed(s->dw, s_dev, s->stream)) return fail(LXW_ERR_CUDA, "lxw_moment_limit: launch failed");
+  return LXW_OK;
+}
+
+lxw_status lxw_shock_limit(lxw_solver* s, double* Q, double* theta) {
+  if (!s || !Q) return fail(LXW_ERR_ARG, "lxw_shock_limit: null argument");
+  StepArgs a = make_args(s, 0.0, 0.0, 0, nullptr, nullptr);
+  if (launch_shock_limit(s->kind, s->deg, s->dm, Q, a, theta, s->stream, s->opt.block_threads))
+    return fail(LXW_ERR_CUDA, "lxw_shock_limit: launch failed");
+  return LXW_OK;
+}
+
+int lxw_step_launches(const lxw_solver* s) { return s ? step_launch_count(0, s->opt.shock_limiter) : 0; }
+
+lxw_status lxw_profile_step(lxw_solver* s, double* Q, double cfl, float* ms) {
+  if (!s || !Q || !ms || !(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_profile_step: bad argument");
+  StepArgs a = make_args(s, 0.0, cfl, 0, nullptr, nullptr);
+  if (launch_step(s->kind, s->deg, s->dm, s->dw, Q, a, s->stream, s->opt.block_threads, s->events))
+    return fail(LXW_ERR_CUDA, "lxw_profile_step: launch failed");
+  const int n = step_launch_count(0, s->opt.shock_limiter);
+  LXW_CUDA(cudaEventSynchronize((cudaEvent_t)s->events[n]));
+  for (int k = 0; k < n; ++k) LXW_CUDA(cudaEventElapsedTime(&ms[k], (cudaEvent_t)s->events[k], (cudaEvent_t)s->events[k + 1]));
+  return LXW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// lxw_internal.h -- data structures shared by the library's host code
+// (lxw_host.cpp) and its CUDA kernels (lxw_kernels.cu).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/lxw.h"
+
+namespace lxw {
+
+constexpr int kMaxML = 10;
+constexpr int kMaxQ = 16;     // interior points (degree 3: 4 x 4)
+constexpr int kMaxMQ = 4;     // points per edge
+constexpr int kMaxE = 4;
+constexpr int kMaxPts = kMaxQ + kMaxE * kMaxMQ;
+constexpr int kMaxProj = 36;  // (degree + 3)^2 projection points
+
+// Quadrature and basis tables of one (element kind, degree).  Kept in the
+// device's __constant__ bank: every thread of a warp reads the same entry at
+// the same time, so the accesses are broadcasts.
+struct Tables {
+  int ML, NQ, MQ, E, NPT, NPJ;
+  double w[kMaxQ];                 // interior weights, sum 1
+  double ew[kMaxMQ];               // edge Gauss-Legendre weights, sum 2
+  double phi[kMaxPts][kMaxML];     // basis at interior points then edge points
+  double dxi[kMaxPts][kMaxML];     // d phi / d xi
+  double deta[kMaxPts][kMaxML];    // d phi / d eta
+};
+
+// Projection tables (initial condition only).
+struct ProjTables {
+  int ML, NPJ;
+  double w[kMaxProj];
+  double phi[kMaxProj][kMaxML];
+};
+
+// Device geometry, structure of arrays indexed [.. ][N] so that one thread
+// per element reads coalesced.
+struct DevMesh {
+  int N, E;
+  const double* area;     // [N]
+  const double* jinv;     // [4][N]: dxi/dx, dxi/dy, deta/dx, deta/dy
+  const double* nrm;      // [E][2][N]: outward normal scaled by edge length
+  const double* sdx;      // [N]: spacing for the shock limiter alpha
+  const int* nbr;         // [E][N]: neighbour id, or -1 - bc code on the boundary
+  const int* nbk;         // [E][N]: neighbour's local edge
+  double hmin;            // min_i 2|T_i| / P_i
+};
+
+// Device workspace of one solver.
+struct DevWork {
+  double* trace;          // [E][MQ][8][N]: q (4) and n_out . F_T (4) at edge points
+  double* flux;           // [E][8][N]: outward f^LxW (4), f^LxF (4)
+  double* prop;           // [E][N]: Lambda proposals
+  unsigned long long* smax;  // wave speed (bits of a non-negative double)
+  unsigned int* status;      // LXW_ST_* bits
+  double* diag;           // [16] reduction slots (see lxw_kernels.cu)
+};
+
+struct StepArgs {
+  double dt_in, cfl, gamma, eps0, alpha0;
+  int shock_limiter;
+  int want_diag;
+  double* theta_cell;     // [2][N] or null
+  double* theta_edge;     // [N][E] or null
+};
+
+// Kernel launchers (lxw_kernels.cu).  All enqueue on `stream`, allocate nothing.
+// Copies the tables of one (kind, degree) into the device's constant bank
+// (synchronous; done when a solver is created on the current device).
+int upload_tables(int kind, int deg, const Tables& t);
+// events (nullable): ev[0..launches] recorded before each launch and after the last
+int launch_step(int kind, int deg, const DevMesh& m, const DevWork& w,
+                double* Q, const StepArgs& a, void* stream, int block, void** events = nullptr);
+int launch_moment_limit(int kind, int deg, const DevMesh& m, const DevWork& w,
+                        double* Q, const StepArgs& a, double* theta, void* stream, int block);
+int launch_shock_limit(int kind, int deg, const DevMesh& m, double* Q,
+                       const StepArgs& a, double* theta, void* stream, int block);
+int launch_project(const ProjTables& t, int N, double gamma, const double* prim, double* Q,
+                   void* stream);
+int launch_copy_speed(const DevWork& w, double* s_dev, void* stream);
+int step_launch_count(int want_diag, int shock_limiter);
+
+}  // namespace lxw

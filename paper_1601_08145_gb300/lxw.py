@@ -1,0 +1,253 @@
+"""Thin Python binding of the C ABI in include/lxw.h (ctypes).
+
+Argument marshalling only: every step of the path runs in liblxw.so's CUDA
+kernels.  Device buffers are torch CUDA tensors (float64, contiguous),
+passed by data_ptr(); host buffers are numpy arrays.  Function names follow
+the C entry points.  Importing works without a GPU; calling the library
+needs liblxw.so built in-tree (``paper_1601_08145_gb300.build``) and fails
+loudly when it is missing.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblxw.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_NONPOSITIVE, ERR_CFL, ERR_NAN, ERR_BOUNDS, ERR_TIMEOUT, ERR_NOMEM = range(9)
+BC_PERIODIC, BC_REFLECT, BC_TRANSPARENT = 0, 1, 2
+KIND_QUAD, KIND_TRI = 0, 1
+ST_NONPOSITIVE, ST_CFL, ST_NAN = 1, 2, 4
+
+# every extern "C" symbol declared in include/lxw.h
+EXPORTS = [
+    "lxw_last_error", "lxw_options_default", "lxw_mesh_cartesian", "lxw_mesh_triangles",
+    "lxw_mesh_destroy", "lxw_mesh_num_elements", "lxw_solver_create", "lxw_solver_destroy",
+    "lxw_solver_set_stream", "lxw_solver_info", "lxw_projection_points", "lxw_project",
+    "lxw_step", "lxw_run", "lxw_run_host", "lxw_moment_limit", "lxw_shock_limit",
+    "lxw_step_launches", "lxw_profile_step",
+]
+
+
+class Options(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("eps0", C.c_double), ("alpha0", C.c_double),
+                ("shock_limiter", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
+                ("reserved", C.c_int * 9)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("s", C.c_double), ("dt", C.c_double), ("min_rho", C.c_double), ("min_p", C.c_double),
+                ("mass", C.c_double), ("momx", C.c_double), ("momy", C.c_double), ("energy", C.c_double),
+                ("n_mom", C.c_double), ("n_edge", C.c_double), ("n_sc", C.c_double),
+                ("status", C.c_int), ("reserved", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class LxwError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lxw status {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+def lib():
+    """Load liblxw.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1601_08145_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    L.lxw_last_error.restype = C.c_char_p
+    L.lxw_options_default.argtypes = [C.POINTER(Options)]
+    L.lxw_mesh_cartesian.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _ip, C.POINTER(_vp)]
+    L.lxw_mesh_triangles.argtypes = [C.c_int, _dp, C.c_int, _ip, _ip, C.POINTER(_vp)]
+    L.lxw_mesh_destroy.argtypes = [_vp]
+    L.lxw_mesh_destroy.restype = None
+    L.lxw_mesh_num_elements.argtypes = [_vp]
+    L.lxw_solver_create.argtypes = [_vp, C.c_int, C.POINTER(Options), _vp, C.POINTER(_vp)]
+    L.lxw_solver_destroy.argtypes = [_vp]
+    L.lxw_solver_destroy.restype = None
+    L.lxw_solver_set_stream.argtypes = [_vp, _vp]
+    L.lxw_solver_info.argtypes = [_vp, _ip, _ip, _ip, _ip, _ip]
+    L.lxw_projection_points.argtypes = [_vp, _dp]
+    L.lxw_project.argtypes = [_vp, _vp, _vp]
+    L.lxw_step.argtypes = [_vp, _vp, C.c_double, C.c_double, C.POINTER(Diag), _vp, _vp]
+    L.lxw_run.argtypes = [_vp, _vp, C.c_int, C.c_double, C.POINTER(Diag)]
+    L.lxw_run_host.argtypes = [_vp, _vp, C.c_int, C.c_double, C.POINTER(Diag)]
+    L.lxw_moment_limit.argtypes = [_vp, _vp, _vp, _vp]
+    L.lxw_shock_limit.argtypes = [_vp, _vp, _vp]
+    L.lxw_step_launches.argtypes = [_vp]
+    L.lxw_profile_step.argtypes = [_vp, _vp, C.c_double, C.POINTER(C.c_float)]
+    _lib = L
+    return L
+
+
+def _check(st, allow=()):
+    if st != OK and st not in allow:
+        raise LxwError(st, lib().lxw_last_error().decode())
+    return st
+
+
+def _ptr(t, shape=None, what="tensor"):
+    """data_ptr of a contiguous float64 CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+        raise ValueError(f"{what}: need a contiguous float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what}: shape {tuple(t.shape)} != {tuple(shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def lxw_options_default(**kw):
+    o = Options()
+    _check(lib().lxw_options_default(C.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Mesh:
+    def __init__(self, handle):
+        self.h = handle
+        self.N = lib().lxw_mesh_num_elements(handle)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lxw_mesh_destroy(self.h)
+            self.h = None
+
+
+def lxw_mesh_cartesian(nx, ny, box=(0.0, 1.0, 0.0, 1.0), bc=(BC_PERIODIC,) * 4):
+    h = _vp()
+    b = (C.c_int * 4)(*bc)
+    _check(lib().lxw_mesh_cartesian(nx, ny, box[0], box[1], box[2], box[3], b, C.byref(h)))
+    return Mesh(h)
+
+
+def lxw_mesh_triangles(xy, tv, ebc=None):
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tv = np.ascontiguousarray(tv, dtype=np.int32)
+    e = None if ebc is None else np.ascontiguousarray(ebc, dtype=np.int32)
+    h = _vp()
+    _check(lib().lxw_mesh_triangles(len(xy), xy.ctypes.data_as(_dp), len(tv), tv.ctypes.data_as(_ip),
+                                    e.ctypes.data_as(_ip) if e is not None else None, C.byref(h)))
+    return Mesh(h)
+
+
+class Solver:
+    def __init__(self, handle, mesh):
+        self.h = handle
+        self.mesh = mesh
+        N, E, ML, npts, nproj = (C.c_int() for _ in range(5))
+        _check(lib().lxw_solver_info(handle, C.byref(N), C.byref(E), C.byref(ML), C.byref(npts), C.byref(nproj)))
+        self.N, self.E, self.ML, self.npts, self.nproj = N.value, E.value, ML.value, npts.value, nproj.value
+
+    @property
+    def state_shape(self):
+        return (self.N, 4, self.ML)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lxw_solver_destroy(self.h)
+            self.h = None
+
+
+def lxw_solver_create(mesh, degree, options=None, stream=None):
+    h = _vp()
+    _check(lib().lxw_solver_create(mesh.h, degree, C.byref(options) if options is not None else None,
+                                   _stream_handle(stream), C.byref(h)))
+    return Solver(h, mesh)
+
+
+def lxw_solver_set_stream(solver, stream):
+    _check(lib().lxw_solver_set_stream(solver.h, _stream_handle(stream)))
+
+
+def lxw_projection_points(solver):
+    xy = np.zeros((solver.N, solver.nproj, 2))
+    _check(lib().lxw_projection_points(solver.h, xy.ctypes.data_as(_dp)))
+    return xy
+
+
+def lxw_project(solver, prim, Q):
+    _check(lib().lxw_project(solver.h, _ptr(prim, (solver.N, solver.nproj, 4), "prim"),
+                             _ptr(Q, solver.state_shape, "Q")))
+
+
+def _diag_result(st, d):
+    out = d.as_dict()
+    out["return_status"] = st
+    return out
+
+
+def lxw_step(solver, Q, dt=0.0, cfl=0.1, diag=False, theta_cell=None, theta_edge=None):
+    d = Diag() if diag else None
+    st = _check(lib().lxw_step(solver.h, _ptr(Q, solver.state_shape, "Q"), dt, cfl,
+                               C.byref(d) if d is not None else None,
+                               _ptr(theta_cell, (2, solver.N), "theta_cell"),
+                               _ptr(theta_edge, (solver.N, solver.E), "theta_edge")),
+                allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN))
+    return _diag_result(st, d) if d is not None else None
+
+
+def lxw_run(solver, Q, nsteps, cfl, diag=False):
+    d = Diag() if diag else None
+    st = _check(lib().lxw_run(solver.h, _ptr(Q, solver.state_shape, "Q"), nsteps, cfl,
+                              C.byref(d) if d is not None else None), allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN))
+    return _diag_result(st, d) if d is not None else None
+
+
+def lxw_run_host(solver, Qh, nsteps, cfl, diag=False):
+    """Qh: host buffer (numpy float64 array or pinned CPU torch tensor) [N][4][ML]."""
+    if isinstance(Qh, np.ndarray):
+        assert Qh.dtype == np.float64 and Qh.flags.c_contiguous and Qh.shape == solver.state_shape
+        p = C.c_void_p(Qh.ctypes.data)
+    else:
+        assert (not Qh.is_cuda) and Qh.element_size() == 8 and Qh.is_contiguous() and tuple(Qh.shape) == solver.state_shape
+        p = C.c_void_p(Qh.data_ptr())
+    d = Diag() if diag else None
+    st = _check(lib().lxw_run_host(solver.h, p, nsteps, cfl, C.byref(d) if d is not None else None),
+                allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN))
+    return _diag_result(st, d) if d is not None else None
+
+
+def lxw_moment_limit(solver, Q, theta=None, s_out=None):
+    _check(lib().lxw_moment_limit(solver.h, _ptr(Q, solver.state_shape, "Q"), _ptr(theta, (solver.N,), "theta"),
+                                  _ptr(s_out, (1,), "s_out")))
+
+
+def lxw_shock_limit(solver, Q, theta=None):
+    _check(lib().lxw_shock_limit(solver.h, _ptr(Q, solver.state_shape, "Q"), _ptr(theta, (solver.N,), "theta")))
+
+
+def lxw_step_launches(solver):
+    return lib().lxw_step_launches(solver.h)
+
+
+PHASES = ["reset", "moment", "ck", "edge", "update", "shock"]
+
+
+def lxw_profile_step(solver, Q, cfl):
+    """One step with per-launch CUDA-event timing; returns {phase: ms}."""
+    n = lxw_step_launches(solver)
+    ms = (C.c_float * n)()
+    _check(lib().lxw_profile_step(solver.h, _ptr(Q, solver.state_shape, "Q"), cfl, ms))
+    return {PHASES[k]: float(ms[k]) for k in range(n)}
