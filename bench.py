@@ -214,6 +214,7 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(0.5)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()

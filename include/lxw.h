@@ -165,6 +165,18 @@ int lxw_step_launches(const lxw_solver* s);
  * are created with the solver. */
 lxw_status lxw_profile_step(lxw_solver* s, double* Q_dev, double cfl, float* ms_host);
 
+/* Per-phase inspection (same kernels as lxw_step).  lxw_step_phases runs only
+ * the first nphases phases of a step (1 moment limiter + wave speed, 2 CK
+ * flux and volume integral, 3 edge fluxes and flux-limiter proposals,
+ * 4 blended update, 5 shock limiter) in place on Q_dev.  lxw_workspace_copy
+ * copies a workspace buffer to host memory after it: which = 0 edge traces
+ * [E][MQ][8][N] (q then n_out.F_T at each edge point, n_out the outward
+ * normal scaled by the edge length), 1 outward fluxes [E][8][N] (f^LxW then
+ * f^LxF), 2 Lambda proposals [E][N], 3 wave speed and dt [2]; count = number
+ * of doubles the caller's buffer holds (LXW_ERR_ARG if too small). */
+lxw_status lxw_step_phases(lxw_solver* s, double* Q_dev, double dt, double cfl, int nphases);
+lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* host_out, size_t count);
+
 #ifdef __cplusplus
 }
 #endif

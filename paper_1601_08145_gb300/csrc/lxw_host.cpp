@@ -71,12 +71,19 @@ void gauss_legendre(int n, double* x, double* w) {
   if (n % 2) x[n / 2] = 0.0;
 }
 
-// normalised Legendre value/derivative, (1/2) Int_{-1}^{1} L_n^2 = 1
+// normalised Legendre value/derivative, (1/2) Int_{-1}^{1} L_n^2 = 1.  The
+// derivative follows P'_{k+1} = P'_{k-1} + (2k+1) P_k, which has no
+// division and so holds at the edge points x = +-1 of the reference square.
 void legendre_norm(int n, double x, double& v, double& d) {
-  long double p, dp;
-  legendre_eval(n, x, p, dp);
-  if (n == 0) dp = 0.0L;
-  // derivative at |x| = 1 would divide by zero; the tables never sample there
+  long double p0 = 1.0L, p1 = x, d0 = 0.0L, d1 = 1.0L;
+  long double p = 1.0L, dp = 0.0L;
+  if (n == 1) { p = p1; dp = d1; }
+  for (int k = 1; k < n; ++k) {
+    long double p2 = ((2 * k + 1) * (long double)x * p1 - k * p0) / (k + 1);
+    long double d2 = d0 + (2 * k + 1) * p1;
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+    p = p2; dp = d2;
+  }
   long double s = sqrtl(2.0L * n + 1.0L);
   v = (double)(s * p);
   d = (double)(s * dp);
@@ -236,6 +243,7 @@ struct lxw_solver {
   cudaGraphExec_t graph = nullptr;
   double* graph_Q = nullptr;
   double graph_cfl = 0.0;
+  double last_dt_in = 0.0, last_cfl = 0.0;
   void* events[8] = {};          // cudaEvent_t of lxw_profile_step
   ~lxw_solver() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -581,6 +589,41 @@ lxw_status lxw_shock_limit(lxw_solver* s, double* Q, double* theta) {
 }
 
 int lxw_step_launches(const lxw_solver* s) { return s ? step_launch_count(0, s->opt.shock_limiter) : 0; }
+
+lxw_status lxw_step_phases(lxw_solver* s, double* Q, double dt, double cfl, int nphases) {
+  if (!s || !Q || nphases < 1) return fail(LXW_ERR_ARG, "lxw_step_phases: bad argument");
+  if (!(dt > 0.0) && !(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_step_phases: need dt > 0 or cfl > 0");
+  StepArgs a = make_args(s, dt, cfl, 0, nullptr, nullptr);
+  s->last_dt_in = dt; s->last_cfl = cfl;
+  if (launch_step(s->kind, s->deg, s->dm, s->dw, Q, a, s->stream, s->opt.block_threads, nullptr, nphases))
+    return fail(LXW_ERR_CUDA, "lxw_step_phases: launch failed");
+  return LXW_OK;
+}
+
+lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* out, size_t count) {
+  if (!s || !out) return fail(LXW_ERR_ARG, "lxw_workspace_copy: null argument");
+  const size_t N = s->N, E = s->E, MQ = s->tab.MQ;
+  const double* src = nullptr;
+  size_t n = 0;
+  if (which == 0) { src = s->dw.trace; n = E * MQ * 8 * N; }
+  else if (which == 1) { src = s->dw.flux; n = E * 8 * N; }
+  else if (which == 2) { src = s->dw.prop; n = E * N; }
+  else if (which == 3) {
+    if (count < 2) return fail(LXW_ERR_ARG, "lxw_workspace_copy: buffer too small");
+    unsigned long long b = 0;
+    LXW_CUDA(cudaMemcpyAsync(&b, s->dw.smax, sizeof(b), cudaMemcpyDeviceToHost, s->stream));
+    LXW_CUDA(cudaStreamSynchronize(s->stream));
+    std::memcpy(&out[0], &b, sizeof(double));
+    out[1] = s->last_dt_in > 0.0 ? s->last_dt_in : s->last_cfl * s->dm.hmin / out[0];
+    return LXW_OK;
+  } else {
+    return fail(LXW_ERR_ARG, "lxw_workspace_copy: unknown buffer");
+  }
+  if (count < n) return fail(LXW_ERR_ARG, "lxw_workspace_copy: buffer too small");
+  LXW_CUDA(cudaMemcpyAsync(out, src, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  LXW_CUDA(cudaStreamSynchronize(s->stream));
+  return LXW_OK;
+}
 
 lxw_status lxw_profile_step(lxw_solver* s, double* Q, double cfl, float* ms) {
   if (!s || !Q || !ms || !(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_profile_step: bad argument");

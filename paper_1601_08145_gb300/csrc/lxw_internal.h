@@ -70,8 +70,10 @@ struct StepArgs {
 // (synchronous; done when a solver is created on the current device).
 int upload_tables(int kind, int deg, const Tables& t);
 // events (nullable): ev[0..launches] recorded before each launch and after the last
+// upto: number of phases to run (1 moment .. 5 shock; larger = all)
 int launch_step(int kind, int deg, const DevMesh& m, const DevWork& w,
-                double* Q, const StepArgs& a, void* stream, int block, void** events = nullptr);
+                double* Q, const StepArgs& a, void* stream, int block, void** events = nullptr,
+                int upto = 99);
 int launch_moment_limit(int kind, int deg, const DevMesh& m, const DevWork& w,
                         double* Q, const StepArgs& a, double* theta, void* stream, int block);
 int launch_shock_limit(int kind, int deg, const DevMesh& m, double* Q,

@@ -690,7 +690,7 @@ inline int grid_for(int N, int block) { return (N + block - 1) / block; }
 
 template <int KD, int E, int ML, int NQ, int MQ>
 int step_impl(const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a, cudaStream_t st, int block,
-              void** events) {
+              void** events, int upto) {
   const int grid = grid_for(m.N, block);
   DevDiag* dd = reinterpret_cast<DevDiag*>(w.diag);
   int ne = 0;
@@ -700,13 +700,16 @@ int step_impl(const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a, 
   mark();
   k_moment<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, Q, a, a.theta_cell);
   mark();
+  if (upto < 2) return cudaGetLastError() == cudaSuccess ? 0 : -1;
   k_ck<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, Q, a);
   mark();
+  if (upto < 3) return cudaGetLastError() == cudaSuccess ? 0 : -1;
   k_edge<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, Q, a);
   mark();
+  if (upto < 4) return cudaGetLastError() == cudaSuccess ? 0 : -1;
   k_update<E, ML><<<grid, block, 0, st>>>(m, w, Q, a);
   mark();
-  if (a.shock_limiter) {
+  if (a.shock_limiter && upto >= 5) {
     k_shock<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, Q, a, a.theta_cell ? a.theta_cell + m.N : nullptr,
                                                        a.want_diag ? &dd->nsc : nullptr);
     mark();
@@ -741,8 +744,9 @@ int shock_impl(const DevMesh& m, double* Q, const StepArgs& a, double* theta, cu
   } while (0)
 
 int launch_step(int kind, int deg, const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a,
-                void* stream, int block, void** events) {
-#define CALL_STEP(KD, E, ML, NQ, MQ) step_impl<KD, E, ML, NQ, MQ>(m, w, Q, a, (cudaStream_t)stream, block, events)
+                void* stream, int block, void** events, int upto) {
+#define CALL_STEP(KD, E, ML, NQ, MQ) \
+  step_impl<KD, E, ML, NQ, MQ>(m, w, Q, a, (cudaStream_t)stream, block, events, upto)
   LXW_DISPATCH(kind, deg, CALL_STEP);
 #undef CALL_STEP
 }

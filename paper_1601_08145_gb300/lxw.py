@@ -26,7 +26,7 @@ EXPORTS = [
     "lxw_mesh_destroy", "lxw_mesh_num_elements", "lxw_solver_create", "lxw_solver_destroy",
     "lxw_solver_set_stream", "lxw_solver_info", "lxw_projection_points", "lxw_project",
     "lxw_step", "lxw_run", "lxw_run_host", "lxw_moment_limit", "lxw_shock_limit",
-    "lxw_step_launches", "lxw_profile_step",
+    "lxw_step_launches", "lxw_profile_step", "lxw_step_phases", "lxw_workspace_copy",
 ]
 
 
@@ -87,6 +87,8 @@ def lib():
     L.lxw_shock_limit.argtypes = [_vp, _vp, _vp]
     L.lxw_step_launches.argtypes = [_vp]
     L.lxw_profile_step.argtypes = [_vp, _vp, C.c_double, C.POINTER(C.c_float)]
+    L.lxw_step_phases.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int]
+    L.lxw_workspace_copy.argtypes = [_vp, C.c_int, _dp, C.c_size_t]
     _lib = L
     return L
 
@@ -159,6 +161,7 @@ class Solver:
         N, E, ML, npts, nproj = (C.c_int() for _ in range(5))
         _check(lib().lxw_solver_info(handle, C.byref(N), C.byref(E), C.byref(ML), C.byref(npts), C.byref(nproj)))
         self.N, self.E, self.ML, self.npts, self.nproj = N.value, E.value, ML.value, npts.value, nproj.value
+        self.mq = 3 if self.ML == 6 else 4     # edge points per edge: degree + 1
 
     @property
     def state_shape(self):
@@ -251,3 +254,16 @@ def lxw_profile_step(solver, Q, cfl):
     ms = (C.c_float * n)()
     _check(lib().lxw_profile_step(solver.h, _ptr(Q, solver.state_shape, "Q"), cfl, ms))
     return {PHASES[k]: float(ms[k]) for k in range(n)}
+
+
+def lxw_step_phases(solver, Q, dt, cfl, nphases):
+    _check(lib().lxw_step_phases(solver.h, _ptr(Q, solver.state_shape, "Q"), dt, cfl, nphases))
+
+
+def lxw_workspace_copy(solver, which):
+    """Workspace buffer after lxw_step_phases: 0 traces [E][MQ][8][N],
+    1 fluxes [E][8][N], 2 proposals [E][N], 3 (s, dt)."""
+    shapes = {0: (solver.E, solver.mq, 8, solver.N), 1: (solver.E, 8, solver.N), 2: (solver.E, solver.N), 3: (2,)}
+    out = np.zeros(shapes[which])
+    _check(lib().lxw_workspace_copy(solver.h, which, out.ctypes.data_as(_dp), out.size))
+    return out

@@ -134,7 +134,8 @@ def test_one_step_parity_limiters_active(L, O, kind, deg, bc):
                                   rho_range=(0.01, 3.0), p_range=(0.001, 3.0))
     Qo, do, Qg, dg, tc, te = step_both(L, os_, ls, Q0, cfl=0.9)
     assert do["status"] == 0 and dg["status"] == 0
-    assert abs(dg["s"] - do["s"]) <= 1e-14 * do["s"] and abs(dg["dt"] - do["dt"]) <= 1e-14 * do["dt"]
+    # s is a max over point values of states limited near vacuum: agreement to 1e-13
+    assert abs(dg["s"] - do["s"]) <= 1e-13 * do["s"] and abs(dg["dt"] - do["dt"]) <= 1e-13 * do["dt"]
     assert do["n_mom"] > 0 and do["n_sc"] > 0
     assert rel_l1(Qg, Qo) < 1e-13
     assert np.abs(Qg - Qo).max() < 1e-11 * np.abs(Qo).max()
