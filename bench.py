@@ -62,7 +62,7 @@ def ck_flops_per_element(kind, deg):
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64 (derived, and the measured probe)
 # DRAM bytes per k_ck launch from the ncu capture summarised in profiles/ (None until captured
 # for the current kernel version)
-CK_TRAFFIC_BYTES = None
+CK_TRAFFIC_BYTES = 27_383_296 + 40_022_272   # k_ck of the FP64 form, profiles/k_ck_rarefy224_p2_fp64.md
 
 
 def build_workload(L, name, stream):
@@ -208,6 +208,10 @@ def main():
     Q = project(L, sol, w)
     dof = sol.N * 4 * sol.ML
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    try:
+        fp64_probe = L.lxw_fma_peak(True)
+    except Exception:
+        fp64_probe = None
     for _ in range(max(args.warmup, 3)):
         L.lxw_profile_step(sol, Q, w["cfl"])
     torch.cuda.synchronize()
@@ -241,6 +245,9 @@ def main():
     roofline = {"kernel": "k_ck", "dominant_kernel": dom, "bound": "alu", "pipe": "fp64",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": CK_TRAFFIC_BYTES,
+                "peak_source": "derived (GB300 FP64 nominal, recipe table)",
+                "peak_measured_fma_probe": fp64_probe,
+                "frac_of_measured_probe": achieved / fp64_probe if fp64_probe else None,
                 "algorithmic_flops_per_launch": flops, "launch_ms": ck_ms}
 
     # end to end through the public C ABI on HOST memory: H2D of the state,

@@ -177,6 +177,14 @@ lxw_status lxw_profile_step(lxw_solver* s, double* Q_dev, double cfl, float* ms_
 lxw_status lxw_step_phases(lxw_solver* s, double* Q_dev, double dt, double cfl, int nphases);
 lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* host_out, size_t count);
 
+/* Measurement aid (no counterpart in the paper): throughput in TFLOP/s of
+ * fused multiply-adds on the plain FP64 (fp64 = 1) or FP32 (fp64 = 0) pipe
+ * of the current device, from one timed launch of independent FMA chains on
+ * every SM (legacy default stream, synchronous, allocates nothing).  The
+ * element kernels do their arithmetic on these pipes; this is their roofline
+ * denominator. */
+lxw_status lxw_fma_peak(int fp64, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -796,3 +796,4 @@ void decode_diag(const double* raw, double out[9]) {
 size_t diag_bytes() { return sizeof(DevDiag); }
 
 }  // namespace lxw
+

@@ -27,6 +27,7 @@ EXPORTS = [
     "lxw_solver_set_stream", "lxw_solver_info", "lxw_projection_points", "lxw_project",
     "lxw_step", "lxw_run", "lxw_run_host", "lxw_moment_limit", "lxw_shock_limit",
     "lxw_step_launches", "lxw_profile_step", "lxw_step_phases", "lxw_workspace_copy",
+    "lxw_fma_peak",
 ]
 
 
@@ -89,6 +90,7 @@ def lib():
     L.lxw_profile_step.argtypes = [_vp, _vp, C.c_double, C.POINTER(C.c_float)]
     L.lxw_step_phases.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int]
     L.lxw_workspace_copy.argtypes = [_vp, C.c_int, _dp, C.c_size_t]
+    L.lxw_fma_peak.argtypes = [C.c_int, _dp]
     _lib = L
     return L
 
@@ -267,3 +269,10 @@ def lxw_workspace_copy(solver, which):
     out = np.zeros(shapes[which])
     _check(lib().lxw_workspace_copy(solver.h, which, out.ctypes.data_as(_dp), out.size))
     return out
+
+
+def lxw_fma_peak(fp64=True):
+    """Measured FMA throughput (TFLOP/s) of the FP64 or FP32 pipe."""
+    v = C.c_double()
+    _check(lib().lxw_fma_peak(int(bool(fp64)), C.byref(v)))
+    return v.value
