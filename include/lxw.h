@@ -185,6 +185,30 @@ lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* host_out, size_t
  * denominator. */
 lxw_status lxw_fma_peak(int fp64, double* tflops);
 
+/* Allocation-free form of lxw_moment_limit, for callers that cannot call
+ * cudaMalloc: code running while a stream is captured into a CUDA graph,
+ * code whose device memory is owned by another allocator (a framework's
+ * caching pool, a fixed budget), code that must avoid cudaMalloc's implicit
+ * device synchronisation.  The paper has no counterpart; it is the same
+ * moment limiter and wave-speed maximum, without a solver.
+ * Q_dev[n_elements][4][ML] is limited in place; theta_dev[n_elements]
+ * (nullable) receives theta; s_dev[0] (device double) receives the wave
+ * speed.  No geometry is needed (the limiter is element-local).
+ * Scratch: the reduction's running maxima live in a static device array of
+ * 513 64-bit words (about 4 KB) that every GPU loading the library holds
+ * until exit; n_elements above 16,777,216 (512 slots x 32,768 elements) is
+ * rejected with LXW_ERR_ARG.  The array is shared by every call and keeps
+ * the last call's contents; each call clears the slots it uses first.  Calls
+ * that overlap on the GPU (concurrent streams, or several host threads) race
+ * on it and must be serialised by the caller.  The first call on a device
+ * finds the array's device address and loads the basis tables into the
+ * constant bank (once per device, with that device current); make that first
+ * call before any stream capture.  Allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library call.  Errors: LXW_ERR_ARG (null pointer,
+ * kind/degree, size, gamma <= 1, eps0 <= 0), LXW_ERR_CUDA. */
+lxw_status lxw_moment_limit_noalloc(int kind, int degree, int n_elements, double gamma, double eps0,
+                                    double* Q_dev, double* theta_dev, double* s_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

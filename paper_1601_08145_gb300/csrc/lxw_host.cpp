@@ -219,6 +219,13 @@ void projection_reference_points(int kind, int deg, std::vector<double>& xi, std
 
 }  // namespace
 
+void lxw::set_last_error(const char* msg) { g_err = msg; }
+
+void lxw::make_tables(int kind, int deg, Tables& t) {
+  ProjTables pt;
+  build_tables(kind, deg, t, pt);
+}
+
 // ------------------------------------------------------------------ mesh
 struct lxw_mesh {
   int kind, N, E;

@@ -66,6 +66,10 @@ struct StepArgs {
 };
 
 // Kernel launchers (lxw_kernels.cu).  All enqueue on `stream`, allocate nothing.
+// Sets the message lxw_last_error() returns on this thread.
+void set_last_error(const char* msg);
+// Builds the quadrature / basis tables of one (kind, degree) on the host.
+void make_tables(int kind, int deg, Tables& t);
 // Copies the tables of one (kind, degree) into the device's constant bank
 // (synchronous; done when a solver is created on the current device).
 int upload_tables(int kind, int deg, const Tables& t);

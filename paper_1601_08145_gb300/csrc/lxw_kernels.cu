@@ -797,3 +797,108 @@ size_t diag_bytes() { return sizeof(DevDiag); }
 
 }  // namespace lxw
 
+// ====================================================================
+// Allocation-free variant of the moment limiter and wave-speed reduction.
+//
+// Some callers cannot call cudaMalloc: code that runs while a stream is
+// being captured into a CUDA graph, code whose device memory belongs to
+// another allocator (a framework's caching pool or a fixed memory budget),
+// and code that must not take cudaMalloc's implicit device synchronisation.
+// lxw_moment_limit_noalloc serves them: it needs no solver (whose creation
+// allocates), only the caller's state, theta and speed buffers.  The
+// reduction scratch of the wave speed -- one running maximum per chunk of
+// kNoAllocChunk elements and a status word -- lives in the file-scope array
+// below, which every GPU that loads the library holds until exit.
+// ====================================================================
+#include <mutex>
+
+namespace lxw {
+namespace {
+
+constexpr int kNoAllocChunk = 32768;          // elements per reduction slot
+constexpr int kNoAllocSlots = 512;            // -> at most 16,777,216 elements
+constexpr int kMaxDevices = 64;
+
+// slot maxima (bits of non-negative doubles), then one status word
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocSlots + 1];
+
+__global__ void k_noalloc_clear(int nslots) {
+  for (int c = threadIdx.x; c <= nslots; c += blockDim.x) g_noalloc_scratch[c] = 0ull;
+}
+
+__global__ void k_noalloc_finish(int nslots, double* s_dev) {
+  unsigned long long m = 0ull;
+  for (int c = 0; c < nslots; ++c) m = m > g_noalloc_scratch[c] ? m : g_noalloc_scratch[c];
+  *s_dev = __longlong_as_double((long long)m);
+}
+
+std::mutex g_noalloc_mu;
+unsigned long long* g_noalloc_addr[kMaxDevices] = {};
+bool g_noalloc_tables[kMaxDevices][4] = {};
+
+template <int KD, int E, int ML, int NQ, int MQ>
+int noalloc_impl(int N, double* Q, const StepArgs& a, double* theta, double* s_dev, cudaStream_t st,
+                 unsigned long long* scratch) {
+  const int nslots = (N + kNoAllocChunk - 1) / kNoAllocChunk;
+  k_noalloc_clear<<<1, 256, 0, st>>>(nslots);
+  for (int c = 0; c < nslots; ++c) {
+    const int n = N - c * kNoAllocChunk < kNoAllocChunk ? N - c * kNoAllocChunk : kNoAllocChunk;
+    DevMesh m{};
+    m.N = n;                                   // the moment kernel reads only N
+    DevWork w{};
+    w.smax = scratch + c;
+    w.status = reinterpret_cast<unsigned int*>(scratch + kNoAllocSlots);
+    k_moment<KD, E, ML, NQ, MQ><<<grid_for(n, 128), 128, 0, st>>>(
+        m, w, Q + (size_t)c * kNoAllocChunk * 4 * ML, a, theta ? theta + (size_t)c * kNoAllocChunk : nullptr);
+  }
+  k_noalloc_finish<<<1, 1, 0, st>>>(nslots, s_dev);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+}  // namespace lxw
+
+extern "C" lxw_status lxw_moment_limit_noalloc(int kind, int degree, int n_elements, double gamma, double eps0,
+                                               double* Q_dev, double* theta_dev, double* s_dev, void* stream) {
+  using namespace lxw;
+  auto err = [](lxw_status st, const char* msg) { set_last_error(msg); return st; };
+  if (!Q_dev || !s_dev) return err(LXW_ERR_ARG, "lxw_moment_limit_noalloc: null Q_dev or s_dev");
+  if ((kind != LXW_KIND_QUAD && kind != LXW_KIND_TRI) || (degree != 2 && degree != 3))
+    return err(LXW_ERR_ARG, "lxw_moment_limit_noalloc: kind must be quad/triangle and degree 2 or 3");
+  if (n_elements < 1 || n_elements > kNoAllocChunk * kNoAllocSlots)
+    return err(LXW_ERR_ARG, "lxw_moment_limit_noalloc: n_elements must be in [1, 16777216] (static scratch capacity)");
+  if (!(gamma > 1.0) || !(eps0 > 0.0)) return err(LXW_ERR_ARG, "lxw_moment_limit_noalloc: need gamma > 1 and eps0 > 0");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return err(LXW_ERR_CUDA, "lxw_moment_limit_noalloc: no usable current device");
+  const int kd = (kind == LXW_KIND_QUAD ? 0 : 2) + (degree == 3 ? 1 : 0);
+  unsigned long long* scratch = nullptr;
+  {
+    // once per device (with that device current): the device address of the
+    // scratch array and this variant's tables in the constant bank
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+        return err(LXW_ERR_CUDA, "lxw_moment_limit_noalloc: cudaGetSymbolAddress of the scratch array failed");
+      g_noalloc_addr[dev] = static_cast<unsigned long long*>(p);
+    }
+    if (!g_noalloc_tables[dev][kd]) {
+      Tables t;
+      make_tables(kind, degree, t);
+      if (upload_tables(kind, degree, t)) return err(LXW_ERR_CUDA, "lxw_moment_limit_noalloc: table upload failed");
+      g_noalloc_tables[dev][kd] = true;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  StepArgs a{};
+  a.gamma = gamma;
+  a.eps0 = eps0;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if (kd == 0) rc = noalloc_impl<0, 4, 6, 9, 3>(n_elements, Q_dev, a, theta_dev, s_dev, st, scratch);
+  else if (kd == 1) rc = noalloc_impl<1, 4, 10, 16, 4>(n_elements, Q_dev, a, theta_dev, s_dev, st, scratch);
+  else if (kd == 2) rc = noalloc_impl<2, 3, 6, 9, 3>(n_elements, Q_dev, a, theta_dev, s_dev, st, scratch);
+  else rc = noalloc_impl<3, 3, 10, 16, 4>(n_elements, Q_dev, a, theta_dev, s_dev, st, scratch);
+  return rc ? err(LXW_ERR_CUDA, "lxw_moment_limit_noalloc: launch failed") : LXW_OK;
+}

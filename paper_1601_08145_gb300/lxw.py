@@ -27,7 +27,7 @@ EXPORTS = [
     "lxw_solver_set_stream", "lxw_solver_info", "lxw_projection_points", "lxw_project",
     "lxw_step", "lxw_run", "lxw_run_host", "lxw_moment_limit", "lxw_shock_limit",
     "lxw_step_launches", "lxw_profile_step", "lxw_step_phases", "lxw_workspace_copy",
-    "lxw_fma_peak",
+    "lxw_moment_limit_noalloc", "lxw_fma_peak",
 ]
 
 
@@ -91,6 +91,7 @@ def lib():
     L.lxw_step_phases.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int]
     L.lxw_workspace_copy.argtypes = [_vp, C.c_int, _dp, C.c_size_t]
     L.lxw_fma_peak.argtypes = [C.c_int, _dp]
+    L.lxw_moment_limit_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp, _vp, _vp]
     _lib = L
     return L
 
@@ -269,6 +270,15 @@ def lxw_workspace_copy(solver, which):
     out = np.zeros(shapes[which])
     _check(lib().lxw_workspace_copy(solver.h, which, out.ctypes.data_as(_dp), out.size))
     return out
+
+
+def lxw_moment_limit_noalloc(kind, degree, Q, theta=None, s_out=None, gamma=1.4, eps0=1e-12, stream=None):
+    """Allocation-free moment limiter + wave speed (no solver needed).
+    Q: [N][4][ML] float64 CUDA tensor, in place; theta [N], s_out [1]."""
+    N = Q.shape[0]
+    _check(lib().lxw_moment_limit_noalloc(kind, degree, N, gamma, eps0, _ptr(Q, None, "Q"),
+                                          _ptr(theta, (N,), "theta"), _ptr(s_out, (1,), "s_out"),
+                                          _stream_handle(stream)))
 
 
 def lxw_fma_peak(fp64=True):
