@@ -44,7 +44,14 @@ typedef enum {
 
 enum { LXW_BC_PERIODIC = 0, LXW_BC_REFLECT = 1, LXW_BC_TRANSPARENT = 2 };
 enum { LXW_KIND_QUAD = 0, LXW_KIND_TRI = 1 };
-enum { LXW_PREC_FP64 = 0 };
+/* Precision forms.  LXW_PREC_FP64: every operation in FP64; the state is
+ * Q[N][4][ML] doubles.  LXW_PREC_MIXED: FP32 bulk (point values, CK flux,
+ * projections, LLF point fluxes, volume / edge integrals, shock limiter)
+ * with FP64 cell averages, FP64 blended update and FP64 limiter solves where
+ * an FP32 screen with an error margin cannot prove theta = 1; the state is
+ * the packed layout of lxw_state_pack (averages double [4][N], then higher
+ * modes float [4][ML-1][N]). */
+enum { LXW_PREC_FP64 = 0, LXW_PREC_MIXED = 1 };
 
 /* device status bits (returned in lxw_diag.status) */
 enum { LXW_ST_NONPOSITIVE = 1, LXW_ST_CFL = 2, LXW_ST_NAN = 4 };
@@ -76,6 +83,8 @@ typedef struct {
   double n_sc;              /* cells with shock-limiter theta < 1 (Sec. 4.1)        */
   int status;               /* LXW_ST_* bits seen on the device during the step     */
   int reserved;
+  double n_fp64_moment;     /* mixed form: cells whose moment limiter ran in FP64   */
+  double n_fp64_edge;       /* mixed form: cells whose flux-limiter solve ran in FP64 */
 } lxw_diag;
 
 const char* lxw_last_error(void);
@@ -113,6 +122,15 @@ lxw_status lxw_solver_set_stream(lxw_solver* s, void* stream);
  * (interior + edge quadrature points), nproj projection points. */
 lxw_status lxw_solver_info(const lxw_solver* s, int* N, int* E, int* ML, int* npts, int* nproj);
 
+/* Bytes of the solver's state buffer (N*4*ML*8 for FP64; N*4*8 + N*4*(ML-1)*4
+ * for the mixed form).  lxw_state_pack converts Q64_dev[N][4][ML] doubles into
+ * the solver's state layout (a copy for FP64 solvers); lxw_state_unpack
+ * converts back.  Both asynchronous on the solver's stream; buffers must not
+ * overlap. */
+size_t lxw_state_bytes(const lxw_solver* s);
+lxw_status lxw_state_pack(lxw_solver* s, const double* Q64_dev, void* state_dev);
+lxw_status lxw_state_unpack(lxw_solver* s, const void* state_dev, double* Q64_dev);
+
 /* Physical coordinates of the initial-condition projection points
  * xy_host[N][nproj][2] (Gauss rule with degree+3 points per direction). */
 lxw_status lxw_projection_points(const lxw_solver* s, double* xy_host);
@@ -123,7 +141,8 @@ lxw_status lxw_project(lxw_solver* s, const double* prim_dev, double* Q_dev);
 
 /* --- the hot path --------------------------------------------------------- */
 
-/* One LxW-DG time step, in place on Q_dev[N][4][ML] (Sec. 3.3 Steps 1-6 and
+/* One LxW-DG time step, in place on the state Q_dev (FP64 solvers:
+ * Q[N][4][ML]; mixed solvers: the packed layout) (Sec. 3.3 Steps 1-6 and
  * the shock-capturing limiter, outline Step 5):
  *   moment limiter (Sec. 3.1) -> global wave speed s -> CK time-averaged flux
  *   and volume integral (Sec. 2.2-2.3) -> LLF edge flux, f^LxW, f^LxF (Step 3)

@@ -243,8 +243,11 @@ struct lxw_solver {
   ProjTables ptab;
   DevMesh dm{};
   DevWork dw{};
+  DevWorkMx dwm{};               // mixed form workspace
+  bool mixed = false;
   std::vector<void*> allocs;
-  double* Qdev = nullptr;        // state buffer of lxw_run_host
+  double* Qdev = nullptr;        // FP64 staging buffer of lxw_run_host
+  double* Sdev = nullptr;        // packed state of lxw_run_host (mixed form)
   double* host_diag = nullptr;   // pinned
   std::vector<double> xproj;     // [N][NPJ][2]
   cudaGraphExec_t graph = nullptr;
@@ -368,7 +371,8 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
   lxw_options opt;
   if (optp) opt = *optp; else lxw_options_default(&opt);
   if (!(opt.gamma > 1.0)) return fail(LXW_ERR_ARG, "lxw_solver_create: gamma must exceed 1");
-  if (opt.precision != LXW_PREC_FP64) return fail(LXW_ERR_ARG, "lxw_solver_create: unsupported precision");
+  if (opt.precision != LXW_PREC_FP64 && opt.precision != LXW_PREC_MIXED)
+    return fail(LXW_ERR_ARG, "lxw_solver_create: unsupported precision");
   if (opt.block_threads <= 0) opt.block_threads = 128;
   if (opt.block_threads % 32 || opt.block_threads > 1024) return fail(LXW_ERR_ARG, "lxw_solver_create: block_threads must be a multiple of 32 <= 1024");
   lxw_solver* s = new (std::nothrow) lxw_solver;
@@ -433,8 +437,19 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
   s->dw.prop = (double*)dalloc(sizeof(double) * (size_t)E * N);
   s->dw.smax = (unsigned long long*)dalloc(sizeof(unsigned long long));
   s->dw.status = (unsigned int*)dalloc(sizeof(unsigned int));
-  s->dw.diag = (double*)dalloc(diag_bytes());
+  s->dw.diag = (double*)dalloc(sizeof(DiagBlock) > diag_bytes() ? sizeof(DiagBlock) : diag_bytes());
   s->Qdev = (double*)dalloc(sizeof(double) * (size_t)N * 4 * s->ML);
+  s->mixed = opt.precision == LXW_PREC_MIXED;
+  if (s->mixed) {
+    // the FP32 traces / f^LxW fit in the FP64 buffers
+    s->dwm.trace = reinterpret_cast<float*>(s->dw.trace);
+    s->dwm.fw = reinterpret_cast<float*>(s->dw.flux);
+    s->dwm.prop = s->dw.prop;
+    s->dwm.avg_new = (double*)dalloc(sizeof(double) * 4 * (size_t)N);
+    s->dwm.smax = s->dw.smax; s->dwm.status = s->dw.status; s->dwm.diag = s->dw.diag;
+    s->Sdev = (double*)dalloc(lxw_state_bytes(s));
+    if (!s->dwm.avg_new || !s->Sdev) { delete s; return fail(LXW_ERR_NOMEM, "lxw_solver_create: device allocation failed"); }
+  }
   if (!d_area || !d_jinv || !d_nrm || !d_sdx || !d_nbr || !d_nbk || !s->dw.trace || !s->dw.flux || !s->dw.prop ||
       !s->dw.smax || !s->dw.status || !s->dw.diag || !s->Qdev) {
     delete s;
@@ -459,7 +474,8 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
   cudaError_t e4 = cudaMemcpy(d_sdx, sdx.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
   cudaError_t e5 = cudaMemcpy(d_nbr, nbr.data(), sizeof(int) * E * N, cudaMemcpyHostToDevice);
   cudaError_t e6 = cudaMemcpy(d_nbk, nbk.data(), sizeof(int) * E * N, cudaMemcpyHostToDevice);
-  if (e1 || e2 || e3 || e4 || e5 || e6 || upload_tables(s->kind, degree, s->tab)) {
+  if (e1 || e2 || e3 || e4 || e5 || e6 || upload_tables(s->kind, degree, s->tab) ||
+      (s->mixed && upload_tables_mx(s->kind, degree, s->tab))) {
     delete s;
     return fail(LXW_ERR_CUDA, "lxw_solver_create: upload failed");
   }
@@ -506,9 +522,15 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   return a;
 }
 
+static int do_step(lxw_solver* s, double* Q, const StepArgs& a, cudaStream_t st, void** ev = nullptr,
+                   int upto = 99) {
+  if (s->mixed) return launch_step_mx(s->kind, s->deg, s->dm, s->dwm, Q, a, st, s->opt.block_threads, ev, upto);
+  return launch_step(s->kind, s->deg, s->dm, s->dw, Q, a, st, s->opt.block_threads, ev, upto);
+}
+
 static lxw_status read_diag(lxw_solver* s, double dt, double cfl, lxw_diag* d) {
   double* h = s->host_diag;
-  LXW_CUDA(cudaMemcpyAsync(h, s->dw.diag, diag_bytes(), cudaMemcpyDeviceToHost, s->stream));
+  LXW_CUDA(cudaMemcpyAsync(h, s->dw.diag, sizeof(DiagBlock), cudaMemcpyDeviceToHost, s->stream));
   LXW_CUDA(cudaMemcpyAsync(h + 32, s->dw.smax, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream));
   LXW_CUDA(cudaMemcpyAsync(h + 33, s->dw.status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s->stream));
   LXW_CUDA(cudaStreamSynchronize(s->stream));
@@ -525,6 +547,9 @@ static lxw_status read_diag(lxw_solver* s, double dt, double cfl, lxw_diag* d) {
   d->min_rho = v[4]; d->min_p = v[5];
   d->n_mom = v[6]; d->n_edge = v[7]; d->n_sc = v[8];
   d->status = (int)st;
+  const DiagBlock* blk = reinterpret_cast<const DiagBlock*>(h);
+  d->n_fp64_moment = (double)blk->fb_mom;
+  d->n_fp64_edge = (double)blk->fb_edge;
   if (st & LXW_ST_NONPOSITIVE) return fail(LXW_ERR_NONPOSITIVE, "lxw_step: non-positive cell average at step start");
   if (st & LXW_ST_CFL) return fail(LXW_ERR_CFL, "lxw_step: Gamma^rho < 0 (dt above the low-order CFL bound)");
   if (st & LXW_ST_NAN) return fail(LXW_ERR_NAN, "lxw_step: non-finite state");
@@ -536,7 +561,7 @@ lxw_status lxw_step(lxw_solver* s, double* Q, double dt, double cfl, lxw_diag* d
   if (!s || !Q) return fail(LXW_ERR_ARG, "lxw_step: null argument");
   if (!(dt > 0.0) && !(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_step: need dt > 0 or cfl > 0");
   StepArgs a = make_args(s, dt, cfl, diag != nullptr, theta_cell, theta_edge);
-  if (launch_step(s->kind, s->deg, s->dm, s->dw, Q, a, s->stream, s->opt.block_threads))
+  if (do_step(s, Q, a, s->stream))
     return fail(LXW_ERR_CUDA, std::string("lxw_step: launch failed: ") + cudaGetErrorString(cudaGetLastError()));
   if (diag) return read_diag(s, dt, cfl, diag);
   return LXW_OK;
@@ -553,7 +578,7 @@ lxw_status lxw_run(lxw_solver* s, double* Q, int nsteps, double cfl, lxw_diag* d
       StepArgs a = make_args(s, 0.0, cfl, 0, nullptr, nullptr);
       cudaGraph_t g = nullptr;
       LXW_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-      int rc = launch_step(s->kind, s->deg, s->dm, s->dw, Q, a, s->cap_stream, s->opt.block_threads);
+      int rc = do_step(s, Q, a, s->cap_stream);
       cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
       if (rc || ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail(LXW_ERR_CUDA, "lxw_run: graph capture failed"); }
       cudaError_t ie = cudaGraphInstantiate(&s->graph, g, 0);
@@ -571,24 +596,60 @@ lxw_status lxw_run_host(lxw_solver* s, double* Qh, int nsteps, double cfl, lxw_d
   if (!s || !Qh) return fail(LXW_ERR_ARG, "lxw_run_host: null argument");
   const size_t bytes = sizeof(double) * (size_t)s->N * 4 * s->ML;
   LXW_CUDA(cudaMemcpyAsync(s->Qdev, Qh, bytes, cudaMemcpyHostToDevice, s->stream));
-  lxw_status st = lxw_run(s, s->Qdev, nsteps, cfl, diag);
+  double* state = s->Qdev;
+  if (s->mixed) {
+    if (launch_pack(s->ML, s->N, s->Qdev, s->Sdev, s->stream)) return fail(LXW_ERR_CUDA, "lxw_run_host: pack failed");
+    state = s->Sdev;
+  }
+  lxw_status st = lxw_run(s, state, nsteps, cfl, diag);
   if (st != LXW_OK && st != LXW_ERR_NONPOSITIVE && st != LXW_ERR_CFL && st != LXW_ERR_NAN) return st;
+  if (s->mixed && launch_unpack(s->ML, s->N, s->Sdev, s->Qdev, s->stream))
+    return fail(LXW_ERR_CUDA, "lxw_run_host: unpack failed");
   LXW_CUDA(cudaMemcpyAsync(Qh, s->Qdev, bytes, cudaMemcpyDeviceToHost, s->stream));
   LXW_CUDA(cudaStreamSynchronize(s->stream));
   return st;
 }
 
+size_t lxw_state_bytes(const lxw_solver* s) {
+  if (!s) return 0;
+  if (s->mixed) return sizeof(double) * 4 * (size_t)s->N + sizeof(float) * 4 * (size_t)(s->ML - 1) * s->N;
+  return sizeof(double) * 4 * (size_t)s->ML * s->N;
+}
+
+lxw_status lxw_state_pack(lxw_solver* s, const double* Q64, void* state) {
+  if (!s || !Q64 || !state) return fail(LXW_ERR_ARG, "lxw_state_pack: null argument");
+  if (!s->mixed) {
+    LXW_CUDA(cudaMemcpyAsync(state, Q64, lxw_state_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+    return LXW_OK;
+  }
+  if (launch_pack(s->ML, s->N, Q64, (double*)state, s->stream)) return fail(LXW_ERR_CUDA, "lxw_state_pack: launch failed");
+  return LXW_OK;
+}
+
+lxw_status lxw_state_unpack(lxw_solver* s, const void* state, double* Q64) {
+  if (!s || !Q64 || !state) return fail(LXW_ERR_ARG, "lxw_state_unpack: null argument");
+  if (!s->mixed) {
+    LXW_CUDA(cudaMemcpyAsync(Q64, state, lxw_state_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+    return LXW_OK;
+  }
+  if (launch_unpack(s->ML, s->N, (const double*)state, Q64, s->stream))
+    return fail(LXW_ERR_CUDA, "lxw_state_unpack: launch failed");
+  return LXW_OK;
+}
+
 lxw_status lxw_moment_limit(lxw_solver* s, double* Q, double* theta, double* s_dev) {
   if (!s || !Q) return fail(LXW_ERR_ARG, "lxw_moment_limit: null argument");
   StepArgs a = make_args(s, 0.0, 0.0, 0, nullptr, nullptr);
-  if (launch_moment_limit(s->kind, s->deg, s->dm, s->dw, Q, a, theta, s->stream, s->opt.block_threads))
-    return fail(LXW_ERR_CUDA, "lxw_moment_limit: launch failed");
+  int rc = s->mixed ? launch_moment_limit_mx(s->kind, s->deg, s->dm, s->dwm, Q, a, theta, s->stream, s->opt.block_threads)
+                    : launch_moment_limit(s->kind, s->deg, s->dm, s->dw, Q, a, theta, s->stream, s->opt.block_threads);
+  if (rc) return fail(LXW_ERR_CUDA, "lxw_moment_limit: launch failed");
   if (s_dev && launch_copy_speed(s->dw, s_dev, s->stream)) return fail(LXW_ERR_CUDA, "lxw_moment_limit: launch failed");
   return LXW_OK;
 }
 
 lxw_status lxw_shock_limit(lxw_solver* s, double* Q, double* theta) {
   if (!s || !Q) return fail(LXW_ERR_ARG, "lxw_shock_limit: null argument");
+  if (s->mixed) return fail(LXW_ERR_ARG, "lxw_shock_limit: the mixed form runs the shock limiter inside lxw_step only");
   StepArgs a = make_args(s, 0.0, 0.0, 0, nullptr, nullptr);
   if (launch_shock_limit(s->kind, s->deg, s->dm, Q, a, theta, s->stream, s->opt.block_threads))
     return fail(LXW_ERR_CUDA, "lxw_shock_limit: launch failed");
@@ -602,7 +663,7 @@ lxw_status lxw_step_phases(lxw_solver* s, double* Q, double dt, double cfl, int 
   if (!(dt > 0.0) && !(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_step_phases: need dt > 0 or cfl > 0");
   StepArgs a = make_args(s, dt, cfl, 0, nullptr, nullptr);
   s->last_dt_in = dt; s->last_cfl = cfl;
-  if (launch_step(s->kind, s->deg, s->dm, s->dw, Q, a, s->stream, s->opt.block_threads, nullptr, nphases))
+  if (do_step(s, Q, a, s->stream, nullptr, nphases))
     return fail(LXW_ERR_CUDA, "lxw_step_phases: launch failed");
   return LXW_OK;
 }
@@ -612,6 +673,23 @@ lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* out, size_t coun
   const size_t N = s->N, E = s->E, MQ = s->tab.MQ;
   const double* src = nullptr;
   size_t n = 0;
+  if (s->mixed && (which == 0 || which == 1)) {
+    // FP32 buffers: traces [E][MQ][8][N]; f^LxW [E][4][N] returned as [E][8][N] with zero f^LxF
+    const size_t nf = which == 0 ? E * MQ * 8 * N : E * 4 * N, nout = which == 0 ? nf : E * 8 * N;
+    if (count < nout) return fail(LXW_ERR_ARG, "lxw_workspace_copy: buffer too small");
+    std::vector<float> tmp(nf);
+    LXW_CUDA(cudaMemcpyAsync(tmp.data(), which == 0 ? (const void*)s->dwm.trace : (const void*)s->dwm.fw,
+                             nf * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    LXW_CUDA(cudaStreamSynchronize(s->stream));
+    if (which == 0) {
+      for (size_t k = 0; k < nf; ++k) out[k] = tmp[k];
+    } else {
+      for (size_t k = 0; k < E; ++k)
+        for (size_t c = 0; c < 8; ++c)
+          for (size_t i = 0; i < N; ++i) out[(k * 8 + c) * N + i] = c < 4 ? tmp[(k * 4 + c) * N + i] : 0.0;
+    }
+    return LXW_OK;
+  }
   if (which == 0) { src = s->dw.trace; n = E * MQ * 8 * N; }
   else if (which == 1) { src = s->dw.flux; n = E * 8 * N; }
   else if (which == 2) { src = s->dw.prop; n = E * N; }
@@ -635,7 +713,7 @@ lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* out, size_t coun
 lxw_status lxw_profile_step(lxw_solver* s, double* Q, double cfl, float* ms) {
   if (!s || !Q || !ms || !(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_profile_step: bad argument");
   StepArgs a = make_args(s, 0.0, cfl, 0, nullptr, nullptr);
-  if (launch_step(s->kind, s->deg, s->dm, s->dw, Q, a, s->stream, s->opt.block_threads, s->events))
+  if (do_step(s, Q, a, s->stream, s->events))
     return fail(LXW_ERR_CUDA, "lxw_profile_step: launch failed");
   const int n = step_launch_count(0, s->opt.shock_limiter);
   LXW_CUDA(cudaEventSynchronize((cudaEvent_t)s->events[n]));

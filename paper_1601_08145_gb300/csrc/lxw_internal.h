@@ -57,6 +57,25 @@ struct DevWork {
   double* diag;           // [16] reduction slots (see lxw_kernels.cu)
 };
 
+// Workspace of the mixed-precision form (FP32 bulk, FP64 averages).
+struct DevWorkMx {
+  float* trace;           // [E][MQ][8][N]: q (4) and n_out . F_T (4), FP32
+  float* fw;              // [E][4][N]: outward f^LxW, FP32 sums
+  double* prop;           // [E][N]: Lambda proposals
+  double* avg_new;        // [4][N]: updated averages before the shock limiter commits them
+  unsigned long long* smax;
+  unsigned int* status;
+  double* diag;           // DiagBlock
+};
+
+// Diagnostics block on the device (both forms).
+struct DiagBlock {
+  double sum[4];
+  unsigned long long minr, minp;      // order-preserving bits of min rho, min p
+  unsigned long long nmom, nedge, nsc;
+  unsigned long long fb_mom, fb_edge; // mixed form: cells that took the FP64 limiter path
+};
+
 struct StepArgs {
   double dt_in, cfl, gamma, eps0, alpha0;
   int shock_limiter;
@@ -86,5 +105,15 @@ int launch_project(const ProjTables& t, int N, double gamma, const double* prim,
                    void* stream);
 int launch_copy_speed(const DevWork& w, double* s_dev, void* stream);
 int step_launch_count(int want_diag, int shock_limiter);
+
+// Mixed-precision form (lxw_kernels_mx.cu).  State layout: averages double
+// [4][N] followed by higher modes float [4][ML-1][N].
+int upload_tables_mx(int kind, int deg, const Tables& t);
+int launch_step_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state,
+                   const StepArgs& a, void* stream, int block, void** events = nullptr, int upto = 99);
+int launch_moment_limit_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state,
+                           const StepArgs& a, double* theta, void* stream, int block);
+int launch_pack(int ML, int N, const double* Q64, double* state, void* stream);
+int launch_unpack(int ML, int N, const double* state, double* Q64, void* stream);
 
 }  // namespace lxw

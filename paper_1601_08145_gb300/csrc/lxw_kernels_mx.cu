@@ -1,0 +1,946 @@
+// lxw_kernels_mx.cu -- mixed-precision form of the LxW-DG step for sm_103a.
+//
+// GB300 runs FP32 fused multiply-adds ~60x faster than FP64 ones, so the
+// bulk of the step -- point values, the CK time-averaged flux, the
+// projections, the LLF point fluxes, volume and edge integrals -- runs in
+// FP32 with FP32 higher modes and traces.  FP64 stays where the positivity
+// guarantee lives (Sec. 3): the cell averages and their blended update
+// (Step 6), the Lax-Friedrichs fluxes that enter that update, the Gamma /
+// Lambda / box-corner / mu solve of the flux limiter (Steps 4-5) and the
+// moment limiter's theta (Sec. 3.1).  Those FP64 solves run only where an
+// FP32 screen with an explicit error margin cannot show that the exact
+// answer is theta = 1 (no limiting); where it can, the FP64 computation
+// would return exactly 1 and is skipped.
+//
+// State layout: averages double [4][N], then higher modes float [4][ML-1][N]
+// (structure of arrays: a warp's loads of one coefficient are coalesced).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "lxw_internal.h"
+
+namespace lxw {
+namespace {
+
+struct TablesF {
+  float w[kMaxQ];
+  float ew[kMaxMQ];
+  float phi[kMaxPts][kMaxML];
+  float dxi[kMaxPts][kMaxML];
+  float deta[kMaxPts][kMaxML];
+};
+__constant__ TablesF c_tabf[4];
+// exact (FP64) basis values at the limiter points, for the FP64 moment-limiter path
+__constant__ double c_phi64[4][kMaxPts][kMaxML];
+
+constexpr float kTol = 1e-5f;            // relative margin of the FP32 screens (FP32 error ~5e-7)
+constexpr float kSpeedInflate = 1.00001f; // s from FP32 point values, inflated to bound the exact one
+
+// ----------------------------------------------------------- FP32 physics
+struct PtF {
+  float r, m, n, e, ri, u, v, p;
+};
+__device__ __forceinline__ PtF ptf(float g1, float r, float m, float n, float e) {
+  PtF s;
+  s.r = r; s.m = m; s.n = n; s.e = e;
+  s.ri = 1.0f / r;
+  s.u = m * s.ri; s.v = n * s.ri;
+  s.p = g1 * (e - 0.5f * (m * s.u + n * s.v));
+  return s;
+}
+__device__ __forceinline__ void fluxf(const PtF& s, float F[4], float G[4]) {
+  float h = s.e + s.p;
+  F[0] = s.m; F[1] = s.m * s.u + s.p; F[2] = s.m * s.v; F[3] = h * s.u;
+  G[0] = s.n; G[1] = s.n * s.u; G[2] = s.n * s.v + s.p; G[3] = h * s.v;
+}
+__device__ __forceinline__ void d1f(float g1, const PtF& s, const float w[4], float F[4], float G[4], float& du,
+                                    float& dv, float& dp) {
+  du = (w[1] - s.u * w[0]) * s.ri;
+  dv = (w[2] - s.v * w[0]) * s.ri;
+  float dK = s.u * w[1] + s.v * w[2] - 0.5f * (s.u * s.u + s.v * s.v) * w[0];
+  dp = g1 * (w[3] - dK);
+  float h = s.e + s.p, dh = w[3] + dp;
+  F[0] = w[1]; F[1] = w[1] * s.u + s.m * du + dp; F[2] = w[1] * s.v + s.m * dv; F[3] = dh * s.u + h * du;
+  G[0] = w[2]; G[1] = w[2] * s.u + s.n * du; G[2] = w[2] * s.v + s.n * dv + dp; G[3] = dh * s.v + h * dv;
+}
+__device__ __forceinline__ void d2f(float g1, const PtF& s, const float w[4], float du, float dv, float dp,
+                                    float F[4], float G[4]) {
+  float ddu = -2.0f * du * w[0] * s.ri, ddv = -2.0f * dv * w[0] * s.ri;
+  float ddp = -g1 * s.r * (du * du + dv * dv);
+  float h = s.e + s.p, dh = w[3] + dp;
+  F[0] = 0.0f; F[1] = 2.0f * w[1] * du + s.m * ddu + ddp; F[2] = 2.0f * w[1] * dv + s.m * ddv;
+  F[3] = ddp * s.u + 2.0f * dh * du + h * ddu;
+  G[0] = 0.0f; G[1] = 2.0f * w[2] * du + s.n * ddu; G[2] = 2.0f * w[2] * dv + s.n * ddv + ddp;
+  G[3] = ddp * s.v + 2.0f * dh * dv + h * ddv;
+}
+__device__ __forceinline__ float speedf(float g, float r, float m, float n, float e) {
+  float ri = 1.0f / r, k2 = m * m + n * n;
+  float p = (g - 1.0f) * (e - 0.5f * k2 * ri);
+  p = p > 0.0f ? p : 0.0f;
+  return sqrtf(k2) * ri + sqrtf(g * p * ri);
+}
+template <typename T>
+__device__ __forceinline__ void ghostq(int bc, T nxh, T nyh, const T qi[4], T qo[4]) {
+  qo[0] = qi[0]; qo[3] = qi[3];
+  if (bc == LXW_BC_REFLECT) {
+    T mn = qi[1] * nxh + qi[2] * nyh;
+    qo[1] = qi[1] - T(2) * mn * nxh;
+    qo[2] = qi[2] - T(2) * mn * nyh;
+  } else {
+    qo[1] = qi[1]; qo[2] = qi[2];
+  }
+}
+
+// ----------------------------------------------------------- FP64 helpers
+__device__ __forceinline__ void flux64(double g1, const double q[4], double F[4], double G[4]) {
+  double ri = 1.0 / q[0];
+  double u = q[1] * ri, v = q[2] * ri;
+  double p = g1 * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+  double h = q[3] + p;
+  F[0] = q[1]; F[1] = q[1] * u + p; F[2] = q[1] * v; F[3] = h * u;
+  G[0] = q[2]; G[1] = q[2] * u; G[2] = q[2] * v + p; G[3] = h * v;
+}
+// Lax-Friedrichs edge flux from two averages (Sec. 3.2), outward for the
+// element owning qi.  The two sides of an edge call it with (n, qi, qj) and
+// (-n, qj, qi) and get exact negatives.
+__device__ __forceinline__ void lxf64(double g1, double s, double nx, double ny, const double qi[4],
+                                      const double qj[4], double f[4]) {
+  double Fi[4], Gi[4], Fj[4], Gj[4];
+  flux64(g1, qi, Fi, Gi);
+  flux64(g1, qj, Fj, Gj);
+  const double hs = 0.5 * s * sqrt(nx * nx + ny * ny);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    double ai = __fma_rn(nx, Fi[v], __dmul_rn(ny, Gi[v]));
+    double aj = __fma_rn(nx, Fj[v], __dmul_rn(ny, Gj[v]));
+    f[v] = __fma_rn(-hs, __dsub_rn(qj[v], qi[v]), __dmul_rn(0.5, __dadd_rn(ai, aj)));
+  }
+}
+
+__device__ __forceinline__ unsigned long long obits(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double step_dt_mx(const DevWorkMx& w, const DevMesh& m, const StepArgs& a) {
+  double s = __longlong_as_double((long long)*w.smax);
+  return a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin / s;
+}
+
+// accessors of the packed state
+struct MxState {
+  double* avg;   // [4][N]
+  float* hi;     // [4][ML-1][N]
+};
+template <int ML>
+__device__ __forceinline__ MxState mx_state(double* state, int N) {
+  MxState st;
+  st.avg = state;
+  st.hi = reinterpret_cast<float*>(state + 4 * (size_t)N);
+  return st;
+}
+template <int ML>
+__device__ __forceinline__ float& hi_at(const MxState& st, int N, int v, int l, int i) {
+  return st.hi[((size_t)v * (ML - 1) + (l - 1)) * N + i];
+}
+
+__global__ void k_reset_mx(DevWorkMx w, int want_diag) {
+  *w.smax = 0ull;
+  *w.status = 0u;
+  if (want_diag) {
+    DiagBlock* d = reinterpret_cast<DiagBlock*>(w.diag);
+    for (int c = 0; c < 4; ++c) d->sum[c] = 0.0;
+    d->minr = d->minp = ~0ull;
+    d->nmom = d->nedge = d->nsc = d->fb_mom = d->fb_edge = 0ull;
+  }
+}
+
+__device__ __forceinline__ void block_max(float v, unsigned long long* dst) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(dst, (unsigned long long)__double_as_longlong((double)v * kSpeedInflate));
+}
+
+// ---------------------------------------------------------- k_moment_mx
+// Sec. 3.1.  FP32 screen: every limiter point has rho and p above their
+// floors by more than the FP32 error bound -> theta = 1 exactly.  Otherwise
+// the FP64 algorithm (Steps 0-2) runs on the promoted coefficients.
+template <int KD, int E, int ML, int NQ, int MQ>
+__global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+                                                   const StepArgs a, double* __restrict__ theta_out) {
+  constexpr int NPT = NQ + E * MQ;
+  const TablesF& t = c_tabf[KD];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = m.N;
+  float smax = 0.0f;
+  if (i < N) {
+    MxState st = mx_state<ML>(state, N);
+    const float g = (float)a.gamma, g1 = g - 1.0f;
+    double a64[4];
+    float a32[4], c[4][ML];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      a64[v] = st.avg[(size_t)v * N + i];
+      a32[v] = (float)a64[v];
+#pragma unroll
+      for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
+    }
+    // --- FP32 screen
+    bool clear = a32[0] > 0.0f;
+    const float eps0 = (float)a.eps0;
+    {
+      const float ri = 1.0f / a32[0];
+      const float pb = g1 * (a32[3] - 0.5f * (a32[1] * a32[1] + a32[2] * a32[2]) * ri);
+      const float bb = fabsf(a32[3]) + 0.5f * (a32[1] * a32[1] + a32[2] * a32[2]) * ri;
+      clear = clear && pb > kTol * g1 * bb;
+      const float er = fminf(eps0, 0.5f * a32[0]) * (1.0f + kTol);
+      const float ep = fminf(eps0, 0.5f * pb) * (1.0f + kTol);
+#pragma unroll 1
+      for (int p = 0; p < NPT; ++p) {
+        float q[4], S[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          float acc = a32[v], sa = fabsf(a32[v]);
+#pragma unroll
+          for (int l = 1; l < ML; ++l) {
+            float term = c[v][l] * t.phi[p][l];
+            acc += term; sa += fabsf(term);
+          }
+          q[v] = acc; S[v] = sa;
+        }
+        const float rinv = 1.0f / q[0];
+        const float u = q[1] * rinv, vv = q[2] * rinv;
+        const float pp = g1 * (q[3] - 0.5f * (q[1] * u + q[2] * vv));
+        const float B = S[3] + fabsf(u) * S[1] + fabsf(vv) * S[2] + 0.5f * (u * u + vv * vv) * S[0];
+        clear = clear && q[0] > er + kTol * S[0] && pp > ep + kTol * g1 * B;
+        smax = fmaxf(smax, speedf(g, q[0], q[1], q[2], q[3]));
+      }
+      if (clear) smax = fmaxf(smax, speedf(g, a32[0], a32[1], a32[2], a32[3]));
+    }
+    double th = 1.0;
+    if (!clear) {
+      // --- FP64 path: the algorithm of Sec. 3.1 on the promoted coefficients
+      atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->fb_mom, 1ull);
+      const double gg = a.gamma, gd1 = gg - 1.0;
+      const double rb = a64[0], mb = a64[1], nb = a64[2], eb = a64[3];
+      const double pb = rb > 0.0 ? gd1 * (eb - 0.5 * (mb * mb + nb * nb) / rb) : -1.0;
+      if (!(rb > 0.0) || !(pb > 0.0)) {
+        atomicOr(w.status, (unsigned)LXW_ST_NONPOSITIVE);
+        th = 0.0;
+      } else {
+        const double er = fmin(a.eps0, 0.5 * rb);
+        double thr = 1.0;
+#pragma unroll 1
+        for (int p = 0; p < NPT; ++p) {
+          double d = 0.0;
+#pragma unroll
+          for (int l = 1; l < ML; ++l) d = fma((double)c[0][l], c_phi64[KD][p][l], d);
+          double rm = rb + d;
+          if (rm < er) thr = fmin(thr, (rb - er) / (rb - rm));
+        }
+        const double ep = fmin(a.eps0, 0.5 * pb);
+        th = thr;
+#pragma unroll 1
+        for (int p = 0; p < NPT; ++p) {
+          double d[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            double acc = 0.0;
+#pragma unroll
+            for (int l = 1; l < ML; ++l) acc = fma((double)c[v][l], c_phi64[KD][p][l], acc);
+            d[v] = acc;
+          }
+          double r = rb + thr * d[0], mm = mb + thr * d[1], nn = nb + thr * d[2], ee = eb + thr * d[3];
+          double pt = gd1 * (ee - 0.5 * (mm * mm + nn * nn) / r);
+          if (pt < ep) th = fmin(th, thr * (pb - ep) / (pb - pt));
+        }
+        th = fmax(th, 0.0);
+      }
+      // speeds of the limited state (FP32)
+      smax = 0.0f;
+      if (th > 0.0 || a32[0] > 0.0f) {
+        const float thf = (float)th;
+        if (a32[0] > 0.0f) smax = speedf(g, a32[0], a32[1], a32[2], a32[3]);
+#pragma unroll 1
+        for (int p = 0; p < NPT; ++p) {
+          float q[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 1; l < ML; ++l) acc += c[v][l] * t.phi[p][l];
+            q[v] = a32[v] + thf * acc;
+          }
+          if (q[0] > 0.0f) smax = fmaxf(smax, speedf(g, q[0], q[1], q[2], q[3]));
+        }
+      }
+      if (th < 1.0) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+          for (int l = 1; l < ML; ++l) hi_at<ML>(st, N, v, l, i) = (float)(th * (double)c[v][l]);
+        if (a.want_diag) atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->nmom, 1ull);
+      }
+    }
+    if (theta_out) theta_out[i] = th;
+  }
+  block_max(smax, w.smax);
+}
+
+
+// ---------------------------------------------------------- k_ck_mx
+// Sec. 2.2-2.3 in FP32: contravariant flux projections, q_t, F_t,
+// projection, q_tt, F_tt, F_T; volume integral added to the FP32 higher
+// modes; traces (q, n_out.F_T) at the edge points.
+template <int KD, int E, int ML, int NQ, int MQ>
+__global__ void __launch_bounds__(128) k_ck_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+                                               const StepArgs a) {
+  constexpr int NPT = NQ + E * MQ;
+  const TablesF& t = c_tabf[KD];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = m.N;
+  if (i >= N) return;
+  MxState st = mx_state<ML>(state, N);
+  const float g1 = (float)(a.gamma - 1.0);
+  const double dt64 = step_dt_mx(w, m, a);
+  const float dt = (float)dt64, c1 = 0.5f * dt, c2 = (float)(dt64 * dt64 / 6.0);
+  float c[4][ML];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    c[v][0] = (float)st.avg[(size_t)v * N + i];
+#pragma unroll
+    for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
+  }
+  const float jxx = (float)m.jinv[i], jxy = (float)m.jinv[N + i];
+  const float jyx = (float)m.jinv[2 * N + i], jyy = (float)m.jinv[3 * N + i];
+  float Hx[4][ML], Hy[4][ML];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) { Hx[v][l] = 0.0f; Hy[v][l] = 0.0f; }
+#pragma unroll 1
+  for (int k = 0; k < NQ; ++k) {
+    float q[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int l = 0; l < ML; ++l) acc = fmaf(c[v][l], t.phi[k][l], acc);
+      q[v] = acc;
+    }
+    PtF s = ptf(g1, q[0], q[1], q[2], q[3]);
+    float F[4], G[4];
+    fluxf(s, F, G);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float fx = t.w[k] * (jxx * F[v] + jxy * G[v]);
+      float fy = t.w[k] * (jyx * F[v] + jyy * G[v]);
+#pragma unroll
+      for (int l = 0; l < ML; ++l) { Hx[v][l] = fmaf(fx, t.phi[k][l], Hx[v][l]); Hy[v][l] = fmaf(fy, t.phi[k][l], Hy[v][l]); }
+    }
+  }
+  float Tx[4][ML], Ty[4][ML];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) { Tx[v][l] = 0.0f; Ty[v][l] = 0.0f; }
+#pragma unroll 1
+  for (int k = 0; k < NQ; ++k) {
+    float q[4], qt[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float acc = 0.0f, dv = 0.0f;
+#pragma unroll
+      for (int l = 0; l < ML; ++l) {
+        acc = fmaf(c[v][l], t.phi[k][l], acc);
+        dv = fmaf(Hx[v][l], t.dxi[k][l], dv);
+        dv = fmaf(Hy[v][l], t.deta[k][l], dv);
+      }
+      q[v] = acc; qt[v] = -dv;
+    }
+    PtF s = ptf(g1, q[0], q[1], q[2], q[3]);
+    float F1[4], G1[4], du, dvv, dp;
+    d1f(g1, s, qt, F1, G1, du, dvv, dp);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float fx = t.w[k] * (jxx * F1[v] + jxy * G1[v]);
+      float fy = t.w[k] * (jyx * F1[v] + jyy * G1[v]);
+#pragma unroll
+      for (int l = 0; l < ML; ++l) { Tx[v][l] = fmaf(fx, t.phi[k][l], Tx[v][l]); Ty[v][l] = fmaf(fy, t.phi[k][l], Ty[v][l]); }
+    }
+  }
+  float Vv[4][ML];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Vv[v][l] = 0.0f;
+#pragma unroll 1
+  for (int p = 0; p < NPT; ++p) {
+    float q[4], qt[4], qtt[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float acc = 0.0f, e1 = 0.0f, e2 = 0.0f;
+#pragma unroll
+      for (int l = 0; l < ML; ++l) {
+        acc = fmaf(c[v][l], t.phi[p][l], acc);
+        e1 = fmaf(Hx[v][l], t.dxi[p][l], e1);
+        e1 = fmaf(Hy[v][l], t.deta[p][l], e1);
+        e2 = fmaf(Tx[v][l], t.dxi[p][l], e2);
+        e2 = fmaf(Ty[v][l], t.deta[p][l], e2);
+      }
+      q[v] = acc; qt[v] = -e1; qtt[v] = -e2;
+    }
+    PtF s = ptf(g1, q[0], q[1], q[2], q[3]);
+    float F[4], G[4], F1[4], G1[4], F2[4], G2[4], F3[4], G3[4];
+    float du, dvv, dp, eu, ev, ep;
+    fluxf(s, F, G);
+    d1f(g1, s, qt, F1, G1, du, dvv, dp);
+    d2f(g1, s, qt, du, dvv, dp, F2, G2);
+    d1f(g1, s, qtt, F3, G3, eu, ev, ep);
+    float FT[4], GT[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      FT[v] = F[v] + c1 * F1[v] + c2 * (F2[v] + F3[v]);
+      GT[v] = G[v] + c1 * G1[v] + c2 * (G2[v] + G3[v]);
+    }
+    if (p < NQ) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float fx = t.w[p] * (jxx * FT[v] + jxy * GT[v]);
+        float fy = t.w[p] * (jyx * FT[v] + jyy * GT[v]);
+#pragma unroll
+        for (int l = 1; l < ML; ++l) Vv[v][l] = fmaf(fx, t.dxi[p][l], fmaf(fy, t.deta[p][l], Vv[v][l]));
+      }
+    } else {
+      const int k = (p - NQ) / MQ, pe = (p - NQ) % MQ;
+      const float nx = (float)m.nrm[(2 * k) * N + i], ny = (float)m.nrm[(2 * k + 1) * N + i];
+      float* tr = w.trace + ((size_t)(k * MQ + pe) * 8) * N + i;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        tr[(size_t)v * N] = q[v];
+        tr[(size_t)(4 + v) * N] = nx * FT[v] + ny * GT[v];
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int l = 1; l < ML; ++l) hi_at<ML>(st, N, v, l, i) = c[v][l] + dt * Vv[v][l];
+}
+
+// ---------------------------------------------------------- k_edge_mx
+// Sec. 3.3 Step 3 in FP32 (LLF at the edge points in the owner's order, so
+// the two sides produce exact negatives; f^LxW; edge integral of the higher
+// modes) and Steps 4-5: an FP32 screen shows Lambda = 1 and mu_c = 1 for
+// every corner with an error margin, else the FP64 algorithm runs.
+template <int KD, int E, int ML, int NQ, int MQ>
+__global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+                                                 const StepArgs a) {
+  const TablesF& t = c_tabf[KD];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = m.N;
+  if (i >= N) return;
+  MxState st = mx_state<ML>(state, N);
+  const double s64 = __longlong_as_double((long long)*w.smax);
+  const double dt64 = step_dt_mx(w, m, a);
+  const float s = (float)s64, g1f = (float)(a.gamma - 1.0);
+  const double area = m.area[i];
+  const float dta = (float)(dt64 / area);
+  double qb64[4];
+  float qb[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) { qb64[v] = st.avg[(size_t)v * N + i]; qb[v] = (float)qb64[v]; }
+  float Ei[4][ML];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Ei[v][l] = 0.0f;
+  float fW[E][4], fF[E][4];
+  PtF sb = ptf(g1f, qb[0], qb[1], qb[2], qb[3]);
+  float Fb[4], Gb[4];
+  fluxf(sb, Fb, Gb);
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const int j = m.nbr[k * N + i];
+    const int kj = m.nbk[k * N + i];
+    const float nx = (float)m.nrm[(2 * k) * N + i], ny = (float)m.nrm[(2 * k + 1) * N + i];
+    const float ln = sqrtf(nx * nx + ny * ny);
+    const float hs = 0.5f * s * ln;
+    const bool owner = j < 0 || i < j || (i == j && k < kj);
+    float qn[4];
+    if (j >= 0) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) qn[v] = (float)st.avg[(size_t)v * N + j];
+    } else {
+      ghostq<float>(-1 - j, nx / ln, ny / ln, qb, qn);
+    }
+    {  // FP32 Lax-Friedrichs flux, used only by the screen
+      PtF sn = ptf(g1f, qn[0], qn[1], qn[2], qn[3]);
+      float Fn[4], Gn[4];
+      fluxf(sn, Fn, Gn);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float ai = nx * Fb[v] + ny * Gb[v], an = nx * Fn[v] + ny * Gn[v];
+        fF[k][v] = 0.5f * (ai + an) - hs * (qn[v] - qb[v]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) fW[k][v] = 0.0f;
+#pragma unroll
+    for (int qo = 0; qo < MQ; ++qo) {
+      const int p = owner ? qo : MQ - 1 - qo;
+      const float* tr = w.trace + ((size_t)(k * MQ + p) * 8) * N + i;
+      float qi[4], Fi[4], qx[4], Fx[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { qi[v] = tr[(size_t)v * N]; Fi[v] = tr[(size_t)(4 + v) * N]; }
+      if (j >= 0) {
+        const float* tj = w.trace + ((size_t)(kj * MQ + (MQ - 1 - p)) * 8) * N + j;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { qx[v] = tj[(size_t)v * N]; Fx[v] = -tj[(size_t)(4 + v) * N]; }
+      } else if (-1 - j == LXW_BC_REFLECT) {
+        const float nxh = nx / ln, nyh = ny / ln;
+        ghostq<float>(LXW_BC_REFLECT, nxh, nyh, qi, qx);
+        float R[4];
+        ghostq<float>(LXW_BC_REFLECT, nxh, nyh, Fi, R);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Fx[v] = -R[v];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { qx[v] = qi[v]; Fx[v] = Fi[v]; }
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float fs = __fmaf_rn(-hs, __fsub_rn(qx[v], qi[v]), __fmul_rn(0.5f, __fadd_rn(Fi[v], Fx[v])));
+        fW[k][v] = __fmaf_rn(0.5f * t.ew[qo], fs, fW[k][v]);
+        const float hw = 0.5f * t.ew[p] * fs;
+#pragma unroll
+        for (int l = 1; l < ML; ++l) Ei[v][l] = fmaf(hw, t.phi[NQ + k * MQ + p][l], Ei[v][l]);
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int l = 1; l < ML; ++l) hi_at<ML>(st, N, v, l, i) -= dta * Ei[v][l];
+
+  // ---- FP32 screen of Steps 4-5 (Lambda = 1 for all edges, mu = 1 for all corners)
+  const float tol = kTol;
+  const float Tdt = (float)(area / dt64);
+  float gam = Tdt * qb[0], negabs = 0.0f, errr = Tdt * fabsf(qb[0]);
+  float Sv[4], ql[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) { Sv[v] = fabsf(qb[v]); ql[v] = qb[v]; }
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    gam -= fF[k][0];
+    negabs += fmaxf(0.0f, fW[k][0] - fF[k][0]);
+    errr += fabsf(fF[k][0]) + fabsf(fW[k][0]);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      ql[v] -= dta * fF[k][v];
+      Sv[v] += dta * (fabsf(fF[k][v]) + fabsf(fW[k][v]));
+    }
+  }
+  bool clear = gam - Tdt * (float)a.eps0 - negabs > 2.0f * tol * errr && ql[0] > tol * Sv[0];
+  // kappa = min(eps0, p^LxF/2)/(gamma-1) of the FP64 solve, bounded from above
+  const float kl = 0.5f * (ql[1] * ql[1] + ql[2] * ql[2]) / ql[0];
+  const float pl32 = g1f * (ql[3] - kl);
+  const float kap = fminf((float)a.eps0, 0.5f * pl32 + tol * g1f * (fabsf(ql[3]) + kl)) / g1f;
+  const float herr = tol * (Sv[0] * Sv[3] + Sv[1] * Sv[1] + Sv[2] * Sv[2] + kap * Sv[0]);
+  auto hval = [&](const float q[4]) { return q[0] * q[3] - 0.5f * (q[1] * q[1] + q[2] * q[2]) - kap * q[0]; };
+  clear = clear && pl32 > 0.0f && hval(ql) > herr;
+#pragma unroll
+  for (int cm = 1; cm < (1 << E); ++cm) {
+    float qc[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float acc = ql[v];
+#pragma unroll
+      for (int k = 0; k < E; ++k)
+        if ((cm >> k) & 1) acc += dta * (fF[k][v] - fW[k][v]);
+      qc[v] = acc;
+    }
+    clear = clear && qc[0] > tol * Sv[0] && hval(qc) > herr;
+  }
+  double prop[E];
+  if (clear) {
+#pragma unroll
+    for (int k = 0; k < E; ++k) prop[k] = 1.0;
+  } else {
+    // ---- FP64 path (Sec. 3.3 Steps 4-5 as in the FP64 form)
+    atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->fb_edge, 1ull);
+    const double g1 = a.gamma - 1.0;
+    double fF64[E][4], fW64[E][4];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int j = m.nbr[k * N + i];
+      const double nx = m.nrm[(2 * k) * N + i], ny = m.nrm[(2 * k + 1) * N + i];
+      double qn[4];
+      if (j >= 0) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qn[v] = st.avg[(size_t)v * N + j];
+      } else {
+        const double ln = sqrt(nx * nx + ny * ny);
+        ghostq<double>(-1 - j, nx / ln, ny / ln, qb64, qn);
+      }
+      lxf64(g1, s64, nx, ny, qb64, qn, fF64[k]);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) fW64[k][v] = (double)fW[k][v];
+    }
+    const double dta64 = dt64 / area;
+    double Gam0 = area / dt64 * qb64[0];
+#pragma unroll
+    for (int k = 0; k < E; ++k) Gam0 -= fF64[k][0];
+    if (Gam0 < 0.0) atomicOr(w.status, (unsigned)LXW_ST_CFL);
+    double neg = 0.0;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      double df = fF64[k][0] - fW64[k][0];
+      if (df < 0.0) neg += df;
+    }
+    double ql64[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < E; ++k) acc += fF64[k][v];
+      ql64[v] = qb64[v] - dta64 * acc;
+    }
+    double er = fmax(fmin(a.eps0, 0.5 * ql64[0]), 0.0);
+    double lneg = 1.0;
+    if (neg < 0.0) lneg = fmin(1.0, fmax(0.0, (Gam0 - area / dt64 * er) / (-neg)));
+    double lam[E], dq[E][4];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      lam[k] = (fF64[k][0] - fW64[k][0]) < 0.0 ? lneg : 1.0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dq[k][v] = dta64 * lam[k] * (fF64[k][v] - fW64[k][v]);
+    }
+    const double pl = ql64[0] > 0.0 ? g1 * (ql64[3] - 0.5 * (ql64[1] * ql64[1] + ql64[2] * ql64[2]) / ql64[0]) : -1.0;
+    double mmin[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) mmin[k] = 1.0;
+    if (!(ql64[0] > 0.0) || !(pl > 0.0)) {
+#pragma unroll
+      for (int k = 0; k < E; ++k) mmin[k] = 0.0;
+    } else {
+      const double kap = fmin(a.eps0, 0.5 * pl) / g1;
+      const double h0 = ql64[0] * ql64[3] - 0.5 * (ql64[1] * ql64[1] + ql64[2] * ql64[2]) - kap * ql64[0];
+#pragma unroll 1
+      for (int cm = 1; cm < (1 << E); ++cm) {
+        double d[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < E; ++k)
+          if ((cm >> k) & 1)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) d[v] += dq[k][v];
+        const double h1 = ql64[0] * d[3] + d[0] * ql64[3] - (ql64[1] * d[1] + ql64[2] * d[2]) - kap * d[0];
+        const double h2 = d[0] * d[3] - 0.5 * (d[1] * d[1] + d[2] * d[2]);
+        double mu = 1.0;
+        if (!(ql64[0] + d[0] > 0.0) || h0 + h1 + h2 < 0.0) {
+          double disc = fmax(h1 * h1 - 4.0 * h0 * h2, 0.0);
+          double den = -h1 + sqrt(disc);
+          mu = den > 0.0 ? fmin(1.0, fmax(0.0, 2.0 * h0 / den)) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < E; ++k)
+          if ((cm >> k) & 1) mmin[k] = fmin(mmin[k], mu);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < E; ++k) prop[k] = lam[k] * mmin[k];
+  }
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    w.prop[k * N + i] = prop[k];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) w.fw[(size_t)(k * 4 + v) * N + i] = fW[k][v];
+  }
+}
+
+// ---------------------------------------------------------- k_update_mx
+// Sec. 3.3 Step 6 in FP64: theta_e = min of both proposals; the LxF flux is
+// evaluated (FP64, from the old averages) only on edges with theta_e < 1.
+// New averages go to avg_new; the old ones stay readable for the neighbours.
+template <int E, int ML>
+__global__ void __launch_bounds__(128) k_update_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+                                                   const StepArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = m.N;
+  if (i >= N) return;
+  MxState st = mx_state<ML>(state, N);
+  const double s64 = __longlong_as_double((long long)*w.smax);
+  const double dt = step_dt_mx(w, m, a);
+  const double g1 = a.gamma - 1.0;
+  double qb[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) qb[v] = st.avg[(size_t)v * N + i];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const int j = m.nbr[k * N + i];
+    double th = w.prop[k * N + i];
+    if (j >= 0) th = fmin(th, w.prop[m.nbk[k * N + i] * N + j]);
+    if (a.theta_edge) a.theta_edge[(size_t)i * E + k] = th;
+    double fw[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) fw[v] = (double)w.fw[(size_t)(k * 4 + v) * N + i];
+    if (th < 1.0) {
+      if (a.want_diag && (j < 0 || i < j || (i == j && k < m.nbk[k * N + i])))
+        atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->nedge, 1ull);
+      const double nx = m.nrm[(2 * k) * N + i], ny = m.nrm[(2 * k + 1) * N + i];
+      double qn[4], ff[4];
+      if (j >= 0) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qn[v] = st.avg[(size_t)v * N + j];
+      } else {
+        const double ln = sqrt(nx * nx + ny * ny);
+        ghostq<double>(-1 - j, nx / ln, ny / ln, qb, qn);
+      }
+      lxf64(g1, s64, nx, ny, qb, qn, ff);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[v] += th * fw[v] + (1.0 - th) * ff[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[v] += fw[v];
+    }
+  }
+  const double dta = dt / m.area[i];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) w.avg_new[(size_t)v * N + i] = qb[v] - dta * acc[v];
+}
+
+// ---------------------------------------------------------- k_shock_mx
+// Sec. 4.1 on the new state in FP32 (neighbour averages from avg_new), then
+// commits the new averages.  With the shock limiter off only the commit runs.
+template <int KD, int E, int ML, int NQ, int MQ>
+__global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+                                                  const StepArgs a, double* __restrict__ theta_out, int limit) {
+  constexpr int NPT = NQ + E * MQ;
+  const TablesF& t = c_tabf[KD];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = m.N;
+  if (i >= N) return;
+  MxState st = mx_state<ML>(state, N);
+  double an[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) an[v] = w.avg_new[(size_t)v * N + i];
+  if (limit) {
+    const float g1 = (float)(a.gamma - 1.0);
+    float c[4][ML];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      c[v][0] = (float)an[v];
+#pragma unroll
+      for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
+    }
+    float th = 1.0f;
+    if (!(c[0][0] > 0.0f)) {
+      th = 0.0f;
+    } else {
+      PtF sb = ptf(g1, c[0][0], c[1][0], c[2][0], c[3][0]);
+      const float wb[4] = {sb.r, sb.u, sb.v, sb.p};
+      const float dx = (float)m.sdx[i];
+      const float al = (float)a.alpha0 * dx * sqrtf(dx);
+      float Mx[4], Mn[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { Mx[v] = wb[v] + al; Mn[v] = wb[v] - al; }
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        const int j = m.nbr[k * N + i];
+        float qn[4];
+        if (j >= 0) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) qn[v] = (float)w.avg_new[(size_t)v * N + j];
+        } else {
+          const float nx = (float)m.nrm[(2 * k) * N + i], ny = (float)m.nrm[(2 * k + 1) * N + i];
+          const float ln = sqrtf(nx * nx + ny * ny);
+          const float qbv[4] = {c[0][0], c[1][0], c[2][0], c[3][0]};
+          ghostq<float>(-1 - j, nx / ln, ny / ln, qbv, qn);
+        }
+        if (!(qn[0] > 0.0f)) continue;
+        PtF sn = ptf(g1, qn[0], qn[1], qn[2], qn[3]);
+        const float wn[4] = {sn.r, sn.u, sn.v, sn.p};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { Mx[v] = fmaxf(Mx[v], wn[v]); Mn[v] = fminf(Mn[v], wn[v]); }
+      }
+      float hx[4], hn[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { hx[v] = -3e38f; hn[v] = 3e38f; }
+      bool bad = false;
+#pragma unroll 1
+      for (int p = 0; p < NPT; ++p) {
+        float q[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int l = 0; l < ML; ++l) acc = fmaf(c[v][l], t.phi[p][l], acc);
+          q[v] = acc;
+        }
+        if (!(q[0] > 0.0f)) { bad = true; break; }
+        PtF sp = ptf(g1, q[0], q[1], q[2], q[3]);
+        const float wp[4] = {sp.r, sp.u, sp.v, sp.p};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { hx[v] = fmaxf(hx[v], wp[v]); hn[v] = fminf(hn[v], wp[v]); }
+      }
+      if (bad) {
+        th = 0.0f;
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          if (hx[v] > wb[v]) th = fminf(th, (Mx[v] - wb[v]) / (hx[v] - wb[v]));
+          if (hn[v] < wb[v]) th = fminf(th, (wb[v] - Mn[v]) / (wb[v] - hn[v]));
+        }
+        th = fmaxf(th, 0.0f);
+      }
+    }
+    if (th < 1.0f) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int l = 1; l < ML; ++l) hi_at<ML>(st, N, v, l, i) = th * c[v][l];
+      if (a.want_diag) atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->nsc, 1ull);
+    }
+    if (theta_out) theta_out[i] = th;
+  } else if (theta_out) {
+    theta_out[i] = 1.0;
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) st.avg[(size_t)v * N + i] = an[v];
+}
+
+template <int ML>
+__global__ void __launch_bounds__(256) k_diag_mx(const DevMesh m, const DevWorkMx w, const double* __restrict__ state,
+                                                 double gamma) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = m.N;
+  DiagBlock* d = reinterpret_cast<DiagBlock*>(w.diag);
+  if (i < N) {
+    double q[4];
+    for (int v = 0; v < 4; ++v) q[v] = state[(size_t)v * N + i];
+    double p = (gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+    bool finite = true;
+    for (int v = 0; v < 4; ++v) finite = finite && isfinite(q[v]);
+    const float* hi = reinterpret_cast<const float*>(state + 4 * (size_t)N);
+    for (int c = 0; c < 4 * (ML - 1); ++c) finite = finite && isfinite(hi[(size_t)c * N + i]);
+    if (!finite) atomicOr(w.status, (unsigned)LXW_ST_NAN);
+    const double ar = m.area[i];
+    for (int v = 0; v < 4; ++v) atomicAdd(&d->sum[v], ar * q[v]);
+    atomicMin(&d->minr, obits(q[0]));
+    atomicMin(&d->minp, obits(p));
+  }
+}
+
+__global__ void k_pack(int ML, int N, const double* __restrict__ Q64, double* __restrict__ state) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float* hi = reinterpret_cast<float*>(state + 4 * (size_t)N);
+  for (int v = 0; v < 4; ++v) {
+    state[(size_t)v * N + i] = Q64[((size_t)i * 4 + v) * ML];
+    for (int l = 1; l < ML; ++l) hi[((size_t)v * (ML - 1) + l - 1) * N + i] = (float)Q64[((size_t)i * 4 + v) * ML + l];
+  }
+}
+
+__global__ void k_unpack(int ML, int N, const double* __restrict__ state, double* __restrict__ Q64) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float* hi = reinterpret_cast<const float*>(state + 4 * (size_t)N);
+  for (int v = 0; v < 4; ++v) {
+    Q64[((size_t)i * 4 + v) * ML] = state[(size_t)v * N + i];
+    for (int l = 1; l < ML; ++l) Q64[((size_t)i * 4 + v) * ML + l] = (double)hi[((size_t)v * (ML - 1) + l - 1) * N + i];
+  }
+}
+
+inline int gridn(int N, int block) { return (N + block - 1) / block; }
+
+template <int KD, int E, int ML, int NQ, int MQ>
+int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const StepArgs& a, cudaStream_t st, int block,
+                 void** events, int upto) {
+  const int grid = gridn(m.N, block);
+  int ne = 0;
+  auto mark = [&]() { if (events) cudaEventRecord((cudaEvent_t)events[ne++], st); };
+  auto ok = [&]() { return cudaGetLastError() == cudaSuccess ? 0 : -1; };
+  mark();
+  k_reset_mx<<<1, 1, 0, st>>>(w, 1);
+  mark();
+  k_moment_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, a.theta_cell);
+  mark();
+  if (upto < 2) return ok();
+  k_ck_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a);
+  mark();
+  if (upto < 3) return ok();
+  k_edge_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a);
+  mark();
+  if (upto < 4) return ok();
+  k_update_mx<E, ML><<<grid, block, 0, st>>>(m, w, state, a);
+  mark();
+  const int limit = a.shock_limiter && upto >= 5;
+  k_shock_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, a.theta_cell ? a.theta_cell + m.N : nullptr,
+                                                        limit);
+  mark();
+  if (a.want_diag) k_diag_mx<ML><<<gridn(m.N, 256), 256, 0, st>>>(m, w, state, a.gamma);
+  return ok();
+}
+
+template <int KD, int E, int ML, int NQ, int MQ>
+int moment_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const StepArgs& a, double* theta,
+                   cudaStream_t st, int block) {
+  k_reset_mx<<<1, 1, 0, st>>>(w, 1);
+  k_moment_mx<KD, E, ML, NQ, MQ><<<gridn(m.N, block), block, 0, st>>>(m, w, state, a, theta);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+#define LXW_DISPATCH_MX(kind, deg, CALL)                                \
+  do {                                                                  \
+    if (kind == LXW_KIND_QUAD && deg == 2) return CALL(0, 4, 6, 9, 3);   \
+    if (kind == LXW_KIND_QUAD && deg == 3) return CALL(1, 4, 10, 16, 4); \
+    if (kind == LXW_KIND_TRI && deg == 2) return CALL(2, 3, 6, 9, 3);    \
+    if (kind == LXW_KIND_TRI && deg == 3) return CALL(3, 3, 10, 16, 4);  \
+    return -2;                                                          \
+  } while (0)
+
+int launch_step_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state, const StepArgs& a,
+                   void* stream, int block, void** events, int upto) {
+#define CALL_SMX(KD, E, ML, NQ, MQ) step_mx_impl<KD, E, ML, NQ, MQ>(m, w, state, a, (cudaStream_t)stream, block, events, upto)
+  LXW_DISPATCH_MX(kind, deg, CALL_SMX);
+#undef CALL_SMX
+}
+
+int launch_moment_limit_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state,
+                           const StepArgs& a, double* theta, void* stream, int block) {
+#define CALL_MMX(KD, E, ML, NQ, MQ) moment_mx_impl<KD, E, ML, NQ, MQ>(m, w, state, a, theta, (cudaStream_t)stream, block)
+  LXW_DISPATCH_MX(kind, deg, CALL_MMX);
+#undef CALL_MMX
+}
+
+int launch_pack(int ML, int N, const double* Q64, double* state, void* stream) {
+  k_pack<<<gridn(N, 128), 128, 0, (cudaStream_t)stream>>>(ML, N, Q64, state);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_unpack(int ML, int N, const double* state, double* Q64, void* stream) {
+  k_unpack<<<gridn(N, 128), 128, 0, (cudaStream_t)stream>>>(ML, N, state, Q64);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int upload_tables_mx(int kind, int deg, const Tables& t) {
+  const int kd = (kind == LXW_KIND_QUAD ? 0 : 2) + (deg == 3 ? 1 : 0);
+  TablesF f{};
+  for (int k = 0; k < kMaxQ; ++k) f.w[k] = (float)t.w[k];
+  for (int k = 0; k < kMaxMQ; ++k) f.ew[k] = (float)t.ew[k];
+  for (int p = 0; p < kMaxPts; ++p)
+    for (int l = 0; l < kMaxML; ++l) {
+      f.phi[p][l] = (float)t.phi[p][l];
+      f.dxi[p][l] = (float)t.dxi[p][l];
+      f.deta[p][l] = (float)t.deta[p][l];
+    }
+  if (cudaMemcpyToSymbol(c_tabf, &f, sizeof(TablesF), kd * sizeof(TablesF)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_phi64, t.phi, sizeof(t.phi), kd * sizeof(t.phi)) != cudaSuccess) return -1;
+  return 0;
+}
+
+}  // namespace lxw

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "liblxw.so")
 OK, ERR_ARG, ERR_CUDA, ERR_NONPOSITIVE, ERR_CFL, ERR_NAN, ERR_BOUNDS, ERR_TIMEOUT, ERR_NOMEM = range(9)
 BC_PERIODIC, BC_REFLECT, BC_TRANSPARENT = 0, 1, 2
 KIND_QUAD, KIND_TRI = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
 ST_NONPOSITIVE, ST_CFL, ST_NAN = 1, 2, 4
 
 # every extern "C" symbol declared in include/lxw.h
@@ -27,7 +28,7 @@ EXPORTS = [
     "lxw_solver_set_stream", "lxw_solver_info", "lxw_projection_points", "lxw_project",
     "lxw_step", "lxw_run", "lxw_run_host", "lxw_moment_limit", "lxw_shock_limit",
     "lxw_step_launches", "lxw_profile_step", "lxw_step_phases", "lxw_workspace_copy",
-    "lxw_moment_limit_noalloc", "lxw_fma_peak",
+    "lxw_moment_limit_noalloc", "lxw_fma_peak", "lxw_state_bytes", "lxw_state_pack", "lxw_state_unpack",
 ]
 
 
@@ -41,7 +42,8 @@ class Diag(C.Structure):
     _fields_ = [("s", C.c_double), ("dt", C.c_double), ("min_rho", C.c_double), ("min_p", C.c_double),
                 ("mass", C.c_double), ("momx", C.c_double), ("momy", C.c_double), ("energy", C.c_double),
                 ("n_mom", C.c_double), ("n_edge", C.c_double), ("n_sc", C.c_double),
-                ("status", C.c_int), ("reserved", C.c_int)]
+                ("status", C.c_int), ("reserved", C.c_int),
+                ("n_fp64_moment", C.c_double), ("n_fp64_edge", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -91,6 +93,10 @@ def lib():
     L.lxw_step_phases.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int]
     L.lxw_workspace_copy.argtypes = [_vp, C.c_int, _dp, C.c_size_t]
     L.lxw_fma_peak.argtypes = [C.c_int, _dp]
+    L.lxw_state_bytes.argtypes = [_vp]
+    L.lxw_state_bytes.restype = C.c_size_t
+    L.lxw_state_pack.argtypes = [_vp, _vp, _vp]
+    L.lxw_state_unpack.argtypes = [_vp, _vp, _vp]
     L.lxw_moment_limit_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp, _vp, _vp]
     _lib = L
     return L
@@ -165,9 +171,16 @@ class Solver:
         _check(lib().lxw_solver_info(handle, C.byref(N), C.byref(E), C.byref(ML), C.byref(npts), C.byref(nproj)))
         self.N, self.E, self.ML, self.npts, self.nproj = N.value, E.value, ML.value, npts.value, nproj.value
         self.mq = 3 if self.ML == 6 else 4     # edge points per edge: degree + 1
-
+        self.state_bytes = lib().lxw_state_bytes(handle)
+        self.mixed = self.state_bytes != self.N * 4 * self.ML * 8
     @property
     def state_shape(self):
+        """Shape of the float64 tensor holding the solver's state: Q[N][4][ML]
+        for FP64 solvers, the packed bytes (as float64 words) for mixed ones."""
+        return (self.state_bytes // 8,) if self.mixed else (self.N, 4, self.ML)
+
+    @property
+    def q64_shape(self):
         return (self.N, 4, self.ML)
 
     def __del__(self):
@@ -194,8 +207,35 @@ def lxw_projection_points(solver):
 
 
 def lxw_project(solver, prim, Q):
+    """Projection into Q64[N][4][ML] (pack it for mixed solvers)."""
     _check(lib().lxw_project(solver.h, _ptr(prim, (solver.N, solver.nproj, 4), "prim"),
-                             _ptr(Q, solver.state_shape, "Q")))
+                             _ptr(Q, solver.q64_shape, "Q")))
+
+
+def lxw_state_pack(solver, Q64, state):
+    _check(lib().lxw_state_pack(solver.h, _ptr(Q64, solver.q64_shape, "Q64"), _ptr(state, solver.state_shape, "state")))
+
+
+def lxw_state_unpack(solver, state, Q64):
+    _check(lib().lxw_state_unpack(solver.h, _ptr(state, solver.state_shape, "state"), _ptr(Q64, solver.q64_shape, "Q64")))
+
+
+def new_state(solver, Q64=None):
+    """A device state tensor for the solver, optionally packed from Q64."""
+    import torch
+    st = torch.zeros(solver.state_shape, dtype=torch.float64, device="cuda")
+    if Q64 is not None:
+        lxw_state_pack(solver, Q64, st)
+    return st
+
+
+def to_q64(solver, state):
+    import torch
+    if not solver.mixed:
+        return state
+    Q = torch.empty(solver.q64_shape, dtype=torch.float64, device="cuda")
+    lxw_state_unpack(solver, state, Q)
+    return Q
 
 
 def _diag_result(st, d):
@@ -224,10 +264,10 @@ def lxw_run(solver, Q, nsteps, cfl, diag=False):
 def lxw_run_host(solver, Qh, nsteps, cfl, diag=False):
     """Qh: host buffer (numpy float64 array or pinned CPU torch tensor) [N][4][ML]."""
     if isinstance(Qh, np.ndarray):
-        assert Qh.dtype == np.float64 and Qh.flags.c_contiguous and Qh.shape == solver.state_shape
+        assert Qh.dtype == np.float64 and Qh.flags.c_contiguous and Qh.shape == solver.q64_shape
         p = C.c_void_p(Qh.ctypes.data)
     else:
-        assert (not Qh.is_cuda) and Qh.element_size() == 8 and Qh.is_contiguous() and tuple(Qh.shape) == solver.state_shape
+        assert (not Qh.is_cuda) and Qh.element_size() == 8 and Qh.is_contiguous() and tuple(Qh.shape) == solver.q64_shape
         p = C.c_void_p(Qh.data_ptr())
     d = Diag() if diag else None
     st = _check(lib().lxw_run_host(solver.h, p, nsteps, cfl, C.byref(d) if d is not None else None),

@@ -1,0 +1,164 @@
+"""The mixed-precision form (FP32 bulk, FP64 averages / update / limiter
+solves) against the FP64 oracle and the FP64 GPU form.
+
+Tolerances follow from the arithmetic: one mixed step differs from the FP64
+step by FP32 rounding of the bulk terms (~1e-6 relative in the higher modes,
+~1e-7 of the flux increment in the averages); conservation stays at FP64
+round-off because both sides of an edge add the same FP32 flux, negated, in
+FP64; positivity of the averages is kept exactly by the FP64 limiter.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+QUAD, TRI = 0, 1
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_1601_08145_gb300 import build
+    build.build()
+    from paper_1601_08145_gb300 import lxw
+    return lxw
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.lib()
+    return oracle
+
+
+def solver(L, kind, deg, n, mixed=True, bc=(0, 0, 0, 0), box=(0.0, 1.0, 0.0, 1.0), tri_bc=None, **opt):
+    if kind == QUAD:
+        mesh = L.lxw_mesh_cartesian(n, n, box, bc)
+    else:
+        xy, tv = synth.structured_triangles(n, jitter=0.2, seed=20160129, box=box)
+        ebc = None if tri_bc is None else np.full((len(tv), 3), tri_bc, dtype=np.int32)
+        mesh = L.lxw_mesh_triangles(xy, tv, ebc)
+    o = L.lxw_options_default(precision=L.PREC_MIXED if mixed else L.PREC_FP64)
+    for k, v in opt.items():
+        setattr(o, k, v)
+    return L.lxw_solver_create(mesh, deg, o, stream=torch.cuda.current_stream())
+
+
+def oracle_solver(O, kind, deg, n, bc=(0, 0, 0, 0), box=(0.0, 1.0, 0.0, 1.0), tri_bc=None, **kw):
+    if kind == QUAD:
+        m = O.Mesh.cartesian(n, n, box, bc)
+    else:
+        xy, tv = synth.structured_triangles(n, jitter=0.2, seed=20160129, box=box)
+        ebc = None if tri_bc is None else np.full((len(tv), 3), tri_bc, dtype=np.int32)
+        m = O.Mesh.triangles(xy, tv, ebc)
+    return O.Solver(m, deg, **kw)
+
+
+def project(L, s, ic):
+    xy = L.lxw_projection_points(s)
+    r, u, v, p = ic(xy[..., 0], xy[..., 1])
+    prim = torch.from_numpy(np.stack(np.broadcast_arrays(r, u, v, p), axis=-1).copy()).cuda()
+    Q = torch.zeros(s.q64_shape, dtype=torch.float64, device="cuda")
+    L.lxw_project(s, prim, Q)
+    return Q
+
+
+@pytest.mark.parametrize("kind,deg", [(QUAD, 2), (TRI, 3)])
+def test_pack_roundtrip(L, kind, deg):
+    s = solver(L, kind, deg, 9)
+    Q0 = torch.from_numpy(synth.random_modal_state(s.N, s.ML, seed=3, amp=0.3)).cuda()
+    st = L.new_state(s, Q0)
+    Q1 = L.to_q64(s, st)
+    torch.cuda.synchronize()
+    assert torch.equal(Q1[:, :, 0], Q0[:, :, 0])                     # averages stay FP64
+    assert torch.equal(Q1[:, :, 1:], Q0[:, :, 1:].float().double())  # higher modes are FP32
+
+
+@pytest.mark.parametrize("kind,deg", [(QUAD, 2), (QUAD, 3), (TRI, 2), (TRI, 3)])
+def test_one_mixed_step_close_to_oracle(L, O, kind, deg):
+    bc = 2
+    s = solver(L, kind, deg, 12, bc=(bc,) * 4, tri_bc=bc if kind == TRI else None)
+    so = oracle_solver(O, kind, deg, 12, bc=(bc,) * 4, tri_bc=bc if kind == TRI else None)
+    Q0 = synth.random_modal_state(s.N, s.ML, seed=5 + deg, amp=0.3)
+    Q0[:, :, 1:] = Q0[:, :, 1:].astype(np.float32)                    # both start from FP32-representable modes
+    Qo = Q0.copy(); do = so.step(Qo, cfl=0.3)
+    st = L.new_state(s, torch.from_numpy(Q0).cuda())
+    d = L.lxw_step(s, st, 0.0, 0.3, diag=True)
+    Qg = L.to_q64(s, st).cpu().numpy()
+    assert d["status"] == 0 and do["status"] == 0
+    assert abs(d["s"] / do["s"] - 1) < 3e-5
+    sc = np.abs(Qo).max(axis=0, keepdims=True) + 1e-3
+    assert np.abs(Qg[:, :, 0] - Qo[:, :, 0]).max() < 1e-5 * np.abs(Qo[:, :, 0]).max()
+    assert (np.abs(Qg - Qo) / sc).max() < 1e-3
+    assert np.abs(Qg - Qo).sum() / np.abs(Qo).sum() < 1e-5
+
+
+def test_mixed_conservation_and_no_fallback_on_smooth_data(L):
+    s = solver(L, QUAD, 2, 32)
+    st = L.new_state(s, project(L, s, synth.ic_smooth))
+    d0 = L.lxw_step(s, st, 0.0, 0.1, diag=True)
+    for _ in range(30):
+        d = L.lxw_step(s, st, 0.0, 0.1, diag=True)
+        assert d["n_fp64_moment"] == 0 and d["n_fp64_edge"] == 0 and d["n_mom"] == 0 and d["n_edge"] == 0
+    for k in ("mass", "momx", "momy", "energy"):
+        assert abs(d[k] - d0[k]) <= 1e-13 * max(1.0, abs(d0[k]))
+
+
+def test_mixed_positivity_blast_and_rarefaction(L):
+    cases = [(QUAD, 2, 48, (1, 1, 1, 1), (-1.1, 1.1, -1.1, 1.1), synth.ic_blast(48), None),
+             (TRI, 2, 24, (0, 0, 0, 0), (0.0, 1.0, 0.0, 1.0), synth.ic_rarefy, None),
+             (TRI, 3, 16, (0, 0, 0, 0), (0.0, 1.0, 0.0, 1.0), synth.ic_rarefy, None)]
+    for kind, deg, n, bc, box, ic, tb in cases:
+        s = solver(L, kind, deg, n, bc=bc, box=box)
+        st = L.new_state(s, project(L, s, ic))
+        fb = 0
+        for k in range(120):
+            d = L.lxw_step(s, st, 0.0, 0.1, diag=True)
+            assert d["status"] == 0 and d["min_rho"] > 0 and d["min_p"] > 0, (kind, deg, k, d)
+            fb += d["n_fp64_moment"] + d["n_fp64_edge"]
+        assert fb < 0.5 * 120 * s.N                     # the FP32 screens decide most cells
+
+
+def test_mixed_l1_error_equals_fp64_on_exact_wave(L):
+    """Config of the smooth advected wave (32x32, P2, CFL 0.1, t = 0.1, all
+    limiters on): the mixed form's L1 density error against the exact
+    solution is within 5 % of the FP64 GPU form's."""
+    T = 0.1
+    errs = {}
+    for mixed in (False, True):
+        s = solver(L, QUAD, 2, 32, mixed=mixed)
+        Q = project(L, s, synth.ic_smooth)
+        st = L.new_state(s, Q) if mixed else Q
+        t = 0.0
+        while t < T - 1e-12:
+            d = L.lxw_step(s, st, 0.0, 0.1, diag=True)
+            t += d["dt"]
+        Qe = L.to_q64(s, st).cpu().numpy()
+        # error at the projection points with the oracle-independent rule of the library
+        xy = L.lxw_projection_points(s)
+        from oracle import oracle as O   # only to evaluate the modal field at points
+        so = O.Solver(O.Mesh.cartesian(32, 32), 2)
+        q = so.eval_projection_points(Qe)
+        w = so.projection_weights()
+        ex = synth.exact_smooth_density(xy[..., 0], xy[..., 1], t)
+        errs[mixed] = float(np.sum(w[None, :] * np.abs(q[..., 0] - ex)) / (32 * 32))
+    print("L1 errors fp64 / mixed", errs)
+    assert errs[True] <= 1.05 * errs[False]
+
+
+def test_mixed_run_graph_and_host_path(L):
+    s = solver(L, TRI, 2, 20)
+    Q = project(L, s, synth.ic_rarefy)
+    A = L.new_state(s, Q); B = L.new_state(s, Q)
+    for _ in range(5):
+        L.lxw_step(s, A, 0.0, 0.1)
+    L.lxw_run(s, B, 5, 0.1)
+    torch.cuda.synchronize()
+    assert torch.equal(A, B)
+    H = Q.cpu().numpy().copy()
+    L.lxw_run_host(s, H, 5, 0.1)
+    assert np.array_equal(H, L.to_q64(s, A).cpu().numpy())
