@@ -59,20 +59,23 @@ def ck_flops_per_element(kind, deg):
     return contract + 250 * npt
 
 
-FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64 (derived, and the measured probe)
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64 (recipe table; the FMA probe measures 1.253)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x 2 flop x max SM clock
 # DRAM bytes per k_ck launch from the ncu capture summarised in profiles/ (None until captured
 # for the current kernel version)
 CK_TRAFFIC_BYTES = 27_383_296 + 40_022_272   # k_ck of the FP64 form, profiles/k_ck_rarefy224_p2_fp64.md
+CK_MX_TRAFFIC_BYTES = None                   # k_ck_mx: not captured yet
 
 
-def build_workload(L, name, stream):
+def build_workload(L, name, stream, mixed):
     w = WORKLOADS[name]
     if w["kind"] == "tri":
         xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
         mesh = L.lxw_mesh_triangles(xy, tv)
     else:
         mesh = L.lxw_mesh_cartesian(w["n"], w["n"], w.get("box", (0.0, 1.0, 0.0, 1.0)), w.get("bc", (0, 0, 0, 0)))
-    sol = L.lxw_solver_create(mesh, w["deg"], stream=stream)
+    opt = L.lxw_options_default(precision=L.PREC_MIXED if mixed else L.PREC_FP64)
+    sol = L.lxw_solver_create(mesh, w["deg"], opt, stream=stream)
     return w, sol
 
 
@@ -82,9 +85,9 @@ def project(L, sol, w):
     xy = L.lxw_projection_points(sol)
     r, u, v, p = ic(xy[..., 0], xy[..., 1])
     prim = torch.from_numpy(np.stack(np.broadcast_arrays(r, u, v, p), axis=-1).copy()).cuda()
-    Q = torch.empty(sol.state_shape, dtype=torch.float64, device="cuda")
+    Q = torch.empty(sol.q64_shape, dtype=torch.float64, device="cuda")
     L.lxw_project(sol, prim, Q)
-    return Q
+    return L.new_state(sol, Q) if sol.mixed else Q
 
 
 class ClockSampler:
@@ -204,56 +207,73 @@ def main():
     if world > 1:
         dist.barrier()
     stream = torch.cuda.current_stream()
-    w, sol = build_workload(L, args.workload, stream)
-    Q = project(L, sol, w)
-    dof = sol.N * 4 * sol.ML
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     try:
-        fp64_probe = L.lxw_fma_peak(True)
+        probes = {"fp64": L.lxw_fma_peak(True), "fp32": L.lxw_fma_peak(False)}
     except Exception:
-        fp64_probe = None
-    for _ in range(max(args.warmup, 3)):
-        L.lxw_profile_step(sol, Q, w["cfl"])
-    torch.cuda.synchronize()
+        probes = {"fp64": None, "fp32": None}
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.5)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    phases = []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        phases.append(L.lxw_profile_step(sol, Q, w["cfl"]))
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    step_ms = [sum(p.values()) for p in phases]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
-    value = world * dof * args.steps / (total_ms / 1e3)
-    mean_phase = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
-    dom = max(mean_phase, key=mean_phase.get)
+    def timed_form(mixed, clocks=None):
+        w, sol = build_workload(L, args.workload, stream, mixed)
+        Q = project(L, sol, w)
+        for _ in range(max(args.warmup, 3)):
+            L.lxw_profile_step(sol, Q, w["cfl"])
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.5)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        phases = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            phases.append(L.lxw_profile_step(sol, Q, w["cfl"]))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clk = clocks.stop() if clocks else None
+        total_ms = sum(sum(p.values()) for p in phases)
+        if world > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = t.item()
+        dof = sol.N * 4 * sol.ML
+        mean_phase = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+        return dict(w=w, sol=sol, Q=Q, total_ms=total_ms, dof=dof, value=world * dof * args.steps / (total_ms / 1e3),
+                    phases=mean_phase, clocks=clk)
+
+    fp64 = timed_form(False)
+    mx = timed_form(True, ClockSampler(local))
+    w, sol, dof = mx["w"], mx["sol"], mx["dof"]
+
+    # accuracy of the mixed form: relative L1 distance of the density after the same steps
+    Qm = L.to_q64(sol, mx["Q"])
+    rho_m, rho_f = Qm[:, 0, 0], fp64["Q"][:, 0, 0]
+    l1_rel = (torch.abs(rho_m - rho_f).sum() / torch.abs(rho_f).sum()).item()
+
     flops = ck_flops_per_element(w["kind"], w["deg"]) * sol.N
-    ck_ms = mean_phase["ck"]
+    ck_ms = mx["phases"]["ck"]
     achieved = flops / (ck_ms / 1e3) / 1e12
-    roofline = {"kernel": "k_ck", "dominant_kernel": dom, "bound": "alu", "pipe": "fp64",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": CK_TRAFFIC_BYTES,
-                "peak_source": "derived (GB300 FP64 nominal, recipe table)",
-                "peak_measured_fma_probe": fp64_probe,
-                "frac_of_measured_probe": achieved / fp64_probe if fp64_probe else None,
+    dom = max(mx["phases"], key=mx["phases"].get)
+    roofline = {"kernel": "k_ck_mx", "dominant_kernel": dom, "bound": "alu", "pipe": "fp32",
+                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": CK_MX_TRAFFIC_BYTES,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                "peak_measured_fma_probe": probes["fp32"],
+                "frac_of_measured_probe": achieved / probes["fp32"] if probes["fp32"] else None,
                 "algorithmic_flops_per_launch": flops, "launch_ms": ck_ms}
+    f64_ck = fp64["phases"]["ck"]
+    f64_ach = flops / (f64_ck / 1e3) / 1e12
+    plain = {"value": fp64["value"], "ms_per_step": fp64["total_ms"] / args.steps, "phases_ms": fp64["phases"],
+             "roofline": {"kernel": "k_ck", "bound": "alu", "pipe": "fp64", "achieved": f64_ach,
+                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f64_ach / FP64_PEAK_TFLOPS,
+                          "traffic": CK_TRAFFIC_BYTES, "peak_measured_fma_probe": probes["fp64"]}}
 
     # end to end through the public C ABI on HOST memory: H2D of the state,
     # one step, D2H of the result, every step
-    Qh = torch.empty(sol.state_shape, dtype=torch.float64).pin_memory()
-    Qh.copy_(Q.cpu())
+    Qh = torch.empty(sol.q64_shape, dtype=torch.float64).pin_memory()
+    Qh.copy_(Qm.cpu())
     L.lxw_run_host(sol, Qh, 1, w["cfl"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -269,18 +289,21 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    out = {"metric": METRIC, "value": mx["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": mx["total_ms"] / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": w["desc"], "elements": sol.N, "degree": w["deg"], "dof_per_step": dof,
-                      "form": "plain FP64 GPU", "cfl": w["cfl"],
-                      "l2": "flushed between timed steps (256 MB write)",
+                      "form": "mixed: FP32 bulk, FP64 averages/update/limiter solves (learned indicator not built)",
+                      "cfl": w["cfl"], "l2": "flushed between timed steps (256 MB write)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "roofline": roofline,
            "e2e": e2e,
            "gpu_launches": args.steps * L.lxw_step_launches(sol),
-           "clocks": clk,
-           "phases_ms": mean_phase}
+           "clocks": mx["clocks"],
+           "phases_ms": mx["phases"],
+           "plain_fp64": plain,
+           "speedup_vs_plain_fp64": mx["value"] / fp64["value"],
+           "l1_rel_density_mixed_vs_fp64": l1_rel}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], _, _ = cpu_baseline(args.workload)
     print(json.dumps(out))

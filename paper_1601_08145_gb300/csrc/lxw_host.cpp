@@ -656,7 +656,9 @@ lxw_status lxw_shock_limit(lxw_solver* s, double* Q, double* theta) {
   return LXW_OK;
 }
 
-int lxw_step_launches(const lxw_solver* s) { return s ? step_launch_count(0, s->opt.shock_limiter) : 0; }
+// the mixed form always launches its shock kernel (it also commits the new averages)
+static int launches_of(const lxw_solver* s) { return s->mixed ? 6 : step_launch_count(0, s->opt.shock_limiter); }
+int lxw_step_launches(const lxw_solver* s) { return s ? launches_of(s) : 0; }
 
 lxw_status lxw_step_phases(lxw_solver* s, double* Q, double dt, double cfl, int nphases) {
   if (!s || !Q || nphases < 1) return fail(LXW_ERR_ARG, "lxw_step_phases: bad argument");
@@ -715,7 +717,7 @@ lxw_status lxw_profile_step(lxw_solver* s, double* Q, double cfl, float* ms) {
   StepArgs a = make_args(s, 0.0, cfl, 0, nullptr, nullptr);
   if (do_step(s, Q, a, s->stream, s->events))
     return fail(LXW_ERR_CUDA, "lxw_profile_step: launch failed");
-  const int n = step_launch_count(0, s->opt.shock_limiter);
+  const int n = launches_of(s);
   LXW_CUDA(cudaEventSynchronize((cudaEvent_t)s->events[n]));
   for (int k = 0; k < n; ++k) LXW_CUDA(cudaEventElapsedTime(&ms[k], (cudaEvent_t)s->events[k], (cudaEvent_t)s->events[k + 1]));
   return LXW_OK;
