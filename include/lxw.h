@@ -177,11 +177,12 @@ lxw_status lxw_shock_limit(lxw_solver* s, double* Q_dev, double* theta_dev);
 /* Number of kernel launches one lxw_step enqueues (diag_host NULL). */
 int lxw_step_launches(const lxw_solver* s);
 
-/* lxw_step (dt from cfl, no diagnostics) with a CUDA event recorded on the
- * solver's stream around each kernel; synchronises and writes the duration
- * in milliseconds of each launch to ms_host[lxw_step_launches(s)] in launch
- * order (reset, moment, ck, edge, update[, shock]).  Tracing aid: the events
- * are created with the solver. */
+/* lxw_step (dt from cfl, no diagnostics) replayed from a CUDA graph with an
+ * event node around each kernel (captured on first use, rebuilt when Q_dev
+ * or cfl change), on the solver's stream; synchronises and writes the device
+ * duration in milliseconds of each launch to ms_host[lxw_step_launches(s)]
+ * in launch order (reset, moment, ck, edge, update[, shock]).  Tracing aid:
+ * the events are created with the solver. */
 lxw_status lxw_profile_step(lxw_solver* s, double* Q_dev, double cfl, float* ms_host);
 
 /* Per-phase inspection (same kernels as lxw_step).  lxw_step_phases runs only

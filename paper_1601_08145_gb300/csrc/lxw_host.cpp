@@ -255,8 +255,12 @@ struct lxw_solver {
   double graph_cfl = 0.0;
   double last_dt_in = 0.0, last_cfl = 0.0;
   void* events[8] = {};          // cudaEvent_t of lxw_profile_step
+  cudaGraphExec_t pgraph = nullptr;   // one step with event nodes between the kernels
+  double* pgraph_Q = nullptr;
+  double pgraph_cfl = 0.0;
   ~lxw_solver() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (pgraph) cudaGraphExecDestroy(pgraph);
     for (void* e : events) if (e) cudaEventDestroy((cudaEvent_t)e);
     for (void* p : allocs) cudaFree(p);
     if (host_diag) cudaFreeHost(host_diag);
@@ -714,9 +718,22 @@ lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* out, size_t coun
 
 lxw_status lxw_profile_step(lxw_solver* s, double* Q, double cfl, float* ms) {
   if (!s || !Q || !ms || !(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_profile_step: bad argument");
-  StepArgs a = make_args(s, 0.0, cfl, 0, nullptr, nullptr);
-  if (do_step(s, Q, a, s->stream, s->events))
-    return fail(LXW_ERR_CUDA, "lxw_profile_step: launch failed");
+  // the step is replayed from a graph with an event node around every kernel,
+  // so the intervals are device time without host launch gaps
+  if (!s->pgraph || s->pgraph_Q != Q || s->pgraph_cfl != cfl) {
+    if (s->pgraph) { cudaGraphExecDestroy(s->pgraph); s->pgraph = nullptr; }
+    StepArgs a = make_args(s, 0.0, cfl, 0, nullptr, nullptr);
+    cudaGraph_t g = nullptr;
+    LXW_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = do_step(s, Q, a, s->cap_stream, s->events);
+    cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
+    if (rc || ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail(LXW_ERR_CUDA, "lxw_profile_step: capture failed"); }
+    cudaError_t ie = cudaGraphInstantiate(&s->pgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) { s->pgraph = nullptr; return fail(LXW_ERR_CUDA, "lxw_profile_step: instantiation failed"); }
+    s->pgraph_Q = Q; s->pgraph_cfl = cfl;
+  }
+  LXW_CUDA(cudaGraphLaunch(s->pgraph, s->stream));
   const int n = launches_of(s);
   LXW_CUDA(cudaEventSynchronize((cudaEvent_t)s->events[n]));
   for (int k = 0; k < n; ++k) LXW_CUDA(cudaEventElapsedTime(&ms[k], (cudaEvent_t)s->events[k], (cudaEvent_t)s->events[k + 1]));
