@@ -694,7 +694,7 @@ int step_impl(const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a, 
   const int grid = grid_for(m.N, block);
   DevDiag* dd = reinterpret_cast<DevDiag*>(w.diag);
   int ne = 0;
-  auto mark = [&]() { if (events) cudaEventRecord((cudaEvent_t)events[ne++], st); };
+  auto mark = [&]() { if (events) cudaEventRecordWithFlags((cudaEvent_t)events[ne++], st, cudaEventRecordExternal); };
   mark();
   k_reset<<<1, 1, 0, st>>>(w, a.want_diag);
   mark();

@@ -860,7 +860,7 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
                  void** events, int upto) {
   const int grid = gridn(m.N, block);
   int ne = 0;
-  auto mark = [&]() { if (events) cudaEventRecord((cudaEvent_t)events[ne++], st); };
+  auto mark = [&]() { if (events) cudaEventRecordWithFlags((cudaEvent_t)events[ne++], st, cudaEventRecordExternal); };
   auto ok = [&]() { return cudaGetLastError() == cudaSuccess ? 0 : -1; };
   mark();
   k_reset_mx<<<1, 1, 0, st>>>(w, 1);
