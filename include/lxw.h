@@ -49,8 +49,8 @@ enum { LXW_KIND_QUAD = 0, LXW_KIND_TRI = 1 };
  * projections, LLF point fluxes, volume / edge integrals, shock limiter)
  * with FP64 cell averages, FP64 blended update and FP64 limiter solves where
  * an FP32 screen with an error margin cannot prove theta = 1; the state is
- * the packed layout of lxw_state_pack (averages double [4][N], then higher
- * modes float [4][ML-1][N]). */
+ * the packed layout of lxw_state_pack (averages double [4][N], their FP32
+ * copy float [4][N], then higher modes float [4][ML-1][N]). */
 enum { LXW_PREC_FP64 = 0, LXW_PREC_MIXED = 1 };
 
 /* device status bits (returned in lxw_diag.status) */
@@ -122,7 +122,7 @@ lxw_status lxw_solver_set_stream(lxw_solver* s, void* stream);
  * (interior + edge quadrature points), nproj projection points. */
 lxw_status lxw_solver_info(const lxw_solver* s, int* N, int* E, int* ML, int* npts, int* nproj);
 
-/* Bytes of the solver's state buffer (N*4*ML*8 for FP64; N*4*8 + N*4*(ML-1)*4
+/* Bytes of the solver's state buffer (N*4*ML*8 for FP64; N*4*8 + N*4*ML*4
  * for the mixed form).  lxw_state_pack converts Q64_dev[N][4][ML] doubles into
  * the solver's state layout (a copy for FP64 solvers); lxw_state_unpack
  * converts back.  Both asynchronous on the solver's stream; buffers must not

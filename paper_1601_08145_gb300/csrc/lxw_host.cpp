@@ -448,11 +448,34 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
     // the FP32 traces / f^LxW fit in the FP64 buffers
     s->dwm.trace = reinterpret_cast<float*>(s->dw.trace);
     s->dwm.fw = reinterpret_cast<float*>(s->dw.flux);
-    s->dwm.prop = s->dw.prop;
+    s->dwm.prop = reinterpret_cast<float*>(s->dw.prop);
     s->dwm.avg_new = (double*)dalloc(sizeof(double) * 4 * (size_t)N);
+    s->dwm.avgn32 = (float*)dalloc(sizeof(float) * 4 * (size_t)N);
+    s->dwm.scal = (ScalMx*)dalloc(sizeof(ScalMx));
     s->dwm.smax = s->dw.smax; s->dwm.status = s->dw.status; s->dwm.diag = s->dw.diag;
     s->Sdev = (double*)dalloc(lxw_state_bytes(s));
-    if (!s->dwm.avg_new || !s->Sdev) { delete s; return fail(LXW_ERR_NOMEM, "lxw_solver_create: device allocation failed"); }
+    float* j32 = (float*)dalloc(sizeof(float) * 4 * (size_t)N);
+    float* n32 = (float*)dalloc(sizeof(float) * (size_t)E * 2 * N);
+    float* s32 = (float*)dalloc(sizeof(float) * (size_t)N);
+    float* ia32 = (float*)dalloc(sizeof(float) * (size_t)N);
+    double* ia64 = (double*)dalloc(sizeof(double) * (size_t)N);
+    if (!s->dwm.avg_new || !s->dwm.avgn32 || !s->dwm.scal || !s->Sdev || !j32 || !n32 || !s32 || !ia32 || !ia64) {
+      delete s;
+      return fail(LXW_ERR_NOMEM, "lxw_solver_create: device allocation failed");
+    }
+    std::vector<float> hj(jinv.begin(), jinv.end()), hn(nrm.begin(), nrm.end()), hs(sdx.begin(), sdx.end());
+    std::vector<float> hia(N);
+    std::vector<double> hia64(N);
+    for (int e = 0; e < N; ++e) { hia64[e] = 1.0 / area[e]; hia[e] = (float)hia64[e]; }
+    if (cudaMemcpy(j32, hj.data(), sizeof(float) * hj.size(), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(n32, hn.data(), sizeof(float) * hn.size(), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(s32, hs.data(), sizeof(float) * hs.size(), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(ia32, hia.data(), sizeof(float) * N, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(ia64, hia64.data(), sizeof(double) * N, cudaMemcpyHostToDevice)) {
+      delete s;
+      return fail(LXW_ERR_CUDA, "lxw_solver_create: upload failed");
+    }
+    s->dm.jinv32 = j32; s->dm.nrm32 = n32; s->dm.sdx32 = s32; s->dm.inva32 = ia32; s->dm.inva = ia64;
   }
   if (!d_area || !d_jinv || !d_nrm || !d_sdx || !d_nbr || !d_nbk || !s->dw.trace || !s->dw.flux || !s->dw.prop ||
       !s->dw.smax || !s->dw.status || !s->dw.diag || !s->Qdev) {
@@ -484,6 +507,7 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
     return fail(LXW_ERR_CUDA, "lxw_solver_create: upload failed");
   }
   s->dm.N = N; s->dm.E = E; s->dm.area = d_area; s->dm.jinv = d_jinv; s->dm.nrm = d_nrm; s->dm.sdx = d_sdx;
+  // (FP32 geometry copies of the mixed form were set above)
   s->dm.nbr = d_nbr; s->dm.nbk = d_nbk; s->dm.hmin = hmin;
   *out = s;
   return LXW_OK;
@@ -523,6 +547,7 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   StepArgs a{};
   a.dt_in = dt; a.cfl = cfl; a.gamma = s->opt.gamma; a.eps0 = s->opt.eps0; a.alpha0 = s->opt.alpha0;
   a.shock_limiter = s->opt.shock_limiter; a.want_diag = want_diag; a.theta_cell = tc; a.theta_edge = te;
+  a.gamma_f = (float)a.gamma; a.eps0_f = (float)a.eps0; a.alpha0_f = (float)a.alpha0;
   return a;
 }
 
@@ -616,7 +641,7 @@ lxw_status lxw_run_host(lxw_solver* s, double* Qh, int nsteps, double cfl, lxw_d
 
 size_t lxw_state_bytes(const lxw_solver* s) {
   if (!s) return 0;
-  if (s->mixed) return sizeof(double) * 4 * (size_t)s->N + sizeof(float) * 4 * (size_t)(s->ML - 1) * s->N;
+  if (s->mixed) return sizeof(double) * 4 * (size_t)s->N + sizeof(float) * 4 * (size_t)s->ML * s->N;
   return sizeof(double) * 4 * (size_t)s->ML * s->N;
 }
 
@@ -694,6 +719,14 @@ lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* out, size_t coun
         for (size_t c = 0; c < 8; ++c)
           for (size_t i = 0; i < N; ++i) out[(k * 8 + c) * N + i] = c < 4 ? tmp[(k * 4 + c) * N + i] : 0.0;
     }
+    return LXW_OK;
+  }
+  if (s->mixed && which == 2) {
+    if (count < E * N) return fail(LXW_ERR_ARG, "lxw_workspace_copy: buffer too small");
+    std::vector<float> tmp(E * N);
+    LXW_CUDA(cudaMemcpyAsync(tmp.data(), s->dwm.prop, E * N * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    LXW_CUDA(cudaStreamSynchronize(s->stream));
+    for (size_t k = 0; k < E * N; ++k) out[k] = tmp[k];
     return LXW_OK;
   }
   if (which == 0) { src = s->dw.trace; n = E * MQ * 8 * N; }

@@ -45,6 +45,12 @@ struct DevMesh {
   const int* nbr;         // [E][N]: neighbour id, or -1 - bc code on the boundary
   const int* nbk;         // [E][N]: neighbour's local edge
   double hmin;            // min_i 2|T_i| / P_i
+  // FP32 copies for the mixed form (null for FP64 solvers)
+  const float* jinv32;    // [4][N]
+  const float* nrm32;     // [E][2][N]
+  const float* sdx32;     // [N]
+  const float* inva32;    // [N]: 1 / |T_i|
+  const double* inva;     // [N]: 1 / |T_i|
 };
 
 // Device workspace of one solver.
@@ -57,12 +63,20 @@ struct DevWork {
   double* diag;           // [16] reduction slots (see lxw_kernels.cu)
 };
 
+// Per-step scalars of the mixed form, computed once on the device.
+struct ScalMx {
+  double s, dt;           // wave speed (inflated FP32 maximum) and time step
+  float s32, dt32, c1, c2;  // FP32: s, dt, dt/2, dt^2/6
+};
+
 // Workspace of the mixed-precision form (FP32 bulk, FP64 averages).
 struct DevWorkMx {
   float* trace;           // [E][MQ][8][N]: q (4) and n_out . F_T (4), FP32
   float* fw;              // [E][4][N]: outward f^LxW, FP32 sums
-  double* prop;           // [E][N]: Lambda proposals
+  float* prop;            // [E][N]: Lambda proposals, rounded down to FP32
   double* avg_new;        // [4][N]: updated averages before the shock limiter commits them
+  float* avgn32;          // [4][N]: FP32 copy of avg_new
+  ScalMx* scal;
   unsigned long long* smax;
   unsigned int* status;
   double* diag;           // DiagBlock
@@ -78,6 +92,7 @@ struct DiagBlock {
 
 struct StepArgs {
   double dt_in, cfl, gamma, eps0, alpha0;
+  float gamma_f, eps0_f, alpha0_f;   // FP32 copies for the mixed form
   int shock_limiter;
   int want_diag;
   double* theta_cell;     // [2][N] or null
@@ -107,7 +122,8 @@ int launch_copy_speed(const DevWork& w, double* s_dev, void* stream);
 int step_launch_count(int want_diag, int shock_limiter);
 
 // Mixed-precision form (lxw_kernels_mx.cu).  State layout: averages double
-// [4][N] followed by higher modes float [4][ML-1][N].
+// [4][N], an FP32 copy of the averages float [4][N], higher modes float
+// [4][ML-1][N].
 int upload_tables_mx(int kind, int deg, const Tables& t);
 int launch_step_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state,
                    const StepArgs& a, void* stream, int block, void** events = nullptr, int upto = 99);

@@ -12,8 +12,14 @@
 // answer is theta = 1 (no limiting); where it can, the FP64 computation
 // would return exactly 1 and is skipped.
 //
-// State layout: averages double [4][N], then higher modes float [4][ML-1][N]
-// (structure of arrays: a warp's loads of one coefficient are coalesced).
+// State layout: averages double [4][N], their FP32 copy float [4][N] (kept
+// in step with the doubles so the FP32 kernels never convert), then higher
+// modes float [4][ML-1][N] (structure of arrays: a warp's loads of one
+// coefficient are coalesced).  On GB300 every FP64-pipe instruction --
+// DFMA, DADD, DSETP, double<->float conversion, the DDIV sequence -- runs at
+// the FP64 rate, so the FP32 kernels use FP32 geometry copies and per-step
+// scalars computed once (k_scalars) and touch no double at all unless a
+// screen sends a cell to its FP64 path.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -124,21 +130,28 @@ __device__ __forceinline__ unsigned long long obits(double x) {
   return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
 }
 
-__device__ __forceinline__ double step_dt_mx(const DevWorkMx& w, const DevMesh& m, const StepArgs& a) {
-  double s = __longlong_as_double((long long)*w.smax);
-  return a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin / s;
+// one thread: the step's wave speed and time step, in FP64 and FP32
+__global__ void k_scalars(const DevMesh m, const DevWorkMx w, const StepArgs a) {
+  const double s = __longlong_as_double((long long)*w.smax);
+  const double dt = a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin / s;
+  ScalMx sc;
+  sc.s = s; sc.dt = dt;
+  sc.s32 = (float)s; sc.dt32 = (float)dt; sc.c1 = (float)(0.5 * dt); sc.c2 = (float)(dt * dt / 6.0);
+  *w.scal = sc;
 }
 
 // accessors of the packed state
 struct MxState {
   double* avg;   // [4][N]
+  float* a32;    // [4][N]
   float* hi;     // [4][ML-1][N]
 };
 template <int ML>
 __device__ __forceinline__ MxState mx_state(double* state, int N) {
   MxState st;
   st.avg = state;
-  st.hi = reinterpret_cast<float*>(state + 4 * (size_t)N);
+  st.a32 = reinterpret_cast<float*>(state + 4 * (size_t)N);
+  st.hi = st.a32 + 4 * (size_t)N;
   return st;
 }
 template <int ML>
@@ -176,24 +189,22 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
   float smax = 0.0f;
   if (i < N) {
     MxState st = mx_state<ML>(state, N);
-    const float g = (float)a.gamma, g1 = g - 1.0f;
-    double a64[4];
+    const float g = a.gamma_f, g1 = g - 1.0f;
     float a32[4], c[4][ML];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      a64[v] = st.avg[(size_t)v * N + i];
-      a32[v] = (float)a64[v];
+      a32[v] = st.a32[(size_t)v * N + i];
 #pragma unroll
       for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
     }
     // --- FP32 screen
     bool clear = a32[0] > 0.0f;
-    const float eps0 = (float)a.eps0;
+    const float eps0 = a.eps0_f;
     {
       const float ri = 1.0f / a32[0];
-      const float pb = g1 * (a32[3] - 0.5f * (a32[1] * a32[1] + a32[2] * a32[2]) * ri);
-      const float bb = fabsf(a32[3]) + 0.5f * (a32[1] * a32[1] + a32[2] * a32[2]) * ri;
-      clear = clear && pb > kTol * g1 * bb;
+      const float kb = 0.5f * (a32[1] * a32[1] + a32[2] * a32[2]) * ri;
+      const float pb = g1 * (a32[3] - kb);
+      clear = clear && pb > kTol * g1 * (fabsf(a32[3]) + kb);
       const float er = fminf(eps0, 0.5f * a32[0]) * (1.0f + kTol);
       const float ep = fminf(eps0, 0.5f * pb) * (1.0f + kTol);
 #pragma unroll 1
@@ -211,10 +222,12 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
         }
         const float rinv = 1.0f / q[0];
         const float u = q[1] * rinv, vv = q[2] * rinv;
-        const float pp = g1 * (q[3] - 0.5f * (q[1] * u + q[2] * vv));
+        const float k2 = q[1] * u + q[2] * vv;
+        const float pp = g1 * (q[3] - 0.5f * k2);
         const float B = S[3] + fabsf(u) * S[1] + fabsf(vv) * S[2] + 0.5f * (u * u + vv * vv) * S[0];
         clear = clear && q[0] > er + kTol * S[0] && pp > ep + kTol * g1 * B;
-        smax = fmaxf(smax, speedf(g, q[0], q[1], q[2], q[3]));
+        const float pc = pp > 0.0f ? pp : 0.0f;
+        smax = fmaxf(smax, sqrtf(u * u + vv * vv) + sqrtf(g * pc * rinv));
       }
       if (clear) smax = fmaxf(smax, speedf(g, a32[0], a32[1], a32[2], a32[3]));
     }
@@ -222,8 +235,9 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
     if (!clear) {
       // --- FP64 path: the algorithm of Sec. 3.1 on the promoted coefficients
       atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->fb_mom, 1ull);
-      const double gg = a.gamma, gd1 = gg - 1.0;
-      const double rb = a64[0], mb = a64[1], nb = a64[2], eb = a64[3];
+      const double gd1 = a.gamma - 1.0;
+      const double rb = st.avg[i], mb = st.avg[(size_t)N + i], nb = st.avg[2 * (size_t)N + i],
+                   eb = st.avg[3 * (size_t)N + i];
       const double pb = rb > 0.0 ? gd1 * (eb - 0.5 * (mb * mb + nb * nb) / rb) : -1.0;
       if (!(rb > 0.0) || !(pb > 0.0)) {
         atomicOr(w.status, (unsigned)LXW_ST_NONPOSITIVE);
@@ -259,21 +273,19 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
       }
       // speeds of the limited state (FP32)
       smax = 0.0f;
-      if (th > 0.0 || a32[0] > 0.0f) {
-        const float thf = (float)th;
-        if (a32[0] > 0.0f) smax = speedf(g, a32[0], a32[1], a32[2], a32[3]);
+      const float thf = (float)th;
+      if (a32[0] > 0.0f) smax = speedf(g, a32[0], a32[1], a32[2], a32[3]);
 #pragma unroll 1
-        for (int p = 0; p < NPT; ++p) {
-          float q[4];
+      for (int p = 0; p < NPT; ++p) {
+        float q[4];
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            float acc = 0.0f;
+        for (int v = 0; v < 4; ++v) {
+          float acc = 0.0f;
 #pragma unroll
-            for (int l = 1; l < ML; ++l) acc += c[v][l] * t.phi[p][l];
-            q[v] = a32[v] + thf * acc;
-          }
-          if (q[0] > 0.0f) smax = fmaxf(smax, speedf(g, q[0], q[1], q[2], q[3]));
+          for (int l = 1; l < ML; ++l) acc += c[v][l] * t.phi[p][l];
+          q[v] = a32[v] + thf * acc;
         }
+        if (q[0] > 0.0f) smax = fmaxf(smax, speedf(g, q[0], q[1], q[2], q[3]));
       }
       if (th < 1.0) {
 #pragma unroll
@@ -288,7 +300,6 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
   block_max(smax, w.smax);
 }
 
-
 // ---------------------------------------------------------- k_ck_mx
 // Sec. 2.2-2.3 in FP32: contravariant flux projections, q_t, F_t,
 // projection, q_tt, F_tt, F_T; volume integral added to the FP32 higher
@@ -302,18 +313,18 @@ __global__ void __launch_bounds__(128) k_ck_mx(const DevMesh m, const DevWorkMx 
   const int N = m.N;
   if (i >= N) return;
   MxState st = mx_state<ML>(state, N);
-  const float g1 = (float)(a.gamma - 1.0);
-  const double dt64 = step_dt_mx(w, m, a);
-  const float dt = (float)dt64, c1 = 0.5f * dt, c2 = (float)(dt64 * dt64 / 6.0);
+  const float g1 = a.gamma_f - 1.0f;
+  const ScalMx sc = *w.scal;
+  const float dt = sc.dt32, c1 = sc.c1, c2 = sc.c2;
   float c[4][ML];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    c[v][0] = (float)st.avg[(size_t)v * N + i];
+    c[v][0] = st.a32[(size_t)v * N + i];
 #pragma unroll
     for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
   }
-  const float jxx = (float)m.jinv[i], jxy = (float)m.jinv[N + i];
-  const float jyx = (float)m.jinv[2 * N + i], jyy = (float)m.jinv[3 * N + i];
+  const float jxx = m.jinv32[i], jxy = m.jinv32[N + i];
+  const float jyx = m.jinv32[2 * N + i], jyy = m.jinv32[3 * N + i];
   float Hx[4][ML], Hy[4][ML];
 #pragma unroll
   for (int v = 0; v < 4; ++v)
@@ -414,7 +425,7 @@ __global__ void __launch_bounds__(128) k_ck_mx(const DevMesh m, const DevWorkMx 
       }
     } else {
       const int k = (p - NQ) / MQ, pe = (p - NQ) % MQ;
-      const float nx = (float)m.nrm[(2 * k) * N + i], ny = (float)m.nrm[(2 * k + 1) * N + i];
+      const float nx = m.nrm32[(2 * k) * N + i], ny = m.nrm32[(2 * k + 1) * N + i];
       float* tr = w.trace + ((size_t)(k * MQ + pe) * 8) * N + i;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -442,15 +453,16 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
   const int N = m.N;
   if (i >= N) return;
   MxState st = mx_state<ML>(state, N);
-  const double s64 = __longlong_as_double((long long)*w.smax);
-  const double dt64 = step_dt_mx(w, m, a);
-  const float s = (float)s64, g1f = (float)(a.gamma - 1.0);
-  const double area = m.area[i];
-  const float dta = (float)(dt64 / area);
-  double qb64[4];
+  const ScalMx sc = *w.scal;
+  const float s = sc.s32, g1f = a.gamma_f - 1.0f;
+  const float dta = sc.dt32 * m.inva32[i];
   float qb[4];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) { qb64[v] = st.avg[(size_t)v * N + i]; qb[v] = (float)qb64[v]; }
+  for (int v = 0; v < 4; ++v) qb[v] = st.a32[(size_t)v * N + i];
+  // gather the neighbour indices and every trace value first (memory-level parallelism)
+  int nb[E], nk[E];
+#pragma unroll
+  for (int k = 0; k < E; ++k) { nb[k] = m.nbr[k * N + i]; nk[k] = m.nbk[k * N + i]; }
   float Ei[4][ML];
 #pragma unroll
   for (int v = 0; v < 4; ++v)
@@ -462,18 +474,47 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
   fluxf(sb, Fb, Gb);
 #pragma unroll
   for (int k = 0; k < E; ++k) {
-    const int j = m.nbr[k * N + i];
-    const int kj = m.nbk[k * N + i];
-    const float nx = (float)m.nrm[(2 * k) * N + i], ny = (float)m.nrm[(2 * k + 1) * N + i];
+    const int j = nb[k], kj = nk[k];
+    const float nx = m.nrm32[(2 * k) * N + i], ny = m.nrm32[(2 * k + 1) * N + i];
     const float ln = sqrtf(nx * nx + ny * ny);
     const float hs = 0.5f * s * ln;
     const bool owner = j < 0 || i < j || (i == j && k < kj);
+    // slot qo holds edge point number qo in the owner's order (own point p)
+    float qi[MQ][4], Fi[MQ][4], qx[MQ][4], Fx[MQ][4];
+#pragma unroll
+    for (int qo = 0; qo < MQ; ++qo) {
+      const int pp = owner ? qo : MQ - 1 - qo;
+      const float* tr = w.trace + ((size_t)(k * MQ + pp) * 8) * N + i;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { qi[qo][v] = tr[(size_t)v * N]; Fi[qo][v] = tr[(size_t)(4 + v) * N]; }
+    }
     float qn[4];
     if (j >= 0) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) qn[v] = (float)st.avg[(size_t)v * N + j];
+      for (int v = 0; v < 4; ++v) qn[v] = st.a32[(size_t)v * N + j];
+#pragma unroll
+      for (int qo = 0; qo < MQ; ++qo) {
+        const int pp = owner ? qo : MQ - 1 - qo;
+        const float* tj = w.trace + ((size_t)(kj * MQ + (MQ - 1 - pp)) * 8) * N + j;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { qx[qo][v] = tj[(size_t)v * N]; Fx[qo][v] = -tj[(size_t)(4 + v) * N]; }
+      }
     } else {
-      ghostq<float>(-1 - j, nx / ln, ny / ln, qb, qn);
+      const float nxh = nx / ln, nyh = ny / ln;
+      ghostq<float>(-1 - j, nxh, nyh, qb, qn);
+#pragma unroll
+      for (int pp = 0; pp < MQ; ++pp) {
+        if (-1 - j == LXW_BC_REFLECT) {
+          ghostq<float>(LXW_BC_REFLECT, nxh, nyh, qi[pp], qx[pp]);
+          float R[4];
+          ghostq<float>(LXW_BC_REFLECT, nxh, nyh, Fi[pp], R);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) Fx[pp][v] = -R[v];
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) { qx[pp][v] = qi[pp][v]; Fx[pp][v] = Fi[pp][v]; }
+        }
+      }
     }
     {  // FP32 Lax-Friedrichs flux, used only by the screen
       PtF sn = ptf(g1f, qn[0], qn[1], qn[2], qn[3]);
@@ -490,28 +531,9 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
 #pragma unroll
     for (int qo = 0; qo < MQ; ++qo) {
       const int p = owner ? qo : MQ - 1 - qo;
-      const float* tr = w.trace + ((size_t)(k * MQ + p) * 8) * N + i;
-      float qi[4], Fi[4], qx[4], Fx[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) { qi[v] = tr[(size_t)v * N]; Fi[v] = tr[(size_t)(4 + v) * N]; }
-      if (j >= 0) {
-        const float* tj = w.trace + ((size_t)(kj * MQ + (MQ - 1 - p)) * 8) * N + j;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) { qx[v] = tj[(size_t)v * N]; Fx[v] = -tj[(size_t)(4 + v) * N]; }
-      } else if (-1 - j == LXW_BC_REFLECT) {
-        const float nxh = nx / ln, nyh = ny / ln;
-        ghostq<float>(LXW_BC_REFLECT, nxh, nyh, qi, qx);
-        float R[4];
-        ghostq<float>(LXW_BC_REFLECT, nxh, nyh, Fi, R);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) Fx[v] = -R[v];
-      } else {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) { qx[v] = qi[v]; Fx[v] = Fi[v]; }
-      }
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        float fs = __fmaf_rn(-hs, __fsub_rn(qx[v], qi[v]), __fmul_rn(0.5f, __fadd_rn(Fi[v], Fx[v])));
+        float fs = __fmaf_rn(-hs, __fsub_rn(qx[qo][v], qi[qo][v]), __fmul_rn(0.5f, __fadd_rn(Fi[qo][v], Fx[qo][v])));
         fW[k][v] = __fmaf_rn(0.5f * t.ew[qo], fs, fW[k][v]);
         const float hw = 0.5f * t.ew[p] * fs;
 #pragma unroll
@@ -526,7 +548,7 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
 
   // ---- FP32 screen of Steps 4-5 (Lambda = 1 for all edges, mu = 1 for all corners)
   const float tol = kTol;
-  const float Tdt = (float)(area / dt64);
+  const float Tdt = 1.0f / dta;
   float gam = Tdt * qb[0], negabs = 0.0f, errr = Tdt * fabsf(qb[0]);
   float Sv[4], ql[4];
 #pragma unroll
@@ -542,12 +564,12 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
       Sv[v] += dta * (fabsf(fF[k][v]) + fabsf(fW[k][v]));
     }
   }
-  bool clear = gam - Tdt * (float)a.eps0 - negabs > 2.0f * tol * errr && ql[0] > tol * Sv[0];
+  bool clear = gam - Tdt * a.eps0_f - negabs > 4.0f * tol * errr && ql[0] > tol * Sv[0];
   // kappa = min(eps0, p^LxF/2)/(gamma-1) of the FP64 solve, bounded from above
   const float kl = 0.5f * (ql[1] * ql[1] + ql[2] * ql[2]) / ql[0];
   const float pl32 = g1f * (ql[3] - kl);
-  const float kap = fminf((float)a.eps0, 0.5f * pl32 + tol * g1f * (fabsf(ql[3]) + kl)) / g1f;
-  const float herr = tol * (Sv[0] * Sv[3] + Sv[1] * Sv[1] + Sv[2] * Sv[2] + kap * Sv[0]);
+  const float kap = fminf(a.eps0_f, 0.5f * pl32 + tol * g1f * (fabsf(ql[3]) + kl)) / g1f;
+  const float herr = 2.0f * tol * (Sv[0] * Sv[3] + Sv[1] * Sv[1] + Sv[2] * Sv[2] + kap * Sv[0]);
   auto hval = [&](const float q[4]) { return q[0] * q[3] - 0.5f * (q[1] * q[1] + q[2] * q[2]) - kap * q[0]; };
   clear = clear && pl32 > 0.0f && hval(ql) > herr;
 #pragma unroll
@@ -563,18 +585,22 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
     }
     clear = clear && qc[0] > tol * Sv[0] && hval(qc) > herr;
   }
-  double prop[E];
+  float prop[E];
   if (clear) {
 #pragma unroll
-    for (int k = 0; k < E; ++k) prop[k] = 1.0;
+    for (int k = 0; k < E; ++k) prop[k] = 1.0f;
   } else {
     // ---- FP64 path (Sec. 3.3 Steps 4-5 as in the FP64 form)
     atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->fb_edge, 1ull);
-    const double g1 = a.gamma - 1.0;
+    const double g1 = a.gamma - 1.0, s64 = sc.s, dt64 = sc.dt;
+    const double area = m.area[i], dta64 = dt64 * m.inva[i];
+    double qb64[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qb64[v] = st.avg[(size_t)v * N + i];
     double fF64[E][4], fW64[E][4];
 #pragma unroll
     for (int k = 0; k < E; ++k) {
-      const int j = m.nbr[k * N + i];
+      const int j = nb[k];
       const double nx = m.nrm[(2 * k) * N + i], ny = m.nrm[(2 * k + 1) * N + i];
       double qn[4];
       if (j >= 0) {
@@ -588,7 +614,6 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
 #pragma unroll
       for (int v = 0; v < 4; ++v) fW64[k][v] = (double)fW[k][v];
     }
-    const double dta64 = dt64 / area;
     double Gam0 = area / dt64 * qb64[0];
 #pragma unroll
     for (int k = 0; k < E; ++k) Gam0 -= fF64[k][0];
@@ -625,8 +650,8 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
 #pragma unroll
       for (int k = 0; k < E; ++k) mmin[k] = 0.0;
     } else {
-      const double kap = fmin(a.eps0, 0.5 * pl) / g1;
-      const double h0 = ql64[0] * ql64[3] - 0.5 * (ql64[1] * ql64[1] + ql64[2] * ql64[2]) - kap * ql64[0];
+      const double kap64 = fmin(a.eps0, 0.5 * pl) / g1;
+      const double h0 = ql64[0] * ql64[3] - 0.5 * (ql64[1] * ql64[1] + ql64[2] * ql64[2]) - kap64 * ql64[0];
 #pragma unroll 1
       for (int cm = 1; cm < (1 << E); ++cm) {
         double d[4] = {0.0, 0.0, 0.0, 0.0};
@@ -635,7 +660,7 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
           if ((cm >> k) & 1)
 #pragma unroll
             for (int v = 0; v < 4; ++v) d[v] += dq[k][v];
-        const double h1 = ql64[0] * d[3] + d[0] * ql64[3] - (ql64[1] * d[1] + ql64[2] * d[2]) - kap * d[0];
+        const double h1 = ql64[0] * d[3] + d[0] * ql64[3] - (ql64[1] * d[1] + ql64[2] * d[2]) - kap64 * d[0];
         const double h2 = d[0] * d[3] - 0.5 * (d[1] * d[1] + d[2] * d[2]);
         double mu = 1.0;
         if (!(ql64[0] + d[0] > 0.0) || h0 + h1 + h2 < 0.0) {
@@ -648,8 +673,9 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
           if ((cm >> k) & 1) mmin[k] = fmin(mmin[k], mu);
       }
     }
+    // theta rounded down to FP32 keeps the update inside the positive box
 #pragma unroll
-    for (int k = 0; k < E; ++k) prop[k] = lam[k] * mmin[k];
+    for (int k = 0; k < E; ++k) prop[k] = __double2float_rd(lam[k] * mmin[k]);
   }
 #pragma unroll
   for (int k = 0; k < E; ++k) {
@@ -662,7 +688,8 @@ __global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkM
 // ---------------------------------------------------------- k_update_mx
 // Sec. 3.3 Step 6 in FP64: theta_e = min of both proposals; the LxF flux is
 // evaluated (FP64, from the old averages) only on edges with theta_e < 1.
-// New averages go to avg_new; the old ones stay readable for the neighbours.
+// New averages go to avg_new (and an FP32 copy); the old ones stay readable
+// for the neighbours.
 template <int E, int ML>
 __global__ void __launch_bounds__(128) k_update_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                    const StepArgs a) {
@@ -670,50 +697,70 @@ __global__ void __launch_bounds__(128) k_update_mx(const DevMesh m, const DevWor
   const int N = m.N;
   if (i >= N) return;
   MxState st = mx_state<ML>(state, N);
-  const double s64 = __longlong_as_double((long long)*w.smax);
-  const double dt = step_dt_mx(w, m, a);
-  const double g1 = a.gamma - 1.0;
-  double qb[4];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) qb[v] = st.avg[(size_t)v * N + i];
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float th[E];
+  bool all_one = true;
 #pragma unroll
   for (int k = 0; k < E; ++k) {
     const int j = m.nbr[k * N + i];
-    double th = w.prop[k * N + i];
-    if (j >= 0) th = fmin(th, w.prop[m.nbk[k * N + i] * N + j]);
-    if (a.theta_edge) a.theta_edge[(size_t)i * E + k] = th;
-    double fw[4];
+    float t = w.prop[k * N + i];
+    if (j >= 0) t = fminf(t, w.prop[m.nbk[k * N + i] * N + j]);
+    th[k] = t;
+    all_one = all_one && t == 1.0f;
+    if (a.theta_edge) a.theta_edge[(size_t)i * E + k] = t;
+  }
+  double qb[4], acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int v = 0; v < 4; ++v) fw[v] = (double)w.fw[(size_t)(k * 4 + v) * N + i];
-    if (th < 1.0) {
-      if (a.want_diag && (j < 0 || i < j || (i == j && k < m.nbk[k * N + i])))
-        atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->nedge, 1ull);
-      const double nx = m.nrm[(2 * k) * N + i], ny = m.nrm[(2 * k + 1) * N + i];
-      double qn[4], ff[4];
-      if (j >= 0) {
+  for (int v = 0; v < 4; ++v) qb[v] = st.avg[(size_t)v * N + i];
+  if (all_one) {
+    // the common case: f^LxW only, summed exactly in FP64
 #pragma unroll
-        for (int v = 0; v < 4; ++v) qn[v] = st.avg[(size_t)v * N + j];
+    for (int k = 0; k < E; ++k)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[v] += (double)w.fw[(size_t)(k * 4 + v) * N + i];
+  } else {
+    const ScalMx sc = *w.scal;
+    const double g1 = a.gamma - 1.0;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int j = m.nbr[k * N + i];
+      double fw[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) fw[v] = (double)w.fw[(size_t)(k * 4 + v) * N + i];
+      if (th[k] < 1.0f) {
+        if (a.want_diag && (j < 0 || i < j || (i == j && k < m.nbk[k * N + i])))
+          atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->nedge, 1ull);
+        const double nx = m.nrm[(2 * k) * N + i], ny = m.nrm[(2 * k + 1) * N + i];
+        double qn[4], ff[4];
+        if (j >= 0) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) qn[v] = st.avg[(size_t)v * N + j];
+        } else {
+          const double ln = sqrt(nx * nx + ny * ny);
+          ghostq<double>(-1 - j, nx / ln, ny / ln, qb, qn);
+        }
+        lxf64(g1, sc.s, nx, ny, qb, qn, ff);
+        const double t = (double)th[k];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] += t * fw[v] + (1.0 - t) * ff[v];
       } else {
-        const double ln = sqrt(nx * nx + ny * ny);
-        ghostq<double>(-1 - j, nx / ln, ny / ln, qb, qn);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] += fw[v];
       }
-      lxf64(g1, s64, nx, ny, qb, qn, ff);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[v] += th * fw[v] + (1.0 - th) * ff[v];
-    } else {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[v] += fw[v];
     }
   }
-  const double dta = dt / m.area[i];
+  const double dta = w.scal->dt * m.inva[i];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) w.avg_new[(size_t)v * N + i] = qb[v] - dta * acc[v];
+  for (int v = 0; v < 4; ++v) {
+    const double an = qb[v] - dta * acc[v];
+    w.avg_new[(size_t)v * N + i] = an;
+    w.avgn32[(size_t)v * N + i] = (float)an;
+  }
 }
 
 // ---------------------------------------------------------- k_shock_mx
-// Sec. 4.1 on the new state in FP32 (neighbour averages from avg_new), then
-// commits the new averages.  With the shock limiter off only the commit runs.
+// Sec. 4.1 on the new state in FP32 (neighbour averages from the FP32 copy
+// of avg_new), then commits the new averages (FP64 and FP32).  With the
+// shock limiter off only the commit runs.
 template <int KD, int E, int ML, int NQ, int MQ>
 __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                   const StepArgs a, double* __restrict__ theta_out, int limit) {
@@ -723,15 +770,15 @@ __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWork
   const int N = m.N;
   if (i >= N) return;
   MxState st = mx_state<ML>(state, N);
-  double an[4];
+  float an32[4];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) an[v] = w.avg_new[(size_t)v * N + i];
+  for (int v = 0; v < 4; ++v) an32[v] = w.avgn32[(size_t)v * N + i];
   if (limit) {
-    const float g1 = (float)(a.gamma - 1.0);
+    const float g1 = a.gamma_f - 1.0f;
     float c[4][ML];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      c[v][0] = (float)an[v];
+      c[v][0] = an32[v];
 #pragma unroll
       for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
     }
@@ -741,8 +788,8 @@ __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWork
     } else {
       PtF sb = ptf(g1, c[0][0], c[1][0], c[2][0], c[3][0]);
       const float wb[4] = {sb.r, sb.u, sb.v, sb.p};
-      const float dx = (float)m.sdx[i];
-      const float al = (float)a.alpha0 * dx * sqrtf(dx);
+      const float dx = m.sdx32[i];
+      const float al = a.alpha0_f * dx * sqrtf(dx);
       float Mx[4], Mn[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) { Mx[v] = wb[v] + al; Mn[v] = wb[v] - al; }
@@ -752,12 +799,11 @@ __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWork
         float qn[4];
         if (j >= 0) {
 #pragma unroll
-          for (int v = 0; v < 4; ++v) qn[v] = (float)w.avg_new[(size_t)v * N + j];
+          for (int v = 0; v < 4; ++v) qn[v] = w.avgn32[(size_t)v * N + j];
         } else {
-          const float nx = (float)m.nrm[(2 * k) * N + i], ny = (float)m.nrm[(2 * k + 1) * N + i];
+          const float nx = m.nrm32[(2 * k) * N + i], ny = m.nrm32[(2 * k + 1) * N + i];
           const float ln = sqrtf(nx * nx + ny * ny);
-          const float qbv[4] = {c[0][0], c[1][0], c[2][0], c[3][0]};
-          ghostq<float>(-1 - j, nx / ln, ny / ln, qbv, qn);
+          ghostq<float>(-1 - j, nx / ln, ny / ln, an32, qn);
         }
         if (!(qn[0] > 0.0f)) continue;
         PtF sn = ptf(g1, qn[0], qn[1], qn[2], qn[3]);
@@ -808,7 +854,10 @@ __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWork
     theta_out[i] = 1.0;
   }
 #pragma unroll
-  for (int v = 0; v < 4; ++v) st.avg[(size_t)v * N + i] = an[v];
+  for (int v = 0; v < 4; ++v) {
+    st.avg[(size_t)v * N + i] = w.avg_new[(size_t)v * N + i];
+    st.a32[(size_t)v * N + i] = an32[v];
+  }
 }
 
 template <int ML>
@@ -823,7 +872,7 @@ __global__ void __launch_bounds__(256) k_diag_mx(const DevMesh m, const DevWorkM
     double p = (gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
     bool finite = true;
     for (int v = 0; v < 4; ++v) finite = finite && isfinite(q[v]);
-    const float* hi = reinterpret_cast<const float*>(state + 4 * (size_t)N);
+    const float* hi = reinterpret_cast<const float*>(state + 4 * (size_t)N) + 4 * (size_t)N;
     for (int c = 0; c < 4 * (ML - 1); ++c) finite = finite && isfinite(hi[(size_t)c * N + i]);
     if (!finite) atomicOr(w.status, (unsigned)LXW_ST_NAN);
     const double ar = m.area[i];
@@ -836,9 +885,12 @@ __global__ void __launch_bounds__(256) k_diag_mx(const DevMesh m, const DevWorkM
 __global__ void k_pack(int ML, int N, const double* __restrict__ Q64, double* __restrict__ state) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  float* hi = reinterpret_cast<float*>(state + 4 * (size_t)N);
+  float* a32 = reinterpret_cast<float*>(state + 4 * (size_t)N);
+  float* hi = a32 + 4 * (size_t)N;
   for (int v = 0; v < 4; ++v) {
-    state[(size_t)v * N + i] = Q64[((size_t)i * 4 + v) * ML];
+    const double av = Q64[((size_t)i * 4 + v) * ML];
+    state[(size_t)v * N + i] = av;
+    a32[(size_t)v * N + i] = (float)av;
     for (int l = 1; l < ML; ++l) hi[((size_t)v * (ML - 1) + l - 1) * N + i] = (float)Q64[((size_t)i * 4 + v) * ML + l];
   }
 }
@@ -846,7 +898,7 @@ __global__ void k_pack(int ML, int N, const double* __restrict__ Q64, double* __
 __global__ void k_unpack(int ML, int N, const double* __restrict__ state, double* __restrict__ Q64) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const float* hi = reinterpret_cast<const float*>(state + 4 * (size_t)N);
+  const float* hi = reinterpret_cast<const float*>(state + 4 * (size_t)N) + 4 * (size_t)N;
   for (int v = 0; v < 4; ++v) {
     Q64[((size_t)i * 4 + v) * ML] = state[(size_t)v * N + i];
     for (int l = 1; l < ML; ++l) Q64[((size_t)i * 4 + v) * ML + l] = (double)hi[((size_t)v * (ML - 1) + l - 1) * N + i];
@@ -866,6 +918,7 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
   k_reset_mx<<<1, 1, 0, st>>>(w, 1);
   mark();
   k_moment_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, a.theta_cell);
+  k_scalars<<<1, 1, 0, st>>>(m, w, a);
   mark();
   if (upto < 2) return ok();
   k_ck_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a);
@@ -889,6 +942,7 @@ int moment_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const St
                    cudaStream_t st, int block) {
   k_reset_mx<<<1, 1, 0, st>>>(w, 1);
   k_moment_mx<KD, E, ML, NQ, MQ><<<gridn(m.N, block), block, 0, st>>>(m, w, state, a, theta);
+  k_scalars<<<1, 1, 0, st>>>(m, w, a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
