@@ -18,6 +18,7 @@ LIB = os.path.join(HERE, "liblxw.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lxw_kernels.cu", "lxw_kernels_mx.cu", "lxw_host.cpp", "lxw_peak.cu"]
+FAST_FP32 = {"lxw_kernels_mx.cu"}
 
 
 def _nvcc():
@@ -44,6 +45,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + common
         if src.endswith(".cu"):
             cmd += ARCH + ["-lineinfo", "--expt-relaxed-constexpr"]
+            if src in FAST_FP32:
+                # FP32-only bulk: approximate reciprocal / square root (MUFU based,
+                # a few ulp) and flush-to-zero; FP64 code is not affected
+                cmd += ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
             if verbose:
                 cmd += ["-Xptxas", "-v"]
         else:

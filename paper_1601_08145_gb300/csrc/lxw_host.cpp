@@ -221,6 +221,24 @@ void projection_reference_points(int kind, int deg, std::vector<double>& xi, std
 
 void lxw::set_last_error(const char* msg) { g_err = msg; }
 
+void lxw::make_deriv_tables(const Tables& t, DerivTables& d) {
+  std::memset(&d, 0, sizeof(d));
+  double D[2][kMaxML][kMaxML] = {};
+  for (int m = 0; m < t.ML; ++m)
+    for (int l = 0; l < t.ML; ++l)
+      for (int k = 0; k < t.NQ; ++k) {
+        D[0][m][l] += t.w[k] * t.dxi[k][m] * t.phi[k][l];
+        D[1][m][l] += t.w[k] * t.deta[k][m] * t.phi[k][l];
+      }
+  for (int c = 0; c < 2; ++c)
+    for (int k = 0; k < t.NQ; ++k)
+      for (int l = 0; l < t.ML; ++l) {
+        double acc = 0.0;
+        for (int m = 0; m < t.ML; ++m) acc += t.phi[k][m] * D[c][m][l];
+        d.W[c][k][l] = t.w[k] * acc;
+      }
+}
+
 void lxw::make_tables(int kind, int deg, Tables& t) {
   ProjTables pt;
   build_tables(kind, deg, t, pt);

@@ -124,6 +124,14 @@ int step_launch_count(int want_diag, int shock_limiter);
 // Mixed-precision form (lxw_kernels_mx.cu).  State layout: averages double
 // [4][N], an FP32 copy of the averages float [4][N], higher modes float
 // [4][ML-1][N].
+// Weighted differentiation tables: W[d][k][l] = w_k sum_m phi_m(x_k) D_d[m][l]
+// with D_d[m][l] = (1/|T0|) Int d(phi_m)/d(xi_d) phi_l (exact by the interior
+// rule), so that the modal coefficients of div F^h are
+// -sum_k (W[0][k][l] F_xi(x_k) + W[1][k][l] F_eta(x_k)).
+struct DerivTables {
+  double W[2][kMaxQ][kMaxML];
+};
+void make_deriv_tables(const Tables& t, DerivTables& d);
 int upload_tables_mx(int kind, int deg, const Tables& t);
 int launch_step_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state,
                    const StepArgs& a, void* stream, int block, void** events = nullptr, int upto = 99);

@@ -38,8 +38,8 @@ struct TablesF {
   float deta[kMaxPts][kMaxML];
 };
 __constant__ TablesF c_tabf[4];
-// exact (FP64) basis values at the limiter points, for the FP64 moment-limiter path
-__constant__ double c_phi64[4][kMaxPts][kMaxML];
+// weighted differentiation tables (DerivTables, FP32)
+__constant__ float c_wd[4][2][kMaxQ][kMaxML];
 
 constexpr float kTol = 1e-5f;            // relative margin of the FP32 screens (FP32 error ~5e-7)
 constexpr float kSpeedInflate = 1.00001f; // s from FP32 point values, inflated to bound the exact one
@@ -170,9 +170,19 @@ __global__ void k_reset_mx(DevWorkMx w, int want_diag) {
   }
 }
 
+// CTA maximum of a non-negative value, one atomic per CTA (every thread of
+// the CTA must call it; blockDim.x a multiple of 32, at most 1024)
 __device__ __forceinline__ void block_max(float v, unsigned long long* dst) {
+  __shared__ float red[32];
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(dst, (unsigned long long)__double_as_longlong((double)v * kSpeedInflate));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomicMax(dst, (unsigned long long)__double_as_longlong((double)v * kSpeedInflate));
+  }
 }
 
 // ---------------------------------------------------------- k_moment_mx
@@ -249,7 +259,7 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
         for (int p = 0; p < NPT; ++p) {
           double d = 0.0;
 #pragma unroll
-          for (int l = 1; l < ML; ++l) d = fma((double)c[0][l], c_phi64[KD][p][l], d);
+          for (int l = 1; l < ML; ++l) d = fma((double)c[0][l], (double)t.phi[p][l], d);
           double rm = rb + d;
           if (rm < er) thr = fmin(thr, (rb - er) / (rb - rm));
         }
@@ -262,7 +272,7 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
           for (int v = 0; v < 4; ++v) {
             double acc = 0.0;
 #pragma unroll
-            for (int l = 1; l < ML; ++l) acc = fma((double)c[v][l], c_phi64[KD][p][l], acc);
+            for (int l = 1; l < ML; ++l) acc = fma((double)c[v][l], (double)t.phi[p][l], acc);
             d[v] = acc;
           }
           double r = rb + thr * d[0], mm = mb + thr * d[1], nn = nb + thr * d[2], ee = eb + thr * d[3];
@@ -301,9 +311,14 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
 }
 
 // ---------------------------------------------------------- k_ck_mx
-// Sec. 2.2-2.3 in FP32: contravariant flux projections, q_t, F_t,
-// projection, q_tt, F_tt, F_T; volume integral added to the FP32 higher
-// modes; traces (q, n_out.F_T) at the edge points.
+// Sec. 2.2-2.3 in FP32.  div F^h is a polynomial of degree deg-1 and so lies
+// in the modal space: q_t = -div F^h and q_tt = -div (F_t)^h are carried as
+// modal coefficients Qt, Qtt, accumulated straight from the contravariant
+// fluxes at the interior points with the weighted differentiation tables
+// (the same values as projecting F and differentiating the expansion, with
+// fewer operations and 24 live coefficients per field instead of 48).
+// Then F_T at every point, the volume integral added to the FP32 higher
+// modes, and traces (q, n_out.F_T) at the edge points.
 template <int KD, int E, int ML, int NQ, int MQ>
 __global__ void __launch_bounds__(128) k_ck_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                const StepArgs a) {
@@ -325,11 +340,12 @@ __global__ void __launch_bounds__(128) k_ck_mx(const DevMesh m, const DevWorkMx 
   }
   const float jxx = m.jinv32[i], jxy = m.jinv32[N + i];
   const float jyx = m.jinv32[2 * N + i], jyy = m.jinv32[3 * N + i];
-  float Hx[4][ML], Hy[4][ML];
+  // pass 1: Qt = modal coefficients of q_t = -div F^h
+  float Qt[4][ML];
 #pragma unroll
   for (int v = 0; v < 4; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) { Hx[v][l] = 0.0f; Hy[v][l] = 0.0f; }
+    for (int l = 0; l < ML; ++l) Qt[v][l] = 0.0f;
 #pragma unroll 1
   for (int k = 0; k < NQ; ++k) {
     float q[4];
@@ -345,42 +361,41 @@ __global__ void __launch_bounds__(128) k_ck_mx(const DevMesh m, const DevWorkMx 
     fluxf(s, F, G);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      float fx = t.w[k] * (jxx * F[v] + jxy * G[v]);
-      float fy = t.w[k] * (jyx * F[v] + jyy * G[v]);
+      const float fx = jxx * F[v] + jxy * G[v], fy = jyx * F[v] + jyy * G[v];
 #pragma unroll
-      for (int l = 0; l < ML; ++l) { Hx[v][l] = fmaf(fx, t.phi[k][l], Hx[v][l]); Hy[v][l] = fmaf(fy, t.phi[k][l], Hy[v][l]); }
+      for (int l = 0; l < ML; ++l) Qt[v][l] = fmaf(-fx, c_wd[KD][0][k][l], fmaf(-fy, c_wd[KD][1][k][l], Qt[v][l]));
     }
   }
-  float Tx[4][ML], Ty[4][ML];
+  // pass 2: Qtt = modal coefficients of q_tt = -div (F'(q) q_t)^h
+  float Qtt[4][ML];
 #pragma unroll
   for (int v = 0; v < 4; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) { Tx[v][l] = 0.0f; Ty[v][l] = 0.0f; }
+    for (int l = 0; l < ML; ++l) Qtt[v][l] = 0.0f;
 #pragma unroll 1
   for (int k = 0; k < NQ; ++k) {
     float q[4], qt[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      float acc = 0.0f, dv = 0.0f;
+      float acc = 0.0f, d1 = 0.0f;
 #pragma unroll
       for (int l = 0; l < ML; ++l) {
         acc = fmaf(c[v][l], t.phi[k][l], acc);
-        dv = fmaf(Hx[v][l], t.dxi[k][l], dv);
-        dv = fmaf(Hy[v][l], t.deta[k][l], dv);
+        d1 = fmaf(Qt[v][l], t.phi[k][l], d1);
       }
-      q[v] = acc; qt[v] = -dv;
+      q[v] = acc; qt[v] = d1;
     }
     PtF s = ptf(g1, q[0], q[1], q[2], q[3]);
     float F1[4], G1[4], du, dvv, dp;
     d1f(g1, s, qt, F1, G1, du, dvv, dp);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      float fx = t.w[k] * (jxx * F1[v] + jxy * G1[v]);
-      float fy = t.w[k] * (jyx * F1[v] + jyy * G1[v]);
+      const float fx = jxx * F1[v] + jxy * G1[v], fy = jyx * F1[v] + jyy * G1[v];
 #pragma unroll
-      for (int l = 0; l < ML; ++l) { Tx[v][l] = fmaf(fx, t.phi[k][l], Tx[v][l]); Ty[v][l] = fmaf(fy, t.phi[k][l], Ty[v][l]); }
+      for (int l = 0; l < ML; ++l) Qtt[v][l] = fmaf(-fx, c_wd[KD][0][k][l], fmaf(-fy, c_wd[KD][1][k][l], Qtt[v][l]));
     }
   }
+  // pass 3: F_T at every point; volume integral (interior), traces (edges)
   float Vv[4][ML];
 #pragma unroll
   for (int v = 0; v < 4; ++v)
@@ -394,13 +409,12 @@ __global__ void __launch_bounds__(128) k_ck_mx(const DevMesh m, const DevWorkMx 
       float acc = 0.0f, e1 = 0.0f, e2 = 0.0f;
 #pragma unroll
       for (int l = 0; l < ML; ++l) {
-        acc = fmaf(c[v][l], t.phi[p][l], acc);
-        e1 = fmaf(Hx[v][l], t.dxi[p][l], e1);
-        e1 = fmaf(Hy[v][l], t.deta[p][l], e1);
-        e2 = fmaf(Tx[v][l], t.dxi[p][l], e2);
-        e2 = fmaf(Ty[v][l], t.deta[p][l], e2);
+        const float ph = t.phi[p][l];
+        acc = fmaf(c[v][l], ph, acc);
+        e1 = fmaf(Qt[v][l], ph, e1);
+        e2 = fmaf(Qtt[v][l], ph, e2);
       }
-      q[v] = acc; qt[v] = -e1; qtt[v] = -e2;
+      q[v] = acc; qt[v] = e1; qtt[v] = e2;
     }
     PtF s = ptf(g1, q[0], q[1], q[2], q[3]);
     float F[4], G[4], F1[4], G1[4], F2[4], G2[4], F3[4], G3[4];
@@ -993,7 +1007,13 @@ int upload_tables_mx(int kind, int deg, const Tables& t) {
       f.deta[p][l] = (float)t.deta[p][l];
     }
   if (cudaMemcpyToSymbol(c_tabf, &f, sizeof(TablesF), kd * sizeof(TablesF)) != cudaSuccess) return -1;
-  if (cudaMemcpyToSymbol(c_phi64, t.phi, sizeof(t.phi), kd * sizeof(t.phi)) != cudaSuccess) return -1;
+  DerivTables d;
+  make_deriv_tables(t, d);
+  float wd[2][kMaxQ][kMaxML];
+  for (int c = 0; c < 2; ++c)
+    for (int k = 0; k < kMaxQ; ++k)
+      for (int l = 0; l < kMaxML; ++l) wd[c][k][l] = (float)d.W[c][k][l];
+  if (cudaMemcpyToSymbol(c_wd, wd, sizeof(wd), kd * sizeof(wd)) != cudaSuccess) return -1;
   return 0;
 }
 
