@@ -246,6 +246,8 @@ def main():
     fp64 = timed_form(False)
     mx = timed_form(True, ClockSampler(local))
     w, sol, dof = mx["w"], mx["sol"], mx["dof"]
+    # one more (untimed) step with diagnostics: how often the FP64 paths ran
+    dmx = L.lxw_step(sol, mx["Q"], 0.0, w["cfl"], diag=True)
 
     # accuracy of the mixed form: relative L1 distance of the density after the same steps
     Qm = L.to_q64(sol, mx["Q"])
@@ -303,6 +305,8 @@ def main():
            "phases_ms": mx["phases"],
            "plain_fp64": plain,
            "speedup_vs_plain_fp64": mx["value"] / fp64["value"],
+           "mixed_fp64_path_cells": {"moment": dmx["n_fp64_moment"], "flux_limiter": dmx["n_fp64_edge"],
+                                     "of": sol.N},
            "l1_rel_density_mixed_vs_fp64": l1_rel}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], _, _ = cpu_baseline(args.workload)

@@ -726,11 +726,25 @@ __global__ void __launch_bounds__(128) k_update_mx(const DevMesh m, const DevWor
 #pragma unroll
   for (int v = 0; v < 4; ++v) qb[v] = st.avg[(size_t)v * N + i];
   if (all_one) {
-    // the common case: f^LxW only, summed exactly in FP64
+    // the common case: f^LxW only.  The E FP32 values are summed without
+    // rounding error (Knuth's TwoSum in FP32 gives sum = hi + lo exactly up
+    // to the last addition of the small parts), so only hi and lo go through
+    // the slow FP64 pipe; the cell's flux sum keeps its FP64 accuracy and
+    // both sides of an edge still add exact negatives.
 #pragma unroll
-    for (int k = 0; k < E; ++k)
+    for (int v = 0; v < 4; ++v) {
+      float hi = w.fw[(size_t)v * N + i], lo = 0.0f;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[v] += (double)w.fw[(size_t)(k * 4 + v) * N + i];
+      for (int k = 1; k < E; ++k) {
+        const float b = w.fw[(size_t)(k * 4 + v) * N + i];
+        const float s1 = __fadd_rn(hi, b);
+        const float bb = __fsub_rn(s1, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bb)), __fsub_rn(b, bb));
+        hi = s1;
+        lo = __fadd_rn(lo, err);
+      }
+      acc[v] = (double)hi + (double)lo;
+    }
   } else {
     const ScalMx sc = *w.scal;
     const double g1 = a.gamma - 1.0;
