@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
 // Then F_T at every point, the volume integral added to the FP32 higher
 // modes, and traces (q, n_out.F_T) at the edge points.
 template <int KD, int E, int ML, int NQ, int MQ>
-__global__ void __launch_bounds__(128) k_ck_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+__global__ void __launch_bounds__(128, ML == 6 ? 4 : 2) k_ck_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                const StepArgs a) {
   constexpr int NPT = NQ + E * MQ;
   const TablesF& t = c_tabf[KD];
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(128) k_ck_mx(const DevMesh m, const DevWorkMx 
 // modes) and Steps 4-5: an FP32 screen shows Lambda = 1 and mu_c = 1 for
 // every corner with an error margin, else the FP64 algorithm runs.
 template <int KD, int E, int ML, int NQ, int MQ>
-__global__ void __launch_bounds__(128) k_edge_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+__global__ void __launch_bounds__(128, ML == 6 ? 4 : 3) k_edge_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                  const StepArgs a) {
   const TablesF& t = c_tabf[KD];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
