@@ -68,8 +68,12 @@ typedef struct {
   double alpha0;
   int shock_limiter;
   int precision;
-  int block_threads;        /* threads per CTA of the element kernels (0 = 128)   */
-  int reserved[9];
+  int block_threads;        /* elements (threads) per CTA of the element kernels;
+                               mixed form: also the tile size of the work list
+                               (0 = 128; at most 128)                          */
+  int ctas_per_sm;          /* mixed form: persistent CTAs per SM looping over the
+                               work list (0 = one CTA per tile)                 */
+  int reserved[8];
 } lxw_options;
 
 /* Per-step diagnostics (filled when a non-NULL pointer is passed). */
@@ -130,6 +134,27 @@ lxw_status lxw_solver_info(const lxw_solver* s, int* N, int* E, int* ML, int* np
 size_t lxw_state_bytes(const lxw_solver* s);
 lxw_status lxw_state_pack(lxw_solver* s, const double* Q64_dev, void* state_dev);
 lxw_status lxw_state_unpack(lxw_solver* s, const void* state_dev, double* Q64_dev);
+
+/* Batch of independent problems (Sec. 1.5: problems share nothing) stepped
+ * together: one solver over the disjoint union of the meshes (same element
+ * kind), each problem with its own wave speed s and time step dt (Eq. LLF,
+ * CFL rule).  Elements are numbered mesh 0 first, then mesh 1, ...; the
+ * state is the concatenation of the problems' states in that order.  The
+ * mixed form's kernels run persistent CTAs over a work list of (problem,
+ * tile) pairs, so one launch per phase covers every problem and one CUDA
+ * graph covers a step.  Several problems need LXW_PREC_MIXED.  Meshes may be
+ * destroyed after the call. */
+lxw_status lxw_batch_create(int nmesh, const lxw_mesh* const* meshes, int degree, const lxw_options* opt,
+                            void* stream, lxw_solver** out);
+/* Per-problem wave speed and time step of the last step (synchronises);
+ * s_host / dt_host hold nprob doubles each (nullable). */
+lxw_status lxw_batch_scalars(lxw_solver* s, int* nprob, double* s_host, double* dt_host);
+/* Autotuner: times `reps` steps of each candidate (elements per CTA in
+ * {32, 64, 128} x persistent CTAs per SM in {0 (one per tile), 1, 2, 3, 4,
+ * 6, 8}) on a scratch copy of state_dev (restored afterwards), keeps the
+ * fastest in the solver and returns it.  Allocates a scratch state. */
+lxw_status lxw_autotune(lxw_solver* s, void* state_dev, double cfl, int reps, int* block_threads,
+                        int* ctas_per_sm, float* best_ms);
 
 /* Physical coordinates of the initial-condition projection points
  * xy_host[N][nproj][2] (Gauss rule with degree+3 points per direction). */

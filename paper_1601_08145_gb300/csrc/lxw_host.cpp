@@ -3,6 +3,7 @@
 // graph replay, and the extern "C" entry points declared in include/lxw.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -263,6 +264,11 @@ struct lxw_solver {
   DevWork dw{};
   DevWorkMx dwm{};               // mixed form workspace
   bool mixed = false;
+  std::vector<int> pstart;       // problem element ranges [nprob + 1]
+  std::vector<double> hmin_p;    // per problem
+  int4* d_tiles = nullptr;       // work list (owned through allocs)
+  int tiles_cap = 0;
+  int sms = 0;
   std::vector<void*> allocs;
   double* Qdev = nullptr;        // FP64 staging buffer of lxw_run_host
   double* Sdev = nullptr;        // packed state of lxw_run_host (mixed form)
@@ -387,7 +393,10 @@ lxw_status lxw_mesh_triangles(int nv, const double* xy, int nt, const int* tv, c
 void lxw_mesh_destroy(lxw_mesh* m) { delete m; }
 int lxw_mesh_num_elements(const lxw_mesh* m) { return m ? m->N : 0; }
 
-lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options* optp, void* stream, lxw_solver** out) {
+static lxw_status build_tiles(lxw_solver* s);
+
+static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& pstart, int degree,
+                              const lxw_options* optp, void* stream, lxw_solver** out) {
   if (!mesh || !out) return fail(LXW_ERR_ARG, "lxw_solver_create: null argument");
   if (degree != 2 && degree != 3) return fail(LXW_ERR_ARG, "lxw_solver_create: degree must be 2 or 3");
   lxw_options opt;
@@ -396,7 +405,9 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
   if (opt.precision != LXW_PREC_FP64 && opt.precision != LXW_PREC_MIXED)
     return fail(LXW_ERR_ARG, "lxw_solver_create: unsupported precision");
   if (opt.block_threads <= 0) opt.block_threads = 128;
-  if (opt.block_threads % 32 || opt.block_threads > 1024) return fail(LXW_ERR_ARG, "lxw_solver_create: block_threads must be a multiple of 32 <= 1024");
+  if (opt.block_threads % 32 || opt.block_threads > 128)
+    return fail(LXW_ERR_ARG, "lxw_solver_create: block_threads must be a multiple of 32, at most 128");
+  if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 32) return fail(LXW_ERR_ARG, "lxw_solver_create: ctas_per_sm must be in [0, 32]");
   lxw_solver* s = new (std::nothrow) lxw_solver;
   if (!s) return fail(LXW_ERR_NOMEM, "lxw_solver_create: out of memory");
   s->kind = mesh->kind; s->deg = degree; s->N = mesh->N; s->E = mesh->E; s->opt = opt;
@@ -409,6 +420,9 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
   std::vector<double> area(N), jinv((size_t)4 * N), nrm((size_t)E * 2 * N), sdx(N);
   std::vector<int> nbr((size_t)E * N), nbk((size_t)E * N);
   double hmin = 1e300;
+  const int nprob = (int)pstart.size() - 1;
+  s->pstart = pstart;
+  s->hmin_p.assign(nprob, 1e300);
   s->xproj.resize((size_t)N * s->ptab.NPJ * 2);
   std::vector<double> pxi, peta;
   projection_reference_points(mesh->kind, degree, pxi, peta);
@@ -436,6 +450,11 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
       nbk[(size_t)k * N + e] = mesh->nbk[(size_t)e * E + k];
     }
     hmin = std::fmin(hmin, 2.0 * area[e] / P);
+    {
+      int pb = 0;
+      while (pb + 1 < nprob && e >= pstart[pb + 1]) ++pb;
+      s->hmin_p[pb] = std::fmin(s->hmin_p[pb], 2.0 * area[e] / P);
+    }
     sdx[e] = mesh->kind == LXW_KIND_QUAD ? 2.0 * J[0] : std::sqrt(2.0 * area[e]);
     for (int p = 0; p < s->ptab.NPJ; ++p) {
       s->xproj[((size_t)e * s->ptab.NPJ + p) * 2] = o[0] + J[0] * pxi[p] + J[1] * peta[p];
@@ -457,7 +476,7 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
   s->dw.trace = (double*)dalloc(sizeof(double) * (size_t)E * MQ * 8 * N);
   s->dw.flux = (double*)dalloc(sizeof(double) * (size_t)E * 8 * N);
   s->dw.prop = (double*)dalloc(sizeof(double) * (size_t)E * N);
-  s->dw.smax = (unsigned long long*)dalloc(sizeof(unsigned long long));
+  s->dw.smax = (unsigned long long*)dalloc(sizeof(unsigned long long) * nprob);
   s->dw.status = (unsigned int*)dalloc(sizeof(unsigned int));
   s->dw.diag = (double*)dalloc(sizeof(DiagBlock) > diag_bytes() ? sizeof(DiagBlock) : diag_bytes());
   s->Qdev = (double*)dalloc(sizeof(double) * (size_t)N * 4 * s->ML);
@@ -469,7 +488,7 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
     s->dwm.prop = reinterpret_cast<float*>(s->dw.prop);
     s->dwm.avg_new = (double*)dalloc(sizeof(double) * 4 * (size_t)N);
     s->dwm.avgn32 = (float*)dalloc(sizeof(float) * 4 * (size_t)N);
-    s->dwm.scal = (ScalMx*)dalloc(sizeof(ScalMx));
+    s->dwm.scal = (ScalMx*)dalloc(sizeof(ScalMx) * nprob);
     s->dwm.smax = s->dw.smax; s->dwm.status = s->dw.status; s->dwm.diag = s->dw.diag;
     s->Sdev = (double*)dalloc(lxw_state_bytes(s));
     float* j32 = (float*)dalloc(sizeof(float) * 4 * (size_t)N);
@@ -526,8 +545,74 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
   }
   s->dm.N = N; s->dm.E = E; s->dm.area = d_area; s->dm.jinv = d_jinv; s->dm.nrm = d_nrm; s->dm.sdx = d_sdx;
   // (FP32 geometry copies of the mixed form were set above)
-  s->dm.nbr = d_nbr; s->dm.nbk = d_nbk; s->dm.hmin = hmin;
+  s->dm.nbr = d_nbr; s->dm.nbk = d_nbk; s->dm.hmin = s->hmin_p[0];
+  s->dm.nprob = nprob;
+  double* d_hp = (double*)dalloc(sizeof(double) * nprob);
+  if (!d_hp || cudaMemcpy(d_hp, s->hmin_p.data(), sizeof(double) * nprob, cudaMemcpyHostToDevice) != cudaSuccess) {
+    delete s;
+    return fail(LXW_ERR_CUDA, "lxw_solver_create: upload failed");
+  }
+  s->dm.hmin_p = d_hp;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+  lxw_status ts = build_tiles(s);
+  if (ts != LXW_OK) { delete s; return ts; }
+  (void)hmin;
   *out = s;
+  return LXW_OK;
+}
+
+lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options* opt, void* stream,
+                             lxw_solver** out) {
+  if (!mesh) return fail(LXW_ERR_ARG, "lxw_solver_create: null mesh");
+  return create_impl(mesh, std::vector<int>{0, mesh->N}, degree, opt, stream, out);
+}
+
+lxw_status lxw_batch_create(int nmesh, const lxw_mesh* const* meshes, int degree, const lxw_options* opt,
+                            void* stream, lxw_solver** out) {
+  if (nmesh < 1 || !meshes || !out) return fail(LXW_ERR_ARG, "lxw_batch_create: bad argument");
+  lxw_options o;
+  if (opt) o = *opt; else lxw_options_default(&o);
+  if (o.precision != LXW_PREC_MIXED && nmesh > 1)
+    return fail(LXW_ERR_ARG, "lxw_batch_create: batches of several problems need the mixed precision form");
+  lxw_mesh u;
+  u.kind = meshes[0] ? meshes[0]->kind : 0; u.E = meshes[0] ? meshes[0]->E : 0; u.N = 0;
+  std::vector<int> pstart(1, 0);
+  for (int p = 0; p < nmesh; ++p) {
+    const lxw_mesh* m = meshes[p];
+    if (!m || m->kind != u.kind) return fail(LXW_ERR_ARG, "lxw_batch_create: meshes must exist and share the element kind");
+    const int off = u.N;
+    u.vx.insert(u.vx.end(), m->vx.begin(), m->vx.end());
+    for (size_t k = 0; k < m->nbr.size(); ++k) {
+      u.nbr.push_back(m->nbr[k] >= 0 ? m->nbr[k] + off : m->nbr[k]);
+      u.nbk.push_back(m->nbk[k]);
+    }
+    u.N += m->N;
+    pstart.push_back(u.N);
+  }
+  return create_impl(&u, pstart, degree, &o, stream, out);
+}
+
+// work list of the mixed kernels: tiles of at most block_threads elements,
+// never spanning two problems
+static lxw_status build_tiles(lxw_solver* s) {
+  const int T = s->opt.block_threads;
+  std::vector<int4> tl;
+  for (size_t p = 0; p + 1 < s->pstart.size(); ++p)
+    for (int a = s->pstart[p]; a < s->pstart[p + 1]; a += T)
+      tl.push_back(make_int4(a, std::min(T, s->pstart[p + 1] - a), (int)p, 0));
+  if ((int)tl.size() > s->tiles_cap) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(int4) * tl.size()) != cudaSuccess) return fail(LXW_ERR_NOMEM, "tile list allocation failed");
+    s->allocs.push_back(p);
+    s->d_tiles = (int4*)p;
+    s->tiles_cap = (int)tl.size();
+  }
+  if (cudaMemcpy(s->d_tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(LXW_ERR_CUDA, "tile list upload failed");
+  s->dm.tiles = s->d_tiles;
+  s->dm.ntiles = (int)tl.size();
   return LXW_OK;
 }
 
@@ -566,6 +651,7 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   a.dt_in = dt; a.cfl = cfl; a.gamma = s->opt.gamma; a.eps0 = s->opt.eps0; a.alpha0 = s->opt.alpha0;
   a.shock_limiter = s->opt.shock_limiter; a.want_diag = want_diag; a.theta_cell = tc; a.theta_edge = te;
   a.gamma_f = (float)a.gamma; a.eps0_f = (float)a.eps0; a.alpha0_f = (float)a.alpha0;
+  a.grid = s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm * s->sms : 0;   // persistent CTAs, or one per tile
   return a;
 }
 
@@ -590,6 +676,13 @@ static lxw_status read_diag(lxw_solver* s, double dt, double cfl, lxw_diag* d) {
   std::memcpy(&st, h + 33, sizeof(unsigned int));
   d->s = sp;
   d->dt = dt > 0.0 ? dt : cfl * s->dm.hmin / sp;
+  if (s->mixed) {
+    // largest wave speed and smallest time step over the problems
+    std::vector<ScalMx> sc(s->dm.nprob);
+    LXW_CUDA(cudaMemcpy(sc.data(), s->dwm.scal, sizeof(ScalMx) * sc.size(), cudaMemcpyDeviceToHost));
+    d->s = 0.0; d->dt = 1e300;
+    for (const ScalMx& c : sc) { d->s = std::max(d->s, c.s); d->dt = std::min(d->dt, c.dt); }
+  }
   d->mass = v[0]; d->momx = v[1]; d->momy = v[2]; d->energy = v[3];
   d->min_rho = v[4]; d->min_p = v[5];
   d->n_mom = v[6]; d->n_edge = v[7]; d->n_sc = v[8];
@@ -706,6 +799,71 @@ lxw_status lxw_shock_limit(lxw_solver* s, double* Q, double* theta) {
 // the mixed form always launches its shock kernel (it also commits the new averages)
 static int launches_of(const lxw_solver* s) { return s->mixed ? 6 : step_launch_count(0, s->opt.shock_limiter); }
 int lxw_step_launches(const lxw_solver* s) { return s ? launches_of(s) : 0; }
+
+lxw_status lxw_batch_scalars(lxw_solver* s, int* nprob, double* s_host, double* dt_host) {
+  if (!s) return fail(LXW_ERR_ARG, "lxw_batch_scalars: null solver");
+  if (nprob) *nprob = s->dm.nprob;
+  if (!s_host && !dt_host) return LXW_OK;
+  if (!s->mixed) return fail(LXW_ERR_ARG, "lxw_batch_scalars: needs the mixed form");
+  LXW_CUDA(cudaStreamSynchronize(s->stream));
+  std::vector<ScalMx> sc(s->dm.nprob);
+  LXW_CUDA(cudaMemcpy(sc.data(), s->dwm.scal, sizeof(ScalMx) * sc.size(), cudaMemcpyDeviceToHost));
+  for (size_t p = 0; p < sc.size(); ++p) {
+    if (s_host) s_host[p] = sc[p].s;
+    if (dt_host) dt_host[p] = sc[p].dt;
+  }
+  return LXW_OK;
+}
+
+static void drop_graphs(lxw_solver* s) {
+  if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+  if (s->pgraph) { cudaGraphExecDestroy(s->pgraph); s->pgraph = nullptr; }
+}
+
+lxw_status lxw_autotune(lxw_solver* s, void* state, double cfl, int reps, int* bt, int* cps, float* best_ms) {
+  if (!s || !state || !(cfl > 0.0) || reps < 1) return fail(LXW_ERR_ARG, "lxw_autotune: bad argument");
+  const size_t bytes = lxw_state_bytes(s);
+  void* save = nullptr;
+  LXW_CUDA(cudaStreamSynchronize(s->stream));
+  LXW_CUDA(cudaMalloc(&save, bytes));
+  LXW_CUDA(cudaMemcpy(save, state, bytes, cudaMemcpyDeviceToDevice));
+  const int blocks[3] = {32, 64, 128};
+  const int ctas[7] = {0, 1, 2, 3, 4, 6, 8};
+  const lxw_options keep = s->opt;
+  float best = 1e30f;
+  int bb = keep.block_threads, bc = keep.ctas_per_sm;
+  lxw_status st = LXW_OK;
+  float ms[8];
+  for (int b : blocks) {
+    for (int c : ctas) {
+      if (!s->mixed && c != 0) continue;
+      s->opt.block_threads = b; s->opt.ctas_per_sm = c;
+      drop_graphs(s);
+      if ((st = build_tiles(s)) != LXW_OK) break;
+      cudaMemcpy(state, save, bytes, cudaMemcpyDeviceToDevice);
+      if ((st = lxw_profile_step(s, (double*)state, cfl, ms)) != LXW_OK) break;   // warm-up + capture
+      float tot = 0.0f;
+      for (int r = 0; r < reps; ++r) {
+        if ((st = lxw_profile_step(s, (double*)state, cfl, ms)) != LXW_OK) break;
+        for (int k = 0; k < launches_of(s); ++k) tot += ms[k];
+      }
+      if (st != LXW_OK) break;
+      if (tot / reps < best) { best = tot / reps; bb = b; bc = c; }
+    }
+    if (st != LXW_OK) break;
+  }
+  s->opt.block_threads = bb; s->opt.ctas_per_sm = bc;
+  drop_graphs(s);
+  lxw_status tst = build_tiles(s);
+  cudaMemcpy(state, save, bytes, cudaMemcpyDeviceToDevice);
+  cudaFree(save);
+  if (st != LXW_OK) return st;
+  if (tst != LXW_OK) return tst;
+  if (bt) *bt = bb;
+  if (cps) *cps = bc;
+  if (best_ms) *best_ms = best;
+  return LXW_OK;
+}
 
 lxw_status lxw_step_phases(lxw_solver* s, double* Q, double dt, double cfl, int nphases) {
   if (!s || !Q || nphases < 1) return fail(LXW_ERR_ARG, "lxw_step_phases: bad argument");

@@ -51,6 +51,12 @@ struct DevMesh {
   const float* sdx32;     // [N]
   const float* inva32;    // [N]: 1 / |T_i|
   const double* inva;     // [N]: 1 / |T_i|
+  // mixed form work list: tiles (start element, count, problem id, 0); each
+  // problem is a contiguous element range, hmin per problem
+  const int4* tiles;
+  int ntiles;
+  int nprob;
+  const double* hmin_p;   // [nprob]
 };
 
 // Device workspace of one solver.
@@ -76,8 +82,8 @@ struct DevWorkMx {
   float* prop;            // [E][N]: Lambda proposals, rounded down to FP32
   double* avg_new;        // [4][N]: updated averages before the shock limiter commits them
   float* avgn32;          // [4][N]: FP32 copy of avg_new
-  ScalMx* scal;
-  unsigned long long* smax;
+  ScalMx* scal;           // [nprob]
+  unsigned long long* smax;  // [nprob]
   unsigned int* status;
   double* diag;           // DiagBlock
 };
@@ -91,6 +97,7 @@ struct DiagBlock {
 };
 
 struct StepArgs {
+  int grid;                          // mixed form: persistent CTAs (0 = one per tile)
   double dt_in, cfl, gamma, eps0, alpha0;
   float gamma_f, eps0_f, alpha0_f;   // FP32 copies for the mixed form
   int shock_limiter;

@@ -130,14 +130,16 @@ __device__ __forceinline__ unsigned long long obits(double x) {
   return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
 }
 
-// one thread: the step's wave speed and time step, in FP64 and FP32
+// per problem (one thread each): the step's wave speed and time step, in FP64 and FP32
 __global__ void k_scalars(const DevMesh m, const DevWorkMx w, const StepArgs a) {
-  const double s = __longlong_as_double((long long)*w.smax);
-  const double dt = a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin / s;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m.nprob) return;
+  const double s = __longlong_as_double((long long)w.smax[p]);
+  const double dt = a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin_p[p] / s;
   ScalMx sc;
   sc.s = s; sc.dt = dt;
   sc.s32 = (float)s; sc.dt32 = (float)dt; sc.c1 = (float)(0.5 * dt); sc.c2 = (float)(dt * dt / 6.0);
-  *w.scal = sc;
+  w.scal[p] = sc;
 }
 
 // accessors of the packed state
@@ -159,8 +161,9 @@ __device__ __forceinline__ float& hi_at(const MxState& st, int N, int v, int l, 
   return st.hi[((size_t)v * (ML - 1) + (l - 1)) * N + i];
 }
 
-__global__ void k_reset_mx(DevWorkMx w, int want_diag) {
-  *w.smax = 0ull;
+__global__ void k_reset_mx(DevWorkMx w, int nprob, int want_diag) {
+  for (int p = threadIdx.x; p < nprob; p += blockDim.x) w.smax[p] = 0ull;
+  if (threadIdx.x != 0) return;
   *w.status = 0u;
   if (want_diag) {
     DiagBlock* d = reinterpret_cast<DiagBlock*>(w.diag);
@@ -183,6 +186,7 @@ __device__ __forceinline__ void block_max(float v, unsigned long long* dst) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (lane == 0) atomicMax(dst, (unsigned long long)__double_as_longlong((double)v * kSpeedInflate));
   }
+  __syncthreads();   // red[] is reused by the next tile
 }
 
 // ---------------------------------------------------------- k_moment_mx
@@ -190,14 +194,13 @@ __device__ __forceinline__ void block_max(float v, unsigned long long* dst) {
 // floors by more than the FP32 error bound -> theta = 1 exactly.  Otherwise
 // the FP64 algorithm (Steps 0-2) runs on the promoted coefficients.
 template <int KD, int E, int ML, int NQ, int MQ>
-__global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
-                                                   const StepArgs a, double* __restrict__ theta_out) {
+__device__ __forceinline__ float moment_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
+                                             const StepArgs& a, double* __restrict__ theta_out, const int i) {
   constexpr int NPT = NQ + E * MQ;
   const TablesF& t = c_tabf[KD];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = m.N;
   float smax = 0.0f;
-  if (i < N) {
+  {
     MxState st = mx_state<ML>(state, N);
     const float g = a.gamma_f, g1 = g - 1.0f;
     float a32[4], c[4][ML];
@@ -307,7 +310,18 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
     }
     if (theta_out) theta_out[i] = th;
   }
-  block_max(smax, w.smax);
+  return smax;
+}
+
+template <int KD, int E, int ML, int NQ, int MQ>
+__global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+                                                   const StepArgs a, double* __restrict__ theta_out) {
+  for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
+    const int4 tile = m.tiles[tl];
+    float sm = 0.0f;
+    if ((int)threadIdx.x < tile.y) sm = moment_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, tile.x + threadIdx.x);
+    block_max(sm, &w.smax[tile.z]);
+  }
 }
 
 // ---------------------------------------------------------- k_ck_mx
@@ -320,16 +334,14 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
 // Then F_T at every point, the volume integral added to the FP32 higher
 // modes, and traces (q, n_out.F_T) at the edge points.
 template <int KD, int E, int ML, int NQ, int MQ>
-__global__ void __launch_bounds__(128, ML == 6 ? 4 : 2) k_ck_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
-                                               const StepArgs a) {
+__device__ __forceinline__ void ck_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
+                                        const StepArgs& a, const int i, const int pid) {
   constexpr int NPT = NQ + E * MQ;
   const TablesF& t = c_tabf[KD];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = m.N;
-  if (i >= N) return;
   MxState st = mx_state<ML>(state, N);
   const float g1 = a.gamma_f - 1.0f;
-  const ScalMx sc = *w.scal;
+  const ScalMx sc = w.scal[pid];
   const float dt = sc.dt32, c1 = sc.c1, c2 = sc.c2;
   float c[4][ML];
 #pragma unroll
@@ -454,20 +466,27 @@ __global__ void __launch_bounds__(128, ML == 6 ? 4 : 2) k_ck_mx(const DevMesh m,
     for (int l = 1; l < ML; ++l) hi_at<ML>(st, N, v, l, i) = c[v][l] + dt * Vv[v][l];
 }
 
+template <int KD, int E, int ML, int NQ, int MQ>
+__global__ void __launch_bounds__(128, ML == 6 ? 4 : 2) k_ck_mx(const DevMesh m, const DevWorkMx w,
+                                                                double* __restrict__ state, const StepArgs a) {
+  for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
+    const int4 tile = m.tiles[tl];
+    if ((int)threadIdx.x < tile.y) ck_elem<KD, E, ML, NQ, MQ>(m, w, state, a, tile.x + threadIdx.x, tile.z);
+  }
+}
+
 // ---------------------------------------------------------- k_edge_mx
 // Sec. 3.3 Step 3 in FP32 (LLF at the edge points in the owner's order, so
 // the two sides produce exact negatives; f^LxW; edge integral of the higher
 // modes) and Steps 4-5: an FP32 screen shows Lambda = 1 and mu_c = 1 for
 // every corner with an error margin, else the FP64 algorithm runs.
 template <int KD, int E, int ML, int NQ, int MQ>
-__global__ void __launch_bounds__(128, ML == 6 ? 4 : 3) k_edge_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
-                                                 const StepArgs a) {
+__device__ __forceinline__ void edge_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
+                                          const StepArgs& a, const int i, const int pid) {
   const TablesF& t = c_tabf[KD];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = m.N;
-  if (i >= N) return;
   MxState st = mx_state<ML>(state, N);
-  const ScalMx sc = *w.scal;
+  const ScalMx sc = w.scal[pid];
   const float s = sc.s32, g1f = a.gamma_f - 1.0f;
   const float dta = sc.dt32 * m.inva32[i];
   float qb[4];
@@ -699,17 +718,24 @@ __global__ void __launch_bounds__(128, ML == 6 ? 4 : 3) k_edge_mx(const DevMesh 
   }
 }
 
+template <int KD, int E, int ML, int NQ, int MQ>
+__global__ void __launch_bounds__(128, ML == 6 ? 4 : 3) k_edge_mx(const DevMesh m, const DevWorkMx w,
+                                                                  double* __restrict__ state, const StepArgs a) {
+  for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
+    const int4 tile = m.tiles[tl];
+    if ((int)threadIdx.x < tile.y) edge_elem<KD, E, ML, NQ, MQ>(m, w, state, a, tile.x + threadIdx.x, tile.z);
+  }
+}
+
 // ---------------------------------------------------------- k_update_mx
 // Sec. 3.3 Step 6 in FP64: theta_e = min of both proposals; the LxF flux is
 // evaluated (FP64, from the old averages) only on edges with theta_e < 1.
 // New averages go to avg_new (and an FP32 copy); the old ones stay readable
 // for the neighbours.
 template <int E, int ML>
-__global__ void __launch_bounds__(128) k_update_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
-                                                   const StepArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void update_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
+                                            const StepArgs& a, const int i, const int pid) {
   const int N = m.N;
-  if (i >= N) return;
   MxState st = mx_state<ML>(state, N);
   float th[E];
   bool all_one = true;
@@ -746,7 +772,7 @@ __global__ void __launch_bounds__(128) k_update_mx(const DevMesh m, const DevWor
       acc[v] = (double)hi + (double)lo;
     }
   } else {
-    const ScalMx sc = *w.scal;
+    const ScalMx sc = w.scal[pid];
     const double g1 = a.gamma - 1.0;
 #pragma unroll
     for (int k = 0; k < E; ++k) {
@@ -776,7 +802,7 @@ __global__ void __launch_bounds__(128) k_update_mx(const DevMesh m, const DevWor
       }
     }
   }
-  const double dta = w.scal->dt * m.inva[i];
+  const double dta = w.scal[pid].dt * m.inva[i];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const double an = qb[v] - dta * acc[v];
@@ -785,18 +811,26 @@ __global__ void __launch_bounds__(128) k_update_mx(const DevMesh m, const DevWor
   }
 }
 
+template <int E, int ML>
+__global__ void __launch_bounds__(128) k_update_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+                                                   const StepArgs a) {
+  for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
+    const int4 tile = m.tiles[tl];
+    if ((int)threadIdx.x < tile.y) update_elem<E, ML>(m, w, state, a, tile.x + threadIdx.x, tile.z);
+  }
+}
+
 // ---------------------------------------------------------- k_shock_mx
 // Sec. 4.1 on the new state in FP32 (neighbour averages from the FP32 copy
 // of avg_new), then commits the new averages (FP64 and FP32).  With the
 // shock limiter off only the commit runs.
 template <int KD, int E, int ML, int NQ, int MQ>
-__global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
-                                                  const StepArgs a, double* __restrict__ theta_out, int limit) {
+__device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
+                                           const StepArgs& a, double* __restrict__ theta_out, const int limit,
+                                           const int i) {
   constexpr int NPT = NQ + E * MQ;
   const TablesF& t = c_tabf[KD];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = m.N;
-  if (i >= N) return;
   MxState st = mx_state<ML>(state, N);
   float an32[4];
 #pragma unroll
@@ -888,6 +922,15 @@ __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWork
   }
 }
 
+template <int KD, int E, int ML, int NQ, int MQ>
+__global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+                                                  const StepArgs a, double* __restrict__ theta_out, int limit) {
+  for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
+    const int4 tile = m.tiles[tl];
+    if ((int)threadIdx.x < tile.y) shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, limit, tile.x + threadIdx.x);
+  }
+}
+
 template <int ML>
 __global__ void __launch_bounds__(256) k_diag_mx(const DevMesh m, const DevWorkMx w, const double* __restrict__ state,
                                                  double gamma) {
@@ -938,15 +981,15 @@ inline int gridn(int N, int block) { return (N + block - 1) / block; }
 template <int KD, int E, int ML, int NQ, int MQ>
 int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const StepArgs& a, cudaStream_t st, int block,
                  void** events, int upto) {
-  const int grid = gridn(m.N, block);
+  const int grid = a.grid > 0 && a.grid < m.ntiles ? a.grid : m.ntiles;
   int ne = 0;
   auto mark = [&]() { if (events) cudaEventRecordWithFlags((cudaEvent_t)events[ne++], st, cudaEventRecordExternal); };
   auto ok = [&]() { return cudaGetLastError() == cudaSuccess ? 0 : -1; };
   mark();
-  k_reset_mx<<<1, 1, 0, st>>>(w, 1);
+  k_reset_mx<<<1, 256, 0, st>>>(w, m.nprob, 1);
   mark();
   k_moment_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, a.theta_cell);
-  k_scalars<<<1, 1, 0, st>>>(m, w, a);
+  k_scalars<<<gridn(m.nprob, 128), 128, 0, st>>>(m, w, a);
   mark();
   if (upto < 2) return ok();
   k_ck_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a);
@@ -968,9 +1011,10 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
 template <int KD, int E, int ML, int NQ, int MQ>
 int moment_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const StepArgs& a, double* theta,
                    cudaStream_t st, int block) {
-  k_reset_mx<<<1, 1, 0, st>>>(w, 1);
-  k_moment_mx<KD, E, ML, NQ, MQ><<<gridn(m.N, block), block, 0, st>>>(m, w, state, a, theta);
-  k_scalars<<<1, 1, 0, st>>>(m, w, a);
+  const int grid = a.grid > 0 && a.grid < m.ntiles ? a.grid : m.ntiles;
+  k_reset_mx<<<1, 256, 0, st>>>(w, m.nprob, 1);
+  k_moment_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, theta);
+  k_scalars<<<gridn(m.nprob, 128), 128, 0, st>>>(m, w, a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

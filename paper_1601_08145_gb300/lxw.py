@@ -29,13 +29,14 @@ EXPORTS = [
     "lxw_step", "lxw_run", "lxw_run_host", "lxw_moment_limit", "lxw_shock_limit",
     "lxw_step_launches", "lxw_profile_step", "lxw_step_phases", "lxw_workspace_copy",
     "lxw_moment_limit_noalloc", "lxw_fma_peak", "lxw_state_bytes", "lxw_state_pack", "lxw_state_unpack",
+    "lxw_batch_create", "lxw_batch_scalars", "lxw_autotune",
 ]
 
 
 class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("eps0", C.c_double), ("alpha0", C.c_double),
                 ("shock_limiter", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
-                ("reserved", C.c_int * 9)]
+                ("ctas_per_sm", C.c_int), ("reserved", C.c_int * 8)]
 
 
 class Diag(C.Structure):
@@ -93,6 +94,9 @@ def lib():
     L.lxw_step_phases.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int]
     L.lxw_workspace_copy.argtypes = [_vp, C.c_int, _dp, C.c_size_t]
     L.lxw_fma_peak.argtypes = [C.c_int, _dp]
+    L.lxw_batch_create.argtypes = [C.c_int, C.POINTER(_vp), C.c_int, C.POINTER(Options), _vp, C.POINTER(_vp)]
+    L.lxw_batch_scalars.argtypes = [_vp, C.POINTER(C.c_int), _dp, _dp]
+    L.lxw_autotune.argtypes = [_vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]
     L.lxw_state_bytes.argtypes = [_vp]
     L.lxw_state_bytes.restype = C.c_size_t
     L.lxw_state_pack.argtypes = [_vp, _vp, _vp]
@@ -326,3 +330,29 @@ def lxw_fma_peak(fp64=True):
     v = C.c_double()
     _check(lib().lxw_fma_peak(int(bool(fp64)), C.byref(v)))
     return v.value
+
+
+def lxw_batch_create(meshes, degree, options=None, stream=None):
+    """One solver over the disjoint union of independent problems."""
+    arr = (_vp * len(meshes))(*[m.h for m in meshes])
+    h = _vp()
+    _check(lib().lxw_batch_create(len(meshes), arr, degree, C.byref(options) if options is not None else None,
+                                  _stream_handle(stream), C.byref(h)))
+    sol = Solver(h, list(meshes))
+    sol.offsets = np.cumsum([0] + [m.N for m in meshes])
+    return sol
+
+
+def lxw_batch_scalars(solver):
+    n = C.c_int()
+    _check(lib().lxw_batch_scalars(solver.h, C.byref(n), None, None))
+    sv = np.zeros(n.value); dv = np.zeros(n.value)
+    _check(lib().lxw_batch_scalars(solver.h, C.byref(n), sv.ctypes.data_as(_dp), dv.ctypes.data_as(_dp)))
+    return sv, dv
+
+
+def lxw_autotune(solver, state, cfl, reps=5):
+    b = C.c_int(); c = C.c_int(); ms = C.c_float()
+    _check(lib().lxw_autotune(solver.h, _ptr(state, solver.state_shape, "state"), cfl, reps,
+                              C.byref(b), C.byref(c), C.byref(ms)))
+    return {"block_threads": b.value, "ctas_per_sm": c.value, "ms_per_step": ms.value}

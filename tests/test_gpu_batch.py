@@ -1,0 +1,103 @@
+"""Batched independent problems (one solver over the disjoint union of the
+meshes, persistent CTAs over a (problem, tile) work list, one graph per
+step) against the same problems stepped one solver each.
+
+Each problem's wave speed and time step are reductions over its own
+elements (exact maxima), and every per-element computation is independent
+of how elements are grouped into CTAs, so the batch must reproduce the
+individual runs bit for bit, for every work-list configuration.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_1601_08145_gb300 import build
+    build.build()
+    from paper_1601_08145_gb300 import lxw
+    return lxw
+
+
+def quadrant_problem(L, n, seed):
+    mesh = L.lxw_mesh_cartesian(n, n, (0.0, 1.0, 0.0, 1.0), (2, 2, 2, 2))
+    return mesh, synth.ic_quadrants(seed)
+
+
+def projected(L, sol, ic):
+    xy = L.lxw_projection_points(sol)
+    r, u, v, p = ic(xy[..., 0], xy[..., 1])
+    prim = torch.from_numpy(np.stack(np.broadcast_arrays(r, u, v, p), axis=-1).copy()).cuda()
+    Q = torch.zeros(sol.q64_shape, dtype=torch.float64, device="cuda")
+    L.lxw_project(sol, prim, Q)
+    return Q
+
+
+@pytest.mark.parametrize("ctas,block", [(0, 128), (2, 128), (1, 64), (3, 32)])
+def test_batch_equals_individual_runs(L, ctas, block):
+    sizes = [7, 13, 24, 5, 31]
+    opt = L.lxw_options_default(precision=L.PREC_MIXED, ctas_per_sm=ctas, block_threads=block)
+    probs = [quadrant_problem(L, n, 100 + k) for k, n in enumerate(sizes)]
+    # individual solvers
+    singles = []
+    for mesh, ic in probs:
+        s = L.lxw_solver_create(mesh, 2, L.lxw_options_default(precision=L.PREC_MIXED),
+                                stream=torch.cuda.current_stream())
+        st = L.new_state(s, projected(L, s, ic))
+        for _ in range(12):
+            L.lxw_step(s, st, 0.0, 0.3)
+        singles.append(L.to_q64(s, st))
+    # the batch
+    b = L.lxw_batch_create([m for m, _ in probs], 2, opt, stream=torch.cuda.current_stream())
+    Q = torch.cat([projected(L, L.lxw_solver_create(m, 2, stream=torch.cuda.current_stream()), ic)
+                   for m, ic in probs])
+    st = L.new_state(b, Q)
+    L.lxw_run(b, st, 11, 0.3)
+    d = L.lxw_step(b, st, 0.0, 0.3, diag=True)
+    assert d["status"] == 0
+    Qb = L.to_q64(b, st)
+    torch.cuda.synchronize()
+    off = b.offsets
+    for k in range(len(sizes)):
+        assert torch.equal(Qb[off[k]:off[k + 1]], singles[k]), k
+    sv, dv = L.lxw_batch_scalars(b)
+    assert len(sv) == len(sizes) and np.all(sv > 0) and len(set(np.round(dv, 15))) > 1
+
+
+def test_autotune_keeps_results_and_restores_state(L):
+    probs = [quadrant_problem(L, n, 7 + n) for n in (40, 17, 64, 9)]
+    b = L.lxw_batch_create([m for m, _ in probs], 2, L.lxw_options_default(precision=L.PREC_MIXED),
+                           stream=torch.cuda.current_stream())
+    Q = torch.cat([projected(L, L.lxw_solver_create(m, 2, stream=torch.cuda.current_stream()), ic)
+                   for m, ic in probs])
+    A = L.new_state(b, Q)
+    B = A.clone()
+    L.lxw_run(b, A, 5, 0.3)
+    res = L.lxw_autotune(b, B, 0.3, reps=2)
+    torch.cuda.synchronize()
+    assert torch.equal(B, L.new_state(b, Q))              # restored
+    assert res["block_threads"] in (32, 64, 128) and res["ctas_per_sm"] in (0, 1, 2, 3, 4, 6, 8)
+    L.lxw_run(b, B, 5, 0.3)
+    torch.cuda.synchronize()
+    assert torch.equal(A, B)                              # the tuned configuration computes the same state
+
+
+def test_ensemble_positivity(L):
+    """A 24-problem ensemble of quadrant Riemann data stays positive."""
+    sizes = synth.ensemble_sizes(24, 8, 40, seed=4242)
+    probs = [quadrant_problem(L, int(n), 1000 + k) for k, n in enumerate(sizes)]
+    b = L.lxw_batch_create([m for m, _ in probs], 2, L.lxw_options_default(precision=L.PREC_MIXED, ctas_per_sm=2),
+                           stream=torch.cuda.current_stream())
+    Q = torch.cat([projected(L, L.lxw_solver_create(m, 2, stream=torch.cuda.current_stream()), ic)
+                   for m, ic in probs])
+    st = L.new_state(b, Q)
+    for _ in range(40):
+        d = L.lxw_step(b, st, 0.0, 0.3, diag=True)
+        assert d["status"] == 0 and d["min_rho"] > 0 and d["min_p"] > 0
