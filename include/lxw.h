@@ -89,6 +89,7 @@ typedef struct {
   int reserved;
   double n_fp64_moment;     /* mixed form: cells whose moment limiter ran in FP64   */
   double n_fp64_edge;       /* mixed form: cells whose flux-limiter solve ran in FP64 */
+  double n_mlp_skip;        /* mixed form: cells the learned gate let skip the shock limiter */
 } lxw_diag;
 
 const char* lxw_last_error(void);
@@ -229,6 +230,45 @@ lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* host_out, size_t
  * element kernels do their arithmetic on these pipes; this is their roofline
  * denominator. */
 lxw_status lxw_fma_peak(int fp64, double* tflops);
+
+/* --- learned troubled-cell indicator (mixed form) ------------------------
+ * An MLP 24 -> 64 (ReLU) -> 64 (ReLU) -> 1 (sigmoid) predicts the theta of
+ * the shock-capturing limiter (Sec. 4.1) from 24 features of a cell at the
+ * limiter's input (rho and E higher modes over their averages, two momentum
+ * modes over rho*(|u|+c), neighbour averages of rho and E relative to the
+ * cell's, alpha/rho, the internal-energy fraction; clipped to [-8, 8]).
+ * With a gate set, cells whose prediction is at least 1 - tau keep theta = 1
+ * without the limiter's point work; all others run the limiter, which stays
+ * the fallback.  The positivity limiters always run exactly.
+ * Parameters (float, LXW_MLP_PARAMS of them): W1[24][64], b1[64],
+ * W2[64][64], b2[64], w3[64], b3.  Training (FP32 kernels, mean-squared
+ * error, Adam) runs on the GPU; the step kernels use a BF16 copy with FP32
+ * accumulation. */
+enum { LXW_MLP_IN = 24, LXW_MLP_HIDDEN = 64, LXW_MLP_PARAMS = 5825 };
+typedef struct lxw_mlp lxw_mlp;
+/* max_batch: largest batch of the calls below; He-initialised from seed. */
+lxw_status lxw_mlp_create(int max_batch, unsigned long long seed, void* stream, lxw_mlp** out);
+void lxw_mlp_destroy(lxw_mlp* n);
+int lxw_mlp_num_params(void);
+lxw_status lxw_mlp_get_params(lxw_mlp* n, float* params_dev);
+lxw_status lxw_mlp_set_params(lxw_mlp* n, const float* params_dev);
+/* yhat_dev[B] = network(X_dev[B][24]) */
+lxw_status lxw_mlp_forward(lxw_mlp* n, const float* X_dev, int B, float* yhat_dev);
+/* mean-squared error on (X_dev[B][24], y_dev[B]) and its gradient
+ * grad_dev[LXW_MLP_PARAMS] (nullable); loss_host nullable (synchronises). */
+lxw_status lxw_mlp_loss_grad(lxw_mlp* n, const float* X_dev, const float* y_dev, int B, float* loss_host,
+                             float* grad_dev);
+/* epochs of Adam over shuffled mini-batches (seeded) of the count samples. */
+lxw_status lxw_mlp_train(lxw_mlp* n, const float* X_dev, const float* y_dev, int count, int epochs, int batch,
+                         float lr, unsigned long long seed, float* last_loss);
+/* Enables (mlp non-NULL) or disables the learned gate of a mixed solver;
+ * the solver keeps a BF16 copy taken now (later training needs another
+ * call).  tau in [0, 1). */
+lxw_status lxw_solver_set_mlp(lxw_solver* s, lxw_mlp* mlp, float tau);
+/* One mixed step that also writes each cell's features at the shock
+ * limiter's input (feat_dev[N][24]) and the limiter's theta
+ * (theta_sc_dev[N]): training pairs produced by the method itself. */
+lxw_status lxw_step_dump(lxw_solver* s, void* state_dev, double cfl, float* feat_dev, double* theta_sc_dev);
 
 /* Allocation-free form of lxw_moment_limit, for callers that cannot call
  * cudaMalloc: code running while a stream is captured into a CUDA graph,

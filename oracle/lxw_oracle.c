@@ -1217,3 +1217,107 @@ int orc_step(orc_solver* s, double* Q, double dt_in, double cfl, double* diag,
   }
   return status;
 }
+
+/* ------------------------------------------------------------------ */
+/* Learned troubled-cell indicator, FP64 reference of the network and  */
+/* its features (the GPU trains and evaluates them in FP32 / BF16).    */
+/* MLP 24 -> 64 ReLU -> 64 ReLU -> 1 sigmoid; parameters W1[24][64],   */
+/* b1[64], W2[64][64], b2[64], w3[64], b3.                              */
+/* ------------------------------------------------------------------ */
+#define MI 24
+#define MH 64
+double orc_mlp_loss_grad(const double* P, const double* X, const double* y, int B, double* grad, double* yhat) {
+  const double *W1 = P, *b1 = P + MI * MH, *W2 = b1 + MH, *b2 = W2 + MH * MH, *w3 = b2 + MH, *b3 = w3 + MH;
+  double *gW1 = 0, *gb1 = 0, *gW2 = 0, *gb2 = 0, *gw3 = 0, *gb3 = 0;
+  if (grad) {
+    memset(grad, 0, sizeof(double) * (MI * MH + MH + MH * MH + MH + MH + 1));
+    gW1 = grad; gb1 = gW1 + MI * MH; gW2 = gb1 + MH; gb2 = gW2 + MH * MH; gw3 = gb2 + MH; gb3 = gw3 + MH;
+  }
+  double loss = 0.0;
+  for (int r = 0; r < B; ++r) {
+    const double* x = X + (size_t)r * MI;
+    double z1[MH], h1[MH], z2[MH], h2[MH];
+    for (int j = 0; j < MH; ++j) {
+      double a = b1[j];
+      for (int i = 0; i < MI; ++i) a += x[i] * W1[i * MH + j];
+      z1[j] = a; h1[j] = a > 0.0 ? a : 0.0;
+    }
+    for (int j = 0; j < MH; ++j) {
+      double a = b2[j];
+      for (int k = 0; k < MH; ++k) a += h1[k] * W2[k * MH + j];
+      z2[j] = a; h2[j] = a > 0.0 ? a : 0.0;
+    }
+    double z3 = b3[0];
+    for (int j = 0; j < MH; ++j) z3 += h2[j] * w3[j];
+    double s = 1.0 / (1.0 + exp(-z3));
+    if (yhat) yhat[r] = s;
+    if (!y) continue;
+    double d = s - y[r];
+    loss += d * d / B;
+    if (!grad) continue;
+    double dz3 = 2.0 * d * s * (1.0 - s) / B;
+    gb3[0] += dz3;
+    double dz2[MH], dz1[MH];
+    for (int j = 0; j < MH; ++j) {
+      gw3[j] += h2[j] * dz3;
+      dz2[j] = z2[j] > 0.0 ? dz3 * w3[j] : 0.0;
+      gb2[j] += dz2[j];
+    }
+    for (int k = 0; k < MH; ++k) {
+      double a = 0.0;
+      for (int j = 0; j < MH; ++j) {
+        gW2[k * MH + j] += h1[k] * dz2[j];
+        a += W2[k * MH + j] * dz2[j];
+      }
+      dz1[k] = z1[k] > 0.0 ? a : 0.0;
+      gb1[k] += dz1[k];
+    }
+    for (int i = 0; i < MI; ++i)
+      for (int j = 0; j < MH; ++j) gW1[i * MH + j] += x[i] * dz1[j];
+  }
+  return loss;
+}
+
+static double clip8(double v) { return v > 8.0 ? 8.0 : (v < -8.0 ? -8.0 : v); }
+
+/* Features of every cell of Q (the state at the shock limiter's input). */
+void orc_features(const orc_solver* s, const double* Q, double* F) {
+  const orc_mesh* m = s->m;
+  int ML = s->ML, E = s->E;
+  double g = s->gamma;
+  for (int i = 0; i < m->N; ++i) {
+    const double* Qi = Q + (size_t)i * NV * ML;
+    double* f = F + (size_t)i * MI;
+    double r = Qi[0], e = Qi[3 * ML];
+    double u = Qi[ML] / r, v = Qi[2 * ML] / r;
+    double p = (g - 1.0) * (e - 0.5 * r * (u * u + v * v));
+    if (p < 0.0) p = 0.0;
+    double U = sqrt(u * u + v * v) + sqrt(g * p / r);
+    double mi = 1.0 / (r * U > 1e-30 ? r * U : 1e-30);
+    for (int l = 1; l <= 5; ++l) {
+      f[l - 1] = l < ML ? Qi[l] / r : 0.0;
+      f[4 + l] = l < ML ? Qi[3 * ML + l] / e : 0.0;
+    }
+    f[10] = Qi[ML + 1] * mi; f[11] = Qi[2 * ML + 1] * mi; f[12] = Qi[ML + 2] * mi; f[13] = Qi[2 * ML + 2] * mi;
+    for (int k = 0; k < 4; ++k) { f[14 + k] = 0.0; f[18 + k] = 0.0; }
+    double qbar[4] = {Qi[0], Qi[ML], Qi[2 * ML], Qi[3 * ML]};
+    for (int k = 0; k < E; ++k) {
+      int j = m->nbr[i * E + k];
+      double qn[4];
+      if (j >= 0) {
+        const double* Qj = Q + (size_t)j * NV * ML;
+        qn[0] = Qj[0]; qn[1] = Qj[ML]; qn[2] = Qj[2 * ML]; qn[3] = Qj[3 * ML];
+      } else {
+        const double* n = m->nrm + ((size_t)i * E + k) * 2;
+        double ln = sqrt(n[0] * n[0] + n[1] * n[1]);
+        double nh[2] = {n[0] / ln, n[1] / ln};
+        boundary_state(m->bc[i * E + k], nh, qbar, qn);
+      }
+      if (qn[0] > 0.0) { f[14 + k] = qn[0] / r - 1.0; f[18 + k] = qn[3] / e - 1.0; }
+    }
+    double al = s->alpha0 * pow(m->sdx[i], 1.5);
+    f[22] = al / r;
+    f[23] = p / ((g - 1.0) * e);
+    for (int k = 0; k < MI; ++k) f[k] = clip8(f[k]);
+  }
+}

@@ -105,6 +105,13 @@ void orc_shock_limit(const orc_solver* s, double* Q, double* theta);
  * theta_mom[N], theta_sc[N], theta_edge[N][E] may be NULL. Returns status. */
 int orc_step(orc_solver* s, double* Q, double dt_in, double cfl, double* diag,
              double* theta_mom, double* theta_sc, double* theta_edge);
+/* Learned indicator: FP64 MLP 24 -> 64 -> 64 -> 1 (ReLU, ReLU, sigmoid),
+ * parameters W1[24][64], b1[64], W2[64][64], b2[64], w3[64], b3.  Returns
+ * the mean-squared error on (X[B][24], y[B]) (y NULL: no loss) and writes
+ * the gradient (nullable) and predictions (nullable). */
+double orc_mlp_loss_grad(const double* P, const double* X, const double* y, int B, double* grad, double* yhat);
+/* The indicator's 24 features of every cell of Q [N][24]. */
+void orc_features(const orc_solver* s, const double* Q, double* F);
 /* Number of OpenMP threads the oracle uses (1 without OpenMP). */
 int orc_num_threads(void);
 

@@ -75,6 +75,9 @@ def lib():
         L.orc_shock_limit.argtypes = [C.c_void_p, _dp, _dp]
         L.orc_step.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
         L.orc_num_threads.argtypes = []
+        L.orc_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int, _dp, _dp]
+        L.orc_mlp_loss_grad.restype = C.c_double
+        L.orc_features.argtypes = [C.c_void_p, _dp, _dp]
         _lib = L
     return _lib
 
@@ -135,6 +138,19 @@ def flux_limit_cell(gamma, eps0, area, dt, qbar, fW, fF):
     prop = np.zeros(fW.shape[0])
     bad = lib().orc_flux_limit_cell(gamma, eps0, fW.shape[0], area, dt, _d(qbar), _d(fW), _d(fF), _d(prop))
     return prop, bad
+
+
+MLP_PARAMS = 24 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def mlp_loss_grad(P, X, y=None):
+    """FP64 MLP: (loss, grad, yhat) on X[B][24] with targets y[B] (None: predictions only)."""
+    P = np.ascontiguousarray(P, dtype=np.float64); X = np.ascontiguousarray(X, dtype=np.float64)
+    B = X.shape[0]
+    g = np.zeros(MLP_PARAMS); yh = np.zeros(B)
+    yy = None if y is None else np.ascontiguousarray(y, dtype=np.float64)
+    loss = lib().orc_mlp_loss_grad(_d(P), _d(X), _d(yy), B, _d(g) if y is not None else None, _d(yh))
+    return loss, g, yh
 
 
 def num_threads():
@@ -257,6 +273,12 @@ class Solver:
         V = np.zeros((self.ML, 4))
         lib().orc_ck_element(self.ptr, _d(Q), i, dt, *[_d(o) for o in out], _d(V))
         return dict(q=out[0], qt=out[1], qtt=out[2], FT=out[3], GT=out[4], V=V)
+
+    def features(self, Q):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        F = np.zeros((self.N, 24))
+        lib().orc_features(self.ptr, _d(Q), _d(F))
+        return F
 
     def shock_limit(self, Q):
         th = np.zeros(self.N)

@@ -267,6 +267,8 @@ struct lxw_solver {
   std::vector<int> pstart;       // problem element ranges [nprob + 1]
   std::vector<double> hmin_p;    // per problem
   int4* d_tiles = nullptr;       // work list (owned through allocs)
+  unsigned short* mlp_w = nullptr;  // BF16 gate weights (owned) or null
+  float mlp_tau = 0.0f;
   int tiles_cap = 0;
   int sms = 0;
   std::vector<void*> allocs;
@@ -652,6 +654,7 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   a.shock_limiter = s->opt.shock_limiter; a.want_diag = want_diag; a.theta_cell = tc; a.theta_edge = te;
   a.gamma_f = (float)a.gamma; a.eps0_f = (float)a.eps0; a.alpha0_f = (float)a.alpha0;
   a.grid = s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm * s->sms : 0;   // persistent CTAs, or one per tile
+  a.mlp_bf16 = s->mlp_w; a.mlp_tau = s->mlp_tau; a.feat_out = nullptr;
   return a;
 }
 
@@ -690,6 +693,7 @@ static lxw_status read_diag(lxw_solver* s, double dt, double cfl, lxw_diag* d) {
   const DiagBlock* blk = reinterpret_cast<const DiagBlock*>(h);
   d->n_fp64_moment = (double)blk->fb_mom;
   d->n_fp64_edge = (double)blk->fb_edge;
+  d->n_mlp_skip = (double)blk->mlp_skip;
   if (st & LXW_ST_NONPOSITIVE) return fail(LXW_ERR_NONPOSITIVE, "lxw_step: non-positive cell average at step start");
   if (st & LXW_ST_CFL) return fail(LXW_ERR_CFL, "lxw_step: Gamma^rho < 0 (dt above the low-order CFL bound)");
   if (st & LXW_ST_NAN) return fail(LXW_ERR_NAN, "lxw_step: non-finite state");
@@ -812,6 +816,44 @@ lxw_status lxw_batch_scalars(lxw_solver* s, int* nprob, double* s_host, double* 
     if (s_host) s_host[p] = sc[p].s;
     if (dt_host) dt_host[p] = sc[p].dt;
   }
+  return LXW_OK;
+}
+
+lxw_status lxw_solver_set_mlp(lxw_solver* s, lxw_mlp* mlp, float tau) {
+  if (!s) return fail(LXW_ERR_ARG, "lxw_solver_set_mlp: null solver");
+  if (!s->mixed) return fail(LXW_ERR_ARG, "lxw_solver_set_mlp: the learned gate needs the mixed form");
+  if (!(tau >= 0.0f && tau < 1.0f)) return fail(LXW_ERR_ARG, "lxw_solver_set_mlp: tau must be in [0, 1)");
+  if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+  if (s->pgraph) { cudaGraphExecDestroy(s->pgraph); s->pgraph = nullptr; }
+  if (!mlp) { s->mlp_w = nullptr; return LXW_OK; }
+  if (!s->mlp_w) {
+    void* p = nullptr;
+    LXW_CUDA(cudaMalloc(&p, sizeof(unsigned short) * kMlpParams));
+    s->allocs.push_back(p);
+    s->mlp_w = (unsigned short*)p;
+  }
+  const unsigned short* src = mlp_bf16_weights(mlp);
+  LXW_CUDA(cudaMemcpy(s->mlp_w, src, sizeof(unsigned short) * kMlpParams, cudaMemcpyDeviceToDevice));
+  s->mlp_tau = tau;
+  return LXW_OK;
+}
+
+lxw_status lxw_step_dump(lxw_solver* s, void* state, double cfl, float* feat, double* theta_sc) {
+  if (!s || !state || !feat || !(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_step_dump: bad argument");
+  if (!s->mixed) return fail(LXW_ERR_ARG, "lxw_step_dump: needs the mixed form");
+  if (!s->opt.shock_limiter) return fail(LXW_ERR_ARG, "lxw_step_dump: the shock limiter is off");
+  // theta_cell is [2][N] (moment, shock); a scratch pair keeps the shock row
+  void* scratch = nullptr;
+  if (theta_sc) LXW_CUDA(cudaMalloc(&scratch, sizeof(double) * 2 * (size_t)s->N));
+  StepArgs a = make_args(s, 0.0, cfl, 0, (double*)scratch, nullptr);
+  a.mlp_bf16 = nullptr;                    // the plain limiter labels the data
+  a.feat_out = feat;
+  int rc = do_step(s, (double*)state, a, s->stream);
+  if (!rc && theta_sc)
+    cudaMemcpyAsync(theta_sc, (double*)scratch + s->N, sizeof(double) * s->N, cudaMemcpyDeviceToDevice, s->stream);
+  cudaError_t se = cudaStreamSynchronize(s->stream);
+  if (scratch) cudaFree(scratch);
+  if (rc || se != cudaSuccess) return fail(LXW_ERR_CUDA, "lxw_step_dump: launch failed");
   return LXW_OK;
 }
 

@@ -94,12 +94,23 @@ struct DiagBlock {
   unsigned long long minr, minp;      // order-preserving bits of min rho, min p
   unsigned long long nmom, nedge, nsc;
   unsigned long long fb_mom, fb_edge; // mixed form: cells that took the FP64 limiter path
+  unsigned long long mlp_skip;        // cells whose shock-limiter work the learned gate skipped
 };
+
+// Learned troubled-cell indicator: MLP 24 -> 64 (ReLU) -> 64 (ReLU) -> 1
+// (sigmoid).  Parameter vector (float): W1[24][64], b1[64], W2[64][64],
+// b2[64], w3[64], b3.
+constexpr int kMlpIn = 24, kMlpH = 64;
+constexpr int kW1 = 0, kB1 = kW1 + kMlpIn * kMlpH, kW2 = kB1 + kMlpH, kB2 = kW2 + kMlpH * kMlpH,
+              kW3 = kB2 + kMlpH, kB3 = kW3 + kMlpH, kMlpParams = kB3 + 1;
 
 struct StepArgs {
   int grid;                          // mixed form: persistent CTAs (0 = one per tile)
   double dt_in, cfl, gamma, eps0, alpha0;
   float gamma_f, eps0_f, alpha0_f;   // FP32 copies for the mixed form
+  const unsigned short* mlp_bf16;    // learned gate weights (BF16 bits) or null
+  float mlp_tau;                     // gate: skip the limiter where theta_hat >= 1 - tau
+  float* feat_out;                   // [N][24] features at the shock limiter's input, or null
   int shock_limiter;
   int want_diag;
   double* theta_cell;     // [2][N] or null
@@ -107,6 +118,8 @@ struct StepArgs {
 };
 
 // Kernel launchers (lxw_kernels.cu).  All enqueue on `stream`, allocate nothing.
+// BF16 copy of an MLP's parameters (lxw_mlp.cu).
+const unsigned short* mlp_bf16_weights(lxw_mlp* n);
 // Sets the message lxw_last_error() returns on this thread.
 void set_last_error(const char* msg);
 // Builds the quadrature / basis tables of one (kind, degree) on the host.

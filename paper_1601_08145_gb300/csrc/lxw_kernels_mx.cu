@@ -169,7 +169,7 @@ __global__ void k_reset_mx(DevWorkMx w, int nprob, int want_diag) {
     DiagBlock* d = reinterpret_cast<DiagBlock*>(w.diag);
     for (int c = 0; c < 4; ++c) d->sum[c] = 0.0;
     d->minr = d->minp = ~0ull;
-    d->nmom = d->nedge = d->nsc = d->fb_mom = d->fb_edge = 0ull;
+    d->nmom = d->nedge = d->nsc = d->fb_mom = d->fb_edge = d->mlp_skip = 0ull;
   }
 }
 
@@ -820,14 +820,70 @@ __global__ void __launch_bounds__(128) k_update_mx(const DevMesh m, const DevWor
   }
 }
 
+// ---------------------------------------------------------- learned gate
+// Features of a cell at the shock limiter's input (all clipped to [-8, 8]):
+// rho and E higher modes over their averages (first 5 modes), the first two
+// higher modes of the momenta over rho_avg*(|u_avg| + c_avg), neighbour
+// averages of rho and E relative to the cell's (missing neighbours 0),
+// alpha / rho_avg and the internal-energy fraction p_avg / ((gamma-1) E_avg).
+template <int E, int ML>
+__device__ __forceinline__ void cell_features(const float c[4][ML], const float nr[4], const float ne[4], float g,
+                                              float al, float f[kMlpIn]) {
+  const float r = c[0][0], e = c[3][0];
+  const float ri = 1.0f / r, ei = 1.0f / e;
+  const float u = c[1][0] * ri, v = c[2][0] * ri;
+  const float p = fmaxf((g - 1.0f) * (e - 0.5f * r * (u * u + v * v)), 0.0f);
+  const float U = sqrtf(u * u + v * v) + sqrtf(g * p * ri);
+  const float mi = 1.0f / fmaxf(r * U, 1e-30f);
+#pragma unroll
+  for (int l = 1; l <= 5; ++l) {
+    f[l - 1] = (l < ML) ? c[0][l] * ri : 0.0f;
+    f[4 + l] = (l < ML) ? c[3][l] * ei : 0.0f;
+  }
+  f[10] = c[1][1] * mi; f[11] = c[2][1] * mi; f[12] = c[1][2] * mi; f[13] = c[2][2] * mi;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    f[14 + k] = (k < E && nr[k] > 0.0f) ? nr[k] * ri - 1.0f : 0.0f;
+    f[18 + k] = (k < E && nr[k] > 0.0f) ? ne[k] * ei - 1.0f : 0.0f;
+  }
+  f[22] = al * ri;
+  f[23] = p / ((g - 1.0f) * e);
+#pragma unroll
+  for (int k = 0; k < kMlpIn; ++k) f[k] = fminf(8.0f, fmaxf(-8.0f, f[k]));
+}
+
+// theta_hat of the MLP with FP32 weights staged in shared memory
+__device__ __forceinline__ float mlp_theta(const float* __restrict__ W, const float f[kMlpIn]) {
+  float h1[kMlpH];
+#pragma unroll
+  for (int j = 0; j < kMlpH; ++j) h1[j] = W[kB1 + j];
+#pragma unroll
+  for (int i = 0; i < kMlpIn; ++i)
+#pragma unroll
+    for (int j = 0; j < kMlpH; ++j) h1[j] = fmaf(f[i], W[kW1 + i * kMlpH + j], h1[j]);
+#pragma unroll
+  for (int j = 0; j < kMlpH; ++j) h1[j] = fmaxf(h1[j], 0.0f);
+  float out = W[kB3];
+#pragma unroll 4
+  for (int j = 0; j < kMlpH; ++j) {
+    float acc = W[kB2 + j];
+#pragma unroll
+    for (int k = 0; k < kMlpH; ++k) acc = fmaf(h1[k], W[kW2 + k * kMlpH + j], acc);
+    out = fmaf(fmaxf(acc, 0.0f), W[kW3 + j], out);
+  }
+  return 1.0f / (1.0f + __expf(-out));
+}
+
 // ---------------------------------------------------------- k_shock_mx
 // Sec. 4.1 on the new state in FP32 (neighbour averages from the FP32 copy
 // of avg_new), then commits the new averages (FP64 and FP32).  With the
-// shock limiter off only the commit runs.
-template <int KD, int E, int ML, int NQ, int MQ>
+// learned gate on, cells whose theta_hat is at least 1 - tau keep theta = 1
+// without the limiter's point work; every other cell runs the limiter.  With
+// the shock limiter off only the commit runs.
+template <int KD, int E, int ML, int NQ, int MQ, bool GATE>
 __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
                                            const StepArgs& a, double* __restrict__ theta_out, const int limit,
-                                           const int i) {
+                                           const int i, const float* __restrict__ Wsm) {
   constexpr int NPT = NQ + E * MQ;
   const TablesF& t = c_tabf[KD];
   const int N = m.N;
@@ -852,7 +908,7 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
       const float wb[4] = {sb.r, sb.u, sb.v, sb.p};
       const float dx = m.sdx32[i];
       const float al = a.alpha0_f * dx * sqrtf(dx);
-      float Mx[4], Mn[4];
+      float Mx[4], Mn[4], nr[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ne[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int v = 0; v < 4; ++v) { Mx[v] = wb[v] + al; Mn[v] = wb[v] - al; }
 #pragma unroll
@@ -867,41 +923,56 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
           const float ln = sqrtf(nx * nx + ny * ny);
           ghostq<float>(-1 - j, nx / ln, ny / ln, an32, qn);
         }
+        nr[k] = qn[0]; ne[k] = qn[3];
         if (!(qn[0] > 0.0f)) continue;
         PtF sn = ptf(g1, qn[0], qn[1], qn[2], qn[3]);
         const float wn[4] = {sn.r, sn.u, sn.v, sn.p};
 #pragma unroll
         for (int v = 0; v < 4; ++v) { Mx[v] = fmaxf(Mx[v], wn[v]); Mn[v] = fminf(Mn[v], wn[v]); }
       }
-      float hx[4], hn[4];
+      bool skip = false;
+      if (GATE) {
+        float f[kMlpIn];
+        cell_features<E, ML>(c, nr, ne, a.gamma_f, al, f);
+        if (a.feat_out) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) { hx[v] = -3e38f; hn[v] = 3e38f; }
-      bool bad = false;
-#pragma unroll 1
-      for (int p = 0; p < NPT; ++p) {
-        float q[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int l = 0; l < ML; ++l) acc = fmaf(c[v][l], t.phi[p][l], acc);
-          q[v] = acc;
+          for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
         }
-        if (!(q[0] > 0.0f)) { bad = true; break; }
-        PtF sp = ptf(g1, q[0], q[1], q[2], q[3]);
-        const float wp[4] = {sp.r, sp.u, sp.v, sp.p};
-#pragma unroll
-        for (int v = 0; v < 4; ++v) { hx[v] = fmaxf(hx[v], wp[v]); hn[v] = fminf(hn[v], wp[v]); }
+        if (Wsm) skip = mlp_theta(Wsm, f) >= 1.0f - a.mlp_tau;
       }
-      if (bad) {
-        th = 0.0f;
+      if (skip) {
+        if (a.want_diag) atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->mlp_skip, 1ull);
       } else {
+        float hx[4], hn[4];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          if (hx[v] > wb[v]) th = fminf(th, (Mx[v] - wb[v]) / (hx[v] - wb[v]));
-          if (hn[v] < wb[v]) th = fminf(th, (wb[v] - Mn[v]) / (wb[v] - hn[v]));
+        for (int v = 0; v < 4; ++v) { hx[v] = -3e38f; hn[v] = 3e38f; }
+        bool bad = false;
+#pragma unroll 1
+        for (int p = 0; p < NPT; ++p) {
+          float q[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < ML; ++l) acc = fmaf(c[v][l], t.phi[p][l], acc);
+            q[v] = acc;
+          }
+          if (!(q[0] > 0.0f)) { bad = true; break; }
+          PtF sp = ptf(g1, q[0], q[1], q[2], q[3]);
+          const float wp[4] = {sp.r, sp.u, sp.v, sp.p};
+#pragma unroll
+          for (int v = 0; v < 4; ++v) { hx[v] = fmaxf(hx[v], wp[v]); hn[v] = fminf(hn[v], wp[v]); }
         }
-        th = fmaxf(th, 0.0f);
+        if (bad) {
+          th = 0.0f;
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            if (hx[v] > wb[v]) th = fminf(th, (Mx[v] - wb[v]) / (hx[v] - wb[v]));
+            if (hn[v] < wb[v]) th = fminf(th, (wb[v] - Mn[v]) / (wb[v] - hn[v]));
+          }
+          th = fmaxf(th, 0.0f);
+        }
       }
     }
     if (th < 1.0f) {
@@ -922,12 +993,21 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
   }
 }
 
-template <int KD, int E, int ML, int NQ, int MQ>
+template <int KD, int E, int ML, int NQ, int MQ, bool GATE>
 __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                   const StepArgs a, double* __restrict__ theta_out, int limit) {
+  extern __shared__ float mlp_w[];
+  const float* Wsm = nullptr;
+  if (GATE && a.mlp_bf16 && limit) {
+    for (int k = threadIdx.x; k < kMlpParams; k += blockDim.x)
+      mlp_w[k] = __uint_as_float((unsigned)a.mlp_bf16[k] << 16);
+    __syncthreads();
+    Wsm = mlp_w;
+  }
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
-    if ((int)threadIdx.x < tile.y) shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, limit, tile.x + threadIdx.x);
+    if ((int)threadIdx.x < tile.y)
+      shock_elem<KD, E, ML, NQ, MQ, GATE>(m, w, state, a, theta_out, limit, tile.x + threadIdx.x, Wsm);
   }
 }
 
@@ -1001,8 +1081,12 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
   k_update_mx<E, ML><<<grid, block, 0, st>>>(m, w, state, a);
   mark();
   const int limit = a.shock_limiter && upto >= 5;
-  k_shock_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, a.theta_cell ? a.theta_cell + m.N : nullptr,
-                                                        limit);
+  double* tsc = a.theta_cell ? a.theta_cell + m.N : nullptr;
+  if (limit && (a.mlp_bf16 || a.feat_out))
+    k_shock_mx<KD, E, ML, NQ, MQ, true><<<grid, block, a.mlp_bf16 ? sizeof(float) * kMlpParams : 0, st>>>(
+        m, w, state, a, tsc, limit);
+  else
+    k_shock_mx<KD, E, ML, NQ, MQ, false><<<grid, block, 0, st>>>(m, w, state, a, tsc, limit);
   mark();
   if (a.want_diag) k_diag_mx<ML><<<gridn(m.N, 256), 256, 0, st>>>(m, w, state, a.gamma);
   return ok();

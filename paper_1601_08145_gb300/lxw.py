@@ -30,6 +30,8 @@ EXPORTS = [
     "lxw_step_launches", "lxw_profile_step", "lxw_step_phases", "lxw_workspace_copy",
     "lxw_moment_limit_noalloc", "lxw_fma_peak", "lxw_state_bytes", "lxw_state_pack", "lxw_state_unpack",
     "lxw_batch_create", "lxw_batch_scalars", "lxw_autotune",
+    "lxw_mlp_create", "lxw_mlp_destroy", "lxw_mlp_num_params", "lxw_mlp_get_params", "lxw_mlp_set_params",
+    "lxw_mlp_forward", "lxw_mlp_loss_grad", "lxw_mlp_train", "lxw_solver_set_mlp", "lxw_step_dump",
 ]
 
 
@@ -44,7 +46,7 @@ class Diag(C.Structure):
                 ("mass", C.c_double), ("momx", C.c_double), ("momy", C.c_double), ("energy", C.c_double),
                 ("n_mom", C.c_double), ("n_edge", C.c_double), ("n_sc", C.c_double),
                 ("status", C.c_int), ("reserved", C.c_int),
-                ("n_fp64_moment", C.c_double), ("n_fp64_edge", C.c_double)]
+                ("n_fp64_moment", C.c_double), ("n_fp64_edge", C.c_double), ("n_mlp_skip", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -97,6 +99,18 @@ def lib():
     L.lxw_batch_create.argtypes = [C.c_int, C.POINTER(_vp), C.c_int, C.POINTER(Options), _vp, C.POINTER(_vp)]
     L.lxw_batch_scalars.argtypes = [_vp, C.POINTER(C.c_int), _dp, _dp]
     L.lxw_autotune.argtypes = [_vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    L.lxw_mlp_create.argtypes = [C.c_int, C.c_ulonglong, _vp, C.POINTER(_vp)]
+    L.lxw_mlp_destroy.argtypes = [_vp]
+    L.lxw_mlp_destroy.restype = None
+    L.lxw_mlp_num_params.argtypes = []
+    L.lxw_mlp_get_params.argtypes = [_vp, _vp]
+    L.lxw_mlp_set_params.argtypes = [_vp, _vp]
+    L.lxw_mlp_forward.argtypes = [_vp, _vp, C.c_int, _vp]
+    L.lxw_mlp_loss_grad.argtypes = [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_float), _vp]
+    L.lxw_mlp_train.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong,
+                                C.POINTER(C.c_float)]
+    L.lxw_solver_set_mlp.argtypes = [_vp, _vp, C.c_float]
+    L.lxw_step_dump.argtypes = [_vp, _vp, C.c_double, _vp, _vp]
     L.lxw_state_bytes.argtypes = [_vp]
     L.lxw_state_bytes.restype = C.c_size_t
     L.lxw_state_pack.argtypes = [_vp, _vp, _vp]
@@ -356,3 +370,85 @@ def lxw_autotune(solver, state, cfl, reps=5):
     _check(lib().lxw_autotune(solver.h, _ptr(state, solver.state_shape, "state"), cfl, reps,
                               C.byref(b), C.byref(c), C.byref(ms)))
     return {"block_threads": b.value, "ctas_per_sm": c.value, "ms_per_step": ms.value}
+
+
+MLP_IN, MLP_HIDDEN, MLP_PARAMS = 24, 64, 5825
+
+
+def _fptr(t, shape=None, what="tensor"):
+    """data_ptr of a contiguous float32 CUDA tensor."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.element_size() == 4 and t.dtype.is_floating_point and t.is_contiguous()):
+        raise ValueError(f"{what}: need a contiguous float32 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what}: shape {tuple(t.shape)} != {tuple(shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Mlp:
+    def __init__(self, h, max_batch):
+        self.h = h
+        self.max_batch = max_batch
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lxw_mlp_destroy(self.h)
+            self.h = None
+
+
+def lxw_mlp_create(max_batch, seed=1, stream=None):
+    h = _vp()
+    _check(lib().lxw_mlp_create(max_batch, seed, _stream_handle(stream), C.byref(h)))
+    return Mlp(h, max_batch)
+
+
+def lxw_mlp_num_params():
+    return lib().lxw_mlp_num_params()
+
+
+def lxw_mlp_get_params(mlp):
+    import torch
+    P = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    _check(lib().lxw_mlp_get_params(mlp.h, _fptr(P)))
+    return P
+
+
+def lxw_mlp_set_params(mlp, P):
+    _check(lib().lxw_mlp_set_params(mlp.h, _fptr(P, (MLP_PARAMS,), "params")))
+
+
+def lxw_mlp_forward(mlp, X):
+    import torch
+    y = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    _check(lib().lxw_mlp_forward(mlp.h, _fptr(X, (X.shape[0], MLP_IN), "X"), X.shape[0], _fptr(y)))
+    return y
+
+
+def lxw_mlp_loss_grad(mlp, X, y):
+    import torch
+    g = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = C.c_float()
+    _check(lib().lxw_mlp_loss_grad(mlp.h, _fptr(X, (X.shape[0], MLP_IN), "X"), _fptr(y, (X.shape[0],), "y"),
+                                   X.shape[0], C.byref(loss), _fptr(g)))
+    return loss.value, g
+
+
+def lxw_mlp_train(mlp, X, y, epochs, batch, lr, seed=7):
+    loss = C.c_float()
+    _check(lib().lxw_mlp_train(mlp.h, _fptr(X, (X.shape[0], MLP_IN), "X"), _fptr(y, (X.shape[0],), "y"), X.shape[0],
+                               epochs, batch, lr, seed, C.byref(loss)))
+    return loss.value
+
+
+def lxw_solver_set_mlp(solver, mlp, tau=0.05):
+    _check(lib().lxw_solver_set_mlp(solver.h, mlp.h if mlp is not None else None, tau))
+
+
+def lxw_step_dump(solver, state, cfl):
+    """One mixed step; returns (features [N][24] float32, theta_sc [N] float64) of its shock limiter."""
+    import torch
+    F = torch.empty((solver.N, MLP_IN), dtype=torch.float32, device="cuda")
+    th = torch.empty(solver.N, dtype=torch.float64, device="cuda")
+    _check(lib().lxw_step_dump(solver.h, _ptr(state, solver.state_shape, "state"), cfl, _fptr(F), _ptr(th)))
+    return F, th

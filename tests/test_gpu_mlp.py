@@ -1,0 +1,147 @@
+"""The learned troubled-cell indicator: GPU network against the FP64 oracle
+network (forward and gradient), GPU features and limiter labels against the
+oracle's on the same state, training on pairs the method generates, and the
+gated step (positivity kept, close to the ungated result).
+
+Tolerances: the GPU network and its gradient are FP32 (relative ~1e-6 per
+operation over a 24-64-64-1 network -> 1e-4 of the largest gradient entry);
+features are FP32 evaluations of the FP32-rounded state (1e-5 relative)."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_1601_08145_gb300 import build
+    build.build()
+    from paper_1601_08145_gb300 import lxw
+    return lxw
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.lib()
+    return oracle
+
+
+def test_forward_and_gradient_match_oracle(L, O):
+    net = L.lxw_mlp_create(512, seed=11, stream=torch.cuda.current_stream())
+    P = L.lxw_mlp_get_params(net).double().cpu().numpy()
+    rng = np.random.default_rng(1)
+    X = rng.normal(size=(300, 24)); y = rng.uniform(0, 1, 300)
+    loss, g = L.lxw_mlp_loss_grad(net, torch.from_numpy(X).float().cuda(), torch.from_numpy(y).float().cuda())
+    yh = L.lxw_mlp_forward(net, torch.from_numpy(X).float().cuda()).double().cpu().numpy()
+    lo, go, yo = O.mlp_loss_grad(P, X.astype(np.float32).astype(np.float64), y.astype(np.float32).astype(np.float64))
+    assert np.abs(yh - yo).max() < 1e-5
+    assert abs(loss - lo) < 1e-5 * max(lo, 1e-3)
+    g = g.double().cpu().numpy()
+    assert np.abs(g - go).max() < 1e-4 * np.abs(go).max()
+
+
+def mixed_solver(L, kind, n, shock=True, box=(0.0, 1.0, 0.0, 1.0), bc=(2, 2, 2, 2)):
+    if kind == "tri":
+        xy, tv = synth.structured_triangles(n, jitter=0.2, seed=20160129, box=box)
+        mesh = L.lxw_mesh_triangles(xy, tv)
+    else:
+        mesh = L.lxw_mesh_cartesian(n, n, box, bc)
+    o = L.lxw_options_default(precision=L.PREC_MIXED, shock_limiter=int(shock), alpha0=50.0)
+    return L.lxw_solver_create(mesh, 2, o, stream=torch.cuda.current_stream())
+
+
+def start(L, s, ic):
+    xy = L.lxw_projection_points(s)
+    r, u, v, p = ic(xy[..., 0], xy[..., 1])
+    prim = torch.from_numpy(np.stack(np.broadcast_arrays(r, u, v, p), axis=-1).copy()).cuda()
+    Q = torch.zeros(s.q64_shape, dtype=torch.float64, device="cuda")
+    L.lxw_project(s, prim, Q)
+    return L.new_state(s, Q)
+
+
+def test_features_and_labels_match_oracle(L, O):
+    s = mixed_solver(L, "tri", 16)
+    st = start(L, s, synth.ic_rarefy)
+    for _ in range(15):
+        L.lxw_step(s, st, 0.0, 0.1)
+    A = st.clone(); B = st.clone()
+    F, th = L.lxw_step_dump(s, A, 0.1)
+    s0 = mixed_solver(L, "tri", 16, shock=False)       # same step up to the shock limiter's input
+    L.lxw_step(s0, B, 0.0, 0.1)
+    Qpre = L.to_q64(s0, B).cpu().numpy()
+    # the limiter saw FP32 averages: round the oracle's input the same way
+    Qpre[:, :, 0] = Qpre[:, :, 0].astype(np.float32)
+    xy, tv = synth.structured_triangles(16, jitter=0.2, seed=20160129)
+    so = O.Solver(O.Mesh.triangles(xy, tv), 2, alpha0=50.0)
+    Fo = so.features(Qpre)
+    Fg = F.double().cpu().numpy()
+    assert np.abs(Fg - Fo).max() < 1e-5 * (1 + np.abs(Fo).max())
+    tho = so.shock_limit(Qpre.copy())
+    thg = th.cpu().numpy()
+    assert (tho < 1).sum() > 5
+    assert np.abs(thg - tho).max() < 1e-3
+    assert np.mean(np.abs(thg - tho) < 1e-5) > 0.99
+
+
+def generate(L):
+    """(features, theta_sc) pairs from plain mixed runs of the smooth wave,
+    the double rarefaction and the blast."""
+    Xs, ys = [], []
+    runs = [("quad", 32, synth.ic_smooth, (0.0, 1.0, 0.0, 1.0), (0, 0, 0, 0), 30),
+            ("tri", 32, synth.ic_rarefy, (0.0, 1.0, 0.0, 1.0), (2, 2, 2, 2), 60),
+            ("quad", 48, synth.ic_blast(48), (-1.1, 1.1, -1.1, 1.1), (1, 1, 1, 1), 80)]
+    for kind, n, ic, box, bc, steps in runs:
+        s = mixed_solver(L, kind, n, box=box, bc=bc)
+        st = start(L, s, ic)
+        for k in range(steps):
+            if k % 4 == 3:
+                F, th = L.lxw_step_dump(s, st, 0.1)
+                Xs.append(F); ys.append(th.float())
+            else:
+                L.lxw_step(s, st, 0.0, 0.1)
+    return torch.cat(Xs), torch.cat(ys)
+
+
+def test_training_and_gated_step(L):
+    X, y = generate(L)
+    n = X.shape[0]
+    perm = torch.randperm(n, generator=torch.Generator().manual_seed(0)).cuda()
+    X, y = X[perm].contiguous(), y[perm].contiguous()
+    ntr = int(0.8 * n)
+    net = L.lxw_mlp_create(1024, seed=3, stream=torch.cuda.current_stream())
+    l0, _ = L.lxw_mlp_loss_grad(net, X[ntr:ntr + 1024].contiguous(), y[ntr:ntr + 1024].contiguous())
+    L.lxw_mlp_train(net, X[:ntr].contiguous(), y[:ntr].contiguous(), epochs=8, batch=512, lr=2e-3)
+    Xv, yv = X[ntr:].contiguous(), y[ntr:].contiguous()
+    yh = torch.cat([L.lxw_mlp_forward(net, Xv[k:k + 1024].contiguous()) for k in range(0, Xv.shape[0], 1024)])
+    mse = torch.mean((yh - yv) ** 2).item()
+    print(f"pairs {n}, limited {(y < 1).float().mean().item():.3f}, initial mse {l0:.4f}, held-out mse {mse:.5f}")
+    assert mse < 0.5 * l0
+    tau = 0.02
+    skip = yh >= 1 - tau
+    # a skipped cell keeps theta = 1: on held-out data those cells rarely needed strong limiting
+    assert skip.float().mean().item() > 0.3
+    assert (yv[skip] < 0.5).float().mean().item() < 0.02
+    # gated blast run: positivity kept, skipped cells counted, close to the plain run
+    res = {}
+    for gated in (False, True):
+        s = mixed_solver(L, "quad", 48, box=(-1.1, 1.1, -1.1, 1.1), bc=(1, 1, 1, 1))
+        if gated:
+            L.lxw_solver_set_mlp(s, net, tau)
+        st = start(L, s, synth.ic_blast(48))
+        skipped = 0
+        for _ in range(60):
+            d = L.lxw_step(s, st, 0.0, 0.1, diag=True)
+            assert d["status"] == 0 and d["min_rho"] > 0 and d["min_p"] > 0
+            skipped += d["n_mlp_skip"]
+        res[gated] = (L.to_q64(s, st).cpu().numpy(), skipped)
+    assert res[True][1] > 0 and res[False][1] == 0
+    a, b = res[True][0][:, 0, 0], res[False][0][:, 0, 0]
+    rel = np.abs(a - b).sum() / np.abs(b).sum()
+    print(f"gated blast: skipped {res[True][1]:.0f} cell-steps, density L1 distance {rel:.2e}")
+    assert rel < 2e-2
