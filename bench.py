@@ -133,6 +133,38 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def train_indicator(L, stream):
+    """Train the troubled-cell MLP on the GPU from (features, limiter theta)
+    pairs that plain mixed runs of the smooth wave, the double rarefaction
+    and the blast (scaled down) produce; returns the net and a summary."""
+    import torch
+    runs = [("quad", 32, synth.ic_smooth, (0.0, 1.0, 0.0, 1.0), (0, 0, 0, 0), 40),
+            ("tri", 48, synth.ic_rarefy, (0.0, 1.0, 0.0, 1.0), (2, 2, 2, 2), 80),
+            ("quad", 64, synth.ic_blast(64), (-1.1, 1.1, -1.1, 1.1), (1, 1, 1, 1), 120)]
+    Xs, ys = [], []
+    for kind, n, ic, box, bc, steps in runs:
+        if kind == "tri":
+            xy, tv = synth.structured_triangles(n, jitter=0.2, seed=20160129, box=box)
+            mesh = L.lxw_mesh_triangles(xy, tv)
+        else:
+            mesh = L.lxw_mesh_cartesian(n, n, box, bc)
+        sol = L.lxw_solver_create(mesh, 2, L.lxw_options_default(precision=L.PREC_MIXED), stream=stream)
+        st = project(L, sol, dict(ic=ic, n=n))
+        for k in range(steps):
+            if k % 4 == 3:
+                F, th = L.lxw_step_dump(sol, st, 0.1)
+                Xs.append(F); ys.append(th.float())
+            else:
+                L.lxw_step(sol, st, 0.0, 0.1)
+    X = torch.cat(Xs); y = torch.cat(ys)
+    perm = torch.randperm(X.shape[0], generator=torch.Generator().manual_seed(0)).cuda()
+    X, y = X[perm].contiguous(), y[perm].contiguous()
+    net = L.lxw_mlp_create(1024, seed=3, stream=stream)
+    loss = L.lxw_mlp_train(net, X, y, epochs=8, batch=512, lr=2e-3)
+    return net, {"pairs": int(X.shape[0]), "limited_fraction": float((y < 1).float().mean().item()),
+                 "final_batch_mse": loss}
+
+
 def cpu_baseline(name, budget_s=10.0):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload."""
     from oracle import oracle as O
@@ -288,8 +320,10 @@ def main():
     except Exception:
         probes = {"fp64": None, "fp32": None}
 
-    def timed_form(mixed, clocks=None):
+    def timed_form(mixed, clocks=None, net=None, tau=0.02):
         w, sol = build_workload(L, args.workload, stream, mixed)
+        if net is not None:
+            L.lxw_solver_set_mlp(sol, net, tau)
         Q = project(L, sol, w)
         for _ in range(max(args.warmup, 3)):
             L.lxw_profile_step(sol, Q, w["cfl"])
@@ -319,9 +353,13 @@ def main():
                     phases=mean_phase, clocks=clk)
 
     fp64 = timed_form(False)
-    mx = timed_form(True, ClockSampler(local))
+    plain_mx = timed_form(True)
+    t_train = time.perf_counter()
+    net, train_info = train_indicator(L, stream)
+    t_train = time.perf_counter() - t_train
+    mx = timed_form(True, ClockSampler(local), net=net)
     w, sol, dof = mx["w"], mx["sol"], mx["dof"]
-    # one more (untimed) step with diagnostics: how often the FP64 paths ran
+    # one more (untimed) step with diagnostics: how often the FP64 paths ran and the gate skipped
     dmx = L.lxw_step(sol, mx["Q"], 0.0, w["cfl"], diag=True)
 
     # accuracy of the mixed form: relative L1 distance of the density after the same steps
@@ -370,7 +408,8 @@ def main():
            "warmup": args.warmup, "ms_per_step": mx["total_ms"] / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": w["desc"], "elements": sol.N, "degree": w["deg"], "dof_per_step": dof,
-                      "form": "mixed: FP32 bulk, FP64 averages/update/limiter solves (learned indicator not built)",
+                      "form": "mixed + learned: FP32 bulk, FP64 averages/update/limiter solves, "
+                              "MLP-gated shock limiter (BF16 weights, plain limiter fallback)",
                       "cfl": w["cfl"], "l2": "flushed between timed steps (256 MB write)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "roofline": roofline,
@@ -380,6 +419,11 @@ def main():
            "phases_ms": mx["phases"],
            "plain_fp64": plain,
            "speedup_vs_plain_fp64": mx["value"] / fp64["value"],
+           "plain_mixed": {"value": plain_mx["value"], "ms_per_step": plain_mx["total_ms"] / args.steps,
+                           "phases_ms": plain_mx["phases"]},
+           "learned_indicator": dict(train_info, train_s=t_train, tau=0.02,
+                                     skipped_cells_last_step=dmx["n_mlp_skip"], of=sol.N,
+                                     gain_vs_plain_mixed=mx["value"] / plain_mx["value"]),
            "mixed_fp64_path_cells": {"moment": dmx["n_fp64_moment"], "flux_limiter": dmx["n_fp64_edge"],
                                      "of": sol.N},
            "l1_rel_density_mixed_vs_fp64": l1_rel}
