@@ -270,6 +270,17 @@ lxw_status lxw_solver_set_mlp(lxw_solver* s, lxw_mlp* mlp, float tau);
  * (theta_sc_dev[N]): training pairs produced by the method itself. */
 lxw_status lxw_step_dump(lxw_solver* s, void* state_dev, double cfl, float* feat_dev, double* theta_sc_dev);
 
+/* One mixed step gated by the solver's network (lxw_solver_set_mlp), that
+ * also writes the network's output theta_hat for every cell
+ * (gate_dev[N], FP32; NaN where the cell's new averages are not positive,
+ * so that the limiter runs without asking the network) and, when feat_dev
+ * is not null, the cell's features (feat_dev[N][24]).  The network runs on
+ * the tensor cores: BF16 features and weights, FP32 accumulation, the
+ * hidden layer rounded to BF16 between the two matrix products, FP32
+ * output layer and sigmoid.  Errors: LXW_ERR_ARG (null pointer, FP64
+ * form, shock limiter off, no network), LXW_ERR_CUDA. */
+lxw_status lxw_step_gate(lxw_solver* s, void* state_dev, double cfl, float* gate_dev, float* feat_dev);
+
 /* Allocation-free form of lxw_moment_limit, for callers that cannot call
  * cudaMalloc: code running while a stream is captured into a CUDA graph,
  * code whose device memory is owned by another allocator (a framework's

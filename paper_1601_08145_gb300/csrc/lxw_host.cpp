@@ -267,7 +267,8 @@ struct lxw_solver {
   std::vector<int> pstart;       // problem element ranges [nprob + 1]
   std::vector<double> hmin_p;    // per problem
   int4* d_tiles = nullptr;       // work list (owned through allocs)
-  unsigned short* mlp_w = nullptr;  // BF16 gate weights (owned) or null
+  GateWeights* gate_buf = nullptr;  // gate weights (owned), allocated by the first lxw_solver_set_mlp
+  const GateWeights* mlp_w = nullptr;  // gate_buf while a network is attached, else null
   float mlp_tau = 0.0f;
   int tiles_cap = 0;
   int sms = 0;
@@ -654,7 +655,8 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   a.shock_limiter = s->opt.shock_limiter; a.want_diag = want_diag; a.theta_cell = tc; a.theta_edge = te;
   a.gamma_f = (float)a.gamma; a.eps0_f = (float)a.eps0; a.alpha0_f = (float)a.alpha0;
   a.grid = s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm * s->sms : 0;   // persistent CTAs, or one per tile
-  a.mlp_bf16 = s->mlp_w; a.mlp_tau = s->mlp_tau; a.feat_out = nullptr;
+  a.sms = s->sms;
+  a.gate_w = s->mlp_w; a.mlp_tau = s->mlp_tau; a.feat_out = nullptr; a.gate_out = nullptr;
   return a;
 }
 
@@ -826,14 +828,14 @@ lxw_status lxw_solver_set_mlp(lxw_solver* s, lxw_mlp* mlp, float tau) {
   if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
   if (s->pgraph) { cudaGraphExecDestroy(s->pgraph); s->pgraph = nullptr; }
   if (!mlp) { s->mlp_w = nullptr; return LXW_OK; }
-  if (!s->mlp_w) {
+  if (!s->gate_buf) {
     void* p = nullptr;
-    LXW_CUDA(cudaMalloc(&p, sizeof(unsigned short) * kMlpParams));
+    LXW_CUDA(cudaMalloc(&p, sizeof(GateWeights)));
     s->allocs.push_back(p);
-    s->mlp_w = (unsigned short*)p;
+    s->gate_buf = (GateWeights*)p;
   }
-  const unsigned short* src = mlp_bf16_weights(mlp);
-  LXW_CUDA(cudaMemcpy(s->mlp_w, src, sizeof(unsigned short) * kMlpParams, cudaMemcpyDeviceToDevice));
+  if (mlp_gate_weights(mlp, s->gate_buf)) return fail(LXW_ERR_CUDA, "lxw_solver_set_mlp: weight layout failed");
+  s->mlp_w = s->gate_buf;
   s->mlp_tau = tau;
   return LXW_OK;
 }
@@ -846,7 +848,7 @@ lxw_status lxw_step_dump(lxw_solver* s, void* state, double cfl, float* feat, do
   void* scratch = nullptr;
   if (theta_sc) LXW_CUDA(cudaMalloc(&scratch, sizeof(double) * 2 * (size_t)s->N));
   StepArgs a = make_args(s, 0.0, cfl, 0, (double*)scratch, nullptr);
-  a.mlp_bf16 = nullptr;                    // the plain limiter labels the data
+  a.gate_w = nullptr;                      // the plain limiter labels the data
   a.feat_out = feat;
   int rc = do_step(s, (double*)state, a, s->stream);
   if (!rc && theta_sc)
@@ -854,6 +856,22 @@ lxw_status lxw_step_dump(lxw_solver* s, void* state, double cfl, float* feat, do
   cudaError_t se = cudaStreamSynchronize(s->stream);
   if (scratch) cudaFree(scratch);
   if (rc || se != cudaSuccess) return fail(LXW_ERR_CUDA, "lxw_step_dump: launch failed");
+  return LXW_OK;
+}
+
+lxw_status lxw_step_gate(lxw_solver* s, void* state, double cfl, float* gate, float* feat) {
+  if (!s || !state || !gate || !(cfl > 0.0)) return fail(LXW_ERR_ARG, "lxw_step_gate: bad argument");
+  if (!s->mixed) return fail(LXW_ERR_ARG, "lxw_step_gate: needs the mixed form");
+  if (!s->opt.shock_limiter) return fail(LXW_ERR_ARG, "lxw_step_gate: the shock limiter is off");
+  if (!s->mlp_w) return fail(LXW_ERR_ARG, "lxw_step_gate: no network attached (lxw_solver_set_mlp)");
+  // all-ones bytes are a NaN: cells whose averages fail the positivity check get no theta_hat
+  LXW_CUDA(cudaMemsetAsync(gate, 0xff, sizeof(float) * (size_t)s->N, s->stream));
+  StepArgs a = make_args(s, 0.0, cfl, 0, nullptr, nullptr);
+  a.gate_out = gate;
+  a.feat_out = feat;
+  int rc = do_step(s, (double*)state, a, s->stream);
+  cudaError_t se = cudaStreamSynchronize(s->stream);
+  if (rc || se != cudaSuccess) return fail(LXW_ERR_CUDA, "lxw_step_gate: launch failed");
   return LXW_OK;
 }
 

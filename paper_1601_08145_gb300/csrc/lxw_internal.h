@@ -104,13 +104,28 @@ constexpr int kMlpIn = 24, kMlpH = 64;
 constexpr int kW1 = 0, kB1 = kW1 + kMlpIn * kMlpH, kW2 = kB1 + kMlpH, kB2 = kW2 + kMlpH * kMlpH,
               kW3 = kB2 + kMlpH, kB3 = kW3 + kMlpH, kMlpParams = kB3 + 1;
 
+// The gate's weights in the shock kernel's shared-memory layout: BF16 W1 and
+// W2 stored output-major (row n holds the weights into hidden unit n), so
+// that an mma.sync B fragment is one 32-bit load; rows padded (24 -> 40,
+// 64 -> 72 halves) so the 8 rows a fragment touches fall in distinct banks.
+// Biases, output weights and output bias are the BF16 values widened to FP32.
+constexpr int kGateK1 = 40, kGateK2 = 72;
+struct GateWeights {
+  unsigned short w1t[kMlpH][kGateK1];
+  unsigned short w2t[kMlpH][kGateK2];
+  float b1[kMlpH], b2[kMlpH], w3[kMlpH], b3, pad[3];
+};
+static_assert(sizeof(GateWeights) % 16 == 0, "GateWeights is copied in 16-byte words");
+
 struct StepArgs {
   int grid;                          // mixed form: persistent CTAs (0 = one per tile)
   double dt_in, cfl, gamma, eps0, alpha0;
   float gamma_f, eps0_f, alpha0_f;   // FP32 copies for the mixed form
-  const unsigned short* mlp_bf16;    // learned gate weights (BF16 bits) or null
+  int sms;                           // SMs of the device (persistent grid of the gated shock kernel)
+  const GateWeights* gate_w;         // learned gate weights or null
   float mlp_tau;                     // gate: skip the limiter where theta_hat >= 1 - tau
   float* feat_out;                   // [N][24] features at the shock limiter's input, or null
+  float* gate_out;                   // [N] network output theta_hat (needs the gate), or null
   int shock_limiter;
   int want_diag;
   double* theta_cell;     // [2][N] or null
@@ -118,8 +133,9 @@ struct StepArgs {
 };
 
 // Kernel launchers (lxw_kernels.cu).  All enqueue on `stream`, allocate nothing.
-// BF16 copy of an MLP's parameters (lxw_mlp.cu).
-const unsigned short* mlp_bf16_weights(lxw_mlp* n);
+// Writes an MLP's parameters, rounded to BF16, into a device GateWeights
+// (lxw_mlp.cu); synchronises the MLP's stream.  0 on success.
+int mlp_gate_weights(lxw_mlp* n, GateWeights* out_dev);
 // Sets the message lxw_last_error() returns on this thread.
 void set_last_error(const char* msg);
 // Builds the quadrature / basis tables of one (kind, degree) on the host.

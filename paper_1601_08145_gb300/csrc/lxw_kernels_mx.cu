@@ -190,136 +190,210 @@ __device__ __forceinline__ void block_max(float v, unsigned long long* dst) {
 }
 
 // ---------------------------------------------------------- k_moment_mx
-// Sec. 3.1.  FP32 screen: every limiter point has rho and p above their
-// floors by more than the FP32 error bound -> theta = 1 exactly.  Otherwise
-// the FP64 algorithm (Steps 0-2) runs on the promoted coefficients.
+// Sec. 3.1.  FP32 screen, one thread per cell: a limiter point whose FP32
+// density (pressure) clears its floor by more than the FP32 error bound
+// cannot constrain theta -- the density is linear in theta, and the pressure
+// along theta is concave (above the chord from the average's pressure,
+// >= 2 eps_p, to the point's, > eps_p).  A cell all of whose points clear
+// keeps theta = 1 exactly.  The other (cell, point) pairs are listed per
+// warp in shared memory and evaluated in FP64, 32 pairs at a time, one per
+// lane: Step 1 (density) then Step 2 (pressure of the density-limited
+// state).  Each cell's theta is the minimum of its pairs' candidates, taken
+// with shared-memory atomicMin on the bit patterns of the (positive)
+// doubles, which is exact in any order: the same theta as a serial loop over
+// all points.
 template <int KD, int E, int ML, int NQ, int MQ>
-__device__ __forceinline__ float moment_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
-                                             const StepArgs& a, double* __restrict__ theta_out, const int i) {
+__device__ __forceinline__ float moment_screen(const DevMesh& m, double* __restrict__ state, const StepArgs& a,
+                                               const int i, unsigned& mr, unsigned& mp) {
   constexpr int NPT = NQ + E * MQ;
   const TablesF& t = c_tabf[KD];
   const int N = m.N;
+  MxState st = mx_state<ML>(state, N);
+  const float g = a.gamma_f, g1 = g - 1.0f;
+  float a32[4], c[4][ML];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    a32[v] = st.a32[(size_t)v * N + i];
+#pragma unroll
+    for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
+  }
   float smax = 0.0f;
-  {
-    MxState st = mx_state<ML>(state, N);
-    const float g = a.gamma_f, g1 = g - 1.0f;
-    float a32[4], c[4][ML];
+  const float eps0 = a.eps0_f;
+  const float ri = 1.0f / a32[0];
+  const float kb = 0.5f * (a32[1] * a32[1] + a32[2] * a32[2]) * ri;
+  const float pb = g1 * (a32[3] - kb);
+  const bool avg_ok = a32[0] > 0.0f && pb > kTol * g1 * (fabsf(a32[3]) + kb);
+  const float er = fminf(eps0, 0.5f * a32[0]) * (1.0f + kTol);
+  const float ep = fminf(eps0, 0.5f * pb) * (1.0f + kTol);
+  mr = 0u; mp = 0u;
+#pragma unroll 1
+  for (int p = 0; p < NPT; ++p) {
+    float q[4], S[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      a32[v] = st.a32[(size_t)v * N + i];
+      float acc = a32[v], sa = fabsf(a32[v]);
 #pragma unroll
-      for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
+      for (int l = 1; l < ML; ++l) {
+        float term = c[v][l] * t.phi[p][l];
+        acc += term; sa += fabsf(term);
+      }
+      q[v] = acc; S[v] = sa;
     }
-    // --- FP32 screen
-    bool clear = a32[0] > 0.0f;
-    const float eps0 = a.eps0_f;
-    {
-      const float ri = 1.0f / a32[0];
-      const float kb = 0.5f * (a32[1] * a32[1] + a32[2] * a32[2]) * ri;
-      const float pb = g1 * (a32[3] - kb);
-      clear = clear && pb > kTol * g1 * (fabsf(a32[3]) + kb);
-      const float er = fminf(eps0, 0.5f * a32[0]) * (1.0f + kTol);
-      const float ep = fminf(eps0, 0.5f * pb) * (1.0f + kTol);
-#pragma unroll 1
-      for (int p = 0; p < NPT; ++p) {
-        float q[4], S[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          float acc = a32[v], sa = fabsf(a32[v]);
-#pragma unroll
-          for (int l = 1; l < ML; ++l) {
-            float term = c[v][l] * t.phi[p][l];
-            acc += term; sa += fabsf(term);
-          }
-          q[v] = acc; S[v] = sa;
-        }
-        const float rinv = 1.0f / q[0];
-        const float u = q[1] * rinv, vv = q[2] * rinv;
-        const float k2 = q[1] * u + q[2] * vv;
-        const float pp = g1 * (q[3] - 0.5f * k2);
-        const float B = S[3] + fabsf(u) * S[1] + fabsf(vv) * S[2] + 0.5f * (u * u + vv * vv) * S[0];
-        clear = clear && q[0] > er + kTol * S[0] && pp > ep + kTol * g1 * B;
-        const float pc = pp > 0.0f ? pp : 0.0f;
-        smax = fmaxf(smax, sqrtf(u * u + vv * vv) + sqrtf(g * pc * rinv));
-      }
-      if (clear) smax = fmaxf(smax, speedf(g, a32[0], a32[1], a32[2], a32[3]));
-    }
-    double th = 1.0;
-    if (!clear) {
-      // --- FP64 path: the algorithm of Sec. 3.1 on the promoted coefficients
-      atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->fb_mom, 1ull);
-      const double gd1 = a.gamma - 1.0;
-      const double rb = st.avg[i], mb = st.avg[(size_t)N + i], nb = st.avg[2 * (size_t)N + i],
-                   eb = st.avg[3 * (size_t)N + i];
-      const double pb = rb > 0.0 ? gd1 * (eb - 0.5 * (mb * mb + nb * nb) / rb) : -1.0;
-      if (!(rb > 0.0) || !(pb > 0.0)) {
-        atomicOr(w.status, (unsigned)LXW_ST_NONPOSITIVE);
-        th = 0.0;
-      } else {
-        const double er = fmin(a.eps0, 0.5 * rb);
-        double thr = 1.0;
-#pragma unroll 1
-        for (int p = 0; p < NPT; ++p) {
-          double d = 0.0;
-#pragma unroll
-          for (int l = 1; l < ML; ++l) d = fma((double)c[0][l], (double)t.phi[p][l], d);
-          double rm = rb + d;
-          if (rm < er) thr = fmin(thr, (rb - er) / (rb - rm));
-        }
-        const double ep = fmin(a.eps0, 0.5 * pb);
-        th = thr;
-#pragma unroll 1
-        for (int p = 0; p < NPT; ++p) {
-          double d[4];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            double acc = 0.0;
-#pragma unroll
-            for (int l = 1; l < ML; ++l) acc = fma((double)c[v][l], (double)t.phi[p][l], acc);
-            d[v] = acc;
-          }
-          double r = rb + thr * d[0], mm = mb + thr * d[1], nn = nb + thr * d[2], ee = eb + thr * d[3];
-          double pt = gd1 * (ee - 0.5 * (mm * mm + nn * nn) / r);
-          if (pt < ep) th = fmin(th, thr * (pb - ep) / (pb - pt));
-        }
-        th = fmax(th, 0.0);
-      }
-      // speeds of the limited state (FP32)
-      smax = 0.0f;
-      const float thf = (float)th;
-      if (a32[0] > 0.0f) smax = speedf(g, a32[0], a32[1], a32[2], a32[3]);
-#pragma unroll 1
-      for (int p = 0; p < NPT; ++p) {
-        float q[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int l = 1; l < ML; ++l) acc += c[v][l] * t.phi[p][l];
-          q[v] = a32[v] + thf * acc;
-        }
-        if (q[0] > 0.0f) smax = fmaxf(smax, speedf(g, q[0], q[1], q[2], q[3]));
-      }
-      if (th < 1.0) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-#pragma unroll
-          for (int l = 1; l < ML; ++l) hi_at<ML>(st, N, v, l, i) = (float)(th * (double)c[v][l]);
-        if (a.want_diag) atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->nmom, 1ull);
-      }
-    }
-    if (theta_out) theta_out[i] = th;
+    const float rinv = 1.0f / q[0];
+    const float u = q[1] * rinv, vv = q[2] * rinv;
+    const float k2 = q[1] * u + q[2] * vv;
+    const float pp = g1 * (q[3] - 0.5f * k2);
+    const float B = S[3] + fabsf(u) * S[1] + fabsf(vv) * S[2] + 0.5f * (u * u + vv * vv) * S[0];
+    const bool rok = q[0] > er + kTol * S[0];
+    const bool pok = rok && pp > ep + kTol * g1 * B;
+    mr |= rok ? 0u : (1u << p);
+    mp |= pok ? 0u : (1u << p);
+    const float pc = pp > 0.0f ? pp : 0.0f;
+    smax = fmaxf(smax, sqrtf(u * u + vv * vv) + sqrtf(g * pc * rinv));
   }
+  if (!avg_ok) {                       // the averages themselves are too close to call in FP32
+    mr = mp = NPT == 32 ? 0xffffffffu : ((1u << NPT) - 1u);
+  }
+  if (!(mr | mp)) smax = fmaxf(smax, speedf(g, a32[0], a32[1], a32[2], a32[3]));
   return smax;
 }
+
+// Runs f(cell_lane, point) once for every set bit of every lane's mask,
+// spread over the warp's lanes (list: the warp's shared scratch, >= 32 * 32
+// entries).  All 32 lanes must call it.
+template <class F>
+__device__ __forceinline__ void warp_pairs(unsigned mask, unsigned short* list, F&& f) {
+  const int lane = threadIdx.x & 31;
+  const int cnt = __popc(mask);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int off = incl - cnt;
+  while (mask) {
+    const int p = __ffs(mask) - 1;
+    mask &= mask - 1;
+    list[off++] = (unsigned short)((lane << 8) | p);
+  }
+  __syncwarp();
+  for (int k = lane; k < total; k += 32) {
+    const unsigned e = list[k];
+    f((int)(e >> 8), (int)(e & 255u));
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(unsigned long long u) { return __longlong_as_double((long long)u); }
 
 template <int KD, int E, int ML, int NQ, int MQ>
 __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                    const StepArgs a, double* __restrict__ theta_out) {
+  constexpr int NPT = NQ + E * MQ;
+  static_assert(NPT <= 32, "a cell's limiter points fit one 32-bit mask");
+  __shared__ unsigned short pair_list[4][32 * 32];
+  __shared__ unsigned long long th_slot[4][32];
+  __shared__ double thr_s[4][32], pb_s[4][32];
+  const TablesF& t = c_tabf[KD];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  DiagBlock* dg = reinterpret_cast<DiagBlock*>(w.diag);
+  const int N = m.N;
+  MxState st = mx_state<ML>(state, N);
+  const double gd1 = a.gamma - 1.0;
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
+    const int i = tile.x + threadIdx.x;
+    const int wbase = tile.x + warp * 32;      // element of lane 0 of this warp
     float sm = 0.0f;
-    if ((int)threadIdx.x < tile.y) sm = moment_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, tile.x + threadIdx.x);
+    unsigned mr = 0u, mp = 0u;
+    if ((int)threadIdx.x < tile.y) sm = moment_screen<KD, E, ML, NQ, MQ>(m, state, a, i, mr, mp);
+    bool need = (mr | mp) != 0u;
+    if (__any_sync(0xffffffffu, need)) {
+      // FP64 averages of the cells that need the FP64 path
+      bool bad = false;
+      if (need) {
+        const double rb = st.avg[i], mb = st.avg[(size_t)N + i], nb = st.avg[2 * (size_t)N + i],
+                     eb = st.avg[3 * (size_t)N + i];
+        const double pb = rb > 0.0 ? gd1 * (eb - 0.5 * (mb * mb + nb * nb) / rb) : -1.0;
+        bad = !(rb > 0.0) || !(pb > 0.0);
+        if (bad) mr = mp = 0u;
+        pb_s[warp][lane] = pb;
+      }
+      th_slot[warp][lane] = dbits(1.0);
+      __syncwarp();
+      // Step 1: density candidates
+      warp_pairs(mr, pair_list[warp], [&](int cl, int p) {
+        const int ci = wbase + cl;
+        const double rb = st.avg[ci];
+        double d = 0.0;
+#pragma unroll
+        for (int l = 1; l < ML; ++l) d = fma((double)hi_at<ML>(st, N, 0, l, ci), (double)t.phi[p][l], d);
+        const double rm = rb + d;
+        const double er = fmin(a.eps0, 0.5 * rb);
+        if (rm < er) atomicMin(&th_slot[warp][cl], dbits((rb - er) / (rb - rm)));
+      });
+      const double thr = bitsd(th_slot[warp][lane]);
+      thr_s[warp][lane] = thr;
+      __syncwarp();
+      // Step 2: pressure candidates of the density-limited state (th starts at thr)
+      warp_pairs(mp, pair_list[warp], [&](int cl, int p) {
+        const int ci = wbase + cl;
+        const double thr_c = thr_s[warp][cl], pb = pb_s[warp][cl];
+        double d[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          double acc = 0.0;
+#pragma unroll
+          for (int l = 1; l < ML; ++l) acc = fma((double)hi_at<ML>(st, N, v, l, ci), (double)t.phi[p][l], acc);
+          d[v] = acc;
+        }
+        const double r = st.avg[ci] + thr_c * d[0], mm = st.avg[(size_t)N + ci] + thr_c * d[1],
+                     nn = st.avg[2 * (size_t)N + ci] + thr_c * d[2], ee = st.avg[3 * (size_t)N + ci] + thr_c * d[3];
+        const double pt = gd1 * (ee - 0.5 * (mm * mm + nn * nn) / r);
+        const double ep = fmin(a.eps0, 0.5 * pb);
+        if (pt < ep) atomicMin(&th_slot[warp][cl], dbits(thr_c * (pb - ep) / (pb - pt)));
+      });
+      if (need) {
+        double th = bad ? 0.0 : fmax(bitsd(th_slot[warp][lane]), 0.0);
+        atomicAdd(&dg->fb_mom, 1ull);
+        if (bad) atomicOr(w.status, (unsigned)LXW_ST_NONPOSITIVE);
+        // speeds of the limited state (FP32)
+        const float g = a.gamma_f, thf = (float)th;
+        float a32[4], c[4][ML];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          a32[v] = st.a32[(size_t)v * N + i];
+#pragma unroll
+          for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
+        }
+        sm = a32[0] > 0.0f ? speedf(g, a32[0], a32[1], a32[2], a32[3]) : 0.0f;
+#pragma unroll 1
+        for (int p = 0; p < NPT; ++p) {
+          float q[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 1; l < ML; ++l) acc += c[v][l] * t.phi[p][l];
+            q[v] = a32[v] + thf * acc;
+          }
+          if (q[0] > 0.0f) sm = fmaxf(sm, speedf(g, q[0], q[1], q[2], q[3]));
+        }
+        if (th < 1.0) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int l = 1; l < ML; ++l) hi_at<ML>(st, N, v, l, i) = (float)(th * (double)c[v][l]);
+          if (a.want_diag) atomicAdd(&dg->nmom, 1ull);
+        }
+        if (theta_out) theta_out[i] = th;
+      }
+      __syncwarp();
+    }
+    if (!need && (int)threadIdx.x < tile.y && theta_out) theta_out[i] = 1.0;
     block_max(sm, &w.smax[tile.z]);
   }
 }
@@ -852,38 +926,159 @@ __device__ __forceinline__ void cell_features(const float c[4][ML], const float 
   for (int k = 0; k < kMlpIn; ++k) f[k] = fminf(8.0f, fmaxf(-8.0f, f[k]));
 }
 
-// theta_hat of the MLP with FP32 weights staged in shared memory
-__device__ __forceinline__ float mlp_theta(const float* __restrict__ W, const float f[kMlpIn]) {
-  float h1[kMlpH];
-#pragma unroll
-  for (int j = 0; j < kMlpH; ++j) h1[j] = W[kB1 + j];
-#pragma unroll
-  for (int i = 0; i < kMlpIn; ++i)
-#pragma unroll
-    for (int j = 0; j < kMlpH; ++j) h1[j] = fmaf(f[i], W[kW1 + i * kMlpH + j], h1[j]);
-#pragma unroll
-  for (int j = 0; j < kMlpH; ++j) h1[j] = fmaxf(h1[j], 0.0f);
-  float out = W[kB3];
-#pragma unroll 4
-  for (int j = 0; j < kMlpH; ++j) {
-    float acc = W[kB2 + j];
-#pragma unroll
-    for (int k = 0; k < kMlpH; ++k) acc = fmaf(h1[k], W[kW2 + k * kMlpH + j], acc);
-    out = fmaf(fmaxf(acc, 0.0f), W[kW3 + j], out);
-  }
-  return 1.0f / (1.0f + __expf(-out));
+// ---- tensor-core inference of the gate (BF16 mma.sync m16n8k16, FP32 accumulate)
+// One warp evaluates the network for its 32 cells as two 16-row M tiles:
+// H1 = relu(X W1 + b1) with X [32 x 32] (24 features, zero padded), then
+// H2 = relu(H1 W2 + b2) with H1 rounded to BF16 (the accumulator fragment
+// of the first product is, element for element, the A fragment of the
+// second), then theta_hat = sigmoid(H2 w3 + b3) on the CUDA cores.
+constexpr int KP1 = kGateK1;
+struct GateSmem {
+  GateWeights w;
+  unsigned short feat[4][32][KP1];   // features of 4 warps (128 threads) x 32 cells, BF16
+};
+
+__device__ __forceinline__ unsigned short f2bf(float x) {
+  unsigned u = __float_as_uint(x);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (unsigned short)(u >> 16);
+}
+__device__ __forceinline__ unsigned pack2(unsigned short lo, unsigned short hi) { return (unsigned)lo | ((unsigned)hi << 16); }
+__device__ __forceinline__ unsigned ld2(const unsigned short* p) { return *reinterpret_cast<const unsigned*>(p); }
+
+__device__ __forceinline__ void mma_bf16(float d[4], const unsigned a[4], const unsigned b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// ---------------------------------------------------------- k_shock_mx
-// Sec. 4.1 on the new state in FP32 (neighbour averages from the FP32 copy
-// of avg_new), then commits the new averages (FP64 and FP32).  With the
-// learned gate on, cells whose theta_hat is at least 1 - tau keep theta = 1
-// without the limiter's point work; every other cell runs the limiter.  With
-// the shock limiter off only the commit runs.
-template <int KD, int E, int ML, int NQ, int MQ, bool GATE>
+// copy the prepared GateWeights into the CTA's shared memory (16-byte words)
+__device__ __forceinline__ void stage_gate(GateSmem& g, const GateWeights* __restrict__ src) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(&g.w);
+  constexpr int n4 = (int)(sizeof(GateWeights) / 16);
+  for (int k = threadIdx.x; k < n4; k += blockDim.x) d4[k] = __ldg(s4 + k);
+}
+
+// theta_hat for the 32 cells of this warp, whose features are in g.feat[warp];
+// returns the value of the calling lane's cell.  All 32 lanes must call it.
+__device__ __forceinline__ float gate_mma(const GateSmem& g, int warp) {
+  const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+  const GateWeights& W = g.w;
+  // layer 1: [32 x 32] x [32 x 64], each B fragment used by both M tiles
+  float d1[2][8][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) d1[mt][nt][0] = d1[mt][nt][1] = d1[mt][nt][2] = d1[mt][nt][3] = 0.0f;
+#pragma unroll
+  for (int kt = 0; kt < 2; ++kt) {
+    const int c0 = kt * 16 + 2 * tq;
+    unsigned a[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r0 = mt * 16 + gq;
+      // A register order of m16n8k16: (row g, k 0-7), (row g+8, k 0-7), (row g, k 8-15), (row g+8, k 8-15)
+      a[mt][0] = ld2(&g.feat[warp][r0][c0]);     a[mt][1] = ld2(&g.feat[warp][r0 + 8][c0]);
+      a[mt][2] = ld2(&g.feat[warp][r0][c0 + 8]); a[mt][3] = ld2(&g.feat[warp][r0 + 8][c0 + 8]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const unsigned b[2] = {ld2(&W.w1t[nt * 8 + gq][c0]), ld2(&W.w1t[nt * 8 + gq][c0 + 8])};
+      mma_bf16(d1[0][nt], a[0], b);
+      mma_bf16(d1[1][nt], a[1], b);
+    }
+  }
+  // bias + ReLU, rounded to BF16 and repacked as the A fragments of layer 2
+  unsigned a2[2][4][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const int col = nt * 8 + 2 * tq;
+    const float bb0 = W.b1[col], bb1 = W.b1[col + 1];
+    const int kt = nt >> 1, half = nt & 1;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      a2[mt][kt][half * 2 + 0] = pack2(f2bf(fmaxf(d1[mt][nt][0] + bb0, 0.0f)), f2bf(fmaxf(d1[mt][nt][1] + bb1, 0.0f)));
+      a2[mt][kt][half * 2 + 1] = pack2(f2bf(fmaxf(d1[mt][nt][2] + bb0, 0.0f)), f2bf(fmaxf(d1[mt][nt][3] + bb1, 0.0f)));
+    }
+  }
+  // layer 2: [32 x 64] x [64 x 64], then the output layer
+  float o[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    float d2[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+      const int c0 = kt * 16 + 2 * tq;
+      const unsigned b[2] = {ld2(&W.w2t[nt * 8 + gq][c0]), ld2(&W.w2t[nt * 8 + gq][c0 + 8])};
+      mma_bf16(d2[0], a2[0][kt], b);
+      mma_bf16(d2[1], a2[1][kt], b);
+    }
+    const int col = nt * 8 + 2 * tq;
+    const float bb0 = W.b2[col], bb1 = W.b2[col + 1], w0 = W.w3[col], w1 = W.w3[col + 1];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      o[mt][0] += fmaxf(d2[mt][0] + bb0, 0.0f) * w0 + fmaxf(d2[mt][1] + bb1, 0.0f) * w1;   // row g
+      o[mt][1] += fmaxf(d2[mt][2] + bb0, 0.0f) * w0 + fmaxf(d2[mt][3] + bb1, 0.0f) * w1;   // row g + 8
+    }
+  }
+  // sum over the 4 lanes of a group
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      o[mt][h] += __shfl_xor_sync(0xffffffffu, o[mt][h], 1);
+      o[mt][h] += __shfl_xor_sync(0xffffffffu, o[mt][h], 2);
+    }
+  // lane l owns cell row l: M tile l/16, row l%16, held by lanes 4*((l%16)%8) .. +3
+  const int rr = lane & 15, src = (rr & 7) * 4;
+  const float v00 = __shfl_sync(0xffffffffu, o[0][0], src), v01 = __shfl_sync(0xffffffffu, o[0][1], src);
+  const float v10 = __shfl_sync(0xffffffffu, o[1][0], src), v11 = __shfl_sync(0xffffffffu, o[1][1], src);
+  const float z = (lane < 16 ? (rr < 8 ? v00 : v01) : (rr < 8 ? v10 : v11)) + W.b3;
+  return 1.0f / (1.0f + __expf(-z));
+}
+
+// the gate's features of element i at the shock limiter's input (false: no features, run the limiter)
+template <int E, int ML>
+__device__ __forceinline__ bool gate_features(const DevMesh& m, const DevWorkMx& w, const double* __restrict__ state,
+                                              const StepArgs& a, const int i, float f[kMlpIn]) {
+  const int N = m.N;
+  MxState st = mx_state<ML>(const_cast<double*>(state), N);
+  float c[4][ML];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    c[v][0] = w.avgn32[(size_t)v * N + i];
+#pragma unroll
+    for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
+  }
+  if (!(c[0][0] > 0.0f) || !(c[3][0] > 0.0f)) return false;
+  float nr[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ne[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const float an[4] = {c[0][0], c[1][0], c[2][0], c[3][0]};
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const int j = m.nbr[k * N + i];
+    float qn[4];
+    if (j >= 0) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) qn[v] = w.avgn32[(size_t)v * N + j];
+    } else {
+      const float nx = m.nrm32[(2 * k) * N + i], ny = m.nrm32[(2 * k + 1) * N + i];
+      const float ln = sqrtf(nx * nx + ny * ny);
+      ghostq<float>(-1 - j, nx / ln, ny / ln, an, qn);
+    }
+    nr[k] = qn[0]; ne[k] = qn[3];
+  }
+  const float dx = m.sdx32[i];
+  cell_features<E, ML>(c, nr, ne, a.gamma_f, a.alpha0_f * dx * sqrtf(dx), f);
+  return true;
+}
+
+template <int KD, int E, int ML, int NQ, int MQ>
 __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
                                            const StepArgs& a, double* __restrict__ theta_out, const int limit,
-                                           const int i, const float* __restrict__ Wsm) {
+                                           const int i, const bool skip) {
   constexpr int NPT = NQ + E * MQ;
   const TablesF& t = c_tabf[KD];
   const int N = m.N;
@@ -929,16 +1124,6 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
         const float wn[4] = {sn.r, sn.u, sn.v, sn.p};
 #pragma unroll
         for (int v = 0; v < 4; ++v) { Mx[v] = fmaxf(Mx[v], wn[v]); Mn[v] = fminf(Mn[v], wn[v]); }
-      }
-      bool skip = false;
-      if (GATE) {
-        float f[kMlpIn];
-        cell_features<E, ML>(c, nr, ne, a.gamma_f, al, f);
-        if (a.feat_out) {
-#pragma unroll
-          for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
-        }
-        if (Wsm) skip = mlp_theta(Wsm, f) >= 1.0f - a.mlp_tau;
       }
       if (skip) {
         if (a.want_diag) atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->mlp_skip, 1ull);
@@ -996,18 +1181,40 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
 template <int KD, int E, int ML, int NQ, int MQ, bool GATE>
 __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                   const StepArgs a, double* __restrict__ theta_out, int limit) {
-  extern __shared__ float mlp_w[];
-  const float* Wsm = nullptr;
-  if (GATE && a.mlp_bf16 && limit) {
-    for (int k = threadIdx.x; k < kMlpParams; k += blockDim.x)
-      mlp_w[k] = __uint_as_float((unsigned)a.mlp_bf16[k] << 16);
+  extern __shared__ __align__(16) unsigned char gate_raw[];
+  GateSmem& g = *reinterpret_cast<GateSmem*>(gate_raw);
+  const bool net = GATE && a.gate_w != nullptr && limit;
+  if (net) {
+    stage_gate(g, a.gate_w);
     __syncthreads();
-    Wsm = mlp_w;
   }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
-    if ((int)threadIdx.x < tile.y)
-      shock_elem<KD, E, ML, NQ, MQ, GATE>(m, w, state, a, theta_out, limit, tile.x + threadIdx.x, Wsm);
+    const bool active = (int)threadIdx.x < tile.y;
+    const int i = tile.x + threadIdx.x;
+    bool skip = false;
+    if (GATE && limit) {
+      float f[kMlpIn];
+      const bool ok = active && gate_features<E, ML>(m, w, state, a, i, f);
+      if (ok && a.feat_out) {
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
+      }
+      if (net) {
+        unsigned* row = reinterpret_cast<unsigned*>(&g.feat[warp][lane][0]);
+#pragma unroll
+        for (int k = 0; k < kMlpIn / 2; ++k) row[k] = ok ? pack2(f2bf(f[2 * k]), f2bf(f[2 * k + 1])) : 0u;
+#pragma unroll
+        for (int k = kMlpIn / 2; k < 16; ++k) row[k] = 0u;
+        __syncwarp();
+        const float th_hat = gate_mma(g, warp);
+        __syncwarp();
+        if (ok && a.gate_out) a.gate_out[i] = th_hat;
+        skip = ok && th_hat >= 1.0f - a.mlp_tau;
+      }
+    }
+    if (active) shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, limit, i, skip);
   }
 }
 
@@ -1082,9 +1289,15 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
   mark();
   const int limit = a.shock_limiter && upto >= 5;
   double* tsc = a.theta_cell ? a.theta_cell + m.N : nullptr;
-  if (limit && (a.mlp_bf16 || a.feat_out))
-    k_shock_mx<KD, E, ML, NQ, MQ, true><<<grid, block, a.mlp_bf16 ? sizeof(float) * kMlpParams : 0, st>>>(
-        m, w, state, a, tsc, limit);
+  if (limit && (a.gate_w || a.feat_out)) {
+    // persistent CTAs (every CTA stages the weights once): as many as fit on the device
+    static int per_sm = 0;
+    if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shock_mx<KD, E, ML, NQ, MQ, true>, block,
+                                                                 sizeof(GateSmem)) != cudaSuccess)
+      per_sm = 1;
+    const int gg = a.gate_w ? std::min(m.ntiles, std::max(per_sm, 1) * std::max(a.sms, 1)) : grid;
+    k_shock_mx<KD, E, ML, NQ, MQ, true><<<gg, block, a.gate_w ? sizeof(GateSmem) : 0, st>>>(m, w, state, a, tsc, limit);
+  }
   else
     k_shock_mx<KD, E, ML, NQ, MQ, false><<<grid, block, 0, st>>>(m, w, state, a, tsc, limit);
   mark();

@@ -14,6 +14,8 @@
 
 #include "lxw_internal.h"
 
+using namespace lxw;
+
 namespace {
 
 constexpr int TB = 16;   // GEMM tile
@@ -108,18 +110,30 @@ __global__ void k_gather(int B, const int* __restrict__ idx, const float* __rest
   if (c == 0) yb[r] = y[s];
 }
 
-__global__ void k_to_bf16(int n, const float* __restrict__ p, unsigned short* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  // round to nearest even
-  unsigned u = __float_as_uint(p[i]);
+// round to nearest even (the parameters are finite)
+__device__ __forceinline__ unsigned short bf16_rne(float x) {
+  unsigned u = __float_as_uint(x);
   u += 0x7fffu + ((u >> 16) & 1u);
-  out[i] = (unsigned short)(u >> 16);
+  return (unsigned short)(u >> 16);
+}
+__device__ __forceinline__ float bf16_widen(unsigned short h) { return __uint_as_float((unsigned)h << 16); }
+
+// parameter vector -> GateWeights (zero padding included)
+__global__ void k_gate_layout(const float* __restrict__ p, GateWeights* __restrict__ g) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kMlpH * kGateK2; k += gridDim.x * blockDim.x) {
+    const int n = k / kGateK2, c = k % kGateK2;
+    g->w2t[n][c] = c < kMlpH ? bf16_rne(p[kW2 + c * kMlpH + n]) : (unsigned short)0;
+    if (c < kGateK1) g->w1t[n][c] = c < kMlpIn ? bf16_rne(p[kW1 + c * kMlpH + n]) : (unsigned short)0;
+    if (c < kMlpH && n == 0) {
+      g->b1[c] = bf16_widen(bf16_rne(p[kB1 + c]));
+      g->b2[c] = bf16_widen(bf16_rne(p[kB2 + c]));
+      g->w3[c] = bf16_widen(bf16_rne(p[kW3 + c]));
+    }
+    if (k == 0) { g->b3 = bf16_widen(bf16_rne(p[kB3])); g->pad[0] = g->pad[1] = g->pad[2] = 0.0f; }
+  }
 }
 
 }  // namespace
-
-using namespace lxw;
 
 struct lxw_mlp {
   int maxB = 0;
@@ -128,7 +142,6 @@ struct lxw_mlp {
   float *Z1 = nullptr, *H1 = nullptr, *Z2 = nullptr, *H2 = nullptr, *z3 = nullptr, *yhat = nullptr, *dz = nullptr;
   float *dH = nullptr, *Xb = nullptr, *yb = nullptr, *loss = nullptr;
   int* idx = nullptr;
-  unsigned short* bf16 = nullptr;
   int adam_t = 0;
   std::vector<void*> allocs;
   ~lxw_mlp() { for (void* p : allocs) cudaFree(p); }
@@ -212,7 +225,6 @@ lxw_status lxw_mlp_create(int max_batch, unsigned long long seed, void* stream, 
   n->Xb = (float*)al(sizeof(float) * B * kMlpIn); n->yb = (float*)al(sizeof(float) * B);
   n->idx = (int*)al(sizeof(int) * B);
   n->loss = (float*)al(sizeof(float));
-  n->bf16 = (unsigned short*)al(sizeof(unsigned short) * kMlpParams);
   for (void* p : n->allocs)
     if (!p) { delete n; return mfail(LXW_ERR_NOMEM, "lxw_mlp_create: device allocation failed"); }
   // He initialisation from SplitMix64 (Box-Muller), zero biases
@@ -308,10 +320,8 @@ lxw_status lxw_mlp_train(lxw_mlp* n, const float* X, const float* y, int count, 
 }  // extern "C"
 
 namespace lxw {
-// BF16 copy of the parameters for the step kernels (kept inside the MLP object)
-const unsigned short* mlp_bf16_weights(lxw_mlp* n) {
-  k_to_bf16<<<(kMlpParams + 255) / 256, 256, 0, n->stream>>>(kMlpParams, n->params, n->bf16);
-  cudaStreamSynchronize(n->stream);
-  return n->bf16;
+int mlp_gate_weights(lxw_mlp* n, GateWeights* out) {
+  k_gate_layout<<<(kMlpH * kGateK2 + 255) / 256, 256, 0, n->stream>>>(n->params, out);
+  return cudaStreamSynchronize(n->stream) == cudaSuccess ? 0 : -1;
 }
 }  // namespace lxw

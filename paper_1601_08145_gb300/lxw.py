@@ -32,6 +32,7 @@ EXPORTS = [
     "lxw_batch_create", "lxw_batch_scalars", "lxw_autotune",
     "lxw_mlp_create", "lxw_mlp_destroy", "lxw_mlp_num_params", "lxw_mlp_get_params", "lxw_mlp_set_params",
     "lxw_mlp_forward", "lxw_mlp_loss_grad", "lxw_mlp_train", "lxw_solver_set_mlp", "lxw_step_dump",
+    "lxw_step_gate",
 ]
 
 
@@ -111,6 +112,7 @@ def lib():
                                 C.POINTER(C.c_float)]
     L.lxw_solver_set_mlp.argtypes = [_vp, _vp, C.c_float]
     L.lxw_step_dump.argtypes = [_vp, _vp, C.c_double, _vp, _vp]
+    L.lxw_step_gate.argtypes = [_vp, _vp, C.c_double, _vp, _vp]
     L.lxw_state_bytes.argtypes = [_vp]
     L.lxw_state_bytes.restype = C.c_size_t
     L.lxw_state_pack.argtypes = [_vp, _vp, _vp]
@@ -452,3 +454,14 @@ def lxw_step_dump(solver, state, cfl):
     th = torch.empty(solver.N, dtype=torch.float64, device="cuda")
     _check(lib().lxw_step_dump(solver.h, _ptr(state, solver.state_shape, "state"), cfl, _fptr(F), _ptr(th)))
     return F, th
+
+
+def lxw_step_gate(solver, state, cfl, features=False):
+    """One step gated by the solver's network; returns theta_hat [N] float32
+    (NaN where the network was not asked) and, with features=True, the
+    features [N][24] it saw."""
+    import torch
+    g = torch.empty(solver.N, dtype=torch.float32, device="cuda")
+    F = torch.empty((solver.N, MLP_IN), dtype=torch.float32, device="cuda") if features else None
+    _check(lib().lxw_step_gate(solver.h, _ptr(state, solver.state_shape, "state"), cfl, _fptr(g), _fptr(F)))
+    return (g, F) if features else g

@@ -145,3 +145,50 @@ def test_training_and_gated_step(L):
     rel = np.abs(a - b).sum() / np.abs(b).sum()
     print(f"gated blast: skipped {res[True][1]:.0f} cell-steps, density L1 distance {rel:.2e}")
     assert rel < 2e-2
+
+
+def bf16(x):
+    """Round float32 values to BF16 (nearest even), returned as float32."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32)
+
+
+def gate_reference(P, F):
+    """The gate's network in float64 on BF16-rounded features, weights and
+    hidden layer 1 (the rounding the tensor-core path applies), biases and
+    the output layer from BF16 weights: the same operation up to FP32
+    accumulation order."""
+    W = bf16(P).astype(np.float64)
+    W1 = W[:24 * 64].reshape(24, 64); b1 = W[1536:1600]
+    W2 = W[1600:1600 + 4096].reshape(64, 64); b2 = W[5696:5760]
+    w3 = W[5760:5824]; b3 = W[5824]
+    X = bf16(F).astype(np.float64)
+    H1 = bf16(np.maximum(X @ W1 + b1, 0.0).astype(np.float32)).astype(np.float64)
+    H2 = np.maximum(H1 @ W2 + b2, 0.0)
+    return 1.0 / (1.0 + np.exp(-(H2 @ w3 + b3)))
+
+
+@pytest.mark.parametrize("kind,n", [("tri", 21), ("quad", 19)])
+def test_tensor_core_gate_matches_reference_network(L, kind, n):
+    """theta_hat of every cell from the mma.sync path against the same
+    network evaluated in float64 on the features the kernel saw; ragged
+    tiles (N not a multiple of 32) included."""
+    net = L.lxw_mlp_create(256, seed=17, stream=torch.cuda.current_stream())
+    P = L.lxw_mlp_get_params(net).cpu().numpy()
+    assert P.size == 5825
+    box, bc, ic = ((-1.1, 1.1, -1.1, 1.1), (1, 1, 1, 1), synth.ic_blast(n)) if kind == "quad" else \
+        ((0.0, 1.0, 0.0, 1.0), (2, 2, 2, 2), synth.ic_rarefy)
+    s = mixed_solver(L, kind, n, box=box, bc=bc)
+    L.lxw_solver_set_mlp(s, net, 0.0)                     # tau 0: only theta_hat >= 1 would skip
+    st = start(L, s, ic)
+    for _ in range(3):
+        L.lxw_step(s, st, 0.0, 0.1)
+    g, F = L.lxw_step_gate(s, st, 0.1, features=True)
+    g = g.cpu().numpy(); F = F.cpu().numpy()
+    asked = ~np.isnan(g)
+    assert asked.sum() == s.N
+    ref = gate_reference(P, F)
+    # FP32 accumulation of 24 + 64 BF16 products: ~1e-6 relative in z, sigmoid' <= 1/4
+    assert np.abs(g - ref).max() < 2e-5, np.abs(g - ref).max()
+    assert g.std() > 1e-3                                 # the cells do not all give one value
