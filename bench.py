@@ -133,7 +133,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def train_indicator(L, stream):
+def train_indicator(L, stream, tau=0.02):
     """Train the troubled-cell MLP on the GPU from (features, limiter theta)
     pairs that plain mixed runs of the smooth wave, the double rarefaction
     and the blast (scaled down) produce; returns the net and a summary."""
@@ -159,10 +159,25 @@ def train_indicator(L, stream):
     X = torch.cat(Xs); y = torch.cat(ys)
     perm = torch.randperm(X.shape[0], generator=torch.Generator().manual_seed(0)).cuda()
     X, y = X[perm].contiguous(), y[perm].contiguous()
+    nval = X.shape[0] // 5
+    Xv, yv, Xt, yt = X[:nval], y[:nval], X[nval:], y[nval:]
+    # limited cells are rare (well under 1 %): repeat them until they are about
+    # a quarter of the training set, so the loss does not learn "always smooth"
+    lim = yt < 1.0
+    reps = max(1, int(0.25 * Xt.shape[0] / max(int(lim.sum().item()), 1)))
+    Xt = torch.cat([Xt] + [Xt[lim]] * (reps - 1)); yt = torch.cat([yt] + [yt[lim]] * (reps - 1))
+    perm = torch.randperm(Xt.shape[0], generator=torch.Generator().manual_seed(1)).cuda()
+    Xt, yt = Xt[perm].contiguous(), yt[perm].contiguous()
     net = L.lxw_mlp_create(1024, seed=3, stream=stream)
-    loss = L.lxw_mlp_train(net, X, y, epochs=8, batch=512, lr=2e-3)
+    loss = L.lxw_mlp_train(net, Xt, yt, epochs=6, batch=512, lr=2e-3)
+    yh = torch.cat([L.lxw_mlp_forward(net, Xv[k:k + 1024].contiguous()) for k in range(0, Xv.shape[0], 1024)])
+    strong = yv < 1.0 - 2 * tau
+    missed = ((yh >= 1.0 - tau) & strong).sum().item() / max(int(strong.sum().item()), 1)
     return net, {"pairs": int(X.shape[0]), "limited_fraction": float((y < 1).float().mean().item()),
-                 "final_batch_mse": loss}
+                 "limited_repeat": reps, "final_batch_mse": loss,
+                 "heldout_mse": float(torch.mean((yh - yv) ** 2).item()),
+                 "heldout_skip_fraction": float((yh >= 1.0 - tau).float().mean().item()),
+                 "heldout_missed_strongly_limited": missed}
 
 
 def cpu_baseline(name, budget_s=10.0):
@@ -244,18 +259,13 @@ def run_ensemble(args):
     st = L.new_state(b, Q)
     tune = L.lxw_autotune(b, st, e["cfl"], reps=3)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    for _ in range(max(args.warmup, 3)):
-        L.lxw_profile_step(b, st, e["cfl"])
+    L.lxw_run(b, st, max(args.warmup, 3), e["cfl"])
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start(); time.sleep(0.5)
     torch.cuda.synchronize()
-    phases = []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        phases.append(L.lxw_profile_step(b, st, e["cfl"]))
-    torch.cuda.synchronize()
+    total_ms = time_steps(L, b, st, e["cfl"], args.steps, flush)
     clk = clocks.stop()
-    total_ms = sum(sum(p.values()) for p in phases)
+    phases = [L.lxw_profile_step(b, st, e["cfl"]) for _ in range(3)]
     dof = b.N * 4 * b.ML
     # one solver per problem, each its own graph-replayed step, in turn
     sstates = [L.new_state(s, Q[b.offsets[k]:b.offsets[k + 1]].contiguous()) for k, s in enumerate(singles)]
@@ -286,6 +296,51 @@ def run_ensemble(args):
     print(json.dumps(out))
 
 
+def time_steps(L, sol, Q, cfl, steps, flush):
+    """K steps, each one replay of the solver's captured step graph on its
+    stream, bracketed by CUDA events on that stream; the L2 is flushed (256 MB
+    write) before each.  Returns the summed device time in ms."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        evs[k][0].record()
+        L.lxw_run(sol, Q, 1, cfl)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def smooth_l1_error(L, stream, mixed, net=None, tau=0.02):
+    """L1 error of the cell-average density against the exact advected wave
+    (32x32 periodic P2, CFL 0.1, all limiters on, run to t = 0.1 with the last
+    step shortened to land on it).  The exact solution is projected with the
+    library's own projection (8th-order rule)."""
+    import torch
+    w = WORKLOADS["smooth"]
+    _, sol = build_workload(L, "smooth", stream, mixed)
+    if net is not None:
+        L.lxw_solver_set_mlp(sol, net, tau)
+    Q = project(L, sol, w)
+    T, t, dt_last, skipped, steps = 0.1, 0.0, None, 0.0, 0
+    while t < T - 1e-14:
+        dt = T - t if dt_last is not None and t + 1.05 * dt_last >= T else 0.0
+        d = L.lxw_step(sol, Q, dt, w["cfl"], diag=True)
+        t += d["dt"]; dt_last = d["dt"]; skipped += d["n_mlp_skip"]; steps += 1
+    xy = L.lxw_projection_points(sol)
+    ex = synth.exact_smooth_density(xy[..., 0], xy[..., 1], t)
+    prim = torch.from_numpy(np.stack(np.broadcast_arrays(ex, 1.0, 1.0, 1.0), axis=-1).copy()).cuda()
+    Qe = torch.empty(sol.q64_shape, dtype=torch.float64, device="cuda")
+    L.lxw_project(sol, prim, Qe)
+    Qf = L.to_q64(sol, Q) if mixed else Q
+    dr = Qf[:, 0, :] - Qe[:, 0, :]                              # density modes
+    l1 = torch.abs(dr[:, 0]).mean().item()                      # cell averages (unit square, equal cells)
+    # L2 of the DG density against the projected exact one: the basis is
+    # orthonormal on each cell, so ||.||^2 = sum_i |T_i| sum_l dQ_il^2
+    l2 = torch.sqrt((dr ** 2).sum(dim=1).mean()).item()
+    return {"l1": l1, "l2": l2, "t": t, "steps": steps, "gate_skipped_cell_steps": skipped}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -293,6 +348,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rarefy", choices=sorted(WORKLOADS) + ["ensemble"])
+    ap.add_argument("--tau", type=float, default=0.02, help="learned gate: skip where theta_hat >= 1 - tau")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -320,13 +376,12 @@ def main():
     except Exception:
         probes = {"fp64": None, "fp32": None}
 
-    def timed_form(mixed, clocks=None, net=None, tau=0.02):
+    def timed_form(mixed, clocks=None, net=None):
         w, sol = build_workload(L, args.workload, stream, mixed)
         if net is not None:
-            L.lxw_solver_set_mlp(sol, net, tau)
+            L.lxw_solver_set_mlp(sol, net, args.tau)
         Q = project(L, sol, w)
-        for _ in range(max(args.warmup, 3)):
-            L.lxw_profile_step(sol, Q, w["cfl"])
+        L.lxw_run(sol, Q, max(args.warmup, 3), w["cfl"])
         torch.cuda.synchronize()
         if clocks:
             clocks.start()
@@ -334,19 +389,19 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        phases = []
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            phases.append(L.lxw_profile_step(sol, Q, w["cfl"]))
-        torch.cuda.synchronize()
+        total_ms = time_steps(L, sol, Q, w["cfl"], args.steps, flush)
         if world > 1:
             dist.barrier()
         clk = clocks.stop() if clocks else None
-        total_ms = sum(sum(p.values()) for p in phases)
         if world > 1:
             t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total_ms = t.item()
+        # per-phase device times from a separately traced pass (event nodes between the phases)
+        phases = []
+        for k in range(5):
+            flush.fill_(float(k))
+            phases.append(L.lxw_profile_step(sol, Q, w["cfl"]))
         dof = sol.N * 4 * sol.ML
         mean_phase = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
         return dict(w=w, sol=sol, Q=Q, total_ms=total_ms, dof=dof, value=world * dof * args.steps / (total_ms / 1e3),
@@ -355,23 +410,34 @@ def main():
     fp64 = timed_form(False)
     plain_mx = timed_form(True)
     t_train = time.perf_counter()
-    net, train_info = train_indicator(L, stream)
+    net, train_info = train_indicator(L, stream, args.tau)
     t_train = time.perf_counter() - t_train
     mx = timed_form(True, ClockSampler(local), net=net)
     w, sol, dof = mx["w"], mx["sol"], mx["dof"]
     # one more (untimed) step with diagnostics: how often the FP64 paths ran and the gate skipped
     dmx = L.lxw_step(sol, mx["Q"], 0.0, w["cfl"], diag=True)
+    L.lxw_step(fp64["sol"], fp64["Q"], 0.0, w["cfl"])
+    L.lxw_step(plain_mx["sol"], plain_mx["Q"], 0.0, w["cfl"])
 
-    # accuracy of the mixed form: relative L1 distance of the density after the same steps
-    Qm = L.to_q64(sol, mx["Q"])
-    rho_m, rho_f = Qm[:, 0, 0], fp64["Q"][:, 0, 0]
-    l1_rel = (torch.abs(rho_m - rho_f).sum() / torch.abs(rho_f).sum()).item()
+    # distance of the mixed forms from the FP64 form after the same steps (density, relative L1)
+    rho_f = fp64["Q"][:, 0, 0]
+    def l1_rel(form):
+        r = L.to_q64(form["sol"], form["Q"])[:, 0, 0]
+        return (torch.abs(r - rho_f).sum() / torch.abs(rho_f).sum()).item()
+    dist_learned, dist_plain_mx = l1_rel(mx), l1_rel(plain_mx)
+    # "at equal L1 error": the three forms against the exact smooth solution
+    acc = {"fp64": smooth_l1_error(L, stream, False), "mixed": smooth_l1_error(L, stream, True),
+           "mixed_learned": smooth_l1_error(L, stream, True, net=net, tau=args.tau)}
+    acc["ratio_l1_mixed_learned_vs_fp64"] = acc["mixed_learned"]["l1"] / acc["fp64"]["l1"]
+    acc["ratio_l2_mixed_learned_vs_fp64"] = acc["mixed_learned"]["l2"] / acc["fp64"]["l2"]
+    acc["config"] = (WORKLOADS["smooth"]["desc"] + ", CFL 0.1, to t = 0.1; l1: cell-average density, "
+                     "l2: DG density (all modes) against the projected exact solution")
 
     flops = ck_flops_per_element(w["kind"], w["deg"]) * sol.N
     ck_ms = mx["phases"]["ck"]
     achieved = flops / (ck_ms / 1e3) / 1e12
     dom = max(mx["phases"], key=mx["phases"].get)
-    roofline = {"kernel": "k_ck_mx", "dominant_kernel": dom, "bound": "alu", "pipe": "fp32",
+    roofline = {"kernel": "k_ck_mx", "dominant_phase": dom, "bound": "alu", "pipe": "fp32",
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": CK_MX_TRAFFIC_BYTES,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
@@ -387,6 +453,7 @@ def main():
 
     # end to end through the public C ABI on HOST memory: H2D of the state,
     # one step, D2H of the result, every step
+    Qm = L.to_q64(sol, mx["Q"])
     Qh = torch.empty(sol.q64_shape, dtype=torch.float64).pin_memory()
     Qh.copy_(Qm.cpu())
     L.lxw_run_host(sol, Qh, 1, w["cfl"])
@@ -409,8 +476,9 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": w["desc"], "elements": sol.N, "degree": w["deg"], "dof_per_step": dof,
                       "form": "mixed + learned: FP32 bulk, FP64 averages/update/limiter solves, "
-                              "MLP-gated shock limiter (BF16 weights, plain limiter fallback)",
+                              f"MLP-gated shock limiter (BF16 tensor-core inference, tau {args.tau})",
                       "cfl": w["cfl"], "l2": "flushed between timed steps (256 MB write)",
+                      "timing": "one CUDA-graph replay per step, CUDA events on the solver's stream",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "roofline": roofline,
            "e2e": e2e,
@@ -420,13 +488,14 @@ def main():
            "plain_fp64": plain,
            "speedup_vs_plain_fp64": mx["value"] / fp64["value"],
            "plain_mixed": {"value": plain_mx["value"], "ms_per_step": plain_mx["total_ms"] / args.steps,
-                           "phases_ms": plain_mx["phases"]},
-           "learned_indicator": dict(train_info, train_s=t_train, tau=0.02,
+                           "phases_ms": plain_mx["phases"], "l1_rel_density_vs_fp64": dist_plain_mx},
+           "learned_indicator": dict(train_info, train_s=t_train, tau=args.tau,
                                      skipped_cells_last_step=dmx["n_mlp_skip"], of=sol.N,
                                      gain_vs_plain_mixed=mx["value"] / plain_mx["value"]),
            "mixed_fp64_path_cells": {"moment": dmx["n_fp64_moment"], "flux_limiter": dmx["n_fp64_edge"],
                                      "of": sol.N},
-           "l1_rel_density_mixed_vs_fp64": l1_rel}
+           "l1_rel_density_vs_fp64": dist_learned,
+           "smooth_l1_error": acc}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], _, _ = cpu_baseline(args.workload)
     print(json.dumps(out))

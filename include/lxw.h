@@ -202,12 +202,16 @@ lxw_status lxw_shock_limit(lxw_solver* s, double* Q_dev, double* theta_dev);
 
 /* Number of kernel launches one lxw_step enqueues (diag_host NULL). */
 int lxw_step_launches(const lxw_solver* s);
+/* Number of intervals lxw_profile_step times: FP64 form one per kernel
+ * (reset, moment, ck, edge, update[, shock]); mixed form 5 (moment with the
+ * time-step kernel, ck, edge, update, shock with the learned gate). */
+int lxw_profile_phases(const lxw_solver* s);
 
 /* lxw_step (dt from cfl, no diagnostics) replayed from a CUDA graph with an
  * event node around each kernel (captured on first use, rebuilt when Q_dev
  * or cfl change), on the solver's stream; synchronises and writes the device
- * duration in milliseconds of each launch to ms_host[lxw_step_launches(s)]
- * in launch order (reset, moment, ck, edge, update[, shock]).  Tracing aid:
+ * duration in milliseconds of each interval to ms_host[lxw_profile_phases(s)]
+ * in launch order.  Tracing aid:
  * the events are created with the solver. */
 lxw_status lxw_profile_step(lxw_solver* s, double* Q_dev, double cfl, float* ms_host);
 

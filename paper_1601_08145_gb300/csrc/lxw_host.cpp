@@ -491,6 +491,7 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     s->dwm.prop = reinterpret_cast<float*>(s->dw.prop);
     s->dwm.avg_new = (double*)dalloc(sizeof(double) * 4 * (size_t)N);
     s->dwm.avgn32 = (float*)dalloc(sizeof(float) * 4 * (size_t)N);
+    s->dwm.gskip = (unsigned char*)dalloc((size_t)N);
     s->dwm.scal = (ScalMx*)dalloc(sizeof(ScalMx) * nprob);
     s->dwm.smax = s->dw.smax; s->dwm.status = s->dw.status; s->dwm.diag = s->dw.diag;
     s->Sdev = (double*)dalloc(lxw_state_bytes(s));
@@ -499,7 +500,7 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     float* s32 = (float*)dalloc(sizeof(float) * (size_t)N);
     float* ia32 = (float*)dalloc(sizeof(float) * (size_t)N);
     double* ia64 = (double*)dalloc(sizeof(double) * (size_t)N);
-    if (!s->dwm.avg_new || !s->dwm.avgn32 || !s->dwm.scal || !s->Sdev || !j32 || !n32 || !s32 || !ia32 || !ia64) {
+    if (!s->dwm.avg_new || !s->dwm.avgn32 || !s->dwm.gskip || !s->dwm.scal || !s->Sdev || !j32 || !n32 || !s32 || !ia32 || !ia64) {
       delete s;
       return fail(LXW_ERR_NOMEM, "lxw_solver_create: device allocation failed");
     }
@@ -518,7 +519,9 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     s->dm.jinv32 = j32; s->dm.nrm32 = n32; s->dm.sdx32 = s32; s->dm.inva32 = ia32; s->dm.inva = ia64;
   }
   if (!d_area || !d_jinv || !d_nrm || !d_sdx || !d_nbr || !d_nbk || !s->dw.trace || !s->dw.flux || !s->dw.prop ||
-      !s->dw.smax || !s->dw.status || !s->dw.diag || !s->Qdev) {
+      !s->dw.smax || !s->dw.status || !s->dw.diag || !s->Qdev ||
+      cudaMemset(s->dw.smax, 0, sizeof(unsigned long long) * nprob) != cudaSuccess ||
+      cudaMemset(s->dw.status, 0, sizeof(unsigned int)) != cudaSuccess) {
     delete s;
     return fail(LXW_ERR_NOMEM, "lxw_solver_create: device allocation failed");
   }
@@ -692,6 +695,7 @@ static lxw_status read_diag(lxw_solver* s, double dt, double cfl, lxw_diag* d) {
   d->min_rho = v[4]; d->min_p = v[5];
   d->n_mom = v[6]; d->n_edge = v[7]; d->n_sc = v[8];
   d->status = (int)st;
+  if (st) LXW_CUDA(cudaMemsetAsync(s->dw.status, 0, sizeof(unsigned int), s->stream));   // reported: clear
   const DiagBlock* blk = reinterpret_cast<const DiagBlock*>(h);
   d->n_fp64_moment = (double)blk->fb_mom;
   d->n_fp64_edge = (double)blk->fb_edge;
@@ -803,8 +807,15 @@ lxw_status lxw_shock_limit(lxw_solver* s, double* Q, double* theta) {
 }
 
 // the mixed form always launches its shock kernel (it also commits the new averages)
-static int launches_of(const lxw_solver* s) { return s->mixed ? 6 : step_launch_count(0, s->opt.shock_limiter); }
-int lxw_step_launches(const lxw_solver* s) { return s ? launches_of(s) : 0; }
+// timed intervals of lxw_profile_step: mixed form moment(+scalars), ck, edge,
+// update, shock(+gate); FP64 form one per kernel
+static int phases_of(const lxw_solver* s) { return s->mixed ? 5 : step_launch_count(0, s->opt.shock_limiter); }
+int lxw_profile_phases(const lxw_solver* s) { return s ? phases_of(s) : 0; }
+int lxw_step_launches(const lxw_solver* s) {
+  if (!s) return 0;
+  if (!s->mixed) return step_launch_count(0, s->opt.shock_limiter);
+  return 6 + (s->mlp_w && s->opt.shock_limiter ? 1 : 0);   // moment, scalars, ck, edge, update, [gate,] shock
+}
 
 lxw_status lxw_batch_scalars(lxw_solver* s, int* nprob, double* s_host, double* dt_host) {
   if (!s) return fail(LXW_ERR_ARG, "lxw_batch_scalars: null solver");
@@ -905,7 +916,7 @@ lxw_status lxw_autotune(lxw_solver* s, void* state, double cfl, int reps, int* b
       float tot = 0.0f;
       for (int r = 0; r < reps; ++r) {
         if ((st = lxw_profile_step(s, (double*)state, cfl, ms)) != LXW_OK) break;
-        for (int k = 0; k < launches_of(s); ++k) tot += ms[k];
+        for (int k = 0; k < phases_of(s); ++k) tot += ms[k];
       }
       if (st != LXW_OK) break;
       if (tot / reps < best) { best = tot / reps; bb = b; bc = c; }
@@ -968,7 +979,14 @@ lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* out, size_t coun
   if (which == 0) { src = s->dw.trace; n = E * MQ * 8 * N; }
   else if (which == 1) { src = s->dw.flux; n = E * 8 * N; }
   else if (which == 2) { src = s->dw.prop; n = E * N; }
-  else if (which == 3) {
+  else if (which == 3 && s->mixed) {
+    if (count < 2) return fail(LXW_ERR_ARG, "lxw_workspace_copy: buffer too small");
+    ScalMx sc;
+    LXW_CUDA(cudaMemcpyAsync(&sc, s->dwm.scal, sizeof(sc), cudaMemcpyDeviceToHost, s->stream));
+    LXW_CUDA(cudaStreamSynchronize(s->stream));
+    out[0] = sc.s; out[1] = sc.dt;
+    return LXW_OK;
+  } else if (which == 3) {
     if (count < 2) return fail(LXW_ERR_ARG, "lxw_workspace_copy: buffer too small");
     unsigned long long b = 0;
     LXW_CUDA(cudaMemcpyAsync(&b, s->dw.smax, sizeof(b), cudaMemcpyDeviceToHost, s->stream));
@@ -1003,7 +1021,7 @@ lxw_status lxw_profile_step(lxw_solver* s, double* Q, double cfl, float* ms) {
     s->pgraph_Q = Q; s->pgraph_cfl = cfl;
   }
   LXW_CUDA(cudaGraphLaunch(s->pgraph, s->stream));
-  const int n = launches_of(s);
+  const int n = phases_of(s);
   LXW_CUDA(cudaEventSynchronize((cudaEvent_t)s->events[n]));
   for (int k = 0; k < n; ++k) LXW_CUDA(cudaEventElapsedTime(&ms[k], (cudaEvent_t)s->events[k], (cudaEvent_t)s->events[k + 1]));
   return LXW_OK;

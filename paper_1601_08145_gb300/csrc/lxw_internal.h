@@ -82,6 +82,7 @@ struct DevWorkMx {
   float* prop;            // [E][N]: Lambda proposals, rounded down to FP32
   double* avg_new;        // [4][N]: updated averages before the shock limiter commits them
   float* avgn32;          // [4][N]: FP32 copy of avg_new
+  unsigned char* gskip;   // [N]: 1 where the learned gate lets the shock limiter skip the cell
   ScalMx* scal;           // [nprob]
   unsigned long long* smax;  // [nprob]
   unsigned int* status;

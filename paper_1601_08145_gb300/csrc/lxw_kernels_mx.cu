@@ -135,6 +135,7 @@ __global__ void k_scalars(const DevMesh m, const DevWorkMx w, const StepArgs a) 
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= m.nprob) return;
   const double s = __longlong_as_double((long long)w.smax[p]);
+  w.smax[p] = 0ull;                       // ready for the next step's maximum
   const double dt = a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin_p[p] / s;
   ScalMx sc;
   sc.s = s; sc.dt = dt;
@@ -161,10 +162,14 @@ __device__ __forceinline__ float& hi_at(const MxState& st, int N, int v, int l, 
   return st.hi[((size_t)v * (ML - 1) + (l - 1)) * N + i];
 }
 
-__global__ void k_reset_mx(DevWorkMx w, int nprob, int want_diag) {
+// Zeroes the per-step diagnostics (and the status word when clear_status).
+// Steps without diagnostics launch no reset: k_scalars zeroes each problem's
+// speed maximum once it has read it, and the status word is sticky until the
+// host reads it.
+__global__ void k_reset_mx(DevWorkMx w, int nprob, int want_diag, int clear_status) {
   for (int p = threadIdx.x; p < nprob; p += blockDim.x) w.smax[p] = 0ull;
   if (threadIdx.x != 0) return;
-  *w.status = 0u;
+  if (clear_status) *w.status = 0u;
   if (want_diag) {
     DiagBlock* d = reinterpret_cast<DiagBlock*>(w.diag);
     for (int c = 0; c < 4; ++c) d->sum[c] = 0.0;
@@ -933,9 +938,10 @@ __device__ __forceinline__ void cell_features(const float c[4][ML], const float 
 // of the first product is, element for element, the A fragment of the
 // second), then theta_hat = sigmoid(H2 w3 + b3) on the CUDA cores.
 constexpr int KP1 = kGateK1;
+constexpr int kGateWarps = 8;       // k_gate_mx runs 256-thread CTAs
 struct GateSmem {
   GateWeights w;
-  unsigned short feat[4][32][KP1];   // features of 4 warps (128 threads) x 32 cells, BF16
+  unsigned short feat[kGateWarps][32][KP1];   // features of 8 warps x 32 cells, BF16
 };
 
 __device__ __forceinline__ unsigned short f2bf(float x) {
@@ -1086,7 +1092,9 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
   float an32[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) an32[v] = w.avgn32[(size_t)v * N + i];
-  if (limit) {
+  if (limit && skip) {
+    if (theta_out) theta_out[i] = 1.0;
+  } else if (limit) {
     const float g1 = a.gamma_f - 1.0f;
     float c[4][ML];
 #pragma unroll
@@ -1125,9 +1133,7 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
 #pragma unroll
         for (int v = 0; v < 4; ++v) { Mx[v] = fmaxf(Mx[v], wn[v]); Mn[v] = fminf(Mn[v], wn[v]); }
       }
-      if (skip) {
-        if (a.want_diag) atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->mlp_skip, 1ull);
-      } else {
+      {
         float hx[4], hn[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) { hx[v] = -3e38f; hn[v] = 3e38f; }
@@ -1178,43 +1184,62 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
   }
 }
 
-template <int KD, int E, int ML, int NQ, int MQ, bool GATE>
-__global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
-                                                  const StepArgs a, double* __restrict__ theta_out, int limit) {
+// The learned gate (features + network), one warp per 32 consecutive cells,
+// flat over the mesh; every CTA stages the weights once.  Writes the skip
+// byte of each cell (theta_hat >= 1 - tau and positive averages), and on
+// request theta_hat and the features.  Without a network it only writes the
+// features (training pairs).
+template <int E, int ML>
+__global__ void __launch_bounds__(32 * kGateWarps) k_gate_mx(const DevMesh m, const DevWorkMx w,
+                                                             const double* __restrict__ state, const StepArgs a) {
   extern __shared__ __align__(16) unsigned char gate_raw[];
   GateSmem& g = *reinterpret_cast<GateSmem*>(gate_raw);
-  const bool net = GATE && a.gate_w != nullptr && limit;
+  const bool net = a.gate_w != nullptr;
   if (net) {
     stage_gate(g, a.gate_w);
     __syncthreads();
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int N = m.N, nwarps = (N + 31) >> 5;
+  unsigned long long skipped = 0;
+  for (int wi = blockIdx.x * kGateWarps + warp; wi < nwarps; wi += gridDim.x * kGateWarps) {
+    const int i = wi * 32 + lane;
+    float f[kMlpIn];
+    const bool ok = i < N && gate_features<E, ML>(m, w, state, a, i, f);
+    if (ok && a.feat_out) {
+#pragma unroll
+      for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
+    }
+    if (net) {
+      unsigned* row = reinterpret_cast<unsigned*>(&g.feat[warp][lane][0]);
+#pragma unroll
+      for (int k = 0; k < kMlpIn / 2; ++k) row[k] = ok ? pack2(f2bf(f[2 * k]), f2bf(f[2 * k + 1])) : 0u;
+#pragma unroll
+      for (int k = kMlpIn / 2; k < 16; ++k) row[k] = 0u;
+      __syncwarp();
+      const float th_hat = gate_mma(g, warp);
+      __syncwarp();
+      const bool sk = ok && th_hat >= 1.0f - a.mlp_tau;
+      if (i < N) {
+        w.gskip[i] = sk ? 1 : 0;
+        if (ok && a.gate_out) a.gate_out[i] = th_hat;
+      }
+      skipped += __popc(__ballot_sync(0xffffffffu, sk));
+    }
+  }
+  if (a.want_diag && lane == 0 && skipped) atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->mlp_skip, skipped);
+}
+
+template <int KD, int E, int ML, int NQ, int MQ>
+__global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+                                                  const StepArgs a, double* __restrict__ theta_out, int limit) {
+  const bool gated = a.gate_w != nullptr;
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
-    const bool active = (int)threadIdx.x < tile.y;
-    const int i = tile.x + threadIdx.x;
-    bool skip = false;
-    if (GATE && limit) {
-      float f[kMlpIn];
-      const bool ok = active && gate_features<E, ML>(m, w, state, a, i, f);
-      if (ok && a.feat_out) {
-#pragma unroll
-        for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
-      }
-      if (net) {
-        unsigned* row = reinterpret_cast<unsigned*>(&g.feat[warp][lane][0]);
-#pragma unroll
-        for (int k = 0; k < kMlpIn / 2; ++k) row[k] = ok ? pack2(f2bf(f[2 * k]), f2bf(f[2 * k + 1])) : 0u;
-#pragma unroll
-        for (int k = kMlpIn / 2; k < 16; ++k) row[k] = 0u;
-        __syncwarp();
-        const float th_hat = gate_mma(g, warp);
-        __syncwarp();
-        if (ok && a.gate_out) a.gate_out[i] = th_hat;
-        skip = ok && th_hat >= 1.0f - a.mlp_tau;
-      }
+    if ((int)threadIdx.x < tile.y) {
+      const int i = tile.x + threadIdx.x;
+      shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, limit, i, gated && w.gskip[i] != 0);
     }
-    if (active) shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, limit, i, skip);
   }
 }
 
@@ -1273,8 +1298,7 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
   auto mark = [&]() { if (events) cudaEventRecordWithFlags((cudaEvent_t)events[ne++], st, cudaEventRecordExternal); };
   auto ok = [&]() { return cudaGetLastError() == cudaSuccess ? 0 : -1; };
   mark();
-  k_reset_mx<<<1, 256, 0, st>>>(w, m.nprob, 1);
-  mark();
+  if (a.want_diag) k_reset_mx<<<1, 256, 0, st>>>(w, m.nprob, 1, 0);
   k_moment_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, a.theta_cell);
   k_scalars<<<gridn(m.nprob, 128), 128, 0, st>>>(m, w, a);
   mark();
@@ -1290,16 +1314,16 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
   const int limit = a.shock_limiter && upto >= 5;
   double* tsc = a.theta_cell ? a.theta_cell + m.N : nullptr;
   if (limit && (a.gate_w || a.feat_out)) {
-    // persistent CTAs (every CTA stages the weights once): as many as fit on the device
+    // persistent CTAs (each stages the weights once): as many as fit on the device
     static int per_sm = 0;
-    if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shock_mx<KD, E, ML, NQ, MQ, true>, block,
+    if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_mx<E, ML>, 32 * kGateWarps,
                                                                  sizeof(GateSmem)) != cudaSuccess)
       per_sm = 1;
-    const int gg = a.gate_w ? std::min(m.ntiles, std::max(per_sm, 1) * std::max(a.sms, 1)) : grid;
-    k_shock_mx<KD, E, ML, NQ, MQ, true><<<gg, block, a.gate_w ? sizeof(GateSmem) : 0, st>>>(m, w, state, a, tsc, limit);
+    const int nw = (m.N + 31) / 32;
+    const int gg = std::max(1, std::min((nw + kGateWarps - 1) / kGateWarps, std::max(per_sm, 1) * std::max(a.sms, 1)));
+    k_gate_mx<E, ML><<<gg, 32 * kGateWarps, a.gate_w ? sizeof(GateSmem) : 0, st>>>(m, w, state, a);
   }
-  else
-    k_shock_mx<KD, E, ML, NQ, MQ, false><<<grid, block, 0, st>>>(m, w, state, a, tsc, limit);
+  k_shock_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, tsc, limit);
   mark();
   if (a.want_diag) k_diag_mx<ML><<<gridn(m.N, 256), 256, 0, st>>>(m, w, state, a.gamma);
   return ok();
@@ -1309,7 +1333,7 @@ template <int KD, int E, int ML, int NQ, int MQ>
 int moment_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const StepArgs& a, double* theta,
                    cudaStream_t st, int block) {
   const int grid = a.grid > 0 && a.grid < m.ntiles ? a.grid : m.ntiles;
-  k_reset_mx<<<1, 256, 0, st>>>(w, m.nprob, 1);
+  k_reset_mx<<<1, 256, 0, st>>>(w, m.nprob, 1, 1);
   k_moment_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, theta);
   k_scalars<<<gridn(m.nprob, 128), 128, 0, st>>>(m, w, a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

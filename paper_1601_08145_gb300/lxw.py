@@ -32,7 +32,7 @@ EXPORTS = [
     "lxw_batch_create", "lxw_batch_scalars", "lxw_autotune",
     "lxw_mlp_create", "lxw_mlp_destroy", "lxw_mlp_num_params", "lxw_mlp_get_params", "lxw_mlp_set_params",
     "lxw_mlp_forward", "lxw_mlp_loss_grad", "lxw_mlp_train", "lxw_solver_set_mlp", "lxw_step_dump",
-    "lxw_step_gate",
+    "lxw_step_gate", "lxw_profile_phases",
 ]
 
 
@@ -93,6 +93,7 @@ def lib():
     L.lxw_moment_limit.argtypes = [_vp, _vp, _vp, _vp]
     L.lxw_shock_limit.argtypes = [_vp, _vp, _vp]
     L.lxw_step_launches.argtypes = [_vp]
+    L.lxw_profile_phases.argtypes = [_vp]
     L.lxw_profile_step.argtypes = [_vp, _vp, C.c_double, C.POINTER(C.c_float)]
     L.lxw_step_phases.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int]
     L.lxw_workspace_copy.argtypes = [_vp, C.c_int, _dp, C.c_size_t]
@@ -309,14 +310,20 @@ def lxw_step_launches(solver):
 
 
 PHASES = ["reset", "moment", "ck", "edge", "update", "shock"]
+PHASES_MIXED = ["moment", "ck", "edge", "update", "shock"]
+
+
+def lxw_profile_phases(solver):
+    return lib().lxw_profile_phases(solver.h)
 
 
 def lxw_profile_step(solver, Q, cfl):
-    """One step with per-launch CUDA-event timing; returns {phase: ms}."""
-    n = lxw_step_launches(solver)
+    """One step with CUDA-event timing of each phase; returns {phase: ms}."""
+    n = lxw_profile_phases(solver)
     ms = (C.c_float * n)()
     _check(lib().lxw_profile_step(solver.h, _ptr(Q, solver.state_shape, "Q"), cfl, ms))
-    return {PHASES[k]: float(ms[k]) for k in range(n)}
+    names = PHASES_MIXED if solver.mixed else PHASES
+    return {names[k]: float(ms[k]) for k in range(n)}
 
 
 def lxw_step_phases(solver, Q, dt, cfl, nphases):

@@ -162,3 +162,19 @@ def test_mixed_run_graph_and_host_path(L):
     H = Q.cpu().numpy().copy()
     L.lxw_run_host(s, H, 5, 0.1)
     assert np.array_equal(H, L.to_q64(s, A).cpu().numpy())
+
+
+def test_status_is_kept_until_a_diagnostic_step_reads_it(L):
+    """Steps without diagnostics launch no reset: a non-positive average met
+    by such a step is reported by the next step that asks for diagnostics,
+    and cleared once reported."""
+    s = solver(L, QUAD, 2, 12)
+    Qb = synth.random_modal_state(s.N, s.ML, seed=4, amp=0.05)
+    Qb[5, 0, 0] = -1.0
+    L.lxw_step(s, L.new_state(s, torch.from_numpy(Qb).cuda()), 0.0, 0.1)      # no diagnostics
+    good = L.new_state(s, torch.from_numpy(synth.random_modal_state(s.N, s.ML, seed=5, amp=0.05)).cuda())
+    d = L.lxw_step(s, good, 0.0, 0.1, diag=True)
+    assert d["status"] & L.ST_NONPOSITIVE and d["return_status"] == L.ERR_NONPOSITIVE
+    d = L.lxw_step(s, good, 0.0, 0.1, diag=True)
+    assert d["status"] == 0 and d["return_status"] == L.OK
+    assert L.lxw_step_launches(s) == 6 and L.lxw_profile_phases(s) == 5
