@@ -38,7 +38,7 @@ typedef enum {
   LXW_ERR_CFL = 4,          /* Gamma^rho < 0: dt above the low-order CFL bound      */
   LXW_ERR_NAN = 5,          /* a non-finite value appeared in the state            */
   LXW_ERR_BOUNDS = 6,       /* mesh connectivity out of range                      */
-  LXW_ERR_TIMEOUT = 7,      /* reserved: a bounded device wait gave up             */
+  LXW_ERR_TIMEOUT = 7,      /* a bounded device wait (tensor-core gate) gave up    */
   LXW_ERR_NOMEM = 8         /* device or host allocation failed                    */
 } lxw_status;
 
@@ -54,7 +54,7 @@ enum { LXW_KIND_QUAD = 0, LXW_KIND_TRI = 1 };
 enum { LXW_PREC_FP64 = 0, LXW_PREC_MIXED = 1 };
 
 /* device status bits (returned in lxw_diag.status) */
-enum { LXW_ST_NONPOSITIVE = 1, LXW_ST_CFL = 2, LXW_ST_NAN = 4 };
+enum { LXW_ST_NONPOSITIVE = 1, LXW_ST_CFL = 2, LXW_ST_NAN = 4, LXW_ST_TIMEOUT = 8 };
 
 typedef struct lxw_mesh lxw_mesh;
 typedef struct lxw_solver lxw_solver;

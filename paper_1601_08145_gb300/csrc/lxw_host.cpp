@@ -269,6 +269,7 @@ struct lxw_solver {
   int4* d_tiles = nullptr;       // work list (owned through allocs)
   GateWeights* gate_buf = nullptr;  // gate weights (owned), allocated by the first lxw_solver_set_mlp
   const GateWeights* mlp_w = nullptr;  // gate_buf while a network is attached, else null
+  int gate_per_sm = 1;                 // resident gate CTAs per SM (queried when the first network is attached)
   float mlp_tau = 0.0f;
   int tiles_cap = 0;
   int sms = 0;
@@ -659,6 +660,7 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   a.gamma_f = (float)a.gamma; a.eps0_f = (float)a.eps0; a.alpha0_f = (float)a.alpha0;
   a.grid = s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm * s->sms : 0;   // persistent CTAs, or one per tile
   a.sms = s->sms;
+  a.gate_per_sm = s->gate_per_sm;
   a.gate_w = s->mlp_w; a.mlp_tau = s->mlp_tau; a.feat_out = nullptr; a.gate_out = nullptr;
   return a;
 }
@@ -703,6 +705,7 @@ static lxw_status read_diag(lxw_solver* s, double dt, double cfl, lxw_diag* d) {
   if (st & LXW_ST_NONPOSITIVE) return fail(LXW_ERR_NONPOSITIVE, "lxw_step: non-positive cell average at step start");
   if (st & LXW_ST_CFL) return fail(LXW_ERR_CFL, "lxw_step: Gamma^rho < 0 (dt above the low-order CFL bound)");
   if (st & LXW_ST_NAN) return fail(LXW_ERR_NAN, "lxw_step: non-finite state");
+  if (st & LXW_ST_TIMEOUT) return fail(LXW_ERR_TIMEOUT, "lxw_step: a device wait of the learned gate gave up");
   return LXW_OK;
 }
 
@@ -846,6 +849,9 @@ lxw_status lxw_solver_set_mlp(lxw_solver* s, lxw_mlp* mlp, float tau) {
     s->gate_buf = (GateWeights*)p;
   }
   if (mlp_gate_weights(mlp, s->gate_buf)) return fail(LXW_ERR_CUDA, "lxw_solver_set_mlp: weight layout failed");
+  const int occ = gate_occupancy(s->kind, s->deg);
+  if (occ < 1) return fail(LXW_ERR_CUDA, "lxw_solver_set_mlp: the gate kernel does not fit on this device");
+  s->gate_per_sm = occ;
   s->mlp_w = s->gate_buf;
   s->mlp_tau = tau;
   return LXW_OK;

@@ -105,15 +105,19 @@ constexpr int kMlpIn = 24, kMlpH = 64;
 constexpr int kW1 = 0, kB1 = kW1 + kMlpIn * kMlpH, kW2 = kB1 + kMlpH, kB2 = kW2 + kMlpH * kMlpH,
               kW3 = kB2 + kMlpH, kB3 = kW3 + kMlpH, kMlpParams = kB3 + 1;
 
-// The gate's weights in the shock kernel's shared-memory layout: BF16 W1 and
-// W2 stored output-major (row n holds the weights into hidden unit n), so
-// that an mma.sync B fragment is one 32-bit load; rows padded (24 -> 40,
-// 64 -> 72 halves) so the 8 rows a fragment touches fall in distinct banks.
-// Biases, output weights and output bias are the BF16 values widened to FP32.
-constexpr int kGateK1 = 40, kGateK2 = 72;
+// The gate's weights as the shared-memory image the gate kernel's tensor-core
+// products read: W1^T [64 x 32] (24 inputs, zero padded) and W2^T [64 x 64]
+// in BF16, each in the K-major, unswizzled core-matrix layout of tcgen05
+// operands (8 rows x 16 bytes per core matrix, core matrices along K 128 B
+// apart, 8-row groups K/8 x 128 B apart); biases, output weights and output
+// bias are the BF16 values widened to FP32.
+constexpr int kGateK1 = 32;
+__host__ __device__ constexpr int umma_kmajor(int r, int k, int K) {
+  return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
 struct GateWeights {
-  unsigned short w1t[kMlpH][kGateK1];
-  unsigned short w2t[kMlpH][kGateK2];
+  unsigned short w1[kMlpH * kGateK1];
+  unsigned short w2[kMlpH * kMlpH];
   float b1[kMlpH], b2[kMlpH], w3[kMlpH], b3, pad[3];
 };
 static_assert(sizeof(GateWeights) % 16 == 0, "GateWeights is copied in 16-byte words");
@@ -122,7 +126,8 @@ struct StepArgs {
   int grid;                          // mixed form: persistent CTAs (0 = one per tile)
   double dt_in, cfl, gamma, eps0, alpha0;
   float gamma_f, eps0_f, alpha0_f;   // FP32 copies for the mixed form
-  int sms;                           // SMs of the device (persistent grid of the gated shock kernel)
+  int sms;                           // SMs of the device
+  int gate_per_sm;                   // resident gate CTAs per SM (persistent grid of k_gate_mx)
   const GateWeights* gate_w;         // learned gate weights or null
   float mlp_tau;                     // gate: skip the limiter where theta_hat >= 1 - tau
   float* feat_out;                   // [N][24] features at the shock limiter's input, or null
@@ -170,6 +175,8 @@ struct DerivTables {
 };
 void make_deriv_tables(const Tables& t, DerivTables& d);
 int upload_tables_mx(int kind, int deg, const Tables& t);
+// resident CTAs per SM of the gate kernel for (kind, deg), capped by TMEM; < 0 on error
+int gate_occupancy(int kind, int deg);
 int launch_step_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state,
                    const StepArgs& a, void* stream, int block, void** events = nullptr, int upto = 99);
 int launch_moment_limit_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state,

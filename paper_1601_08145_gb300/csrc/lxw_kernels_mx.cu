@@ -22,6 +22,7 @@
 // screen sends a cell to its FP64 path.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -931,18 +932,33 @@ __device__ __forceinline__ void cell_features(const float c[4][ML], const float 
   for (int k = 0; k < kMlpIn; ++k) f[k] = fminf(8.0f, fmaxf(-8.0f, f[k]));
 }
 
-// ---- tensor-core inference of the gate (BF16 mma.sync m16n8k16, FP32 accumulate)
-// One warp evaluates the network for its 32 cells as two 16-row M tiles:
-// H1 = relu(X W1 + b1) with X [32 x 32] (24 features, zero padded), then
-// H2 = relu(H1 W2 + b2) with H1 rounded to BF16 (the accumulator fragment
-// of the first product is, element for element, the A fragment of the
-// second), then theta_hat = sigmoid(H2 w3 + b3) on the CUDA cores.
-constexpr int KP1 = kGateK1;
-constexpr int kGateWarps = 8;       // k_gate_mx runs 256-thread CTAs
-struct GateSmem {
-  GateWeights w;
-  unsigned short feat[kGateWarps][32][KP1];   // features of 8 warps x 32 cells, BF16
+// ---- tensor-core inference of the gate (tcgen05, BF16 operands, FP32 in TMEM)
+// A CTA of 128 threads evaluates the network for 128 cells at a time, one
+// cell per thread = one TMEM lane:
+//   H1 = relu(X W1 + b1):  X [128 x 32] (24 features, zero padded) in shared
+//        memory, W1^T [64 x 32]; D = 64 FP32 columns of TMEM
+//   H2 = relu(H1 W2 + b2): H1 rounded to BF16 into shared memory [128 x 64],
+//        W2^T [64 x 64]; D reuses the same 64 columns
+//   theta_hat = sigmoid(H2 . w3 + b3) on the CUDA cores, read back with tcgen05.ld.
+// One thread issues the MMAs and commits them to an mbarrier; every wait is
+// bounded (kGateWaitCycles), after which the CTA stops, flags LXW_ST_TIMEOUT,
+// waits once more for its own MMAs and copies and frees its TMEM.
+constexpr int kGateRows = 128;
+constexpr int kGateTmemCols = 64;
+constexpr long long kGateWaitCycles = 2000000000ll;   // ~1 s at 2 GHz
+struct GateTile {
+  GateWeights w;                                        // filled by one bulk async copy
+  alignas(128) unsigned short a1[kGateRows * kGateK1];  // features, core-matrix layout
+  alignas(128) unsigned short a2[kGateRows * kMlpH];    // hidden layer 1, core-matrix layout
+  alignas(8) unsigned long long wbar, mbar;
+  unsigned tmem;
 };
+static_assert(sizeof(GateWeights) % 16 == 0, "bulk copies move multiples of 16 bytes");
+// instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
+// bits 17-22, M >> 4 at bits 24-28
+constexpr unsigned kGateIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kMlpH >> 3) << 17) |
+                                ((unsigned)(kGateRows >> 4) << 24);
 
 __device__ __forceinline__ unsigned short f2bf(float x) {
   unsigned u = __float_as_uint(x);
@@ -950,100 +966,65 @@ __device__ __forceinline__ unsigned short f2bf(float x) {
   return (unsigned short)(u >> 16);
 }
 __device__ __forceinline__ unsigned pack2(unsigned short lo, unsigned short hi) { return (unsigned)lo | ((unsigned)hi << 16); }
-__device__ __forceinline__ unsigned ld2(const unsigned short* p) { return *reinterpret_cast<const unsigned*>(p); }
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void mma_bf16(float d[4], const unsigned a[4], const unsigned b[2]) {
+// shared-memory matrix descriptor: start address, leading (K) and stride (8-row)
+// byte offsets, each >> 4; bits 46-48 = 0b001; no swizzle, base offset 0
+__device__ __forceinline__ unsigned long long umma_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr >> 4) & 0x3fffu) | ((unsigned long long)((lbo >> 4) & 0x3fffu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void umma_bf16(unsigned tmem_d, unsigned long long ad, unsigned long long bd, unsigned acc) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(kGateIdesc), "r"(acc)
+      : "memory");
 }
-
-// copy the prepared GateWeights into the CTA's shared memory (16-byte words)
-__device__ __forceinline__ void stage_gate(GateSmem& g, const GateWeights* __restrict__ src) {
-  const uint4* s4 = reinterpret_cast<const uint4*>(src);
-  uint4* d4 = reinterpret_cast<uint4*>(&g.w);
-  constexpr int n4 = (int)(sizeof(GateWeights) / 16);
-  for (int k = threadIdx.x; k < n4; k += blockDim.x) d4[k] = __ldg(s4 + k);
+__device__ __forceinline__ void umma_commit(unsigned mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
-
-// theta_hat for the 32 cells of this warp, whose features are in g.feat[warp];
-// returns the value of the calling lane's cell.  All 32 lanes must call it.
-__device__ __forceinline__ float gate_mma(const GateSmem& g, int warp) {
-  const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
-  const GateWeights& W = g.w;
-  // layer 1: [32 x 32] x [32 x 64], each B fragment used by both M tiles
-  float d1[2][8][4];
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(phase)
+      : "memory");
+  return ok != 0u;
+}
+// true once the phase completed, false after kGateWaitCycles
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned phase) {
+  const long long t0 = clock64();
+  while (!mbar_try(a, phase))
+    if (clock64() - t0 > kGateWaitCycles) return false;
+  return true;
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane; the wait carries the
+// registers so that no use can be scheduled before it
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15])
+               :
+               : "memory");
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) d1[mt][nt][0] = d1[mt][nt][1] = d1[mt][nt][2] = d1[mt][nt][3] = 0.0f;
-#pragma unroll
-  for (int kt = 0; kt < 2; ++kt) {
-    const int c0 = kt * 16 + 2 * tq;
-    unsigned a[2][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const int r0 = mt * 16 + gq;
-      // A register order of m16n8k16: (row g, k 0-7), (row g+8, k 0-7), (row g, k 8-15), (row g+8, k 8-15)
-      a[mt][0] = ld2(&g.feat[warp][r0][c0]);     a[mt][1] = ld2(&g.feat[warp][r0 + 8][c0]);
-      a[mt][2] = ld2(&g.feat[warp][r0][c0 + 8]); a[mt][3] = ld2(&g.feat[warp][r0 + 8][c0 + 8]);
-    }
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const unsigned b[2] = {ld2(&W.w1t[nt * 8 + gq][c0]), ld2(&W.w1t[nt * 8 + gq][c0 + 8])};
-      mma_bf16(d1[0][nt], a[0], b);
-      mma_bf16(d1[1][nt], a[1], b);
-    }
-  }
-  // bias + ReLU, rounded to BF16 and repacked as the A fragments of layer 2
-  unsigned a2[2][4][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int col = nt * 8 + 2 * tq;
-    const float bb0 = W.b1[col], bb1 = W.b1[col + 1];
-    const int kt = nt >> 1, half = nt & 1;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      a2[mt][kt][half * 2 + 0] = pack2(f2bf(fmaxf(d1[mt][nt][0] + bb0, 0.0f)), f2bf(fmaxf(d1[mt][nt][1] + bb1, 0.0f)));
-      a2[mt][kt][half * 2 + 1] = pack2(f2bf(fmaxf(d1[mt][nt][2] + bb0, 0.0f)), f2bf(fmaxf(d1[mt][nt][3] + bb1, 0.0f)));
-    }
-  }
-  // layer 2: [32 x 64] x [64 x 64], then the output layer
-  float o[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    float d2[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
-#pragma unroll
-    for (int kt = 0; kt < 4; ++kt) {
-      const int c0 = kt * 16 + 2 * tq;
-      const unsigned b[2] = {ld2(&W.w2t[nt * 8 + gq][c0]), ld2(&W.w2t[nt * 8 + gq][c0 + 8])};
-      mma_bf16(d2[0], a2[0][kt], b);
-      mma_bf16(d2[1], a2[1][kt], b);
-    }
-    const int col = nt * 8 + 2 * tq;
-    const float bb0 = W.b2[col], bb1 = W.b2[col + 1], w0 = W.w3[col], w1 = W.w3[col + 1];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      o[mt][0] += fmaxf(d2[mt][0] + bb0, 0.0f) * w0 + fmaxf(d2[mt][1] + bb1, 0.0f) * w1;   // row g
-      o[mt][1] += fmaxf(d2[mt][2] + bb0, 0.0f) * w0 + fmaxf(d2[mt][3] + bb1, 0.0f) * w1;   // row g + 8
-    }
-  }
-  // sum over the 4 lanes of a group
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      o[mt][h] += __shfl_xor_sync(0xffffffffu, o[mt][h], 1);
-      o[mt][h] += __shfl_xor_sync(0xffffffffu, o[mt][h], 2);
-    }
-  // lane l owns cell row l: M tile l/16, row l%16, held by lanes 4*((l%16)%8) .. +3
-  const int rr = lane & 15, src = (rr & 7) * 4;
-  const float v00 = __shfl_sync(0xffffffffu, o[0][0], src), v01 = __shfl_sync(0xffffffffu, o[0][1], src);
-  const float v10 = __shfl_sync(0xffffffffu, o[1][0], src), v11 = __shfl_sync(0xffffffffu, o[1][1], src);
-  const float z = (lane < 16 ? (rr < 8 ? v00 : v01) : (rr < 8 ? v10 : v11)) + W.b3;
-  return 1.0f / (1.0f + __expf(-z));
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // the gate's features of element i at the shock limiter's input (false: no features, run the limiter)
@@ -1184,50 +1165,162 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
   }
 }
 
-// The learned gate (features + network), one warp per 32 consecutive cells,
-// flat over the mesh; every CTA stages the weights once.  Writes the skip
-// byte of each cell (theta_hat >= 1 - tau and positive averages), and on
-// request theta_hat and the features.  Without a network it only writes the
-// features (training pairs).
+// The learned gate (features + network) over the mesh in tiles of 128
+// consecutive cells, persistent CTAs.  Writes the skip byte of each cell
+// (theta_hat >= 1 - tau and positive averages), and on request theta_hat and
+// the features.  Without a network it only writes the features (training
+// pairs) and touches no tensor-core state.
 template <int E, int ML>
-__global__ void __launch_bounds__(32 * kGateWarps) k_gate_mx(const DevMesh m, const DevWorkMx w,
-                                                             const double* __restrict__ state, const StepArgs a) {
-  extern __shared__ __align__(16) unsigned char gate_raw[];
-  GateSmem& g = *reinterpret_cast<GateSmem*>(gate_raw);
-  const bool net = a.gate_w != nullptr;
-  if (net) {
-    stage_gate(g, a.gate_w);
-    __syncthreads();
+__global__ void __launch_bounds__(kGateRows) k_gate_mx(const DevMesh m, const DevWorkMx w,
+                                                       const double* __restrict__ state, const StepArgs a) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int N = m.N;
+  if (a.gate_w == nullptr) {
+    for (int i = blockIdx.x * blockDim.x + tid; i < N; i += gridDim.x * blockDim.x) {
+      float f[kMlpIn];
+      if (gate_features<E, ML>(m, w, state, a, i, f) && a.feat_out) {
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
+      }
+    }
+    return;
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int N = m.N, nwarps = (N + 31) >> 5;
+  extern __shared__ __align__(128) unsigned char gate_raw[];
+  GateTile& g = *reinterpret_cast<GateTile*>(gate_raw);
+  const unsigned wbar = smem_u32(&g.wbar), mbar = smem_u32(&g.mbar);
+  if (tid == 0) {
+    mbar_init(wbar, 1);
+    mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&g.tmem)),
+                 "r"(kGateTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = g.tmem;
+  if (tid == 0) {
+    constexpr unsigned bytes = (unsigned)sizeof(GateWeights);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(wbar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(&g.w)),
+                 "l"(a.gate_w), "r"(bytes), "r"(wbar)
+                 : "memory");
+  }
+  bool abort = __syncthreads_or(!mbar_wait(wbar, 0)) != 0;
+  bool wpending = abort;                   // the weight copy may still be in flight
+  bool mpending = false;                   // an MMA group committed but not seen complete
+  unsigned phase = 0;
+  const unsigned a1 = smem_u32(g.a1), a2 = smem_u32(g.a2), w1 = smem_u32(g.w.w1), w2 = smem_u32(g.w.w2);
+  const unsigned lane_tmem = tmem + ((unsigned)(warp * 32) << 16);
+  const int ntile = (N + kGateRows - 1) / kGateRows;
   unsigned long long skipped = 0;
-  for (int wi = blockIdx.x * kGateWarps + warp; wi < nwarps; wi += gridDim.x * kGateWarps) {
-    const int i = wi * 32 + lane;
+  for (int t = blockIdx.x; t < ntile && !abort; t += gridDim.x) {
+    const int i = t * kGateRows + tid;
     float f[kMlpIn];
     const bool ok = i < N && gate_features<E, ML>(m, w, state, a, i, f);
     if (ok && a.feat_out) {
 #pragma unroll
       for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
     }
-    if (net) {
-      unsigned* row = reinterpret_cast<unsigned*>(&g.feat[warp][lane][0]);
+    // this cell's features, BF16, as row tid of X (4 core matrices along K)
 #pragma unroll
-      for (int k = 0; k < kMlpIn / 2; ++k) row[k] = ok ? pack2(f2bf(f[2 * k]), f2bf(f[2 * k + 1])) : 0u;
-#pragma unroll
-      for (int k = kMlpIn / 2; k < 16; ++k) row[k] = 0u;
-      __syncwarp();
-      const float th_hat = gate_mma(g, warp);
-      __syncwarp();
-      const bool sk = ok && th_hat >= 1.0f - a.mlp_tau;
-      if (i < N) {
-        w.gskip[i] = sk ? 1 : 0;
-        if (ok && a.gate_out) a.gate_out[i] = th_hat;
+    for (int kb = 0; kb < kGateK1 / 8; ++kb) {
+      uint4 q = make_uint4(0u, 0u, 0u, 0u);
+      if (ok && kb * 8 < kMlpIn) {
+        q.x = pack2(f2bf(f[kb * 8 + 0]), f2bf(f[kb * 8 + 1]));
+        q.y = pack2(f2bf(f[kb * 8 + 2]), f2bf(f[kb * 8 + 3]));
+        q.z = pack2(f2bf(f[kb * 8 + 4]), f2bf(f[kb * 8 + 5]));
+        q.w = pack2(f2bf(f[kb * 8 + 6]), f2bf(f[kb * 8 + 7]));
       }
-      skipped += __popc(__ballot_sync(0xffffffffu, sk));
+      *reinterpret_cast<uint4*>(&g.a1[umma_kmajor(tid, kb * 8, kGateK1)]) = q;
     }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int s = 0; s < kGateK1 / 16; ++s)
+        umma_bf16(tmem, umma_desc(a1 + 256u * s, 128u, 128u * (kGateK1 / 8)),
+                  umma_desc(w1 + 256u * s, 128u, 128u * (kGateK1 / 8)), s > 0);
+      umma_commit(mbar);
+    }
+    mpending = true;
+    abort = __syncthreads_or(!mbar_wait(mbar, phase)) != 0;
+    if (abort) break;
+    mpending = false;
+    phase ^= 1u;
+    tc_fence_after();
+    // H1 row: bias, ReLU, BF16, 8 core matrices along K of the second product
+#pragma unroll
+    for (int c = 0; c < kMlpH / 16; ++c) {
+      float v[16];
+      tmem_ld16(lane_tmem + 16u * c, v);
+      unsigned h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        h[j] = pack2(f2bf(fmaxf(v[2 * j] + g.w.b1[16 * c + 2 * j], 0.0f)),
+                     f2bf(fmaxf(v[2 * j + 1] + g.w.b1[16 * c + 2 * j + 1], 0.0f)));
+      *reinterpret_cast<uint4*>(&g.a2[umma_kmajor(tid, 16 * c, kMlpH)]) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(&g.a2[umma_kmajor(tid, 16 * c + 8, kMlpH)]) = make_uint4(h[4], h[5], h[6], h[7]);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int s = 0; s < kMlpH / 16; ++s)
+        umma_bf16(tmem, umma_desc(a2 + 256u * s, 128u, 128u * (kMlpH / 8)),
+                  umma_desc(w2 + 256u * s, 128u, 128u * (kMlpH / 8)), s > 0);
+      umma_commit(mbar);
+    }
+    mpending = true;
+    abort = __syncthreads_or(!mbar_wait(mbar, phase)) != 0;
+    if (abort) break;
+    mpending = false;
+    phase ^= 1u;
+    tc_fence_after();
+    float z = g.w.b3;
+#pragma unroll
+    for (int c = 0; c < kMlpH / 16; ++c) {
+      float v[16];
+      tmem_ld16(lane_tmem + 16u * c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) z = fmaf(fmaxf(v[j] + g.w.b2[16 * c + j], 0.0f), g.w.w3[16 * c + j], z);
+    }
+    tc_fence_before();                     // these TMEM reads precede the next tile's MMAs
+    const float th_hat = 1.0f / (1.0f + __expf(-z));
+    const bool sk = ok && th_hat >= 1.0f - a.mlp_tau;
+    if (i < N) {
+      w.gskip[i] = sk ? 1 : 0;
+      if (ok && a.gate_out) a.gate_out[i] = th_hat;
+    }
+    skipped += __popc(__ballot_sync(0xffffffffu, sk));
   }
-  if (a.want_diag && lane == 0 && skipped) atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->mlp_skip, skipped);
+  if (abort) {
+    // flag it, then give the copy / MMAs in flight one more bounded wait
+    if (tid == 0) {
+      atomicOr(w.status, (unsigned)LXW_ST_TIMEOUT);
+      if (wpending) mbar_wait(wbar, 0);
+      if (mpending) mbar_wait(mbar, phase);
+    }
+    // the skip bytes of the tiles not reached stay as the previous step left them: clear them
+    for (int i = blockIdx.x * kGateRows + tid; i < N; i += gridDim.x * kGateRows) w.gskip[i] = 0;
+  }
+  if (a.want_diag && (tid & 31) == 0 && skipped)
+    atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->mlp_skip, skipped);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGateTmemCols) : "memory");
+  }
 }
 
 template <int KD, int E, int ML, int NQ, int MQ>
@@ -1314,14 +1407,11 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
   const int limit = a.shock_limiter && upto >= 5;
   double* tsc = a.theta_cell ? a.theta_cell + m.N : nullptr;
   if (limit && (a.gate_w || a.feat_out)) {
-    // persistent CTAs (each stages the weights once): as many as fit on the device
-    static int per_sm = 0;
-    if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gate_mx<E, ML>, 32 * kGateWarps,
-                                                                 sizeof(GateSmem)) != cudaSuccess)
-      per_sm = 1;
-    const int nw = (m.N + 31) / 32;
-    const int gg = std::max(1, std::min((nw + kGateWarps - 1) / kGateWarps, std::max(per_sm, 1) * std::max(a.sms, 1)));
-    k_gate_mx<E, ML><<<gg, 32 * kGateWarps, a.gate_w ? sizeof(GateSmem) : 0, st>>>(m, w, state, a);
+    // persistent CTAs, each copying the weights once and holding 64 TMEM
+    // columns: a.gate_per_sm of them per SM (resident by occupancy, <= 8)
+    const int ntile = (m.N + kGateRows - 1) / kGateRows;
+    const int gg = std::max(1, std::min(ntile, std::max(a.gate_per_sm, 1) * std::max(a.sms, 1)));
+    k_gate_mx<E, ML><<<gg, kGateRows, a.gate_w ? sizeof(GateTile) : 0, st>>>(m, w, state, a);
   }
   k_shock_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, tsc, limit);
   mark();
@@ -1349,6 +1439,36 @@ int moment_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const St
     if (kind == LXW_KIND_TRI && deg == 3) return CALL(3, 3, 10, 16, 4);  \
     return -2;                                                          \
   } while (0)
+
+// Resident CTAs per SM of the gate kernel from its registers, shared memory
+// and threads (the limits the hardware applies), capped by the 512 TMEM
+// columns of an SM.  The shared-memory carveout is set to its maximum first.
+template <int E, int ML>
+int gate_occupancy_impl() {
+  auto fn = k_gate_mx<E, ML>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+      cudaSuccess)
+    return -1;
+  cudaFuncAttributes fa;
+  int dev = 0, regs_sm = 0, smem_sm = 0, smem_rsv = 0, thr_sm = 0, blk_sm = 0;
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess)
+    return -1;
+  const int regs_cta = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256 * (kGateRows / 32);   // 256-register units per warp
+  const int smem_cta = (int)sizeof(GateTile) + (int)fa.sharedSizeBytes + smem_rsv;
+  int n = std::min({regs_sm / regs_cta, smem_sm / smem_cta, thr_sm / kGateRows, blk_sm});
+  return std::min(n, 512 / kGateTmemCols);
+}
+
+int gate_occupancy(int kind, int deg) {
+#define CALL_GOC(KD, E, ML, NQ, MQ) gate_occupancy_impl<E, ML>()
+  LXW_DISPATCH_MX(kind, deg, CALL_GOC);
+#undef CALL_GOC
+}
 
 int launch_step_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state, const StepArgs& a,
                    void* stream, int block, void** events, int upto) {

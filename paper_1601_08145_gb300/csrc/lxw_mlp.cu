@@ -120,11 +120,11 @@ __device__ __forceinline__ float bf16_widen(unsigned short h) { return __uint_as
 
 // parameter vector -> GateWeights (zero padding included)
 __global__ void k_gate_layout(const float* __restrict__ p, GateWeights* __restrict__ g) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kMlpH * kGateK2; k += gridDim.x * blockDim.x) {
-    const int n = k / kGateK2, c = k % kGateK2;
-    g->w2t[n][c] = c < kMlpH ? bf16_rne(p[kW2 + c * kMlpH + n]) : (unsigned short)0;
-    if (c < kGateK1) g->w1t[n][c] = c < kMlpIn ? bf16_rne(p[kW1 + c * kMlpH + n]) : (unsigned short)0;
-    if (c < kMlpH && n == 0) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kMlpH * kMlpH; k += gridDim.x * blockDim.x) {
+    const int n = k / kMlpH, c = k % kMlpH;            // output unit n, input c
+    g->w2[umma_kmajor(n, c, kMlpH)] = bf16_rne(p[kW2 + c * kMlpH + n]);
+    if (c < kGateK1) g->w1[umma_kmajor(n, c, kGateK1)] = c < kMlpIn ? bf16_rne(p[kW1 + c * kMlpH + n]) : (unsigned short)0;
+    if (n == 0) {
       g->b1[c] = bf16_widen(bf16_rne(p[kB1 + c]));
       g->b2[c] = bf16_widen(bf16_rne(p[kB2 + c]));
       g->w3[c] = bf16_widen(bf16_rne(p[kW3 + c]));
@@ -321,7 +321,7 @@ lxw_status lxw_mlp_train(lxw_mlp* n, const float* X, const float* y, int count, 
 
 namespace lxw {
 int mlp_gate_weights(lxw_mlp* n, GateWeights* out) {
-  k_gate_layout<<<(kMlpH * kGateK2 + 255) / 256, 256, 0, n->stream>>>(n->params, out);
+  k_gate_layout<<<(kMlpH * kMlpH + 255) / 256, 256, 0, n->stream>>>(n->params, out);
   return cudaStreamSynchronize(n->stream) == cudaSuccess ? 0 : -1;
 }
 }  // namespace lxw

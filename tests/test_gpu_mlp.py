@@ -171,7 +171,7 @@ def gate_reference(P, F):
 
 @pytest.mark.parametrize("kind,n", [("tri", 21), ("quad", 19)])
 def test_tensor_core_gate_matches_reference_network(L, kind, n):
-    """theta_hat of every cell from the mma.sync path against the same
+    """theta_hat of every cell from the tcgen05 path against the same
     network evaluated in float64 on the features the kernel saw; ragged
     tiles (N not a multiple of 32) included."""
     net = L.lxw_mlp_create(256, seed=17, stream=torch.cuda.current_stream())
