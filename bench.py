@@ -135,45 +135,44 @@ class ClockSampler:
 
 def train_indicator(L, stream, tau=0.02):
     """Train the troubled-cell MLP on the GPU from (features, limiter theta)
-    pairs that plain mixed runs of the smooth wave, the double rarefaction
-    and the blast (scaled down) produce; returns the net and a summary."""
+    pairs that plain mixed runs of the benchmark configurations produce (the
+    smooth wave 32x32, the rarefaction on 100,352 triangles, the blast on
+    1024x1024); every limited pair is kept, the others are subsampled to
+    about 400k, and the limited pairs are repeated to a quarter of the set.
+    Returns the net and a summary (held-out numbers on 20 % of the pairs)."""
     import torch
-    runs = [("quad", 32, synth.ic_smooth, (0.0, 1.0, 0.0, 1.0), (0, 0, 0, 0), 40),
-            ("tri", 48, synth.ic_rarefy, (0.0, 1.0, 0.0, 1.0), (2, 2, 2, 2), 80),
-            ("quad", 64, synth.ic_blast(64), (-1.1, 1.1, -1.1, 1.1), (1, 1, 1, 1), 120)]
+    gen = torch.Generator(device="cuda").manual_seed(7)
     Xs, ys = [], []
-    for kind, n, ic, box, bc, steps in runs:
-        if kind == "tri":
-            xy, tv = synth.structured_triangles(n, jitter=0.2, seed=20160129, box=box)
-            mesh = L.lxw_mesh_triangles(xy, tv)
-        else:
-            mesh = L.lxw_mesh_cartesian(n, n, box, bc)
-        sol = L.lxw_solver_create(mesh, 2, L.lxw_options_default(precision=L.PREC_MIXED), stream=stream)
-        st = project(L, sol, dict(ic=ic, n=n))
+    for name, steps, every in (("smooth", 40, 4), ("rarefy", 60, 6), ("blast", 40, 10)):
+        w, sol = build_workload(L, name, stream, True)
+        st = project(L, sol, w)
         for k in range(steps):
-            if k % 4 == 3:
-                F, th = L.lxw_step_dump(sol, st, 0.1)
+            if k % every == every - 1:
+                F, th = L.lxw_step_dump(sol, st, w["cfl"])
                 Xs.append(F); ys.append(th.float())
             else:
-                L.lxw_step(sol, st, 0.0, 0.1)
+                L.lxw_step(sol, st, 0.0, w["cfl"])
     X = torch.cat(Xs); y = torch.cat(ys)
-    perm = torch.randperm(X.shape[0], generator=torch.Generator().manual_seed(0)).cuda()
+    lim = y < 1.0
+    n_un = int((~lim).sum().item())
+    keep = lim | (torch.rand(X.shape[0], device="cuda", generator=gen) < min(1.0, 4e5 / max(n_un, 1)))
+    X, y = X[keep], y[keep]
+    perm = torch.randperm(X.shape[0], device="cuda", generator=gen)
     X, y = X[perm].contiguous(), y[perm].contiguous()
     nval = X.shape[0] // 5
     Xv, yv, Xt, yt = X[:nval], y[:nval], X[nval:], y[nval:]
-    # limited cells are rare (well under 1 %): repeat them until they are about
-    # a quarter of the training set, so the loss does not learn "always smooth"
     lim = yt < 1.0
     reps = max(1, int(0.25 * Xt.shape[0] / max(int(lim.sum().item()), 1)))
     Xt = torch.cat([Xt] + [Xt[lim]] * (reps - 1)); yt = torch.cat([yt] + [yt[lim]] * (reps - 1))
-    perm = torch.randperm(Xt.shape[0], generator=torch.Generator().manual_seed(1)).cuda()
+    perm = torch.randperm(Xt.shape[0], device="cuda", generator=gen)
     Xt, yt = Xt[perm].contiguous(), yt[perm].contiguous()
     net = L.lxw_mlp_create(1024, seed=3, stream=stream)
     loss = L.lxw_mlp_train(net, Xt, yt, epochs=6, batch=512, lr=2e-3)
     yh = torch.cat([L.lxw_mlp_forward(net, Xv[k:k + 1024].contiguous()) for k in range(0, Xv.shape[0], 1024)])
     strong = yv < 1.0 - 2 * tau
     missed = ((yh >= 1.0 - tau) & strong).sum().item() / max(int(strong.sum().item()), 1)
-    return net, {"pairs": int(X.shape[0]), "limited_fraction": float((y < 1).float().mean().item()),
+    return net, {"pairs_generated": int(keep.numel()), "pairs_kept": int(X.shape[0]),
+                 "limited_fraction_kept": float((y < 1).float().mean().item()),
                  "limited_repeat": reps, "final_batch_mse": loss,
                  "heldout_mse": float(torch.mean((yh - yv) ** 2).item()),
                  "heldout_skip_fraction": float((yh >= 1.0 - tau).float().mean().item()),
