@@ -43,6 +43,10 @@ WORKLOADS = {
                   desc="blast: 1024x1024 Cartesian, P2, point energy 0.979264 in the 4 centre cells, reflective"),
     "smooth": dict(kind="quad", n=32, deg=2, cfl=0.1, ic=synth.ic_smooth,
                    desc="smooth: 32x32 periodic Cartesian, P2, advected density wave"),
+    "rarefy1m": dict(kind="tri", n=724, deg=2, cfl=0.1, ic=synth.ic_rarefy,
+                     desc="rarefaction: 724x724x2 = 1,048,352 jittered triangles, P2, rho=1 p=0.4 u=-+2, transparent"),
+    "blast2048": dict(kind="quad", n=2048, deg=2, cfl=0.1, ic=None, bc=(1, 1, 1, 1), box=(-1.1, 1.1, -1.1, 1.1),
+                      desc="blast: 2048x2048 Cartesian, P2, point energy 0.979264 in the 4 centre cells, reflective"),
 }
 ENSEMBLE = dict(count=256, lo=32, hi=256, seed=4242, deg=2, cfl=0.3,
                 desc="ensemble: 256 independent Cartesian problems n_p x n_p, n_p ~ U{32..256} (seed 4242), "
@@ -67,7 +71,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x 2 
 # DRAM bytes per k_ck launch from the ncu capture summarised in profiles/ (None until captured
 # for the current kernel version)
 CK_TRAFFIC_BYTES = 27_383_296 + 40_022_272   # k_ck of the FP64 form, profiles/k_ck_rarefy224_p2_fp64.md
-CK_MX_TRAFFIC_BYTES = None                   # k_ck_mx: not captured yet
+CK_MX_TRAFFIC_BYTES = 13766400   # k_ck_mx DRAM read + write per launch, rarefaction 100k (ncu)
 
 
 def build_workload(L, name, stream, mixed):
@@ -349,6 +353,9 @@ def main():
     ap.add_argument("--workload", default="rarefy", choices=sorted(WORKLOADS) + ["ensemble"])
     ap.add_argument("--tau", type=float, default=0.02, help="learned gate: skip where theta_hat >= 1 - tau")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default work list of the mixed forms")
+    ap.add_argument("--form", default="all", choices=["all", "learned", "mixed", "fp64"],
+                    help="all: FP64, mixed and mixed + learned (headline); otherwise time only that form")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -380,6 +387,9 @@ def main():
         if net is not None:
             L.lxw_solver_set_mlp(sol, net, args.tau)
         Q = project(L, sol, w)
+        tune = None
+        if mixed and not args.no_autotune:
+            tune = L.lxw_autotune(sol, Q, w["cfl"], reps=3)     # on a scratch copy; Q is restored
         L.lxw_run(sol, Q, max(args.warmup, 3), w["cfl"])
         torch.cuda.synchronize()
         if clocks:
@@ -404,7 +414,58 @@ def main():
         dof = sol.N * 4 * sol.ML
         mean_phase = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
         return dict(w=w, sol=sol, Q=Q, total_ms=total_ms, dof=dof, value=world * dof * args.steps / (total_ms / 1e3),
-                    phases=mean_phase, clocks=clk)
+                    phases=mean_phase, clocks=clk, tune=tune)
+
+    def e2e_of(sol, state, cfl):
+        """End to end through the public C ABI on HOST memory: H2D of the
+        state, one step, D2H of the result, every step."""
+        Qh = torch.empty(sol.q64_shape, dtype=torch.float64).pin_memory()
+        Qh.copy_((L.to_q64(sol, state) if sol.mixed else state).cpu())
+        L.lxw_run_host(sol, Qh, 1, cfl)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            L.lxw_run_host(sol, Qh, 1, cfl)
+        e2e_s = time.perf_counter() - t0
+        dof = sol.N * 4 * sol.ML
+        return {"value": world * dof * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": dof * 8,
+                "d2h_bytes_per_step": dof * 8}
+
+    if args.form != "all":
+        mixed = args.form != "fp64"
+        net, info = train_indicator(L, stream, args.tau) if args.form == "learned" else (None, None)
+        f = timed_form(mixed, ClockSampler(local), net=net)
+        w, sol = f["w"], f["sol"]
+        flops = ck_flops_per_element(w["kind"], w["deg"]) * sol.N
+        ck_ms = f["phases"]["ck"]
+        ach = flops / (ck_ms / 1e3) / 1e12
+        peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+        e2e = e2e_of(sol, f["Q"], w["cfl"])
+        if world > 1:
+            dist.barrier()
+        if rank == 0:
+            out = {"metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                   "warmup": args.warmup, "ms_per_step": f["total_ms"] / args.steps, "higher_is_better": True,
+                   "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
+                   "data": "synthetic",
+                   "config": {"workload": w["desc"], "elements": sol.N, "degree": w["deg"], "form": args.form,
+                              "cfl": w["cfl"], "l2": "flushed between timed steps (256 MB write)",
+                              "timing": "one CUDA-graph replay per step, CUDA events on the solver's stream",
+                              "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "roofline": {"kernel": "k_ck_mx" if mixed else "k_ck", "bound": "alu",
+                                "pipe": "fp32" if mixed else "fp64", "achieved": ach, "peak": peak,
+                                "unit": "TFLOP/s", "frac": ach / peak,
+                                "traffic": (CK_MX_TRAFFIC_BYTES if mixed else CK_TRAFFIC_BYTES)
+                                if args.workload == "rarefy" else None,
+                                "algorithmic_flops_per_launch": flops, "launch_ms": ck_ms},
+                   "e2e": e2e, "gpu_launches": args.steps * L.lxw_step_launches(sol), "clocks": f["clocks"],
+                   "phases_ms": f["phases"], "autotune": f["tune"], "learned_indicator": info}
+            if world == 1 and not args.no_cpu_baseline:
+                out["cpu_baseline"], _, _ = cpu_baseline(args.workload)
+            print(json.dumps(out))
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     fp64 = timed_form(False)
     plain_mx = timed_form(True)
@@ -438,7 +499,8 @@ def main():
     dom = max(mx["phases"], key=mx["phases"].get)
     roofline = {"kernel": "k_ck_mx", "dominant_phase": dom, "bound": "alu", "pipe": "fp32",
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": CK_MX_TRAFFIC_BYTES,
+                "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": CK_MX_TRAFFIC_BYTES if args.workload == "rarefy" else None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                 "peak_measured_fma_probe": probes["fp32"],
                 "frac_of_measured_probe": achieved / probes["fp32"] if probes["fp32"] else None,
@@ -450,19 +512,7 @@ def main():
                           "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f64_ach / FP64_PEAK_TFLOPS,
                           "traffic": CK_TRAFFIC_BYTES, "peak_measured_fma_probe": probes["fp64"]}}
 
-    # end to end through the public C ABI on HOST memory: H2D of the state,
-    # one step, D2H of the result, every step
-    Qm = L.to_q64(sol, mx["Q"])
-    Qh = torch.empty(sol.q64_shape, dtype=torch.float64).pin_memory()
-    Qh.copy_(Qm.cpu())
-    L.lxw_run_host(sol, Qh, 1, w["cfl"])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        L.lxw_run_host(sol, Qh, 1, w["cfl"])
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * dof * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": dof * 8,
-           "d2h_bytes_per_step": dof * 8}
+    e2e = e2e_of(sol, mx["Q"], w["cfl"])
     if world > 1:
         dist.barrier()
 
@@ -486,8 +536,10 @@ def main():
            "phases_ms": mx["phases"],
            "plain_fp64": plain,
            "speedup_vs_plain_fp64": mx["value"] / fp64["value"],
+           "autotune": mx["tune"],
            "plain_mixed": {"value": plain_mx["value"], "ms_per_step": plain_mx["total_ms"] / args.steps,
-                           "phases_ms": plain_mx["phases"], "l1_rel_density_vs_fp64": dist_plain_mx},
+                           "phases_ms": plain_mx["phases"], "l1_rel_density_vs_fp64": dist_plain_mx,
+                           "autotune": plain_mx["tune"]},
            "learned_indicator": dict(train_info, train_s=t_train, tau=args.tau,
                                      skipped_cells_last_step=dmx["n_mlp_skip"], of=sol.N,
                                      gain_vs_plain_mixed=mx["value"] / plain_mx["value"]),
