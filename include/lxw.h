@@ -204,7 +204,7 @@ lxw_status lxw_shock_limit(lxw_solver* s, double* Q_dev, double* theta_dev);
 int lxw_step_launches(const lxw_solver* s);
 /* Number of intervals lxw_profile_step times: FP64 form one per kernel
  * (reset, moment, ck, edge, update[, shock]); mixed form 5 (moment with the
- * time-step kernel, ck, edge, update, shock with the learned gate). */
+ * time step, ck, edge, update, shock with the learned gate). */
 int lxw_profile_phases(const lxw_solver* s);
 
 /* lxw_step (dt from cfl, no diagnostics) replayed from a CUDA graph with an

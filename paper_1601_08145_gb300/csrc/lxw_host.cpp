@@ -493,6 +493,7 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     s->dwm.avg_new = (double*)dalloc(sizeof(double) * 4 * (size_t)N);
     s->dwm.avgn32 = (float*)dalloc(sizeof(float) * 4 * (size_t)N);
     s->dwm.gskip = (unsigned char*)dalloc((size_t)N);
+    s->dwm.done = (unsigned int*)dalloc(sizeof(unsigned int));
     s->dwm.scal = (ScalMx*)dalloc(sizeof(ScalMx) * nprob);
     s->dwm.smax = s->dw.smax; s->dwm.status = s->dw.status; s->dwm.diag = s->dw.diag;
     s->Sdev = (double*)dalloc(lxw_state_bytes(s));
@@ -501,7 +502,8 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     float* s32 = (float*)dalloc(sizeof(float) * (size_t)N);
     float* ia32 = (float*)dalloc(sizeof(float) * (size_t)N);
     double* ia64 = (double*)dalloc(sizeof(double) * (size_t)N);
-    if (!s->dwm.avg_new || !s->dwm.avgn32 || !s->dwm.gskip || !s->dwm.scal || !s->Sdev || !j32 || !n32 || !s32 || !ia32 || !ia64) {
+    if (!s->dwm.avg_new || !s->dwm.avgn32 || !s->dwm.gskip || !s->dwm.done ||
+        cudaMemset(s->dwm.done, 0, sizeof(unsigned int)) != cudaSuccess || !s->dwm.scal || !s->Sdev || !j32 || !n32 || !s32 || !ia32 || !ia64) {
       delete s;
       return fail(LXW_ERR_NOMEM, "lxw_solver_create: device allocation failed");
     }
@@ -796,7 +798,13 @@ lxw_status lxw_moment_limit(lxw_solver* s, double* Q, double* theta, double* s_d
   int rc = s->mixed ? launch_moment_limit_mx(s->kind, s->deg, s->dm, s->dwm, Q, a, theta, s->stream, s->opt.block_threads)
                     : launch_moment_limit(s->kind, s->deg, s->dm, s->dw, Q, a, theta, s->stream, s->opt.block_threads);
   if (rc) return fail(LXW_ERR_CUDA, "lxw_moment_limit: launch failed");
-  if (s_dev && launch_copy_speed(s->dw, s_dev, s->stream)) return fail(LXW_ERR_CUDA, "lxw_moment_limit: launch failed");
+  if (s_dev) {
+    // the mixed moment kernel leaves each problem's s in its scalars (and clears the maximum)
+    if (s->mixed)
+      LXW_CUDA(cudaMemcpyAsync(s_dev, &s->dwm.scal[0].s, sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    else if (launch_copy_speed(s->dw, s_dev, s->stream))
+      return fail(LXW_ERR_CUDA, "lxw_moment_limit: launch failed");
+  }
   return LXW_OK;
 }
 
@@ -810,14 +818,14 @@ lxw_status lxw_shock_limit(lxw_solver* s, double* Q, double* theta) {
 }
 
 // the mixed form always launches its shock kernel (it also commits the new averages)
-// timed intervals of lxw_profile_step: mixed form moment(+scalars), ck, edge,
-// update, shock(+gate); FP64 form one per kernel
+// timed intervals of lxw_profile_step: mixed form moment (+ scalars), ck, edge,
+// update, shock (+ gate); FP64 form one per kernel
 static int phases_of(const lxw_solver* s) { return s->mixed ? 5 : step_launch_count(0, s->opt.shock_limiter); }
 int lxw_profile_phases(const lxw_solver* s) { return s ? phases_of(s) : 0; }
 int lxw_step_launches(const lxw_solver* s) {
   if (!s) return 0;
   if (!s->mixed) return step_launch_count(0, s->opt.shock_limiter);
-  return 6 + (s->mlp_w && s->opt.shock_limiter ? 1 : 0);   // moment, scalars, ck, edge, update, [gate,] shock
+  return 5 + (s->mlp_w && s->opt.shock_limiter ? 1 : 0);   // moment, ck, edge, update, [gate,] shock
 }
 
 lxw_status lxw_batch_scalars(lxw_solver* s, int* nprob, double* s_host, double* dt_host) {

@@ -87,6 +87,7 @@ struct DevWorkMx {
   unsigned long long* smax;  // [nprob]
   unsigned int* status;
   double* diag;           // DiagBlock
+  unsigned int* done;     // CTAs of the moment kernel that have finished (the last one computes scal)
 };
 
 // Diagnostics block on the device (both forms).

@@ -18,8 +18,8 @@
 // coefficient are coalesced).  On GB300 every FP64-pipe instruction --
 // DFMA, DADD, DSETP, double<->float conversion, the DDIV sequence -- runs at
 // the FP64 rate, so the FP32 kernels use FP32 geometry copies and per-step
-// scalars computed once (k_scalars) and touch no double at all unless a
-// screen sends a cell to its FP64 path.
+// scalars computed once per step (by the last CTA of the moment kernel) and
+// touch no double at all unless a screen sends a cell to its FP64 path.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -132,16 +132,15 @@ __device__ __forceinline__ unsigned long long obits(double x) {
 }
 
 // per problem (one thread each): the step's wave speed and time step, in FP64 and FP32
-__global__ void k_scalars(const DevMesh m, const DevWorkMx w, const StepArgs a) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= m.nprob) return;
-  const double s = __longlong_as_double((long long)w.smax[p]);
-  w.smax[p] = 0ull;                       // ready for the next step's maximum
+// a problem's wave speed and time step from its running maximum (Sec. 3.2 s,
+// the CFL rule), with the FP32 copies the bulk kernels use
+__device__ __forceinline__ ScalMx make_scal(const DevMesh& m, const DevWorkMx& w, const StepArgs& a, int p) {
+  const double s = __longlong_as_double((long long)__ldcg(w.smax + p));
   const double dt = a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin_p[p] / s;
   ScalMx sc;
   sc.s = s; sc.dt = dt;
   sc.s32 = (float)s; sc.dt32 = (float)dt; sc.c1 = (float)(0.5 * dt); sc.c2 = (float)(dt * dt / 6.0);
-  w.scal[p] = sc;
+  return sc;
 }
 
 // accessors of the packed state
@@ -164,9 +163,9 @@ __device__ __forceinline__ float& hi_at(const MxState& st, int N, int v, int l, 
 }
 
 // Zeroes the per-step diagnostics (and the status word when clear_status).
-// Steps without diagnostics launch no reset: k_scalars zeroes each problem's
-// speed maximum once it has read it, and the status word is sticky until the
-// host reads it.
+// Steps without diagnostics launch no reset: the moment kernel's last CTA
+// zeroes each problem's speed maximum once it has read it, and the status word
+// is sticky until the host reads it.
 __global__ void k_reset_mx(DevWorkMx w, int nprob, int want_diag, int clear_status) {
   for (int p = threadIdx.x; p < nprob; p += blockDim.x) w.smax[p] = 0ull;
   if (threadIdx.x != 0) return;
@@ -402,6 +401,23 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
     if (!need && (int)threadIdx.x < tile.y && theta_out) theta_out[i] = 1.0;
     block_max(sm, &w.smax[tile.z]);
   }
+  // The last CTA to finish (its maxima, like every other CTA's, are in before
+  // its count) turns each problem's maximum into (s, dt) and clears it for the
+  // next step.  No CTA waits on another.
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(w.done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    for (int p = threadIdx.x; p < m.nprob; p += blockDim.x) {
+      w.scal[p] = make_scal(m, w, a, p);
+      w.smax[p] = 0ull;
+    }
+    if (threadIdx.x == 0) *w.done = 0u;
+  }
 }
 
 // ---------------------------------------------------------- k_ck_mx
@@ -415,13 +431,12 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
 // modes, and traces (q, n_out.F_T) at the edge points.
 template <int KD, int E, int ML, int NQ, int MQ>
 __device__ __forceinline__ void ck_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
-                                        const StepArgs& a, const int i, const int pid) {
+                                        const StepArgs& a, const int i, const ScalMx& sc) {
   constexpr int NPT = NQ + E * MQ;
   const TablesF& t = c_tabf[KD];
   const int N = m.N;
   MxState st = mx_state<ML>(state, N);
   const float g1 = a.gamma_f - 1.0f;
-  const ScalMx sc = w.scal[pid];
   const float dt = sc.dt32, c1 = sc.c1, c2 = sc.c2;
   float c[4][ML];
 #pragma unroll
@@ -551,7 +566,7 @@ __global__ void __launch_bounds__(128, ML == 6 ? 4 : 2) k_ck_mx(const DevMesh m,
                                                                 double* __restrict__ state, const StepArgs a) {
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
-    if ((int)threadIdx.x < tile.y) ck_elem<KD, E, ML, NQ, MQ>(m, w, state, a, tile.x + threadIdx.x, tile.z);
+    if ((int)threadIdx.x < tile.y) ck_elem<KD, E, ML, NQ, MQ>(m, w, state, a, tile.x + threadIdx.x, w.scal[tile.z]);
   }
 }
 
@@ -1393,7 +1408,6 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
   mark();
   if (a.want_diag) k_reset_mx<<<1, 256, 0, st>>>(w, m.nprob, 1, 0);
   k_moment_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, a.theta_cell);
-  k_scalars<<<gridn(m.nprob, 128), 128, 0, st>>>(m, w, a);
   mark();
   if (upto < 2) return ok();
   k_ck_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a);
@@ -1425,7 +1439,6 @@ int moment_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const St
   const int grid = a.grid > 0 && a.grid < m.ntiles ? a.grid : m.ntiles;
   k_reset_mx<<<1, 256, 0, st>>>(w, m.nprob, 1, 1);
   k_moment_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, theta);
-  k_scalars<<<gridn(m.nprob, 128), 128, 0, st>>>(m, w, a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
