@@ -492,7 +492,6 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     s->dwm.prop = reinterpret_cast<float*>(s->dw.prop);
     s->dwm.avg_new = (double*)dalloc(sizeof(double) * 4 * (size_t)N);
     s->dwm.avgn32 = (float*)dalloc(sizeof(float) * 4 * (size_t)N);
-    s->dwm.gskip = (unsigned char*)dalloc((size_t)N);
     s->dwm.done = (unsigned int*)dalloc(sizeof(unsigned int));
     s->dwm.scal = (ScalMx*)dalloc(sizeof(ScalMx) * nprob);
     s->dwm.smax = s->dw.smax; s->dwm.status = s->dw.status; s->dwm.diag = s->dw.diag;
@@ -502,7 +501,7 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     float* s32 = (float*)dalloc(sizeof(float) * (size_t)N);
     float* ia32 = (float*)dalloc(sizeof(float) * (size_t)N);
     double* ia64 = (double*)dalloc(sizeof(double) * (size_t)N);
-    if (!s->dwm.avg_new || !s->dwm.avgn32 || !s->dwm.gskip || !s->dwm.done ||
+    if (!s->dwm.avg_new || !s->dwm.avgn32 || !s->dwm.done ||
         cudaMemset(s->dwm.done, 0, sizeof(unsigned int)) != cudaSuccess || !s->dwm.scal || !s->Sdev || !j32 || !n32 || !s32 || !ia32 || !ia64) {
       delete s;
       return fail(LXW_ERR_NOMEM, "lxw_solver_create: device allocation failed");

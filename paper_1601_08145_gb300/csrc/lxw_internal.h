@@ -82,7 +82,6 @@ struct DevWorkMx {
   float* prop;            // [E][N]: Lambda proposals, rounded down to FP32
   double* avg_new;        // [4][N]: updated averages before the shock limiter commits them
   float* avgn32;          // [4][N]: FP32 copy of avg_new
-  unsigned char* gskip;   // [N]: 1 where the learned gate lets the shock limiter skip the cell
   ScalMx* scal;           // [nprob]
   unsigned long long* smax;  // [nprob]
   unsigned int* status;
@@ -128,7 +127,7 @@ struct StepArgs {
   double dt_in, cfl, gamma, eps0, alpha0;
   float gamma_f, eps0_f, alpha0_f;   // FP32 copies for the mixed form
   int sms;                           // SMs of the device
-  int gate_per_sm;                   // resident gate CTAs per SM (persistent grid of k_gate_mx)
+  int gate_per_sm;                   // resident CTAs per SM of the gated shock kernel (its persistent grid)
   const GateWeights* gate_w;         // learned gate weights or null
   float mlp_tau;                     // gate: skip the limiter where theta_hat >= 1 - tau
   float* feat_out;                   // [N][24] features at the shock limiter's input, or null

@@ -1180,14 +1180,20 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
   }
 }
 
-// The learned gate (features + network) over the mesh in tiles of 128
-// consecutive cells, persistent CTAs.  Writes the skip byte of each cell
-// (theta_hat >= 1 - tau and positive averages), and on request theta_hat and
-// the features.  Without a network it only writes the features (training
-// pairs) and touches no tensor-core state.
-template <int E, int ML>
-__global__ void __launch_bounds__(kGateRows) k_gate_mx(const DevMesh m, const DevWorkMx w,
-                                                       const double* __restrict__ state, const StepArgs a) {
+// The shock limiter behind the learned gate (features + network), over the
+// mesh in tiles of 128 consecutive cells, persistent CTAs.  Each thread
+// computes its cell's features; the CTA evaluates the network on the tensor
+// cores; a cell whose theta_hat >= 1 - tau (and whose averages are positive)
+// keeps theta_sc = 1, every other cell runs the plain limiter; every cell
+// commits its new averages.  On request it writes theta_hat and the
+// features.  Without a network it writes the features (training pairs),
+// runs the plain limiter everywhere and touches no tensor-core state.  If a
+// device wait gives up, the CTA flags LXW_ST_TIMEOUT and runs the plain
+// limiter on the rest of its cells.
+template <int KD, int E, int ML, int NQ, int MQ>
+__global__ void __launch_bounds__(kGateRows, 4) k_shock_gate_mx(const DevMesh m, const DevWorkMx w,
+                                                             double* __restrict__ state, const StepArgs a,
+                                                             double* __restrict__ theta_out) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const int N = m.N;
   if (a.gate_w == nullptr) {
@@ -1197,6 +1203,7 @@ __global__ void __launch_bounds__(kGateRows) k_gate_mx(const DevMesh m, const De
 #pragma unroll
         for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
       }
+      shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, 1, i, false);
     }
     return;
   }
@@ -1227,14 +1234,14 @@ __global__ void __launch_bounds__(kGateRows) k_gate_mx(const DevMesh m, const De
                  : "memory");
   }
   bool abort = __syncthreads_or(!mbar_wait(wbar, 0)) != 0;
-  bool wpending = abort;                   // the weight copy may still be in flight
-  bool mpending = false;                   // an MMA group committed but not seen complete
+  const bool wpending = abort;            // the weight copy may still be in flight
+  bool mpending = false;                  // an MMA group committed but not seen complete
   unsigned phase = 0;
   const unsigned a1 = smem_u32(g.a1), a2 = smem_u32(g.a2), w1 = smem_u32(g.w.w1), w2 = smem_u32(g.w.w2);
   const unsigned lane_tmem = tmem + ((unsigned)(warp * 32) << 16);
   const int ntile = (N + kGateRows - 1) / kGateRows;
   unsigned long long skipped = 0;
-  for (int t = blockIdx.x; t < ntile && !abort; t += gridDim.x) {
+  for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
     const int i = t * kGateRows + tid;
     float f[kMlpIn];
     const bool ok = i < N && gate_features<E, ML>(m, w, state, a, i, f);
@@ -1242,91 +1249,90 @@ __global__ void __launch_bounds__(kGateRows) k_gate_mx(const DevMesh m, const De
 #pragma unroll
       for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
     }
-    // this cell's features, BF16, as row tid of X (4 core matrices along K)
+    bool sk = false;
+    if (!abort) {
+      // this cell's features, BF16, as row tid of X (4 core matrices along K)
 #pragma unroll
-    for (int kb = 0; kb < kGateK1 / 8; ++kb) {
-      uint4 q = make_uint4(0u, 0u, 0u, 0u);
-      if (ok && kb * 8 < kMlpIn) {
-        q.x = pack2(f2bf(f[kb * 8 + 0]), f2bf(f[kb * 8 + 1]));
-        q.y = pack2(f2bf(f[kb * 8 + 2]), f2bf(f[kb * 8 + 3]));
-        q.z = pack2(f2bf(f[kb * 8 + 4]), f2bf(f[kb * 8 + 5]));
-        q.w = pack2(f2bf(f[kb * 8 + 6]), f2bf(f[kb * 8 + 7]));
+      for (int kb = 0; kb < kGateK1 / 8; ++kb) {
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+        if (ok && kb * 8 < kMlpIn) {
+          q.x = pack2(f2bf(f[kb * 8 + 0]), f2bf(f[kb * 8 + 1]));
+          q.y = pack2(f2bf(f[kb * 8 + 2]), f2bf(f[kb * 8 + 3]));
+          q.z = pack2(f2bf(f[kb * 8 + 4]), f2bf(f[kb * 8 + 5]));
+          q.w = pack2(f2bf(f[kb * 8 + 6]), f2bf(f[kb * 8 + 7]));
+        }
+        *reinterpret_cast<uint4*>(&g.a1[umma_kmajor(tid, kb * 8, kGateK1)]) = q;
       }
-      *reinterpret_cast<uint4*>(&g.a1[umma_kmajor(tid, kb * 8, kGateK1)]) = q;
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+#pragma unroll
+        for (int s = 0; s < kGateK1 / 16; ++s)
+          umma_bf16(tmem, umma_desc(a1 + 256u * s, 128u, 128u * (kGateK1 / 8)),
+                    umma_desc(w1 + 256u * s, 128u, 128u * (kGateK1 / 8)), s > 0);
+        umma_commit(mbar);
+      }
+      mpending = true;
+      abort = __syncthreads_or(!mbar_wait(mbar, phase)) != 0;
     }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
+    if (!abort) {
+      mpending = false;
+      phase ^= 1u;
       tc_fence_after();
+      // H1 row: bias, ReLU, BF16, 8 core matrices along K of the second product
 #pragma unroll
-      for (int s = 0; s < kGateK1 / 16; ++s)
-        umma_bf16(tmem, umma_desc(a1 + 256u * s, 128u, 128u * (kGateK1 / 8)),
-                  umma_desc(w1 + 256u * s, 128u, 128u * (kGateK1 / 8)), s > 0);
-      umma_commit(mbar);
+      for (int c = 0; c < kMlpH / 16; ++c) {
+        float v[16];
+        tmem_ld16(lane_tmem + 16u * c, v);
+        unsigned h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          h[j] = pack2(f2bf(fmaxf(v[2 * j] + g.w.b1[16 * c + 2 * j], 0.0f)),
+                       f2bf(fmaxf(v[2 * j + 1] + g.w.b1[16 * c + 2 * j + 1], 0.0f)));
+        *reinterpret_cast<uint4*>(&g.a2[umma_kmajor(tid, 16 * c, kMlpH)]) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(&g.a2[umma_kmajor(tid, 16 * c + 8, kMlpH)]) = make_uint4(h[4], h[5], h[6], h[7]);
+      }
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+#pragma unroll
+        for (int s = 0; s < kMlpH / 16; ++s)
+          umma_bf16(tmem, umma_desc(a2 + 256u * s, 128u, 128u * (kMlpH / 8)),
+                    umma_desc(w2 + 256u * s, 128u, 128u * (kMlpH / 8)), s > 0);
+        umma_commit(mbar);
+      }
+      mpending = true;
+      abort = __syncthreads_or(!mbar_wait(mbar, phase)) != 0;
     }
-    mpending = true;
-    abort = __syncthreads_or(!mbar_wait(mbar, phase)) != 0;
-    if (abort) break;
-    mpending = false;
-    phase ^= 1u;
-    tc_fence_after();
-    // H1 row: bias, ReLU, BF16, 8 core matrices along K of the second product
-#pragma unroll
-    for (int c = 0; c < kMlpH / 16; ++c) {
-      float v[16];
-      tmem_ld16(lane_tmem + 16u * c, v);
-      unsigned h[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        h[j] = pack2(f2bf(fmaxf(v[2 * j] + g.w.b1[16 * c + 2 * j], 0.0f)),
-                     f2bf(fmaxf(v[2 * j + 1] + g.w.b1[16 * c + 2 * j + 1], 0.0f)));
-      *reinterpret_cast<uint4*>(&g.a2[umma_kmajor(tid, 16 * c, kMlpH)]) = make_uint4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<uint4*>(&g.a2[umma_kmajor(tid, 16 * c + 8, kMlpH)]) = make_uint4(h[4], h[5], h[6], h[7]);
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
+    if (!abort) {
+      mpending = false;
+      phase ^= 1u;
       tc_fence_after();
+      float z = g.w.b3;
 #pragma unroll
-      for (int s = 0; s < kMlpH / 16; ++s)
-        umma_bf16(tmem, umma_desc(a2 + 256u * s, 128u, 128u * (kMlpH / 8)),
-                  umma_desc(w2 + 256u * s, 128u, 128u * (kMlpH / 8)), s > 0);
-      umma_commit(mbar);
-    }
-    mpending = true;
-    abort = __syncthreads_or(!mbar_wait(mbar, phase)) != 0;
-    if (abort) break;
-    mpending = false;
-    phase ^= 1u;
-    tc_fence_after();
-    float z = g.w.b3;
+      for (int c = 0; c < kMlpH / 16; ++c) {
+        float v[16];
+        tmem_ld16(lane_tmem + 16u * c, v);
 #pragma unroll
-    for (int c = 0; c < kMlpH / 16; ++c) {
-      float v[16];
-      tmem_ld16(lane_tmem + 16u * c, v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) z = fmaf(fmaxf(v[j] + g.w.b2[16 * c + j], 0.0f), g.w.w3[16 * c + j], z);
-    }
-    tc_fence_before();                     // these TMEM reads precede the next tile's MMAs
-    const float th_hat = 1.0f / (1.0f + __expf(-z));
-    const bool sk = ok && th_hat >= 1.0f - a.mlp_tau;
-    if (i < N) {
-      w.gskip[i] = sk ? 1 : 0;
+        for (int j = 0; j < 16; ++j) z = fmaf(fmaxf(v[j] + g.w.b2[16 * c + j], 0.0f), g.w.w3[16 * c + j], z);
+      }
+      tc_fence_before();                   // these TMEM reads precede the next tile's MMAs
+      const float th_hat = 1.0f / (1.0f + __expf(-z));
+      sk = ok && th_hat >= 1.0f - a.mlp_tau;
       if (ok && a.gate_out) a.gate_out[i] = th_hat;
     }
     skipped += __popc(__ballot_sync(0xffffffffu, sk));
+    if (i < N) shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, 1, i, sk);
   }
-  if (abort) {
+  if (abort && tid == 0) {
     // flag it, then give the copy / MMAs in flight one more bounded wait
-    if (tid == 0) {
-      atomicOr(w.status, (unsigned)LXW_ST_TIMEOUT);
-      if (wpending) mbar_wait(wbar, 0);
-      if (mpending) mbar_wait(mbar, phase);
-    }
-    // the skip bytes of the tiles not reached stay as the previous step left them: clear them
-    for (int i = blockIdx.x * kGateRows + tid; i < N; i += gridDim.x * kGateRows) w.gskip[i] = 0;
+    atomicOr(w.status, (unsigned)LXW_ST_TIMEOUT);
+    if (wpending) mbar_wait(wbar, 0);
+    if (mpending) mbar_wait(mbar, phase);
   }
   if (a.want_diag && (tid & 31) == 0 && skipped)
     atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->mlp_skip, skipped);
@@ -1341,13 +1347,10 @@ __global__ void __launch_bounds__(kGateRows) k_gate_mx(const DevMesh m, const De
 template <int KD, int E, int ML, int NQ, int MQ>
 __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                   const StepArgs a, double* __restrict__ theta_out, int limit) {
-  const bool gated = a.gate_w != nullptr;
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
-    if ((int)threadIdx.x < tile.y) {
-      const int i = tile.x + threadIdx.x;
-      shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, limit, i, gated && w.gskip[i] != 0);
-    }
+    if ((int)threadIdx.x < tile.y)
+      shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, limit, tile.x + threadIdx.x, false);
   }
 }
 
@@ -1425,9 +1428,10 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
     // columns: a.gate_per_sm of them per SM (resident by occupancy, <= 8)
     const int ntile = (m.N + kGateRows - 1) / kGateRows;
     const int gg = std::max(1, std::min(ntile, std::max(a.gate_per_sm, 1) * std::max(a.sms, 1)));
-    k_gate_mx<E, ML><<<gg, kGateRows, a.gate_w ? sizeof(GateTile) : 0, st>>>(m, w, state, a);
+    k_shock_gate_mx<KD, E, ML, NQ, MQ><<<gg, kGateRows, a.gate_w ? sizeof(GateTile) : 0, st>>>(m, w, state, a, tsc);
+  } else {
+    k_shock_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, tsc, limit);
   }
-  k_shock_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, tsc, limit);
   mark();
   if (a.want_diag) k_diag_mx<ML><<<gridn(m.N, 256), 256, 0, st>>>(m, w, state, a.gamma);
   return ok();
@@ -1456,9 +1460,9 @@ int moment_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const St
 // Resident CTAs per SM of the gate kernel from its registers, shared memory
 // and threads (the limits the hardware applies), capped by the 512 TMEM
 // columns of an SM.  The shared-memory carveout is set to its maximum first.
-template <int E, int ML>
+template <int KD, int E, int ML, int NQ, int MQ>
 int gate_occupancy_impl() {
-  auto fn = k_gate_mx<E, ML>;
+  auto fn = k_shock_gate_mx<KD, E, ML, NQ, MQ>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
       cudaSuccess)
     return -1;
@@ -1478,7 +1482,7 @@ int gate_occupancy_impl() {
 }
 
 int gate_occupancy(int kind, int deg) {
-#define CALL_GOC(KD, E, ML, NQ, MQ) gate_occupancy_impl<E, ML>()
+#define CALL_GOC(KD, E, ML, NQ, MQ) gate_occupancy_impl<KD, E, ML, NQ, MQ>()
   LXW_DISPATCH_MX(kind, deg, CALL_GOC);
 #undef CALL_GOC
 }

@@ -46,14 +46,14 @@ def test_forward_and_gradient_match_oracle(L, O):
     assert np.abs(g - go).max() < 1e-4 * np.abs(go).max()
 
 
-def mixed_solver(L, kind, n, shock=True, box=(0.0, 1.0, 0.0, 1.0), bc=(2, 2, 2, 2)):
+def mixed_solver(L, kind, n, shock=True, box=(0.0, 1.0, 0.0, 1.0), bc=(2, 2, 2, 2), deg=2):
     if kind == "tri":
         xy, tv = synth.structured_triangles(n, jitter=0.2, seed=20160129, box=box)
         mesh = L.lxw_mesh_triangles(xy, tv)
     else:
         mesh = L.lxw_mesh_cartesian(n, n, box, bc)
     o = L.lxw_options_default(precision=L.PREC_MIXED, shock_limiter=int(shock), alpha0=50.0)
-    return L.lxw_solver_create(mesh, 2, o, stream=torch.cuda.current_stream())
+    return L.lxw_solver_create(mesh, deg, o, stream=torch.cuda.current_stream())
 
 
 def start(L, s, ic):
@@ -169,8 +169,8 @@ def gate_reference(P, F):
     return 1.0 / (1.0 + np.exp(-(H2 @ w3 + b3)))
 
 
-@pytest.mark.parametrize("kind,n", [("tri", 21), ("quad", 19)])
-def test_tensor_core_gate_matches_reference_network(L, kind, n):
+@pytest.mark.parametrize("kind,n,deg", [("tri", 21, 2), ("quad", 19, 2), ("tri", 13, 3), ("quad", 11, 3)])
+def test_tensor_core_gate_matches_reference_network(L, kind, n, deg):
     """theta_hat of every cell from the tcgen05 path against the same
     network evaluated in float64 on the features the kernel saw; ragged
     tiles (N not a multiple of 32) included."""
@@ -179,7 +179,7 @@ def test_tensor_core_gate_matches_reference_network(L, kind, n):
     assert P.size == 5825
     box, bc, ic = ((-1.1, 1.1, -1.1, 1.1), (1, 1, 1, 1), synth.ic_blast(n)) if kind == "quad" else \
         ((0.0, 1.0, 0.0, 1.0), (2, 2, 2, 2), synth.ic_rarefy)
-    s = mixed_solver(L, kind, n, box=box, bc=bc)
+    s = mixed_solver(L, kind, n, box=box, bc=bc, deg=deg)
     L.lxw_solver_set_mlp(s, net, 0.0)                     # tau 0: only theta_hat >= 1 would skip
     st = start(L, s, ic)
     for _ in range(3):
@@ -189,6 +189,12 @@ def test_tensor_core_gate_matches_reference_network(L, kind, n):
     asked = ~np.isnan(g)
     assert asked.sum() == s.N
     ref = gate_reference(P, F)
-    # FP32 accumulation of 24 + 64 BF16 products: ~1e-6 relative in z, sigmoid' <= 1/4
-    assert np.abs(g - ref).max() < 2e-5, np.abs(g - ref).max()
+    # FP32 accumulation of 24 + 64 BF16 products: ~1e-6 relative in z, sigmoid' <= 1/4.
+    # The first hidden layer is rounded to BF16 after an FP32 (tensor core) or
+    # float64 (here) sum: where the two sums straddle a BF16 rounding boundary one
+    # hidden unit differs by one BF16 ulp (2^-8 relative), which moves theta_hat by
+    # at most ulp * |h| * sum_n |W2 w3| / 4, a few 1e-3 for these weights.
+    d = np.abs(g - ref)
+    assert np.mean(d < 2e-5) > 0.99, np.sort(d)[-5:]
+    assert d.max() < 5e-3, d.max()
     assert g.std() > 1e-3                                 # the cells do not all give one value
