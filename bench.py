@@ -299,6 +299,21 @@ def run_ensemble(args):
     print(json.dumps(out))
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (every rank gets it): the timed
+    region of the slowest replica."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed (each rank the same replica workload) per
+    second of the slowest rank's timed region."""
+    return world * units_per_rank / seconds
+
+
 def time_steps(L, sol, Q, cfl, steps, flush):
     """K steps, each one replay of the solver's captured step graph on its
     stream, bracketed by CUDA events on that stream; the L2 is flushed (256 MB
@@ -403,9 +418,7 @@ def main():
             dist.barrier()
         clk = clocks.stop() if clocks else None
         if world > 1:
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = t.item()
+            total_ms = max_over_ranks(total_ms, dist, "cuda")
         # per-phase device times from a separately traced pass (event nodes between the phases)
         phases = []
         for k in range(5):
@@ -413,7 +426,8 @@ def main():
             phases.append(L.lxw_profile_step(sol, Q, w["cfl"]))
         dof = sol.N * 4 * sol.ML
         mean_phase = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
-        return dict(w=w, sol=sol, Q=Q, total_ms=total_ms, dof=dof, value=world * dof * args.steps / (total_ms / 1e3),
+        return dict(w=w, sol=sol, Q=Q, total_ms=total_ms, dof=dof,
+                    value=whole_job_rate(dof * args.steps, world, total_ms / 1e3),
                     phases=mean_phase, clocks=clk, tune=tune)
 
     def e2e_of(sol, state, cfl):
