@@ -41,6 +41,10 @@ struct TablesF {
 __constant__ TablesF c_tabf[4];
 // weighted differentiation tables (DerivTables, FP32)
 __constant__ float c_wd[4][2][kMaxQ][kMaxML];
+// the basis at the limiter points in FP64, for the moment limiter's FP64 path
+// (an FP32 table promoted to double would put 1e-7 into point values whose
+// pressure the secant then divides by near vacuum)
+__constant__ double c_phid[4][kMaxPts][kMaxML];
 
 constexpr float kTol = 1e-5f;            // relative margin of the FP32 screens (FP32 error ~5e-7)
 constexpr float kSpeedInflate = 1.00001f; // s from FP32 point values, inflated to bound the exact one
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
         const double rb = st.avg[ci];
         double d = 0.0;
 #pragma unroll
-        for (int l = 1; l < ML; ++l) d = fma((double)hi_at<ML>(st, N, 0, l, ci), (double)t.phi[p][l], d);
+        for (int l = 1; l < ML; ++l) d = fma((double)hi_at<ML>(st, N, 0, l, ci), c_phid[KD][p][l], d);
         const double rm = rb + d;
         const double er = fmin(a.eps0, 0.5 * rb);
         if (rm < er) atomicMin(&th_slot[warp][cl], dbits((rb - er) / (rb - rm)));
@@ -352,7 +356,7 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
         for (int v = 0; v < 4; ++v) {
           double acc = 0.0;
 #pragma unroll
-          for (int l = 1; l < ML; ++l) acc = fma((double)hi_at<ML>(st, N, v, l, ci), (double)t.phi[p][l], acc);
+          for (int l = 1; l < ML; ++l) acc = fma((double)hi_at<ML>(st, N, v, l, ci), c_phid[KD][p][l], acc);
           d[v] = acc;
         }
         const double r = st.avg[ci] + thr_c * d[0], mm = st.avg[(size_t)N + ci] + thr_c * d[1],
@@ -1530,6 +1534,9 @@ int upload_tables_mx(int kind, int deg, const Tables& t) {
     for (int k = 0; k < kMaxQ; ++k)
       for (int l = 0; l < kMaxML; ++l) wd[c][k][l] = (float)d.W[c][k][l];
   if (cudaMemcpyToSymbol(c_wd, wd, sizeof(wd), kd * sizeof(wd)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(c_phid, t.phi, sizeof(double) * kMaxPts * kMaxML,
+                         kd * sizeof(double) * kMaxPts * kMaxML) != cudaSuccess)
+    return -1;
   return 0;
 }
 

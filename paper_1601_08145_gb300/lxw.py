@@ -271,14 +271,14 @@ def lxw_step(solver, Q, dt=0.0, cfl=0.1, diag=False, theta_cell=None, theta_edge
                                C.byref(d) if d is not None else None,
                                _ptr(theta_cell, (2, solver.N), "theta_cell"),
                                _ptr(theta_edge, (solver.N, solver.E), "theta_edge")),
-                allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN))
+                allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN, ERR_TIMEOUT))
     return _diag_result(st, d) if d is not None else None
 
 
 def lxw_run(solver, Q, nsteps, cfl, diag=False):
     d = Diag() if diag else None
     st = _check(lib().lxw_run(solver.h, _ptr(Q, solver.state_shape, "Q"), nsteps, cfl,
-                              C.byref(d) if d is not None else None), allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN))
+                              C.byref(d) if d is not None else None), allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN, ERR_TIMEOUT))
     return _diag_result(st, d) if d is not None else None
 
 
@@ -292,7 +292,7 @@ def lxw_run_host(solver, Qh, nsteps, cfl, diag=False):
         p = C.c_void_p(Qh.data_ptr())
     d = Diag() if diag else None
     st = _check(lib().lxw_run_host(solver.h, p, nsteps, cfl, C.byref(d) if d is not None else None),
-                allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN))
+                allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN, ERR_TIMEOUT))
     return _diag_result(st, d) if d is not None else None
 
 

@@ -178,3 +178,33 @@ def test_status_is_kept_until_a_diagnostic_step_reads_it(L):
     d = L.lxw_step(s, good, 0.0, 0.1, diag=True)
     assert d["status"] == 0 and d["return_status"] == L.OK
     assert L.lxw_step_launches(s) == 5 and L.lxw_profile_phases(s) == 5
+
+
+@pytest.mark.parametrize("kind,n", [(TRI, 224), (QUAD, 1024), (QUAD, 2048)])
+def test_full_size_one_mixed_step_against_oracle(L, O, kind, n):
+    """The benchmark sizes (100,352 triangles; 1024^2 and 2048^2 squares), in
+    the launch configuration the autotuner picks for them, from a random
+    near-vacuum state with every limiter active: one mixed step against the
+    oracle's step, element by element within the FP32 budget, and positive."""
+    bc = 2
+    s = solver(L, kind, 2, n, bc=(bc,) * 4, tri_bc=bc if kind == TRI else None)
+    so = oracle_solver(O, kind, 2, n, bc=(bc,) * 4, tri_bc=bc if kind == TRI else None)
+    Q0 = synth.random_modal_state(s.N, s.ML, seed=77 + n, amp=0.3, rho_range=(0.01, 3.0), p_range=(0.001, 3.0))
+    Q0[:, :, 1:] = Q0[:, :, 1:].astype(np.float32)
+    scratch = L.new_state(s, torch.from_numpy(Q0).cuda())
+    L.lxw_autotune(s, scratch, 0.3, reps=1)
+    Qo = Q0.copy(); do = so.step(Qo, cfl=0.3)
+    st = L.new_state(s, torch.from_numpy(Q0).cuda())
+    d = L.lxw_step(s, st, 0.0, 0.3, diag=True)
+    Qg = L.to_q64(s, st).cpu().numpy()
+    assert d["status"] == 0 and do["status"] == 0 and d["min_rho"] > 0 and d["min_p"] > 0
+    assert d["n_mom"] > 0 and d["n_sc"] > 0                          # the limiters did act
+    # s is the largest FP32 speed over ~10^7 point values; the pressure inside
+    # c = sqrt(gamma p / rho) cancels (E - |m|^2 / 2 rho), so the FP32 error at
+    # the argmax point grows like 1e-7 E / p.  (Positivity needs s only above
+    # the averages' speeds: FP32 to 1e-7 under the 1e-5 inflation.)
+    assert abs(d["s"] / do["s"] - 1) < 2e-4
+    sc = np.abs(Qo).max(axis=0, keepdims=True) + 1e-3
+    assert np.abs(Qg[:, :, 0] - Qo[:, :, 0]).max() < 1e-5 * np.abs(Qo[:, :, 0]).max()
+    assert (np.abs(Qg - Qo) / sc).max() < 1e-3
+    assert np.abs(Qg - Qo).sum() / np.abs(Qo).sum() < 1e-5
