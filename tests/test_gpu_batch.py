@@ -101,3 +101,37 @@ def test_ensemble_positivity(L):
     for _ in range(40):
         d = L.lxw_step(b, st, 0.0, 0.3, diag=True)
         assert d["status"] == 0 and d["min_rho"] > 0 and d["min_p"] > 0
+
+
+def test_gated_batch_equals_gated_individual_runs(L):
+    """The learned gate on a batch: its tensor-core tiles of 128 cells
+    straddle problems, but every output row of the network depends only on its
+    own cell, so the batch reproduces the problems gated one by one, bit for bit."""
+    sizes = [9, 30, 17]
+    net = L.lxw_mlp_create(256, seed=21, stream=torch.cuda.current_stream())
+    probs = [quadrant_problem(L, n, 300 + k) for k, n in enumerate(sizes)]
+    opt = L.lxw_options_default(precision=L.PREC_MIXED)
+    singles = []
+    for mesh, ic in probs:
+        s = L.lxw_solver_create(mesh, 2, opt, stream=torch.cuda.current_stream())
+        L.lxw_solver_set_mlp(s, net, 0.3)
+        st = L.new_state(s, projected(L, s, ic))
+        skipped = 0
+        for _ in range(6):
+            skipped += L.lxw_step(s, st, 0.0, 0.3, diag=True)["n_mlp_skip"]
+        singles.append((L.to_q64(s, st), skipped))
+    b = L.lxw_batch_create([m for m, _ in probs], 2, opt, stream=torch.cuda.current_stream())
+    L.lxw_solver_set_mlp(b, net, 0.3)
+    Q = torch.cat([projected(L, L.lxw_solver_create(m, 2, stream=torch.cuda.current_stream()), ic)
+                   for m, ic in probs])
+    st = L.new_state(b, Q)
+    skipped = 0
+    for _ in range(6):
+        d = L.lxw_step(b, st, 0.0, 0.3, diag=True)
+        assert d["status"] == 0
+        skipped += d["n_mlp_skip"]
+    Qb = L.to_q64(b, st)
+    off = b.offsets
+    for k in range(len(sizes)):
+        assert torch.equal(Qb[off[k]:off[k + 1]], singles[k][0]), k
+    assert skipped == sum(x[1] for x in singles) and skipped > 0
