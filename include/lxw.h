@@ -188,9 +188,11 @@ lxw_status lxw_step(lxw_solver* s, double* Q_dev, double dt, double cfl, lxw_dia
  * (nullable) receives the last step's diagnostics. */
 lxw_status lxw_run(lxw_solver* s, double* Q_dev, int nsteps, double cfl, lxw_diag* diag_host);
 
-/* End-to-end form of lxw_run on HOST memory: copies Q_host (pinned or
- * pageable, [N][4][ML]) to the solver's device state, runs nsteps and copies
- * the result back, synchronously. */
+/* End-to-end form of lxw_run on HOST memory: brings Q_host ([N][4][ML],
+ * pinned or pageable) to the solver's device state, runs nsteps and returns
+ * the result to Q_host, synchronously.  Pageable memory is copied; for the
+ * mixed form, pinned (device-mapped) memory is read and written directly by
+ * the layout-conversion kernels, one pass over the host link each way. */
 lxw_status lxw_run_host(lxw_solver* s, double* Q_host, int nsteps, double cfl, lxw_diag* diag_host);
 
 /* Single phases of the step, for per-phase checks (same kernels as lxw_step):

@@ -749,17 +749,34 @@ lxw_status lxw_run(lxw_solver* s, double* Q, int nsteps, double cfl, lxw_diag* d
 lxw_status lxw_run_host(lxw_solver* s, double* Qh, int nsteps, double cfl, lxw_diag* diag) {
   if (!s || !Qh) return fail(LXW_ERR_ARG, "lxw_run_host: null argument");
   const size_t bytes = sizeof(double) * (size_t)s->N * 4 * s->ML;
-  LXW_CUDA(cudaMemcpyAsync(s->Qdev, Qh, bytes, cudaMemcpyHostToDevice, s->stream));
+  // pinned host memory is mapped into the device's address space: the mixed
+  // form's pack / unpack kernels then read and write it directly (one pass
+  // over the host link each way, no staging copy); pageable memory is copied
+  cudaPointerAttributes pa{};
+  double* mapped = nullptr;
+  if (s->mixed && cudaPointerGetAttributes(&pa, Qh) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+      pa.devicePointer != nullptr)
+    mapped = static_cast<double*>(pa.devicePointer);
+  cudaGetLastError();   // a pageable pointer may leave an error code behind
   double* state = s->Qdev;
   if (s->mixed) {
-    if (launch_pack(s->ML, s->N, s->Qdev, s->Sdev, s->stream)) return fail(LXW_ERR_CUDA, "lxw_run_host: pack failed");
+    if (!mapped) LXW_CUDA(cudaMemcpyAsync(s->Qdev, Qh, bytes, cudaMemcpyHostToDevice, s->stream));
+    if (launch_pack(s->ML, s->N, mapped ? mapped : s->Qdev, s->Sdev, s->stream))
+      return fail(LXW_ERR_CUDA, "lxw_run_host: pack failed");
     state = s->Sdev;
+  } else {
+    LXW_CUDA(cudaMemcpyAsync(s->Qdev, Qh, bytes, cudaMemcpyHostToDevice, s->stream));
   }
   lxw_status st = lxw_run(s, state, nsteps, cfl, diag);
-  if (st != LXW_OK && st != LXW_ERR_NONPOSITIVE && st != LXW_ERR_CFL && st != LXW_ERR_NAN) return st;
-  if (s->mixed && launch_unpack(s->ML, s->N, s->Sdev, s->Qdev, s->stream))
-    return fail(LXW_ERR_CUDA, "lxw_run_host: unpack failed");
-  LXW_CUDA(cudaMemcpyAsync(Qh, s->Qdev, bytes, cudaMemcpyDeviceToHost, s->stream));
+  if (st != LXW_OK && st != LXW_ERR_NONPOSITIVE && st != LXW_ERR_CFL && st != LXW_ERR_NAN && st != LXW_ERR_TIMEOUT)
+    return st;
+  if (s->mixed) {
+    if (launch_unpack(s->ML, s->N, s->Sdev, mapped ? mapped : s->Qdev, s->stream))
+      return fail(LXW_ERR_CUDA, "lxw_run_host: unpack failed");
+    if (!mapped) LXW_CUDA(cudaMemcpyAsync(Qh, s->Qdev, bytes, cudaMemcpyDeviceToHost, s->stream));
+  } else {
+    LXW_CUDA(cudaMemcpyAsync(Qh, s->Qdev, bytes, cudaMemcpyDeviceToHost, s->stream));
+  }
   LXW_CUDA(cudaStreamSynchronize(s->stream));
   return st;
 }

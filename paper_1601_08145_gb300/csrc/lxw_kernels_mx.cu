@@ -1380,26 +1380,74 @@ __global__ void __launch_bounds__(256) k_diag_mx(const DevMesh m, const DevWorkM
   }
 }
 
-__global__ void k_pack(int ML, int N, const double* __restrict__ Q64, double* __restrict__ state) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  float* a32 = reinterpret_cast<float*>(state + 4 * (size_t)N);
-  float* hi = a32 + 4 * (size_t)N;
-  for (int v = 0; v < 4; ++v) {
-    const double av = Q64[((size_t)i * 4 + v) * ML];
-    state[(size_t)v * N + i] = av;
-    a32[(size_t)v * N + i] = (float)av;
-    for (int l = 1; l < ML; ++l) hi[((size_t)v * (ML - 1) + l - 1) * N + i] = (float)Q64[((size_t)i * 4 + v) * ML + l];
+// Q64[N][4][ML] (element-major, the ABI layout) <-> the mixed state layout,
+// through shared memory so that both sides are read and written in
+// consecutive words: 128 elements per CTA.  Q64 may be host memory mapped
+// into the device's address space (pinned), read or written here directly.
+constexpr int kPackRows = 128;
+// vec: Q64 is 16-byte aligned (every CTA's block of 128 x 4 ML doubles then is)
+template <int ML>
+__global__ void __launch_bounds__(kPackRows) k_pack(int N, const double* __restrict__ Q64,
+                                                    double* __restrict__ state, int vec) {
+  __shared__ __align__(16) double buf[kPackRows * 4 * ML];
+  const int base = blockIdx.x * kPackRows;
+  const int n = min(kPackRows, N - base);
+  const double* src = Q64 + (size_t)base * 4 * ML;
+  if (vec) {
+    const int pairs = n * 2 * ML;
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    double2* b2 = reinterpret_cast<double2*>(buf);
+#pragma unroll 4
+    for (int k = threadIdx.x; k < pairs; k += blockDim.x) b2[k] = s2[k];   // several loads in flight per thread
+  } else {
+#pragma unroll 4
+    for (int k = threadIdx.x; k < n * 4 * ML; k += blockDim.x) buf[k] = src[k];
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < n) {
+    const int i = base + threadIdx.x;
+    float* a32 = reinterpret_cast<float*>(state + 4 * (size_t)N);
+    float* hi = a32 + 4 * (size_t)N;
+    const double* e = buf + threadIdx.x * 4 * ML;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const double av = e[v * ML];
+      state[(size_t)v * N + i] = av;
+      a32[(size_t)v * N + i] = (float)av;
+#pragma unroll
+      for (int l = 1; l < ML; ++l) hi[((size_t)v * (ML - 1) + l - 1) * N + i] = (float)e[v * ML + l];
+    }
   }
 }
 
-__global__ void k_unpack(int ML, int N, const double* __restrict__ state, double* __restrict__ Q64) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const float* hi = reinterpret_cast<const float*>(state + 4 * (size_t)N) + 4 * (size_t)N;
-  for (int v = 0; v < 4; ++v) {
-    Q64[((size_t)i * 4 + v) * ML] = state[(size_t)v * N + i];
-    for (int l = 1; l < ML; ++l) Q64[((size_t)i * 4 + v) * ML + l] = (double)hi[((size_t)v * (ML - 1) + l - 1) * N + i];
+template <int ML>
+__global__ void __launch_bounds__(kPackRows) k_unpack(int N, const double* __restrict__ state,
+                                                      double* __restrict__ Q64, int vec) {
+  __shared__ __align__(16) double buf[kPackRows * 4 * ML];
+  const int base = blockIdx.x * kPackRows;
+  const int n = min(kPackRows, N - base);
+  if ((int)threadIdx.x < n) {
+    const int i = base + threadIdx.x;
+    const float* hi = reinterpret_cast<const float*>(state + 4 * (size_t)N) + 4 * (size_t)N;
+    double* e = buf + threadIdx.x * 4 * ML;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      e[v * ML] = state[(size_t)v * N + i];
+#pragma unroll
+      for (int l = 1; l < ML; ++l) e[v * ML + l] = (double)hi[((size_t)v * (ML - 1) + l - 1) * N + i];
+    }
+  }
+  __syncthreads();
+  double* dst = Q64 + (size_t)base * 4 * ML;
+  if (vec) {
+    const int pairs = n * 2 * ML;
+    double2* d2 = reinterpret_cast<double2*>(dst);
+    const double2* b2 = reinterpret_cast<const double2*>(buf);
+#pragma unroll 4
+    for (int k = threadIdx.x; k < pairs; k += blockDim.x) d2[k] = b2[k];
+  } else {
+#pragma unroll 4
+    for (int k = threadIdx.x; k < n * 4 * ML; k += blockDim.x) dst[k] = buf[k];
   }
 }
 
@@ -1506,12 +1554,20 @@ int launch_moment_limit_mx(int kind, int deg, const DevMesh& m, const DevWorkMx&
 }
 
 int launch_pack(int ML, int N, const double* Q64, double* state, void* stream) {
-  k_pack<<<gridn(N, 128), 128, 0, (cudaStream_t)stream>>>(ML, N, Q64, state);
+  const int vec = (reinterpret_cast<uintptr_t>(Q64) & 15u) == 0;
+  if (ML == 6)
+    k_pack<6><<<gridn(N, kPackRows), kPackRows, 0, (cudaStream_t)stream>>>(N, Q64, state, vec);
+  else
+    k_pack<10><<<gridn(N, kPackRows), kPackRows, 0, (cudaStream_t)stream>>>(N, Q64, state, vec);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_unpack(int ML, int N, const double* state, double* Q64, void* stream) {
-  k_unpack<<<gridn(N, 128), 128, 0, (cudaStream_t)stream>>>(ML, N, state, Q64);
+  const int vec = (reinterpret_cast<uintptr_t>(Q64) & 15u) == 0;
+  if (ML == 6)
+    k_unpack<6><<<gridn(N, kPackRows), kPackRows, 0, (cudaStream_t)stream>>>(N, state, Q64, vec);
+  else
+    k_unpack<10><<<gridn(N, kPackRows), kPackRows, 0, (cudaStream_t)stream>>>(N, state, Q64, vec);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

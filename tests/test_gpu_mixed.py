@@ -76,6 +76,12 @@ def test_pack_roundtrip(L, kind, deg):
     torch.cuda.synchronize()
     assert torch.equal(Q1[:, :, 0], Q0[:, :, 0])                     # averages stay FP64
     assert torch.equal(Q1[:, :, 1:], Q0[:, :, 1:].float().double())  # higher modes are FP32
+    # a source 8 bytes off a 16-byte boundary takes the scalar copy path: same state
+    flat = torch.empty(Q0.numel() + 1, dtype=torch.float64, device="cuda")
+    Qm = flat[1:].view(Q0.shape)
+    Qm.copy_(Q0)
+    assert Qm.data_ptr() % 16 == 8
+    assert torch.equal(L.new_state(s, Qm), st)
 
 
 @pytest.mark.parametrize("kind,deg", [(QUAD, 2), (QUAD, 3), (TRI, 2), (TRI, 3)])
@@ -160,8 +166,11 @@ def test_mixed_run_graph_and_host_path(L):
     torch.cuda.synchronize()
     assert torch.equal(A, B)
     H = Q.cpu().numpy().copy()
-    L.lxw_run_host(s, H, 5, 0.1)
+    L.lxw_run_host(s, H, 5, 0.1)                        # pageable: staged copies
     assert np.array_equal(H, L.to_q64(s, A).cpu().numpy())
+    P = Q.cpu().pin_memory()
+    L.lxw_run_host(s, P, 5, 0.1)                        # pinned: read and written in place by the kernels
+    assert np.array_equal(P.numpy(), H)
 
 
 def test_status_is_kept_until_a_diagnostic_step_reads_it(L):
