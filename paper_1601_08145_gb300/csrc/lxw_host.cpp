@@ -841,7 +841,7 @@ int lxw_profile_phases(const lxw_solver* s) { return s ? phases_of(s) : 0; }
 int lxw_step_launches(const lxw_solver* s) {
   if (!s) return 0;
   if (!s->mixed) return step_launch_count(0, s->opt.shock_limiter);
-  return 5 + (s->mlp_w && s->opt.shock_limiter ? 1 : 0);   // moment, ck, edge, update, [gate,] shock
+  return 5;   // moment, ck, edge, update, shock (the learned gate runs inside the shock kernel)
 }
 
 lxw_status lxw_batch_scalars(lxw_solver* s, int* nprob, double* s_host, double* dt_host) {
