@@ -118,7 +118,11 @@ int lxw_mesh_num_elements(const lxw_mesh* mesh);
 
 /* degree 2 or 3.  stream: cudaStream_t (NULL = legacy default stream) on
  * which every later call of this solver is enqueued.  Allocates all device
- * memory the solver needs; later calls allocate nothing. */
+ * memory the step needs: lxw_step, lxw_run, lxw_run_host, lxw_profile_step
+ * and the phase calls allocate nothing (lxw_run and lxw_profile_step
+ * instantiate a CUDA graph on first use).  lxw_solver_set_mlp (the gate's
+ * weight image, once), lxw_autotune (a scratch state) and lxw_step_dump
+ * (a scratch theta pair) allocate as they say. */
 lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options* opt,
                              void* stream, lxw_solver** out);
 void lxw_solver_destroy(lxw_solver* s);
@@ -152,8 +156,9 @@ lxw_status lxw_batch_create(int nmesh, const lxw_mesh* const* meshes, int degree
 lxw_status lxw_batch_scalars(lxw_solver* s, int* nprob, double* s_host, double* dt_host);
 /* Autotuner: times `reps` steps of each candidate (elements per CTA in
  * {32, 64, 128} x persistent CTAs per SM in {0 (one per tile), 1, 2, 3, 4,
- * 6, 8}) on a scratch copy of state_dev (restored afterwards), keeps the
- * fastest in the solver and returns it.  Allocates a scratch state. */
+ * 6, 8}; FP64 solvers: elements per CTA only) on a scratch copy of
+ * state_dev (restored afterwards), keeps the fastest in the solver and
+ * returns it (output pointers nullable).  Allocates a scratch state. */
 lxw_status lxw_autotune(lxw_solver* s, void* state_dev, double cfl, int reps, int* block_threads,
                         int* ctas_per_sm, float* best_ms);
 
@@ -178,8 +183,10 @@ lxw_status lxw_project(lxw_solver* s, const double* prim_dev, double* Q_dev);
  * theta_edge_dev (nullable) receives [N][E] theta_e seen from each element.
  * diag_host (nullable) synchronises the stream and fills the diagnostics;
  * with diag_host NULL the call is asynchronous and graph-capturable.
- * Returns LXW_ERR_NONPOSITIVE / LXW_ERR_CFL / LXW_ERR_NAN only when diag_host
- * is given and the device flagged the condition (the step still completes). */
+ * Returns LXW_ERR_NONPOSITIVE / LXW_ERR_CFL / LXW_ERR_NAN / LXW_ERR_TIMEOUT
+ * only when diag_host is given and the device flagged the condition during
+ * this step or a step since the last diagnostics (the status bits are kept
+ * until read); the steps still complete. */
 lxw_status lxw_step(lxw_solver* s, double* Q_dev, double dt, double cfl, lxw_diag* diag_host,
                     double* theta_cell_dev, double* theta_edge_dev);
 
@@ -248,8 +255,11 @@ lxw_status lxw_fma_peak(int fp64, double* tflops);
  * the fallback.  The positivity limiters always run exactly.
  * Parameters (float, LXW_MLP_PARAMS of them): W1[24][64], b1[64],
  * W2[64][64], b2[64], w3[64], b3.  Training (FP32 kernels, mean-squared
- * error, Adam) runs on the GPU; the step kernels use a BF16 copy with FP32
- * accumulation. */
+ * error, Adam) runs on the GPU; the gated shock kernel evaluates a BF16 copy
+ * on the tensor cores (tcgen05, FP32 accumulation in tensor memory), 128
+ * cells per tile, and runs the plain limiter for the cells it does not
+ * clear.  Its device waits are bounded (about a second): on expiry it sets
+ * LXW_ST_TIMEOUT and limits the rest of its cells with the plain limiter. */
 enum { LXW_MLP_IN = 24, LXW_MLP_HIDDEN = 64, LXW_MLP_PARAMS = 5825 };
 typedef struct lxw_mlp lxw_mlp;
 /* max_batch: largest batch of the calls below; He-initialised from seed. */
@@ -268,12 +278,16 @@ lxw_status lxw_mlp_loss_grad(lxw_mlp* n, const float* X_dev, const float* y_dev,
 lxw_status lxw_mlp_train(lxw_mlp* n, const float* X_dev, const float* y_dev, int count, int epochs, int batch,
                          float lr, unsigned long long seed, float* last_loss);
 /* Enables (mlp non-NULL) or disables the learned gate of a mixed solver;
- * the solver keeps a BF16 copy taken now (later training needs another
- * call).  tau in [0, 1). */
+ * the solver keeps a BF16 copy taken now, laid out as the tensor-core
+ * operands (later training needs another call).  tau in [0, 1).  Errors:
+ * LXW_ERR_ARG (FP64 solver, tau), LXW_ERR_CUDA. */
 lxw_status lxw_solver_set_mlp(lxw_solver* s, lxw_mlp* mlp, float tau);
-/* One mixed step that also writes each cell's features at the shock
- * limiter's input (feat_dev[N][24]) and the limiter's theta
- * (theta_sc_dev[N]): training pairs produced by the method itself. */
+/* One mixed step (plain limiter, no gate) that also writes each cell's
+ * features at the shock limiter's input (feat_dev[N][24]; rows of cells with
+ * non-positive new averages are left untouched) and the limiter's theta
+ * (theta_sc_dev[N], nullable): training pairs produced by the method itself.
+ * Synchronous; allocates a scratch theta pair when theta_sc_dev is given.
+ * Errors: LXW_ERR_ARG (FP64 form, shock limiter off), LXW_ERR_CUDA. */
 lxw_status lxw_step_dump(lxw_solver* s, void* state_dev, double cfl, float* feat_dev, double* theta_sc_dev);
 
 /* One mixed step gated by the solver's network (lxw_solver_set_mlp), that
