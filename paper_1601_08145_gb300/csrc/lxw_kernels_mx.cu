@@ -45,6 +45,9 @@ __constant__ float c_wd[4][2][kMaxQ][kMaxML];
 // (an FP32 table promoted to double would put 1e-7 into point values whose
 // pressure the secant then divides by near vacuum)
 __constant__ double c_phid[4][kMaxPts][kMaxML];
+// max over the limiter points of |phi_l|: the moment screen's per-cell bound
+// of the point values' magnitude sums
+__constant__ float c_phimax[4][kMaxML];
 
 constexpr float kTol = 1e-5f;            // relative margin of the FP32 screens (FP32 error ~5e-7)
 constexpr float kSpeedInflate = 1.00001f; // s from FP32 point values, inflated to bound the exact one
@@ -235,18 +238,25 @@ __device__ __forceinline__ float moment_screen(const DevMesh& m, double* __restr
   const float er = fminf(eps0, 0.5f * a32[0]) * (1.0f + kTol);
   const float ep = fminf(eps0, 0.5f * pb) * (1.0f + kTol);
   mr = 0u; mp = 0u;
+  // S_v bounds |a_v| + sum_l |c_vl phi_l(p)| at every point, so the FP32
+  // error of each point value is below 1e-5 S_v with a wide margin
+  float S[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    float sa = fabsf(a32[v]);
+#pragma unroll
+    for (int l = 1; l < ML; ++l) sa = fmaf(fabsf(c[v][l]), c_phimax[KD][l], sa);
+    S[v] = sa;
+  }
 #pragma unroll 1
   for (int p = 0; p < NPT; ++p) {
-    float q[4], S[4];
+    float q[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      float acc = a32[v], sa = fabsf(a32[v]);
+      float acc = a32[v];
 #pragma unroll
-      for (int l = 1; l < ML; ++l) {
-        float term = c[v][l] * t.phi[p][l];
-        acc += term; sa += fabsf(term);
-      }
-      q[v] = acc; S[v] = sa;
+      for (int l = 1; l < ML; ++l) acc = fmaf(c[v][l], t.phi[p][l], acc);
+      q[v] = acc;
     }
     const float rinv = 1.0f / q[0];
     const float u = q[1] * rinv, vv = q[2] * rinv;
@@ -1593,6 +1603,13 @@ int upload_tables_mx(int kind, int deg, const Tables& t) {
   if (cudaMemcpyToSymbol(c_phid, t.phi, sizeof(double) * kMaxPts * kMaxML,
                          kd * sizeof(double) * kMaxPts * kMaxML) != cudaSuccess)
     return -1;
+  float pm[kMaxML];
+  for (int l = 0; l < kMaxML; ++l) {
+    double mx = 0.0;
+    for (int p = 0; p < kMaxPts; ++p) mx = std::max(mx, std::fabs(t.phi[p][l]));
+    pm[l] = (float)(mx * (1.0 + 1e-6));   // rounded up
+  }
+  if (cudaMemcpyToSymbol(c_phimax, pm, sizeof(pm), kd * sizeof(pm)) != cudaSuccess) return -1;
   return 0;
 }
 
