@@ -255,10 +255,12 @@ lxw_status lxw_fma_peak(int fp64, double* tflops);
  * the fallback.  The positivity limiters always run exactly.
  * Parameters (float, LXW_MLP_PARAMS of them): W1[24][64], b1[64],
  * W2[64][64], b2[64], w3[64], b3.  Training (FP32 kernels, mean-squared
- * error, Adam) runs on the GPU; the gated shock kernel evaluates a BF16 copy
- * on the tensor cores (tcgen05, FP32 accumulation in tensor memory), 128
- * cells per tile, and runs the plain limiter for the cells it does not
- * clear.  Its device waits are bounded (about a second): on expiry it sets
+ * error, Adam) runs on the GPU; the gated shock kernel first applies the
+ * limiter's exact screen (every primitive provably within alpha of its
+ * average: theta = 1), evaluates a BF16 copy of the network on the tensor
+ * cores (tcgen05, FP32 accumulation in tensor memory) for the tiles of 128
+ * cells that hold a cell the screen cannot clear, and runs the plain
+ * limiter for the cells neither clears.  Its device waits are bounded (about a second): on expiry it sets
  * LXW_ST_TIMEOUT and limits the rest of its cells with the plain limiter. */
 enum { LXW_MLP_IN = 24, LXW_MLP_HIDDEN = 64, LXW_MLP_PARAMS = 5825 };
 typedef struct lxw_mlp lxw_mlp;

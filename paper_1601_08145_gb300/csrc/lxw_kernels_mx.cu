@@ -1091,6 +1091,57 @@ __device__ __forceinline__ bool gate_features(const DevMesh& m, const DevWorkMx&
   return true;
 }
 
+// Exact shortcut of the shock limiter (Sec. 4.1, reading G14).  Its bounds
+// satisfy M >= w_avg + alpha and m <= w_avg - alpha, so theta_sc = 1 whenever
+// every primitive moves by at most alpha over the cell's points.  Per-cell
+// bounds of the conserved excursions D_v >= |sum_l c_vl phi_l(p)| give those
+// of the primitives: u_p - u = (dm_x - u drho) / rho_p, and
+// p_p - p = (g-1)(dE - u.dm + |u|^2 drho / 2) - (g-1)|dm - u drho|^2 / (2 rho_p).
+// The margins (1e-5 of the magnitudes) cover the FP32 evaluation of the full
+// path, which then returns exactly 1 as well.  c[v][0] holds the averages.
+template <int KD, int ML>
+__device__ __forceinline__ bool shock_screen(const float c[4][ML], const PtF& sb, float g1, float al) {
+  float D[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    float d = 0.0f;
+#pragma unroll
+    for (int l = 1; l < ML; ++l) d = fmaf(fabsf(c[v][l]), c_phimax[KD][l], d);
+    D[v] = d * (1.0f + kTol);
+  }
+  const float rmin = sb.r - D[0] - kTol * sb.r;
+  if (!(rmin > 0.0f && D[0] + kTol * (sb.r + D[0] + al) <= al)) return false;
+  const float au = fabsf(sb.u), av = fabsf(sb.v);
+  const float bu = D[1] + au * D[0], bv = D[2] + av * D[0];
+  const float eu = bu / rmin, ev = bv / rmin;
+  const float ep = g1 * (D[3] + au * D[1] + av * D[2] + 0.5f * (au * au + av * av) * D[0]) +
+                   g1 * (bu * bu + bv * bv) / (2.0f * rmin);
+  const float mp = g1 * (fabsf(c[3][0]) + D[3] + (fabsf(c[1][0]) + D[1]) * (au + eu) +
+                         (fabsf(c[2][0]) + D[2]) * (av + ev));
+  return eu + kTol * (au + eu + al) <= al && ev + kTol * (av + ev + al) <= al &&
+         ep + kTol * (mp + fabsf(sb.p) + al) <= al;
+}
+
+// the screen for element i from the state (new averages, modes), or false
+template <int KD, int ML>
+__device__ __forceinline__ bool shock_screen_at(const DevMesh& m, const DevWorkMx& w, const double* __restrict__ state,
+                                                const StepArgs& a, const int i) {
+  const int N = m.N;
+  MxState st = mx_state<ML>(const_cast<double*>(state), N);
+  float c[4][ML];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    c[v][0] = w.avgn32[(size_t)v * N + i];
+#pragma unroll
+    for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
+  }
+  if (!(c[0][0] > 0.0f)) return false;
+  const float g1 = a.gamma_f - 1.0f;
+  const PtF sb = ptf(g1, c[0][0], c[1][0], c[2][0], c[3][0]);
+  const float dx = m.sdx32[i];
+  return shock_screen<KD, ML>(c, sb, g1, a.alpha0_f * dx * sqrtf(dx));
+}
+
 template <int KD, int E, int ML, int NQ, int MQ>
 __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
                                            const StepArgs& a, double* __restrict__ theta_out, const int limit,
@@ -1121,9 +1172,11 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
       const float wb[4] = {sb.r, sb.u, sb.v, sb.p};
       const float dx = m.sdx32[i];
       const float al = a.alpha0_f * dx * sqrtf(dx);
+      const bool clear = shock_screen<KD, ML>(c, sb, g1, al);
       float Mx[4], Mn[4], nr[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ne[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int v = 0; v < 4; ++v) { Mx[v] = wb[v] + al; Mn[v] = wb[v] - al; }
+      if (!clear) {
 #pragma unroll
       for (int k = 0; k < E; ++k) {
         const int j = m.nbr[k * N + i];
@@ -1175,6 +1228,7 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
           th = fmaxf(th, 0.0f);
         }
       }
+      }   // !clear
     }
     if (th < 1.0f) {
 #pragma unroll
@@ -1195,11 +1249,12 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
 }
 
 // The shock limiter behind the learned gate (features + network), over the
-// mesh in tiles of 128 consecutive cells, persistent CTAs.  Each thread
-// computes its cell's features; the CTA evaluates the network on the tensor
-// cores; a cell whose theta_hat >= 1 - tau (and whose averages are positive)
-// keeps theta_sc = 1, every other cell runs the plain limiter; every cell
-// commits its new averages.  On request it writes theta_hat and the
+// mesh in tiles of 128 consecutive cells, persistent CTAs.  The exact screen
+// (shock_screen) clears what it can; a tile holding any other cell computes
+// its features and evaluates the network on the tensor cores; a cell the
+// screen did not clear whose theta_hat >= 1 - tau (and whose averages are
+// positive) keeps theta_sc = 1, every other cell runs the plain limiter;
+// every cell commits its new averages.  On request it writes theta_hat and the
 // features.  Without a network it writes the features (training pairs),
 // runs the plain limiter everywhere and touches no tensor-core state.  If a
 // device wait gives up, the CTA flags LXW_ST_TIMEOUT and runs the plain
@@ -1257,14 +1312,18 @@ __global__ void __launch_bounds__(kGateRows, 4) k_shock_gate_mx(const DevMesh m,
   unsigned long long skipped = 0;
   for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
     const int i = t * kGateRows + tid;
+    // the network rules only on tiles holding a cell the exact screen cannot clear
+    const bool clr = i < N && shock_screen_at<KD, ML>(m, w, state, a, i);
+    bool need_net = __syncthreads_or(i < N && !clr) != 0;
+    if (a.gate_out || a.feat_out) need_net = true;          // inspection: every cell's theta_hat / features
     float f[kMlpIn];
-    const bool ok = i < N && gate_features<E, ML>(m, w, state, a, i, f);
+    const bool ok = need_net && i < N && gate_features<E, ML>(m, w, state, a, i, f);
     if (ok && a.feat_out) {
 #pragma unroll
       for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
     }
     bool sk = false;
-    if (!abort) {
+    if (need_net && !abort) {
       // this cell's features, BF16, as row tid of X (4 core matrices along K)
 #pragma unroll
       for (int kb = 0; kb < kGateK1 / 8; ++kb) {
@@ -1291,7 +1350,7 @@ __global__ void __launch_bounds__(kGateRows, 4) k_shock_gate_mx(const DevMesh m,
       mpending = true;
       abort = __syncthreads_or(!mbar_wait(mbar, phase)) != 0;
     }
-    if (!abort) {
+    if (need_net && !abort) {
       mpending = false;
       phase ^= 1u;
       tc_fence_after();
@@ -1322,7 +1381,7 @@ __global__ void __launch_bounds__(kGateRows, 4) k_shock_gate_mx(const DevMesh m,
       mpending = true;
       abort = __syncthreads_or(!mbar_wait(mbar, phase)) != 0;
     }
-    if (!abort) {
+    if (need_net && !abort) {
       mpending = false;
       phase ^= 1u;
       tc_fence_after();
@@ -1336,11 +1395,12 @@ __global__ void __launch_bounds__(kGateRows, 4) k_shock_gate_mx(const DevMesh m,
       }
       tc_fence_before();                   // these TMEM reads precede the next tile's MMAs
       const float th_hat = 1.0f / (1.0f + __expf(-z));
-      sk = ok && th_hat >= 1.0f - a.mlp_tau;
+      sk = ok && !clr && th_hat >= 1.0f - a.mlp_tau;
       if (ok && a.gate_out) a.gate_out[i] = th_hat;
     }
     skipped += __popc(__ballot_sync(0xffffffffu, sk));
-    if (i < N) shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, 1, i, sk);
+    // a cell the screen cleared keeps theta = 1 exactly as the limiter would
+    if (i < N) shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, 1, i, sk || clr);
   }
   if (abort && tid == 0) {
     // flag it, then give the copy / MMAs in flight one more bounded wait
