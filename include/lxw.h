@@ -73,7 +73,10 @@ typedef struct {
                                (0 = 128; at most 128)                          */
   int ctas_per_sm;          /* mixed form: persistent CTAs per SM looping over the
                                work list (0 = one CTA per tile)                 */
-  int reserved[8];
+  int high_occupancy;       /* mixed form: 1 = the edge and gated-shock kernels'
+                               variants with more resident CTAs per SM (fewer
+                               registers), faster on large meshes (0 default)  */
+  int reserved[7];
 } lxw_options;
 
 /* Per-step diagnostics (filled when a non-NULL pointer is passed). */
@@ -156,11 +159,12 @@ lxw_status lxw_batch_create(int nmesh, const lxw_mesh* const* meshes, int degree
 lxw_status lxw_batch_scalars(lxw_solver* s, int* nprob, double* s_host, double* dt_host);
 /* Autotuner: times `reps` steps of each candidate (elements per CTA in
  * {32, 64, 128} x persistent CTAs per SM in {0 (one per tile), 1, 2, 3, 4,
- * 6, 8}; FP64 solvers: elements per CTA only) on a scratch copy of
+ * 6, 8} x high_occupancy in {0, 1}; FP64 solvers: elements per CTA only)
+ * on a scratch copy of
  * state_dev (restored afterwards), keeps the fastest in the solver and
  * returns it (output pointers nullable).  Allocates a scratch state. */
 lxw_status lxw_autotune(lxw_solver* s, void* state_dev, double cfl, int reps, int* block_threads,
-                        int* ctas_per_sm, float* best_ms);
+                        int* ctas_per_sm, float* best_ms, int* high_occupancy);
 
 /* Physical coordinates of the initial-condition projection points
  * xy_host[N][nproj][2] (Gauss rule with degree+3 points per direction). */

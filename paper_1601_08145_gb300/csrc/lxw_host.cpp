@@ -269,7 +269,7 @@ struct lxw_solver {
   int4* d_tiles = nullptr;       // work list (owned through allocs)
   GateWeights* gate_buf = nullptr;  // gate weights (owned), allocated by the first lxw_solver_set_mlp
   const GateWeights* mlp_w = nullptr;  // gate_buf while a network is attached, else null
-  int gate_per_sm = 1;                 // resident gate CTAs per SM (queried when the first network is attached)
+  int gate_per_sm[2] = {1, 1};         // resident gate CTAs per SM of each variant (queried when a network is attached)
   float mlp_tau = 0.0f;
   int tiles_cap = 0;
   int sms = 0;
@@ -412,6 +412,8 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
   if (opt.block_threads % 32 || opt.block_threads > 128)
     return fail(LXW_ERR_ARG, "lxw_solver_create: block_threads must be a multiple of 32, at most 128");
   if (opt.ctas_per_sm < 0 || opt.ctas_per_sm > 32) return fail(LXW_ERR_ARG, "lxw_solver_create: ctas_per_sm must be in [0, 32]");
+  if (opt.high_occupancy != 0 && opt.high_occupancy != 1)
+    return fail(LXW_ERR_ARG, "lxw_solver_create: high_occupancy must be 0 or 1");
   lxw_solver* s = new (std::nothrow) lxw_solver;
   if (!s) return fail(LXW_ERR_NOMEM, "lxw_solver_create: out of memory");
   s->kind = mesh->kind; s->deg = degree; s->N = mesh->N; s->E = mesh->E; s->opt = opt;
@@ -661,7 +663,8 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   a.gamma_f = (float)a.gamma; a.eps0_f = (float)a.eps0; a.alpha0_f = (float)a.alpha0;
   a.grid = s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm * s->sms : 0;   // persistent CTAs, or one per tile
   a.sms = s->sms;
-  a.gate_per_sm = s->gate_per_sm;
+  a.hi_occupancy = s->opt.high_occupancy;
+  a.gate_per_sm = s->gate_per_sm[s->opt.high_occupancy ? 1 : 0];
   a.gate_w = s->mlp_w; a.mlp_tau = s->mlp_tau; a.feat_out = nullptr; a.gate_out = nullptr;
   return a;
 }
@@ -873,9 +876,11 @@ lxw_status lxw_solver_set_mlp(lxw_solver* s, lxw_mlp* mlp, float tau) {
     s->gate_buf = (GateWeights*)p;
   }
   if (mlp_gate_weights(mlp, s->gate_buf)) return fail(LXW_ERR_CUDA, "lxw_solver_set_mlp: weight layout failed");
-  const int occ = gate_occupancy(s->kind, s->deg);
-  if (occ < 1) return fail(LXW_ERR_CUDA, "lxw_solver_set_mlp: the gate kernel does not fit on this device");
-  s->gate_per_sm = occ;
+  for (int hi = 0; hi < 2; ++hi) {
+    const int occ = gate_occupancy(s->kind, s->deg, hi);
+    if (occ < 1) return fail(LXW_ERR_CUDA, "lxw_solver_set_mlp: the gate kernel does not fit on this device");
+    s->gate_per_sm[hi] = occ;
+  }
   s->mlp_w = s->gate_buf;
   s->mlp_tau = tau;
   return LXW_OK;
@@ -921,7 +926,8 @@ static void drop_graphs(lxw_solver* s) {
   if (s->pgraph) { cudaGraphExecDestroy(s->pgraph); s->pgraph = nullptr; }
 }
 
-lxw_status lxw_autotune(lxw_solver* s, void* state, double cfl, int reps, int* bt, int* cps, float* best_ms) {
+lxw_status lxw_autotune(lxw_solver* s, void* state, double cfl, int reps, int* bt, int* cps, float* best_ms,
+                        int* hiocc) {
   if (!s || !state || !(cfl > 0.0) || reps < 1) return fail(LXW_ERR_ARG, "lxw_autotune: bad argument");
   const size_t bytes = lxw_state_bytes(s);
   void* save = nullptr;
@@ -932,13 +938,14 @@ lxw_status lxw_autotune(lxw_solver* s, void* state, double cfl, int reps, int* b
   const int ctas[7] = {0, 1, 2, 3, 4, 6, 8};
   const lxw_options keep = s->opt;
   float best = 1e30f;
-  int bb = keep.block_threads, bc = keep.ctas_per_sm;
+  int bb = keep.block_threads, bc = keep.ctas_per_sm, bh = keep.high_occupancy;
   lxw_status st = LXW_OK;
   float ms[8];
+  for (int hi = 0; hi < (s->mixed ? 2 : 1) && st == LXW_OK; ++hi)
   for (int b : blocks) {
     for (int c : ctas) {
       if (!s->mixed && c != 0) continue;
-      s->opt.block_threads = b; s->opt.ctas_per_sm = c;
+      s->opt.block_threads = b; s->opt.ctas_per_sm = c; s->opt.high_occupancy = hi;
       drop_graphs(s);
       if ((st = build_tiles(s)) != LXW_OK) break;
       cudaMemcpy(state, save, bytes, cudaMemcpyDeviceToDevice);
@@ -949,11 +956,11 @@ lxw_status lxw_autotune(lxw_solver* s, void* state, double cfl, int reps, int* b
         for (int k = 0; k < phases_of(s); ++k) tot += ms[k];
       }
       if (st != LXW_OK) break;
-      if (tot / reps < best) { best = tot / reps; bb = b; bc = c; }
+      if (tot / reps < best) { best = tot / reps; bb = b; bc = c; bh = hi; }
     }
     if (st != LXW_OK) break;
   }
-  s->opt.block_threads = bb; s->opt.ctas_per_sm = bc;
+  s->opt.block_threads = bb; s->opt.ctas_per_sm = bc; s->opt.high_occupancy = bh;
   drop_graphs(s);
   lxw_status tst = build_tiles(s);
   cudaMemcpy(state, save, bytes, cudaMemcpyDeviceToDevice);
@@ -963,6 +970,7 @@ lxw_status lxw_autotune(lxw_solver* s, void* state, double cfl, int reps, int* b
   if (bt) *bt = bb;
   if (cps) *cps = bc;
   if (best_ms) *best_ms = best;
+  if (hiocc) *hiocc = bh;
   return LXW_OK;
 }
 

@@ -128,6 +128,7 @@ struct StepArgs {
   float gamma_f, eps0_f, alpha0_f;   // FP32 copies for the mixed form
   int sms;                           // SMs of the device
   int gate_per_sm;                   // resident CTAs per SM of the gated shock kernel (its persistent grid)
+  int hi_occupancy;                  // mixed form: the edge / gated-shock variants with more CTAs per SM
   const GateWeights* gate_w;         // learned gate weights or null
   float mlp_tau;                     // gate: skip the limiter where theta_hat >= 1 - tau
   float* feat_out;                   // [N][24] features at the shock limiter's input, or null
@@ -176,7 +177,7 @@ struct DerivTables {
 void make_deriv_tables(const Tables& t, DerivTables& d);
 int upload_tables_mx(int kind, int deg, const Tables& t);
 // resident CTAs per SM of the gate kernel for (kind, deg), capped by TMEM; < 0 on error
-int gate_occupancy(int kind, int deg);
+int gate_occupancy(int kind, int deg, int hi_occupancy);
 int launch_step_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state,
                    const StepArgs& a, void* stream, int block, void** events = nullptr, int upto = 99);
 int launch_moment_limit_mx(int kind, int deg, const DevMesh& m, const DevWorkMx& w, double* state,

@@ -827,8 +827,10 @@ __device__ __forceinline__ void edge_elem(const DevMesh& m, const DevWorkMx& w, 
   }
 }
 
-template <int KD, int E, int ML, int NQ, int MQ>
-__global__ void __launch_bounds__(128, ML == 6 ? 4 : 3) k_edge_mx(const DevMesh m, const DevWorkMx w,
+// HI: the variant with more resident CTAs per SM (fewer registers, some
+// spills), which pays on large meshes; the autotuner chooses
+template <int KD, int E, int ML, int NQ, int MQ, bool HI>
+__global__ void __launch_bounds__(128, ML == 6 ? (HI ? 5 : 4) : 3) k_edge_mx(const DevMesh m, const DevWorkMx w,
                                                                   double* __restrict__ state, const StepArgs a) {
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
@@ -1259,8 +1261,8 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
 // runs the plain limiter everywhere and touches no tensor-core state.  If a
 // device wait gives up, the CTA flags LXW_ST_TIMEOUT and runs the plain
 // limiter on the rest of its cells.
-template <int KD, int E, int ML, int NQ, int MQ>
-__global__ void __launch_bounds__(kGateRows, 4) k_shock_gate_mx(const DevMesh m, const DevWorkMx w,
+template <int KD, int E, int ML, int NQ, int MQ, bool HI>
+__global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const DevMesh m, const DevWorkMx w,
                                                              double* __restrict__ state, const StepArgs a,
                                                              double* __restrict__ theta_out) {
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -1538,7 +1540,10 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
   k_ck_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a);
   mark();
   if (upto < 3) return ok();
-  k_edge_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a);
+  if (a.hi_occupancy)
+    k_edge_mx<KD, E, ML, NQ, MQ, true><<<grid, block, 0, st>>>(m, w, state, a);
+  else
+    k_edge_mx<KD, E, ML, NQ, MQ, false><<<grid, block, 0, st>>>(m, w, state, a);
   mark();
   if (upto < 4) return ok();
   k_update_mx<E, ML><<<grid, block, 0, st>>>(m, w, state, a);
@@ -1550,7 +1555,11 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
     // columns: a.gate_per_sm of them per SM (resident by occupancy, <= 8)
     const int ntile = (m.N + kGateRows - 1) / kGateRows;
     const int gg = std::max(1, std::min(ntile, std::max(a.gate_per_sm, 1) * std::max(a.sms, 1)));
-    k_shock_gate_mx<KD, E, ML, NQ, MQ><<<gg, kGateRows, a.gate_w ? sizeof(GateTile) : 0, st>>>(m, w, state, a, tsc);
+    const size_t smem = a.gate_w ? sizeof(GateTile) : 0;
+    if (a.hi_occupancy)
+      k_shock_gate_mx<KD, E, ML, NQ, MQ, true><<<gg, kGateRows, smem, st>>>(m, w, state, a, tsc);
+    else
+      k_shock_gate_mx<KD, E, ML, NQ, MQ, false><<<gg, kGateRows, smem, st>>>(m, w, state, a, tsc);
   } else {
     k_shock_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, tsc, limit);
   }
@@ -1582,9 +1591,9 @@ int moment_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const St
 // Resident CTAs per SM of the gate kernel from its registers, shared memory
 // and threads (the limits the hardware applies), capped by the 512 TMEM
 // columns of an SM.  The shared-memory carveout is set to its maximum first.
-template <int KD, int E, int ML, int NQ, int MQ>
+template <int KD, int E, int ML, int NQ, int MQ, bool HI>
 int gate_occupancy_impl() {
-  auto fn = k_shock_gate_mx<KD, E, ML, NQ, MQ>;
+  auto fn = k_shock_gate_mx<KD, E, ML, NQ, MQ, HI>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
       cudaSuccess)
     return -1;
@@ -1603,8 +1612,9 @@ int gate_occupancy_impl() {
   return std::min(n, 512 / kGateTmemCols);
 }
 
-int gate_occupancy(int kind, int deg) {
-#define CALL_GOC(KD, E, ML, NQ, MQ) gate_occupancy_impl<KD, E, ML, NQ, MQ>()
+int gate_occupancy(int kind, int deg, int hi) {
+#define CALL_GOC(KD, E, ML, NQ, MQ) \
+  (hi ? gate_occupancy_impl<KD, E, ML, NQ, MQ, true>() : gate_occupancy_impl<KD, E, ML, NQ, MQ, false>())
   LXW_DISPATCH_MX(kind, deg, CALL_GOC);
 #undef CALL_GOC
 }

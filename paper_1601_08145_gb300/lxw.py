@@ -39,7 +39,7 @@ EXPORTS = [
 class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("eps0", C.c_double), ("alpha0", C.c_double),
                 ("shock_limiter", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
-                ("ctas_per_sm", C.c_int), ("reserved", C.c_int * 8)]
+                ("ctas_per_sm", C.c_int), ("high_occupancy", C.c_int), ("reserved", C.c_int * 7)]
 
 
 class Diag(C.Structure):
@@ -100,7 +100,8 @@ def lib():
     L.lxw_fma_peak.argtypes = [C.c_int, _dp]
     L.lxw_batch_create.argtypes = [C.c_int, C.POINTER(_vp), C.c_int, C.POINTER(Options), _vp, C.POINTER(_vp)]
     L.lxw_batch_scalars.argtypes = [_vp, C.POINTER(C.c_int), _dp, _dp]
-    L.lxw_autotune.argtypes = [_vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    L.lxw_autotune.argtypes = [_vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                               C.POINTER(C.c_float), C.POINTER(C.c_int)]
     L.lxw_mlp_create.argtypes = [C.c_int, C.c_ulonglong, _vp, C.POINTER(_vp)]
     L.lxw_mlp_destroy.argtypes = [_vp]
     L.lxw_mlp_destroy.restype = None
@@ -375,10 +376,10 @@ def lxw_batch_scalars(solver):
 
 
 def lxw_autotune(solver, state, cfl, reps=5):
-    b = C.c_int(); c = C.c_int(); ms = C.c_float()
+    b = C.c_int(); c = C.c_int(); ms = C.c_float(); hi = C.c_int()
     _check(lib().lxw_autotune(solver.h, _ptr(state, solver.state_shape, "state"), cfl, reps,
-                              C.byref(b), C.byref(c), C.byref(ms)))
-    return {"block_threads": b.value, "ctas_per_sm": c.value, "ms_per_step": ms.value}
+                              C.byref(b), C.byref(c), C.byref(ms), C.byref(hi)))
+    return {"block_threads": b.value, "ctas_per_sm": c.value, "high_occupancy": hi.value, "ms_per_step": ms.value}
 
 
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 24, 64, 5825

@@ -40,10 +40,12 @@ def projected(L, sol, ic):
     return Q
 
 
-@pytest.mark.parametrize("ctas,block", [(0, 128), (2, 128), (1, 64), (3, 32)])
-def test_batch_equals_individual_runs(L, ctas, block):
+@pytest.mark.parametrize("ctas,block,hi", [(0, 128, 0), (2, 128, 0), (1, 64, 1), (3, 32, 0)])
+def test_batch_equals_individual_runs(L, ctas, block, hi):
+    """hi: the high-occupancy kernel variants in the batch against the default
+    variants one by one (the same arithmetic, other register budgets)."""
     sizes = [7, 13, 24, 5, 31]
-    opt = L.lxw_options_default(precision=L.PREC_MIXED, ctas_per_sm=ctas, block_threads=block)
+    opt = L.lxw_options_default(precision=L.PREC_MIXED, ctas_per_sm=ctas, block_threads=block, high_occupancy=hi)
     probs = [quadrant_problem(L, n, 100 + k) for k, n in enumerate(sizes)]
     # individual solvers
     singles = []
@@ -84,6 +86,7 @@ def test_autotune_keeps_results_and_restores_state(L):
     torch.cuda.synchronize()
     assert torch.equal(B, L.new_state(b, Q))              # restored
     assert res["block_threads"] in (32, 64, 128) and res["ctas_per_sm"] in (0, 1, 2, 3, 4, 6, 8)
+    assert res["high_occupancy"] in (0, 1)
     L.lxw_run(b, B, 5, 0.3)
     torch.cuda.synchronize()
     assert torch.equal(A, B)                              # the tuned configuration computes the same state
