@@ -43,6 +43,8 @@ WORKLOADS = {
                   desc="blast: 1024x1024 Cartesian, P2, point energy 0.979264 in the 4 centre cells, reflective"),
     "smooth": dict(kind="quad", n=32, deg=2, cfl=0.1, ic=synth.ic_smooth,
                    desc="smooth: 32x32 periodic Cartesian, P2, advected density wave"),
+    "rarefy_p3": dict(kind="tri", n=224, deg=3, cfl=0.1, ic=synth.ic_rarefy,
+                      desc="rarefaction: 224x224x2 = 100,352 jittered triangles, P3, rho=1 p=0.4 u=-+2, transparent"),
     "rarefy1m": dict(kind="tri", n=724, deg=2, cfl=0.1, ic=synth.ic_rarefy,
                      desc="rarefaction: 724x724x2 = 1,048,352 jittered triangles, P2, rho=1 p=0.4 u=-+2, transparent"),
     "blast2048": dict(kind="quad", n=2048, deg=2, cfl=0.1, ic=None, bc=(1, 1, 1, 1), box=(-1.1, 1.1, -1.1, 1.1),

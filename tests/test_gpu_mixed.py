@@ -189,15 +189,15 @@ def test_status_is_kept_until_a_diagnostic_step_reads_it(L):
     assert L.lxw_step_launches(s) == 5 and L.lxw_profile_phases(s) == 5
 
 
-@pytest.mark.parametrize("kind,n", [(TRI, 224), (QUAD, 1024), (QUAD, 2048)])
-def test_full_size_one_mixed_step_against_oracle(L, O, kind, n):
-    """The benchmark sizes (100,352 triangles; 1024^2 and 2048^2 squares), in
+@pytest.mark.parametrize("kind,n,deg", [(TRI, 224, 2), (TRI, 224, 3), (QUAD, 1024, 2), (QUAD, 2048, 2)])
+def test_full_size_one_mixed_step_against_oracle(L, O, kind, n, deg):
+    """The benchmark sizes (100,352 triangles, P2 and P3; 1024^2 and 2048^2 squares), in
     the launch configuration the autotuner picks for them, from a random
     near-vacuum state with every limiter active: one mixed step against the
     oracle's step, element by element within the FP32 budget, and positive."""
     bc = 2
-    s = solver(L, kind, 2, n, bc=(bc,) * 4, tri_bc=bc if kind == TRI else None)
-    so = oracle_solver(O, kind, 2, n, bc=(bc,) * 4, tri_bc=bc if kind == TRI else None)
+    s = solver(L, kind, deg, n, bc=(bc,) * 4, tri_bc=bc if kind == TRI else None)
+    so = oracle_solver(O, kind, deg, n, bc=(bc,) * 4, tri_bc=bc if kind == TRI else None)
     Q0 = synth.random_modal_state(s.N, s.ML, seed=77 + n, amp=0.3, rho_range=(0.01, 3.0), p_range=(0.001, 3.0))
     Q0[:, :, 1:] = Q0[:, :, 1:].astype(np.float32)
     scratch = L.new_state(s, torch.from_numpy(Q0).cuda())
