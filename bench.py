@@ -202,8 +202,19 @@ def cpu_baseline(name, budget_s=10.0):
         s.step(Q, cfl=w["cfl"]); k += 1
     dt = time.perf_counter() - t0
     dof = s.N * 4 * s.ML
-    return {"value": dof * k / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{k} full steps of the {name} workload ({s.N} elements) from its initial data, {dt:.1f} s"}, k, dt
+    out = {"value": dof * k / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+           "sample": f"{k} full steps of the {name} workload ({s.N} elements) from its initial data, {dt:.1f} s"}
+    # the same oracle on one core: the reference arm in a child process with one OpenMP thread
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1", RANK="0", WORLD_SIZE="1")
+        r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", name,
+                            "--steps", "3", "--warmup", "1"], env=env, capture_output=True, text=True, timeout=600)
+        one = json.loads(r.stdout.strip().splitlines()[-1])
+        out["one_core"] = {"value": one["value"], "cores": one["cpu_baseline"]["cores"],
+                           "sample": "3 full steps after 1 warm-up step, OMP_NUM_THREADS=1"}
+    except Exception as e:   # the multi-core number stands on its own
+        out["one_core"] = {"value": None, "error": str(e)[:200]}
+    return out, k, dt
 
 
 def run_reference(args):
@@ -364,8 +375,8 @@ def smooth_l1_error(L, stream, mixed, net=None, tau=0.02):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rarefy", choices=sorted(WORKLOADS) + ["ensemble"])
     ap.add_argument("--tau", type=float, default=0.02, help="learned gate: skip where theta_hat >= 1 - tau")
