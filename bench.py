@@ -77,7 +77,10 @@ CK_MX_TRAFFIC_BYTES = 13766400   # k_ck_mx DRAM read + write per launch, rarefac
 
 
 def build_workload(L, name, stream, mixed):
-    w = WORKLOADS[name]
+    return build_solver(L, WORKLOADS[name], stream, mixed)
+
+
+def build_solver(L, w, stream, mixed):
     if w["kind"] == "tri":
         xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
         mesh = L.lxw_mesh_triangles(xy, tv)
@@ -372,6 +375,102 @@ def smooth_l1_error(L, stream, mixed, net=None, tau=0.02):
     return {"l1": l1, "l2": l2, "t": t, "steps": steps, "gate_skipped_cell_steps": skipped}
 
 
+def run_to(L, sol, Q, T, cfl):
+    """Steps with dt from the CFL rule until t = T, the last one shortened;
+    returns the number of steps."""
+    t, dt_last, k = 0.0, None, 0
+    while t < T * (1.0 - 1e-13):
+        dt = T - t if dt_last is not None and t + 1.05 * dt_last >= T else 0.0
+        d = L.lxw_step(sol, Q, dt, cfl, diag=True)
+        t += d["dt"]; dt_last = d["dt"]; k += 1
+    return k
+
+
+def locate(w, nc, pts):
+    """Element of the half-resolution mesh (nc x nc squares, or their 2 nc^2
+    triangles with the same jitter rule) holding each point, and the point's
+    reference coordinates there."""
+    x0, x1, y0, y1 = w.get("box", (0.0, 1.0, 0.0, 1.0))
+    hx, hy = (x1 - x0) / nc, (y1 - y0) / nc
+    x, y = pts[:, 0], pts[:, 1]
+    ix = np.clip(np.floor((x - x0) / hx).astype(np.int64), 0, nc - 1)
+    iy = np.clip(np.floor((y - y0) / hy).astype(np.int64), 0, nc - 1)
+    if w["kind"] == "quad":
+        ref = np.stack([2.0 * ((x - x0) / hx - ix) - 1.0, 2.0 * ((y - y0) / hy - iy) - 1.0], axis=1)
+        return iy * nc + ix, ref
+    xy, tv = synth.structured_triangles(nc, jitter=0.2, seed=20160129, box=(x0, x1, y0, y1))
+    best = np.full(len(x), -1, dtype=np.int64)
+    bmin = np.full(len(x), -np.inf)
+    bref = np.zeros((len(x), 2))
+    # vertices move by at most 0.2 h: the point lies in a triangle of the 3 x 3 squares around it
+    for dj in (-1, 0, 1):
+        for di in (-1, 0, 1):
+            si, sj = ix + di, iy + dj
+            ok = (si >= 0) & (si < nc) & (sj >= 0) & (sj < nc)
+            for half in (0, 1):
+                t = np.where(ok, 2 * (np.clip(sj, 0, nc - 1) * nc + np.clip(si, 0, nc - 1)) + half, 0)
+                v0, v1, v2 = xy[tv[t, 0]], xy[tv[t, 1]], xy[tv[t, 2]]
+                ax, ay, bx, by = v1[:, 0] - v0[:, 0], v1[:, 1] - v0[:, 1], v2[:, 0] - v0[:, 0], v2[:, 1] - v0[:, 1]
+                det = ax * by - ay * bx
+                px, py = x - v0[:, 0], y - v0[:, 1]
+                xi = (px * by - py * bx) / det
+                eta = (ax * py - ay * px) / det
+                lm = np.minimum(np.minimum(xi, eta), 1.0 - xi - eta)
+                upd = ok & (lm > bmin)
+                best = np.where(upd, t, best); bmin = np.where(upd, lm, bmin)
+                bref[upd] = np.stack([xi[upd], eta[upd]], axis=1)
+    assert np.all(bmin > -1e-9), "a point outside the coarse mesh"
+    return best, bref
+
+
+def discretization_check(L, stream, name, net, tau, steps):
+    """How 'equal' the errors are where no exact solution exists: the L1
+    distance (density cell averages, area-weighted) of the mixed + learned
+    result from the FP64 result at the same time, against the FP64 form's
+    discretization-error estimate || u_N - P(u_{N/2}) ||_L1, P the L2
+    projection of the half-resolution solution onto the fine elements."""
+    import torch
+    w = WORKLOADS[name]
+    _, sf = build_workload(L, name, stream, False)
+    Qf = project(L, sf, w)
+    T = 0.0
+    for _ in range(steps):
+        T += L.lxw_step(sf, Qf, 0.0, w["cfl"], diag=True)["dt"]
+    _, sm = build_workload(L, name, stream, True)
+    L.lxw_solver_set_mlp(sm, net, tau)
+    Qm = project(L, sm, w)
+    km = run_to(L, sm, Qm, T, w["cfl"])
+    nc = w["n"] // 2
+    wc = dict(w, n=nc)
+    _, sc = build_solver(L, wc, stream, False)
+    Qc = project(L, sc, wc)
+    kc = run_to(L, sc, Qc, T, w["cfl"])
+    # the coarse density at the fine projection points, projected onto the fine elements
+    pts = L.lxw_projection_points(sf)
+    N, npj = pts.shape[0], pts.shape[1]
+    elem, ref = locate(w, nc, pts.reshape(-1, 2))
+    phi = L.lxw_basis_eval(0 if w["kind"] == "quad" else 1, w["deg"], ref)
+    rc = np.einsum("pl,pl->p", Qc[:, 0, :].cpu().numpy()[elem], phi).reshape(N, npj)
+    prim = np.stack([rc, np.zeros_like(rc), np.zeros_like(rc), np.ones_like(rc)], axis=-1)
+    Qp = torch.zeros(sf.q64_shape, dtype=torch.float64, device="cuda")
+    L.lxw_project(sf, torch.from_numpy(np.ascontiguousarray(prim)).cuda(), Qp)
+    rho_f = Qf[:, 0, 0].cpu().numpy()
+    rho_p = Qp[:, 0, 0].cpu().numpy()
+    rho_m = L.to_q64(sm, Qm)[:, 0, 0].cpu().numpy()
+    if w["kind"] == "quad":
+        area = np.full(N, 1.0 / N)
+    else:
+        xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
+        v0, v1, v2 = xy[tv[:, 0]], xy[tv[:, 1]], xy[tv[:, 2]]
+        area = 0.5 * np.abs((v1[:, 0] - v0[:, 0]) * (v2[:, 1] - v0[:, 1]) - (v1[:, 1] - v0[:, 1]) * (v2[:, 0] - v0[:, 0]))
+    e = float(np.sum(area * np.abs(rho_f - rho_p)))
+    dist = float(np.sum(area * np.abs(rho_m - rho_f)))
+    return {"t": T, "steps_fine": steps, "steps_mixed_learned": km, "steps_coarse": kc, "coarse_elements": sc.N,
+            "l1_fp64_minus_projected_coarse": e, "l1_mixed_learned_minus_fp64": dist, "ratio": dist / e,
+            "target_ratio_at_most": 0.1,
+            "norm": "sum over fine elements of |T_i| |rho_avg difference| (density cell averages)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,6 +614,8 @@ def main():
     # "at equal L1 error": the three forms against the exact smooth solution
     acc = {"fp64": smooth_l1_error(L, stream, False), "mixed": smooth_l1_error(L, stream, True),
            "mixed_learned": smooth_l1_error(L, stream, True, net=net, tau=args.tau)}
+    disc = (discretization_check(L, stream, args.workload, net, args.tau, min(args.steps, 100))
+            if args.workload != "smooth" else None)
     acc["ratio_l1_mixed_learned_vs_fp64"] = acc["mixed_learned"]["l1"] / acc["fp64"]["l1"]
     acc["ratio_l2_mixed_learned_vs_fp64"] = acc["mixed_learned"]["l2"] / acc["fp64"]["l2"]
     acc["config"] = (WORKLOADS["smooth"]["desc"] + ", CFL 0.1, to t = 0.1; l1: cell-average density, "
@@ -573,7 +674,8 @@ def main():
            "mixed_fp64_path_cells": {"moment": dmx["n_fp64_moment"], "flux_limiter": dmx["n_fp64_edge"],
                                      "of": sol.N},
            "l1_rel_density_vs_fp64": dist_learned,
-           "smooth_l1_error": acc}
+           "smooth_l1_error": acc,
+           "discretization_check": disc}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], _, _ = cpu_baseline(args.workload)
     print(json.dumps(out))

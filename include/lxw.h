@@ -169,6 +169,14 @@ lxw_status lxw_autotune(lxw_solver* s, void* state_dev, double cfl, int reps, in
 /* Physical coordinates of the initial-condition projection points
  * xy_host[N][nproj][2] (Gauss rule with degree+3 points per direction). */
 lxw_status lxw_projection_points(const lxw_solver* s, double* xy_host);
+/* Values of the modal basis phi^(l) (Sec. 1.2; the mode order of the state
+ * layout above) at points of the reference element: ref_xy_host[n][2] in
+ * [-1,1]^2 (quadrilaterals; x = x_c + xi dx/2, y = y_c + eta dy/2) or in
+ * {xi, eta >= 0, xi + eta <= 1} (triangles; x = v0 + (v1 - v0) xi +
+ * (v2 - v0) eta), written to phi_host[n][ML].  Host only, synchronous, no
+ * device work: a post-processing aid (q^h at any point is sum_l Q^(l)
+ * phi^(l) of the element holding it).  Errors: LXW_ERR_ARG. */
+lxw_status lxw_basis_eval(int kind, int degree, int n, const double* ref_xy_host, double* phi_host);
 /* L2 projection Q^(l) = (1/|T0|) Int q phi^(l) (Sec. 1.2) of primitive values
  * prim_dev[N][nproj][4] = (rho, u, v, p) at the projection points into
  * Q_dev[N][4][ML]; the energy follows Eq. eos.  Asynchronous on the stream. */

@@ -650,6 +650,17 @@ lxw_status lxw_projection_points(const lxw_solver* s, double* xy) {
   return LXW_OK;
 }
 
+lxw_status lxw_basis_eval(int kind, int degree, int n, const double* ref_xy, double* phi) {
+  if ((kind != LXW_KIND_QUAD && kind != LXW_KIND_TRI) || (degree != 2 && degree != 3) || n < 0 ||
+      (n > 0 && (!ref_xy || !phi)))
+    return fail(LXW_ERR_ARG, "lxw_basis_eval: bad argument");
+  const int ML = (degree + 1) * (degree + 2) / 2;
+  const TriBasis tb = kind == LXW_KIND_TRI ? triangle_basis(ML) : TriBasis{};
+  for (int k = 0; k < n; ++k)
+    basis_at(kind, ML, tb, ref_xy[2 * k], ref_xy[2 * k + 1], phi + (size_t)k * ML, nullptr, nullptr);
+  return LXW_OK;
+}
+
 lxw_status lxw_project(lxw_solver* s, const double* prim, double* Q) {
   if (!s || !prim || !Q) return fail(LXW_ERR_ARG, "lxw_project: null argument");
   if (launch_project(s->ptab, s->N, s->opt.gamma, prim, Q, s->stream)) return fail(LXW_ERR_CUDA, "lxw_project: launch failed");

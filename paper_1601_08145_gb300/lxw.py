@@ -32,7 +32,7 @@ EXPORTS = [
     "lxw_batch_create", "lxw_batch_scalars", "lxw_autotune",
     "lxw_mlp_create", "lxw_mlp_destroy", "lxw_mlp_num_params", "lxw_mlp_get_params", "lxw_mlp_set_params",
     "lxw_mlp_forward", "lxw_mlp_loss_grad", "lxw_mlp_train", "lxw_solver_set_mlp", "lxw_step_dump",
-    "lxw_step_gate", "lxw_profile_phases",
+    "lxw_step_gate", "lxw_profile_phases", "lxw_basis_eval",
 ]
 
 
@@ -94,6 +94,7 @@ def lib():
     L.lxw_shock_limit.argtypes = [_vp, _vp, _vp]
     L.lxw_step_launches.argtypes = [_vp]
     L.lxw_profile_phases.argtypes = [_vp]
+    L.lxw_basis_eval.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp]
     L.lxw_profile_step.argtypes = [_vp, _vp, C.c_double, C.POINTER(C.c_float)]
     L.lxw_step_phases.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int]
     L.lxw_workspace_copy.argtypes = [_vp, C.c_int, _dp, C.c_size_t]
@@ -226,6 +227,15 @@ def lxw_projection_points(solver):
     xy = np.zeros((solver.N, solver.nproj, 2))
     _check(lib().lxw_projection_points(solver.h, xy.ctypes.data_as(_dp)))
     return xy
+
+
+def lxw_basis_eval(kind, degree, ref_xy):
+    """Basis values [n][ML] at reference points ref_xy[n][2] (host, numpy)."""
+    ref = np.ascontiguousarray(ref_xy, dtype=np.float64).reshape(-1, 2)
+    ML = (degree + 1) * (degree + 2) // 2
+    out = np.zeros((ref.shape[0], ML))
+    _check(lib().lxw_basis_eval(kind, degree, ref.shape[0], ref.ctypes.data_as(_dp), out.ctypes.data_as(_dp)))
+    return out
 
 
 def lxw_project(solver, prim, Q):

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -56,3 +57,22 @@ def test_host_side_errors_without_gpu(libpath):
     assert m.N == 6
     o = lxw.lxw_options_default()
     assert o.gamma == 1.4 and o.eps0 == 1e-12 and o.alpha0 == 500.0 and o.shock_limiter == 1
+
+
+@pytest.mark.parametrize("kind,deg", [(0, 2), (0, 3), (1, 2), (1, 3)])
+def test_basis_eval_matches_the_oracle_basis(kind, deg):
+    """lxw_basis_eval (host only, no GPU) against the oracle's independently
+    built basis (long-double Gram-Schmidt vs the library's Cholesky for
+    triangles) at random reference points."""
+    from oracle import oracle as orc
+    from paper_1601_08145_gb300 import lxw as L
+    rng = np.random.default_rng(3 + kind + deg)
+    if kind == 0:
+        ref = rng.uniform(-1.0, 1.0, size=(200, 2))
+    else:
+        ref = rng.uniform(0.0, 1.0, size=(400, 2))
+        ref = ref[ref.sum(axis=1) <= 1.0][:200]
+    phi = L.lxw_basis_eval(kind, deg, ref)
+    po = orc.basis_eval(kind, deg, ref[:, 0].copy(), ref[:, 1].copy())[0]
+    assert phi.shape == po.shape
+    assert np.abs(phi - po).max() < 1e-12
