@@ -304,3 +304,42 @@ def test_blast_keeps_its_fourfold_symmetry(L, mixed):
             worst = max(worst, np.abs(A - B).max() / sc)
     print(f"blast symmetry ({'mixed' if mixed else 'fp64'}): {worst:.2e}")
     assert worst < tol
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_double_rarefaction_1d_as_y_invariant_2d(L, O, mixed):
+    """The paper's 1D double rarefaction (rho 7, u -+1, p 0.2; Sec. 4.1) on
+    a 128 x 4 strip, periodic in y and transparent in x: positive at every
+    step, the y-carrying modes stay zero (y-invariance), and the result
+    matches the oracle's (FP64 1e-12; mixed within the FP32 budget)."""
+    nx, ny = 128, 4
+    bc = (2, 2, 0, 0)          # left, right transparent; bottom, top periodic
+    ic = lambda x, y: (7.0 + 0 * x, np.where(x < 0.5, -1.0, 1.0), 0 * x, 0.2 + 0 * x)
+    om = O.Mesh.cartesian(nx, ny, (0.0, 1.0, 0.0, 1.0), bc)
+    so = O.Solver(om, 2)
+    Qo = so.project_fn(ic)
+    lm = L.lxw_mesh_cartesian(nx, ny, (0.0, 1.0, 0.0, 1.0), bc)
+    o = L.lxw_options_default(precision=L.PREC_MIXED if mixed else L.PREC_FP64)
+    s = L.lxw_solver_create(lm, 2, o, stream=torch.cuda.current_stream())
+    s64 = L.lxw_solver_create(lm, 2, stream=torch.cuda.current_stream())
+    Q64 = lib_project(L, s64, ic)
+    Qg = L.new_state(s, Q64) if mixed else Q64
+    if mixed:
+        Qo[:, :, 1:] = L.to_q64(s, Qg).cpu().numpy()[:, :, 1:]      # both start from FP32 modes
+    for _ in range(200):
+        do = so.step(Qo, cfl=0.1)
+        d = L.lxw_step(s, Qg, 0.0, 0.1, diag=True)
+        assert d["status"] == 0 and d["min_rho"] > 0 and d["min_p"] > 0
+        assert do["min_rho"] > 0 and do["min_p"] > 0
+    Qh = (L.to_q64(s, Qg) if mixed else Qg).cpu().numpy()
+    # y-invariance: modes carrying eta (L1(y), L1(x)L1(y), L2(y)) and the y-momentum vanish, to
+    # round-off (FP64) or to the FP32 rounding of the modal sums relative to each variable's scale
+    scale = np.abs(Qh[:, :, 0]).max(axis=0)
+    scale[1] = scale[2] = max(scale[1], scale[2])        # both momenta on the momentum scale
+    tol = (1e-5 if mixed else 1e-14) * scale
+    for v in range(4):
+        assert np.abs(Qh[:, v, [2, 3, 5]]).max() < tol[v], v
+    assert np.abs(Qh[:, 2, :]).max() < tol.max()
+    err = rel_l1(Qh, Qo)
+    print(f"double rarefaction ({'mixed' if mixed else 'fp64'}): relative L1 vs oracle {err:.2e}")
+    assert err < (1e-4 if mixed else 1e-12)
