@@ -55,7 +55,7 @@
 #define MAXPTS (MAXQ + MAXE * MAXMQ)
 #define MAXPJ 64    /* projection points */
 
-enum { BC_PERIODIC = 0, BC_REFLECT = 1, BC_TRANSPARENT = 2 };
+enum { BC_PERIODIC = 0, BC_REFLECT = 1, BC_TRANSPARENT = 2, BC_INFLOW = 3 };
 enum { KIND_QUAD = 0, KIND_TRI = 1 };
 
 int orc_num_threads(void) {
@@ -384,38 +384,51 @@ static void mesh_edges(orc_mesh* m) {
   m->nedges = ne;
 }
 
-orc_mesh* orc_mesh_cartesian(int nx, int ny, double x0, double x1, double y0, double y1,
-                             const int* bc) {
+/* nx*ny axis-aligned cells; with a mask, the cells with mask[iy*nx+ix] == 0
+ * are left out (elements numbered in row order of the cells kept) and the
+ * faces a kept cell shares with a left-out one get the code mask_bc. */
+orc_mesh* orc_mesh_cartesian_masked(int nx, int ny, double x0, double x1, double y0, double y1, const int* bc,
+                                    const unsigned char* mask, int mask_bc) {
   if (nx < 1 || ny < 1) return NULL;
   if ((bc[0] == BC_PERIODIC) != (bc[1] == BC_PERIODIC)) return NULL;
   if ((bc[2] == BC_PERIODIC) != (bc[3] == BC_PERIODIC)) return NULL;
-  orc_mesh* m = mesh_alloc(KIND_QUAD, nx * ny);
+  int* id = malloc(sizeof(int) * (size_t)nx * ny);
+  int N = 0;
+  for (int c = 0; c < nx * ny; ++c) id[c] = (!mask || mask[c]) ? N++ : -1;
+  if (N < 1) { free(id); return NULL; }
+  orc_mesh* m = mesh_alloc(KIND_QUAD, N);
   double* X = malloc(sizeof(double) * (nx + 1));
   double* Y = malloc(sizeof(double) * (ny + 1));
   for (int i = 0; i <= nx; ++i) X[i] = x0 + (x1 - x0) * i / nx;
   for (int j = 0; j <= ny; ++j) Y[j] = y0 + (y1 - y0) * j / ny;
   for (int iy = 0; iy < ny; ++iy)
     for (int ix = 0; ix < nx; ++ix) {
-      int i = iy * nx + ix;
+      int c = iy * nx + ix, i = id[c];
+      if (i < 0) continue;
       double* v = m->vx + (size_t)i * 8;
       v[0] = X[ix]; v[1] = Y[iy]; v[2] = X[ix + 1]; v[3] = Y[iy];
       v[4] = X[ix + 1]; v[5] = Y[iy + 1]; v[6] = X[ix]; v[7] = Y[iy + 1];
       /* local edges: 0 bottom, 1 right, 2 top, 3 left (counter-clockwise) */
       int nb[4], nk[4] = {2, 3, 0, 1}, bcode[4] = {bc[2], bc[1], bc[3], bc[0]};
-      nb[0] = iy > 0 ? i - nx : (bc[2] == BC_PERIODIC ? (ny - 1) * nx + ix : -1);
-      nb[1] = ix < nx - 1 ? i + 1 : (bc[1] == BC_PERIODIC ? iy * nx : -1);
-      nb[2] = iy < ny - 1 ? i + nx : (bc[3] == BC_PERIODIC ? ix : -1);
-      nb[3] = ix > 0 ? i - 1 : (bc[0] == BC_PERIODIC ? iy * nx + nx - 1 : -1);
+      nb[0] = iy > 0 ? c - nx : (bc[2] == BC_PERIODIC ? (ny - 1) * nx + ix : -1);
+      nb[1] = ix < nx - 1 ? c + 1 : (bc[1] == BC_PERIODIC ? iy * nx : -1);
+      nb[2] = iy < ny - 1 ? c + nx : (bc[3] == BC_PERIODIC ? ix : -1);
+      nb[3] = ix > 0 ? c - 1 : (bc[0] == BC_PERIODIC ? iy * nx + nx - 1 : -1);
       for (int k = 0; k < 4; ++k) {
-        m->nbr[i * 4 + k] = nb[k];
-        m->nbk[i * 4 + k] = nb[k] >= 0 ? nk[k] : -1;
-        m->bc[i * 4 + k] = nb[k] >= 0 ? BC_PERIODIC : bcode[k];
+        int j = nb[k] >= 0 ? id[nb[k]] : -1;
+        m->nbr[i * 4 + k] = j;
+        m->nbk[i * 4 + k] = j >= 0 ? nk[k] : -1;
+        m->bc[i * 4 + k] = j >= 0 ? BC_PERIODIC : (nb[k] >= 0 ? mask_bc : bcode[k]);
       }
     }
-  free(X); free(Y);
+  free(X); free(Y); free(id);
   mesh_geometry(m);
   mesh_edges(m);
   return m;
+}
+
+orc_mesh* orc_mesh_cartesian(int nx, int ny, double x0, double x1, double y0, double y1, const int* bc) {
+  return orc_mesh_cartesian_masked(nx, ny, x0, x1, y0, y1, bc, NULL, BC_REFLECT);
 }
 
 typedef struct { int a, b, elem, k; } half_edge;
@@ -504,6 +517,7 @@ struct orc_solver {
   double *fstar, *flxw, *flxf;              /* per edge: [ne][MQ][4], [ne][4], [ne][4] */
   double *prop;                             /* [N][E] Lambda proposals */
   double last_dt;
+  double qinf[4];                           /* conserved state of inflow boundaries */
 };
 
 orc_solver* orc_solver_new(const orc_mesh* m, int deg, double gamma) {
@@ -563,6 +577,14 @@ void orc_solver_free(orc_solver* s) {
 }
 void orc_solver_set_params(orc_solver* s, double eps0, double alpha0, int shock_limiter) {
   s->eps0 = eps0; s->alpha0 = alpha0; s->shock_limiter = shock_limiter;
+}
+
+/* the state of inflow boundaries from primitive values (rho, u, v, p) */
+void orc_solver_set_inflow(orc_solver* s, const double* prim) {
+  s->qinf[0] = prim[0];
+  s->qinf[1] = prim[0] * prim[1];
+  s->qinf[2] = prim[0] * prim[2];
+  s->qinf[3] = prim[3] / (s->gamma - 1.0) + 0.5 * prim[0] * (prim[1] * prim[1] + prim[2] * prim[2]);
 }
 int orc_solver_num_modes(const orc_solver* s) { return s->ML; }
 int orc_solver_num_points(const orc_solver* s) { return s->NPT; }
@@ -833,8 +855,15 @@ void orc_ck_element(const orc_solver* s, const double* Q, int i, double dt, doub
 }
 
 /* Sec. 2.4: exterior state at a boundary point; the same map is applied to
- * q, q_t and q_tt.  Reflective flips the normal momentum, transparent copies. */
-static void boundary_state(int bc, const double* nh, const double* qin, double* qout) {
+ * q, q_t and q_tt.  Reflective flips the normal momentum, transparent copies.
+ * Inflow (the shock-diffraction problems of Sec. 4) prescribes a steady
+ * state: q -> q_inflow, q_t and q_tt -> 0 (deriv = 1 marks those). */
+static void boundary_state(int bc, const double* nh, const double* qin, double* qout, const double* qinflow,
+                           int deriv) {
+  if (bc == BC_INFLOW) {
+    for (int v = 0; v < 4; ++v) qout[v] = deriv ? 0.0 : qinflow[v];
+    return;
+  }
   qout[0] = qin[0]; qout[3] = qin[3];
   double mn = qin[1] * nh[0] + qin[2] * nh[1];
   double mt0 = qin[1] - mn * nh[0], mt1 = qin[2] - mn * nh[1];
@@ -915,7 +944,7 @@ static double shock_theta_element(const orc_solver* s, const double* Q, int i) {
       const double* n = m->nrm + ((size_t)i * E + k) * 2;
       double ln = sqrt(n[0] * n[0] + n[1] * n[1]);
       double nh[2] = {n[0] / ln, n[1] / ln};
-      boundary_state(m->bc[i * E + k], nh, qbar, qj);
+      boundary_state(m->bc[i * E + k], nh, qbar, qj, s->qinf, 0);
     }
     if (!(qj[0] > 0.0)) continue;
     double wj[4];
@@ -1096,9 +1125,9 @@ int orc_step(orc_solver* s, double* Q, double dt_in, double cfl, double* diag,
         for (int v = 0; v < NV; ++v) { qp[v] = s->tq[tj + v]; Fp[v] = s->tF[tj + v]; Gp[v] = s->tG[tj + v]; }
       } else {
         double qtp[4], qttp[4];
-        boundary_state(bc, nh, qm, qp);
-        boundary_state(bc, nh, s->tqt + ti, qtp);
-        boundary_state(bc, nh, s->tqtt + ti, qttp);
+        boundary_state(bc, nh, qm, qp, s->qinf, 0);
+        boundary_state(bc, nh, s->tqt + ti, qtp, s->qinf, 1);
+        boundary_state(bc, nh, s->tqtt + ti, qttp, s->qinf, 1);
         ft_from_derivs(g, dt, qp, qtp, qttp, Fp, Gp);
       }
       double* fs = s->fstar + ((size_t)e * MQ + p) * NV;
@@ -1115,7 +1144,7 @@ int orc_step(orc_solver* s, double* Q, double dt_in, double cfl, double* diag,
       const double* Qj = Q + (size_t)j * NV * ML;
       qj[0] = Qj[0]; qj[1] = Qj[ML]; qj[2] = Qj[2 * ML]; qj[3] = Qj[3 * ML];
     } else {
-      boundary_state(bc, nh, qi, qj);
+      boundary_state(bc, nh, qi, qj, s->qinf, 0);
     }
     double Fi[4], Gi[4], Fj[4], Gj[4];
     orc_flux(g, qi, Fi, Gi);
@@ -1311,7 +1340,7 @@ void orc_features(const orc_solver* s, const double* Q, double* F) {
         const double* n = m->nrm + ((size_t)i * E + k) * 2;
         double ln = sqrt(n[0] * n[0] + n[1] * n[1]);
         double nh[2] = {n[0] / ln, n[1] / ln};
-        boundary_state(m->bc[i * E + k], nh, qbar, qn);
+        boundary_state(m->bc[i * E + k], nh, qbar, qn, s->qinf, 0);
       }
       if (qn[0] > 0.0) { f[14 + k] = qn[0] / r - 1.0; f[18 + k] = qn[3] / e - 1.0; }
     }

@@ -19,7 +19,8 @@
  * Conventions shared with the GPU library by documentation only (no code):
  *   state layout Q[N][4][ML], variables (rho, rho*u, rho*v, E), mode order
  *   documented in lxw_oracle.c; boundary codes 0 periodic, 1 reflective,
- *   2 transparent; element kinds 0 quadrilateral (axis-aligned), 1 triangle.
+ *   2 transparent, 3 inflow (the solver's prescribed state); element kinds
+ *   0 quadrilateral (axis-aligned), 1 triangle.
  */
 #ifndef LXW_ORACLE_H
 #define LXW_ORACLE_H
@@ -72,6 +73,12 @@ void orc_mesh_geometry(const orc_mesh* m, double* area, double* perim, double* c
 orc_solver* orc_solver_new(const orc_mesh* m, int deg, double gamma);
 void orc_solver_free(orc_solver* s);
 void orc_solver_set_params(orc_solver* s, double eps0, double alpha0, int shock_limiter);
+/* state of the inflow boundaries, primitive (rho, u, v, p) */
+void orc_solver_set_inflow(orc_solver* s, const double* prim);
+/* Cartesian mesh without the cells of mask == 0 (mask[ny][nx], row order);
+ * faces towards a left-out cell get the code mask_bc */
+orc_mesh* orc_mesh_cartesian_masked(int nx, int ny, double x0, double x1, double y0, double y1, const int* bc,
+                                    const unsigned char* mask, int mask_bc);
 int orc_solver_num_modes(const orc_solver* s);
 int orc_solver_num_points(const orc_solver* s);   /* interior + edge points per element */
 int orc_projection_num_points(const orc_solver* s);

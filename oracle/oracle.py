@@ -13,7 +13,7 @@ from . import build as _build
 
 _lib = None
 
-PERIODIC, REFLECT, TRANSPARENT = 0, 1, 2
+PERIODIC, REFLECT, TRANSPARENT, INFLOW = 0, 1, 2, 3
 QUAD, TRI = 0, 1
 DIAG_KEYS = ["s", "dt", "min_rho", "min_p", "mass", "momx", "momy", "energy",
              "n_mom", "n_edge", "n_sc", "status"]
@@ -44,6 +44,10 @@ def lib():
         L.orc_flux.argtypes = [C.c_double, _dp, _dp, _dp]
         L.orc_mesh_cartesian.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _ip]
         L.orc_mesh_cartesian.restype = C.c_void_p
+        L.orc_mesh_cartesian_masked.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                                _ip, C.POINTER(C.c_ubyte), C.c_int]
+        L.orc_mesh_cartesian_masked.restype = C.c_void_p
+        L.orc_solver_set_inflow.argtypes = [C.c_void_p, _dp]
         L.orc_mesh_triangles.argtypes = [C.c_int, _dp, C.c_int, _ip, _ip]
         L.orc_mesh_triangles.restype = C.c_void_p
         L.orc_mesh_free.argtypes = [C.c_void_p]
@@ -173,6 +177,14 @@ class Mesh:
         return cls(lib().orc_mesh_cartesian(nx, ny, box[0], box[1], box[2], box[3], _i(b)))
 
     @classmethod
+    def cartesian_masked(cls, nx, ny, box, bc, mask, mask_bc=1):
+        """Cartesian mesh without the cells where mask[iy][ix] == 0."""
+        b = np.array(bc, dtype=np.int32)
+        mk = np.ascontiguousarray(mask, dtype=np.uint8).reshape(ny, nx)
+        return cls(lib().orc_mesh_cartesian_masked(nx, ny, box[0], box[1], box[2], box[3], _i(b),
+                                                   mk.ctypes.data_as(C.POINTER(C.c_ubyte)), mask_bc))
+
+    @classmethod
     def triangles(cls, xy, tv, ebc=None):
         xy = np.ascontiguousarray(xy, dtype=np.float64); tv = np.ascontiguousarray(tv, dtype=np.int32)
         e = None if ebc is None else np.ascontiguousarray(ebc, dtype=np.int32)
@@ -206,6 +218,10 @@ class Solver:
         if getattr(self, "ptr", None) and _lib is not None:
             _lib.orc_solver_free(self.ptr)
             self.ptr = None
+
+    def set_inflow(self, prim):
+        """State (rho, u, v, p) of the inflow boundaries."""
+        lib().orc_solver_set_inflow(self.ptr, _d(np.ascontiguousarray(prim, dtype=np.float64)))
 
     def new_state(self):
         return np.zeros((self.N, 4, self.ML))

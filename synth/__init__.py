@@ -159,3 +159,37 @@ def random_modal_state(N: int, ML: int, seed: int, amp: float = 0.3, gamma: floa
     hi = (2.0 * r[:, 4:].reshape(N, 4, ML) - 1.0) * amp
     Q[:, :, 1:] = hi[:, :, 1:] * scale[:, :, None]
     return Q
+
+
+# ------------------------------------------------ shock diffraction over a step
+def normal_shock_state(mach, rho0=1.4, p0=1.0, gamma=1.4):
+    """Primitive state (rho, u, v, p) behind a normal shock of the given Mach
+    number running in +x into gas at rest (rho0, p0): the Rankine-Hugoniot
+    jump conditions."""
+    m2 = mach * mach
+    r = (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p = (2.0 * gamma * m2 - (gamma - 1.0)) / (gamma + 1.0)
+    c0 = np.sqrt(gamma * p0 / rho0)
+    return rho0 * r, mach * c0 * (1.0 - 1.0 / r), 0.0, p0 * p
+
+
+DIFFRACTION_BOX = (0.0, 13.0, 0.0, 11.0)
+DIFFRACTION_STEP = (1.0, 6.0)       # the step occupies [0, 1] x [0, 6]
+DIFFRACTION_MACH = 5.09
+
+
+def diffraction_mask(nx, ny):
+    """mask[ny][nx] of the Cartesian cells kept on [0,13] x [0,11]: every cell
+    whose centre is outside the step [0,1] x [0,6]."""
+    x0, x1, y0, y1 = DIFFRACTION_BOX
+    xc = x0 + (np.arange(nx) + 0.5) * (x1 - x0) / nx
+    yc = y0 + (np.arange(ny) + 0.5) * (y1 - y0) / ny
+    X, Y = np.meshgrid(xc, yc, indexing="xy")
+    return ~((X < DIFFRACTION_STEP[0]) & (Y < DIFFRACTION_STEP[1]))
+
+
+def ic_diffraction(x, y):
+    """Gas at rest (rho 1.4, p 1) with the Mach 5.09 shock at x = 1 above the step."""
+    r1, u1, _, p1 = normal_shock_state(DIFFRACTION_MACH)
+    left = x < DIFFRACTION_STEP[0]
+    return np.where(left, r1, 1.4), np.where(left, u1, 0.0), 0.0 * x, np.where(left, p1, 1.0)
