@@ -49,6 +49,11 @@ WORKLOADS = {
                      desc="rarefaction: 724x724x2 = 1,048,352 jittered triangles, P2, rho=1 p=0.4 u=-+2, transparent"),
     "blast2048": dict(kind="quad", n=2048, deg=2, cfl=0.1, ic=None, bc=(1, 1, 1, 1), box=(-1.1, 1.1, -1.1, 1.1),
                       desc="blast: 2048x2048 Cartesian, P2, point energy 0.979264 in the 4 centre cells, reflective"),
+    "diffraction": dict(kind="step", nx=390, ny=330, deg=2, cfl=0.1, ic=synth.ic_diffraction,
+                        box=synth.DIFFRACTION_BOX, bc=synth.DIFFRACTION_BC,
+                        desc="shock diffraction: Mach 5.09 over a step, 390x330 Cartesian on [0,13]x[0,11] less the "
+                             "step [0,1]x[0,6] (123,300 cells), P2, inflow above the step, walls on it, "
+                             "transparent elsewhere"),
 }
 ENSEMBLE = dict(count=256, lo=32, hi=256, seed=4242, deg=2, cfl=0.3,
                 desc="ensemble: 256 independent Cartesian problems n_p x n_p, n_p ~ U{32..256} (seed 4242), "
@@ -62,7 +67,7 @@ ENSEMBLE = dict(count=256, lo=32, hi=256, seed=4242, deg=2, cfl=0.3,
 def ck_flops_per_element(kind, deg):
     ML = (deg + 1) * (deg + 2) // 2
     NQ = (deg + 1) ** 2
-    NE = (4 if kind == "quad" else 3) * (deg + 1)
+    NE = (3 if kind == "tri" else 4) * (deg + 1)
     npt = NQ + NE
     contract = 2 * 4 * ML * npt + 2 * 2 * 2 * 4 * ML * NQ + 2 * (2 * 2 * 4 * ML * npt) + 2 * 2 * 4 * ML * NQ
     return contract + 250 * npt
@@ -84,11 +89,39 @@ def build_solver(L, w, stream, mixed):
     if w["kind"] == "tri":
         xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
         mesh = L.lxw_mesh_triangles(xy, tv)
+    elif w["kind"] == "step":
+        mesh = L.lxw_mesh_cartesian_masked(w["nx"], w["ny"], w["box"], w["bc"],
+                                           synth.diffraction_mask(w["nx"], w["ny"]), L.BC_REFLECT)
     else:
         mesh = L.lxw_mesh_cartesian(w["n"], w["n"], w.get("box", (0.0, 1.0, 0.0, 1.0)), w.get("bc", (0, 0, 0, 0)))
     opt = L.lxw_options_default(precision=L.PREC_MIXED if mixed else L.PREC_FP64)
     sol = L.lxw_solver_create(mesh, w["deg"], opt, stream=stream)
+    if w["kind"] == "step":
+        L.lxw_solver_set_inflow(sol, synth.normal_shock_state(synth.DIFFRACTION_MACH))
     return w, sol
+
+
+def oracle_solver(w):
+    """The oracle's solver and initial state for a workload."""
+    from oracle import oracle as O
+    if w["kind"] == "tri":
+        xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
+        m = O.Mesh.triangles(xy, tv)
+    elif w["kind"] == "step":
+        m = O.Mesh.cartesian_masked(w["nx"], w["ny"], w["box"], w["bc"], synth.diffraction_mask(w["nx"], w["ny"]),
+                                    O.REFLECT)
+    else:
+        m = O.Mesh.cartesian(w["n"], w["n"], w.get("box", (0.0, 1.0, 0.0, 1.0)), w.get("bc", (0, 0, 0, 0)))
+    s = O.Solver(m, w["deg"])
+    if w["kind"] == "step":
+        s.set_inflow(synth.normal_shock_state(synth.DIFFRACTION_MACH))
+    return s, s.project_fn(w["ic"] or synth.ic_blast(w["n"]))
+
+
+def half_resolution(w):
+    if w["kind"] == "step":
+        return dict(w, nx=w["nx"] // 2, ny=w["ny"] // 2)
+    return dict(w, n=w["n"] // 2)
 
 
 def project(L, sol, w):
@@ -192,13 +225,7 @@ def cpu_baseline(name, budget_s=10.0):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload."""
     from oracle import oracle as O
     w = WORKLOADS[name]
-    if w["kind"] == "tri":
-        xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
-        m = O.Mesh.triangles(xy, tv)
-    else:
-        m = O.Mesh.cartesian(w["n"], w["n"], w.get("box", (0.0, 1.0, 0.0, 1.0)), w.get("bc", (0, 0, 0, 0)))
-    s = O.Solver(m, w["deg"])
-    Q = s.project_fn(w["ic"] or synth.ic_blast(w["n"]))
+    s, Q = oracle_solver(w)
     s.step(Q, cfl=w["cfl"])          # untimed first step (page-in)
     t0 = time.perf_counter(); k = 0
     while k < 3 or (time.perf_counter() - t0 < budget_s and k < 400):
@@ -226,13 +253,7 @@ def run_reference(args):
         return
     from oracle import oracle as O
     w = WORKLOADS[args.workload]
-    if w["kind"] == "tri":
-        xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
-        m = O.Mesh.triangles(xy, tv)
-    else:
-        m = O.Mesh.cartesian(w["n"], w["n"], w.get("box", (0.0, 1.0, 0.0, 1.0)), w.get("bc", (0, 0, 0, 0)))
-    s = O.Solver(m, w["deg"])
-    Q = s.project_fn(w["ic"] or synth.ic_blast(w["n"]))
+    s, Q = oracle_solver(w)
     for _ in range(args.warmup):
         s.step(Q, cfl=w["cfl"])
     t0 = time.perf_counter()
@@ -386,18 +407,25 @@ def run_to(L, sol, Q, T, cfl):
     return k
 
 
-def locate(w, nc, pts):
-    """Element of the half-resolution mesh (nc x nc squares, or their 2 nc^2
-    triangles with the same jitter rule) holding each point, and the point's
-    reference coordinates there."""
-    x0, x1, y0, y1 = w.get("box", (0.0, 1.0, 0.0, 1.0))
-    hx, hy = (x1 - x0) / nc, (y1 - y0) / nc
+def locate(wc, pts):
+    """Element of the half-resolution mesh wc (nc x nc squares, the masked
+    step grid, or 2 nc^2 triangles with the same jitter rule) holding each
+    point, and the point's reference coordinates there."""
+    x0, x1, y0, y1 = wc.get("box", (0.0, 1.0, 0.0, 1.0))
+    ncx, ncy = (wc["nx"], wc["ny"]) if wc["kind"] == "step" else (wc["n"], wc["n"])
+    nc = ncx
+    hx, hy = (x1 - x0) / ncx, (y1 - y0) / ncy
     x, y = pts[:, 0], pts[:, 1]
-    ix = np.clip(np.floor((x - x0) / hx).astype(np.int64), 0, nc - 1)
-    iy = np.clip(np.floor((y - y0) / hy).astype(np.int64), 0, nc - 1)
-    if w["kind"] == "quad":
+    ix = np.clip(np.floor((x - x0) / hx).astype(np.int64), 0, ncx - 1)
+    iy = np.clip(np.floor((y - y0) / hy).astype(np.int64), 0, ncy - 1)
+    if wc["kind"] in ("quad", "step"):
         ref = np.stack([2.0 * ((x - x0) / hx - ix) - 1.0, 2.0 * ((y - y0) / hy - iy) - 1.0], axis=1)
-        return iy * nc + ix, ref
+        cell = iy * ncx + ix
+        if wc["kind"] == "quad":
+            return cell, ref
+        keep = synth.diffraction_mask(ncx, ncy).ravel()
+        assert keep[cell].all(), "a point inside the step"
+        return (np.cumsum(keep) - 1)[cell], ref
     xy, tv = synth.structured_triangles(nc, jitter=0.2, seed=20160129, box=(x0, x1, y0, y1))
     best = np.full(len(x), -1, dtype=np.int64)
     bmin = np.full(len(x), -np.inf)
@@ -440,16 +468,15 @@ def discretization_check(L, stream, name, net, tau, steps):
     L.lxw_solver_set_mlp(sm, net, tau)
     Qm = project(L, sm, w)
     km = run_to(L, sm, Qm, T, w["cfl"])
-    nc = w["n"] // 2
-    wc = dict(w, n=nc)
+    wc = half_resolution(w)
     _, sc = build_solver(L, wc, stream, False)
     Qc = project(L, sc, wc)
     kc = run_to(L, sc, Qc, T, w["cfl"])
     # the coarse density at the fine projection points, projected onto the fine elements
     pts = L.lxw_projection_points(sf)
     N, npj = pts.shape[0], pts.shape[1]
-    elem, ref = locate(w, nc, pts.reshape(-1, 2))
-    phi = L.lxw_basis_eval(0 if w["kind"] == "quad" else 1, w["deg"], ref)
+    elem, ref = locate(wc, pts.reshape(-1, 2))
+    phi = L.lxw_basis_eval(1 if w["kind"] == "tri" else 0, w["deg"], ref)
     rc = np.einsum("pl,pl->p", Qc[:, 0, :].cpu().numpy()[elem], phi).reshape(N, npj)
     prim = np.stack([rc, np.zeros_like(rc), np.zeros_like(rc), np.ones_like(rc)], axis=-1)
     Qp = torch.zeros(sf.q64_shape, dtype=torch.float64, device="cuda")
@@ -457,7 +484,7 @@ def discretization_check(L, stream, name, net, tau, steps):
     rho_f = Qf[:, 0, 0].cpu().numpy()
     rho_p = Qp[:, 0, 0].cpu().numpy()
     rho_m = L.to_q64(sm, Qm)[:, 0, 0].cpu().numpy()
-    if w["kind"] == "quad":
+    if w["kind"] != "tri":
         area = np.full(N, 1.0 / N)
     else:
         xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)

@@ -21,7 +21,9 @@
  *   y^2 [, x^3, x^2y, xy^2, y^3] under (1/|T0|) Int, positive leading term.
  *
  * Boundary codes: LXW_BC_PERIODIC (Cartesian, paired sides),
- * LXW_BC_REFLECT (solid wall) and LXW_BC_TRANSPARENT (outflow), Sec. 2.4.
+ * LXW_BC_REFLECT (solid wall) and LXW_BC_TRANSPARENT (outflow), Sec. 2.4;
+ * LXW_BC_INFLOW (a steady prescribed state, lxw_solver_set_inflow), the
+ * inflow side of the shock-diffraction problem of Sec. 4.
  */
 #ifndef LXW_H
 #define LXW_H
@@ -42,7 +44,7 @@ typedef enum {
   LXW_ERR_NOMEM = 8         /* device or host allocation failed                    */
 } lxw_status;
 
-enum { LXW_BC_PERIODIC = 0, LXW_BC_REFLECT = 1, LXW_BC_TRANSPARENT = 2 };
+enum { LXW_BC_PERIODIC = 0, LXW_BC_REFLECT = 1, LXW_BC_TRANSPARENT = 2, LXW_BC_INFLOW = 3 };
 enum { LXW_KIND_QUAD = 0, LXW_KIND_TRI = 1 };
 /* Precision forms.  LXW_PREC_FP64: every operation in FP64; the state is
  * Q[N][4][ML] doubles.  LXW_PREC_MIXED: FP32 bulk (point values, CK flux,
@@ -107,9 +109,21 @@ lxw_status lxw_options_default(lxw_options* opt);
 lxw_status lxw_mesh_cartesian(int nx, int ny, double x0, double x1, double y0, double y1,
                               const int bc[4], lxw_mesh** out);
 
+/* The same grid without the cells whose mask_host[iy*nx + ix] is 0 (host
+ * array of nx*ny bytes, read during the call; NULL keeps every cell), e.g.
+ * the step of the shock-diffraction problem of Sec. 4.  Elements are the
+ * kept cells numbered in row order (iy, then ix).  A face that a kept cell
+ * shares with a left-out one (also across a periodic side) gets the code
+ * mask_bc (REFLECT, TRANSPARENT or INFLOW).  Errors: LXW_ERR_ARG (bad code
+ * or box, periodic sides unpaired, no cell kept). */
+lxw_status lxw_mesh_cartesian_masked(int nx, int ny, double x0, double x1, double y0, double y1,
+                                     const int bc[4], const unsigned char* mask_host, int mask_bc,
+                                     lxw_mesh** out);
+
 /* Triangles tv[nt][3] (counter-clockwise vertex ids into xy_host[nv][2]).
  * ebc_host[nt][3] (nullable; default transparent) gives the boundary code
- * of triangle-local edge k (vertex k -> k+1), read only on boundary edges.
+ * (REFLECT, TRANSPARENT or INFLOW) of triangle-local edge k (vertex
+ * k -> k+1), read only on boundary edges.
  * Errors: LXW_ERR_BOUNDS (vertex id), LXW_ERR_ARG (non-positive area,
  * an edge shared by more than two triangles). */
 lxw_status lxw_mesh_triangles(int nv, const double* xy_host, int nt, const int* tv_host,
@@ -130,6 +144,15 @@ lxw_status lxw_solver_create(const lxw_mesh* mesh, int degree, const lxw_options
                              void* stream, lxw_solver** out);
 void lxw_solver_destroy(lxw_solver* s);
 lxw_status lxw_solver_set_stream(lxw_solver* s, void* stream);
+/* The state prim_host[4] = (rho, u, v, p) of the LXW_BC_INFLOW faces (host
+ * array, read during the call; default all zero).  Outside such a face the
+ * solution is that state at every point and time: its trace is q_in, the
+ * time-averaged flux there n.F(q_in) (q_t = q_tt = 0), the neighbour
+ * average of the limiters q_in.  The global wave speed stays the maximum
+ * over the cells (Sec. 3.3).  Shared by every problem of a batched solver.
+ * Drops the solver's CUDA graphs (re-captured on the next lxw_run).
+ * Errors: LXW_ERR_ARG (null, rho <= 0 or p <= 0). */
+lxw_status lxw_solver_set_inflow(lxw_solver* s, const double prim_host[4]);
 /* N elements, E edges per element, ML modes, npts limiter points per element
  * (interior + edge quadrature points), nproj projection points. */
 lxw_status lxw_solver_info(const lxw_solver* s, int* N, int* E, int* ML, int* npts, int* nproj);
@@ -272,7 +295,10 @@ lxw_status lxw_fma_peak(int fp64, double* tflops);
  * average: theta = 1), evaluates a BF16 copy of the network on the tensor
  * cores (tcgen05, FP32 accumulation in tensor memory) for the tiles of 128
  * cells that hold a cell the screen cannot clear, and runs the plain
- * limiter for the cells neither clears.  Its device waits are bounded (about a second): on expiry it sets
+ * limiter for the cells neither clears.  The prediction is used only for a
+ * cell whose 24 features all lie inside the network's envelope (per-feature
+ * bounds: those of its training data, or set explicitly); outside it the
+ * limiter runs.  Its device waits are bounded (about a second): on expiry it sets
  * LXW_ST_TIMEOUT and limits the rest of its cells with the plain limiter. */
 enum { LXW_MLP_IN = 24, LXW_MLP_HIDDEN = 64, LXW_MLP_PARAMS = 5825 };
 typedef struct lxw_mlp lxw_mlp;
@@ -288,9 +314,17 @@ lxw_status lxw_mlp_forward(lxw_mlp* n, const float* X_dev, int B, float* yhat_de
  * grad_dev[LXW_MLP_PARAMS] (nullable); loss_host nullable (synchronises). */
 lxw_status lxw_mlp_loss_grad(lxw_mlp* n, const float* X_dev, const float* y_dev, int B, float* loss_host,
                              float* grad_dev);
-/* epochs of Adam over shuffled mini-batches (seeded) of the count samples. */
+/* epochs of Adam over shuffled mini-batches (seeded) of the count samples.
+ * Also widens the envelope to the per-feature range of X_dev (the first
+ * call on a network, or after lxw_mlp_set_envelope(n, NULL, NULL), sets it). */
 lxw_status lxw_mlp_train(lxw_mlp* n, const float* X_dev, const float* y_dev, int count, int epochs, int batch,
                          float lr, unsigned long long seed, float* last_loss);
+/* The envelope: lo_host[24] <= feature <= hi_host[24] is where the gate
+ * uses the prediction.  Both NULL: unbounded (a new network's default; the
+ * next training call sets the envelope).  Takes effect at the next
+ * lxw_solver_set_mlp.  Errors: LXW_ERR_ARG (one NULL, lo > hi). */
+lxw_status lxw_mlp_set_envelope(lxw_mlp* n, const float* lo_host, const float* hi_host);
+lxw_status lxw_mlp_get_envelope(const lxw_mlp* n, float* lo_host, float* hi_host);
 /* Enables (mlp non-NULL) or disables the learned gate of a mixed solver;
  * the solver keeps a BF16 copy taken now, laid out as the tensor-core
  * operands (later training needs another call).  tau in [0, 1).  Errors:

@@ -269,6 +269,7 @@ struct lxw_solver {
   int4* d_tiles = nullptr;       // work list (owned through allocs)
   GateWeights* gate_buf = nullptr;  // gate weights (owned), allocated by the first lxw_solver_set_mlp
   const GateWeights* mlp_w = nullptr;  // gate_buf while a network is attached, else null
+  double qin[4] = {0.0, 0.0, 0.0, 0.0};  // conserved state of LXW_BC_INFLOW faces
   int gate_per_sm[2] = {1, 1};         // resident gate CTAs per SM of each variant (queried when a network is attached)
   float mlp_tau = 0.0f;
   int tiles_cap = 0;
@@ -312,18 +313,25 @@ lxw_status lxw_options_default(lxw_options* opt) {
   return LXW_OK;
 }
 
-lxw_status lxw_mesh_cartesian(int nx, int ny, double x0, double x1, double y0, double y1, const int bc[4],
-                              lxw_mesh** out) {
+lxw_status lxw_mesh_cartesian_masked(int nx, int ny, double x0, double x1, double y0, double y1, const int bc[4],
+                                     const unsigned char* mask, int mask_bc, lxw_mesh** out) {
   if (!out || !bc) return fail(LXW_ERR_ARG, "lxw_mesh_cartesian: null argument");
   if (nx < 1 || ny < 1 || !(x1 > x0) || !(y1 > y0)) return fail(LXW_ERR_ARG, "lxw_mesh_cartesian: bad size or box");
   for (int k = 0; k < 4; ++k)
-    if (bc[k] < 0 || bc[k] > 2) return fail(LXW_ERR_ARG, "lxw_mesh_cartesian: bad boundary code");
+    if (bc[k] < LXW_BC_PERIODIC || bc[k] > LXW_BC_INFLOW) return fail(LXW_ERR_ARG, "lxw_mesh_cartesian: bad boundary code");
+  if (mask_bc < LXW_BC_REFLECT || mask_bc > LXW_BC_INFLOW)
+    return fail(LXW_ERR_ARG, "lxw_mesh_cartesian_masked: mask_bc must be REFLECT, TRANSPARENT or INFLOW");
   if ((bc[0] == LXW_BC_PERIODIC) != (bc[1] == LXW_BC_PERIODIC) || (bc[2] == LXW_BC_PERIODIC) != (bc[3] == LXW_BC_PERIODIC))
     return fail(LXW_ERR_ARG, "lxw_mesh_cartesian: periodic sides must be paired");
+  // compact ids of the kept cells, row order
+  std::vector<int> id((size_t)nx * ny);
+  int N = 0;
+  for (size_t c = 0; c < id.size(); ++c) id[c] = (!mask || mask[c]) ? N++ : -1;
+  if (N < 1) return fail(LXW_ERR_ARG, "lxw_mesh_cartesian_masked: the mask keeps no cell");
   lxw_mesh* m = new (std::nothrow) lxw_mesh;
   if (!m) return fail(LXW_ERR_NOMEM, "lxw_mesh_cartesian: out of memory");
-  m->kind = LXW_KIND_QUAD; m->N = nx * ny; m->E = 4;
-  m->vx.resize((size_t)m->N * 8); m->nbr.resize((size_t)m->N * 4); m->nbk.resize((size_t)m->N * 4);
+  m->kind = LXW_KIND_QUAD; m->N = N; m->E = 4;
+  m->vx.resize((size_t)N * 8); m->nbr.resize((size_t)N * 4); m->nbk.resize((size_t)N * 4);
   std::vector<double> X(nx + 1), Y(ny + 1);
   for (int a = 0; a <= nx; ++a) X[a] = x0 + (x1 - x0) * a / nx;
   for (int b = 0; b <= ny; ++b) Y[b] = y0 + (y1 - y0) * b / ny;
@@ -332,7 +340,8 @@ lxw_status lxw_mesh_cartesian(int nx, int ny, double x0, double x1, double y0, d
   const int opposite[4] = {2, 3, 0, 1};
   for (int iy = 0; iy < ny; ++iy)
     for (int ix = 0; ix < nx; ++ix) {
-      const int e = iy * nx + ix;
+      const int e = id[(size_t)iy * nx + ix];
+      if (e < 0) continue;
       double* v = &m->vx[(size_t)e * 8];
       v[0] = X[ix]; v[1] = Y[iy]; v[2] = X[ix + 1]; v[3] = Y[iy]; v[4] = X[ix + 1]; v[5] = Y[iy + 1]; v[6] = X[ix]; v[7] = Y[iy + 1];
       int jx[4] = {ix, ix + 1, ix, ix - 1}, jy[4] = {iy - 1, iy, iy + 1, iy};
@@ -340,12 +349,18 @@ lxw_status lxw_mesh_cartesian(int nx, int ny, double x0, double x1, double y0, d
         int a = jx[k], b = jy[k];
         bool inside = a >= 0 && a < nx && b >= 0 && b < ny;
         if (!inside && side_bc[k] == LXW_BC_PERIODIC) { a = (a + nx) % nx; b = (b + ny) % ny; inside = true; }
-        m->nbr[(size_t)e * 4 + k] = inside ? b * nx + a : -1 - side_bc[k];
-        m->nbk[(size_t)e * 4 + k] = inside ? opposite[k] : -1;
+        const int j = inside ? id[(size_t)b * nx + a] : -1;
+        m->nbr[(size_t)e * 4 + k] = j >= 0 ? j : -1 - (inside ? mask_bc : side_bc[k]);
+        m->nbk[(size_t)e * 4 + k] = j >= 0 ? opposite[k] : -1;
       }
     }
   *out = m;
   return LXW_OK;
+}
+
+lxw_status lxw_mesh_cartesian(int nx, int ny, double x0, double x1, double y0, double y1, const int bc[4],
+                              lxw_mesh** out) {
+  return lxw_mesh_cartesian_masked(nx, ny, x0, x1, y0, y1, bc, nullptr, LXW_BC_REFLECT, out);
 }
 
 lxw_status lxw_mesh_triangles(int nv, const double* xy, int nt, const int* tv, const int* ebc, lxw_mesh** out) {
@@ -386,7 +401,7 @@ lxw_status lxw_mesh_triangles(int nv, const double* xy, int nt, const int* tv, c
     if (kv.second >= 0) {
       int e = kv.second / 3, k = kv.second % 3;
       int code = ebc ? ebc[kv.second] : LXW_BC_TRANSPARENT;
-      if (code != LXW_BC_REFLECT && code != LXW_BC_TRANSPARENT) { delete m; return fail(LXW_ERR_ARG, "lxw_mesh_triangles: boundary edges need a reflective or transparent code"); }
+      if (code < LXW_BC_REFLECT || code > LXW_BC_INFLOW) { delete m; return fail(LXW_ERR_ARG, "lxw_mesh_triangles: boundary edges need a reflective, transparent or inflow code"); }
       m->nbr[(size_t)e * 3 + k] = -1 - code;
       m->nbk[(size_t)e * 3 + k] = -1;
     }
@@ -677,6 +692,17 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   a.hi_occupancy = s->opt.high_occupancy;
   a.gate_per_sm = s->gate_per_sm[s->opt.high_occupancy ? 1 : 0];
   a.gate_w = s->mlp_w; a.mlp_tau = s->mlp_tau; a.feat_out = nullptr; a.gate_out = nullptr;
+  {  // inflow state and its fluxes (the time-averaged flux of a steady state)
+    const double* q = s->qin;
+    const double u = q[0] > 0.0 ? q[1] / q[0] : 0.0, v = q[0] > 0.0 ? q[2] / q[0] : 0.0;
+    const double p = (a.gamma - 1.0) * (q[3] - 0.5 * (q[1] * u + q[2] * v));
+    const double F[4] = {q[1], q[1] * u + p, q[1] * v, (q[3] + p) * u};
+    const double G[4] = {q[2], q[2] * u, q[2] * v + p, (q[3] + p) * v};
+    for (int k = 0; k < 4; ++k) {
+      a.qin[k] = q[k]; a.fin[k] = F[k]; a.gin[k] = G[k];
+      a.qin32[k] = (float)q[k]; a.fin32[k] = (float)F[k]; a.gin32[k] = (float)G[k];
+    }
+  }
   return a;
 }
 
@@ -935,6 +961,18 @@ lxw_status lxw_step_gate(lxw_solver* s, void* state, double cfl, float* gate, fl
 static void drop_graphs(lxw_solver* s) {
   if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
   if (s->pgraph) { cudaGraphExecDestroy(s->pgraph); s->pgraph = nullptr; }
+}
+
+lxw_status lxw_solver_set_inflow(lxw_solver* s, const double prim[4]) {
+  if (!s || !prim) return fail(LXW_ERR_ARG, "lxw_solver_set_inflow: null argument");
+  if (!(prim[0] > 0.0) || !(prim[3] > 0.0) || !std::isfinite(prim[1]) || !std::isfinite(prim[2]))
+    return fail(LXW_ERR_ARG, "lxw_solver_set_inflow: needs rho > 0, p > 0 and finite velocity");
+  s->qin[0] = prim[0];
+  s->qin[1] = prim[0] * prim[1];
+  s->qin[2] = prim[0] * prim[2];
+  s->qin[3] = prim[3] / (s->opt.gamma - 1.0) + 0.5 * prim[0] * (prim[1] * prim[1] + prim[2] * prim[2]);
+  drop_graphs(s);
+  return LXW_OK;
 }
 
 lxw_status lxw_autotune(lxw_solver* s, void* state, double cfl, int reps, int* bt, int* cps, float* best_ms,

@@ -110,7 +110,8 @@ constexpr int kW1 = 0, kB1 = kW1 + kMlpIn * kMlpH, kW2 = kB1 + kMlpH, kB2 = kW2 
 // in BF16, each in the K-major, unswizzled core-matrix layout of tcgen05
 // operands (8 rows x 16 bytes per core matrix, core matrices along K 128 B
 // apart, 8-row groups K/8 x 128 B apart); biases, output weights and output
-// bias are the BF16 values widened to FP32.
+// bias are the BF16 values widened to FP32; then the per-feature bounds
+// inside which the network's prediction is used.
 constexpr int kGateK1 = 32;
 __host__ __device__ constexpr int umma_kmajor(int r, int k, int K) {
   return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
@@ -119,6 +120,7 @@ struct GateWeights {
   unsigned short w1[kMlpH * kGateK1];
   unsigned short w2[kMlpH * kMlpH];
   float b1[kMlpH], b2[kMlpH], w3[kMlpH], b3, pad[3];
+  float lo[kMlpIn], hi[kMlpIn];      // envelope of the training features (the gate skips only inside it)
 };
 static_assert(sizeof(GateWeights) % 16 == 0, "GateWeights is copied in 16-byte words");
 
@@ -133,6 +135,9 @@ struct StepArgs {
   float mlp_tau;                     // gate: skip the limiter where theta_hat >= 1 - tau
   float* feat_out;                   // [N][24] features at the shock limiter's input, or null
   float* gate_out;                   // [N] network output theta_hat (needs the gate), or null
+  double qin[4];                     // conserved state of LXW_BC_INFLOW faces
+  double fin[4], gin[4];             // its Euler fluxes F(q_in), G(q_in)
+  float qin32[4], fin32[4], gin32[4];  // FP32 copies (mixed form)
   int shock_limiter;
   int want_diag;
   double* theta_cell;     // [2][N] or null

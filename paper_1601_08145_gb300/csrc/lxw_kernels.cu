@@ -104,8 +104,14 @@ __device__ __forceinline__ void block_max_to(double v, unsigned long long* dst) 
 }
 
 // boundary exterior state for reflective (flip normal momentum) or
-// transparent (copy) conditions, Sec. 2.4
-__device__ __forceinline__ void ghost_state(int bc, double nxh, double nyh, const double qi[4], double qo[4]) {
+// transparent (copy) conditions, Sec. 2.4, or the prescribed inflow state
+__device__ __forceinline__ void ghost_state(int bc, double nxh, double nyh, const double qi[4], double qo[4],
+                                            const double qin[4]) {
+  if (bc == LXW_BC_INFLOW) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qo[v] = qin[v];
+    return;
+  }
   qo[0] = qi[0]; qo[3] = qi[3];
   if (bc == LXW_BC_REFLECT) {
     double mn = qi[1] * nxh + qi[2] * nyh;
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(128) k_edge(const DevMesh m, const DevWork w, 
       const double* Qj = Q + (size_t)j * 4 * ML;
       qn[0] = Qj[0]; qn[1] = Qj[ML]; qn[2] = Qj[2 * ML]; qn[3] = Qj[3 * ML];
     } else {
-      ghost_state(-1 - j, nx / ln, ny / ln, qb, qn);
+      ghost_state(-1 - j, nx / ln, ny / ln, qb, qn, a.qin);
     }
     {
       Pt sn = make_pt(g1, qn[0], qn[1], qn[2], qn[3]);
@@ -423,11 +429,15 @@ __global__ void __launch_bounds__(128) k_edge(const DevMesh m, const DevWork w, 
       } else if (-1 - j == LXW_BC_REFLECT) {
         // exterior state R q and n.F_T(R q) = -R (n.F_T(q)) (reflection symmetry of the Euler flux)
         const double nxh = nx / ln, nyh = ny / ln;
-        ghost_state(LXW_BC_REFLECT, nxh, nyh, qi, qx);
+        ghost_state(LXW_BC_REFLECT, nxh, nyh, qi, qx, a.qin);
         double R[4];
-        ghost_state(LXW_BC_REFLECT, nxh, nyh, Fi, R);
+        ghost_state(LXW_BC_REFLECT, nxh, nyh, Fi, R, a.qin);
 #pragma unroll
         for (int v = 0; v < 4; ++v) Fx[v] = -R[v];
+      } else if (-1 - j == LXW_BC_INFLOW) {
+        // a steady exterior state: q_t = q_tt = 0, so F_T = F(q_in)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { qx[v] = a.qin[v]; Fx[v] = __fma_rn(nx, a.fin[v], __dmul_rn(ny, a.gin[v])); }
       } else {
 #pragma unroll
         for (int v = 0; v < 4; ++v) { qx[v] = qi[v]; Fx[v] = Fi[v]; }
@@ -595,7 +605,7 @@ __global__ void __launch_bounds__(128) k_shock(const DevMesh m, double* __restri
         const double nx = m.nrm[(2 * k) * N + i], ny = m.nrm[(2 * k + 1) * N + i];
         const double ln = sqrt(nx * nx + ny * ny);
         const double qbv[4] = {c[0][0], c[1][0], c[2][0], c[3][0]};
-        ghost_state(-1 - j, nx / ln, ny / ln, qbv, qn);
+        ghost_state(-1 - j, nx / ln, ny / ln, qbv, qn, a.qin);
       }
       if (!(qn[0] > 0.0)) continue;
       Pt sn = make_pt(g1, qn[0], qn[1], qn[2], qn[3]);

@@ -95,8 +95,15 @@ __device__ __forceinline__ float speedf(float g, float r, float m, float n, floa
   p = p > 0.0f ? p : 0.0f;
   return sqrtf(k2) * ri + sqrtf(g * p * ri);
 }
+// exterior state of a boundary face: reflective, transparent (Sec. 2.4) or
+// the prescribed inflow state qin
 template <typename T>
-__device__ __forceinline__ void ghostq(int bc, T nxh, T nyh, const T qi[4], T qo[4]) {
+__device__ __forceinline__ void ghostq(int bc, T nxh, T nyh, const T qi[4], T qo[4], const T qin[4]) {
+  if (bc == LXW_BC_INFLOW) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qo[v] = qin[v];
+    return;
+  }
   qo[0] = qi[0]; qo[3] = qi[3];
   if (bc == LXW_BC_REFLECT) {
     T mn = qi[1] * nxh + qi[2] * nyh;
@@ -643,15 +650,19 @@ __device__ __forceinline__ void edge_elem(const DevMesh& m, const DevWorkMx& w, 
       }
     } else {
       const float nxh = nx / ln, nyh = ny / ln;
-      ghostq<float>(-1 - j, nxh, nyh, qb, qn);
+      ghostq<float>(-1 - j, nxh, nyh, qb, qn, a.qin32);
 #pragma unroll
       for (int pp = 0; pp < MQ; ++pp) {
         if (-1 - j == LXW_BC_REFLECT) {
-          ghostq<float>(LXW_BC_REFLECT, nxh, nyh, qi[pp], qx[pp]);
+          ghostq<float>(LXW_BC_REFLECT, nxh, nyh, qi[pp], qx[pp], a.qin32);
           float R[4];
-          ghostq<float>(LXW_BC_REFLECT, nxh, nyh, Fi[pp], R);
+          ghostq<float>(LXW_BC_REFLECT, nxh, nyh, Fi[pp], R, a.qin32);
 #pragma unroll
           for (int v = 0; v < 4; ++v) Fx[pp][v] = -R[v];
+        } else if (-1 - j == LXW_BC_INFLOW) {
+          // the steady inflow state: q_t = q_tt = 0, so n.F_T = n.F(q_in)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) { qx[pp][v] = a.qin32[v]; Fx[pp][v] = nx * a.fin32[v] + ny * a.gin32[v]; }
         } else {
 #pragma unroll
           for (int v = 0; v < 4; ++v) { qx[pp][v] = qi[pp][v]; Fx[pp][v] = Fi[pp][v]; }
@@ -750,7 +761,7 @@ __device__ __forceinline__ void edge_elem(const DevMesh& m, const DevWorkMx& w, 
         for (int v = 0; v < 4; ++v) qn[v] = st.avg[(size_t)v * N + j];
       } else {
         const double ln = sqrt(nx * nx + ny * ny);
-        ghostq<double>(-1 - j, nx / ln, ny / ln, qb64, qn);
+        ghostq<double>(-1 - j, nx / ln, ny / ln, qb64, qn, a.qin);
       }
       lxf64(g1, s64, nx, ny, qb64, qn, fF64[k]);
 #pragma unroll
@@ -901,7 +912,7 @@ __device__ __forceinline__ void update_elem(const DevMesh& m, const DevWorkMx& w
           for (int v = 0; v < 4; ++v) qn[v] = st.avg[(size_t)v * N + j];
         } else {
           const double ln = sqrt(nx * nx + ny * ny);
-          ghostq<double>(-1 - j, nx / ln, ny / ln, qb, qn);
+          ghostq<double>(-1 - j, nx / ln, ny / ln, qb, qn, a.qin);
         }
         lxf64(g1, sc.s, nx, ny, qb, qn, ff);
         const double t = (double)th[k];
@@ -1084,7 +1095,7 @@ __device__ __forceinline__ bool gate_features(const DevMesh& m, const DevWorkMx&
     } else {
       const float nx = m.nrm32[(2 * k) * N + i], ny = m.nrm32[(2 * k + 1) * N + i];
       const float ln = sqrtf(nx * nx + ny * ny);
-      ghostq<float>(-1 - j, nx / ln, ny / ln, an, qn);
+      ghostq<float>(-1 - j, nx / ln, ny / ln, an, qn, a.qin32);
     }
     nr[k] = qn[0]; ne[k] = qn[3];
   }
@@ -1189,7 +1200,7 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
         } else {
           const float nx = m.nrm32[(2 * k) * N + i], ny = m.nrm32[(2 * k + 1) * N + i];
           const float ln = sqrtf(nx * nx + ny * ny);
-          ghostq<float>(-1 - j, nx / ln, ny / ln, an32, qn);
+          ghostq<float>(-1 - j, nx / ln, ny / ln, an32, qn, a.qin32);
         }
         nr[k] = qn[0]; ne[k] = qn[3];
         if (!(qn[0] > 0.0f)) continue;
@@ -1285,7 +1296,17 @@ __global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const D
     mbar_init(wbar, 1);
     mbar_init(mbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the weights travel while the first tiles are screened; the CTA waits
+    // for them only at its first tile that needs the network
+    constexpr unsigned bytes = (unsigned)sizeof(GateWeights);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(wbar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(&g.w)),
+                 "l"(a.gate_w), "r"(bytes), "r"(wbar)
+                 : "memory");
   }
+  // tensor memory up front: taking it inside the tile loop, only where a
+  // tile needs the network, measured slower (about 7 us per launch)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&g.tmem)),
                  "r"(kGateTmemCols)
@@ -1296,34 +1317,37 @@ __global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const D
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = g.tmem;
-  if (tid == 0) {
-    constexpr unsigned bytes = (unsigned)sizeof(GateWeights);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(wbar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(&g.w)),
-                 "l"(a.gate_w), "r"(bytes), "r"(wbar)
-                 : "memory");
-  }
-  bool abort = __syncthreads_or(!mbar_wait(wbar, 0)) != 0;
-  const bool wpending = abort;            // the weight copy may still be in flight
+  bool abort = false;
+  bool wready = false;                    // the weight copy was seen complete
   bool mpending = false;                  // an MMA group committed but not seen complete
   unsigned phase = 0;
   const unsigned a1 = smem_u32(g.a1), a2 = smem_u32(g.a2), w1 = smem_u32(g.w.w1), w2 = smem_u32(g.w.w2);
-  const unsigned lane_tmem = tmem + ((unsigned)(warp * 32) << 16);
+  const unsigned lane_off = (unsigned)(warp * 32) << 16;
   const int ntile = (N + kGateRows - 1) / kGateRows;
   unsigned long long skipped = 0;
   for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
     const int i = t * kGateRows + tid;
     // the network rules only on tiles holding a cell the exact screen cannot clear
     const bool clr = i < N && shock_screen_at<KD, ML>(m, w, state, a, i);
-    bool need_net = __syncthreads_or(i < N && !clr) != 0;
-    if (a.gate_out || a.feat_out) need_net = true;          // inspection: every cell's theta_hat / features
+    const bool inspect = a.gate_out || a.feat_out;          // every cell's theta_hat / features
+    bool need_net = inspect || __syncthreads_or(i < N && !clr) != 0;
+    if (need_net && !abort && !wready) {
+      abort = __syncthreads_or(!mbar_wait(wbar, 0)) != 0;
+      wready = !abort;
+    }
     float f[kMlpIn];
     const bool ok = need_net && i < N && gate_features<E, ML>(m, w, state, a, i, f);
     if (ok && a.feat_out) {
 #pragma unroll
       for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
     }
+    // the network is trusted only inside the envelope of its training features
+    bool inside = ok && !abort;
+    if (inside) {
+#pragma unroll
+      for (int k = 0; k < kMlpIn; ++k) inside = inside && f[k] >= g.w.lo[k] && f[k] <= g.w.hi[k];
+    }
+    if (!inspect && need_net) need_net = __syncthreads_or(inside && !clr) != 0;
     bool sk = false;
     if (need_net && !abort) {
       // this cell's features, BF16, as row tid of X (4 core matrices along K)
@@ -1360,7 +1384,7 @@ __global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const D
 #pragma unroll
       for (int c = 0; c < kMlpH / 16; ++c) {
         float v[16];
-        tmem_ld16(lane_tmem + 16u * c, v);
+        tmem_ld16(tmem + lane_off + 16u * c, v);
         unsigned h[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
@@ -1391,24 +1415,28 @@ __global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const D
 #pragma unroll
       for (int c = 0; c < kMlpH / 16; ++c) {
         float v[16];
-        tmem_ld16(lane_tmem + 16u * c, v);
+        tmem_ld16(tmem + lane_off + 16u * c, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) z = fmaf(fmaxf(v[j] + g.w.b2[16 * c + j], 0.0f), g.w.w3[16 * c + j], z);
       }
       tc_fence_before();                   // these TMEM reads precede the next tile's MMAs
       const float th_hat = 1.0f / (1.0f + __expf(-z));
-      sk = ok && !clr && th_hat >= 1.0f - a.mlp_tau;
+      sk = inside && !clr && th_hat >= 1.0f - a.mlp_tau;
       if (ok && a.gate_out) a.gate_out[i] = th_hat;
     }
     skipped += __popc(__ballot_sync(0xffffffffu, sk));
     // a cell the screen cleared keeps theta = 1 exactly as the limiter would
     if (i < N) shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, 1, i, sk || clr);
   }
-  if (abort && tid == 0) {
-    // flag it, then give the copy / MMAs in flight one more bounded wait
-    atomicOr(w.status, (unsigned)LXW_ST_TIMEOUT);
-    if (wpending) mbar_wait(wbar, 0);
-    if (mpending) mbar_wait(mbar, phase);
+  if (tid == 0) {
+    // the weight copy lands before the CTA leaves (its shared memory is
+    // released at exit); after a timeout, give the copy / MMAs in flight one
+    // more bounded wait and flag it
+    if (!wready && !mbar_wait(wbar, 0)) abort = true;
+    if (abort) {
+      atomicOr(w.status, (unsigned)LXW_ST_TIMEOUT);
+      if (mpending) mbar_wait(mbar, phase);
+    }
   }
   if (a.want_diag && (tid & 31) == 0 && skipped)
     atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->mlp_skip, skipped);

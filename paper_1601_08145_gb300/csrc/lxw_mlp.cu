@@ -110,6 +110,34 @@ __global__ void k_gather(int B, const int* __restrict__ idx, const float* __rest
   if (c == 0) yb[r] = y[s];
 }
 
+// order-preserving int key of a float (NaN excluded), and back
+__device__ __forceinline__ int fkey(float x) {
+  const int i = __float_as_int(x);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+inline float fkey_inv(int k) {
+  const int i = k >= 0 ? k : k ^ 0x7fffffff;
+  float x;
+  std::memcpy(&x, &i, sizeof x);
+  return x;
+}
+
+// per-feature minimum and maximum of X[count][24]: one column per lane
+// group, atomics on the order-preserving keys
+__global__ void k_feature_range(int count, const float* __restrict__ X, int* __restrict__ keys) {
+  const int c = threadIdx.x % lxw::kMlpIn;
+  const int r0 = blockIdx.x * (blockDim.x / lxw::kMlpIn) + threadIdx.x / lxw::kMlpIn;
+  const int rs = gridDim.x * (blockDim.x / lxw::kMlpIn);
+  if (threadIdx.x >= (blockDim.x / lxw::kMlpIn) * lxw::kMlpIn) return;
+  int lo = 0x7fffffff, hi = (int)0x80000000;
+  for (int r = r0; r < count; r += rs) {
+    const int k = fkey(X[(size_t)r * lxw::kMlpIn + c]);
+    lo = min(lo, k); hi = max(hi, k);
+  }
+  atomicMin(keys + c, lo);
+  atomicMax(keys + lxw::kMlpIn + c, hi);
+}
+
 // round to nearest even (the parameters are finite)
 __device__ __forceinline__ unsigned short bf16_rne(float x) {
   unsigned u = __float_as_uint(x);
@@ -138,6 +166,11 @@ __global__ void k_gate_layout(const float* __restrict__ p, GateWeights* __restri
 struct lxw_mlp {
   int maxB = 0;
   cudaStream_t stream = nullptr;
+  // envelope of the training features: the gate uses the prediction only
+  // for cells whose features lie inside it (unbounded until set or trained)
+  bool env_set = false;
+  float lo[kMlpIn], hi[kMlpIn];
+  int* env_keys = nullptr;                  // device: order-preserving keys of min [24], max [24]
   float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
   float *Z1 = nullptr, *H1 = nullptr, *Z2 = nullptr, *H2 = nullptr, *z3 = nullptr, *yhat = nullptr, *dz = nullptr;
   float *dH = nullptr, *Xb = nullptr, *yb = nullptr, *loss = nullptr;
@@ -225,6 +258,8 @@ lxw_status lxw_mlp_create(int max_batch, unsigned long long seed, void* stream, 
   n->Xb = (float*)al(sizeof(float) * B * kMlpIn); n->yb = (float*)al(sizeof(float) * B);
   n->idx = (int*)al(sizeof(int) * B);
   n->loss = (float*)al(sizeof(float));
+  n->env_keys = (int*)al(sizeof(int) * 2 * kMlpIn);
+  for (int k = 0; k < kMlpIn; ++k) { n->lo[k] = -INFINITY; n->hi[k] = INFINITY; }
   for (void* p : n->allocs)
     if (!p) { delete n; return mfail(LXW_ERR_NOMEM, "lxw_mlp_create: device allocation failed"); }
   // He initialisation from SplitMix64 (Box-Muller), zero biases
@@ -284,10 +319,44 @@ lxw_status lxw_mlp_loss_grad(lxw_mlp* n, const float* X, const float* y, int B, 
   return cudaGetLastError() == cudaSuccess ? LXW_OK : mfail(LXW_ERR_CUDA, "lxw_mlp_loss_grad: launch failed");
 }
 
+lxw_status lxw_mlp_set_envelope(lxw_mlp* n, const float* lo, const float* hi) {
+  if (!n || (!lo) != (!hi)) return mfail(LXW_ERR_ARG, "lxw_mlp_set_envelope: bad argument");
+  for (int k = 0; k < kMlpIn; ++k) {
+    if (lo && !(lo[k] <= hi[k])) return mfail(LXW_ERR_ARG, "lxw_mlp_set_envelope: needs lo <= hi");
+    n->lo[k] = lo ? lo[k] : -INFINITY;
+    n->hi[k] = hi ? hi[k] : INFINITY;
+  }
+  n->env_set = lo != nullptr;
+  return LXW_OK;
+}
+
+lxw_status lxw_mlp_get_envelope(const lxw_mlp* n, float* lo, float* hi) {
+  if (!n || !lo || !hi) return mfail(LXW_ERR_ARG, "lxw_mlp_get_envelope: null argument");
+  for (int k = 0; k < kMlpIn; ++k) { lo[k] = n->lo[k]; hi[k] = n->hi[k]; }
+  return LXW_OK;
+}
+
 lxw_status lxw_mlp_train(lxw_mlp* n, const float* X, const float* y, int count, int epochs, int batch, float lr,
                          unsigned long long seed, float* last_loss) {
   if (!n || !X || !y || count < 1 || epochs < 1 || batch < 1 || batch > n->maxB || !(lr > 0.0f))
     return mfail(LXW_ERR_ARG, "lxw_mlp_train: bad argument");
+  {  // widen the envelope by these features (the first training call sets it)
+    int keys[2 * kMlpIn];
+    for (int k = 0; k < kMlpIn; ++k) { keys[k] = 0x7fffffff; keys[kMlpIn + k] = (int)0x80000000; }
+    const int blocks = std::min(1024, (count + 9) / 10);
+    if (cudaMemcpyAsync(n->env_keys, keys, sizeof keys, cudaMemcpyHostToDevice, n->stream))
+      return mfail(LXW_ERR_CUDA, "lxw_mlp_train: copy failed");
+    k_feature_range<<<blocks, 240, 0, n->stream>>>(count, X, n->env_keys);
+    if (cudaMemcpyAsync(keys, n->env_keys, sizeof keys, cudaMemcpyDeviceToHost, n->stream) ||
+        cudaStreamSynchronize(n->stream))
+      return mfail(LXW_ERR_CUDA, "lxw_mlp_train: feature range failed");
+    for (int k = 0; k < kMlpIn; ++k) {
+      const float lo = fkey_inv(keys[k]), hi = fkey_inv(keys[kMlpIn + k]);
+      n->lo[k] = n->env_set ? std::min(n->lo[k], lo) : lo;
+      n->hi[k] = n->env_set ? std::max(n->hi[k], hi) : hi;
+    }
+    n->env_set = true;
+  }
   uint64_t x = seed;
   std::vector<int> perm(count);
   float loss = 0.0f;
@@ -322,6 +391,9 @@ lxw_status lxw_mlp_train(lxw_mlp* n, const float* X, const float* y, int count, 
 namespace lxw {
 int mlp_gate_weights(lxw_mlp* n, GateWeights* out) {
   k_gate_layout<<<(kMlpH * kMlpH + 255) / 256, 256, 0, n->stream>>>(n->params, out);
+  if (cudaMemcpyAsync(out->lo, n->lo, sizeof n->lo, cudaMemcpyHostToDevice, n->stream) ||
+      cudaMemcpyAsync(out->hi, n->hi, sizeof n->hi, cudaMemcpyHostToDevice, n->stream))
+    return -1;
   return cudaStreamSynchronize(n->stream) == cudaSuccess ? 0 : -1;
 }
 }  // namespace lxw

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblxw.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_NONPOSITIVE, ERR_CFL, ERR_NAN, ERR_BOUNDS, ERR_TIMEOUT, ERR_NOMEM = range(9)
-BC_PERIODIC, BC_REFLECT, BC_TRANSPARENT = 0, 1, 2
+BC_PERIODIC, BC_REFLECT, BC_TRANSPARENT, BC_INFLOW = 0, 1, 2, 3
 KIND_QUAD, KIND_TRI = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 ST_NONPOSITIVE, ST_CFL, ST_NAN = 1, 2, 4
@@ -32,7 +32,8 @@ EXPORTS = [
     "lxw_batch_create", "lxw_batch_scalars", "lxw_autotune",
     "lxw_mlp_create", "lxw_mlp_destroy", "lxw_mlp_num_params", "lxw_mlp_get_params", "lxw_mlp_set_params",
     "lxw_mlp_forward", "lxw_mlp_loss_grad", "lxw_mlp_train", "lxw_solver_set_mlp", "lxw_step_dump",
-    "lxw_step_gate", "lxw_profile_phases", "lxw_basis_eval",
+    "lxw_step_gate", "lxw_profile_phases", "lxw_basis_eval", "lxw_mesh_cartesian_masked",
+    "lxw_solver_set_inflow", "lxw_mlp_set_envelope", "lxw_mlp_get_envelope",
 ]
 
 
@@ -84,6 +85,9 @@ def lib():
     L.lxw_solver_destroy.argtypes = [_vp]
     L.lxw_solver_destroy.restype = None
     L.lxw_solver_set_stream.argtypes = [_vp, _vp]
+    L.lxw_mesh_cartesian_masked.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _ip,
+                                            C.POINTER(C.c_ubyte), C.c_int, C.POINTER(_vp)]
+    L.lxw_solver_set_inflow.argtypes = [_vp, _dp]
     L.lxw_solver_info.argtypes = [_vp, _ip, _ip, _ip, _ip, _ip]
     L.lxw_projection_points.argtypes = [_vp, _dp]
     L.lxw_project.argtypes = [_vp, _vp, _vp]
@@ -110,6 +114,8 @@ def lib():
     L.lxw_mlp_get_params.argtypes = [_vp, _vp]
     L.lxw_mlp_set_params.argtypes = [_vp, _vp]
     L.lxw_mlp_forward.argtypes = [_vp, _vp, C.c_int, _vp]
+    L.lxw_mlp_set_envelope.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+    L.lxw_mlp_get_envelope.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.lxw_mlp_loss_grad.argtypes = [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_float), _vp]
     L.lxw_mlp_train.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong,
                                 C.POINTER(C.c_float)]
@@ -176,6 +182,17 @@ def lxw_mesh_cartesian(nx, ny, box=(0.0, 1.0, 0.0, 1.0), bc=(BC_PERIODIC,) * 4):
     return Mesh(h)
 
 
+def lxw_mesh_cartesian_masked(nx, ny, box, bc, mask, mask_bc=BC_REFLECT):
+    """Cartesian grid without the cells where mask[iy][ix] == 0; faces towards
+    those cells get mask_bc."""
+    h = _vp()
+    b = (C.c_int * 4)(*bc)
+    mk = np.ascontiguousarray(mask, dtype=np.uint8).reshape(ny, nx)
+    _check(lib().lxw_mesh_cartesian_masked(nx, ny, box[0], box[1], box[2], box[3], b,
+                                           mk.ctypes.data_as(C.POINTER(C.c_ubyte)), mask_bc, C.byref(h)))
+    return Mesh(h)
+
+
 def lxw_mesh_triangles(xy, tv, ebc=None):
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     tv = np.ascontiguousarray(tv, dtype=np.int32)
@@ -221,6 +238,12 @@ def lxw_solver_create(mesh, degree, options=None, stream=None):
 
 def lxw_solver_set_stream(solver, stream):
     _check(lib().lxw_solver_set_stream(solver.h, _stream_handle(stream)))
+
+
+def lxw_solver_set_inflow(solver, prim):
+    """State (rho, u, v, p) of the solver's inflow faces."""
+    p = np.ascontiguousarray(prim, dtype=np.float64)
+    _check(lib().lxw_solver_set_inflow(solver.h, p.ctypes.data_as(_dp)))
 
 
 def lxw_projection_points(solver):
@@ -459,6 +482,22 @@ def lxw_mlp_train(mlp, X, y, epochs, batch, lr, seed=7):
     _check(lib().lxw_mlp_train(mlp.h, _fptr(X, (X.shape[0], MLP_IN), "X"), _fptr(y, (X.shape[0],), "y"), X.shape[0],
                                epochs, batch, lr, seed, C.byref(loss)))
     return loss.value
+
+
+def lxw_mlp_set_envelope(mlp, lo=None, hi=None):
+    """Per-feature bounds inside which the gate uses the network (None, None: unbounded)."""
+    if lo is None or hi is None:
+        _check(lib().lxw_mlp_set_envelope(mlp.h, None, None))
+        return
+    l = np.ascontiguousarray(lo, dtype=np.float32); h = np.ascontiguousarray(hi, dtype=np.float32)
+    assert l.shape == h.shape == (MLP_IN,)
+    _check(lib().lxw_mlp_set_envelope(mlp.h, l.ctypes.data_as(C.POINTER(C.c_float)), h.ctypes.data_as(C.POINTER(C.c_float))))
+
+
+def lxw_mlp_get_envelope(mlp):
+    l = np.zeros(MLP_IN, np.float32); h = np.zeros(MLP_IN, np.float32)
+    _check(lib().lxw_mlp_get_envelope(mlp.h, l.ctypes.data_as(C.POINTER(C.c_float)), h.ctypes.data_as(C.POINTER(C.c_float))))
+    return l, h
 
 
 def lxw_solver_set_mlp(solver, mlp, tau=0.05):

@@ -176,6 +176,10 @@ def normal_shock_state(mach, rho0=1.4, p0=1.0, gamma=1.4):
 DIFFRACTION_BOX = (0.0, 13.0, 0.0, 11.0)
 DIFFRACTION_STEP = (1.0, 6.0)       # the step occupies [0, 1] x [0, 6]
 DIFFRACTION_MACH = 5.09
+# (left, right, bottom, top) codes: inflow on the left side (which the mesh
+# keeps above the step only), transparent elsewhere; the step's faces are
+# walls through the mask code
+DIFFRACTION_BC = (3, 2, 2, 2)
 
 
 def diffraction_mask(nx, ny):

@@ -146,6 +146,33 @@ def test_training_and_gated_step(L):
     print(f"gated blast: skipped {res[True][1]:.0f} cell-steps, density L1 distance {rel:.2e}")
     assert rel < 2e-2
 
+    # the envelope: training recorded the range of its features exactly
+    lo, hi = L.lxw_mlp_get_envelope(net)
+    Xt = X[:ntr].cpu().numpy()
+    assert np.array_equal(lo, Xt.min(axis=0)) and np.array_equal(hi, Xt.max(axis=0))
+    # an empty envelope: the gate trusts no cell, skips none, and the gated
+    # step is the plain step bit for bit; unbounded again: it skips
+    res = {}
+    for mode in ("plain", "empty", "unbounded"):
+        s = mixed_solver(L, "quad", 48, box=(-1.1, 1.1, -1.1, 1.1), bc=(1, 1, 1, 1))
+        if mode == "empty":
+            L.lxw_mlp_set_envelope(net, np.full(24, 100.0), np.full(24, 100.0))
+        elif mode == "unbounded":
+            L.lxw_mlp_set_envelope(net)
+        if mode != "plain":
+            L.lxw_solver_set_mlp(s, net, 0.5)
+        st = start(L, s, synth.ic_blast(48))
+        skipped = 0
+        for _ in range(20):
+            d = L.lxw_step(s, st, 0.0, 0.1, diag=True)
+            assert d["status"] == 0
+            skipped += d["n_mlp_skip"]
+        res[mode] = (st.clone(), skipped)
+    assert res["empty"][1] == 0 and torch.equal(res["empty"][0], res["plain"][0])
+    assert res["unbounded"][1] > 0
+    L.lxw_mlp_set_envelope(net, lo, hi)
+    assert np.array_equal(L.lxw_mlp_get_envelope(net)[0], lo)
+
 
 def bf16(x):
     """Round float32 values to BF16 (nearest even), returned as float32."""

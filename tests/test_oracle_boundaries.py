@@ -198,13 +198,13 @@ def test_inflow_driven_mach_5_09_shock(orc):
 
 
 def test_diffraction_mesh_and_first_steps(orc):
-    """The step geometry at 1/10 of the paper's resolution: cell count, the
-    faces of the step are walls (mass balance has only the inflow and outflow
-    terms), positivity over the first steps."""
+    """The step geometry at 1/10 of the paper's resolution, its boundaries
+    (inflow above the step, walls on the step, transparent elsewhere): cell
+    count and positivity over the first steps."""
     nx, ny = 39, 33
     mask = synth.diffraction_mask(nx, ny)
     assert mask.sum() == nx * ny - 3 * 18
-    mesh = orc.Mesh.cartesian_masked(nx, ny, synth.DIFFRACTION_BOX, (orc.INFLOW, T_, R_, T_), mask, mask_bc=R_)
+    mesh = orc.Mesh.cartesian_masked(nx, ny, synth.DIFFRACTION_BOX, synth.DIFFRACTION_BC, mask, mask_bc=R_)
     sol = orc.Solver(mesh, 2, gamma=G)
     sol.set_inflow(synth.normal_shock_state(synth.DIFFRACTION_MACH))
     Q = sol.project_fn(synth.ic_diffraction)
