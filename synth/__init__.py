@@ -197,3 +197,68 @@ def ic_diffraction(x, y):
     r1, u1, _, p1 = normal_shock_state(DIFFRACTION_MACH)
     left = x < DIFFRACTION_STEP[0]
     return np.where(left, r1, 1.4), np.where(left, u1, 0.0), 0.0 * x, np.where(left, p1, 1.0)
+
+
+# ------------------------------------------------ Sedov blast on a disk
+SEDOV_RADIUS = 1.1
+SEDOV_ENERGY = 0.979264
+
+
+def disk_triangles(ntri: int, radius: float = SEDOV_RADIUS, jitter: float = 0.15, seed: int = 20160129):
+    """Exactly ntri counter-clockwise triangles covering the polygon inscribed
+    in the circle of the given radius: B points on the circle and the V points
+    of a jittered triangular lattice closest to the centre, Delaunay
+    triangulated (scipy).  All hull points lie on the circle, so Euler's
+    formula fixes the count, ntri = 2 V + B - 2, and B and V are chosen for it.
+    Returns xy [nv][2], tv [ntri][3] (boundary vertices first)."""
+    from scipy.spatial import Delaunay
+
+    def lattice(h):
+        # rows y = j h sqrt(3)/2, odd rows shifted by h/2; the points inside r < radius - h/2
+        mi = int(np.ceil(radius / h)) + 2
+        mj = int(np.ceil(radius / (h * np.sqrt(3.0) / 2.0))) + 2
+        jj, ii = np.meshgrid(np.arange(-mj, mj + 1), np.arange(-mi, mi + 1), indexing="ij")
+        lat = np.stack([(ii + 0.5 * (jj & 1)) * h, jj * h * np.sqrt(3.0) / 2.0], axis=-1).reshape(-1, 2)
+        return lat[np.hypot(lat[:, 0], lat[:, 1]) < radius - 0.5 * h]
+
+    # the spacing at which the ring count that Euler's formula leaves, B = ntri + 2 - 2 V(h),
+    # equals the natural one, 2 pi radius / h (bisection; V(h) falls as h grows)
+    h0 = np.sqrt(np.pi * radius ** 2 * 4.0 / (np.sqrt(3.0) * ntri))
+    lo, hi = 0.8 * h0, 1.25 * h0
+    for _ in range(60):
+        h = 0.5 * (lo + hi)
+        if ntri + 2 - 2 * len(lattice(h)) < 2.0 * np.pi * radius / h:
+            lo = h
+        else:
+            hi = h
+    h = hi
+    inner = lattice(h)
+    B = ntri + 2 - 2 * len(inner)
+    if B < 3:
+        raise ValueError("disk_triangles: no admissible spacing")
+    th = 2.0 * np.pi * np.arange(B) / B
+    ring = radius * np.stack([np.cos(th), np.sin(th)], axis=1)
+    rng = np.random.default_rng(seed)
+    inner = inner + rng.uniform(-jitter, jitter, size=inner.shape) * h
+    xy = np.concatenate([ring, inner])
+    tv = Delaunay(xy).simplices.astype(np.int32)
+    a, b, c = xy[tv[:, 0]], xy[tv[:, 1]], xy[tv[:, 2]]
+    det = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    flip = det < 0
+    tv[flip, 1], tv[flip, 2] = tv[flip, 2].copy(), tv[flip, 1].copy()
+    if len(tv) != ntri:
+        raise ValueError(f"disk_triangles: {len(tv)} triangles, expected {ntri}")
+    return xy, tv
+
+
+def ic_sedov_disk(ntri: int, radius: float = SEDOV_RADIUS, e_total: float = SEDOV_ENERGY, gamma: float = GAMMA):
+    """Gas at rest, rho = 1, E = 1e-12, except E = e_total / (pi r_d^2) inside
+    r_d = sqrt(pi radius^2 / ntri), the mesh's characteristic length."""
+    r_d = np.sqrt(np.pi * radius ** 2 / ntri)
+    e_in = e_total / (np.pi * r_d ** 2)
+
+    def f(x, y):
+        e = np.where(np.hypot(x, y) < r_d, e_in, 1e-12)
+        z = 0.0 * x
+        return 1.0 + z, z, z, (gamma - 1.0) * e
+    return f
