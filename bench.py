@@ -49,6 +49,9 @@ WORKLOADS = {
                      desc="rarefaction: 724x724x2 = 1,048,352 jittered triangles, P2, rho=1 p=0.4 u=-+2, transparent"),
     "blast2048": dict(kind="quad", n=2048, deg=2, cfl=0.1, ic=None, bc=(1, 1, 1, 1), box=(-1.1, 1.1, -1.1, 1.1),
                       desc="blast: 2048x2048 Cartesian, P2, point energy 0.979264 in the 4 centre cells, reflective"),
+    "sedov": dict(kind="disk", n=136270, deg=2, cfl=0.1, ic=synth.ic_sedov_disk(136270),
+                  desc="Sedov blast on a disk: 136,270 Delaunay triangles of the circle of radius 1.1 "
+                       "(jittered triangular lattice), P2, point energy 0.979264 inside r_d, reflective rim"),
     "diffraction": dict(kind="step", nx=390, ny=330, deg=2, cfl=0.1, ic=synth.ic_diffraction,
                         box=synth.DIFFRACTION_BOX, bc=synth.DIFFRACTION_BC,
                         desc="shock diffraction: Mach 5.09 over a step, 390x330 Cartesian on [0,13]x[0,11] less the "
@@ -67,7 +70,7 @@ ENSEMBLE = dict(count=256, lo=32, hi=256, seed=4242, deg=2, cfl=0.3,
 def ck_flops_per_element(kind, deg):
     ML = (deg + 1) * (deg + 2) // 2
     NQ = (deg + 1) ** 2
-    NE = (3 if kind == "tri" else 4) * (deg + 1)
+    NE = (3 if kind in ("tri", "disk") else 4) * (deg + 1)
     npt = NQ + NE
     contract = 2 * 4 * ML * npt + 2 * 2 * 2 * 4 * ML * NQ + 2 * (2 * 2 * 4 * ML * npt) + 2 * 2 * 4 * ML * NQ
     return contract + 250 * npt
@@ -89,6 +92,9 @@ def build_solver(L, w, stream, mixed):
     if w["kind"] == "tri":
         xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
         mesh = L.lxw_mesh_triangles(xy, tv)
+    elif w["kind"] == "disk":
+        xy, tv = synth.disk_triangles(w["n"])
+        mesh = L.lxw_mesh_triangles(xy, tv, np.full((w["n"], 3), L.BC_REFLECT, np.int32))
     elif w["kind"] == "step":
         mesh = L.lxw_mesh_cartesian_masked(w["nx"], w["ny"], w["box"], w["bc"],
                                            synth.diffraction_mask(w["nx"], w["ny"]), L.BC_REFLECT)
@@ -107,6 +113,9 @@ def oracle_solver(w):
     if w["kind"] == "tri":
         xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
         m = O.Mesh.triangles(xy, tv)
+    elif w["kind"] == "disk":
+        xy, tv = synth.disk_triangles(w["n"])
+        m = O.Mesh.triangles(xy, tv, np.full((w["n"], 3), O.REFLECT, np.int32))
     elif w["kind"] == "step":
         m = O.Mesh.cartesian_masked(w["nx"], w["ny"], w["box"], w["bc"], synth.diffraction_mask(w["nx"], w["ny"]),
                                     O.REFLECT)
@@ -121,6 +130,8 @@ def oracle_solver(w):
 def half_resolution(w):
     if w["kind"] == "step":
         return dict(w, nx=w["nx"] // 2, ny=w["ny"] // 2)
+    if w["kind"] == "disk":   # half the spacing: a quarter of the cells, r_d of that mesh
+        return dict(w, n=w["n"] // 4, ic=synth.ic_sedov_disk(w["n"] // 4))
     return dict(w, n=w["n"] // 2)
 
 
@@ -418,6 +429,22 @@ def locate(wc, pts):
     x, y = pts[:, 0], pts[:, 1]
     ix = np.clip(np.floor((x - x0) / hx).astype(np.int64), 0, ncx - 1)
     iy = np.clip(np.floor((y - y0) / hy).astype(np.int64), 0, ncy - 1)
+    if wc["kind"] == "disk":
+        from scipy.spatial import Delaunay
+        xy, tv = synth.disk_triangles(wc["n"])
+        B = int(np.count_nonzero(np.abs(np.hypot(xy[:, 0], xy[:, 1]) - synth.SEDOV_RADIUS) < 1e-12))
+        # points outside the coarse polygon (between its chords and the fine one's) move inside
+        # its inscribed circle
+        rin = synth.SEDOV_RADIUS * np.cos(np.pi / B) * (1.0 - 1e-9)
+        rr = np.hypot(pts[:, 0], pts[:, 1])
+        p = np.where((rr > rin)[:, None], pts * (rin / np.maximum(rr, 1e-300))[:, None], pts)
+        e = Delaunay(xy).find_simplex(p)     # the simplex order is the mesh's (only orientations were fixed)
+        assert np.all(e >= 0), "a point outside the coarse disk mesh"
+        v0, v1, v2 = xy[tv[e, 0]], xy[tv[e, 1]], xy[tv[e, 2]]
+        ax, ay, bx, by = v1[:, 0] - v0[:, 0], v1[:, 1] - v0[:, 1], v2[:, 0] - v0[:, 0], v2[:, 1] - v0[:, 1]
+        det = ax * by - ay * bx
+        px, py = p[:, 0] - v0[:, 0], p[:, 1] - v0[:, 1]
+        return e, np.stack([(px * by - py * bx) / det, (ax * py - ay * px) / det], axis=1)
     if wc["kind"] in ("quad", "step"):
         ref = np.stack([2.0 * ((x - x0) / hx - ix) - 1.0, 2.0 * ((y - y0) / hy - iy) - 1.0], axis=1)
         cell = iy * ncx + ix
@@ -476,7 +503,7 @@ def discretization_check(L, stream, name, net, tau, steps):
     pts = L.lxw_projection_points(sf)
     N, npj = pts.shape[0], pts.shape[1]
     elem, ref = locate(wc, pts.reshape(-1, 2))
-    phi = L.lxw_basis_eval(1 if w["kind"] == "tri" else 0, w["deg"], ref)
+    phi = L.lxw_basis_eval(1 if w["kind"] in ("tri", "disk") else 0, w["deg"], ref)
     rc = np.einsum("pl,pl->p", Qc[:, 0, :].cpu().numpy()[elem], phi).reshape(N, npj)
     prim = np.stack([rc, np.zeros_like(rc), np.zeros_like(rc), np.ones_like(rc)], axis=-1)
     Qp = torch.zeros(sf.q64_shape, dtype=torch.float64, device="cuda")
@@ -484,10 +511,11 @@ def discretization_check(L, stream, name, net, tau, steps):
     rho_f = Qf[:, 0, 0].cpu().numpy()
     rho_p = Qp[:, 0, 0].cpu().numpy()
     rho_m = L.to_q64(sm, Qm)[:, 0, 0].cpu().numpy()
-    if w["kind"] != "tri":
+    if w["kind"] not in ("tri", "disk"):
         area = np.full(N, 1.0 / N)
     else:
-        xy, tv = synth.structured_triangles(w["n"], jitter=0.2, seed=20160129)
+        xy, tv = (synth.disk_triangles(w["n"]) if w["kind"] == "disk"
+                  else synth.structured_triangles(w["n"], jitter=0.2, seed=20160129))
         v0, v1, v2 = xy[tv[:, 0]], xy[tv[:, 1]], xy[tv[:, 2]]
         area = 0.5 * np.abs((v1[:, 0] - v0[:, 0]) * (v2[:, 1] - v0[:, 1]) - (v1[:, 1] - v0[:, 1]) * (v2[:, 0] - v0[:, 0]))
     e = float(np.sum(area * np.abs(rho_f - rho_p)))
