@@ -186,17 +186,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def train_indicator(L, stream, tau=0.02):
+TRAINING_RUNS = (("smooth", 40, 4), ("rarefy", 60, 6), ("blast", 40, 10), ("diffraction", 60, 6), ("sedov", 60, 6))
+
+
+def train_indicator(L, stream, tau=0.01):
     """Train the troubled-cell MLP on the GPU from (features, limiter theta)
     pairs that plain mixed runs of the benchmark configurations produce (the
     smooth wave 32x32, the rarefaction on 100,352 triangles, the blast on
-    1024x1024); every limited pair is kept, the others are subsampled to
-    about 400k, and the limited pairs are repeated to a quarter of the set.
+    1024x1024, the shock diffraction on 123,300 squares, the Sedov disk on
+    136,270 triangles); every limited pair is kept, the others are subsampled
+    to about 400k, and the limited pairs are repeated to a quarter of the set.
     Returns the net and a summary (held-out numbers on 20 % of the pairs)."""
     import torch
     gen = torch.Generator(device="cuda").manual_seed(7)
     Xs, ys = [], []
-    for name, steps, every in (("smooth", 40, 4), ("rarefy", 60, 6), ("blast", 40, 10)):
+    for name, steps, every in TRAINING_RUNS:
         w, sol = build_workload(L, name, stream, True)
         st = project(L, sol, w)
         for k in range(steps):
@@ -533,7 +537,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rarefy", choices=sorted(WORKLOADS) + ["ensemble"])
-    ap.add_argument("--tau", type=float, default=0.02, help="learned gate: skip where theta_hat >= 1 - tau")
+    ap.add_argument("--tau", type=float, default=0.01, help="learned gate: skip where theta_hat >= 1 - tau")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work list of the mixed forms")
     ap.add_argument("--form", default="all", choices=["all", "learned", "mixed", "fp64"],
