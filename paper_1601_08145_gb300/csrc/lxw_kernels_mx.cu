@@ -933,7 +933,7 @@ __device__ __forceinline__ void update_elem(const DevMesh& m, const DevWorkMx& w
   }
 }
 
-// six resident CTAs per SM (80 registers): 1M-element meshes run in full waves
+// six resident CTAs per SM (80 registers): more warps hide the gathers' latency
 // (update 86 -> 70 us on 1024^2 squares); small spills only in the theta < 1 path
 template <int E, int ML>
 __global__ void __launch_bounds__(128, 6) k_update_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
