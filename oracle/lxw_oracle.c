@@ -11,7 +11,9 @@
  *    q_tt = -div (F_t)^h taken of the projected expansions (Sec. 2.3 Step 2).
  *  - Moment limiter secant: theta_m = theta_rho (p0 - eps_p)/(p0 - p^{theta_rho}_m)
  *    where p^{theta_rho}_m < eps_p (Lemma 1 with the density factor), floors
- *    eps_rho = min(eps0, rho_avg/2), eps_p = min(eps0, p_avg/2).
+ *    eps_rho = min(eps0, rho_avg/2), eps_p = min(eps0, p_avg/2).  Optional
+ *    variant (the exact computation Sec. 3.1 mentions): theta_m = the root in
+ *    (0, theta_rho) of rho p - eps_p rho along the limited state, a quadratic.
  *  - Density flux limiter: every edge with a negative density flux
  *    difference gets the same Lambda = (Gamma^rho - |T| eps/dt)/|sum of the
  *    negative ones|, clipped to [0,1] (the four cases of Step 4, extended to
@@ -506,6 +508,7 @@ struct orc_solver {
   int deg, ML, E, NQ, MQ, NPT, NPJ;
   double gamma, eps0, alpha0;
   int shock_limiter;
+  int moment_exact;                         /* Step 2 by the exact root instead of the secant */
   double qx[MAXQ], qy[MAXQ], qw[MAXQ];
   double gs[MAXMQ], gw[MAXMQ];
   /* points: 0..NQ-1 interior, then edge k point p at NQ + k*MQ + p */
@@ -578,6 +581,10 @@ void orc_solver_free(orc_solver* s) {
 void orc_solver_set_params(orc_solver* s, double eps0, double alpha0, int shock_limiter) {
   s->eps0 = eps0; s->alpha0 = alpha0; s->shock_limiter = shock_limiter;
 }
+
+/* Sec. 3.1 notes that the optimal theta could be computed exactly instead
+ * of by Lemma 1's secant; flag 1 selects that variant. */
+void orc_solver_set_moment_exact(orc_solver* s, int flag) { s->moment_exact = flag; }
 
 /* the state of inflow boundaries from primitive values (rho, u, v, p) */
 void orc_solver_set_inflow(orc_solver* s, const double* prim) {
@@ -701,7 +708,8 @@ static double moment_limit_element(const orc_solver* s, double* Qi, int* status)
       if (t < th_r) th_r = t;
     }
   }
-  /* Step 2 (Lemma 1): secant through (0, p0) and (theta_rho, p^{theta_rho}_m) */
+  /* Step 2 (Lemma 1): secant through (0, p0) and (theta_rho, p^{theta_rho}_m);
+   * or, with moment_exact, the point's exact crossing of eps_p */
   double eps_p = fmin(s->eps0, 0.5 * pbar);
   double th = th_r;
   for (int p = 0; p < s->NPT; ++p) {
@@ -709,7 +717,24 @@ static double moment_limit_element(const orc_solver* s, double* Qi, int* status)
     for (int v = 0; v < NV; ++v) qt[v] = qbar[v] + th_r * dev[p][v];
     double pt = pressure(g, qt);
     if (pt < eps_p) {
-      double t = th_r * (pbar - eps_p) / (pbar - pt);
+      double t;
+      if (s->moment_exact) {
+        /* (rho p)^theta - eps_p rho^theta over (g-1) along q(theta) = qbar + theta dev
+         * (the quadratic of Eq. product-rho-p shifted by the floor): h0 + h1 t + h2 t^2,
+         * positive at 0, negative at theta_rho: its one root there, cancellation-free */
+        double kappa = eps_p / (g - 1.0);
+        const double* d = dev[p];
+        double h0 = qbar[0] * qbar[3] - 0.5 * (qbar[1] * qbar[1] + qbar[2] * qbar[2]) - kappa * qbar[0];
+        double h1 = qbar[0] * d[3] + d[0] * qbar[3] - (qbar[1] * d[1] + qbar[2] * d[2]) - kappa * d[0];
+        double h2 = d[0] * d[3] - 0.5 * (d[1] * d[1] + d[2] * d[2]);
+        double disc = h1 * h1 - 4.0 * h0 * h2;
+        if (disc < 0.0) disc = 0.0;
+        double den = -h1 + sqrt(disc);
+        t = den > 0.0 ? 2.0 * h0 / den : 0.0;
+        if (t > th_r) t = th_r;
+      } else {
+        t = th_r * (pbar - eps_p) / (pbar - pt);
+      }
       if (t < th) th = t;
     }
   }

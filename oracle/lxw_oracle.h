@@ -73,6 +73,8 @@ void orc_mesh_geometry(const orc_mesh* m, double* area, double* perim, double* c
 orc_solver* orc_solver_new(const orc_mesh* m, int deg, double gamma);
 void orc_solver_free(orc_solver* s);
 void orc_solver_set_params(orc_solver* s, double eps0, double alpha0, int shock_limiter);
+/* 1: the moment limiter's pressure step by the exact root (Sec. 3.1 remark), 0: secant */
+void orc_solver_set_moment_exact(orc_solver* s, int flag);
 /* state of the inflow boundaries, primitive (rho, u, v, p) */
 void orc_solver_set_inflow(orc_solver* s, const double* prim);
 /* Cartesian mesh without the cells of mask == 0 (mask[ny][nx], row order);

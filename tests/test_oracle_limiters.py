@@ -51,6 +51,44 @@ def test_moment_limiter_positivity_and_feasibility(orc, deg):
             assert ok[grid <= th[i] - 1e-12].all()
 
 
+@pytest.mark.parametrize("deg", [2, 3])
+def test_moment_limiter_exact_root_is_the_largest_feasible_theta(orc, deg):
+    """The exact-root variant (Sec. 3.1 remarks that the optimal theta can be
+    computed exactly): theta equals the supremum of the feasible set
+    {theta: rho >= eps_rho and p >= eps_p at every point}, found here by
+    bisection of that set (an interval [0, theta*]: density is linear and
+    pressure concave in theta), and is never below Lemma 1's secant."""
+    for mesh in small_meshes(orc):
+        exact = orc.Solver(mesh, deg, gamma=G, moment_exact=True)
+        secant = orc.Solver(mesh, deg, gamma=G)
+        Q0 = synth.random_modal_state(mesh.N, exact.ML, seed=200 + deg, amp=1.2)
+        Q0[::2, :, 1:] *= 0.02 * np.arange(1, mesh.N + 1, 2)[:, None, None] / mesh.N
+        Qe, Qs = Q0.copy(), Q0.copy()
+        te, st = exact.moment_limit(Qe)
+        ts, _ = secant.moment_limit(Qs)
+        assert st == 0
+        assert np.all(te >= ts - 1e-15) and np.any(te > ts + 1e-6)
+        assert np.array_equal(Qe[:, :, 0], Q0[:, :, 0])
+        qu = exact.eval_limiter_points(Q0)
+        rbar = Q0[:, 0, 0]; pbar = pressure(Q0[:, :, 0])
+        eps_r = np.minimum(1e-12, rbar / 2); eps_p = np.minimum(1e-12, pbar / 2)
+        for i in range(mesh.N):
+            qb = Q0[i, :, 0]
+
+            def feasible(t):
+                qs = qb[None] + t * (qu[i] - qb[None])
+                return bool(np.all(qs[:, 0] >= eps_r[i]) and np.all(pressure(qs) >= eps_p[i]))
+
+            if feasible(1.0):
+                assert te[i] == 1.0
+                continue
+            lo, hi = 0.0, 1.0
+            for _ in range(200):
+                mid = 0.5 * (lo + hi)
+                lo, hi = (mid, hi) if feasible(mid) else (lo, mid)
+            assert abs(te[i] - lo) <= 1e-9 * max(lo, 1e-3), (i, te[i], lo, ts[i])
+
+
 def test_mu_solve_matches_bisection(orc):
     rng = np.random.default_rng(3)
     hits = 0
