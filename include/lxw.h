@@ -78,7 +78,12 @@ typedef struct {
   int high_occupancy;       /* mixed form: 1 = the edge and gated-shock kernels'
                                variants with more resident CTAs per SM (fewer
                                registers), faster on large meshes (0 default)  */
-  int reserved[7];
+  int moment_exact;         /* 1 = the moment limiter's pressure step takes, per
+                               point, the exact largest theta (the root of
+                               rho p - eps_p rho, a quadratic in theta) instead of
+                               Lemma 1's secant (Sec. 3.1 remarks it can be
+                               computed exactly); never more damping (0 default) */
+  int reserved[6];
 } lxw_options;
 
 /* Per-step diagnostics (filled when a non-NULL pointer is passed). */

@@ -139,6 +139,7 @@ struct StepArgs {
   double fin[4], gin[4];             // its Euler fluxes F(q_in), G(q_in)
   float qin32[4], fin32[4], gin32[4];  // FP32 copies (mixed form)
   int shock_limiter;
+  int moment_exact;                  // moment limiter: exact root instead of the secant
   int want_diag;
   double* theta_cell;     // [2][N] or null
   double* theta_edge;     // [N][E] or null

@@ -122,6 +122,21 @@ __device__ __forceinline__ void ghost_state(int bc, double nxh, double nyh, cons
   }
 }
 
+// Largest theta in [0, thr] keeping p >= ep at a point whose limited state is
+// q(theta) = qbar + theta d (Sec. 3.1: the optimal theta computed exactly).
+// h(theta) = (rho p - ep rho)/(g-1) = h0 + h1 theta + h2 theta^2 is positive
+// at 0 and negative at thr when it is called, so it has one root in between,
+// taken in the cancellation-free form.
+__device__ __forceinline__ double exact_root_theta(double rb, double mb, double nb, double eb, const double d[4],
+                                                   double kappa, double thr) {
+  const double h0 = rb * eb - 0.5 * (mb * mb + nb * nb) - kappa * rb;
+  const double h1 = rb * d[3] + d[0] * eb - (mb * d[1] + nb * d[2]) - kappa * d[0];
+  const double h2 = d[0] * d[3] - 0.5 * (d[1] * d[1] + d[2] * d[2]);
+  const double disc = fmax(h1 * h1 - 4.0 * h0 * h2, 0.0);
+  const double den = -h1 + sqrt(disc);
+  return den > 0.0 ? fmin(2.0 * h0 / den, thr) : 0.0;
+}
+
 // ------------------------------------------------------------ k_reset
 __global__ void k_reset(DevWork w, int want_diag) {
   *w.smax = 0ull;
@@ -138,7 +153,9 @@ __global__ void k_reset(DevWork w, int want_diag) {
 // Sec. 3.1 Steps 0-2 (Lemma 1 secant with the density factor), then the
 // contribution of this element to the global wave speed s (max of |u|+c
 // over the average and the limited point values).
-template <int KD, int E, int ML, int NQ, int MQ>
+// EXACT: the exact-root variant of the pressure step (a separate instance, so
+// that the default one keeps its registers)
+template <int KD, int E, int ML, int NQ, int MQ, bool EXACT = false>
 __global__ void __launch_bounds__(128) k_moment(const DevMesh m, const DevWork w, double* __restrict__ Q,
                                                 const StepArgs a, double* __restrict__ theta_out) {
   constexpr int NPT = NQ + E * MQ;
@@ -187,7 +204,8 @@ __global__ void __launch_bounds__(128) k_moment(const DevMesh m, const DevWork w
         double r = rb + thr * d[p][0], mm = mb + thr * d[p][1], nn = nb + thr * d[p][2], ee = eb + thr * d[p][3];
         double ri = 1.0 / r, kin2 = mm * mm + nn * nn;
         double pt = g1 * (ee - 0.5 * kin2 * ri);
-        if (pt < ep) th = fmin(th, thr * (pb - ep) / (pb - pt));
+        if (pt < ep)
+          th = fmin(th, EXACT ? exact_root_theta(rb, mb, nb, eb, d[p], ep / g1, thr) : thr * (pb - ep) / (pb - pt));
         double pp = pt > 0.0 ? pt : 0.0;
         smax = fmax(smax, sqrt(kin2) * ri + sqrt(g * pp * ri));
       }
@@ -708,7 +726,10 @@ int step_impl(const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a, 
   mark();
   k_reset<<<1, 1, 0, st>>>(w, a.want_diag);
   mark();
-  k_moment<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, Q, a, a.theta_cell);
+  if (a.moment_exact)
+    k_moment<KD, E, ML, NQ, MQ, true><<<grid, block, 0, st>>>(m, w, Q, a, a.theta_cell);
+  else
+    k_moment<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, Q, a, a.theta_cell);
   mark();
   if (upto < 2) return cudaGetLastError() == cudaSuccess ? 0 : -1;
   k_ck<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, Q, a);
@@ -732,7 +753,10 @@ template <int KD, int E, int ML, int NQ, int MQ>
 int moment_impl(const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a, double* theta,
                 cudaStream_t st, int block) {
   k_reset<<<1, 1, 0, st>>>(w, 0);
-  k_moment<KD, E, ML, NQ, MQ><<<grid_for(m.N, block), block, 0, st>>>(m, w, Q, a, theta);
+  if (a.moment_exact)
+    k_moment<KD, E, ML, NQ, MQ, true><<<grid_for(m.N, block), block, 0, st>>>(m, w, Q, a, theta);
+  else
+    k_moment<KD, E, ML, NQ, MQ><<<grid_for(m.N, block), block, 0, st>>>(m, w, Q, a, theta);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

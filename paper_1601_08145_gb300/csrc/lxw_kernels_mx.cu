@@ -115,6 +115,21 @@ __device__ __forceinline__ void ghostq(int bc, T nxh, T nyh, const T qi[4], T qo
 }
 
 // ----------------------------------------------------------- FP64 helpers
+// Largest theta in [0, thr] keeping p >= ep at a point whose limited state is
+// q(theta) = qbar + theta d (Sec. 3.1: the optimal theta computed exactly).
+// h(theta) = (rho p - ep rho)/(g-1) = h0 + h1 theta + h2 theta^2 is positive
+// at 0 and negative at thr when it is called: its one root there, in the
+// cancellation-free form.
+__device__ __forceinline__ double exact_root_theta(double rb, double mb, double nb, double eb, const double d[4],
+                                                   double kappa, double thr) {
+  const double h0 = rb * eb - 0.5 * (mb * mb + nb * nb) - kappa * rb;
+  const double h1 = rb * d[3] + d[0] * eb - (mb * d[1] + nb * d[2]) - kappa * d[0];
+  const double h2 = d[0] * d[3] - 0.5 * (d[1] * d[1] + d[2] * d[2]);
+  const double disc = fmax(h1 * h1 - 4.0 * h0 * h2, 0.0);
+  const double den = -h1 + sqrt(disc);
+  return den > 0.0 ? fmin(2.0 * h0 / den, thr) : 0.0;
+}
+
 __device__ __forceinline__ void flux64(double g1, const double q[4], double F[4], double G[4]) {
   double ri = 1.0 / q[0];
   double u = q[1] * ri, v = q[2] * ri;
@@ -316,7 +331,7 @@ __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned
 __device__ __forceinline__ double bitsd(unsigned long long u) { return __longlong_as_double((long long)u); }
 
 template <int KD, int E, int ML, int NQ, int MQ>
-__global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
+__global__ void __launch_bounds__(128, 6) k_moment_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                    const StepArgs a, double* __restrict__ theta_out) {
   constexpr int NPT = NQ + E * MQ;
   static_assert(NPT <= 32, "a cell's limiter points fit one 32-bit mask");
@@ -376,11 +391,14 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
           for (int l = 1; l < ML; ++l) acc = fma((double)hi_at<ML>(st, N, v, l, ci), c_phid[KD][p][l], acc);
           d[v] = acc;
         }
-        const double r = st.avg[ci] + thr_c * d[0], mm = st.avg[(size_t)N + ci] + thr_c * d[1],
-                     nn = st.avg[2 * (size_t)N + ci] + thr_c * d[2], ee = st.avg[3 * (size_t)N + ci] + thr_c * d[3];
+        const double rb = st.avg[ci], mb = st.avg[(size_t)N + ci], nb = st.avg[2 * (size_t)N + ci],
+                     eb = st.avg[3 * (size_t)N + ci];
+        const double r = rb + thr_c * d[0], mm = mb + thr_c * d[1], nn = nb + thr_c * d[2], ee = eb + thr_c * d[3];
         const double pt = gd1 * (ee - 0.5 * (mm * mm + nn * nn) / r);
         const double ep = fmin(a.eps0, 0.5 * pb);
-        if (pt < ep) atomicMin(&th_slot[warp][cl], dbits(thr_c * (pb - ep) / (pb - pt)));
+        if (pt < ep)
+          atomicMin(&th_slot[warp][cl], dbits(a.moment_exact ? exact_root_theta(rb, mb, nb, eb, d, ep / gd1, thr_c)
+                                                             : thr_c * (pb - ep) / (pb - pt)));
       });
       if (need) {
         double th = bad ? 0.0 : fmax(bitsd(th_slot[warp][lane]), 0.0);
@@ -396,6 +414,7 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
           for (int l = 1; l < ML; ++l) c[v][l] = hi_at<ML>(st, N, v, l, i);
         }
         sm = a32[0] > 0.0f ? speedf(g, a32[0], a32[1], a32[2], a32[3]) : 0.0f;
+        unsigned floor_pts = 0u;
 #pragma unroll 1
         for (int p = 0; p < NPT; ++p) {
           float q[4];
@@ -406,13 +425,39 @@ __global__ void __launch_bounds__(128) k_moment_mx(const DevMesh m, const DevWor
             for (int l = 1; l < ML; ++l) acc += c[v][l] * t.phi[p][l];
             q[v] = a32[v] + thf * acc;
           }
-          if (q[0] > 0.0f) sm = fmaxf(sm, speedf(g, q[0], q[1], q[2], q[3]));
+          const float k2 = q[1] * q[1] + q[2] * q[2];
+          const float p32 = (g - 1.0f) * (q[3] - 0.5f * k2 / q[0]);
+          // resolved in FP32: rho well above the cancellation of its own sum, p
+          // well above that of E - |M|^2/(2 rho) (both within ~1e-5 then)
+          if (q[0] > 1e-2f * a32[0] && p32 > 1e-2f * q[3]) sm = fmaxf(sm, speedf(g, q[0], q[1], q[2], q[3]));
+          else floor_pts |= 1u << p;
+        }
+        // limited points near vacuum or the pressure floor: their density or
+        // pressure cancels below the FP32 rounding, so their speed comes from the
+        // FP64 point state (FP64 averages, the unlimited modes from memory, the
+        // FP64 basis)
+#pragma unroll 1
+        for (unsigned fm = floor_pts; fm; fm &= fm - 1u) {
+          const int p = __ffs(fm) - 1;
+          double r[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            double acc = 0.0;
+#pragma unroll
+            for (int l = 1; l < ML; ++l) acc = fma((double)hi_at<ML>(st, N, v, l, i), c_phid[KD][p][l], acc);
+            r[v] = st.avg[(size_t)v * N + i] + th * acc;
+          }
+          if (r[0] > 0.0) {
+            const double m2 = r[1] * r[1] + r[2] * r[2];
+            const double rp = fmax(gd1 * (r[0] * r[3] - 0.5 * m2), 0.0);   // rho p
+            sm = fmaxf(sm, (float)((sqrt(m2) + sqrt(a.gamma * rp)) / r[0]));
+          }
         }
         if (th < 1.0) {
 #pragma unroll
           for (int v = 0; v < 4; ++v)
 #pragma unroll
-            for (int l = 1; l < ML; ++l) hi_at<ML>(st, N, v, l, i) = (float)(th * (double)c[v][l]);
+            for (int l = 1; l < ML; ++l) hi_at<ML>(st, N, v, l, i) = (float)(th * (double)hi_at<ML>(st, N, v, l, i));
           if (a.want_diag) atomicAdd(&dg->nmom, 1ull);
         }
         if (theta_out) theta_out[i] = th;
@@ -1338,7 +1383,9 @@ __global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const D
       wready = !abort;
     }
     float f[kMlpIn];
-    const bool ok = need_net && i < N && gate_features<E, ML>(m, w, state, a, i, f);
+    // features only where the answer is used (a cleared cell's row of the
+    // product stays zero), or everywhere when inspected
+    const bool ok = need_net && i < N && (!clr || inspect) && gate_features<E, ML>(m, w, state, a, i, f);
     if (ok && a.feat_out) {
 #pragma unroll
       for (int k = 0; k < kMlpIn; ++k) a.feat_out[(size_t)i * kMlpIn + k] = f[k];
