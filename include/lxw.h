@@ -242,6 +242,14 @@ lxw_status lxw_run(lxw_solver* s, double* Q_dev, int nsteps, double cfl, lxw_dia
  * the layout-conversion kernels, one pass over the host link each way. */
 lxw_status lxw_run_host(lxw_solver* s, double* Q_host, int nsteps, double cfl, lxw_diag* diag_host);
 
+/* The same on a HOST copy of the solver's own state layout (lxw_state_bytes
+ * bytes: Q[N][4][ML] for FP64 solvers, the packed layout of lxw_state_pack
+ * for mixed ones, which is 112 instead of 192 bytes per P2 cell): one
+ * host-to-device copy of state_host, nsteps, one device-to-host copy back,
+ * synchronously.  Pinned memory makes the copies asynchronous DMA transfers.
+ * Errors: LXW_ERR_ARG, LXW_ERR_CUDA, and the device statuses of lxw_run. */
+lxw_status lxw_run_host_state(lxw_solver* s, void* state_host, int nsteps, double cfl, lxw_diag* diag_host);
+
 /* Single phases of the step, for per-phase checks (same kernels as lxw_step):
  * moment limiter on Q_dev in place (Sec. 3.1) with theta_dev[N] (nullable)
  * and the global wave speed written to s_dev[0] (device double). */

@@ -824,6 +824,19 @@ lxw_status lxw_run_host(lxw_solver* s, double* Qh, int nsteps, double cfl, lxw_d
   return st;
 }
 
+lxw_status lxw_run_host_state(lxw_solver* s, void* state_host, int nsteps, double cfl, lxw_diag* diag) {
+  if (!s || !state_host) return fail(LXW_ERR_ARG, "lxw_run_host_state: null argument");
+  const size_t bytes = lxw_state_bytes(s);
+  double* state = s->mixed ? s->Sdev : s->Qdev;
+  LXW_CUDA(cudaMemcpyAsync(state, state_host, bytes, cudaMemcpyHostToDevice, s->stream));
+  lxw_status st = lxw_run(s, state, nsteps, cfl, diag);
+  if (st != LXW_OK && st != LXW_ERR_NONPOSITIVE && st != LXW_ERR_CFL && st != LXW_ERR_NAN && st != LXW_ERR_TIMEOUT)
+    return st;
+  LXW_CUDA(cudaMemcpyAsync(state_host, state, bytes, cudaMemcpyDeviceToHost, s->stream));
+  LXW_CUDA(cudaStreamSynchronize(s->stream));
+  return st;
+}
+
 size_t lxw_state_bytes(const lxw_solver* s) {
   if (!s) return 0;
   if (s->mixed) return sizeof(double) * 4 * (size_t)s->N + sizeof(float) * 4 * (size_t)s->ML * s->N;

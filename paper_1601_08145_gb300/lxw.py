@@ -33,7 +33,7 @@ EXPORTS = [
     "lxw_mlp_create", "lxw_mlp_destroy", "lxw_mlp_num_params", "lxw_mlp_get_params", "lxw_mlp_set_params",
     "lxw_mlp_forward", "lxw_mlp_loss_grad", "lxw_mlp_train", "lxw_solver_set_mlp", "lxw_step_dump",
     "lxw_step_gate", "lxw_profile_phases", "lxw_basis_eval", "lxw_mesh_cartesian_masked",
-    "lxw_solver_set_inflow", "lxw_mlp_set_envelope", "lxw_mlp_get_envelope",
+    "lxw_solver_set_inflow", "lxw_mlp_set_envelope", "lxw_mlp_get_envelope", "lxw_run_host_state",
 ]
 
 
@@ -95,6 +95,7 @@ def lib():
     L.lxw_step.argtypes = [_vp, _vp, C.c_double, C.c_double, C.POINTER(Diag), _vp, _vp]
     L.lxw_run.argtypes = [_vp, _vp, C.c_int, C.c_double, C.POINTER(Diag)]
     L.lxw_run_host.argtypes = [_vp, _vp, C.c_int, C.c_double, C.POINTER(Diag)]
+    L.lxw_run_host_state.argtypes = [_vp, _vp, C.c_int, C.c_double, C.POINTER(Diag)]
     L.lxw_moment_limit.argtypes = [_vp, _vp, _vp, _vp]
     L.lxw_shock_limit.argtypes = [_vp, _vp, _vp]
     L.lxw_step_launches.argtypes = [_vp]
@@ -327,6 +328,17 @@ def lxw_run_host(solver, Qh, nsteps, cfl, diag=False):
         p = C.c_void_p(Qh.data_ptr())
     d = Diag() if diag else None
     st = _check(lib().lxw_run_host(solver.h, p, nsteps, cfl, C.byref(d) if d is not None else None),
+                allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN, ERR_TIMEOUT))
+    return _diag_result(st, d) if d is not None else None
+
+
+def lxw_run_host_state(solver, Sh, nsteps, cfl, diag=False):
+    """Sh: CPU torch tensor (pinned for DMA) holding the solver's state layout
+    (float64 words, shape solver.state_shape)."""
+    assert (not Sh.is_cuda) and Sh.element_size() == 8 and Sh.is_contiguous() and tuple(Sh.shape) == solver.state_shape
+    d = Diag() if diag else None
+    st = _check(lib().lxw_run_host_state(solver.h, C.c_void_p(Sh.data_ptr()), nsteps, cfl,
+                                         C.byref(d) if d is not None else None),
                 allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN, ERR_TIMEOUT))
     return _diag_result(st, d) if d is not None else None
 

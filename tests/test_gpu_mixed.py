@@ -171,6 +171,16 @@ def test_mixed_run_graph_and_host_path(L):
     P = Q.cpu().pin_memory()
     L.lxw_run_host(s, P, 5, 0.1)                        # pinned: read and written in place by the kernels
     assert np.array_equal(P.numpy(), H)
+    # the solver's own layout on the host: DMA of the packed state both ways
+    S = L.new_state(s, Q).cpu().pin_memory()
+    L.lxw_run_host_state(s, S, 5, 0.1)
+    assert torch.equal(S, A.cpu())
+    # an FP64 solver's layout is Q[N][4][ML]
+    s64 = solver(L, TRI, 2, 20, mixed=False)
+    A64 = Q.clone(); L.lxw_run(s64, A64, 5, 0.1)
+    S64 = Q.cpu().pin_memory()
+    L.lxw_run_host_state(s64, S64, 5, 0.1)
+    assert torch.equal(S64, A64.cpu())
 
 
 def test_status_is_kept_until_a_diagnostic_step_reads_it(L):
