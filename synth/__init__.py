@@ -248,7 +248,19 @@ def disk_triangles(ntri: int, radius: float = SEDOV_RADIUS, jitter: float = 0.15
     tv[flip, 1], tv[flip, 2] = tv[flip, 2].copy(), tv[flip, 1].copy()
     if len(tv) != ntri:
         raise ValueError(f"disk_triangles: {len(tv)} triangles, expected {ntri}")
-    return xy, tv
+    # triangles in Z-curve order of their centroids (the triangulation's own
+    # order is scattered; neighbours close in memory keep gathers local)
+    cen = (xy[tv[:, 0]] + xy[tv[:, 1]] + xy[tv[:, 2]]) / 3.0
+    ij = np.clip(((cen + radius) / (2.0 * radius) * 65535.0).astype(np.int64), 0, 65535)
+
+    def spread(v):   # bits of a 16-bit integer to the even positions
+        v = (v | (v << 8)) & 0x00FF00FF
+        v = (v | (v << 4)) & 0x0F0F0F0F
+        v = (v | (v << 2)) & 0x33333333
+        return (v | (v << 1)) & 0x55555555
+
+    order = np.argsort(spread(ij[:, 0]) | (spread(ij[:, 1]) << 1), kind="stable")
+    return xy, np.ascontiguousarray(tv[order])
 
 
 def ic_sedov_disk(ntri: int, radius: float = SEDOV_RADIUS, e_total: float = SEDOV_ENERGY, gamma: float = GAMMA):
