@@ -442,8 +442,21 @@ def locate(wc, pts):
         rin = synth.SEDOV_RADIUS * np.cos(np.pi / B) * (1.0 - 1e-9)
         rr = np.hypot(pts[:, 0], pts[:, 1])
         p = np.where((rr > rin)[:, None], pts * (rin / np.maximum(rr, 1e-300))[:, None], pts)
-        e = Delaunay(xy).find_simplex(p)     # the simplex order is the mesh's (only orientations were fixed)
-        assert np.all(e >= 0), "a point outside the coarse disk mesh"
+        tri = Delaunay(xy)
+        ks = tri.find_simplex(p)
+        assert np.all(ks >= 0), "a point outside the coarse disk mesh"
+        # the mesh numbers the same triangles in another order: match vertex triples
+        nv = np.int64(len(xy))
+
+        def key(t):
+            t = np.sort(t.astype(np.int64), axis=1)
+            return (t[:, 0] * nv + t[:, 1]) * nv + t[:, 2]
+
+        kt = key(tv)
+        srt = np.argsort(kt)
+        pos = np.searchsorted(kt[srt], key(tri.simplices[ks]))
+        e = srt[pos]
+        assert np.array_equal(kt[e], key(tri.simplices[ks])), "a simplex missing from the mesh"
         v0, v1, v2 = xy[tv[e, 0]], xy[tv[e, 1]], xy[tv[e, 2]]
         ax, ay, bx, by = v1[:, 0] - v0[:, 0], v1[:, 1] - v0[:, 1], v2[:, 0] - v0[:, 0], v2[:, 1] - v0[:, 1]
         det = ax * by - ay * bx
