@@ -76,3 +76,30 @@ def test_basis_eval_matches_the_oracle_basis(kind, deg):
     po = orc.basis_eval(kind, deg, ref[:, 0].copy(), ref[:, 1].copy())[0]
     assert phi.shape == po.shape
     assert np.abs(phi - po).max() < 1e-12
+
+
+def test_masked_mesh_and_boundary_codes_host_side(libpath):
+    """The mesh builders run on the host: masked grids keep the cells of the
+    mask (row order) and reject bad codes; triangle meshes accept the inflow
+    code on boundary edges and reject unknown ones."""
+    import numpy as np
+    import synth
+    from paper_1601_08145_gb300 import lxw
+    mask = synth.diffraction_mask(39, 33)
+    m = lxw.lxw_mesh_cartesian_masked(39, 33, synth.DIFFRACTION_BOX, synth.DIFFRACTION_BC, mask)
+    assert m.N == int(mask.sum()) == 39 * 33 - 3 * 18
+    full = lxw.lxw_mesh_cartesian_masked(5, 4, (0, 1, 0, 1), (0, 0, 1, 1), np.ones((4, 5), bool))
+    assert full.N == 20
+    for bad in (dict(mask_bc=0), dict(mask_bc=4)):
+        with pytest.raises(lxw.LxwError) as e:
+            lxw.lxw_mesh_cartesian_masked(5, 4, (0, 1, 0, 1), (2, 2, 2, 2), np.ones((4, 5), bool), **bad)
+        assert e.value.code == lxw.ERR_ARG
+    with pytest.raises(lxw.LxwError) as e:
+        lxw.lxw_mesh_cartesian(4, 4, bc=(4, 2, 2, 2))
+    assert e.value.code == lxw.ERR_ARG
+    xy, tv = synth.structured_triangles(4, jitter=0.2, seed=1)
+    t = lxw.lxw_mesh_triangles(xy, tv, np.full((len(tv), 3), lxw.BC_INFLOW, np.int32))
+    assert t.N == len(tv)
+    with pytest.raises(lxw.LxwError) as e:
+        lxw.lxw_mesh_triangles(xy, tv, np.full((len(tv), 3), 7, np.int32))
+    assert e.value.code == lxw.ERR_ARG
