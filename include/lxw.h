@@ -337,6 +337,8 @@ lxw_status lxw_mlp_train(lxw_mlp* n, const float* X_dev, const float* y_dev, int
  * next training call sets the envelope).  Takes effect at the next
  * lxw_solver_set_mlp.  Errors: LXW_ERR_ARG (one NULL, lo > hi). */
 lxw_status lxw_mlp_set_envelope(lxw_mlp* n, const float* lo_host, const float* hi_host);
+/* Copies the current envelope into lo_host[24], hi_host[24] (-inf / +inf
+ * where unbounded).  Errors: LXW_ERR_ARG (null argument). */
 lxw_status lxw_mlp_get_envelope(const lxw_mlp* n, float* lo_host, float* hi_host);
 /* Enables (mlp non-NULL) or disables the learned gate of a mixed solver;
  * the solver keeps a BF16 copy taken now, laid out as the tensor-core
