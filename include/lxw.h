@@ -83,7 +83,17 @@ typedef struct {
                                rho p - eps_p rho, a quadratic in theta) instead of
                                Lemma 1's secant (Sec. 3.1 remarks it can be
                                computed exactly); never more damping (0 default) */
-  int reserved[6];
+  int llf_global;           /* dissipation speed of the high-order point flux
+                               (Eq. LLF): 0 (default) = the local Lax-Friedrichs
+                               speed max(|u| + c) of the two traces at the
+                               point, bounded by the global s; 1 = the global s
+                               itself (the equation's literal wording).  The
+                               Lax-Friedrichs flux of the cell averages always
+                               uses the global s (Sec. 3.2).  With the global s
+                               the paper's convergence test (Sec. 4, Table 1)
+                               drops to second order; the local speed keeps
+                               third order                                     */
+  int reserved[5];
 } lxw_options;
 
 /* Per-step diagnostics (filled when a non-NULL pointer is passed). */

@@ -23,7 +23,16 @@
  *  - mu_c is the largest mu in [0,1] with p >= min(eps0, p^LxF/2) (exact
  *    root of the quadratic rho*p along the segment).
  *  - global wave speed s = max over averages and limited point values of
- *    |u| + c, computed once per step after the moment limiter.
+ *    |u| + c, computed once per step after the moment limiter; it sets dt
+ *    and the Lax-Friedrichs flux f^LxF of the cell averages (Sec. 3.2: the
+ *    global speed is what makes that flux positivity preserving).
+ *  - the dissipation of the high-order point flux (Eq. LLF) is the local
+ *    Lax-Friedrichs speed of the two traces at the point, max(|u|+c) of q-
+ *    and q+, never above the global s (which bounds it in exact arithmetic:
+ *    the edge points are among the limited points).  With the global s in
+ *    that term as well, the paper's own convergence test (Sec. 4, Table 1)
+ *    falls to second order; the local speed gives third order.  The literal
+ *    global reading stays available (orc_solver_set_llf_global).
  *  - dt = cfl * min_i(2|T_i|/P_i) / s.
  *  - the shock-capturing limiter of Sec. 4.1 (cited, not printed) is read
  *    as: for w in (rho,u,v,p), M = max(w_i + alpha, max_j w_j),
@@ -509,6 +518,7 @@ struct orc_solver {
   double gamma, eps0, alpha0;
   int shock_limiter;
   int moment_exact;                         /* Step 2 by the exact root instead of the secant */
+  int llf_global;                           /* Eq. LLF point flux with the global s instead of the local speed */
   double qx[MAXQ], qy[MAXQ], qw[MAXQ];
   double gs[MAXMQ], gw[MAXMQ];
   /* points: 0..NQ-1 interior, then edge k point p at NQ + k*MQ + p */
@@ -585,6 +595,12 @@ void orc_solver_set_params(orc_solver* s, double eps0, double alpha0, int shock_
 /* Sec. 3.1 notes that the optimal theta could be computed exactly instead
  * of by Lemma 1's secant; flag 1 selects that variant. */
 void orc_solver_set_moment_exact(orc_solver* s, int flag) { s->moment_exact = flag; }
+
+/* Eq. LLF names the dissipation speed of the high-order point flux "an
+ * estimate of the maximum global wave speed"; flag 1 uses the global s there
+ * (the literal reading), flag 0 (default) the local Lax-Friedrichs speed of
+ * the two traces (see the readings at the top of this file). */
+void orc_solver_set_llf_global(orc_solver* s, int flag) { s->llf_global = flag; }
 
 /* the state of inflow boundaries from primitive values (rho, u, v, p) */
 void orc_solver_set_inflow(orc_solver* s, const double* prim) {
@@ -1156,9 +1172,17 @@ int orc_step(orc_solver* s, double* Q, double dt_in, double cfl, double* diag,
         ft_from_derivs(g, dt, qp, qtp, qttp, Fp, Gp);
       }
       double* fs = s->fstar + ((size_t)e * MQ + p) * NV;
+      /* dissipation speed: local Lax-Friedrichs speed of the two traces,
+       * bounded by the global s (or the global s itself, literal reading) */
+      double sp = sw;
+      if (!s->llf_global) {
+        double am = wave_speed_point(g, qm), ap = wave_speed_point(g, qp);
+        double a = am > ap ? am : ap;
+        if (a < sp) sp = a;
+      }
       for (int v = 0; v < NV; ++v) {
         /* Eq. LLF times the edge length */
-        fs[v] = 0.5 * (n[0] * (Fp[v] + Fm[v]) + n[1] * (Gp[v] + Gm[v])) - 0.5 * sw * ln * (qp[v] - qm[v]);
+        fs[v] = 0.5 * (n[0] * (Fp[v] + Fm[v]) + n[1] * (Gp[v] + Gm[v])) - 0.5 * sp * ln * (qp[v] - qm[v]);
         fw[v] += 0.5 * s->gw[p] * fs[v];
       }
     }

@@ -75,6 +75,9 @@ void orc_solver_free(orc_solver* s);
 void orc_solver_set_params(orc_solver* s, double eps0, double alpha0, int shock_limiter);
 /* 1: the moment limiter's pressure step by the exact root (Sec. 3.1 remark), 0: secant */
 void orc_solver_set_moment_exact(orc_solver* s, int flag);
+/* flag 1: the high-order point flux (Eq. LLF) dissipates with the global s
+ * instead of the local speed of its two traces (default 0) */
+void orc_solver_set_llf_global(orc_solver* s, int flag);
 /* state of the inflow boundaries, primitive (rho, u, v, p) */
 void orc_solver_set_inflow(orc_solver* s, const double* prim);
 /* Cartesian mesh without the cells of mask == 0 (mask[ny][nx], row order);

@@ -59,6 +59,7 @@ def lib():
         L.orc_solver_free.argtypes = [C.c_void_p]
         L.orc_solver_set_params.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int]
         L.orc_solver_set_moment_exact.argtypes = [C.c_void_p, C.c_int]
+        L.orc_solver_set_llf_global.argtypes = [C.c_void_p, C.c_int]
         for f in (L.orc_solver_num_modes, L.orc_solver_num_points, L.orc_projection_num_points):
             f.argtypes = [C.c_void_p]
         L.orc_projection_points.argtypes = [C.c_void_p, _dp]
@@ -203,13 +204,15 @@ class Mesh:
 
 
 class Solver:
-    def __init__(self, mesh, deg, gamma=1.4, eps0=1e-12, alpha0=500.0, shock_limiter=True, moment_exact=False):
+    def __init__(self, mesh, deg, gamma=1.4, eps0=1e-12, alpha0=500.0, shock_limiter=True, moment_exact=False,
+                 llf_global=False):
         self.mesh = mesh  # keep alive
         self.ptr = lib().orc_solver_new(mesh.ptr, deg, gamma)
         if not self.ptr:
             raise ValueError("oracle solver construction failed")
         lib().orc_solver_set_params(self.ptr, eps0, alpha0, int(bool(shock_limiter)))
         lib().orc_solver_set_moment_exact(self.ptr, int(bool(moment_exact)))
+        lib().orc_solver_set_llf_global(self.ptr, int(bool(llf_global)))
         self.gamma = gamma
         self.N, self.E = mesh.N, mesh.E
         self.ML = lib().orc_solver_num_modes(self.ptr)

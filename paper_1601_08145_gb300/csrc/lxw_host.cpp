@@ -431,6 +431,8 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     return fail(LXW_ERR_ARG, "lxw_solver_create: high_occupancy must be 0 or 1");
   if (opt.moment_exact != 0 && opt.moment_exact != 1)
     return fail(LXW_ERR_ARG, "lxw_solver_create: moment_exact must be 0 or 1");
+  if (opt.llf_global != 0 && opt.llf_global != 1)
+    return fail(LXW_ERR_ARG, "lxw_solver_create: llf_global must be 0 or 1");
   lxw_solver* s = new (std::nothrow) lxw_solver;
   if (!s) return fail(LXW_ERR_NOMEM, "lxw_solver_create: out of memory");
   s->kind = mesh->kind; s->deg = degree; s->N = mesh->N; s->E = mesh->E; s->opt = opt;
@@ -689,6 +691,7 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   a.dt_in = dt; a.cfl = cfl; a.gamma = s->opt.gamma; a.eps0 = s->opt.eps0; a.alpha0 = s->opt.alpha0;
   a.shock_limiter = s->opt.shock_limiter; a.want_diag = want_diag; a.theta_cell = tc; a.theta_edge = te;
   a.moment_exact = s->opt.moment_exact;
+  a.llf_global = s->opt.llf_global;
   a.gamma_f = (float)a.gamma; a.eps0_f = (float)a.eps0; a.alpha0_f = (float)a.alpha0;
   a.grid = s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm * s->sms : 0;   // persistent CTAs, or one per tile
   a.sms = s->sms;

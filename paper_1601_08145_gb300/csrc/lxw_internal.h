@@ -140,6 +140,7 @@ struct StepArgs {
   float qin32[4], fin32[4], gin32[4];  // FP32 copies (mixed form)
   int shock_limiter;
   int moment_exact;                  // moment limiter: exact root instead of the secant
+  int llf_global;                    // LLF point flux: global s instead of the local speed of the traces
   int want_diag;
   double* theta_cell;     // [2][N] or null
   double* theta_edge;     // [N][E] or null

@@ -97,6 +97,19 @@ __device__ __forceinline__ double speed_of(double g, double r, double m, double 
   return sqrt(kin2) * ri + sqrt(g * p * ri);
 }
 
+// |u| + c of a point state for the dissipation of the LLF point flux, in
+// explicitly rounded operations: the two elements of an edge evaluate it on
+// the same two traces and must get the same value (their fluxes are exact
+// negatives).  A non-positive density gives NaN, which the fmin / fmax that
+// combine the speeds discard.
+__device__ __forceinline__ double lf_speed(double g, const double q[4]) {
+  const double ri = __drcp_rn(q[0]);
+  const double kin2 = __fma_rn(q[1], q[1], __dmul_rn(q[2], q[2]));
+  double p = __dmul_rn(g - 1.0, __fma_rn(__dmul_rn(-0.5, kin2), ri, q[3]));
+  p = p > 0.0 ? p : 0.0;
+  return __dadd_rn(__dmul_rn(__dsqrt_rn(kin2), ri), __dsqrt_rn(__dmul_rn(__dmul_rn(g, p), ri)));
+}
+
 __device__ __forceinline__ void block_max_to(double v, unsigned long long* dst) {
   // warp shuffle, then one atomic per warp (values are non-negative)
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -460,10 +473,13 @@ __global__ void __launch_bounds__(128) k_edge(const DevMesh m, const DevWork w, 
 #pragma unroll
         for (int v = 0; v < 4; ++v) { qx[v] = qi[v]; Fx[v] = Fi[v]; }
       }
+      // dissipation speed: the local Lax-Friedrichs speed of the two traces,
+      // at most the global s (or s itself under the literal reading)
+      const double hp = a.llf_global ? hs : 0.5 * fmin(s, fmax(lf_speed(g, qi), lf_speed(g, qx))) * ln;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         // Eq. LLF scaled by the edge length
-        double fs = __fma_rn(-hs, __dsub_rn(qx[v], qi[v]), __dmul_rn(0.5, __dadd_rn(Fi[v], Fx[v])));
+        double fs = __fma_rn(-hp, __dsub_rn(qx[v], qi[v]), __dmul_rn(0.5, __dadd_rn(Fi[v], Fx[v])));
         fW[k][v] = __fma_rn(0.5 * t.ew[qo], fs, fW[k][v]);
         const double hw = 0.5 * t.ew[p] * fs;
 #pragma unroll

@@ -97,6 +97,26 @@ __device__ __forceinline__ float speedf(float g, float r, float m, float n, floa
 }
 // exterior state of a boundary face: reflective, transparent (Sec. 2.4) or
 // the prescribed inflow state qin
+// |u| + c of a point state for the dissipation of the LLF point flux: both
+// elements of an edge evaluate it on the same two traces and must get the
+// same value (their fluxes are exact negatives), so every operation is
+// pinned: the multiplies and adds explicitly rounded, the reciprocal square
+// root and the square roots the hardware's approximations (deterministic;
+// a few ulp, far inside the FP32 budget of a dissipation coefficient).  A
+// non-positive density gives NaN, which the fminf / fmaxf that combine the
+// speeds discard.
+__device__ __forceinline__ float lf_speedf(float g, const float q[4]) {
+  float rs, sk, sp;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(q[0]));
+  const float ri = __fmul_rn(rs, rs);
+  const float kin2 = __fmaf_rn(q[1], q[1], __fmul_rn(q[2], q[2]));
+  float p = __fmul_rn(g - 1.0f, __fmaf_rn(__fmul_rn(-0.5f, kin2), ri, q[3]));
+  p = p > 0.0f ? p : 0.0f;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sk) : "f"(kin2));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sp) : "f"(__fmul_rn(g, p)));
+  return __fmaf_rn(sk, ri, __fmul_rn(sp, rs));
+}
+
 template <typename T>
 __device__ __forceinline__ void ghostq(int bc, T nxh, T nyh, const T qi[4], T qo[4], const T qin[4]) {
   if (bc == LXW_BC_INFLOW) {
@@ -729,9 +749,12 @@ __device__ __forceinline__ void edge_elem(const DevMesh& m, const DevWorkMx& w, 
 #pragma unroll
     for (int qo = 0; qo < MQ; ++qo) {
       const int p = owner ? qo : MQ - 1 - qo;
+      // dissipation speed: the local Lax-Friedrichs speed of the two traces,
+      // at most the global s (or s itself under the literal reading)
+      const float hp = a.llf_global ? hs : 0.5f * fminf(s, fmaxf(lf_speedf(a.gamma_f, qi[qo]), lf_speedf(a.gamma_f, qx[qo]))) * ln;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        float fs = __fmaf_rn(-hs, __fsub_rn(qx[qo][v], qi[qo][v]), __fmul_rn(0.5f, __fadd_rn(Fi[qo][v], Fx[qo][v])));
+        float fs = __fmaf_rn(-hp, __fsub_rn(qx[qo][v], qi[qo][v]), __fmul_rn(0.5f, __fadd_rn(Fi[qo][v], Fx[qo][v])));
         fW[k][v] = __fmaf_rn(0.5f * t.ew[qo], fs, fW[k][v]);
         const float hw = 0.5f * t.ew[p] * fs;
 #pragma unroll

@@ -41,7 +41,7 @@ class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("eps0", C.c_double), ("alpha0", C.c_double),
                 ("shock_limiter", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
                 ("ctas_per_sm", C.c_int), ("high_occupancy", C.c_int), ("moment_exact", C.c_int),
-                ("reserved", C.c_int * 6)]
+                ("llf_global", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class Diag(C.Structure):

@@ -138,14 +138,28 @@ def test_flux_limiter_box_positivity_brute_force(orc, E):
     assert limited > 100
 
 
-def test_step_uses_edge_min_of_proposals(orc):
+@pytest.mark.parametrize("case", ["random_literal_llf", "rarefaction"])
+def test_step_uses_edge_min_of_proposals(orc, case):
     """Through a full step: the new averages equal the blended update at
-    theta_e, and theta_e keeps every state of the box positive."""
-    mesh = orc.Mesh.cartesian(10, 10, bc=(2, 2, 2, 2))
-    sol = orc.Solver(mesh, 2, gamma=G, shock_limiter=False)
-    Q = synth.random_modal_state(mesh.N, sol.ML, seed=78, amp=0.3, rho_range=(0.01, 3.0), p_range=(0.001, 3.0))
-    Qlim = Q.copy(); sol.moment_limit(Qlim)
-    d = sol.step(Q, cfl=0.9, want_theta=True)
+    theta_e, and theta_e keeps every state of the box positive.  Random data
+    wakes the flux limiter when the point flux dissipates with the global s
+    (the literal reading of Eq. LLF); with the local speed (default) a strong
+    rarefaction (u = -+3, p = 0.01) at CFL 0.6 does."""
+    if case == "random_literal_llf":
+        mesh = orc.Mesh.cartesian(10, 10, bc=(2, 2, 2, 2))
+        sol = orc.Solver(mesh, 2, gamma=G, shock_limiter=False, llf_global=True)
+        Q = synth.random_modal_state(mesh.N, sol.ML, seed=78, amp=0.3, rho_range=(0.01, 3.0), p_range=(0.001, 3.0))
+        cfl, warm = 0.9, 0
+    else:
+        mesh = orc.Mesh.cartesian(16, 4, bc=(2, 2, 0, 0))
+        sol = orc.Solver(mesh, 2, gamma=G, shock_limiter=False)
+        Q = sol.project_fn(lambda x, y: (np.ones_like(x), np.where(x < 0.5, -3.0, 3.0), 0 * x, 0.01 + 0 * x))
+        cfl, warm = 0.6, 20
+    for _ in range(warm + 1):
+        Qlim = Q.copy(); sol.moment_limit(Qlim)
+        d = sol.step(Q, cfl=cfl, want_theta=True)
+        if d["n_edge"] > 0:
+            break
     assert d["status"] == 0 and d["n_edge"] > 0
     fw, ff, dt = sol.last_fluxes()
     area = mesh.geometry()[0]
