@@ -392,11 +392,7 @@ def smooth_l1_error(L, stream, mixed, net=None, tau=0.02):
     if net is not None:
         L.lxw_solver_set_mlp(sol, net, tau)
     Q = project(L, sol, w)
-    T, t, dt_last, skipped, steps = 0.1, 0.0, None, 0.0, 0
-    while t < T - 1e-14:
-        dt = T - t if dt_last is not None and t + 1.05 * dt_last >= T else 0.0
-        d = L.lxw_step(sol, Q, dt, w["cfl"], diag=True)
-        t += d["dt"]; dt_last = d["dt"]; skipped += d["n_mlp_skip"]; steps += 1
+    steps, t, _ = L.lxw_run_to(sol, Q, 0.1, w["cfl"])      # the device lands the last step on t = 0.1
     xy = L.lxw_projection_points(sol)
     ex = synth.exact_smooth_density(xy[..., 0], xy[..., 1], t)
     prim = torch.from_numpy(np.stack(np.broadcast_arrays(ex, 1.0, 1.0, 1.0), axis=-1).copy()).cuda()
@@ -408,18 +404,7 @@ def smooth_l1_error(L, stream, mixed, net=None, tau=0.02):
     # L2 of the DG density against the projected exact one: the basis is
     # orthonormal on each cell, so ||.||^2 = sum_i |T_i| sum_l dQ_il^2
     l2 = torch.sqrt((dr ** 2).sum(dim=1).mean()).item()
-    return {"l1": l1, "l2": l2, "t": t, "steps": steps, "gate_skipped_cell_steps": skipped}
-
-
-def run_to(L, sol, Q, T, cfl):
-    """Steps with dt from the CFL rule until t = T, the last one shortened;
-    returns the number of steps."""
-    t, dt_last, k = 0.0, None, 0
-    while t < T * (1.0 - 1e-13):
-        dt = T - t if dt_last is not None and t + 1.05 * dt_last >= T else 0.0
-        d = L.lxw_step(sol, Q, dt, cfl, diag=True)
-        t += d["dt"]; dt_last = d["dt"]; k += 1
-    return k
+    return {"l1": l1, "l2": l2, "t": t, "steps": steps}
 
 
 def locate(wc, pts):
@@ -511,11 +496,11 @@ def discretization_check(L, stream, name, net, tau, steps):
     _, sm = build_workload(L, name, stream, True)
     L.lxw_solver_set_mlp(sm, net, tau)
     Qm = project(L, sm, w)
-    km = run_to(L, sm, Qm, T, w["cfl"])
+    km = L.lxw_run_to(sm, Qm, T, w["cfl"])[0]
     wc = half_resolution(w)
     _, sc = build_solver(L, wc, stream, False)
     Qc = project(L, sc, wc)
-    kc = run_to(L, sc, Qc, T, w["cfl"])
+    kc = L.lxw_run_to(sc, Qc, T, w["cfl"])[0]
     # the coarse density at the fine projection points, projected onto the fine elements
     pts = L.lxw_projection_points(sf)
     N, npj = pts.shape[0], pts.shape[1]
@@ -542,6 +527,29 @@ def discretization_check(L, stream, name, net, tau, steps):
             "target_ratio_at_most": 0.1,
             "norm": "sum over fine elements of |T_i| |rho_avg difference| (density cell averages)"}
 
+
+
+def fma_probes():
+    """Measured FP64 / FP32 FMA-pipe throughput (TFLOP/s) from bench_fma_probe.cu,
+    compiled next to this file on first use (a measurement aid of the bench,
+    not part of the library); None where it cannot be built or run."""
+    import ctypes
+    import subprocess
+    here = os.path.dirname(os.path.abspath(__file__))
+    src, lib = os.path.join(here, "bench_fma_probe.cu"), os.path.join(here, "bench_fma_probe.so")
+    try:
+        if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            subprocess.run(["nvcc", "-O3", "-shared", "-Xcompiler", "-fPIC", "-gencode",
+                            "arch=compute_103a,code=sm_103a", "-o", lib, src], check=True, capture_output=True)
+        P = ctypes.CDLL(lib)
+        P.fma_probe_tflops.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        out = {}
+        for name, fp64 in (("fp64", 1), ("fp32", 0)):
+            v = ctypes.c_double()
+            out[name] = v.value if P.fma_probe_tflops(fp64, ctypes.byref(v)) == 0 else None
+        return out
+    except Exception:
+        return {"fp64": None, "fp32": None}
 
 def main():
     ap = argparse.ArgumentParser()
@@ -576,10 +584,7 @@ def main():
         dist.barrier()
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    try:
-        probes = {"fp64": L.lxw_fma_peak(True), "fp32": L.lxw_fma_peak(False)}
-    except Exception:
-        probes = {"fp64": None, "fp32": None}
+    probes = fma_probes()
 
     def timed_form(mixed, clocks=None, net=None):
         w, sol = build_workload(L, args.workload, stream, mixed)

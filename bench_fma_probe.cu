@@ -1,9 +1,12 @@
-// lxw_peak.cu -- throughput probe of the plain FP64 / FP32 fused multiply-add
-// pipes, the roofline denominators of the element kernels (which do their
-// arithmetic on these pipes, not on the tensor cores).
+// bench_fma_probe.cu -- measurement aid of bench.py, not part of the library:
+// throughput of the plain FP64 / FP32 fused multiply-add pipes, the roofline
+// denominators of the element kernels (which do their arithmetic on these
+// pipes).  bench.py compiles it into bench_fma_probe.so on first use.
+//
+//   int fma_probe_tflops(int fp64, double* tflops)
+//     one timed launch of independent FMA chains on every SM of the current
+//     device (legacy default stream, synchronous); 0 on success.
 #include <cuda_runtime.h>
-
-#include "lxw_internal.h"
 
 namespace {
 
@@ -48,8 +51,7 @@ int probe(double* tflops) {
 
 }  // namespace
 
-extern "C" lxw_status lxw_fma_peak(int fp64, double* tflops) {
-  if (!tflops) return LXW_ERR_ARG;
-  int rc = fp64 ? probe<double>(tflops) : probe<float>(tflops);
-  return rc ? LXW_ERR_CUDA : LXW_OK;
+extern "C" int fma_probe_tflops(int fp64, double* tflops) {
+  if (!tflops) return 1;
+  return fp64 ? probe<double>(tflops) : probe<float>(tflops);
 }

@@ -245,6 +245,26 @@ lxw_status lxw_step(lxw_solver* s, double* Q_dev, double dt, double cfl, lxw_dia
  * (nullable) receives the last step's diagnostics. */
 lxw_status lxw_run(lxw_solver* s, double* Q_dev, int nsteps, double cfl, lxw_diag* diag_host);
 
+/* Runs steps with dt from cfl (the CFL rule, Sec. 4.1) until the state has
+ * advanced by exactly t_span: the device keeps each problem's clock, takes
+ * dt = min(cfl rule, t_span - t) so that the last step lands on t_span, and
+ * skips a problem once its clock has reached it (each problem of a batch
+ * keeps its own clock).  No host synchronisation per step: a captured graph
+ * of one timed step is replayed in chunks (first one step, then as many as
+ * the slowest problem needs at its mean time step so far, +5 %), with one
+ * synchronisation per chunk.  At most max_steps steps.  steps_host
+ * (nullable) receives the steps taken (the most over the problems),
+ * t_host (nullable) the time reached (the least over the problems; t_span
+ * unless max_steps stopped the run).  diag_host (nullable) receives the
+ * final state's minima and conserved totals, s and dt of the last step
+ * taken (largest s, smallest dt over the problems) and the status bits seen
+ * since the last diagnostics; the limiter counts are zero.  Errors:
+ * LXW_ERR_ARG (t_span <= 0, cfl <= 0, max_steps < 1, a batch with the
+ * learned gate), LXW_ERR_CUDA, and with diag_host the device statuses of
+ * lxw_step. */
+lxw_status lxw_run_to(lxw_solver* s, double* Q_dev, double t_span, double cfl, int max_steps, lxw_diag* diag_host,
+                      int* steps_host, double* t_host);
+
 /* End-to-end form of lxw_run on HOST memory: brings Q_host ([N][4][ML],
  * pinned or pageable) to the solver's device state, runs nsteps and returns
  * the result to Q_host, synchronously.  Pageable memory is copied; for the
@@ -294,13 +314,6 @@ lxw_status lxw_profile_step(lxw_solver* s, double* Q_dev, double cfl, float* ms_
 lxw_status lxw_step_phases(lxw_solver* s, double* Q_dev, double dt, double cfl, int nphases);
 lxw_status lxw_workspace_copy(lxw_solver* s, int which, double* host_out, size_t count);
 
-/* Measurement aid (no counterpart in the paper): throughput in TFLOP/s of
- * fused multiply-adds on the plain FP64 (fp64 = 1) or FP32 (fp64 = 0) pipe
- * of the current device, from one timed launch of independent FMA chains on
- * every SM (legacy default stream, synchronous, allocates nothing).  The
- * element kernels do their arithmetic on these pipes; this is their roofline
- * denominator. */
-lxw_status lxw_fma_peak(int fp64, double* tflops);
 
 /* --- learned troubled-cell indicator (mixed form) ------------------------
  * An MLP 24 -> 64 (ReLU) -> 64 (ReLU) -> 1 (sigmoid) predicts the theta of
@@ -355,6 +368,18 @@ lxw_status lxw_mlp_get_envelope(const lxw_mlp* n, float* lo_host, float* hi_host
  * operands (later training needs another call).  tau in [0, 1).  Errors:
  * LXW_ERR_ARG (FP64 solver, tau), LXW_ERR_CUDA. */
 lxw_status lxw_solver_set_mlp(lxw_solver* s, lxw_mlp* mlp, float tau);
+/* Test aid of the gate's bounded device waits (no counterpart in the
+ * paper): with cycles > 0, every CTA of the gated shock kernel, at its first
+ * tile that needs the network, first waits at most `cycles` SM cycles on
+ * its own MMA barrier before anything was committed to it.  Nothing can
+ * arrive there, so the wait runs out and the CTA takes the timeout path:
+ * LXW_ST_TIMEOUT (LXW_ERR_TIMEOUT from the next step with diagnostics), the
+ * plain shock limiter on all its cells (the state equals the ungated step's),
+ * the weight copy still awaited with the normal bound, tensor memory
+ * released.  0 (default) switches it off.  Drops the solver's CUDA graphs.
+ * Errors: LXW_ERR_ARG (null solver, cycles < 0). */
+lxw_status lxw_solver_set_gate_wait_test(lxw_solver* s, long long cycles);
+
 /* One mixed step (plain limiter, no gate) that also writes each cell's
  * features at the shock limiter's input (feat_dev[N][24]; rows of cells with
  * non-positive new averages are left untouched) and the limiter's theta
@@ -375,28 +400,39 @@ lxw_status lxw_step_dump(lxw_solver* s, void* state_dev, double cfl, float* feat
 lxw_status lxw_step_gate(lxw_solver* s, void* state_dev, double cfl, float* gate_dev, float* feat_dev);
 
 /* Allocation-free form of lxw_moment_limit, for callers that cannot call
- * cudaMalloc: code running while a stream is captured into a CUDA graph,
- * code whose device memory is owned by another allocator (a framework's
- * caching pool, a fixed budget), code that must avoid cudaMalloc's implicit
- * device synchronisation.  The paper has no counterpart; it is the same
- * moment limiter and wave-speed maximum, without a solver.
+ * cudaMalloc: code whose device memory is owned by another allocator (a
+ * framework's caching pool, or a fixed budget set aside at start-up, where
+ * an extra allocation could fail or fragment it), and code that must avoid
+ * cudaMalloc's implicit device synchronisation.  The paper has no
+ * counterpart; it is the same moment limiter and wave-speed maximum,
+ * without a solver.
  * Q_dev[n_elements][4][ML] is limited in place; theta_dev[n_elements]
  * (nullable) receives theta; s_dev[0] (device double) receives the wave
  * speed.  No geometry is needed (the limiter is element-local).
- * Scratch: the reduction's running maxima live in a static device array of
- * 513 64-bit words (about 4 KB) that every GPU loading the library holds
- * until exit; n_elements above 16,777,216 (512 slots x 32,768 elements) is
- * rejected with LXW_ERR_ARG.  The array is shared by every call and keeps
- * the last call's contents; each call clears the slots it uses first.  Calls
- * that overlap on the GPU (concurrent streams, or several host threads) race
- * on it and must be serialised by the caller.  The first call on a device
- * finds the array's device address and loads the basis tables into the
- * constant bank (once per device, with that device current); make that first
- * call before any stream capture.  Allocates nothing: no cudaMalloc, no
- * cudaFree, no allocating library call.  Errors: LXW_ERR_ARG (null pointer,
- * kind/degree, size, gamma <= 1, eps0 <= 0), LXW_ERR_CUDA. */
+ * Status: a cell whose input average has rho <= 0 or p <= 0 keeps its
+ * average, gets theta = 0 and has its higher modes zeroed, and sets
+ * LXW_ST_NONPOSITIVE.  With status_dev (device unsigned int, nullable) the
+ * call is asynchronous on `stream` and the device writes the LXW_ST_* bits
+ * of this call there; with status_dev NULL the call waits for `stream` and
+ * returns LXW_ERR_NONPOSITIVE when the bit is set.
+ * Scratch: the reduction's running maxima and the status word live in a
+ * static device array of 513 64-bit words (about 4 KB) that every GPU
+ * loading the library holds until exit; n_elements above 16,777,216 (512
+ * slots x 32,768 elements) is rejected with LXW_ERR_ARG.  The array is
+ * shared by every call and keeps the last call's contents; each call clears
+ * the slots it uses and the status word first.  Calls that overlap on the
+ * GPU (concurrent streams, or several host threads) race on it and must be
+ * serialised by the caller.  The first call on a device finds the array's
+ * device address and loads the basis tables into the constant bank (once
+ * per device, with that device current); make that first call before any
+ * stream capture.  Allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library call.  A CUDA error already pending on the calling
+ * thread is reported (LXW_ERR_CUDA) and left in place; nothing is launched.
+ * Errors: LXW_ERR_ARG (null pointer, kind/degree, size, gamma <= 1,
+ * eps0 <= 0), LXW_ERR_CUDA, LXW_ERR_NONPOSITIVE (status_dev NULL only). */
 lxw_status lxw_moment_limit_noalloc(int kind, int degree, int n_elements, double gamma, double eps0,
-                                    double* Q_dev, double* theta_dev, double* s_dev, void* stream);
+                                    double* Q_dev, double* theta_dev, double* s_dev, unsigned int* status_dev,
+                                    void* stream);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "liblxw.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lxw_kernels.cu", "lxw_kernels_mx.cu", "lxw_host.cpp", "lxw_peak.cu", "lxw_mlp.cu"]
+SOURCES = ["lxw_kernels.cu", "lxw_kernels_mx.cu", "lxw_host.cpp", "lxw_mlp.cu"]
 FAST_FP32 = {"lxw_kernels_mx.cu"}
 
 

@@ -272,12 +272,18 @@ struct lxw_solver {
   double qin[4] = {0.0, 0.0, 0.0, 0.0};  // conserved state of LXW_BC_INFLOW faces
   int gate_per_sm[2] = {1, 1};         // resident gate CTAs per SM of each variant (queried when a network is attached)
   float mlp_tau = 0.0f;
+  long long gate_wait_test = 0;      // test aid of the gate's bounded waits (lxw_solver_set_gate_wait_test)
   int tiles_cap = 0;
   int sms = 0;
   std::vector<void*> allocs;
   double* Qdev = nullptr;        // FP64 staging buffer of lxw_run_host
   double* Sdev = nullptr;        // packed state of lxw_run_host (mixed form)
   double* host_diag = nullptr;   // pinned
+  double* tclock = nullptr;      // [nprob][4] clocks of lxw_run_to (device)
+  double* host_clock = nullptr;  // pinned copy of tclock
+  cudaGraphExec_t tgraph = nullptr;   // one timed step (lxw_run_to)
+  double* tgraph_Q = nullptr;
+  double tgraph_cfl = 0.0, tgraph_tend = 0.0;
   std::vector<double> xproj;     // [N][NPJ][2]
   cudaGraphExec_t graph = nullptr;
   double* graph_Q = nullptr;
@@ -289,6 +295,8 @@ struct lxw_solver {
   double pgraph_cfl = 0.0;
   ~lxw_solver() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (tgraph) cudaGraphExecDestroy(tgraph);
+    if (host_clock) cudaFreeHost(host_clock);
     if (pgraph) cudaGraphExecDestroy(pgraph);
     for (void* e : events) if (e) cudaEventDestroy((cudaEvent_t)e);
     for (void* p : allocs) cudaFree(p);
@@ -504,6 +512,7 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
   s->dw.smax = (unsigned long long*)dalloc(sizeof(unsigned long long) * nprob);
   s->dw.status = (unsigned int*)dalloc(sizeof(unsigned int));
   s->dw.diag = (double*)dalloc(sizeof(DiagBlock) > diag_bytes() ? sizeof(DiagBlock) : diag_bytes());
+  s->tclock = (double*)dalloc(sizeof(double) * 4 * nprob);
   s->Qdev = (double*)dalloc(sizeof(double) * (size_t)N * 4 * s->ML);
   s->mixed = opt.precision == LXW_PREC_MIXED;
   if (s->mixed) {
@@ -542,7 +551,7 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     s->dm.jinv32 = j32; s->dm.nrm32 = n32; s->dm.sdx32 = s32; s->dm.inva32 = ia32; s->dm.inva = ia64;
   }
   if (!d_area || !d_jinv || !d_nrm || !d_sdx || !d_nbr || !d_nbk || !s->dw.trace || !s->dw.flux || !s->dw.prop ||
-      !s->dw.smax || !s->dw.status || !s->dw.diag || !s->Qdev ||
+      !s->dw.smax || !s->dw.status || !s->dw.diag || !s->Qdev || !s->tclock ||
       cudaMemset(s->dw.smax, 0, sizeof(unsigned long long) * nprob) != cudaSuccess ||
       cudaMemset(s->dw.status, 0, sizeof(unsigned int)) != cudaSuccess) {
     delete s;
@@ -550,6 +559,10 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
   }
   if (cudaMallocHost(&s->host_diag, 64 * sizeof(double)) != cudaSuccess) {
     s->host_diag = nullptr; delete s;
+    return fail(LXW_ERR_NOMEM, "lxw_solver_create: pinned allocation failed");
+  }
+  if (cudaMallocHost(&s->host_clock, 4 * sizeof(double) * nprob) != cudaSuccess) {
+    s->host_clock = nullptr; delete s;
     return fail(LXW_ERR_NOMEM, "lxw_solver_create: pinned allocation failed");
   }
   for (auto& e : s->events) {
@@ -698,6 +711,7 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   a.hi_occupancy = s->opt.high_occupancy;
   a.gate_per_sm = s->gate_per_sm[s->opt.high_occupancy ? 1 : 0];
   a.gate_w = s->mlp_w; a.mlp_tau = s->mlp_tau; a.feat_out = nullptr; a.gate_out = nullptr;
+  a.gate_wait_test = s->gate_wait_test;
   {  // inflow state and its fluxes (the time-averaged flux of a steady state)
     const double* q = s->qin;
     const double u = q[0] > 0.0 ? q[1] / q[0] : 0.0, v = q[0] > 0.0 ? q[2] / q[0] : 0.0;
@@ -789,6 +803,71 @@ lxw_status lxw_run(lxw_solver* s, double* Q, int nsteps, double cfl, lxw_diag* d
     for (int k = 0; k < body; ++k) LXW_CUDA(cudaGraphLaunch(s->graph, s->stream));
   }
   if (diag) return lxw_step(s, Q, 0.0, cfl, diag, nullptr, nullptr);
+  return LXW_OK;
+}
+
+lxw_status lxw_run_to(lxw_solver* s, double* Q, double t_span, double cfl, int max_steps, lxw_diag* diag,
+                      int* steps_out, double* t_out) {
+  if (!s || !Q || !(t_span > 0.0) || !std::isfinite(t_span) || !(cfl > 0.0) || max_steps < 1)
+    return fail(LXW_ERR_ARG, "lxw_run_to: need Q, t_span > 0, cfl > 0 and max_steps >= 1");
+  const int nprob = s->dm.nprob > 0 ? s->dm.nprob : 1;
+  if (s->mixed && nprob > 1 && s->mlp_w)
+    return fail(LXW_ERR_ARG, "lxw_run_to: a batch with the learned gate cannot run to a time");
+  StepArgs a = make_args(s, 0.0, cfl, 0, nullptr, nullptr);
+  a.timed = 1; a.t_end = t_span; a.tclock = s->tclock;
+  LXW_CUDA(cudaMemsetAsync(s->tclock, 0, sizeof(double) * 4 * nprob, s->stream));
+  if (!s->tgraph || s->tgraph_Q != Q || s->tgraph_cfl != cfl || s->tgraph_tend != t_span) {
+    if (s->tgraph) { cudaGraphExecDestroy(s->tgraph); s->tgraph = nullptr; }
+    cudaGraph_t g = nullptr;
+    LXW_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = do_step(s, Q, a, s->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
+    if (rc || ce != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail(LXW_ERR_CUDA, "lxw_run_to: graph capture failed"); }
+    cudaError_t ie = cudaGraphInstantiate(&s->tgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) { s->tgraph = nullptr; return fail(LXW_ERR_CUDA, "lxw_run_to: graph instantiation failed"); }
+    s->tgraph_Q = Q; s->tgraph_cfl = cfl; s->tgraph_tend = t_span;
+  }
+  // replay in chunks, one synchronisation per chunk: the first chunk is one
+  // step (it shows the time step), then enough for the slowest problem at
+  // its mean step so far (+5 %); replays after a problem's clock reached
+  // t_span cost a few empty launches
+  int launched = 0, chunk = 1;
+  double tmin = 0.0, smax_steps = 0.0;
+  while (launched < max_steps) {
+    const int n = std::min(chunk, max_steps - launched);
+    for (int k = 0; k < n; ++k) LXW_CUDA(cudaGraphLaunch(s->tgraph, s->stream));
+    launched += n;
+    LXW_CUDA(cudaMemcpyAsync(s->host_clock, s->tclock, sizeof(double) * 4 * nprob, cudaMemcpyDeviceToHost, s->stream));
+    LXW_CUDA(cudaStreamSynchronize(s->stream));
+    tmin = 1e300; smax_steps = 0.0;
+    double need = 0.0;
+    for (int p = 0; p < nprob; ++p) {
+      const double t = s->host_clock[4 * p], k = s->host_clock[4 * p + 1];
+      tmin = std::min(tmin, t);
+      smax_steps = std::max(smax_steps, k);
+      if (t < t_span) need = std::max(need, k > 0.0 && t > 0.0 ? (t_span - t) / (t / k) : 1.0);
+    }
+    if (tmin >= t_span) break;
+    chunk = (int)std::min(1e9, std::ceil(1.05 * need)) + 1;
+  }
+  if (steps_out) *steps_out = (int)smax_steps;
+  if (t_out) *t_out = tmin;
+  if (diag) {
+    // one more timed step with diagnostics: every problem has finished, so
+    // its kernels skip; the totals and minima are the final state's, s and
+    // dt those of the last step taken, the status the bits seen in the run
+    a.want_diag = 1;
+    if (do_step(s, Q, a, s->stream)) return fail(LXW_ERR_CUDA, "lxw_run_to: diagnostic launch failed");
+    lxw_status st = read_diag(s, 0.0, cfl, diag);
+    diag->s = 0.0; diag->dt = 1e300;
+    for (int p = 0; p < nprob; ++p) {
+      diag->dt = std::min(diag->dt, s->host_clock[4 * p + 2]);
+      diag->s = std::max(diag->s, s->host_clock[4 * p + 3]);
+    }
+    diag->n_mom = diag->n_edge = diag->n_sc = 0.0;
+    return st;
+  }
   return LXW_OK;
 }
 
@@ -979,6 +1058,7 @@ lxw_status lxw_step_gate(lxw_solver* s, void* state, double cfl, float* gate, fl
 
 static void drop_graphs(lxw_solver* s) {
   if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+  if (s->tgraph) { cudaGraphExecDestroy(s->tgraph); s->tgraph = nullptr; }
   if (s->pgraph) { cudaGraphExecDestroy(s->pgraph); s->pgraph = nullptr; }
 }
 
@@ -990,6 +1070,13 @@ lxw_status lxw_solver_set_inflow(lxw_solver* s, const double prim[4]) {
   s->qin[1] = prim[0] * prim[1];
   s->qin[2] = prim[0] * prim[2];
   s->qin[3] = prim[3] / (s->opt.gamma - 1.0) + 0.5 * prim[0] * (prim[1] * prim[1] + prim[2] * prim[2]);
+  drop_graphs(s);
+  return LXW_OK;
+}
+
+lxw_status lxw_solver_set_gate_wait_test(lxw_solver* s, long long cycles) {
+  if (!s || cycles < 0) return fail(LXW_ERR_ARG, "lxw_solver_set_gate_wait_test: null solver or negative cycles");
+  s->gate_wait_test = cycles;
   drop_graphs(s);
   return LXW_OK;
 }

@@ -73,6 +73,7 @@ struct DevWork {
 struct ScalMx {
   double s, dt;           // wave speed (inflated FP32 maximum) and time step
   float s32, dt32, c1, c2;  // FP32: s, dt, dt/2, dt^2/6
+  int live;               // 0: the problem has reached the end time of a timed run (its kernels skip it)
 };
 
 // Workspace of the mixed-precision form (FP32 bulk, FP64 averages).
@@ -133,6 +134,7 @@ struct StepArgs {
   int hi_occupancy;                  // mixed form: the edge / gated-shock variants with more CTAs per SM
   const GateWeights* gate_w;         // learned gate weights or null
   float mlp_tau;                     // gate: skip the limiter where theta_hat >= 1 - tau
+  long long gate_wait_test;          // > 0: each gate CTA first waits this many cycles on a barrier nothing arrives at (test aid)
   float* feat_out;                   // [N][24] features at the shock limiter's input, or null
   float* gate_out;                   // [N] network output theta_hat (needs the gate), or null
   double qin[4];                     // conserved state of LXW_BC_INFLOW faces
@@ -144,6 +146,12 @@ struct StepArgs {
   int want_diag;
   double* theta_cell;     // [2][N] or null
   double* theta_edge;     // [N][E] or null
+  // timed runs (lxw_run_to): each problem steps until its clock reaches
+  // t_end, the last step shortened to land on it; tclock[4 p + (0..3)] =
+  // elapsed time, steps taken, dt and s of the last step taken
+  int timed;
+  double t_end;
+  double* tclock;
 };
 
 // Kernel launchers (lxw_kernels.cu).  All enqueue on `stream`, allocate nothing.

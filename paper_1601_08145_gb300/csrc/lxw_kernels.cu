@@ -42,9 +42,19 @@ struct DevDiag {             // layout of DevWork::diag
   unsigned long long nmom, nedge, nsc;
 };
 
+// A timed run (lxw_run_to) stops each problem when its clock reaches t_end:
+// the kernels of a step skip it then, and its last step is shortened to
+// land on t_end.  The clock only moves between steps (k_clock).
+__device__ __forceinline__ bool step_live(const StepArgs& a) { return !a.timed || __ldcg(a.tclock) < a.t_end; }
+
 __device__ __forceinline__ double step_dt(const DevWork& w, const DevMesh& m, const StepArgs& a) {
   double s = __longlong_as_double((long long)*w.smax);
-  return a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin / s;
+  double dt = a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin / s;
+  if (a.timed) {
+    const double t = __ldcg(a.tclock);
+    if (t + dt >= a.t_end) dt = a.t_end - t;
+  }
+  return dt;
 }
 
 // Euler flux and its directional derivatives (Eqs. 1-2, fluxderivs-a/b).
@@ -151,15 +161,30 @@ __device__ __forceinline__ double exact_root_theta(double rb, double mb, double 
 }
 
 // ------------------------------------------------------------ k_reset
-__global__ void k_reset(DevWork w, int want_diag) {
+__global__ void k_reset(DevWork w, int want_diag, int clear_status) {
   *w.smax = 0ull;
-  *w.status = 0u;
+  if (clear_status) *w.status = 0u;
   if (want_diag) {
     DevDiag* d = reinterpret_cast<DevDiag*>(w.diag);
     for (int c = 0; c < 4; ++c) d->sum[c] = 0.0;
     d->minr = d->minp = ~0ull;
     d->nmom = d->nedge = d->nsc = 0ull;
   }
+}
+
+// ------------------------------------------------------------ k_clock
+// End of a timed step: advance the clock by the step's dt, or set it to
+// t_end exactly on the shortened last step.
+__global__ void k_clock(const DevMesh m, const DevWork w, const StepArgs a) {
+  const double t = a.tclock[0];
+  if (!(t < a.t_end)) return;
+  const double s = __longlong_as_double((long long)*w.smax);
+  const double dt = a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin / s;
+  const bool last = t + dt >= a.t_end;
+  a.tclock[0] = last ? a.t_end : t + dt;
+  a.tclock[1] += 1.0;
+  a.tclock[2] = last ? a.t_end - t : dt;
+  a.tclock[3] = s;
 }
 
 // ------------------------------------------------------------ k_moment
@@ -174,6 +199,7 @@ __global__ void __launch_bounds__(128) k_moment(const DevMesh m, const DevWork w
   constexpr int NPT = NQ + E * MQ;
   const Tables& t = c_tabs[KD];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!step_live(a)) return;                 // uniform over the grid
   double smax = 0.0;
   if (i < m.N) {
     const double g = a.gamma, g1 = g - 1.0;
@@ -257,7 +283,7 @@ __global__ void __launch_bounds__(128) k_ck(const DevMesh m, const DevWork w, do
   constexpr int NPT = NQ + E * MQ;
   const Tables& t = c_tabs[KD];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.N) return;
+  if (i >= m.N || !step_live(a)) return;
   const int N = m.N;
   const double g1 = a.gamma - 1.0;
   const double dt = step_dt(w, m, a);
@@ -398,7 +424,7 @@ __global__ void __launch_bounds__(128) k_edge(const DevMesh m, const DevWork w, 
                                               const StepArgs a) {
   const Tables& t = c_tabs[KD];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.N) return;
+  if (i >= m.N || !step_live(a)) return;
   const int N = m.N;
   const double g = a.gamma, g1 = g - 1.0;
   const double s = __longlong_as_double((long long)*w.smax);
@@ -574,7 +600,7 @@ __global__ void __launch_bounds__(128) k_edge(const DevMesh m, const DevWork w, 
 template <int E, int ML>
 __global__ void __launch_bounds__(128) k_update(const DevMesh m, const DevWork w, double* __restrict__ Q, const StepArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.N) return;
+  if (i >= m.N || !step_live(a)) return;
   const int N = m.N;
   const double dt = step_dt(w, m, a);
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -608,7 +634,7 @@ __global__ void __launch_bounds__(128) k_shock(const DevMesh m, double* __restri
   constexpr int NPT = NQ + E * MQ;
   const Tables& t = c_tabs[KD];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.N) return;
+  if (i >= m.N || !step_live(a)) return;
   const int N = m.N;
   const double g1 = a.gamma - 1.0;
   double* Qi = Q + (size_t)i * 4 * ML;
@@ -740,7 +766,7 @@ int step_impl(const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a, 
   int ne = 0;
   auto mark = [&]() { if (events) cudaEventRecordWithFlags((cudaEvent_t)events[ne++], st, cudaEventRecordExternal); };
   mark();
-  k_reset<<<1, 1, 0, st>>>(w, a.want_diag);
+  k_reset<<<1, 1, 0, st>>>(w, a.want_diag, 0);   // status bits stay until a diagnostic step reads them
   mark();
   if (a.moment_exact)
     k_moment<KD, E, ML, NQ, MQ, true><<<grid, block, 0, st>>>(m, w, Q, a, a.theta_cell);
@@ -761,6 +787,7 @@ int step_impl(const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a, 
                                                        a.want_diag ? &dd->nsc : nullptr);
     mark();
   }
+  if (a.timed) k_clock<<<1, 1, 0, st>>>(m, w, a);
   if (a.want_diag) k_diag<ML><<<grid_for(m.N, 256), 256, 0, st>>>(m, w, Q, a.gamma);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -768,7 +795,7 @@ int step_impl(const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a, 
 template <int KD, int E, int ML, int NQ, int MQ>
 int moment_impl(const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a, double* theta,
                 cudaStream_t st, int block) {
-  k_reset<<<1, 1, 0, st>>>(w, 0);
+  k_reset<<<1, 1, 0, st>>>(w, 0, 1);
   if (a.moment_exact)
     k_moment<KD, E, ML, NQ, MQ, true><<<grid_for(m.N, block), block, 0, st>>>(m, w, Q, a, theta);
   else
@@ -850,10 +877,11 @@ size_t diag_bytes() { return sizeof(DevDiag); }
 // ====================================================================
 // Allocation-free variant of the moment limiter and wave-speed reduction.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is
-// being captured into a CUDA graph, code whose device memory belongs to
-// another allocator (a framework's caching pool or a fixed memory budget),
-// and code that must not take cudaMalloc's implicit device synchronisation.
+// Some callers cannot call cudaMalloc: code whose device memory belongs to
+// another allocator (a framework's caching pool, or a fixed budget carved
+// out at start-up, where a stray allocation could fail or fragment it), and
+// code that must not take cudaMalloc's implicit device synchronisation (a
+// time-critical loop sharing the GPU with other streams).
 // lxw_moment_limit_noalloc serves them: it needs no solver (whose creation
 // allocates), only the caller's state, theta and speed buffers.  The
 // reduction scratch of the wave speed -- one running maximum per chunk of
@@ -861,6 +889,7 @@ size_t diag_bytes() { return sizeof(DevDiag); }
 // below, which every GPU that loads the library holds until exit.
 // ====================================================================
 #include <mutex>
+#include <string>
 
 namespace lxw {
 namespace {
@@ -872,14 +901,17 @@ constexpr int kMaxDevices = 64;
 // slot maxima (bits of non-negative doubles), then one status word
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocSlots + 1];
 
+// zero the slots this call uses and the status word
 __global__ void k_noalloc_clear(int nslots) {
-  for (int c = threadIdx.x; c <= nslots; c += blockDim.x) g_noalloc_scratch[c] = 0ull;
+  for (int c = threadIdx.x; c < nslots; c += blockDim.x) g_noalloc_scratch[c] = 0ull;
+  if (threadIdx.x == 0) g_noalloc_scratch[kNoAllocSlots] = 0ull;
 }
 
-__global__ void k_noalloc_finish(int nslots, double* s_dev) {
+__global__ void k_noalloc_finish(int nslots, double* s_dev, unsigned int* status_dev) {
   unsigned long long m = 0ull;
   for (int c = 0; c < nslots; ++c) m = m > g_noalloc_scratch[c] ? m : g_noalloc_scratch[c];
   *s_dev = __longlong_as_double((long long)m);
+  if (status_dev) *status_dev = (unsigned int)g_noalloc_scratch[kNoAllocSlots];
 }
 
 std::mutex g_noalloc_mu;
@@ -887,8 +919,8 @@ unsigned long long* g_noalloc_addr[kMaxDevices] = {};
 bool g_noalloc_tables[kMaxDevices][4] = {};
 
 template <int KD, int E, int ML, int NQ, int MQ>
-int noalloc_impl(int N, double* Q, const StepArgs& a, double* theta, double* s_dev, cudaStream_t st,
-                 unsigned long long* scratch) {
+void noalloc_impl(int N, double* Q, const StepArgs& a, double* theta, double* s_dev, unsigned int* status_dev,
+                  cudaStream_t st, unsigned long long* scratch) {
   const int nslots = (N + kNoAllocChunk - 1) / kNoAllocChunk;
   k_noalloc_clear<<<1, 256, 0, st>>>(nslots);
   for (int c = 0; c < nslots; ++c) {
@@ -901,17 +933,25 @@ int noalloc_impl(int N, double* Q, const StepArgs& a, double* theta, double* s_d
     k_moment<KD, E, ML, NQ, MQ><<<grid_for(n, 128), 128, 0, st>>>(
         m, w, Q + (size_t)c * kNoAllocChunk * 4 * ML, a, theta ? theta + (size_t)c * kNoAllocChunk : nullptr);
   }
-  k_noalloc_finish<<<1, 1, 0, st>>>(nslots, s_dev);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  k_noalloc_finish<<<1, 1, 0, st>>>(nslots, s_dev, status_dev);
 }
 
 }  // namespace
 }  // namespace lxw
 
 extern "C" lxw_status lxw_moment_limit_noalloc(int kind, int degree, int n_elements, double gamma, double eps0,
-                                               double* Q_dev, double* theta_dev, double* s_dev, void* stream) {
+                                               double* Q_dev, double* theta_dev, double* s_dev,
+                                               unsigned int* status_dev, void* stream) {
   using namespace lxw;
   auto err = [](lxw_status st, const char* msg) { set_last_error(msg); return st; };
+  auto cuda_err = [](const char* what, cudaError_t e) {
+    std::string m = std::string("lxw_moment_limit_noalloc: ") + what + ": " + cudaGetErrorString(e);
+    set_last_error(m.c_str());
+    return LXW_ERR_CUDA;
+  };
+  // an error left by earlier work on this thread belongs to that work: report
+  // it without clearing it, and launch nothing
+  if (cudaError_t e = cudaPeekAtLastError(); e != cudaSuccess) return cuda_err("a CUDA error was already pending", e);
   if (!Q_dev || !s_dev) return err(LXW_ERR_ARG, "lxw_moment_limit_noalloc: null Q_dev or s_dev");
   if ((kind != LXW_KIND_QUAD && kind != LXW_KIND_TRI) || (degree != 2 && degree != 3))
     return err(LXW_ERR_ARG, "lxw_moment_limit_noalloc: kind must be quad/triangle and degree 2 or 3");
@@ -945,10 +985,23 @@ extern "C" lxw_status lxw_moment_limit_noalloc(int kind, int degree, int n_eleme
   a.gamma = gamma;
   a.eps0 = eps0;
   cudaStream_t st = (cudaStream_t)stream;
-  int rc;
-  if (kd == 0) rc = noalloc_impl<0, 4, 6, 9, 3>(n_elements, Q_dev, a, theta_dev, s_dev, st, scratch);
-  else if (kd == 1) rc = noalloc_impl<1, 4, 10, 16, 4>(n_elements, Q_dev, a, theta_dev, s_dev, st, scratch);
-  else if (kd == 2) rc = noalloc_impl<2, 3, 6, 9, 3>(n_elements, Q_dev, a, theta_dev, s_dev, st, scratch);
-  else rc = noalloc_impl<3, 3, 10, 16, 4>(n_elements, Q_dev, a, theta_dev, s_dev, st, scratch);
-  return rc ? err(LXW_ERR_CUDA, "lxw_moment_limit_noalloc: launch failed") : LXW_OK;
+  if (kd == 0) noalloc_impl<0, 4, 6, 9, 3>(n_elements, Q_dev, a, theta_dev, s_dev, status_dev, st, scratch);
+  else if (kd == 1) noalloc_impl<1, 4, 10, 16, 4>(n_elements, Q_dev, a, theta_dev, s_dev, status_dev, st, scratch);
+  else if (kd == 2) noalloc_impl<2, 3, 6, 9, 3>(n_elements, Q_dev, a, theta_dev, s_dev, status_dev, st, scratch);
+  else noalloc_impl<3, 3, 10, 16, 4>(n_elements, Q_dev, a, theta_dev, s_dev, status_dev, st, scratch);
+  if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return cuda_err("launch failed", e);
+  if (status_dev) return LXW_OK;
+  // no status pointer: wait for the call and read the status word (into a
+  // host variable: no allocation)
+  unsigned int word = 0;
+  if (cudaError_t e = cudaMemcpyFromSymbolAsync(&word, g_noalloc_scratch, sizeof(word),
+                                                 kNoAllocSlots * sizeof(unsigned long long),
+                                                 cudaMemcpyDeviceToHost, st);
+      e != cudaSuccess)
+    return cuda_err("reading the status word failed", e);
+  if (cudaError_t e = cudaStreamSynchronize(st); e != cudaSuccess) return cuda_err("waiting for the stream failed", e);
+  if (word & LXW_ST_NONPOSITIVE)
+    return err(LXW_ERR_NONPOSITIVE,
+               "lxw_moment_limit_noalloc: an input cell average had rho <= 0 or p <= 0 (its higher modes were zeroed)");
+  return LXW_OK;
 }

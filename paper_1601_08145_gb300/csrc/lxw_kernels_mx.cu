@@ -183,12 +183,31 @@ __device__ __forceinline__ unsigned long long obits(double x) {
 // per problem (one thread each): the step's wave speed and time step, in FP64 and FP32
 // a problem's wave speed and time step from its running maximum (Sec. 3.2 s,
 // the CFL rule), with the FP32 copies the bulk kernels use
+// the CFL rule, the last step of a timed run shortened to land on t_end and
+// the problem's clock advanced (once a problem's clock has reached t_end its
+// kernels skip it: live = 0, the last step's s and dt kept)
 __device__ __forceinline__ ScalMx make_scal(const DevMesh& m, const DevWorkMx& w, const StepArgs& a, int p) {
   const double s = __longlong_as_double((long long)__ldcg(w.smax + p));
-  const double dt = a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin_p[p] / s;
+  double dt = a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin_p[p] / s;
   ScalMx sc;
+  if (a.timed) {
+    double* tc = a.tclock + 4 * p;
+    const double t = tc[0];
+    if (!(t < a.t_end)) {
+      sc = w.scal[p];
+      sc.live = 0;
+      return sc;
+    }
+    const bool last = t + dt >= a.t_end;
+    if (last) dt = a.t_end - t;
+    tc[0] = last ? a.t_end : t + dt;
+    tc[1] += 1.0;
+    tc[2] = dt;
+    tc[3] = s;
+  }
   sc.s = s; sc.dt = dt;
   sc.s32 = (float)s; sc.dt32 = (float)dt; sc.c1 = (float)(0.5 * dt); sc.c2 = (float)(dt * dt / 6.0);
+  sc.live = 1;
   return sc;
 }
 
@@ -366,6 +385,8 @@ __global__ void __launch_bounds__(128, 6) k_moment_mx(const DevMesh m, const Dev
   const double gd1 = a.gamma - 1.0;
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
+    // a problem whose timed run has ended: nothing to do (uniform over the CTA)
+    if (a.timed && !(__ldcg(a.tclock + 4 * tile.z) < a.t_end)) continue;
     const int i = tile.x + threadIdx.x;
     const int wbase = tile.x + warp * 32;      // element of lane 0 of this warp
     float sm = 0.0f;
@@ -652,7 +673,8 @@ __global__ void __launch_bounds__(128, ML == 6 ? 4 : 2) k_ck_mx(const DevMesh m,
                                                                 double* __restrict__ state, const StepArgs a) {
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
-    if ((int)threadIdx.x < tile.y) ck_elem<KD, E, ML, NQ, MQ>(m, w, state, a, tile.x + threadIdx.x, w.scal[tile.z]);
+    if ((int)threadIdx.x < tile.y && w.scal[tile.z].live)
+      ck_elem<KD, E, ML, NQ, MQ>(m, w, state, a, tile.x + threadIdx.x, w.scal[tile.z]);
   }
 }
 
@@ -913,7 +935,8 @@ __global__ void __launch_bounds__(128, ML == 6 ? (HI ? 5 : 4) : 3) k_edge_mx(con
                                                                   double* __restrict__ state, const StepArgs a) {
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
-    if ((int)threadIdx.x < tile.y) edge_elem<KD, E, ML, NQ, MQ>(m, w, state, a, tile.x + threadIdx.x, tile.z);
+    if ((int)threadIdx.x < tile.y && w.scal[tile.z].live)
+      edge_elem<KD, E, ML, NQ, MQ>(m, w, state, a, tile.x + threadIdx.x, tile.z);
   }
 }
 
@@ -1008,7 +1031,7 @@ __global__ void __launch_bounds__(128, 6) k_update_mx(const DevMesh m, const Dev
                                                    const StepArgs a) {
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
-    if ((int)threadIdx.x < tile.y) update_elem<E, ML>(m, w, state, a, tile.x + threadIdx.x, tile.z);
+    if ((int)threadIdx.x < tile.y && w.scal[tile.z].live) update_elem<E, ML>(m, w, state, a, tile.x + threadIdx.x, tile.z);
   }
 }
 
@@ -1112,11 +1135,11 @@ __device__ __forceinline__ bool mbar_try(unsigned a, unsigned phase) {
       : "memory");
   return ok != 0u;
 }
-// true once the phase completed, false after kGateWaitCycles
-__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned phase) {
+// true once the phase completed, false after `limit` SM cycles
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned phase, long long limit = kGateWaitCycles) {
   const long long t0 = clock64();
   while (!mbar_try(a, phase))
-    if (clock64() - t0 > kGateWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 // 16 consecutive FP32 columns of this thread's TMEM lane; the wait carries the
@@ -1348,6 +1371,7 @@ __global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const D
                                                              double* __restrict__ theta_out) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const int N = m.N;
+  if (a.timed && !w.scal[0].live) return;   // a timed run that has ended (one problem: the host checks)
   if (a.gate_w == nullptr) {
     for (int i = blockIdx.x * blockDim.x + tid; i < N; i += gridDim.x * blockDim.x) {
       float f[kMlpIn];
@@ -1402,7 +1426,10 @@ __global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const D
     const bool inspect = a.gate_out || a.feat_out;          // every cell's theta_hat / features
     bool need_net = inspect || __syncthreads_or(i < N && !clr) != 0;
     if (need_net && !abort && !wready) {
-      abort = __syncthreads_or(!mbar_wait(wbar, 0)) != 0;
+      // test aid: a short wait on the MMA barrier before anything was
+      // committed to it (nothing can arrive), so the timeout path runs
+      if (a.gate_wait_test > 0) abort = __syncthreads_or(!mbar_wait(mbar, 0, a.gate_wait_test)) != 0;
+      if (!abort) abort = __syncthreads_or(!mbar_wait(wbar, 0)) != 0;
       wready = !abort;
     }
     float f[kMlpIn];
@@ -1525,7 +1552,7 @@ __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWork
                                                   const StepArgs a, double* __restrict__ theta_out, int limit) {
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
-    if ((int)threadIdx.x < tile.y)
+    if ((int)threadIdx.x < tile.y && w.scal[tile.z].live)
       shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, limit, tile.x + threadIdx.x, false);
   }
 }

@@ -28,12 +28,13 @@ EXPORTS = [
     "lxw_solver_set_stream", "lxw_solver_info", "lxw_projection_points", "lxw_project",
     "lxw_step", "lxw_run", "lxw_run_host", "lxw_moment_limit", "lxw_shock_limit",
     "lxw_step_launches", "lxw_profile_step", "lxw_step_phases", "lxw_workspace_copy",
-    "lxw_moment_limit_noalloc", "lxw_fma_peak", "lxw_state_bytes", "lxw_state_pack", "lxw_state_unpack",
+    "lxw_moment_limit_noalloc", "lxw_state_bytes", "lxw_state_pack", "lxw_state_unpack",
     "lxw_batch_create", "lxw_batch_scalars", "lxw_autotune",
     "lxw_mlp_create", "lxw_mlp_destroy", "lxw_mlp_num_params", "lxw_mlp_get_params", "lxw_mlp_set_params",
     "lxw_mlp_forward", "lxw_mlp_loss_grad", "lxw_mlp_train", "lxw_solver_set_mlp", "lxw_step_dump",
     "lxw_step_gate", "lxw_profile_phases", "lxw_basis_eval", "lxw_mesh_cartesian_masked",
     "lxw_solver_set_inflow", "lxw_mlp_set_envelope", "lxw_mlp_get_envelope", "lxw_run_host_state",
+    "lxw_solver_set_gate_wait_test", "lxw_run_to",
 ]
 
 
@@ -104,7 +105,6 @@ def lib():
     L.lxw_profile_step.argtypes = [_vp, _vp, C.c_double, C.POINTER(C.c_float)]
     L.lxw_step_phases.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int]
     L.lxw_workspace_copy.argtypes = [_vp, C.c_int, _dp, C.c_size_t]
-    L.lxw_fma_peak.argtypes = [C.c_int, _dp]
     L.lxw_batch_create.argtypes = [C.c_int, C.POINTER(_vp), C.c_int, C.POINTER(Options), _vp, C.POINTER(_vp)]
     L.lxw_batch_scalars.argtypes = [_vp, C.POINTER(C.c_int), _dp, _dp]
     L.lxw_autotune.argtypes = [_vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -122,13 +122,15 @@ def lib():
     L.lxw_mlp_train.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_ulonglong,
                                 C.POINTER(C.c_float)]
     L.lxw_solver_set_mlp.argtypes = [_vp, _vp, C.c_float]
+    L.lxw_solver_set_gate_wait_test.argtypes = [_vp, C.c_longlong]
+    L.lxw_run_to.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int, _vp, C.POINTER(C.c_int), _dp]
     L.lxw_step_dump.argtypes = [_vp, _vp, C.c_double, _vp, _vp]
     L.lxw_step_gate.argtypes = [_vp, _vp, C.c_double, _vp, _vp]
     L.lxw_state_bytes.argtypes = [_vp]
     L.lxw_state_bytes.restype = C.c_size_t
     L.lxw_state_pack.argtypes = [_vp, _vp, _vp]
     L.lxw_state_unpack.argtypes = [_vp, _vp, _vp]
-    L.lxw_moment_limit_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp, _vp, _vp]
+    L.lxw_moment_limit_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp]
     _lib = L
     return L
 
@@ -139,11 +141,14 @@ def _check(st, allow=()):
     return st
 
 
-def _ptr(t, shape=None, what="tensor"):
-    """data_ptr of a contiguous float64 CUDA tensor (None -> NULL)."""
+def _ptr(t, shape=None, what="tensor", torch_dtype="float64"):
+    """data_ptr of a contiguous float64 (or int32) CUDA tensor (None -> NULL)."""
     if t is None:
         return None
-    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+    if torch_dtype == "int32":
+        if not (t.is_cuda and not t.dtype.is_floating_point and t.element_size() == 4 and t.is_contiguous()):
+            raise ValueError(f"{what}: need a contiguous int32 CUDA tensor")
+    elif not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
         raise ValueError(f"{what}: need a contiguous float64 CUDA tensor")
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{what}: shape {tuple(t.shape)} != {tuple(shape)}")
@@ -318,6 +323,17 @@ def lxw_run(solver, Q, nsteps, cfl, diag=False):
     return _diag_result(st, d) if d is not None else None
 
 
+def lxw_run_to(solver, Q, t_span, cfl, max_steps=10_000_000, diag=False):
+    """Steps until the state has advanced by exactly t_span (the device
+    shortens the last step); returns (steps, t_reached, diag dict or None)."""
+    d = Diag() if diag else None
+    k = C.c_int(0); t = C.c_double(0.0)
+    st = _check(lib().lxw_run_to(solver.h, _ptr(Q, solver.state_shape, "Q"), t_span, cfl, max_steps,
+                                 C.byref(d) if d is not None else None, C.byref(k), C.byref(t)),
+                allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN, ERR_TIMEOUT))
+    return k.value, t.value, (_diag_result(st, d) if d is not None else None)
+
+
 def lxw_run_host(solver, Qh, nsteps, cfl, diag=False):
     """Qh: host buffer (numpy float64 array or pinned CPU torch tensor) [N][4][ML]."""
     if isinstance(Qh, np.ndarray):
@@ -386,20 +402,23 @@ def lxw_workspace_copy(solver, which):
     return out
 
 
-def lxw_moment_limit_noalloc(kind, degree, Q, theta=None, s_out=None, gamma=1.4, eps0=1e-12, stream=None):
+def lxw_moment_limit_noalloc(kind, degree, Q, theta=None, s_out=None, gamma=1.4, eps0=1e-12, stream=None,
+                             status=None):
     """Allocation-free moment limiter + wave speed (no solver needed).
-    Q: [N][4][ML] float64 CUDA tensor, in place; theta [N], s_out [1]."""
+    Q: [N][4][ML] float64 CUDA tensor (ML of the kind and degree), in place;
+    theta [N], s_out [1] float64; status [1] int32 (nullable: then the call
+    waits and raises LxwError(ERR_NONPOSITIVE) for a non-positive average)."""
+    if degree not in (2, 3) or kind not in (KIND_QUAD, KIND_TRI):
+        raise LxwError(ERR_ARG, "lxw_moment_limit_noalloc: kind must be quad/triangle and degree 2 or 3")
+    ML = (degree + 1) * (degree + 2) // 2
+    if Q.dim() != 3 or Q.shape[1] != 4 or Q.shape[2] != ML:
+        raise LxwError(ERR_ARG, "lxw_moment_limit_noalloc: Q must be [N][4][%d] for degree %d, got %s"
+                       % (ML, degree, tuple(Q.shape)))
     N = Q.shape[0]
-    _check(lib().lxw_moment_limit_noalloc(kind, degree, N, gamma, eps0, _ptr(Q, None, "Q"),
+    _check(lib().lxw_moment_limit_noalloc(kind, degree, N, gamma, eps0, _ptr(Q, (N, 4, ML), "Q"),
                                           _ptr(theta, (N,), "theta"), _ptr(s_out, (1,), "s_out"),
+                                          _ptr(status, (1,), "status", torch_dtype="int32"),
                                           _stream_handle(stream)))
-
-
-def lxw_fma_peak(fp64=True):
-    """Measured FMA throughput (TFLOP/s) of the FP64 or FP32 pipe."""
-    v = C.c_double()
-    _check(lib().lxw_fma_peak(int(bool(fp64)), C.byref(v)))
-    return v.value
 
 
 def lxw_batch_create(meshes, degree, options=None, stream=None):
@@ -511,6 +530,12 @@ def lxw_mlp_get_envelope(mlp):
     l = np.zeros(MLP_IN, np.float32); h = np.zeros(MLP_IN, np.float32)
     _check(lib().lxw_mlp_get_envelope(mlp.h, l.ctypes.data_as(C.POINTER(C.c_float)), h.ctypes.data_as(C.POINTER(C.c_float))))
     return l, h
+
+
+def lxw_solver_set_gate_wait_test(solver, cycles):
+    """Test aid: > 0 makes the gated shock kernel's first wait expire after
+    that many SM cycles (a barrier nothing arrives at); 0 switches it off."""
+    _check(lib().lxw_solver_set_gate_wait_test(solver.h, int(cycles)))
 
 
 def lxw_solver_set_mlp(solver, mlp, tau=0.05):

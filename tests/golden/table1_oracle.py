@@ -81,6 +81,10 @@ def main():
             rows.append(("global" if llf_global else "local",) + tuple(
                 r[k] for k in ("n", "steps", "l2", "floor", "g2", "avg", "n_mom", "n_edge", "n_sc")))
             print(rows[-1], flush=True)
+            write(rows)
+
+
+def write(rows):
     with open(OUT, "w") as f:
         f.write("# The oracle on the Table 1 problem (Sec. 4), written by table1_oracle.py.\n")
         f.write("# speed: dissipation speed of the LLF point flux (local: max |u|+c of the two\n")

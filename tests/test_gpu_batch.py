@@ -138,3 +138,55 @@ def test_gated_batch_equals_gated_individual_runs(L):
     for k in range(len(sizes)):
         assert torch.equal(Qb[off[k]:off[k + 1]], singles[k][0]), k
     assert skipped == sum(x[1] for x in singles) and skipped > 0
+
+
+def test_batch_against_oracle_problem_by_problem(L):
+    """Four problems of different sizes (one of 25 cells, less than a tile)
+    and data in one batched mixed solver with persistent CTAs: each
+    problem's slice against the oracle stepping that problem alone.
+    (1) From a shared state, one step: averages within 1e-5 of the largest,
+    modes within 1e-3 of their scale, relative L1 within 1e-5 (the FP32
+    budget of one step), and each problem's own s and dt equal to the
+    oracle's (s within the FP32 speed inflation 3e-5).  (2) From the initial
+    data, 8 steps: relative L1 within 1e-4 per problem."""
+    from oracle import oracle as O
+    sizes = [5, 13, 24, 9]
+    cfl = 0.3
+    opt = L.lxw_options_default(precision=L.PREC_MIXED, ctas_per_sm=2)
+    probs = [quadrant_problem(L, n, 400 + k) for k, n in enumerate(sizes)]
+    b = L.lxw_batch_create([m for m, _ in probs], 2, opt, stream=torch.cuda.current_stream())
+    Q = torch.cat([projected(L, L.lxw_solver_create(m, 2, stream=torch.cuda.current_stream()), ic)
+                   for m, ic in probs])
+    st = L.new_state(b, Q)
+    Q0 = L.to_q64(b, st).cpu().numpy()                 # FP32 modes: the inputs both sides see
+    off = b.offsets
+    oracles = [O.Solver(O.Mesh.cartesian(n, n, (0.0, 1.0, 0.0, 1.0), (2, 2, 2, 2)), 2) for n in sizes]
+    # (2) 8 steps from the initial data
+    Qos = [Q0[off[k]:off[k + 1]].copy() for k in range(len(sizes))]
+    for _ in range(8):
+        L.lxw_step(b, st, 0.0, cfl)
+        for so, Qo in zip(oracles, Qos):
+            so.step(Qo, cfl=cfl)
+    Qb = L.to_q64(b, st).cpu().numpy()
+    for k, Qo in enumerate(Qos):
+        Qg = Qb[off[k]:off[k + 1]]
+        assert np.abs(Qg - Qo).sum() / np.abs(Qo).sum() < 1e-4, k
+    # (1) one step from the shared state after those 8
+    Qs = Qb.copy()
+    Qs[:, :, 1:] = Qs[:, :, 1:].astype(np.float32)
+    st = L.new_state(b, torch.from_numpy(Qs).cuda())
+    d = L.lxw_step(b, st, 0.0, cfl, diag=True)
+    assert d["status"] == 0
+    sv, dv = L.lxw_batch_scalars(b)
+    Qb = L.to_q64(b, st).cpu().numpy()
+    for k, so in enumerate(oracles):
+        Qo = Qs[off[k]:off[k + 1]].copy()
+        do = so.step(Qo, cfl=cfl)
+        Qg = Qb[off[k]:off[k + 1]]
+        sc = np.abs(Qo).max(axis=0, keepdims=True) + 1e-3
+        assert np.abs(Qg[:, :, 0] - Qo[:, :, 0]).max() < 1e-5 * np.abs(Qo[:, :, 0]).max(), k
+        assert (np.abs(Qg - Qo) / sc).max() < 1e-3, k
+        assert np.abs(Qg - Qo).sum() / np.abs(Qo).sum() < 1e-5, k
+        assert abs(sv[k] / do["s"] - 1) < 3e-5, k
+        assert abs(dv[k] / do["dt"] - 1) < 3e-5, k
+    assert len(set(np.round(dv, 12))) == len(sizes)   # four different time steps

@@ -130,30 +130,31 @@ def test_mixed_positivity_blast_and_rarefaction(L):
 
 
 def test_mixed_l1_error_equals_fp64_on_exact_wave(L):
-    """Config of the smooth advected wave (32x32, P2, CFL 0.1, t = 0.1, all
-    limiters on): the mixed form's L1 density error against the exact
-    solution is within 5 % of the FP64 GPU form's."""
+    """The smooth advected wave (32x32, P2, CFL 0.1, all limiters on) run to
+    t = 0.1 exactly (lxw_run_to): the L1 error of the cell-average density
+    against the exact cell averages, the norm the metric's "equal L1 error"
+    names, is within 5 % of the FP64 GPU form's for the mixed form; the L2
+    error of the DG density within 1 %."""
+    from oracle import oracle as O   # only to project the exact solution and evaluate fields
     T = 0.1
-    errs = {}
+    so = O.Solver(O.Mesh.cartesian(32, 32), 2)
+    Qx = so.project_fn(lambda x, y: (synth.exact_smooth_density(x, y, T), 1.0 + 0 * x, 1.0 + 0 * x, 1.0 + 0 * x))
+    xy = so.projection_points(); w = so.projection_weights()
+    ex = synth.exact_smooth_density(xy[..., 0], xy[..., 1], T)
+    l1, l2 = {}, {}
     for mixed in (False, True):
         s = solver(L, QUAD, 2, 32, mixed=mixed)
         Q = project(L, s, synth.ic_smooth)
         st = L.new_state(s, Q) if mixed else Q
-        t = 0.0
-        while t < T - 1e-12:
-            d = L.lxw_step(s, st, 0.0, 0.1, diag=True)
-            t += d["dt"]
+        steps, t, _ = L.lxw_run_to(s, st, T, 0.1)
+        assert t == T
         Qe = L.to_q64(s, st).cpu().numpy()
-        # error at the projection points with the oracle-independent rule of the library
-        xy = L.lxw_projection_points(s)
-        from oracle import oracle as O   # only to evaluate the modal field at points
-        so = O.Solver(O.Mesh.cartesian(32, 32), 2)
-        q = so.eval_projection_points(Qe)
-        w = so.projection_weights()
-        ex = synth.exact_smooth_density(xy[..., 0], xy[..., 1], t)
-        errs[mixed] = float(np.sum(w[None, :] * np.abs(q[..., 0] - ex)) / (32 * 32))
-    print("L1 errors fp64 / mixed", errs)
-    assert errs[True] <= 1.05 * errs[False]
+        l1[mixed] = float(np.mean(np.abs(Qe[:, 0, 0] - Qx[:, 0, 0])))
+        q = so.eval_projection_points(Qe)[..., 0]
+        l2[mixed] = float(np.sqrt(np.sum(w[None, :] * (q - ex) ** 2) / (32 * 32)))
+    print("cell-average L1 errors fp64 / mixed", l1, "L2", l2)
+    assert l1[True] <= 1.05 * l1[False]
+    assert l2[True] <= 1.01 * l2[False]
 
 
 def test_mixed_run_graph_and_host_path(L):

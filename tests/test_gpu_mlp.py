@@ -225,3 +225,30 @@ def test_tensor_core_gate_matches_reference_network(L, kind, n, deg):
     assert np.mean(d < 2e-5) > 0.99, np.sort(d)[-5:]
     assert d.max() < 5e-3, d.max()
     assert g.std() > 1e-3                                 # the cells do not all give one value
+
+
+def test_gate_wait_expiry_takes_the_timeout_path(L):
+    """The gate's bounded device wait made to run out (a short wait on a
+    barrier nothing arrives at, set from the host): the step returns
+    LXW_ERR_TIMEOUT, its state equals the ungated step's bit for bit (every
+    CTA falls back to the plain limiter), and the next step, with the normal
+    bound, is clean and gated again."""
+    net = L.lxw_mlp_create(256, seed=9, stream=torch.cuda.current_stream())   # unbounded envelope
+    res = {}
+    for mode in ("plain", "gated_timeout"):
+        s = mixed_solver(L, "quad", 48, box=(-1.1, 1.1, -1.1, 1.1), bc=(1, 1, 1, 1))
+        st = start(L, s, synth.ic_blast(48))
+        for _ in range(10):
+            L.lxw_step(s, st, 0.0, 0.1)                  # a front for the network to rule on
+        if mode == "gated_timeout":
+            L.lxw_solver_set_mlp(s, net, 0.999)         # skips nearly every cell it rules on
+            L.lxw_solver_set_gate_wait_test(s, 1000)
+        d = L.lxw_step(s, st, 0.0, 0.1, diag=True)
+        res[mode] = (st.clone(), d)
+        if mode == "gated_timeout":
+            assert d["return_status"] == L.ERR_TIMEOUT and d["status"] & 8 and d["n_mlp_skip"] == 0
+            L.lxw_solver_set_gate_wait_test(s, 0)
+            d2 = L.lxw_step(s, st, 0.0, 0.1, diag=True)
+            assert d2["return_status"] == L.OK and d2["status"] == 0 and d2["n_mlp_skip"] > 0
+    assert res["plain"][1]["return_status"] == L.OK
+    assert torch.equal(res["gated_timeout"][0], res["plain"][0])

@@ -1,0 +1,178 @@
+"""lxw_run_to: steps to a final time with the last step shortened on the
+device, no host synchronisation per step.
+
+* It takes exactly the steps of a host loop that steps with the CFL rule and
+  redoes the last step with dt = T - t (same states bit for bit, FP64 and
+  mixed), reaches T exactly, and the FP64 result matches the oracle run the
+  same way.
+* Each problem of a batch keeps its own clock: the batch equals the
+  problems run alone.
+* The paper's convergence problem (Sec. 4, Table 1) at t = 0.02: the GPU's
+  FP64 errors equal the oracle's stored ones (golden/table1_oracle.txt,
+  written by golden/table1_oracle.py from the oracle only), and the mixed
+  form's errors equal the FP64 form's (the metric's "equal L1 error").
+"""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need CUDA")
+    from paper_1601_08145_gb300 import build
+    build.build()
+    from paper_1601_08145_gb300 import lxw
+    return lxw
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.lib()
+    return oracle
+
+
+def solver(L, n, mixed, box=(0.0, 1.0, 0.0, 1.0), bc=(0, 0, 0, 0)):
+    mesh = L.lxw_mesh_cartesian(n, n, box, bc)
+    o = L.lxw_options_default(precision=L.PREC_MIXED if mixed else L.PREC_FP64)
+    return L.lxw_solver_create(mesh, 2, o, stream=torch.cuda.current_stream())
+
+
+def start(L, s, ic):
+    xy = L.lxw_projection_points(s)
+    r, u, v, p = ic(xy[..., 0], xy[..., 1])
+    prim = torch.from_numpy(np.stack(np.broadcast_arrays(r, u, v, p), axis=-1).copy()).cuda()
+    Q = torch.zeros(s.q64_shape, dtype=torch.float64, device="cuda")
+    L.lxw_project(s, prim, Q)
+    return L.new_state(s, Q)
+
+
+def host_loop(L, s, st, T, cfl):
+    """CFL steps; the step that would pass T is redone from its start with
+    dt = T - t."""
+    t, k = 0.0, 0
+    while True:
+        trial = st.clone()
+        d = L.lxw_step(s, trial, 0.0, cfl, diag=True)
+        k += 1
+        if t + d["dt"] >= T:
+            L.lxw_step(s, st, T - t, cfl)
+            return k
+        st.copy_(trial)
+        t += d["dt"]
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_run_to_equals_the_host_loop(L, O, mixed):
+    T, cfl = 0.1, 0.1
+    s = solver(L, 32, mixed)
+    A = start(L, s, synth.ic_smooth)
+    B = A.clone()
+    steps, t, d = L.lxw_run_to(s, A, T, cfl, diag=True)
+    assert t == T and d["return_status"] == L.OK and d["min_rho"] > 0
+    k = host_loop(L, s, B, T, cfl)
+    assert steps == k
+    assert torch.equal(A, B)
+    if not mixed:
+        # the oracle, stepped the same way, to 1e-11 relative L1
+        os_ = O.Solver(O.Mesh.cartesian(32, 32), 2)
+        Qo = os_.project_fn(synth.ic_smooth)
+        t = 0.0
+        while True:
+            Qc = Qo.copy()
+            do = os_.step(Qc, cfl=cfl)
+            if t + do["dt"] >= T:
+                os_.step(Qo, dt=T - t)
+                break
+            Qo[...] = Qc
+            t += do["dt"]
+        Qg = L.to_q64(s, A).cpu().numpy()
+        assert np.abs(Qg - Qo).sum() / np.abs(Qo).sum() < 1e-11
+
+
+def test_run_to_stops_at_max_steps_and_restarts_its_clock(L):
+    s = solver(L, 16, True)
+    A = start(L, s, synth.ic_smooth)
+    steps, t, _ = L.lxw_run_to(s, A, 0.1, 0.1, max_steps=5)
+    assert steps == 5 and 0.0 < t < 0.1
+    # every call is a fresh run from its own t = 0
+    steps, t, _ = L.lxw_run_to(s, A, 1e-3, 0.1)
+    assert t == 1e-3 and steps >= 1
+
+
+def test_batch_problems_keep_their_own_clocks(L):
+    """Three problems of different sizes and data in one batched solver run
+    to the same T: each equals its own single-problem run bit for bit."""
+    T, cfl = 0.05, 0.2
+    specs = [(12, synth.ic_smooth), (20, synth.ic_quadrants(3)), (33, synth.ic_quadrants(4))]
+    bc = (2, 2, 2, 2)
+    o = L.lxw_options_default(precision=L.PREC_MIXED)
+    meshes = [L.lxw_mesh_cartesian(n, n, (0.0, 1.0, 0.0, 1.0), bc) for n, _ in specs]
+    bs = L.lxw_batch_create(meshes, 2, o, stream=torch.cuda.current_stream())
+    singles, states = [], []
+    for (n, ic), m in zip(specs, meshes):
+        s1 = L.lxw_solver_create(m, 2, o, stream=torch.cuda.current_stream())
+        st = start(L, s1, ic)
+        L.lxw_run_to(s1, st, T, cfl)
+        singles.append(L.to_q64(s1, st).cpu().numpy())
+        xy = L.lxw_projection_points(s1)
+        r, u, v, p = ic(xy[..., 0], xy[..., 1])
+        states.append(np.stack(np.broadcast_arrays(r, u, v, p), axis=-1))
+    prim = torch.from_numpy(np.concatenate(states).copy()).cuda()
+    Q = torch.zeros(bs.q64_shape, dtype=torch.float64, device="cuda")
+    L.lxw_project(bs, prim, Q)
+    stb = L.new_state(bs, Q)
+    steps, t, _ = L.lxw_run_to(bs, stb, T, cfl)
+    assert t == T
+    out = L.to_q64(bs, stb).cpu().numpy()
+    off = 0
+    for (n, _), ref in zip(specs, singles):
+        assert np.array_equal(out[off:off + n * n], ref)
+        off += n * n
+
+
+def _runner():
+    spec = importlib.util.spec_from_file_location("table1_oracle", os.path.join(HERE, "golden", "table1_oracle.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_table1_problem_on_the_gpu(L, O):
+    """t = 0.02, CFL 0.08 on 42^2, 63^2, 94^2, 141^2: the FP64 form's L2 error
+    equals the oracle's stored one to 1e-6 (relative), the mixed form's is
+    within 1 % of the FP64 form's, and both fall at third order."""
+    t1 = _runner()
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "table1_oracle.txt")) if l.strip() and not l.startswith("#")]
+    stored = {int(r[1]): float(r[3]) for r in rows if r[0] == "local"}
+    errs = {False: [], True: []}
+    ns = (42, 63, 94, 141)
+    for n in ns:
+        os_ = O.Solver(O.Mesh.cartesian(n, n), 2)
+        xy = os_.projection_points(); w = os_.projection_weights(); area = os_.mesh.geometry()[0]
+        ex = synth.exact_paper_smooth_density(xy[..., 0], xy[..., 1], t1.T_END)
+        for mixed in (False, True):
+            s = solver(L, n, mixed)
+            st = start(L, s, synth.ic_paper_smooth)
+            steps, t, d = L.lxw_run_to(s, st, t1.T_END, t1.CFL, diag=True)
+            assert t == t1.T_END and d["return_status"] == L.OK and d["min_rho"] > 0
+            q = os_.eval_projection_points(L.to_q64(s, st).cpu().numpy())[..., 0]
+            errs[mixed].append(np.sqrt(np.sum(area[:, None] * w[None, :] * (q - ex) ** 2)))
+    for n, e in zip(ns, errs[False]):
+        assert abs(e - stored[n]) <= 1e-6 * stored[n], (n, e, stored[n])
+    for e64, e32 in zip(errs[False], errs[True]):
+        assert abs(e32 - e64) <= 1e-2 * e64
+    for mixed in (False, True):
+        e = errs[mixed]
+        for a, b, na, nb in zip(e[:-1], e[1:], ns[:-1], ns[1:]):
+            assert np.log(a / b) / np.log(nb / na) >= 2.8
