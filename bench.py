@@ -3,12 +3,15 @@
 
 A step is one pass of the whole hot path (moment limiter, wave speed, CK
 time-averaged flux and volume integral, edge fluxes, flux limiter, blended
-update, shock limiter) over the workload.  Default workload: 224x224 squares
-split into 100,352 jittered triangles (seeded +-20% vertex jitter), P2
-(24 DOF per element), two-rarefaction near-vacuum data, transparent
-boundaries, CFL 0.1 -- the unstructured-triangle configuration the metric is
-quoted on.  Inputs are synthetic and resident in HBM before timing; the L2
-is flushed (256 MB write) between timed steps.
+update, shock limiter) over the workload.  Default workload: the learned-
+indicator configuration -- a 2048x2048 Cartesian P2 point-energy blast
+(4,194,304 cells) and 708x708 squares split into 1,002,528 jittered P2
+triangles with the two-rarefaction near-vacuum data; one step is one step of
+each, the mixed form with the MLP-gated shock limiter timed against the
+plain FP64 form on the same meshes.  The 224x224x2 = 100,352-triangle
+rarefaction (the unstructured configuration of the FP64-vs-mixed
+comparison) is measured beside it.  Inputs are synthetic and resident in
+HBM before timing; the L2 is flushed (256 MB write) between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -47,6 +50,8 @@ WORKLOADS = {
                       desc="rarefaction: 224x224x2 = 100,352 jittered triangles, P3, rho=1 p=0.4 u=-+2, transparent"),
     "rarefy1m": dict(kind="tri", n=724, deg=2, cfl=0.1, ic=synth.ic_rarefy,
                      desc="rarefaction: 724x724x2 = 1,048,352 jittered triangles, P2, rho=1 p=0.4 u=-+2, transparent"),
+    "rarefy708": dict(kind="tri", n=708, deg=2, cfl=0.1, ic=synth.ic_rarefy,
+                      desc="rarefaction: 708x708x2 = 1,002,528 jittered triangles, P2, rho=1 p=0.4 u=-+2, transparent"),
     "blast2048": dict(kind="quad", n=2048, deg=2, cfl=0.1, ic=None, bc=(1, 1, 1, 1), box=(-1.1, 1.1, -1.1, 1.1),
                       desc="blast: 2048x2048 Cartesian, P2, point energy 0.979264 in the 4 centre cells, reflective"),
     "sedov": dict(kind="disk", n=136270, deg=2, cfl=0.1, ic=synth.ic_sedov_disk(136270),
@@ -58,6 +63,23 @@ WORKLOADS = {
                              "step [0,1]x[0,6] (123,300 cells), P2, inflow above the step, walls on it, "
                              "transparent elsewhere"),
 }
+# Workloads made of several meshes: one step is one step of each part.
+CONFIGS = {
+    "config5": dict(parts=("blast2048", "rarefy708"),
+                    desc="learned-indicator configuration: 2048x2048 Cartesian P2 blast (4,194,304 cells, point energy "
+                         "0.979264 in the 4 centre cells, reflective) and 708x708x2 = 1,002,528 jittered P2 "
+                         "triangles (rho=1 p=0.4 u=-+2, transparent); one step = one step of each"),
+}
+
+
+def parts_of(name):
+    return CONFIGS[name]["parts"] if name in CONFIGS else (name,)
+
+
+def desc_of(name):
+    return CONFIGS[name]["desc"] if name in CONFIGS else WORKLOADS[name]["desc"]
+
+
 ENSEMBLE = dict(count=256, lo=32, hi=256, seed=4242, deg=2, cfl=0.3,
                 desc="ensemble: 256 independent Cartesian problems n_p x n_p, n_p ~ U{32..256} (seed 4242), "
                      "P2, four-quadrant Riemann data per problem seed, transparent")
@@ -78,10 +100,27 @@ def ck_flops_per_element(kind, deg):
 
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64 (recipe table; the FMA probe measures 1.253)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x 2 flop x max SM clock
-# DRAM bytes per k_ck launch from the ncu capture summarised in profiles/ (None until captured
-# for the current kernel version)
-CK_TRAFFIC_BYTES = 27_383_296 + 40_022_272   # k_ck of the FP64 form, profiles/k_ck_rarefy224_p2_fp64.md
-CK_MX_TRAFFIC_BYTES = 13766400   # k_ck_mx DRAM read + write per launch, rarefaction 100k (ncu)
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the CK kernel, from ncu captures, per (workload, form): the bytes, the first
+# 16 hex digits of the SHA-256 of the kernel source the capture ran, and the
+# elements of the captured mesh when it was a smaller mesh of the same kind
+# scaled to the workload by the element count (the traffic of this kernel is
+# proportional to it).  A capture of another kernel source reads as None.
+CK_TRAFFIC = {}
+
+
+def kernel_source_hash(mixed):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1601_08145_gb300", "csrc", "lxw_kernels_mx.cu" if mixed else "lxw_kernels.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def ck_traffic(name, mixed, elements):
+    rec = CK_TRAFFIC.get((name, "mixed" if mixed else "fp64"))
+    if rec is None or rec["source"] != kernel_source_hash(mixed):
+        return None
+    return rec["bytes"] * elements / rec.get("captured_elements", elements)
 
 
 def build_workload(L, name, stream, mixed):
@@ -237,51 +276,62 @@ def train_indicator(L, stream, tau=0.01):
 
 
 def cpu_baseline(name, budget_s=10.0):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload."""
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same
+    workload: whole steps of each part, at least one and up to 5 per part
+    (the step window of the measurement plan) or the time budget."""
     from oracle import oracle as O
-    w = WORKLOADS[name]
-    s, Q = oracle_solver(w)
-    s.step(Q, cfl=w["cfl"])          # untimed first step (page-in)
-    t0 = time.perf_counter(); k = 0
-    while k < 3 or (time.perf_counter() - t0 < budget_s and k < 400):
-        s.step(Q, cfl=w["cfl"]); k += 1
-    dt = time.perf_counter() - t0
-    dof = s.N * 4 * s.ML
-    out = {"value": dof * k / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-           "sample": f"{k} full steps of the {name} workload ({s.N} elements) from its initial data, {dt:.1f} s"}
+    dofs, secs, ks = 0.0, 0.0, []
+    for part in parts_of(name):
+        w = WORKLOADS[part]
+        s, Q = oracle_solver(w)
+        s.step(Q, cfl=w["cfl"])          # untimed first step (page-in)
+        t0 = time.perf_counter(); k = 0
+        while k < 1 or (time.perf_counter() - t0 < budget_s / len(parts_of(name)) and k < 5):
+            s.step(Q, cfl=w["cfl"]); k += 1
+        secs += time.perf_counter() - t0
+        dofs += s.N * 4 * s.ML * k
+        ks.append(f"{k} full steps of {part} ({s.N} elements)")
+        del s, Q
+    out = {"value": dofs / secs, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+           "sample": "; ".join(ks) + f" from the initial data, {secs:.1f} s"}
     # the same oracle on one core: the reference arm in a child process with one OpenMP thread
     try:
         env = dict(os.environ, OMP_NUM_THREADS="1", RANK="0", WORLD_SIZE="1")
         r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", name,
-                            "--steps", "3", "--warmup", "1"], env=env, capture_output=True, text=True, timeout=600)
+                            "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=900)
         one = json.loads(r.stdout.strip().splitlines()[-1])
         out["one_core"] = {"value": one["value"], "cores": one["cpu_baseline"]["cores"],
-                           "sample": "3 full steps after 1 warm-up step, OMP_NUM_THREADS=1"}
+                           "sample": "1 full step of each part, OMP_NUM_THREADS=1"}
     except Exception as e:   # the multi-core number stands on its own
         out["one_core"] = {"value": None, "error": str(e)[:200]}
-    return out, k, dt
+    return out, ks, secs
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores,
+    on the same workload (every part), K timed steps after W warm-up steps."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import oracle as O
-    w = WORKLOADS[args.workload]
-    s, Q = oracle_solver(w)
+    sols = [(WORKLOADS[p],) + oracle_solver(WORKLOADS[p]) for p in parts_of(args.workload)]
     for _ in range(args.warmup):
-        s.step(Q, cfl=w["cfl"])
+        for w, s, Q in sols:
+            s.step(Q, cfl=w["cfl"])
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s.step(Q, cfl=w["cfl"])
+        for w, s, Q in sols:
+            s.step(Q, cfl=w["cfl"])
     dt = time.perf_counter() - t0
-    val = s.N * 4 * s.ML * args.steps / dt
+    dof = sum(s.N * 4 * s.ML for _, s, _ in sols)
+    val = dof * args.steps / dt
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": w["desc"], "elements": s.N, "degree": w["deg"], "form": "FP64 CPU oracle"},
+           "config": {"workload": desc_of(args.workload), "elements": sum(s.N for _, s, _ in sols), "degree": 2,
+                      "form": "FP64 CPU oracle"},
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                            "sample": f"{args.steps} full steps after {args.warmup} warm-up steps"},
+                            "sample": f"{args.steps} full steps of every part after {args.warmup} warm-up steps"},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -557,10 +607,11 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rarefy", choices=sorted(WORKLOADS) + ["ensemble"])
+    ap.add_argument("--workload", default="config5", choices=sorted(WORKLOADS) + sorted(CONFIGS) + ["ensemble"])
     ap.add_argument("--tau", type=float, default=0.01, help="learned gate: skip where theta_hat >= 1 - tau")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work list of the mixed forms")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 100,352-triangle secondary line")
     ap.add_argument("--form", default="all", choices=["all", "learned", "mixed", "fp64"],
                     help="all: FP64, mixed and mixed + learned (headline); otherwise time only that form")
     args = ap.parse_args()
@@ -574,6 +625,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -586,8 +638,8 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     probes = fma_probes()
 
-    def timed_form(mixed, clocks=None, net=None):
-        w, sol = build_workload(L, args.workload, stream, mixed)
+    def prepare(name, mixed, net):
+        w, sol = build_workload(L, name, stream, mixed)
         if net is not None:
             L.lxw_solver_set_mlp(sol, net, args.tau)
         Q = project(L, sol, w)
@@ -595,6 +647,13 @@ def main():
         if mixed and not args.no_autotune:
             tune = L.lxw_autotune(sol, Q, w["cfl"], reps=3)     # on a scratch copy; Q is restored
         L.lxw_run(sol, Q, max(args.warmup, 3), w["cfl"])
+        return dict(name=name, w=w, sol=sol, Q=Q, tune=tune, dof=sol.N * 4 * sol.ML)
+
+    def timed_form(workload, mixed, clocks=None, net=None):
+        """Every part of the workload prepared (solver, data, autotuned work
+        list, warm-up), then K timed steps of each; the workload's time is the
+        sum over its parts."""
+        parts = [prepare(p, mixed, net) for p in parts_of(workload)]
         torch.cuda.synchronize()
         if clocks:
             clocks.start()
@@ -602,79 +661,105 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        total_ms = time_steps(L, sol, Q, w["cfl"], args.steps, flush)
+        for f in parts:
+            f["total_ms"] = time_steps(L, f["sol"], f["Q"], f["w"]["cfl"], args.steps, flush)
         if world > 1:
             dist.barrier()
         clk = clocks.stop() if clocks else None
+        total_ms = sum(f["total_ms"] for f in parts)
         if world > 1:
             total_ms = max_over_ranks(total_ms, dist, "cuda")
         # per-phase device times from a separately traced pass (event nodes between the phases)
-        phases = []
-        for k in range(5):
-            flush.fill_(float(k))
-            phases.append(L.lxw_profile_step(sol, Q, w["cfl"]))
-        dof = sol.N * 4 * sol.ML
-        mean_phase = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
-        return dict(w=w, sol=sol, Q=Q, total_ms=total_ms, dof=dof,
-                    value=whole_job_rate(dof * args.steps, world, total_ms / 1e3),
-                    phases=mean_phase, clocks=clk, tune=tune)
+        for f in parts:
+            ph = []
+            for k in range(5):
+                flush.fill_(float(k))
+                ph.append(L.lxw_profile_step(f["sol"], f["Q"], f["w"]["cfl"]))
+            f["phases"] = {k: statistics.mean(p[k] for p in ph) for k in ph[0]}
+        dof = sum(f["dof"] for f in parts)
+        phases = {k: sum(f["phases"][k] for f in parts) for k in parts[0]["phases"]}
+        return dict(parts=parts, total_ms=total_ms, dof=dof, value=whole_job_rate(dof * args.steps, world, total_ms / 1e3),
+                    phases=phases, clocks=clk, launches=sum(L.lxw_step_launches(f["sol"]) for f in parts))
 
-    def e2e_of(sol, state, cfl):
-        """End to end through the public C ABI on HOST memory: every step, the
-        host-to-device copy of the state (pinned, in the solver's own layout:
-        the mixed form's packed FP64 averages + FP32 modes), one step, the
-        device-to-host copy of the result (lxw_run_host_state).  The FP64-layout
-        entry (lxw_run_host: the state as Q[N][4][ML] doubles, converted on
-        the way) is timed beside it."""
-        def timed(fn):
-            fn()
+    def e2e_of(form):
+        """End to end through the public C ABI on HOST memory: every step, for
+        every part, the host-to-device copy of the state (pinned, in the
+        solver's own layout: the mixed form's packed FP64 averages + FP32
+        modes), one step, the device-to-host copy of the result
+        (lxw_run_host_state).  The FP64-layout entry (lxw_run_host: the state
+        as Q[N][4][ML] doubles, converted on the way) is timed beside it."""
+        def timed(fns):
+            for fn in fns:
+                fn()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(args.steps):
-                fn()
+                for fn in fns:
+                    fn()
             return time.perf_counter() - t0
-        dof = sol.N * 4 * sol.ML
-        Sh = torch.empty(sol.state_shape, dtype=torch.float64).pin_memory()
-        Sh.copy_(state.cpu())
-        e2e_s = timed(lambda: L.lxw_run_host_state(sol, Sh, 1, cfl))
-        Qh = torch.empty(sol.q64_shape, dtype=torch.float64).pin_memory()
-        Qh.copy_((L.to_q64(sol, state) if sol.mixed else state).cpu())
-        q64_s = timed(lambda: L.lxw_run_host(sol, Qh, 1, cfl))
+        state_fns, q64_fns, sbytes, qbytes = [], [], 0, 0
+        for f in form["parts"]:
+            sol, cfl = f["sol"], f["w"]["cfl"]
+            Sh = torch.empty(sol.state_shape, dtype=torch.float64).pin_memory()
+            Sh.copy_(f["Q"].cpu())
+            Qh = torch.empty(sol.q64_shape, dtype=torch.float64).pin_memory()
+            Qh.copy_((L.to_q64(sol, f["Q"]) if sol.mixed else f["Q"]).cpu())
+            state_fns.append(lambda sol=sol, Sh=Sh, cfl=cfl: L.lxw_run_host_state(sol, Sh, 1, cfl))
+            q64_fns.append(lambda sol=sol, Qh=Qh, cfl=cfl: L.lxw_run_host(sol, Qh, 1, cfl))
+            sbytes += sol.state_bytes; qbytes += f["dof"] * 8
+        e2e_s, q64_s = timed(state_fns), timed(q64_fns)
+        dof = form["dof"]
         return {"value": world * dof * args.steps / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": sol.state_bytes, "d2h_bytes_per_step": sol.state_bytes,
-                "api": "lxw_run_host_state (host copy of the solver's state layout)",
+                "h2d_bytes_per_step": sbytes, "d2h_bytes_per_step": sbytes,
+                "api": "lxw_run_host_state (host copy of the solver's state layout), every part every step",
                 "fp64_layout": {"value": world * dof * args.steps / q64_s, "api": "lxw_run_host",
-                                "h2d_bytes_per_step": dof * 8, "d2h_bytes_per_step": dof * 8}}
+                                "h2d_bytes_per_step": qbytes, "d2h_bytes_per_step": qbytes}}
+
+    def roofline_of(form, mixed):
+        """The dominant kernel's roofline: the CK kernel (k_ck_mx on the FP32
+        pipe, k_ck on the FP64 pipe); achieved = algorithmic flops of its
+        launches over all parts / their summed CUDA-event time."""
+        flops = sum(ck_flops_per_element(f["w"]["kind"], f["w"]["deg"]) * f["sol"].N for f in form["parts"])
+        ck_ms = sum(f["phases"]["ck"] for f in form["parts"])
+        ach = flops / (ck_ms / 1e3) / 1e12
+        peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+        tr = [ck_traffic(f["name"], mixed, f["sol"].N) for f in form["parts"]]
+        probe = probes["fp32" if mixed else "fp64"]
+        return {"kernel": "k_ck_mx" if mixed else "k_ck", "dominant_phase": max(form["phases"], key=form["phases"].get),
+                "bound": "alu", "pipe": "fp32" if mixed else "fp64", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": sum(tr) / len(tr) if all(t is not None for t in tr) else None,
+                "traffic_per_part": dict(zip([f["name"] for f in form["parts"]], tr)),
+                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if mixed
+                                else "nominal GB300 FP64 rate (recipe table)"),
+                "peak_measured_fma_probe": probe, "frac_of_measured_probe": ach / probe if probe else None,
+                "algorithmic_flops_per_launch": flops / len(form["parts"]),
+                "launch_ms": ck_ms / len(form["parts"]),
+                "per_part": {f["name"]: {"frac": ck_flops_per_element(f["w"]["kind"], f["w"]["deg"]) * f["sol"].N
+                                         / (f["phases"]["ck"] / 1e3) / 1e12 / peak, "launch_ms": f["phases"]["ck"]}
+                             for f in form["parts"]}}
+
+    config = {"workload": desc_of(args.workload), "parts": {p: WORKLOADS[p]["desc"] for p in parts_of(args.workload)},
+              "cfl": 0.1, "l2": "flushed between timed steps (256 MB write)",
+              "timing": "one CUDA-graph replay per step and part, CUDA events on the solver's stream, summed over parts",
+              "parallelism": "replicas" if world > 1 else "single GPU"}
 
     if args.form != "all":
         mixed = args.form != "fp64"
         net, info = train_indicator(L, stream, args.tau) if args.form == "learned" else (None, None)
-        f = timed_form(mixed, ClockSampler(local), net=net)
-        w, sol = f["w"], f["sol"]
-        flops = ck_flops_per_element(w["kind"], w["deg"]) * sol.N
-        ck_ms = f["phases"]["ck"]
-        ach = flops / (ck_ms / 1e3) / 1e12
-        peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
-        e2e = e2e_of(sol, f["Q"], w["cfl"])
+        f = timed_form(args.workload, mixed, ClockSampler(local), net=net)
+        e2e = e2e_of(f)
         if world > 1:
             dist.barrier()
         if rank == 0:
             out = {"metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                    "warmup": args.warmup, "ms_per_step": f["total_ms"] / args.steps, "higher_is_better": True,
                    "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
-                   "data": "synthetic",
-                   "config": {"workload": w["desc"], "elements": sol.N, "degree": w["deg"], "form": args.form,
-                              "cfl": w["cfl"], "l2": "flushed between timed steps (256 MB write)",
-                              "timing": "one CUDA-graph replay per step, CUDA events on the solver's stream",
-                              "parallelism": "replicas" if world > 1 else "single GPU"},
-                   "roofline": {"kernel": "k_ck_mx" if mixed else "k_ck", "bound": "alu",
-                                "pipe": "fp32" if mixed else "fp64", "achieved": ach, "peak": peak,
-                                "unit": "TFLOP/s", "frac": ach / peak,
-                                "traffic": (CK_MX_TRAFFIC_BYTES if mixed else CK_TRAFFIC_BYTES)
-                                if args.workload == "rarefy" else None,
-                                "algorithmic_flops_per_launch": flops, "launch_ms": ck_ms},
-                   "e2e": e2e, "gpu_launches": args.steps * L.lxw_step_launches(sol), "clocks": f["clocks"],
-                   "phases_ms": f["phases"], "autotune": f["tune"], "learned_indicator": info}
+                   "data": "synthetic", "config": dict(config, elements=sum(x["sol"].N for x in f["parts"]),
+                                                       dof_per_step=f["dof"], form=args.form),
+                   "roofline": roofline_of(f, mixed), "e2e": e2e, "gpu_launches": args.steps * f["launches"],
+                   "clocks": f["clocks"], "phases_ms": f["phases"],
+                   "autotune": {x["name"]: x["tune"] for x in f["parts"]}, "learned_indicator": info}
             if world == 1 and not args.no_cpu_baseline:
                 out["cpu_baseline"], _, _ = cpu_baseline(args.workload)
             print(json.dumps(out))
@@ -682,54 +767,59 @@ def main():
             dist.destroy_process_group()
         return
 
-    fp64 = timed_form(False)
-    plain_mx = timed_form(True)
+    fp64 = timed_form(args.workload, False)
+    plain_mx = timed_form(args.workload, True)
     t_train = time.perf_counter()
     net, train_info = train_indicator(L, stream, args.tau)
     t_train = time.perf_counter() - t_train
-    mx = timed_form(True, ClockSampler(local), net=net)
-    w, sol, dof = mx["w"], mx["sol"], mx["dof"]
-    # one more (untimed) step with diagnostics: how often the FP64 paths ran and the gate skipped
-    dmx = L.lxw_step(sol, mx["Q"], 0.0, w["cfl"], diag=True)
-    L.lxw_step(fp64["sol"], fp64["Q"], 0.0, w["cfl"])
-    L.lxw_step(plain_mx["sol"], plain_mx["Q"], 0.0, w["cfl"])
+    mx = timed_form(args.workload, True, ClockSampler(local), net=net)
+    # one more (untimed) step per part with diagnostics: how often the FP64 paths ran and the gate skipped;
+    # the other forms take the same step so that all three compare at the same time
+    diags = {}
+    for a, b, c in zip(mx["parts"], fp64["parts"], plain_mx["parts"]):
+        diags[a["name"]] = L.lxw_step(a["sol"], a["Q"], 0.0, a["w"]["cfl"], diag=True)
+        L.lxw_step(b["sol"], b["Q"], 0.0, b["w"]["cfl"])
+        L.lxw_step(c["sol"], c["Q"], 0.0, c["w"]["cfl"])
 
-    # distance of the mixed forms from the FP64 form after the same steps (density, relative L1)
-    rho_f = fp64["Q"][:, 0, 0]
+    # distance of the mixed forms from the FP64 form after the same steps (density, relative L1), per part
     def l1_rel(form):
-        r = L.to_q64(form["sol"], form["Q"])[:, 0, 0]
-        return (torch.abs(r - rho_f).sum() / torch.abs(rho_f).sum()).item()
+        out = {}
+        for f, g in zip(form["parts"], fp64["parts"]):
+            r = L.to_q64(f["sol"], f["Q"])[:, 0, 0]
+            rf = g["Q"][:, 0, 0]
+            out[f["name"]] = (torch.abs(r - rf).sum() / torch.abs(rf).sum()).item()
+        return out
     dist_learned, dist_plain_mx = l1_rel(mx), l1_rel(plain_mx)
     # "at equal L1 error": the three forms against the exact smooth solution
     acc = {"fp64": smooth_l1_error(L, stream, False), "mixed": smooth_l1_error(L, stream, True),
            "mixed_learned": smooth_l1_error(L, stream, True, net=net, tau=args.tau)}
-    disc = (discretization_check(L, stream, args.workload, net, args.tau, min(args.steps, 100))
-            if args.workload != "smooth" else None)
     acc["ratio_l1_mixed_learned_vs_fp64"] = acc["mixed_learned"]["l1"] / acc["fp64"]["l1"]
     acc["ratio_l2_mixed_learned_vs_fp64"] = acc["mixed_learned"]["l2"] / acc["fp64"]["l2"]
     acc["config"] = (WORKLOADS["smooth"]["desc"] + ", CFL 0.1, to t = 0.1; l1: cell-average density, "
                      "l2: DG density (all modes) against the projected exact solution")
+    disc = {p: discretization_check(L, stream, p, net, args.tau, min(args.steps, 100))
+            for p in parts_of(args.workload) if p != "smooth"}
+    if disc:
+        disc["ratio_max"] = max(d["ratio"] for d in disc.values())
 
-    flops = ck_flops_per_element(w["kind"], w["deg"]) * sol.N
-    ck_ms = mx["phases"]["ck"]
-    achieved = flops / (ck_ms / 1e3) / 1e12
-    dom = max(mx["phases"], key=mx["phases"].get)
-    roofline = {"kernel": "k_ck_mx", "dominant_phase": dom, "bound": "alu", "pipe": "fp32",
-                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": CK_MX_TRAFFIC_BYTES if args.workload == "rarefy" else None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                "peak_measured_fma_probe": probes["fp32"],
-                "frac_of_measured_probe": achieved / probes["fp32"] if probes["fp32"] else None,
-                "algorithmic_flops_per_launch": flops, "launch_ms": ck_ms}
-    f64_ck = fp64["phases"]["ck"]
-    f64_ach = flops / (f64_ck / 1e3) / 1e12
+    roofline = roofline_of(mx, True)
     plain = {"value": fp64["value"], "ms_per_step": fp64["total_ms"] / args.steps, "phases_ms": fp64["phases"],
-             "roofline": {"kernel": "k_ck", "bound": "alu", "pipe": "fp64", "achieved": f64_ach,
-                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": f64_ach / FP64_PEAK_TFLOPS,
-                          "traffic": CK_TRAFFIC_BYTES, "peak_measured_fma_probe": probes["fp64"]}}
+             "roofline": roofline_of(fp64, False)}
+    e2e = e2e_of(mx)
 
-    e2e = e2e_of(sol, mx["Q"], w["cfl"])
+    # the 100,352-triangle rarefaction beside the headline (same network)
+    secondary = None
+    if not args.no_secondary and args.workload != "rarefy":
+        s_mx = timed_form("rarefy", True, net=net)
+        s_pm = timed_form("rarefy", True)
+        s_64 = timed_form("rarefy", False)
+        secondary = {"workload": WORKLOADS["rarefy"]["desc"], "value": s_mx["value"],
+                     "ms_per_step": s_mx["total_ms"] / args.steps, "phases_ms": s_mx["phases"],
+                     "roofline": roofline_of(s_mx, True),
+                     "plain_mixed": {"value": s_pm["value"], "ms_per_step": s_pm["total_ms"] / args.steps},
+                     "plain_fp64": {"value": s_64["value"], "ms_per_step": s_64["total_ms"] / args.steps},
+                     "speedup_vs_plain_fp64": s_mx["value"] / s_64["value"],
+                     "gain_vs_plain_mixed": s_mx["value"] / s_pm["value"]}
     if world > 1:
         dist.barrier()
 
@@ -740,31 +830,33 @@ def main():
     out = {"metric": METRIC, "value": mx["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": mx["total_ms"] / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-           "config": {"workload": w["desc"], "elements": sol.N, "degree": w["deg"], "dof_per_step": dof,
-                      "form": "mixed + learned: FP32 bulk, FP64 averages/update/limiter solves, "
-                              f"MLP-gated shock limiter (BF16 tensor-core inference, tau {args.tau})",
-                      "cfl": w["cfl"], "l2": "flushed between timed steps (256 MB write)",
-                      "timing": "one CUDA-graph replay per step, CUDA events on the solver's stream",
-                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "config": dict(config, elements=sum(f["sol"].N for f in mx["parts"]), dof_per_step=mx["dof"],
+                          form="mixed + learned: FP32 bulk, FP64 averages/update/limiter solves, "
+                               f"MLP-gated shock limiter (BF16 tensor-core inference, tau {args.tau})"),
            "roofline": roofline,
            "e2e": e2e,
-           "gpu_launches": args.steps * L.lxw_step_launches(sol),
+           "gpu_launches": args.steps * mx["launches"],
            "clocks": mx["clocks"],
            "phases_ms": mx["phases"],
+           "per_part": {f["name"]: {"ms_per_step": f["total_ms"] / args.steps, "phases_ms": f["phases"],
+                                    "value": f["dof"] * args.steps / (f["total_ms"] / 1e3), "elements": f["sol"].N}
+                        for f in mx["parts"]},
            "plain_fp64": plain,
            "speedup_vs_plain_fp64": mx["value"] / fp64["value"],
-           "autotune": mx["tune"],
+           "autotune": {f["name"]: f["tune"] for f in mx["parts"]},
            "plain_mixed": {"value": plain_mx["value"], "ms_per_step": plain_mx["total_ms"] / args.steps,
                            "phases_ms": plain_mx["phases"], "l1_rel_density_vs_fp64": dist_plain_mx,
-                           "autotune": plain_mx["tune"]},
+                           "autotune": {f["name"]: f["tune"] for f in plain_mx["parts"]}},
            "learned_indicator": dict(train_info, train_s=t_train, tau=args.tau,
-                                     skipped_cells_last_step=dmx["n_mlp_skip"], of=sol.N,
+                                     skipped_cells_last_step={k: d["n_mlp_skip"] for k, d in diags.items()},
                                      gain_vs_plain_mixed=mx["value"] / plain_mx["value"]),
-           "mixed_fp64_path_cells": {"moment": dmx["n_fp64_moment"], "flux_limiter": dmx["n_fp64_edge"],
-                                     "of": sol.N},
+           "mixed_fp64_path_cells": {k: {"moment": d["n_fp64_moment"], "flux_limiter": d["n_fp64_edge"]}
+                                     for k, d in diags.items()},
+           "positivity_last_step": {k: {"min_rho": d["min_rho"], "min_p": d["min_p"]} for k, d in diags.items()},
            "l1_rel_density_vs_fp64": dist_learned,
            "smooth_l1_error": acc,
-           "discretization_check": disc}
+           "discretization_check": disc,
+           "secondary": secondary}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], _, _ = cpu_baseline(args.workload)
     print(json.dumps(out))
