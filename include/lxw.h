@@ -93,7 +93,15 @@ typedef struct {
                                the paper's convergence test (Sec. 4, Table 1)
                                drops to second order; the local speed keeps
                                third order                                     */
-  int reserved[5];
+  int ck_order;             /* order in time of the Cauchy-Kovalevskaya flux: 0 or
+                               3 (default) = F + dt/2 F_t + dt^2/6 F_tt (Eq.
+                               taylor3-flux); 4 adds dt^3/24 F_ttt, the next
+                               term of the same series (F_ttt = F'''(q)(q_t)^3 +
+                               3 F''(q)(q_t, q_tt) + F'(q) q_ttt, q_ttt = -div
+                               of the projected F_tt), so that P3 elements are
+                               fourth order in time too (the higher-order
+                               direction of the conclusions)                   */
+  int reserved[4];
 } lxw_options;
 
 /* Per-step diagnostics (filled when a non-NULL pointer is passed). */

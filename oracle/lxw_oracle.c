@@ -34,6 +34,10 @@
  *    falls to second order; the local speed gives third order.  The literal
  *    global reading stays available (orc_solver_set_llf_global).
  *  - dt = cfl * min_i(2|T_i|/P_i) / s.
+ *  - optional fourth order in time (ck_order 4): the next term of the Taylor
+ *    series of the time-averaged flux, dt^3/24 F_ttt with F_ttt =
+ *    F'''(q)(q_t,q_t,q_t) + 3 F''(q)(q_t,q_tt) + F'(q) q_ttt and
+ *    q_ttt = -div F_tt^h of the projected F_tt (as for q_t and q_tt).
  *  - the shock-capturing limiter of Sec. 4.1 (cited, not printed) is read
  *    as: for w in (rho,u,v,p), M = max(w_i + alpha, max_j w_j),
  *    m = min(w_i - alpha, min_j w_j) over face neighbours j,
@@ -286,6 +290,51 @@ void orc_flux_d2(double g, const double* q, const double* w, double* F2, double*
   G2[3] = ddp * v + 2.0 * (e + dp) * dv + (E + p) * ddv;
 }
 
+/* Third directional derivative d^3/de^3 F(q + e w) at e = 0 (the third
+ * derivative of the flux along w, a term of the fourth-order time average).
+ * Every quantity along q + e w is kept as its Taylor coefficients in e: rho,
+ * m, n, E are linear; rho u = m gives u_k = (m_k - w_rho u_{k-1}) / rho
+ * (likewise v); K = (m u + n v)/2 and p = (g-1)(E - K) follow by series
+ * products; each flux component is a product of such series, and its third
+ * derivative is 3! times the coefficient of e^3. */
+static double ser_prod(const double* A, const double* B, int k) {
+  double a = 0.0;
+  for (int i = 0; i <= k; ++i) a += A[i] * B[k - i];
+  return a;
+}
+void orc_flux_d3(double g, const double* q, const double* w, double* F3, double* G3) {
+  double M[4] = {q[1], w[1], 0.0, 0.0}, Nn[4] = {q[2], w[2], 0.0, 0.0}, En[4] = {q[3], w[3], 0.0, 0.0};
+  double u[4], v[4], p[4], H[4];
+  for (int k = 0; k < 4; ++k) {
+    u[k] = (M[k] - (k > 0 ? w[0] * u[k - 1] : 0.0)) / q[0];
+    v[k] = (Nn[k] - (k > 0 ? w[0] * v[k - 1] : 0.0)) / q[0];
+  }
+  for (int k = 0; k < 4; ++k) {
+    double K = 0.5 * (ser_prod(M, u, k) + ser_prod(Nn, v, k));
+    p[k] = (g - 1.0) * (En[k] - K);
+    H[k] = En[k] + p[k];
+  }
+  F3[0] = 0.0;
+  F3[1] = 6.0 * (ser_prod(M, u, 3) + p[3]);
+  F3[2] = 6.0 * ser_prod(M, v, 3);
+  F3[3] = 6.0 * ser_prod(H, u, 3);
+  G3[0] = 0.0;
+  G3[1] = 6.0 * ser_prod(Nn, u, 3);
+  G3[2] = 6.0 * (ser_prod(Nn, v, 3) + p[3]);
+  G3[3] = 6.0 * ser_prod(H, v, 3);
+}
+
+/* Mixed second derivative of the flux in the directions a and b, from the
+ * second directional derivative by polarisation:
+ * (d2 along a+b  -  d2 along a-b) / 4. */
+void orc_flux_d11(double g, const double* q, const double* a, const double* b, double* F2, double* G2) {
+  double s[4], d[4], Fs[4], Gs[4], Fd[4], Gd[4];
+  for (int v = 0; v < NV; ++v) { s[v] = a[v] + b[v]; d[v] = a[v] - b[v]; }
+  orc_flux_d2(g, q, s, Fs, Gs);
+  orc_flux_d2(g, q, d, Fd, Gd);
+  for (int v = 0; v < NV; ++v) { F2[v] = 0.25 * (Fs[v] - Fd[v]); G2[v] = 0.25 * (Gs[v] - Gd[v]); }
+}
+
 static double wave_speed_point(double g, const double* q) {
   double u = q[1] / q[0], v = q[2] / q[0];
   double p = pressure(g, q);
@@ -519,6 +568,7 @@ struct orc_solver {
   int shock_limiter;
   int moment_exact;                         /* Step 2 by the exact root instead of the secant */
   int llf_global;                           /* Eq. LLF point flux with the global s instead of the local speed */
+  int ck_order;                             /* 3 (Eq. taylor3-flux) or 4 (one more term of the series) */
   double qx[MAXQ], qy[MAXQ], qw[MAXQ];
   double gs[MAXMQ], gw[MAXMQ];
   /* points: 0..NQ-1 interior, then edge k point p at NQ + k*MQ + p */
@@ -526,7 +576,7 @@ struct orc_solver {
   double phi[MAXPTS][MAXML], dxi[MAXPTS][MAXML], deta[MAXPTS][MAXML];
   double jx[MAXPJ], jy[MAXPJ], jw[MAXPJ], jphi[MAXPJ][MAXML];
   /* per-step work arrays */
-  double *V, *tq, *tqt, *tqtt, *tF, *tG;    /* V[N][ML][4]; traces [N][E][MQ][4] */
+  double *V, *tq, *tqt, *tqtt, *tqttt, *tF, *tG;   /* V[N][ML][4]; traces [N][E][MQ][4] */
   double *fstar, *flxw, *flxf;              /* per edge: [ne][MQ][4], [ne][4], [ne][4] */
   double *prop;                             /* [N][E] Lambda proposals */
   double last_dt;
@@ -537,7 +587,7 @@ orc_solver* orc_solver_new(const orc_mesh* m, int deg, double gamma) {
   if (deg < 1 || deg > 3) return NULL;
   orc_solver* s = calloc(1, sizeof(orc_solver));
   s->m = m; s->deg = deg; s->E = m->E; s->gamma = gamma;
-  s->eps0 = 1e-12; s->alpha0 = 500.0; s->shock_limiter = 1;
+  s->eps0 = 1e-12; s->alpha0 = 500.0; s->shock_limiter = 1; s->ck_order = 3;
   s->ML = orc_num_modes(m->kind, deg);
   int n = deg + 1;
   s->NQ = orc_interior_rule(m->kind, n, s->qx, s->qy, s->qw);
@@ -573,6 +623,7 @@ orc_solver* orc_solver_new(const orc_mesh* m, int deg, double gamma) {
   s->tq = malloc(sizeof(double) * N * E * MQ * NV);
   s->tqt = malloc(sizeof(double) * N * E * MQ * NV);
   s->tqtt = malloc(sizeof(double) * N * E * MQ * NV);
+  s->tqttt = malloc(sizeof(double) * N * E * MQ * NV);
   s->tF = malloc(sizeof(double) * N * E * MQ * NV);
   s->tG = malloc(sizeof(double) * N * E * MQ * NV);
   s->fstar = malloc(sizeof(double) * ne * MQ * NV);
@@ -584,7 +635,7 @@ orc_solver* orc_solver_new(const orc_mesh* m, int deg, double gamma) {
 
 void orc_solver_free(orc_solver* s) {
   if (!s) return;
-  free(s->V); free(s->tq); free(s->tqt); free(s->tqtt); free(s->tF); free(s->tG);
+  free(s->V); free(s->tq); free(s->tqt); free(s->tqtt); free(s->tqttt); free(s->tF); free(s->tG);
   free(s->fstar); free(s->flxw); free(s->flxf); free(s->prop);
   free(s);
 }
@@ -601,6 +652,16 @@ void orc_solver_set_moment_exact(orc_solver* s, int flag) { s->moment_exact = fl
  * (the literal reading), flag 0 (default) the local Lax-Friedrichs speed of
  * the two traces (see the readings at the top of this file). */
 void orc_solver_set_llf_global(orc_solver* s, int flag) { s->llf_global = flag; }
+
+/* Order in time of the CK flux: 3 is Eq. taylor3-flux (F + dt/2 F_t +
+ * dt^2/6 F_tt); 4 adds dt^3/24 F_ttt, the next term of the same series, for
+ * P3 elements (the higher-order direction the conclusions name).  Returns 1
+ * for an order other than 3 or 4. */
+int orc_solver_set_ck_order(orc_solver* s, int order) {
+  if (order != 3 && order != 4) return 1;
+  s->ck_order = order;
+  return 0;
+}
 
 /* the state of inflow boundaries from primitive values (rho, u, v, p) */
 void orc_solver_set_inflow(orc_solver* s, const double* prim) {
@@ -805,7 +866,7 @@ double orc_wave_speed(const orc_solver* s, const double* Q) {
 /* ------------------------------------------------------------------ */
 static void ck_element(const orc_solver* s, const double* Qi, int i, double dt,
                        double (*q)[4], double (*qt)[4], double (*qtt)[4],
-                       double (*FT)[4], double (*GT)[4], double (*V)[4]) {
+                       double (*FT)[4], double (*GT)[4], double (*V)[4], double (*qttt)[4]) {
   const orc_mesh* m = s->m;
   int ML = s->ML, NQ = s->NQ, NPT = s->NPT;
   double g = s->gamma;
@@ -853,7 +914,8 @@ static void ck_element(const orc_solver* s, const double* Qi, int i, double dt,
       }
       Fth[l][v] = a; Gth[l][v] = b;
     }
-  /* q_tt = -div F_t^h and F_tt (Eq. fluxderivs-b), then F_T */
+  /* q_tt = -div F_t^h and F_tt (Eq. fluxderivs-b) at every point */
+  double Ftt[MAXPTS][4], Gtt[MAXPTS][4];
   for (int p = 0; p < NPT; ++p) {
     for (int v = 0; v < NV; ++v) {
       double d = 0.0;
@@ -863,10 +925,44 @@ static void ck_element(const orc_solver* s, const double* Qi, int i, double dt,
     double F2[4], G2[4], F1[4], G1[4];
     orc_flux_d2(g, q[p], qt[p], F2, G2);
     orc_flux_d1(g, q[p], qtt[p], F1, G1);
+    for (int v = 0; v < NV; ++v) { Ftt[p][v] = F2[v] + F1[v]; Gtt[p][v] = G2[v] + G1[v]; }
+  }
+  /* F_T = F + dt/2 F_t + dt^2/6 F_tt (Eq. taylor3-flux) */
+  for (int p = 0; p < NPT; ++p)
     for (int v = 0; v < NV; ++v) {
-      double Ftt = F2[v] + F1[v], Gtt = G2[v] + G1[v];
-      FT[p][v] = F[p][v] + dt / 2.0 * Ft[p][v] + dt * dt / 6.0 * Ftt;
-      GT[p][v] = G[p][v] + dt / 2.0 * Gt[p][v] + dt * dt / 6.0 * Gtt;
+      FT[p][v] = F[p][v] + dt / 2.0 * Ft[p][v] + dt * dt / 6.0 * Ftt[p][v];
+      GT[p][v] = G[p][v] + dt / 2.0 * Gt[p][v] + dt * dt / 6.0 * Gtt[p][v];
+    }
+  /* Fourth order in time (the next term of the same Taylor series of the
+   * time-averaged flux): q_ttt = -div F_tt^h, F_ttt = F'''(q)(q_t,q_t,q_t)
+   * + 3 F''(q)(q_t, q_tt) + F'(q) q_ttt, F_T += dt^3/24 F_ttt */
+  for (int p = 0; p < NPT; ++p)
+    for (int v = 0; v < NV; ++v) qttt[p][v] = 0.0;
+  if (s->ck_order == 4) {
+    double Ftth[MAXML][4], Gtth[MAXML][4];
+    for (int l = 0; l < ML; ++l)
+      for (int v = 0; v < NV; ++v) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < NQ; ++k) {
+          a += s->qw[k] * Ftt[k][v] * s->phi[k][l];
+          b += s->qw[k] * Gtt[k][v] * s->phi[k][l];
+        }
+        Ftth[l][v] = a; Gtth[l][v] = b;
+      }
+    for (int p = 0; p < NPT; ++p) {
+      for (int v = 0; v < NV; ++v) {
+        double d = 0.0;
+        for (int l = 0; l < ML; ++l) d += Ftth[l][v] * bx[p][l] + Gtth[l][v] * by[p][l];
+        qttt[p][v] = -d;
+      }
+      double F3[4], G3[4], Fm[4], Gm[4], F1[4], G1[4];
+      orc_flux_d3(g, q[p], qt[p], F3, G3);
+      orc_flux_d11(g, q[p], qt[p], qtt[p], Fm, Gm);
+      orc_flux_d1(g, q[p], qttt[p], F1, G1);
+      for (int v = 0; v < NV; ++v) {
+        FT[p][v] += dt * dt * dt / 24.0 * (F3[v] + 3.0 * Fm[v] + F1[v]);
+        GT[p][v] += dt * dt * dt / 24.0 * (G3[v] + 3.0 * Gm[v] + G1[v]);
+      }
     }
   }
   /* Step 3: interior integral of Eq. EulerStepExactGalerkin */
@@ -880,8 +976,8 @@ static void ck_element(const orc_solver* s, const double* Qi, int i, double dt,
 
 void orc_ck_element(const orc_solver* s, const double* Q, int i, double dt, double* q,
                     double* qt, double* qtt, double* FT, double* GT, double* V) {
-  double a[MAXPTS][4], b[MAXPTS][4], c[MAXPTS][4], d[MAXPTS][4], e[MAXPTS][4], f[MAXML][4];
-  ck_element(s, Q + (size_t)i * NV * s->ML, i, dt, a, b, c, d, e, f);
+  double a[MAXPTS][4], b[MAXPTS][4], c[MAXPTS][4], d[MAXPTS][4], e[MAXPTS][4], f[MAXML][4], h[MAXPTS][4];
+  ck_element(s, Q + (size_t)i * NV * s->ML, i, dt, a, b, c, d, e, f, h);
   for (int p = 0; p < s->NPT; ++p)
     for (int v = 0; v < NV; ++v) {
       if (q) q[p * 4 + v] = a[p][v];
@@ -915,7 +1011,7 @@ static void boundary_state(int bc, const double* nh, const double* qin, double* 
 
 /* F_T from q, q_t, q_tt at one point (used for boundary states) */
 static void ft_from_derivs(double g, double dt, const double* q, const double* qt, const double* qtt,
-                           double* FT, double* GT) {
+                           const double* qttt, double* FT, double* GT) {
   double F[4], G[4], F1[4], G1[4], F2[4], G2[4], F3[4], G3[4];
   orc_flux(g, q, F, G);
   orc_flux_d1(g, q, qt, F1, G1);
@@ -924,6 +1020,16 @@ static void ft_from_derivs(double g, double dt, const double* q, const double* q
   for (int v = 0; v < NV; ++v) {
     FT[v] = F[v] + dt / 2.0 * F1[v] + dt * dt / 6.0 * (F2[v] + F3[v]);
     GT[v] = G[v] + dt / 2.0 * G1[v] + dt * dt / 6.0 * (G2[v] + G3[v]);
+  }
+  if (qttt) {   /* fourth order: + dt^3/24 (F'''(q_t)^3 + 3 F''(q_t, q_tt) + F'(q_ttt)) */
+    double A[4], B[4], C2[4], D2[4], E1[4], G1b[4];
+    orc_flux_d3(g, q, qt, A, B);
+    orc_flux_d11(g, q, qt, qtt, C2, D2);
+    orc_flux_d1(g, q, qttt, E1, G1b);
+    for (int v = 0; v < NV; ++v) {
+      FT[v] += dt * dt * dt / 24.0 * (A[v] + 3.0 * C2[v] + E1[v]);
+      GT[v] += dt * dt * dt / 24.0 * (B[v] + 3.0 * D2[v] + G1b[v]);
+    }
   }
 }
 
@@ -1131,9 +1237,9 @@ int orc_step(orc_solver* s, double* Q, double dt_in, double cfl, double* diag,
   /* Step 2 (element loop): time-averaged fluxes, volume integrals, traces */
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < N; ++i) {
-    double q[MAXPTS][4], qt[MAXPTS][4], qtt[MAXPTS][4], FT[MAXPTS][4], GT[MAXPTS][4];
+    double q[MAXPTS][4], qt[MAXPTS][4], qtt[MAXPTS][4], FT[MAXPTS][4], GT[MAXPTS][4], qttt[MAXPTS][4];
     double V[MAXML][4];
-    ck_element(s, Q + (size_t)i * NV * ML, i, dt, q, qt, qtt, FT, GT, V);
+    ck_element(s, Q + (size_t)i * NV * ML, i, dt, q, qt, qtt, FT, GT, V, qttt);
     for (int l = 0; l < ML; ++l)
       for (int v = 0; v < NV; ++v) s->V[((size_t)i * ML + l) * NV + v] = V[l][v];
     for (int k = 0; k < E; ++k)
@@ -1142,6 +1248,7 @@ int orc_step(orc_solver* s, double* Q, double dt_in, double cfl, double* diag,
         int src = NQ + k * MQ + p;
         for (int v = 0; v < NV; ++v) {
           s->tq[t + v] = q[src][v]; s->tqt[t + v] = qt[src][v]; s->tqtt[t + v] = qtt[src][v];
+          s->tqttt[t + v] = qttt[src][v];
           s->tF[t + v] = FT[src][v]; s->tG[t + v] = GT[src][v];
         }
       }
@@ -1165,11 +1272,12 @@ int orc_step(orc_solver* s, double* Q, double dt_in, double cfl, double* diag,
         size_t tj = (((size_t)j * E + kj) * MQ + (MQ - 1 - p)) * NV;
         for (int v = 0; v < NV; ++v) { qp[v] = s->tq[tj + v]; Fp[v] = s->tF[tj + v]; Gp[v] = s->tG[tj + v]; }
       } else {
-        double qtp[4], qttp[4];
+        double qtp[4], qttp[4], qtttp[4];
         boundary_state(bc, nh, qm, qp, s->qinf, 0);
         boundary_state(bc, nh, s->tqt + ti, qtp, s->qinf, 1);
         boundary_state(bc, nh, s->tqtt + ti, qttp, s->qinf, 1);
-        ft_from_derivs(g, dt, qp, qtp, qttp, Fp, Gp);
+        boundary_state(bc, nh, s->tqttt + ti, qtttp, s->qinf, 1);
+        ft_from_derivs(g, dt, qp, qtp, qttp, s->ck_order == 4 ? qtttp : NULL, Fp, Gp);
       }
       double* fs = s->fstar + ((size_t)e * MQ + p) * NV;
       /* dissipation speed: local Lax-Friedrichs speed of the two traces,

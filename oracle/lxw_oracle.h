@@ -56,6 +56,10 @@ int orc_interior_rule(int kind, int n, double* xi, double* eta, double* w);
 void orc_flux(double gamma, const double* q, double* F, double* G);
 void orc_flux_d1(double gamma, const double* q, const double* w, double* F1, double* G1);
 void orc_flux_d2(double gamma, const double* q, const double* w, double* F2, double* G2);
+/* third directional derivative of (F, G) along w (fourth-order CK term) */
+void orc_flux_d3(double gamma, const double* q, const double* w, double* F3, double* G3);
+/* mixed second derivative of (F, G) in the directions a and b */
+void orc_flux_d11(double gamma, const double* q, const double* a, const double* b, double* F2, double* G2);
 
 /* Meshes. bc[4] = (left, right, bottom, top). Triangles must be CCW;
  * ebc[nt][3] gives the boundary code of each triangle-local edge k (from
@@ -78,6 +82,8 @@ void orc_solver_set_moment_exact(orc_solver* s, int flag);
 /* flag 1: the high-order point flux (Eq. LLF) dissipates with the global s
  * instead of the local speed of its two traces (default 0) */
 void orc_solver_set_llf_global(orc_solver* s, int flag);
+/* CK time order: 3 (default, Eq. taylor3-flux) or 4; returns 1 otherwise */
+int orc_solver_set_ck_order(orc_solver* s, int order);
 /* state of the inflow boundaries, primitive (rho, u, v, p) */
 void orc_solver_set_inflow(orc_solver* s, const double* prim);
 /* Cartesian mesh without the cells of mask == 0 (mask[ny][nx], row order);

@@ -60,6 +60,9 @@ def lib():
         L.orc_solver_set_params.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int]
         L.orc_solver_set_moment_exact.argtypes = [C.c_void_p, C.c_int]
         L.orc_solver_set_llf_global.argtypes = [C.c_void_p, C.c_int]
+        L.orc_solver_set_ck_order.argtypes = [C.c_void_p, C.c_int]
+        L.orc_flux_d3.argtypes = [C.c_double, _dp, _dp, _dp, _dp]
+        L.orc_flux_d11.argtypes = [C.c_double, _dp, _dp, _dp, _dp, _dp]
         for f in (L.orc_solver_num_modes, L.orc_solver_num_points, L.orc_projection_num_points):
             f.argtypes = [C.c_void_p]
         L.orc_projection_points.argtypes = [C.c_void_p, _dp]
@@ -129,6 +132,21 @@ def flux_d2(gamma, q, w):
     q = np.ascontiguousarray(q, dtype=np.float64); w = np.ascontiguousarray(w, dtype=np.float64)
     F = np.zeros(4); G = np.zeros(4)
     lib().orc_flux_d2(gamma, _d(q), _d(w), _d(F), _d(G))
+    return F, G
+
+
+def flux_d3(gamma, q, w):
+    q = np.ascontiguousarray(q, dtype=np.float64); w = np.ascontiguousarray(w, dtype=np.float64)
+    F = np.zeros(4); G = np.zeros(4)
+    lib().orc_flux_d3(gamma, _d(q), _d(w), _d(F), _d(G))
+    return F, G
+
+
+def flux_d11(gamma, q, a, b):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64); b = np.ascontiguousarray(b, dtype=np.float64)
+    F = np.zeros(4); G = np.zeros(4)
+    lib().orc_flux_d11(gamma, _d(q), _d(a), _d(b), _d(F), _d(G))
     return F, G
 
 
@@ -205,7 +223,7 @@ class Mesh:
 
 class Solver:
     def __init__(self, mesh, deg, gamma=1.4, eps0=1e-12, alpha0=500.0, shock_limiter=True, moment_exact=False,
-                 llf_global=False):
+                 llf_global=False, ck_order=3):
         self.mesh = mesh  # keep alive
         self.ptr = lib().orc_solver_new(mesh.ptr, deg, gamma)
         if not self.ptr:
@@ -213,6 +231,8 @@ class Solver:
         lib().orc_solver_set_params(self.ptr, eps0, alpha0, int(bool(shock_limiter)))
         lib().orc_solver_set_moment_exact(self.ptr, int(bool(moment_exact)))
         lib().orc_solver_set_llf_global(self.ptr, int(bool(llf_global)))
+        if lib().orc_solver_set_ck_order(self.ptr, int(ck_order)):
+            raise ValueError("ck_order must be 3 or 4")
         self.gamma = gamma
         self.N, self.E = mesh.N, mesh.E
         self.ML = lib().orc_solver_num_modes(self.ptr)

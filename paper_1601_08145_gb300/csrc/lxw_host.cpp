@@ -318,6 +318,7 @@ lxw_status lxw_options_default(lxw_options* opt) {
   opt->shock_limiter = 1;
   opt->precision = LXW_PREC_FP64;
   opt->block_threads = 128;
+  opt->ck_order = 3;
   return LXW_OK;
 }
 
@@ -441,6 +442,9 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     return fail(LXW_ERR_ARG, "lxw_solver_create: moment_exact must be 0 or 1");
   if (opt.llf_global != 0 && opt.llf_global != 1)
     return fail(LXW_ERR_ARG, "lxw_solver_create: llf_global must be 0 or 1");
+  if (opt.ck_order == 0) opt.ck_order = 3;
+  if (opt.ck_order != 3 && opt.ck_order != 4)
+    return fail(LXW_ERR_ARG, "lxw_solver_create: ck_order must be 3 or 4");
   lxw_solver* s = new (std::nothrow) lxw_solver;
   if (!s) return fail(LXW_ERR_NOMEM, "lxw_solver_create: out of memory");
   s->kind = mesh->kind; s->deg = degree; s->N = mesh->N; s->E = mesh->E; s->opt = opt;
@@ -705,6 +709,7 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   a.shock_limiter = s->opt.shock_limiter; a.want_diag = want_diag; a.theta_cell = tc; a.theta_edge = te;
   a.moment_exact = s->opt.moment_exact;
   a.llf_global = s->opt.llf_global;
+  a.ck_order = s->opt.ck_order;
   a.gamma_f = (float)a.gamma; a.eps0_f = (float)a.eps0; a.alpha0_f = (float)a.alpha0;
   a.grid = s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm * s->sms : 0;   // persistent CTAs, or one per tile
   a.sms = s->sms;

@@ -143,6 +143,7 @@ struct StepArgs {
   int shock_limiter;
   int moment_exact;                  // moment limiter: exact root instead of the secant
   int llf_global;                    // LLF point flux: global s instead of the local speed of the traces
+  int ck_order;                      // CK flux order in time: 3 (Eq. taylor3-flux) or 4
   int want_diag;
   double* theta_cell;     // [2][N] or null
   double* theta_edge;     // [N][E] or null

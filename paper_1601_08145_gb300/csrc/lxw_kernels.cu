@@ -99,6 +99,53 @@ __device__ __forceinline__ void euler_d2(double g1, const Pt& s, const double w[
   G[3] = ddp * s.v + 2.0 * dh * dv + h * ddv;
 }
 
+// Third derivative of (F, G) along w (a term of the fourth-order time
+// average, Sec. 2.2 series continued): the Taylor coefficients in e of u, v,
+// p along q + e w by series products (rho u = m gives u_k = (m_k - w_rho
+// u_{k-1}) / rho), each flux component's third derivative being 3! times its
+// coefficient of e^3.
+__device__ __forceinline__ void euler_d3(double g1, const Pt& s, const double w[4], double F[4], double G[4]) {
+  const double u1 = (w[1] - s.u * w[0]) * s.ri, v1 = (w[2] - s.v * w[0]) * s.ri;
+  const double u2 = -w[0] * u1 * s.ri, v2 = -w[0] * v1 * s.ri;
+  const double u3 = -w[0] * u2 * s.ri, v3 = -w[0] * v2 * s.ri;
+  // K_3 = (m u_3 + w_m u_2 + n v_3 + w_n v_2) / 2, p_3 = -(g-1) K_3 (E is linear)
+  const double p3 = -g1 * 0.5 * (s.m * u3 + w[1] * u2 + s.n * v3 + w[2] * v2);
+  const double K2 = 0.5 * (s.m * u2 + w[1] * u1 + s.n * v2 + w[2] * v1);
+  const double K1 = 0.5 * (s.m * u1 + w[1] * s.u + s.n * v1 + w[2] * s.v);
+  const double p2 = -g1 * K2, p1 = g1 * (w[3] - K1);
+  const double H0 = s.e + s.p, H1 = w[3] + p1, H2 = p2, H3 = p3;
+  F[0] = 0.0;
+  F[1] = 6.0 * (s.m * u3 + w[1] * u2 + p3);
+  F[2] = 6.0 * (s.m * v3 + w[1] * v2);
+  F[3] = 6.0 * (H0 * u3 + H1 * u2 + H2 * u1 + H3 * s.u);
+  G[0] = 0.0;
+  G[1] = 6.0 * (s.n * u3 + w[2] * u2);
+  G[2] = 6.0 * (s.n * v3 + w[2] * v2 + p3);
+  G[3] = 6.0 * (H0 * v3 + H1 * v2 + H2 * v1 + H3 * s.v);
+}
+// mixed second derivative of (F, G) in the directions a and b, from the
+// bilinear chain rule (no cancellation): with u_a = (a_m - u a_rho)/rho, the
+// mixed derivative of u is -(u_b a_rho + u_a b_rho)/rho and that of p is
+// -(g-1) rho (u_a u_b + v_a v_b); each flux component is a product rule.
+__device__ __forceinline__ void euler_d11(double g1, const Pt& s, const double a[4], const double b[4], double F[4],
+                                          double G[4]) {
+  const double ua = (a[1] - s.u * a[0]) * s.ri, va = (a[2] - s.v * a[0]) * s.ri;
+  const double ub = (b[1] - s.u * b[0]) * s.ri, vb = (b[2] - s.v * b[0]) * s.ri;
+  const double uab = -(ub * a[0] + ua * b[0]) * s.ri, vab = -(vb * a[0] + va * b[0]) * s.ri;
+  const double pa = g1 * (a[3] - (s.u * a[1] + s.v * a[2] - 0.5 * (s.u * s.u + s.v * s.v) * a[0]));
+  const double pb = g1 * (b[3] - (s.u * b[1] + s.v * b[2] - 0.5 * (s.u * s.u + s.v * s.v) * b[0]));
+  const double pab = -g1 * s.r * (ua * ub + va * vb);
+  const double H = s.e + s.p, Ha = a[3] + pa, Hb = b[3] + pb;
+  F[0] = 0.0;
+  F[1] = a[1] * ub + b[1] * ua + s.m * uab + pab;
+  F[2] = a[1] * vb + b[1] * va + s.m * vab;
+  F[3] = pab * s.u + Ha * ub + Hb * ua + H * uab;
+  G[0] = 0.0;
+  G[1] = a[2] * ub + b[2] * ua + s.n * uab;
+  G[2] = a[2] * vb + b[2] * va + s.n * vab + pab;
+  G[3] = pab * s.v + Ha * vb + Hb * va + H * vab;
+}
+
 __device__ __forceinline__ double speed_of(double g, double r, double m, double n, double e) {
   double ri = 1.0 / r;
   double kin2 = m * m + n * n;
@@ -277,7 +324,10 @@ __global__ void __launch_bounds__(128) k_moment(const DevMesh m, const DevWork w
 // dt^2/6 F_tt (Eq. taylor3-flux).  Step 3 interior integral added to the
 // higher moments in place: Q^(l) += dt/|T| Int grad phi . F_T.  Edge points
 // store q and n_out . F_T for the edge phase.
-template <int KD, int E, int ML, int NQ, int MQ>
+// ORD4: fourth order in time (one more term of the series): q_ttt = -div
+// F_tt^h of the projected contravariant F_tt, F_ttt = F'''(q)(q_t,q_t,q_t) +
+// 3 F''(q)(q_t,q_tt) + F'(q) q_ttt, F_T += dt^3/24 F_ttt.
+template <int KD, int E, int ML, int NQ, int MQ, bool ORD4 = false>
 __global__ void __launch_bounds__(128) k_ck(const DevMesh m, const DevWork w, double* __restrict__ Q,
                                             const StepArgs a) {
   constexpr int NPT = NQ + E * MQ;
@@ -354,6 +404,49 @@ __global__ void __launch_bounds__(128) k_ck(const DevMesh m, const DevWork w, do
       for (int l = 0; l < ML; ++l) { Tx[v][l] = fma(fx, t.phi[k][l], Tx[v][l]); Ty[v][l] = fma(fy, t.phi[k][l], Ty[v][l]); }
     }
   }
+  // pass 2b (ORD4): projection of the contravariant F_tt
+  double Ux[4][ORD4 ? ML : 1], Uy[4][ORD4 ? ML : 1];
+  if (ORD4) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int l = 0; l < (ORD4 ? ML : 1); ++l) { Ux[v][l] = 0.0; Uy[v][l] = 0.0; }
+#pragma unroll 1
+    for (int k = 0; k < NQ; ++k) {
+      double q[4], qt[4], qtt[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double acc = 0.0, d1 = 0.0, d2 = 0.0;
+#pragma unroll
+        for (int l = 0; l < ML; ++l) {
+          acc = fma(c[v][l], t.phi[k][l], acc);
+          d1 = fma(Hx[v][l], t.dxi[k][l], d1);
+          d1 = fma(Hy[v][l], t.deta[k][l], d1);
+          d2 = fma(Tx[v][l], t.dxi[k][l], d2);
+          d2 = fma(Ty[v][l], t.deta[k][l], d2);
+        }
+        q[v] = acc; qt[v] = -d1; qtt[v] = -d2;
+      }
+      Pt s = make_pt(g1, q[0], q[1], q[2], q[3]);
+      double F2[4], G2[4], F3[4], G3[4], du, dvv, dp, eu, ev, ep;
+      double F1[4], G1[4];
+      euler_d1(g1, s, qt, F1, G1, du, dvv, dp);
+      euler_d2(g1, s, qt, du, dvv, dp, F2, G2);
+      euler_d1(g1, s, qtt, F3, G3, eu, ev, ep);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const double Ftt = F2[v] + F3[v], Gtt = G2[v] + G3[v];
+        double fx = t.w[k] * (jxx * Ftt + jxy * Gtt);
+        double fy = t.w[k] * (jyx * Ftt + jyy * Gtt);
+#pragma unroll
+        for (int l = 0; l < (ORD4 ? ML : 1); ++l) {
+          Ux[v][l] = fma(fx, t.phi[k][l], Ux[v][l]);
+          Uy[v][l] = fma(fy, t.phi[k][l], Uy[v][l]);
+        }
+      }
+    }
+  }
+  const double c3 = dt * dt * dt / 24.0;
   // pass 3: F_T at every point; volume integral at interior points, traces at edge points
   double Vv[4][ML];
 #pragma unroll
@@ -388,6 +481,28 @@ __global__ void __launch_bounds__(128) k_ck(const DevMesh m, const DevWork w, do
     for (int v = 0; v < 4; ++v) {
       FT[v] = F[v] + c1 * F1[v] + c2 * (F2[v] + F3[v]);
       GT[v] = G[v] + c1 * G1[v] + c2 * (G2[v] + G3[v]);
+    }
+    if (ORD4) {
+      double qttt[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double d3 = 0.0;
+#pragma unroll
+        for (int l = 0; l < (ORD4 ? ML : 1); ++l) {
+          d3 = fma(Ux[v][l], t.dxi[p][l], d3);
+          d3 = fma(Uy[v][l], t.deta[p][l], d3);
+        }
+        qttt[v] = -d3;
+      }
+      double A[4], B[4], C[4], D[4], Fq[4], Gq[4], fu, fv, fp;
+      euler_d3(g1, s, qt, A, B);
+      euler_d11(g1, s, qt, qtt, C, D);
+      euler_d1(g1, s, qttt, Fq, Gq, fu, fv, fp);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        FT[v] += c3 * (A[v] + 3.0 * C[v] + Fq[v]);
+        GT[v] += c3 * (B[v] + 3.0 * D[v] + Gq[v]);
+      }
     }
     if (p < NQ) {
 #pragma unroll
@@ -774,7 +889,10 @@ int step_impl(const DevMesh& m, const DevWork& w, double* Q, const StepArgs& a, 
     k_moment<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, Q, a, a.theta_cell);
   mark();
   if (upto < 2) return cudaGetLastError() == cudaSuccess ? 0 : -1;
-  k_ck<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, Q, a);
+  if (a.ck_order == 4)
+    k_ck<KD, E, ML, NQ, MQ, true><<<grid, block, 0, st>>>(m, w, Q, a);
+  else
+    k_ck<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, Q, a);
   mark();
   if (upto < 3) return cudaGetLastError() == cudaSuccess ? 0 : -1;
   k_edge<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, Q, a);

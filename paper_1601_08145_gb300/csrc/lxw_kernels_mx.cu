@@ -89,6 +89,44 @@ __device__ __forceinline__ void d2f(float g1, const PtF& s, const float w[4], fl
   G[0] = 0.0f; G[1] = 2.0f * w[2] * du + s.n * ddu; G[2] = 2.0f * w[2] * dv + s.n * ddv + ddp;
   G[3] = ddp * s.v + 2.0f * dh * dv + h * ddv;
 }
+// third derivative of (F, G) along w and the mixed second derivative, for
+// the fourth-order time average (see the FP64 kernels)
+__device__ __forceinline__ void d3f(float g1, const PtF& s, const float w[4], float F[4], float G[4]) {
+  const float u1 = (w[1] - s.u * w[0]) * s.ri, v1 = (w[2] - s.v * w[0]) * s.ri;
+  const float u2 = -w[0] * u1 * s.ri, v2 = -w[0] * v1 * s.ri;
+  const float u3 = -w[0] * u2 * s.ri, v3 = -w[0] * v2 * s.ri;
+  const float p3 = -g1 * 0.5f * (s.m * u3 + w[1] * u2 + s.n * v3 + w[2] * v2);
+  const float K2 = 0.5f * (s.m * u2 + w[1] * u1 + s.n * v2 + w[2] * v1);
+  const float K1 = 0.5f * (s.m * u1 + w[1] * s.u + s.n * v1 + w[2] * s.v);
+  const float p2 = -g1 * K2, p1 = g1 * (w[3] - K1);
+  const float H0 = s.e + s.p, H1 = w[3] + p1;
+  F[0] = 0.0f;
+  F[1] = 6.0f * (s.m * u3 + w[1] * u2 + p3);
+  F[2] = 6.0f * (s.m * v3 + w[1] * v2);
+  F[3] = 6.0f * (H0 * u3 + H1 * u2 + p2 * u1 + p3 * s.u);
+  G[0] = 0.0f;
+  G[1] = 6.0f * (s.n * u3 + w[2] * u2);
+  G[2] = 6.0f * (s.n * v3 + w[2] * v2 + p3);
+  G[3] = 6.0f * (H0 * v3 + H1 * v2 + p2 * v1 + p3 * s.v);
+}
+__device__ __forceinline__ void d11f(float g1, const PtF& s, const float a[4], const float b[4], float F[4],
+                                     float G[4]) {
+  const float ua = (a[1] - s.u * a[0]) * s.ri, va = (a[2] - s.v * a[0]) * s.ri;
+  const float ub = (b[1] - s.u * b[0]) * s.ri, vb = (b[2] - s.v * b[0]) * s.ri;
+  const float uab = -(ub * a[0] + ua * b[0]) * s.ri, vab = -(vb * a[0] + va * b[0]) * s.ri;
+  const float pa = g1 * (a[3] - (s.u * a[1] + s.v * a[2] - 0.5f * (s.u * s.u + s.v * s.v) * a[0]));
+  const float pb = g1 * (b[3] - (s.u * b[1] + s.v * b[2] - 0.5f * (s.u * s.u + s.v * s.v) * b[0]));
+  const float pab = -g1 * s.r * (ua * ub + va * vb);
+  const float H = s.e + s.p, Ha = a[3] + pa, Hb = b[3] + pb;
+  F[0] = 0.0f;
+  F[1] = a[1] * ub + b[1] * ua + s.m * uab + pab;
+  F[2] = a[1] * vb + b[1] * va + s.m * vab;
+  F[3] = pab * s.u + Ha * ub + Hb * ua + H * uab;
+  G[0] = 0.0f;
+  G[1] = a[2] * ub + b[2] * ua + s.n * uab;
+  G[2] = a[2] * vb + b[2] * va + s.n * vab + pab;
+  G[3] = pab * s.v + Ha * vb + Hb * va + H * vab;
+}
 __device__ __forceinline__ float speedf(float g, float r, float m, float n, float e) {
   float ri = 1.0f / r, k2 = m * m + n * n;
   float p = (g - 1.0f) * (e - 0.5f * k2 * ri);
@@ -536,7 +574,9 @@ __global__ void __launch_bounds__(128, 6) k_moment_mx(const DevMesh m, const Dev
 // fewer operations and 24 live coefficients per field instead of 48).
 // Then F_T at every point, the volume integral added to the FP32 higher
 // modes, and traces (q, n_out.F_T) at the edge points.
-template <int KD, int E, int ML, int NQ, int MQ>
+// ORD4: fourth order in time, Qttt = modal coefficients of q_ttt = -div
+// (F_tt)^h accumulated like Qt and Qtt, and dt^3/24 F_ttt added to F_T.
+template <int KD, int E, int ML, int NQ, int MQ, bool ORD4 = false>
 __device__ __forceinline__ void ck_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
                                         const StepArgs& a, const int i, const ScalMx& sc) {
   constexpr int NPT = NQ + E * MQ;
@@ -609,6 +649,44 @@ __device__ __forceinline__ void ck_elem(const DevMesh& m, const DevWorkMx& w, do
       for (int l = 0; l < ML; ++l) Qtt[v][l] = fmaf(-fx, c_wd[KD][0][k][l], fmaf(-fy, c_wd[KD][1][k][l], Qtt[v][l]));
     }
   }
+  // pass 2b (ORD4): Qttt = modal coefficients of q_ttt = -div (F_tt)^h
+  constexpr int M4 = ORD4 ? ML : 1;
+  float Qttt[4][M4];
+  if (ORD4) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int l = 0; l < M4; ++l) Qttt[v][l] = 0.0f;
+#pragma unroll 1
+    for (int k = 0; k < NQ; ++k) {
+      float q[4], qt[4], qtt[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float acc = 0.0f, e1 = 0.0f, e2 = 0.0f;
+#pragma unroll
+        for (int l = 0; l < ML; ++l) {
+          const float ph = t.phi[k][l];
+          acc = fmaf(c[v][l], ph, acc);
+          e1 = fmaf(Qt[v][l], ph, e1);
+          e2 = fmaf(Qtt[v][l], ph, e2);
+        }
+        q[v] = acc; qt[v] = e1; qtt[v] = e2;
+      }
+      PtF s = ptf(g1, q[0], q[1], q[2], q[3]);
+      float F1[4], G1[4], F2[4], G2[4], F3[4], G3[4], du, dvv, dp, eu, ev, ep;
+      d1f(g1, s, qt, F1, G1, du, dvv, dp);
+      d2f(g1, s, qt, du, dvv, dp, F2, G2);
+      d1f(g1, s, qtt, F3, G3, eu, ev, ep);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float Ftt = F2[v] + F3[v], Gtt = G2[v] + G3[v];
+        const float fx = jxx * Ftt + jxy * Gtt, fy = jyx * Ftt + jyy * Gtt;
+#pragma unroll
+        for (int l = 0; l < M4; ++l) Qttt[v][l] = fmaf(-fx, c_wd[KD][0][k][l], fmaf(-fy, c_wd[KD][1][k][l], Qttt[v][l]));
+      }
+    }
+  }
+  const float c3 = dt * dt * dt * (1.0f / 24.0f);
   // pass 3: F_T at every point; volume integral (interior), traces (edges)
   float Vv[4][ML];
 #pragma unroll
@@ -643,6 +721,25 @@ __device__ __forceinline__ void ck_elem(const DevMesh& m, const DevWorkMx& w, do
       FT[v] = F[v] + c1 * F1[v] + c2 * (F2[v] + F3[v]);
       GT[v] = G[v] + c1 * G1[v] + c2 * (G2[v] + G3[v]);
     }
+    if (ORD4) {
+      float qttt[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int l = 0; l < M4; ++l) acc = fmaf(Qttt[v][l], t.phi[p][l], acc);
+        qttt[v] = acc;
+      }
+      float A[4], B[4], Cm[4], Dm[4], Fq[4], Gq[4], fu, fv, fp;
+      d3f(g1, s, qt, A, B);
+      d11f(g1, s, qt, qtt, Cm, Dm);
+      d1f(g1, s, qttt, Fq, Gq, fu, fv, fp);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        FT[v] += c3 * (A[v] + 3.0f * Cm[v] + Fq[v]);
+        GT[v] += c3 * (B[v] + 3.0f * Dm[v] + Gq[v]);
+      }
+    }
     if (p < NQ) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -668,13 +765,13 @@ __device__ __forceinline__ void ck_elem(const DevMesh& m, const DevWorkMx& w, do
     for (int l = 1; l < ML; ++l) hi_at<ML>(st, N, v, l, i) = c[v][l] + dt * Vv[v][l];
 }
 
-template <int KD, int E, int ML, int NQ, int MQ>
+template <int KD, int E, int ML, int NQ, int MQ, bool ORD4 = false>
 __global__ void __launch_bounds__(128, ML == 6 ? 4 : 2) k_ck_mx(const DevMesh m, const DevWorkMx w,
                                                                 double* __restrict__ state, const StepArgs a) {
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
     if ((int)threadIdx.x < tile.y && w.scal[tile.z].live)
-      ck_elem<KD, E, ML, NQ, MQ>(m, w, state, a, tile.x + threadIdx.x, w.scal[tile.z]);
+      ck_elem<KD, E, ML, NQ, MQ, ORD4>(m, w, state, a, tile.x + threadIdx.x, w.scal[tile.z]);
   }
 }
 
@@ -1664,7 +1761,10 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
   k_moment_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, a.theta_cell);
   mark();
   if (upto < 2) return ok();
-  k_ck_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a);
+  if (a.ck_order == 4)
+    k_ck_mx<KD, E, ML, NQ, MQ, true><<<grid, block, 0, st>>>(m, w, state, a);
+  else
+    k_ck_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a);
   mark();
   if (upto < 3) return ok();
   if (a.hi_occupancy)

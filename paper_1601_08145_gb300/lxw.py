@@ -42,7 +42,7 @@ class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("eps0", C.c_double), ("alpha0", C.c_double),
                 ("shock_limiter", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
                 ("ctas_per_sm", C.c_int), ("high_occupancy", C.c_int), ("moment_exact", C.c_int),
-                ("llf_global", C.c_int), ("reserved", C.c_int * 5)]
+                ("llf_global", C.c_int), ("ck_order", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class Diag(C.Structure):

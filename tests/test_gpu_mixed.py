@@ -228,3 +228,23 @@ def test_full_size_one_mixed_step_against_oracle(L, O, kind, n, deg):
     assert np.abs(Qg[:, :, 0] - Qo[:, :, 0]).max() < 1e-5 * np.abs(Qo[:, :, 0]).max()
     assert (np.abs(Qg - Qo) / sc).max() < 1e-3
     assert np.abs(Qg - Qo).sum() / np.abs(Qo).sum() < 1e-5
+
+
+@pytest.mark.parametrize("kind", [QUAD, TRI])
+def test_fourth_order_ck_mixed_step_close_to_oracle(L, O, kind):
+    """ck_order 4 in the mixed form (FP32 bulk): one step of P3 random data
+    within the FP32 budget of the oracle's fourth-order step."""
+    bc = 2
+    s = solver(L, kind, 3, 10, bc=(bc,) * 4, tri_bc=bc if kind == TRI else None, ck_order=4)
+    so = oracle_solver(O, kind, 3, 10, bc=(bc,) * 4, tri_bc=bc if kind == TRI else None, ck_order=4)
+    Q0 = synth.random_modal_state(s.N, s.ML, seed=41, amp=0.3)
+    Q0[:, :, 1:] = Q0[:, :, 1:].astype(np.float32)
+    Qo = Q0.copy(); do = so.step(Qo, cfl=0.3)
+    st = L.new_state(s, torch.from_numpy(Q0).cuda())
+    d = L.lxw_step(s, st, 0.0, 0.3, diag=True)
+    Qg = L.to_q64(s, st).cpu().numpy()
+    assert d["status"] == 0 and do["status"] == 0
+    sc = np.abs(Qo).max(axis=0, keepdims=True) + 1e-3
+    assert np.abs(Qg[:, :, 0] - Qo[:, :, 0]).max() < 1e-5 * np.abs(Qo[:, :, 0]).max()
+    assert (np.abs(Qg - Qo) / sc).max() < 1e-3
+    assert np.abs(Qg - Qo).sum() / np.abs(Qo).sum() < 1e-5

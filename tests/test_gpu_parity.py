@@ -364,3 +364,24 @@ def test_double_rarefaction_1d_as_y_invariant_2d(L, O, mixed):
     err = rel_l1(Qh, Qo)
     print(f"double rarefaction ({'mixed' if mixed else 'fp64'}): relative L1 vs oracle {err:.2e}")
     assert err < (1e-4 if mixed else 1e-12)
+
+
+@pytest.mark.parametrize("kind", [QUAD, TRI])
+def test_fourth_order_ck_matches_oracle(L, O, kind):
+    """ck_order 4 (dt^3/24 F_ttt added to the time-averaged flux) on P3: 20
+    steps of the smooth wave against the oracle with the same option, as
+    close as the third-order runs are (1e-12 relative L1, or 10x the
+    third-order distance where the two sides' P3 tables differ more); the
+    added term is active (it moves the state by more than round-off)."""
+    err, states = {}, {}
+    for order in (3, 4):
+        os_, ls = make_pair(L, O, kind, 3, 12, ck_order=order)
+        Qo = os_.project_fn(synth.ic_smooth)
+        Qg = lib_project(L, ls, synth.ic_smooth)
+        Qo, Qgn = run_both(L, os_, ls, Qo, Qg, 20, 0.1)
+        err[order] = rel_l1(Qgn, Qo)
+        states[order] = Qgn
+    print(f"P3 {'quad' if kind == QUAD else 'tri'}: GPU vs oracle, CK order 3 {err[3]:.2e}, order 4 {err[4]:.2e}")
+    assert err[4] < max(1e-12, 10.0 * err[3])
+    d = rel_l1(states[3], states[4])
+    assert 1e-11 < d < 1e-5, d
