@@ -108,9 +108,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x 2 
 # scaled to the workload by the element count (the traffic of this kernel is
 # proportional to it).  A capture of another kernel source reads as None.
 CK_TRAFFIC = {
-    ("blast2048", "mixed"): {"bytes": 151_319_552 + 433_069_568, "source": "444355e1864a102c", "captured_elements": 1_048_576},
-    ("blast", "mixed"): {"bytes": 151_319_552 + 433_069_568, "source": "444355e1864a102c"},
-    ("rarefy708", "mixed"): {"bytes": 136_538_112 + 312_308_992, "source": "444355e1864a102c"},
+    ("blast2048", "mixed"): {"bytes": 151_320_576 + 433_108_736, "source": "2e8775680063edc7", "captured_elements": 1_048_576},
+    ("blast", "mixed"): {"bytes": 151_320_576 + 433_108_736, "source": "2e8775680063edc7"},
+    ("rarefy708", "mixed"): {"bytes": 136_541_696 + 312_284_160, "source": "2e8775680063edc7"},
 }
 
 
