@@ -252,3 +252,64 @@ def test_gate_wait_expiry_takes_the_timeout_path(L):
             assert d2["return_status"] == L.OK and d2["status"] == 0 and d2["n_mlp_skip"] > 0
     assert res["plain"][1]["return_status"] == L.OK
     assert torch.equal(res["gated_timeout"][0], res["plain"][0])
+
+
+@pytest.mark.parametrize("b3", [-30.0, 30.0])
+def test_gated_step_at_one_million_triangles_against_oracle(L, O, b3):
+    """The learned-indicator configuration's triangle mesh (708x708x2 =
+    1,002,528 jittered P2 triangles, the bench's mesh and options), one gated
+    mixed step from near-vacuum data with every limiter active, element by
+    element against the oracle.  The network's output bias is pinned so that
+    its verdict is known: b3 = -30 gives theta_hat ~ 0 (next to nothing
+    skipped: the state is the oracle's step within the FP32 budget); b3 = +30
+    gives theta_hat ~ 1 (next to every cell the exact screen leaves is
+    skipped).  Cells with theta_hat >= 1 - tau carry the oracle's step
+    without the shock limiter, the others its step with it; the averages,
+    which the shock limiter never moves, are the oracle's everywhere."""
+    n = 708
+    xy, tv = synth.structured_triangles(n, jitter=0.2, seed=20160129)
+    s = L.lxw_solver_create(L.lxw_mesh_triangles(xy, tv), 2, L.lxw_options_default(precision=L.PREC_MIXED),
+                            stream=torch.cuda.current_stream())
+    assert s.N == 1_002_528
+    net = L.lxw_mlp_create(256, seed=29, stream=torch.cuda.current_stream())
+    P = L.lxw_mlp_get_params(net)
+    P[5824] = b3
+    L.lxw_mlp_set_params(net, P)
+    L.lxw_solver_set_mlp(s, net, 0.01)
+    # near-vacuum random data in the first eighth of the cells (a band of the
+    # mesh), a uniform state (rho 1, p 0.4, at rest) in the others: the exact
+    # screen clears the uniform cells away from the band and none in it
+    Q0 = synth.random_modal_state(s.N, s.ML, seed=5708, amp=0.3, rho_range=(0.01, 3.0), p_range=(0.001, 3.0))
+    calm = np.arange(s.N) >= s.N // 8
+    Q0[calm] = 0.0
+    Q0[calm, 0, 0] = 1.0
+    Q0[calm, 3, 0] = 0.4 / 0.4
+    Q0[:, :, 1:] = Q0[:, :, 1:].astype(np.float32)
+    st = L.new_state(s, torch.from_numpy(Q0).cuda())
+    g = L.lxw_step_gate(s, st, 0.3).cpu().numpy()
+    Qg = L.to_q64(s, st).cpu().numpy()
+    asked = ~np.isnan(g)
+    skipped = asked & (g >= 0.99)
+    assert asked.sum() >= 0.99 * s.N               # theta_hat is reported for every cell
+    om = O.Mesh.triangles(xy, tv)
+    Qa = Q0.copy(); da = O.Solver(om, 2).step(Qa, cfl=0.3)
+    assert da["n_sc"] > 0 and da["status"] == 0
+    sc = np.abs(Qa).max(axis=0, keepdims=True) + 1e-3
+    # averages: the oracle's everywhere (the shock limiter never moves them)
+    assert np.abs(Qg[:, :, 0] - Qa[:, :, 0]).max() < 1e-5 * np.abs(Qa[:, :, 0]).max()
+    Qb = Q0.copy(); O.Solver(om, 2, shock_limiter=False).step(Qb, cfl=0.3)
+    # cells the gate did not skip: the oracle's step; skipped ones: without the
+    # shock limiter (a cell the exact screen clears has theta = 1 in the
+    # oracle, so there both agree whatever theta_hat says)
+    if (~skipped).any():
+        assert (np.abs(Qg[~skipped] - Qa[~skipped]) / sc).max() < 1e-3
+    if skipped.any():
+        assert (np.abs(Qg[skipped] - Qb[skipped]) / sc).max() < 1e-3
+    if b3 < 0:
+        assert skipped.sum() <= 0.01 * asked.sum()
+        assert np.abs(Qg - Qa).sum() / np.abs(Qa).sum() < 1e-5
+    else:
+        assert skipped.sum() >= 0.99 * asked.sum()
+        # the skipped cells include cells the oracle's shock limiter does change
+        moved = np.abs(Qa[skipped, :, 1:] - Qb[skipped, :, 1:]).max(axis=(1, 2)) > 1e-3 * sc[0, :, 1:].max()
+        assert moved.sum() > 0
