@@ -1047,20 +1047,27 @@ __device__ __forceinline__ void update_elem(const DevMesh& m, const DevWorkMx& w
                                             const StepArgs& a, const int i, const int pid) {
   const int N = m.N;
   MxState st = mx_state<ML>(state, N);
-  float th[E];
-  bool all_one = true;
+  // every load that does not depend on another first (f^LxW, averages, own
+  // proposals, neighbour ids), then the neighbours' proposals
+  float fwv[E][4];
 #pragma unroll
-  for (int k = 0; k < E; ++k) {
-    const int j = m.nbr[k * N + i];
-    float t = w.prop[k * N + i];
-    if (j >= 0) t = fminf(t, w.prop[m.nbk[k * N + i] * N + j]);
-    th[k] = t;
-    all_one = all_one && t == 1.0f;
-    if (a.theta_edge) a.theta_edge[(size_t)i * E + k] = t;
-  }
+  for (int k = 0; k < E; ++k)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) fwv[k][v] = w.fw[(size_t)(k * 4 + v) * N + i];
   double qb[4], acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int v = 0; v < 4; ++v) qb[v] = st.avg[(size_t)v * N + i];
+  int nb[E], nk[E];
+  float th[E];
+#pragma unroll
+  for (int k = 0; k < E; ++k) { nb[k] = m.nbr[k * N + i]; nk[k] = m.nbk[k * N + i]; th[k] = w.prop[k * N + i]; }
+  bool all_one = true;
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    if (nb[k] >= 0) th[k] = fminf(th[k], w.prop[nk[k] * N + nb[k]]);
+    all_one = all_one && th[k] == 1.0f;
+    if (a.theta_edge) a.theta_edge[(size_t)i * E + k] = th[k];
+  }
   if (all_one) {
     // the common case: f^LxW only.  The E FP32 values are summed without
     // rounding error (Knuth's TwoSum in FP32 gives sum = hi + lo exactly up
@@ -1069,10 +1076,10 @@ __device__ __forceinline__ void update_elem(const DevMesh& m, const DevWorkMx& w
     // both sides of an edge still add exact negatives.
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      float hi = w.fw[(size_t)v * N + i], lo = 0.0f;
+      float hi = fwv[0][v], lo = 0.0f;
 #pragma unroll
       for (int k = 1; k < E; ++k) {
-        const float b = w.fw[(size_t)(k * 4 + v) * N + i];
+        const float b = fwv[k][v];
         const float s1 = __fadd_rn(hi, b);
         const float bb = __fsub_rn(s1, hi);
         const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s1, bb)), __fsub_rn(b, bb));
@@ -1086,12 +1093,12 @@ __device__ __forceinline__ void update_elem(const DevMesh& m, const DevWorkMx& w
     const double g1 = a.gamma - 1.0;
 #pragma unroll
     for (int k = 0; k < E; ++k) {
-      const int j = m.nbr[k * N + i];
+      const int j = nb[k];
       double fw[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) fw[v] = (double)w.fw[(size_t)(k * 4 + v) * N + i];
+      for (int v = 0; v < 4; ++v) fw[v] = (double)fwv[k][v];
       if (th[k] < 1.0f) {
-        if (a.want_diag && (j < 0 || i < j || (i == j && k < m.nbk[k * N + i])))
+        if (a.want_diag && (j < 0 || i < j || (i == j && k < nk[k])))
           atomicAdd(&reinterpret_cast<DiagBlock*>(w.diag)->nedge, 1ull);
         const double nx = m.nrm[(2 * k) * N + i], ny = m.nrm[(2 * k + 1) * N + i];
         double qn[4], ff[4];
