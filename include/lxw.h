@@ -101,7 +101,15 @@ typedef struct {
                                of the projected F_tt), so that P3 elements are
                                fourth order in time too (the higher-order
                                direction of the conclusions)                   */
-  int reserved[4];
+  int gate_scan;            /* mixed form with the learned gate: 0 (default) = the
+                               plain shock kernel screens every cell, commits the
+                               ones its exact screen clears and lists the rest,
+                               and the gate kernel takes only the listed cells
+                               (two launches); 1 = the gate kernel screens every
+                               cell itself (one launch, faster on small meshes).
+                               Same state either way; lxw_autotune chooses when
+                               a network is attached                            */
+  int reserved[3];
 } lxw_options;
 
 /* Per-step diagnostics (filled when a non-NULL pointer is passed). */
@@ -205,12 +213,16 @@ lxw_status lxw_batch_create(int nmesh, const lxw_mesh* const* meshes, int degree
 lxw_status lxw_batch_scalars(lxw_solver* s, int* nprob, double* s_host, double* dt_host);
 /* Autotuner: times `reps` steps of each candidate (elements per CTA in
  * {32, 64, 128} x persistent CTAs per SM in {0 (one per tile), 1, 2, 3, 4,
- * 6, 8} x high_occupancy in {0, 1}; FP64 solvers: elements per CTA only)
+ * 6, 8} x high_occupancy in {0, 1}; FP64 solvers: elements per CTA only),
+ * then, with a network attached, gate_scan in {0, 1} for the fastest of those,
  * on a scratch copy of
  * state_dev (restored afterwards), keeps the fastest in the solver and
  * returns it (output pointers nullable).  Allocates a scratch state. */
 lxw_status lxw_autotune(lxw_solver* s, void* state_dev, double cfl, int reps, int* block_threads,
                         int* ctas_per_sm, float* best_ms, int* high_occupancy);
+/* The solver's options as it runs now (after lxw_autotune: the chosen work
+ * list, variants and gate_scan).  Errors: LXW_ERR_ARG (null argument). */
+lxw_status lxw_solver_get_options(const lxw_solver* s, lxw_options* out);
 
 /* Physical coordinates of the initial-condition projection points
  * xy_host[N][nproj][2] (Gauss rule with degree+3 points per direction). */

@@ -442,6 +442,8 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     return fail(LXW_ERR_ARG, "lxw_solver_create: moment_exact must be 0 or 1");
   if (opt.llf_global != 0 && opt.llf_global != 1)
     return fail(LXW_ERR_ARG, "lxw_solver_create: llf_global must be 0 or 1");
+  if (opt.gate_scan != 0 && opt.gate_scan != 1)
+    return fail(LXW_ERR_ARG, "lxw_solver_create: gate_scan must be 0 or 1");
   if (opt.ck_order == 0) opt.ck_order = 3;
   if (opt.ck_order != 3 && opt.ck_order != 4)
     return fail(LXW_ERR_ARG, "lxw_solver_create: ck_order must be 3 or 4");
@@ -527,6 +529,8 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     s->dwm.avg_new = (double*)dalloc(sizeof(double) * 4 * (size_t)N);
     s->dwm.avgn32 = (float*)dalloc(sizeof(float) * 4 * (size_t)N);
     s->dwm.done = (unsigned int*)dalloc(sizeof(unsigned int));
+    s->dwm.gate_list = (int*)dalloc(sizeof(int) * (size_t)N);
+    s->dwm.gate_count = (unsigned int*)dalloc(sizeof(unsigned int));
     s->dwm.scal = (ScalMx*)dalloc(sizeof(ScalMx) * nprob);
     s->dwm.smax = s->dw.smax; s->dwm.status = s->dw.status; s->dwm.diag = s->dw.diag;
     s->Sdev = (double*)dalloc(lxw_state_bytes(s));
@@ -536,7 +540,9 @@ static lxw_status create_impl(const lxw_mesh* mesh, const std::vector<int>& psta
     float* ia32 = (float*)dalloc(sizeof(float) * (size_t)N);
     double* ia64 = (double*)dalloc(sizeof(double) * (size_t)N);
     if (!s->dwm.avg_new || !s->dwm.avgn32 || !s->dwm.done ||
-        cudaMemset(s->dwm.done, 0, sizeof(unsigned int)) != cudaSuccess || !s->dwm.scal || !s->Sdev || !j32 || !n32 || !s32 || !ia32 || !ia64) {
+        cudaMemset(s->dwm.done, 0, sizeof(unsigned int)) != cudaSuccess || !s->dwm.gate_list || !s->dwm.gate_count ||
+        cudaMemset(s->dwm.gate_count, 0, sizeof(unsigned int)) != cudaSuccess || !s->dwm.scal || !s->Sdev || !j32 ||
+        !n32 || !s32 || !ia32 || !ia64) {
       delete s;
       return fail(LXW_ERR_NOMEM, "lxw_solver_create: device allocation failed");
     }
@@ -710,6 +716,7 @@ static StepArgs make_args(const lxw_solver* s, double dt, double cfl, int want_d
   a.moment_exact = s->opt.moment_exact;
   a.llf_global = s->opt.llf_global;
   a.ck_order = s->opt.ck_order;
+  a.gate_scan = s->opt.gate_scan;
   a.gamma_f = (float)a.gamma; a.eps0_f = (float)a.eps0; a.alpha0_f = (float)a.alpha0;
   a.grid = s->opt.ctas_per_sm > 0 ? s->opt.ctas_per_sm * s->sms : 0;   // persistent CTAs, or one per tile
   a.sms = s->sms;
@@ -984,7 +991,9 @@ int lxw_profile_phases(const lxw_solver* s) { return s ? phases_of(s) : 0; }
 int lxw_step_launches(const lxw_solver* s) {
   if (!s) return 0;
   if (!s->mixed) return step_launch_count(0, s->opt.shock_limiter);
-  return 5;   // moment, ck, edge, update, shock (the learned gate runs inside the shock kernel)
+  // moment, ck, edge, update, shock; with the learned gate in its list form
+  // the shock phase is two launches (screen + list, gate on the list)
+  return s->mlp_w && s->opt.shock_limiter && !s->opt.gate_scan ? 6 : 5;
 }
 
 lxw_status lxw_batch_scalars(lxw_solver* s, int* nprob, double* s_host, double* dt_host) {
@@ -1121,6 +1130,26 @@ lxw_status lxw_autotune(lxw_solver* s, void* state, double cfl, int reps, int* b
     if (st != LXW_OK) break;
   }
   s->opt.block_threads = bb; s->opt.ctas_per_sm = bc; s->opt.high_occupancy = bh;
+  if (st == LXW_OK && s->mixed && s->mlp_w && s->opt.shock_limiter) {
+    // the gated limiter's two forms, on the chosen work list
+    if ((st = build_tiles(s)) == LXW_OK) {
+      float bt[2] = {1e30f, 1e30f};
+      for (int g = 0; g < 2 && st == LXW_OK; ++g) {
+        s->opt.gate_scan = g;
+        drop_graphs(s);
+        cudaMemcpy(state, save, bytes, cudaMemcpyDeviceToDevice);
+        if ((st = lxw_profile_step(s, (double*)state, cfl, ms)) != LXW_OK) break;
+        float tot = 0.0f;
+        for (int r = 0; r < reps && st == LXW_OK; ++r) {
+          if ((st = lxw_profile_step(s, (double*)state, cfl, ms)) != LXW_OK) break;
+          for (int k = 0; k < phases_of(s); ++k) tot += ms[k];
+        }
+        bt[g] = tot / reps;
+      }
+      s->opt.gate_scan = bt[1] < bt[0] ? 1 : 0;
+      best = std::min(bt[0], bt[1]);
+    }
+  }
   drop_graphs(s);
   lxw_status tst = build_tiles(s);
   cudaMemcpy(state, save, bytes, cudaMemcpyDeviceToDevice);
@@ -1131,6 +1160,12 @@ lxw_status lxw_autotune(lxw_solver* s, void* state, double cfl, int reps, int* b
   if (cps) *cps = bc;
   if (best_ms) *best_ms = best;
   if (hiocc) *hiocc = bh;
+  return LXW_OK;
+}
+
+lxw_status lxw_solver_get_options(const lxw_solver* s, lxw_options* out) {
+  if (!s || !out) return fail(LXW_ERR_ARG, "lxw_solver_get_options: null argument");
+  *out = s->opt;
   return LXW_OK;
 }
 

@@ -88,6 +88,8 @@ struct DevWorkMx {
   unsigned int* status;
   double* diag;           // DiagBlock
   unsigned int* done;     // CTAs of the moment kernel that have finished (the last one computes scal)
+  int* gate_list;         // [N]: cells the shock limiter's exact screen left, for the gated limiter
+  unsigned int* gate_count;  // entries of gate_list (zeroed by the update kernel every step)
 };
 
 // Diagnostics block on the device (both forms).
@@ -144,6 +146,7 @@ struct StepArgs {
   int moment_exact;                  // moment limiter: exact root instead of the secant
   int llf_global;                    // LLF point flux: global s instead of the local speed of the traces
   int ck_order;                      // CK flux order in time: 3 (Eq. taylor3-flux) or 4
+  int gate_scan;                     // gated limiter: 1 = the gate kernel screens every cell, 0 = list
   int want_diag;
   double* theta_cell;     // [2][N] or null
   double* theta_edge;     // [N][E] or null

@@ -1133,6 +1133,9 @@ __device__ __forceinline__ void update_elem(const DevMesh& m, const DevWorkMx& w
 template <int E, int ML>
 __global__ void __launch_bounds__(128, 6) k_update_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
                                                    const StepArgs a) {
+  // the gated shock limiter's list of this step starts empty (the shock
+  // kernels run after this one)
+  if (blockIdx.x == 0 && threadIdx.x == 0) *w.gate_count = 0u;
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
     if ((int)threadIdx.x < tile.y && w.scal[tile.z].live) update_elem<E, ML>(m, w, state, a, tile.x + threadIdx.x, tile.z);
@@ -1355,14 +1358,17 @@ __device__ __forceinline__ bool shock_screen_at(const DevMesh& m, const DevWorkM
 template <int KD, int E, int ML, int NQ, int MQ>
 __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w, double* __restrict__ state,
                                            const StepArgs& a, double* __restrict__ theta_out, const int limit,
-                                           const int i, const bool skip) {
+                                           const int i, const bool skip, const bool defer = false) {
   constexpr int NPT = NQ + E * MQ;
   const TablesF& t = c_tabf[KD];
   const int N = m.N;
   MxState st = mx_state<ML>(state, N);
+  // the new averages this cell commits at the end, loaded first (the stores
+  // below may alias them as far as the compiler can tell)
   float an32[4];
+  double an64[4];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) an32[v] = w.avgn32[(size_t)v * N + i];
+  for (int v = 0; v < 4; ++v) { an32[v] = w.avgn32[(size_t)v * N + i]; an64[v] = w.avg_new[(size_t)v * N + i]; }
   if (limit && skip) {
     if (theta_out) theta_out[i] = 1.0;
   } else if (limit) {
@@ -1383,6 +1389,11 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
       const float dx = m.sdx32[i];
       const float al = a.alpha0_f * dx * sqrtf(dx);
       const bool clear = shock_screen<KD, ML>(c, sb, g1, al);
+      if (!clear && defer) {
+        // left to the gated limiter, which limits (or skips) and commits it
+        w.gate_list[atomicAdd(w.gate_count, 1u)] = i;
+        return;
+      }
       float Mx[4], Mn[4], nr[4] = {0.0f, 0.0f, 0.0f, 0.0f}, ne[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int v = 0; v < 4; ++v) { Mx[v] = wb[v] + al; Mn[v] = wb[v] - al; }
@@ -1453,7 +1464,7 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
   }
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
-    st.avg[(size_t)v * N + i] = w.avg_new[(size_t)v * N + i];
+    st.avg[(size_t)v * N + i] = an64[v];
     st.a32[(size_t)v * N + i] = an32[v];
   }
 }
@@ -1469,13 +1480,20 @@ __device__ __forceinline__ void shock_elem(const DevMesh& m, const DevWorkMx& w,
 // runs the plain limiter everywhere and touches no tensor-core state.  If a
 // device wait gives up, the CTA flags LXW_ST_TIMEOUT and runs the plain
 // limiter on the rest of its cells.
-template <int KD, int E, int ML, int NQ, int MQ, bool HI>
+// LIST: the cells come from w.gate_list (the ones the plain kernel's exact
+// screen left, in any order), 128 per tile; a CTA with no tile leaves before
+// it takes tensor memory or copies the weights.  Each row of a product
+// depends only on its own cell, so the result is that of the full scan.
+template <int KD, int E, int ML, int NQ, int MQ, bool HI, bool LIST = false>
 __global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const DevMesh m, const DevWorkMx w,
                                                              double* __restrict__ state, const StepArgs a,
                                                              double* __restrict__ theta_out) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const int N = m.N;
   if (a.timed && !w.scal[0].live) return;   // a timed run that has ended (one problem: the host checks)
+  const int count = LIST ? (int)*w.gate_count : N;
+  const int ntile = (count + kGateRows - 1) / kGateRows;
+  if (LIST && (int)blockIdx.x >= ntile) return;
   if (a.gate_w == nullptr) {
     for (int i = blockIdx.x * blockDim.x + tid; i < N; i += gridDim.x * blockDim.x) {
       float f[kMlpIn];
@@ -1521,12 +1539,13 @@ __global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const D
   unsigned phase = 0;
   const unsigned a1 = smem_u32(g.a1), a2 = smem_u32(g.a2), w1 = smem_u32(g.w.w1), w2 = smem_u32(g.w.w2);
   const unsigned lane_off = (unsigned)(warp * 32) << 16;
-  const int ntile = (N + kGateRows - 1) / kGateRows;
   unsigned long long skipped = 0;
   for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
-    const int i = t * kGateRows + tid;
-    // the network rules only on tiles holding a cell the exact screen cannot clear
-    const bool clr = i < N && shock_screen_at<KD, ML>(m, w, state, a, i);
+    const int r = t * kGateRows + tid;
+    const int i = LIST ? (r < count ? w.gate_list[r] : N) : r;
+    // the network rules only on tiles holding a cell the exact screen cannot
+    // clear (a listed cell is one)
+    const bool clr = !LIST && i < N && shock_screen_at<KD, ML>(m, w, state, a, i);
     const bool inspect = a.gate_out || a.feat_out;          // every cell's theta_hat / features
     bool need_net = inspect || __syncthreads_or(i < N && !clr) != 0;
     if (need_net && !abort && !wready) {
@@ -1651,13 +1670,16 @@ __global__ void __launch_bounds__(kGateRows, HI ? 5 : 4) k_shock_gate_mx(const D
   }
 }
 
+// defer: cells the exact screen cannot clear go to the gated limiter's list
+// (k_shock_gate_mx<..., LIST>) instead of being limited and committed here
 template <int KD, int E, int ML, int NQ, int MQ>
 __global__ void __launch_bounds__(128) k_shock_mx(const DevMesh m, const DevWorkMx w, double* __restrict__ state,
-                                                  const StepArgs a, double* __restrict__ theta_out, int limit) {
+                                                  const StepArgs a, double* __restrict__ theta_out, int limit,
+                                                  int defer) {
   for (int tl = blockIdx.x; tl < m.ntiles; tl += gridDim.x) {
     const int4 tile = m.tiles[tl];
     if ((int)threadIdx.x < tile.y && w.scal[tile.z].live)
-      shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, limit, tile.x + threadIdx.x, false);
+      shock_elem<KD, E, ML, NQ, MQ>(m, w, state, a, theta_out, limit, tile.x + threadIdx.x, false, defer != 0);
   }
 }
 
@@ -1790,12 +1812,21 @@ int step_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const Step
     const int ntile = (m.N + kGateRows - 1) / kGateRows;
     const int gg = std::max(1, std::min(ntile, std::max(a.gate_per_sm, 1) * std::max(a.sms, 1)));
     const size_t smem = a.gate_w ? sizeof(GateTile) : 0;
-    if (a.hi_occupancy)
+    if (a.gate_w && !a.gate_out && !a.feat_out && !a.gate_scan) {
+      // the plain kernel screens every cell, commits the cleared ones and
+      // lists the rest; the gate kernel takes only the listed cells
+      k_shock_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, tsc, 1, 1);
+      if (a.hi_occupancy)
+        k_shock_gate_mx<KD, E, ML, NQ, MQ, true, true><<<gg, kGateRows, smem, st>>>(m, w, state, a, tsc);
+      else
+        k_shock_gate_mx<KD, E, ML, NQ, MQ, false, true><<<gg, kGateRows, smem, st>>>(m, w, state, a, tsc);
+    } else if (a.hi_occupancy) {
       k_shock_gate_mx<KD, E, ML, NQ, MQ, true><<<gg, kGateRows, smem, st>>>(m, w, state, a, tsc);
-    else
+    } else {
       k_shock_gate_mx<KD, E, ML, NQ, MQ, false><<<gg, kGateRows, smem, st>>>(m, w, state, a, tsc);
+    }
   } else {
-    k_shock_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, tsc, limit);
+    k_shock_mx<KD, E, ML, NQ, MQ><<<grid, block, 0, st>>>(m, w, state, a, tsc, limit, 0);
   }
   mark();
   if (a.want_diag) k_diag_mx<ML><<<gridn(m.N, 256), 256, 0, st>>>(m, w, state, a.gamma);
@@ -1828,8 +1859,11 @@ int moment_mx_impl(const DevMesh& m, const DevWorkMx& w, double* state, const St
 template <int KD, int E, int ML, int NQ, int MQ, bool HI>
 int gate_occupancy_impl() {
   auto fn = k_shock_gate_mx<KD, E, ML, NQ, MQ, HI>;
+  auto fl = k_shock_gate_mx<KD, E, ML, NQ, MQ, HI, true>;   // the list form: same resources
   if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaFuncSetAttribute(fl, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+          cudaSuccess)
     return -1;
   cudaFuncAttributes fa;
   int dev = 0, regs_sm = 0, smem_sm = 0, smem_rsv = 0, thr_sm = 0, blk_sm = 0;

@@ -34,7 +34,7 @@ EXPORTS = [
     "lxw_mlp_forward", "lxw_mlp_loss_grad", "lxw_mlp_train", "lxw_solver_set_mlp", "lxw_step_dump",
     "lxw_step_gate", "lxw_profile_phases", "lxw_basis_eval", "lxw_mesh_cartesian_masked",
     "lxw_solver_set_inflow", "lxw_mlp_set_envelope", "lxw_mlp_get_envelope", "lxw_run_host_state",
-    "lxw_solver_set_gate_wait_test", "lxw_run_to",
+    "lxw_solver_set_gate_wait_test", "lxw_run_to", "lxw_solver_get_options",
 ]
 
 
@@ -42,7 +42,8 @@ class Options(C.Structure):
     _fields_ = [("gamma", C.c_double), ("eps0", C.c_double), ("alpha0", C.c_double),
                 ("shock_limiter", C.c_int), ("precision", C.c_int), ("block_threads", C.c_int),
                 ("ctas_per_sm", C.c_int), ("high_occupancy", C.c_int), ("moment_exact", C.c_int),
-                ("llf_global", C.c_int), ("ck_order", C.c_int), ("reserved", C.c_int * 4)]
+                ("llf_global", C.c_int), ("ck_order", C.c_int), ("gate_scan", C.c_int),
+                ("reserved", C.c_int * 3)]
 
 
 class Diag(C.Structure):
@@ -123,6 +124,7 @@ def lib():
                                 C.POINTER(C.c_float)]
     L.lxw_solver_set_mlp.argtypes = [_vp, _vp, C.c_float]
     L.lxw_solver_set_gate_wait_test.argtypes = [_vp, C.c_longlong]
+    L.lxw_solver_get_options.argtypes = [_vp, C.POINTER(Options)]
     L.lxw_run_to.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int, _vp, C.POINTER(C.c_int), _dp]
     L.lxw_step_dump.argtypes = [_vp, _vp, C.c_double, _vp, _vp]
     L.lxw_step_gate.argtypes = [_vp, _vp, C.c_double, _vp, _vp]
@@ -444,7 +446,15 @@ def lxw_autotune(solver, state, cfl, reps=5):
     b = C.c_int(); c = C.c_int(); ms = C.c_float(); hi = C.c_int()
     _check(lib().lxw_autotune(solver.h, _ptr(state, solver.state_shape, "state"), cfl, reps,
                               C.byref(b), C.byref(c), C.byref(ms), C.byref(hi)))
-    return {"block_threads": b.value, "ctas_per_sm": c.value, "high_occupancy": hi.value, "ms_per_step": ms.value}
+    return {"block_threads": b.value, "ctas_per_sm": c.value, "high_occupancy": hi.value,
+            "gate_scan": lxw_solver_get_options(solver)["gate_scan"], "ms_per_step": ms.value}
+
+
+def lxw_solver_get_options(solver):
+    """The solver's options as it runs now (after lxw_autotune: its choices)."""
+    o = Options()
+    _check(lib().lxw_solver_get_options(solver.h, C.byref(o)))
+    return {k: getattr(o, k) for k, _ in Options._fields_ if k != "reserved"}
 
 
 MLP_IN, MLP_HIDDEN, MLP_PARAMS = 24, 64, 5825

@@ -286,8 +286,13 @@ def test_gated_step_at_one_million_triangles_against_oracle(L, O, b3):
     Q0[calm, 3, 0] = 0.4 / 0.4
     Q0[:, :, 1:] = Q0[:, :, 1:].astype(np.float32)
     st = L.new_state(s, torch.from_numpy(Q0).cuda())
+    st2 = st.clone()
     g = L.lxw_step_gate(s, st, 0.3).cpu().numpy()
     Qg = L.to_q64(s, st).cpu().numpy()
+    # the ordinary gated step (the plain kernel screens and lists, the gate
+    # kernel takes the listed cells) gives the state of the full scan above
+    d2 = L.lxw_step(s, st2, 0.0, 0.3, diag=True)
+    assert torch.equal(st, st2)
     asked = ~np.isnan(g)
     skipped = asked & (g >= 0.99)
     assert asked.sum() >= 0.99 * s.N               # theta_hat is reported for every cell
@@ -306,10 +311,47 @@ def test_gated_step_at_one_million_triangles_against_oracle(L, O, b3):
     if skipped.any():
         assert (np.abs(Qg[skipped] - Qb[skipped]) / sc).max() < 1e-3
     if b3 < 0:
-        assert skipped.sum() <= 0.01 * asked.sum()
+        assert skipped.sum() <= 0.01 * asked.sum() and d2["n_mlp_skip"] <= 0.01 * s.N
         assert np.abs(Qg - Qa).sum() / np.abs(Qa).sum() < 1e-5
     else:
-        assert skipped.sum() >= 0.99 * asked.sum()
+        assert skipped.sum() >= 0.99 * asked.sum() and d2["n_mlp_skip"] > 0
         # the skipped cells include cells the oracle's shock limiter does change
         moved = np.abs(Qa[skipped, :, 1:] - Qb[skipped, :, 1:]).max(axis=(1, 2)) > 1e-3 * sc[0, :, 1:].max()
         assert moved.sum() > 0
+
+
+@pytest.mark.parametrize("kind,n,deg", [("quad", 48, 2), ("tri", 21, 3)])
+def test_gate_scan_and_list_forms_agree(L, kind, n, deg):
+    """The gated limiter's two forms -- the gate kernel screening every cell
+    (gate_scan 1) or the plain kernel screening and listing the uncleared
+    cells for it (gate_scan 0, two launches) -- give the same states and skip
+    counts bit for bit over several steps, with a network that skips most of
+    the cells it rules on; the autotuner reports the form it keeps."""
+    net = L.lxw_mlp_create(256, seed=9, stream=torch.cuda.current_stream())
+    box, bc, ic = ((-1.1, 1.1, -1.1, 1.1), (1, 1, 1, 1), synth.ic_blast(n)) if kind == "quad" else \
+        ((0.0, 1.0, 0.0, 1.0), (2, 2, 2, 2), synth.ic_rarefy)
+    states, skips = [], []
+    for scan in (0, 1):
+        if kind == "tri":
+            xy, tv = synth.structured_triangles(n, jitter=0.2, seed=20160129, box=box)
+            mesh = L.lxw_mesh_triangles(xy, tv)
+        else:
+            mesh = L.lxw_mesh_cartesian(n, n, box, bc)
+        o = L.lxw_options_default(precision=L.PREC_MIXED, alpha0=50.0, gate_scan=scan)
+        s = L.lxw_solver_create(mesh, deg, o, stream=torch.cuda.current_stream())
+        L.lxw_solver_set_mlp(s, net, 0.999)
+        assert L.lxw_step_launches(s) == (5 if scan else 6)
+        assert L.lxw_solver_get_options(s)["gate_scan"] == scan
+        st = start(L, s, ic)
+        sk = 0
+        for _ in range(12):
+            d = L.lxw_step(s, st, 0.0, 0.1, diag=True)
+            assert d["return_status"] == L.OK
+            sk += d["n_mlp_skip"]
+        states.append(st)
+        skips.append(sk)
+    assert skips[0] == skips[1] and skips[0] > 0
+    assert torch.equal(states[0], states[1])
+    res = L.lxw_autotune(s, st.clone(), 0.1, reps=1)
+    assert res["gate_scan"] in (0, 1)
+    assert L.lxw_step_launches(s) == (5 if res["gate_scan"] else 6)
