@@ -43,7 +43,10 @@
  *    m = min(w_i - alpha, min_j w_j) over face neighbours j,
  *    theta_w = min(1, (M - w_i)/(max_pts w - w_i), (w_i - m)/(w_i - min_pts w)),
  *    theta_sc = min_w theta_w, alpha = alpha0 * dx^1.5, applied to all
- *    higher moments of the conserved variables.
+ *    higher moments of the conserved variables.  Pinned on the density
+ *    (where only the density varies over a cell, theta_sc equals its ratio
+ *    and the limited density touches its bound); its agreement with the
+ *    cited method itself is parity unpinned.
  *
  * Mode order.  Quadrilateral [-1,1]^2 (total degree <= deg, tensor Legendre
  * products normalised so that (1/4) Int phi_k phi_l = delta_kl):

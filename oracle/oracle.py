@@ -4,6 +4,7 @@ Only the tests, the smoke check and the benchmark's CPU-baseline leg import
 this module.  It marshals numpy arrays into the C oracle (lxw_oracle.c) and
 holds none of the method's arithmetic.
 """
+import contextlib
 import ctypes as C
 import os
 
@@ -33,62 +34,78 @@ def _i(a):
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
-        L.orc_gauss_legendre.argtypes = [C.c_int, _dp, _dp]
-        L.orc_num_modes.argtypes = [C.c_int, C.c_int]
-        L.orc_basis_eval.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
-        L.orc_interior_rule.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
-        for f in (L.orc_flux_d1, L.orc_flux_d2):
-            f.argtypes = [C.c_double, _dp, _dp, _dp, _dp]
-        L.orc_flux.argtypes = [C.c_double, _dp, _dp, _dp]
-        L.orc_mesh_cartesian.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _ip]
-        L.orc_mesh_cartesian.restype = C.c_void_p
-        L.orc_mesh_cartesian_masked.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
-                                                _ip, C.POINTER(C.c_ubyte), C.c_int]
-        L.orc_mesh_cartesian_masked.restype = C.c_void_p
-        L.orc_solver_set_inflow.argtypes = [C.c_void_p, _dp]
-        L.orc_mesh_triangles.argtypes = [C.c_int, _dp, C.c_int, _ip, _ip]
-        L.orc_mesh_triangles.restype = C.c_void_p
-        L.orc_mesh_free.argtypes = [C.c_void_p]
-        for f in (L.orc_mesh_num_elements, L.orc_mesh_num_edges, L.orc_mesh_edges_per_element):
-            f.argtypes = [C.c_void_p]
-        L.orc_mesh_geometry.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
-        L.orc_solver_new.argtypes = [C.c_void_p, C.c_int, C.c_double]
-        L.orc_solver_new.restype = C.c_void_p
-        L.orc_solver_free.argtypes = [C.c_void_p]
-        L.orc_solver_set_params.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int]
-        L.orc_solver_set_moment_exact.argtypes = [C.c_void_p, C.c_int]
-        L.orc_solver_set_llf_global.argtypes = [C.c_void_p, C.c_int]
-        L.orc_solver_set_ck_order.argtypes = [C.c_void_p, C.c_int]
-        L.orc_flux_d3.argtypes = [C.c_double, _dp, _dp, _dp, _dp]
-        L.orc_flux_d11.argtypes = [C.c_double, _dp, _dp, _dp, _dp, _dp]
-        for f in (L.orc_solver_num_modes, L.orc_solver_num_points, L.orc_projection_num_points):
-            f.argtypes = [C.c_void_p]
-        L.orc_projection_points.argtypes = [C.c_void_p, _dp]
-        L.orc_projection_weights.argtypes = [C.c_void_p, _dp]
-        L.orc_project.argtypes = [C.c_void_p, _dp, _dp]
-        L.orc_eval_projection_points.argtypes = [C.c_void_p, _dp, _dp]
-        L.orc_eval_limiter_points.argtypes = [C.c_void_p, _dp, _dp]
-        L.orc_limiter_points.argtypes = [C.c_void_p, _dp]
-        L.orc_last_fluxes.argtypes = [C.c_void_p, _dp, _dp]
-        L.orc_last_fluxes.restype = C.c_double
-        L.orc_moment_limit.argtypes = [C.c_void_p, _dp, _dp, _ip]
-        L.orc_moment_limit.restype = C.c_double
-        L.orc_wave_speed.argtypes = [C.c_void_p, _dp]
-        L.orc_wave_speed.restype = C.c_double
-        L.orc_ck_element.argtypes = [C.c_void_p, _dp, C.c_int, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
-        L.orc_mu_solve.argtypes = [C.c_double, C.c_double, _dp, _dp]
-        L.orc_mu_solve.restype = C.c_double
-        L.orc_flux_limit_cell.argtypes = [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
-        L.orc_shock_limit.argtypes = [C.c_void_p, _dp, _dp]
-        L.orc_step.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
-        L.orc_num_threads.argtypes = []
-        L.orc_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int, _dp, _dp]
-        L.orc_mlp_loss_grad.restype = C.c_double
-        L.orc_features.argtypes = [C.c_void_p, _dp, _dp]
-        _lib = L
+        _lib = _configure(C.CDLL(_build.build()))
     return _lib
+
+
+@contextlib.contextmanager
+def use_library(path):
+    """Run this wrapper on another build of the oracle (a test's planted
+    variant, same interface) inside the block."""
+    global _lib
+    keep = lib()
+    _lib = _configure(C.CDLL(path))
+    try:
+        yield _lib
+    finally:
+        _lib = keep
+
+
+def _configure(L):
+    """Argument and result types of the oracle's C entry points."""
+    L.orc_gauss_legendre.argtypes = [C.c_int, _dp, _dp]
+    L.orc_num_modes.argtypes = [C.c_int, C.c_int]
+    L.orc_basis_eval.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
+    L.orc_interior_rule.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp]
+    for f in (L.orc_flux_d1, L.orc_flux_d2):
+        f.argtypes = [C.c_double, _dp, _dp, _dp, _dp]
+    L.orc_flux.argtypes = [C.c_double, _dp, _dp, _dp]
+    L.orc_mesh_cartesian.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _ip]
+    L.orc_mesh_cartesian.restype = C.c_void_p
+    L.orc_mesh_cartesian_masked.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                            _ip, C.POINTER(C.c_ubyte), C.c_int]
+    L.orc_mesh_cartesian_masked.restype = C.c_void_p
+    L.orc_solver_set_inflow.argtypes = [C.c_void_p, _dp]
+    L.orc_mesh_triangles.argtypes = [C.c_int, _dp, C.c_int, _ip, _ip]
+    L.orc_mesh_triangles.restype = C.c_void_p
+    L.orc_mesh_free.argtypes = [C.c_void_p]
+    for f in (L.orc_mesh_num_elements, L.orc_mesh_num_edges, L.orc_mesh_edges_per_element):
+        f.argtypes = [C.c_void_p]
+    L.orc_mesh_geometry.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
+    L.orc_solver_new.argtypes = [C.c_void_p, C.c_int, C.c_double]
+    L.orc_solver_new.restype = C.c_void_p
+    L.orc_solver_free.argtypes = [C.c_void_p]
+    L.orc_solver_set_params.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int]
+    L.orc_solver_set_moment_exact.argtypes = [C.c_void_p, C.c_int]
+    L.orc_solver_set_llf_global.argtypes = [C.c_void_p, C.c_int]
+    L.orc_solver_set_ck_order.argtypes = [C.c_void_p, C.c_int]
+    L.orc_flux_d3.argtypes = [C.c_double, _dp, _dp, _dp, _dp]
+    L.orc_flux_d11.argtypes = [C.c_double, _dp, _dp, _dp, _dp, _dp]
+    for f in (L.orc_solver_num_modes, L.orc_solver_num_points, L.orc_projection_num_points):
+        f.argtypes = [C.c_void_p]
+    L.orc_projection_points.argtypes = [C.c_void_p, _dp]
+    L.orc_projection_weights.argtypes = [C.c_void_p, _dp]
+    L.orc_project.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_eval_projection_points.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_eval_limiter_points.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_limiter_points.argtypes = [C.c_void_p, _dp]
+    L.orc_last_fluxes.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_last_fluxes.restype = C.c_double
+    L.orc_moment_limit.argtypes = [C.c_void_p, _dp, _dp, _ip]
+    L.orc_moment_limit.restype = C.c_double
+    L.orc_wave_speed.argtypes = [C.c_void_p, _dp]
+    L.orc_wave_speed.restype = C.c_double
+    L.orc_ck_element.argtypes = [C.c_void_p, _dp, C.c_int, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_mu_solve.argtypes = [C.c_double, C.c_double, _dp, _dp]
+    L.orc_mu_solve.restype = C.c_double
+    L.orc_flux_limit_cell.argtypes = [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
+    L.orc_shock_limit.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_step.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
+    L.orc_num_threads.argtypes = []
+    L.orc_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int, _dp, _dp]
+    L.orc_mlp_loss_grad.restype = C.c_double
+    L.orc_features.argtypes = [C.c_void_p, _dp, _dp]
+    return L
 
 
 def gauss_legendre(n):

@@ -2,6 +2,8 @@
 random inputs: the moment limiter (Sec. 3.1), the mu quadratic (Sec. 3.3
 Step 5b), the positivity of every state in the final theta box (Steps 4-6)
 and the invariants of the shock-capturing limiter (Sec. 4.1)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -193,3 +195,93 @@ def test_shock_limiter_invariants(orc):
     sm = orc.Solver(orc.Mesh.cartesian(32, 32), 2, gamma=G)
     Qs = sm.project_fn(synth.ic_smooth)
     assert np.all(sm.shock_limit(Qs.copy()) == 1.0)
+
+
+def shock_tightness_failures(orc):
+    """Failures of the density-tightness pin of the shock limiter (G14, Sec.
+    4.1) for the oracle module as it is loaded now; [] when it holds."""
+    n = 8
+    alpha0 = 5.0
+    mesh = orc.Mesh.cartesian(n, n)
+    sol = orc.Solver(mesh, 2, gamma=G, alpha0=alpha0)
+    Q0 = synth.random_modal_state(mesh.N, sol.ML, seed=22, amp=0.6)
+    # in half of the cells velocity and pressure are constant over the cell
+    # (momentum and energy modes follow the density's), so there only the
+    # density can bind
+    u = Q0[:, 1, 0] / Q0[:, 0, 0]; v = Q0[:, 2, 0] / Q0[:, 0, 0]
+    half = np.arange(mesh.N) % 2 == 0
+    Q0[half, 1, 1:] = u[half, None] * Q0[half, 0, 1:]
+    Q0[half, 2, 1:] = v[half, None] * Q0[half, 0, 1:]
+    Q0[half, 3, 1:] = 0.5 * (u[half, None] ** 2 + v[half, None] ** 2) * Q0[half, 0, 1:]
+    Q = Q0.copy()
+    th = sol.shock_limit(Q)
+    alpha = alpha0 * (1.0 / n) ** 1.5
+    rb = Q0[:, 0, 0].reshape(n, n)
+    nb = np.stack([np.roll(rb, 1, 0), np.roll(rb, -1, 0), np.roll(rb, 1, 1), np.roll(rb, -1, 1)])
+    Mx = np.maximum(rb + alpha, nb.max(0)).ravel(); Mn = np.minimum(rb - alpha, nb.min(0)).ravel()
+    r0 = sol.eval_limiter_points(Q0)[..., 0]
+    rbar = Q0[:, 0, 0]
+    hx, hn = r0.max(axis=1), r0.min(axis=1)
+    th_rho = np.ones(mesh.N)
+    up, dn = hx > rbar, hn < rbar
+    th_rho[up] = np.minimum(th_rho[up], (Mx[up] - rbar[up]) / (hx[up] - rbar[up]))
+    th_rho[dn] = np.minimum(th_rho[dn], (rbar[dn] - Mn[dn]) / (rbar[dn] - hn[dn]))
+    th_rho = np.clip(th_rho, 0.0, 1.0)
+    out = []
+    if not np.all(th <= th_rho + 1e-14):
+        out.append("theta above the density's ratio")
+    # cells where only the density varies (and stays positive at every
+    # point): theta is the density's ratio, and the limited density reaches
+    # its bound at the extreme point
+    binding = half & (th_rho < 1.0) & (r0.min(axis=1) > 0.0)
+    if binding.sum() < 3:
+        out.append("fewer than 3 density-bound cells")
+    if binding.any() and np.abs(th[binding] - th_rho[binding]).max() > 1e-13:
+        out.append("theta differs from the density's ratio by %.2e" % np.abs(th[binding] - th_rho[binding]).max())
+    r = sol.eval_limiter_points(Q)[..., 0]
+    gap = np.minimum(np.abs(r.max(axis=1) - Mx), np.abs(r.min(axis=1) - Mn))
+    if binding.any() and gap[binding].max() > 1e-12:
+        out.append("over-limited: the limited density stays %.2e inside its bound" % gap[binding].max())
+    if not np.allclose(Q[:, :, 1:], th[:, None, None] * Q0[:, :, 1:], rtol=1e-15, atol=0):
+        out.append("the higher modes are not scaled by theta")
+    return out
+
+
+def test_shock_limiter_is_tight_on_the_density(orc):
+    """G14 takes theta_sc as the smallest of four ratios, one per primitive;
+    the density is linear in theta, so where only its ratio binds the limited
+    density reaches its bound exactly at the extreme point (no
+    over-limiting), and theta_sc never exceeds the density's ratio."""
+    assert shock_tightness_failures(orc) == []
+
+
+SHOCK_MUTANTS = {
+    # half the theta
+    "half_theta": ("  if (th < 0.0) th = 0.0;\n  return th;", "  if (th < 0.0) th = 0.0;\n  return 0.5 * th;"),
+    # bounds from the cell alone (the neighbours' averages ignored)
+    "no_neighbours": ("    if (!(qj[0] > 0.0)) continue;\n    double wj[4];",
+                      "    if (1) continue;\n    double wj[4];"),
+    # bounds without alpha
+    "no_alpha": ("  for (int c = 0; c < 4; ++c) { Mx[c] = wbar[c] + alpha; Mn[c] = wbar[c] - alpha; }",
+                 "  for (int c = 0; c < 4; ++c) { Mx[c] = wbar[c]; Mn[c] = wbar[c]; }"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SHOCK_MUTANTS))
+def test_over_limiting_shock_variants_fail_the_pin(orc, name):
+    """A planted over-limiting mistake in the oracle's shock limiter (built
+    here from its source with one line changed) fails the tightness pin."""
+    import subprocess
+    import tempfile
+    src_path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "lxw_oracle.c")
+    old, new = SHOCK_MUTANTS[name]
+    src = open(src_path).read()
+    assert src.count(old) == 1, name
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, name + ".c")
+        open(path, "w").write(src.replace(old, new))
+        so = os.path.join(tmp, name + ".so")
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=gnu11", "-I",
+                        os.path.dirname(src_path), "-o", so, path, "-lm"], check=True, capture_output=True)
+        with orc.use_library(so):
+            assert shock_tightness_failures(orc) != []
