@@ -11,15 +11,15 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lxw_oracle.c")
+SRCS = [SRC, os.path.join(HERE, "lxw_oracle3d.c")]
+HDRS = [os.path.join(HERE, "lxw_oracle.h"), os.path.join(HERE, "lxw_oracle3d.h")]
 LIB = os.path.join(HERE, "liblxw_oracle.so")
 
 
 def build(force: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "lxw_oracle.h"))
-    ):
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in SRCS + HDRS):
         return LIB
-    base = ["gcc", "-O3", "-fPIC", "-shared", "-ffp-contract=off", "-std=gnu11", "-o", LIB + ".tmp", SRC, "-lm"]
+    base = ["gcc", "-O3", "-fPIC", "-shared", "-ffp-contract=off", "-std=gnu11", "-o", LIB + ".tmp"] + SRCS + ["-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:

@@ -105,6 +105,40 @@ def _configure(L):
     L.orc_mlp_loss_grad.argtypes = [_dp, _dp, _dp, C.c_int, _dp, _dp]
     L.orc_mlp_loss_grad.restype = C.c_double
     L.orc_features.argtypes = [C.c_void_p, _dp, _dp]
+    if hasattr(L, "orc3_step"):   # the 3D Cartesian oracle (a planted 2D variant may lack it)
+        L.orc3_mode_exponents.argtypes = [C.c_int, _ip]
+        L.orc3_basis_eval.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc3_flux.argtypes = [C.c_double, _dp, _dp]
+        L.orc3_flux_series.argtypes = [C.c_double, C.c_int, _dp, _dp]
+        L.orc3_mesh_cartesian.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _ip]
+        L.orc3_mesh_cartesian.restype = C.c_void_p
+        L.orc3_mesh_free.argtypes = [C.c_void_p]
+        L.orc3_mesh_num_elements.argtypes = [C.c_void_p]
+        L.orc3_mesh_geometry.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
+        L.orc3_solver_new.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.orc3_solver_new.restype = C.c_void_p
+        L.orc3_solver_free.argtypes = [C.c_void_p]
+        L.orc3_solver_set_params.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_int]
+        L.orc3_solver_set_llf_global.argtypes = [C.c_void_p, C.c_int]
+        for f in (L.orc3_solver_num_modes, L.orc3_solver_num_points, L.orc3_projection_num_points):
+            f.argtypes = [C.c_void_p]
+        for f in (L.orc3_projection_points, L.orc3_projection_weights, L.orc3_limiter_points):
+            f.argtypes = [C.c_void_p, _dp]
+        for f in (L.orc3_project, L.orc3_eval_projection_points, L.orc3_eval_limiter_points):
+            f.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc3_moment_limit.argtypes = [C.c_void_p, _dp, _dp, _ip]
+        L.orc3_moment_limit.restype = C.c_double
+        L.orc3_wave_speed.argtypes = [C.c_void_p, _dp]
+        L.orc3_wave_speed.restype = C.c_double
+        L.orc3_ck_element.argtypes = [C.c_void_p, _dp, C.c_int, C.c_double, _dp, _dp, _dp, _dp, _dp]
+        L.orc3_flux_limit_cell.argtypes = [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp,
+                                           _dp]
+        L.orc3_mu_solve.argtypes = [C.c_double, C.c_double, _dp, _dp]
+        L.orc3_mu_solve.restype = C.c_double
+        L.orc3_shock_limit.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc3_step.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp, _dp, _dp, _dp]
+        L.orc3_last_fluxes.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc3_last_fluxes.restype = C.c_double
     return L
 
 
@@ -355,4 +389,169 @@ class Solver:
         d["status"] = int(d["status"])
         if want_theta:
             d.update(theta_mom=tm, theta_sc=ts, theta_edge=te)
+        return d
+
+
+# ---------------------------------------------------------------- 3D Cartesian
+DIAG3_KEYS = ["s", "dt", "min_rho", "min_p", "mass", "momx", "momy", "momz", "energy",
+              "n_mom", "n_face", "n_sc", "status"]
+
+
+def mode_exponents3(deg):
+    """(a, b, c) of each 3D mode, in the state's order."""
+    n = (deg + 1) * (deg + 2) * (deg + 3) // 6
+    abc = np.zeros(3 * n, dtype=np.int32)
+    lib().orc3_mode_exponents(deg, _i(abc))
+    return abc.reshape(n, 3)
+
+
+def basis_eval3(deg, xi, eta, zeta):
+    xi, eta, zeta = (np.ascontiguousarray(a, dtype=np.float64) for a in (xi, eta, zeta))
+    n = (deg + 1) * (deg + 2) * (deg + 3) // 6
+    out = [np.zeros((len(xi), n)) for _ in range(4)]
+    lib().orc3_basis_eval(deg, len(xi), _d(xi), _d(eta), _d(zeta), *[_d(o) for o in out])
+    return out
+
+
+def flux3(gamma, q):
+    F = np.zeros((3, 5))
+    lib().orc3_flux(gamma, _d(np.ascontiguousarray(q, dtype=np.float64)), _d(F))
+    return F
+
+
+def flux_series3(gamma, qs):
+    """Taylor coefficients [K+1][3][5] of F(sum_k qs[k] t^k)."""
+    qs = np.ascontiguousarray(qs, dtype=np.float64)
+    Fs = np.zeros((qs.shape[0], 3, 5))
+    lib().orc3_flux_series(gamma, qs.shape[0] - 1, _d(qs), _d(Fs))
+    return Fs
+
+
+def flux_limit_cell3(gamma, eps0, vol, dt, qbar, fW, fF):
+    fW = np.ascontiguousarray(fW, dtype=np.float64); fF = np.ascontiguousarray(fF, dtype=np.float64)
+    prop = np.zeros(fW.shape[0])
+    bad = lib().orc3_flux_limit_cell(gamma, eps0, fW.shape[0], vol, dt,
+                                     _d(np.ascontiguousarray(qbar, dtype=np.float64)), _d(fW), _d(fF), _d(prop))
+    return prop, bad
+
+
+class Mesh3:
+    """Cartesian nx x ny x nz mesh of box = (x0, x1, y0, y1, z0, z1); bc per
+    side (x-, x+, y-, y+, z-, z+): 0 periodic, 1 reflective, 2 transparent."""
+
+    def __init__(self, nx, ny, nz, box=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0), bc=(0,) * 6):
+        b = np.ascontiguousarray(box, dtype=np.float64)
+        c = np.ascontiguousarray(bc, dtype=np.int32)
+        self.ptr = lib().orc3_mesh_cartesian(nx, ny, nz, _d(b), _i(c))
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.N = lib().orc3_mesh_num_elements(self.ptr)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.orc3_mesh_free(self.ptr)
+            self.ptr = None
+
+    def geometry(self):
+        vol, cx, cy, cz = (np.zeros(self.N) for _ in range(4))
+        lib().orc3_mesh_geometry(self.ptr, _d(vol), _d(cx), _d(cy), _d(cz))
+        return vol, cx, cy, cz
+
+
+class Solver3:
+    def __init__(self, mesh, deg, gamma=1.4, eps0=1e-12, alpha0=500.0, shock_limiter=True, llf_global=False):
+        self.mesh = mesh
+        self.ptr = lib().orc3_solver_new(mesh.ptr, deg, gamma)
+        if not self.ptr:
+            raise ValueError("oracle solver construction failed")
+        lib().orc3_solver_set_params(self.ptr, eps0, alpha0, int(bool(shock_limiter)))
+        lib().orc3_solver_set_llf_global(self.ptr, int(bool(llf_global)))
+        self.gamma, self.deg, self.N = gamma, deg, mesh.N
+        self.ML = lib().orc3_solver_num_modes(self.ptr)
+        self.npts = lib().orc3_solver_num_points(self.ptr)
+        self.nproj = lib().orc3_projection_num_points(self.ptr)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.orc3_solver_free(self.ptr)
+            self.ptr = None
+
+    def new_state(self):
+        return np.zeros((self.N, 5, self.ML))
+
+    def projection_points(self):
+        xyz = np.zeros((self.N, self.nproj, 3))
+        lib().orc3_projection_points(self.ptr, _d(xyz))
+        return xyz
+
+    def projection_weights(self):
+        w = np.zeros(self.nproj)
+        lib().orc3_projection_weights(self.ptr, _d(w))
+        return w
+
+    def project(self, prim):
+        prim = np.ascontiguousarray(prim, dtype=np.float64)
+        assert prim.shape == (self.N, self.nproj, 5)
+        Q = self.new_state()
+        lib().orc3_project(self.ptr, _d(prim), _d(Q))
+        return Q
+
+    def project_fn(self, fn):
+        """Project fn(x, y, z) -> (rho, u, v, w, p)."""
+        xyz = self.projection_points()
+        vals = fn(xyz[..., 0], xyz[..., 1], xyz[..., 2])
+        return self.project(np.stack(np.broadcast_arrays(*vals), axis=-1))
+
+    def eval_projection_points(self, Q):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        q = np.zeros((self.N, self.nproj, 5))
+        lib().orc3_eval_projection_points(self.ptr, _d(Q), _d(q))
+        return q
+
+    def limiter_points(self):
+        xyz = np.zeros((self.N, self.npts, 3))
+        lib().orc3_limiter_points(self.ptr, _d(xyz))
+        return xyz
+
+    def eval_limiter_points(self, Q):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        q = np.zeros((self.N, self.npts, 5))
+        lib().orc3_eval_limiter_points(self.ptr, _d(Q), _d(q))
+        return q
+
+    def moment_limit(self, Q):
+        th = np.zeros(self.N); st = C.c_int(0)
+        lib().orc3_moment_limit(self.ptr, _d(Q), _d(th), C.byref(st))
+        return th, st.value
+
+    def wave_speed(self, Q):
+        return lib().orc3_wave_speed(self.ptr, _d(np.ascontiguousarray(Q, dtype=np.float64)))
+
+    def ck_element(self, Q, i, dt):
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        q, qt, qtt = (np.zeros((self.npts, 5)) for _ in range(3))
+        FT = np.zeros((self.npts, 3, 5)); V = np.zeros((self.ML, 5))
+        lib().orc3_ck_element(self.ptr, _d(Q), i, dt, _d(q), _d(qt), _d(qtt), _d(FT), _d(V))
+        return dict(q=q, qt=qt, qtt=qtt, FT=FT, V=V)
+
+    def shock_limit(self, Q):
+        th = np.zeros(self.N)
+        lib().orc3_shock_limit(self.ptr, _d(Q), _d(th))
+        return th
+
+    def last_fluxes(self):
+        fw = np.zeros((self.N, 6, 5)); ff = np.zeros((self.N, 6, 5))
+        dt = lib().orc3_last_fluxes(self.ptr, _d(fw), _d(ff))
+        return fw, ff, dt
+
+    def step(self, Q, dt=0.0, cfl=0.1, want_theta=False):
+        assert Q.dtype == np.float64 and Q.flags.c_contiguous and Q.shape == (self.N, 5, self.ML)
+        diag = np.zeros(16)
+        tm = ts = tf = None
+        if want_theta:
+            tm = np.zeros(self.N); ts = np.zeros(self.N); tf = np.zeros((self.N, 6))
+        lib().orc3_step(self.ptr, _d(Q), dt, cfl, _d(diag), _d(tm), _d(ts), _d(tf))
+        d = {k: diag[i] for i, k in enumerate(DIAG3_KEYS)}
+        d["status"] = int(d["status"])
+        if want_theta:
+            d.update(theta_mom=tm, theta_sc=ts, theta_face=tf)
         return d

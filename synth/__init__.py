@@ -161,6 +161,24 @@ def random_modal_state(N: int, ML: int, seed: int, amp: float = 0.3, gamma: floa
     return Q
 
 
+def random_modal_state3(N: int, ML: int, seed: int, amp: float = 0.3, gamma: float = GAMMA,
+                        rho_range=(0.5, 2.0), p_range=(0.2, 2.0)):
+    """Random modal coefficients Q[N][5][ML] of 3D cells, (rho, rho u, rho v,
+    rho w, E), built like random_modal_state: random primitive averages, every
+    higher coefficient U[-amp, amp] times its variable's average magnitude."""
+    r = uniform01(seed, N * (5 + 5 * ML)).reshape(N, 5 + 5 * ML)
+    rho = rho_range[0] + (rho_range[1] - rho_range[0]) * r[:, 0]
+    u, v, w = (-1.0 + 2.0 * r[:, k] for k in (1, 2, 3))
+    p = p_range[0] + (p_range[1] - p_range[0]) * r[:, 4]
+    avg = np.stack([rho, rho * u, rho * v, rho * w, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)], axis=1)
+    Q = np.zeros((N, 5, ML))
+    Q[:, :, 0] = avg
+    scale = np.abs(avg) + 0.1 * np.abs(avg[:, :1])
+    hi = (2.0 * r[:, 5:].reshape(N, 5, ML) - 1.0) * amp
+    Q[:, :, 1:] = hi[:, :, 1:] * scale[:, :, None]
+    return Q
+
+
 # ------------------------------------------------ shock diffraction over a step
 def normal_shock_state(mach, rho0=1.4, p0=1.0, gamma=1.4):
     """Primitive state (rho, u, v, p) behind a normal shock of the given Mach

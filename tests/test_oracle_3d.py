@@ -1,0 +1,276 @@
+"""Pins of the 3D Cartesian oracle (the extension the paper says carries
+over directly: end of Sec. 3.3, the 3D Euler equations of Sec. 1.1).
+
+None of the expected values comes from the 3D oracle itself:
+
+* Basis: orthonormal under (1/8) Int over the reference cube (a finer Gauss
+  rule), gradients against central differences.
+* Flux and its Taylor series: coefficient 1 along w is F'(q) w, twice
+  coefficient 2 along q + t a + t^2 b / 2 is F''(q)(a, a) + F'(q) b --
+  against finite differences and, for states without z motion, against the
+  2D oracle's hand-derived Jacobians (an independent implementation).
+* Flux limiter with E faces: with four faces and no z momentum it is the 2D
+  oracle's cell limiter bit for bit; with six faces and 63 corners it is
+  tight: where Lambda < 1 the corner of all negative faces lands on the
+  density floor, where a face was cut the lowest corner lands on the
+  pressure floor, and no corner goes below it.
+* A z-invariant problem (one periodic cell in z, no z velocity) takes the 2D
+  oracle's step mode for mode, with the moment and shock limiters active.
+* Free stream, conservation on periodic meshes, walls, positivity.
+* Third order in space and time on a smooth 3D advection.
+"""
+import numpy as np
+import numpy.polynomial.legendre as npleg
+import pytest
+
+import synth
+
+G = 1.4
+
+
+def test_basis_orthonormal_and_gradients(orc):
+    for deg in (1, 2, 3):
+        x, w = npleg.leggauss(deg + 2)
+        X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+        W = (w[:, None, None] * w[None, :, None] * w[None, None, :]).ravel() / 8.0
+        phi, dx, dy, dz = orc.basis_eval3(deg, X.ravel(), Y.ravel(), Z.ravel())
+        M = phi.T @ (W[:, None] * phi)
+        assert np.allclose(M, np.eye(phi.shape[1]), atol=1e-13)
+        rng = np.random.default_rng(deg)
+        p = rng.uniform(-0.9, 0.9, (7, 3))
+        h = 1e-6
+        for d, D in enumerate((dx, dy, dz)):
+            e = np.zeros(3); e[d] = h
+            fp = orc.basis_eval3(deg, *(p + e).T)[0]
+            fm = orc.basis_eval3(deg, *(p - e).T)[0]
+            Dp = orc.basis_eval3(deg, *p.T)[1 + d]
+            assert np.allclose(Dp, (fp - fm) / (2 * h), atol=1e-7)
+    abc = orc.mode_exponents3(2)
+    assert abc.shape == (10, 3) and np.all(abc.sum(axis=1) <= 2) and len({tuple(r) for r in abc}) == 10
+
+
+def _state(rng):
+    rho, p = rng.uniform(0.5, 2.0), rng.uniform(0.3, 2.0)
+    u = rng.uniform(-1, 1, 3)
+    return np.array([rho, *(rho * u), p / (G - 1) + 0.5 * rho * (u @ u)])
+
+
+def test_flux_series_is_the_flux_derivatives(orc):
+    rng = np.random.default_rng(3)
+    for _ in range(8):
+        q = _state(rng)
+        a = rng.normal(size=5) * np.abs(q) * 0.3
+        b = rng.normal(size=5) * np.abs(q) * 0.3
+        Fs = orc.flux_series3(G, np.stack([q, a, 0.5 * b]))
+        assert np.allclose(Fs[0], orc.flux3(G, q), rtol=1e-14, atol=1e-14)
+        # coefficient 1: F'(q) a by central differences
+        h = 1e-6
+        d1 = (orc.flux3(G, q + h * a) - orc.flux3(G, q - h * a)) / (2 * h)
+        assert np.allclose(Fs[1], d1, rtol=1e-7, atol=1e-8)
+        # twice coefficient 2 of the curve q(t) = q + t a + t^2 b / 2 is the second derivative of F(q(t))
+        h = 1e-3
+        qc = lambda t: q + t * a + 0.5 * t * t * b   # noqa: E731
+        d2 = (orc.flux3(G, qc(h)) - 2 * orc.flux3(G, q) + orc.flux3(G, qc(-h))) / (h * h)
+        sc = 1 + np.abs(d2).max()
+        assert np.allclose(2 * Fs[2], d2, atol=1e-5 * sc)
+        # no z motion: the x and y fluxes and their derivatives are the 2D oracle's
+        q2 = np.array([q[0], q[1], q[2], q[4] - 0.5 * q[3] ** 2 / q[0]])
+        a2 = np.array([a[0], a[1], a[2], a[4]])
+        q3 = np.array([q2[0], q2[1], q2[2], 0.0, q2[3]])
+        a3 = np.array([a2[0], a2[1], a2[2], 0.0, a2[3]])
+        F, Gf = orc.flux(G, q2)
+        F1, G1 = orc.flux_d1(G, q2, a2)
+        F2, G2 = orc.flux_d2(G, q2, a2)
+        S = orc.flux_series3(G, np.stack([q3, a3, np.zeros(5)]))
+        for d, (A, A1, A2) in enumerate(((F, F1, F2), (Gf, G1, G2))):
+            idx = [0, 1, 2, 4]
+            assert np.allclose(S[0][d][idx], A, rtol=1e-14, atol=1e-14)
+            assert np.allclose(S[1][d][idx], A1, rtol=1e-13, atol=1e-13)
+            assert np.allclose(2 * S[2][d][idx], A2, rtol=1e-12, atol=1e-12)
+            assert abs(S[1][d][3]) < 1e-14 and abs(S[2][d][3]) < 1e-14
+
+
+def test_flux_limiter_four_faces_is_the_2d_limiter(orc):
+    rng = np.random.default_rng(5)
+    for trial in range(200):
+        q2 = np.array([rng.uniform(0.01, 2), rng.uniform(-1, 1), rng.uniform(-1, 1), 0.0])
+        q2[3] = rng.uniform(0.001, 2) / (G - 1) + 0.5 * (q2[1] ** 2 + q2[2] ** 2) / q2[0]
+        T, dt = 1.0, rng.uniform(0.05, 0.6)
+        fW = rng.normal(size=(4, 4)) * 0.5
+        fF = fW + rng.normal(size=(4, 4)) * 0.5
+        p2, b2 = orc.flux_limit_cell(G, 1e-3, T, dt, q2, fW, fF)
+        lift = lambda a: np.insert(a, 3, 0.0, axis=-1)   # noqa: E731
+        p3, b3 = orc.flux_limit_cell3(G, 1e-3, T, dt, lift(q2), lift(fW), lift(fF))
+        assert b2 == b3
+        assert np.array_equal(p2, p3), trial
+
+
+def _pressure3(q):
+    return (G - 1) * (q[..., 4] - 0.5 * (q[..., 1] ** 2 + q[..., 2] ** 2 + q[..., 3] ** 2) / q[..., 0])
+
+
+def _cells6(count, seed, which):
+    """Random cells with six faces whose Lax-Friedrichs state is a valid
+    state; "density": the fluxes differ only in density (energy raised so
+    that only the density limits); "pressure": same density fluxes (Lambda
+    = 1), so only the pressure limits."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for trial in range(count):
+        qbar = synth.random_modal_state3(1, 1, seed=seed * 1000 + trial, rho_range=(0.01, 2.0),
+                                         p_range=(1e-3, 2.0))[0, :, 0]
+        T, dt = rng.uniform(0.5, 2.0), rng.uniform(0.05, 0.3)
+        qlxf = synth.random_modal_state3(1, 1, seed=seed * 7000 + trial, rho_range=(1e-4, 1.0),
+                                         p_range=(1e-5, 1.0))[0, :, 0]
+        if which == "density":
+            qbar = qbar.copy(); qbar[4] += 1e4; qlxf = qlxf.copy(); qlxf[4] += 1e4
+        fF = rng.normal(size=(6, 5))
+        fF += ((qbar - qlxf) * T / dt - fF.sum(0)) / 6
+        fW = fF + rng.normal(size=(6, 5)) * np.abs(qbar) * T / dt * rng.uniform(0.05, 1.0)
+        if which == "density":
+            fW[:, 1:] = fF[:, 1:]
+        else:
+            fW[:, 0] = fF[:, 0]
+        out.append((T, dt, qbar, fW, fF))
+    return out
+
+
+def test_flux_limiter_six_faces_is_tight(orc):
+    """Six faces, 63 corners.  Density: where Lambda is in (0, 1) the corner
+    taking every negative face at its proposal has exactly the floor density
+    min(eps0, rho^LxF / 2).  Pressure: every corner of the final box keeps p
+    at the floor min(eps0, p^LxF / 2) or above, and where a face was cut the
+    lowest corner sits on it."""
+    eps0 = 1e-3
+    corner = lambda qbar, T, dt, fW, fF, al: qbar - dt / T * (al @ fW + (1.0 - al) @ fF)   # noqa: E731
+    hits = 0
+    for (T, dt, qbar, fW, fF) in _cells6(200, 17, "density"):
+        prop, bad = orc.flux_limit_cell3(G, eps0, T, dt, qbar, fW, fF)
+        neg = fF[:, 0] - fW[:, 0] < 0
+        if bad or not neg.any() or not (0.0 < prop[neg].max() < 1.0):
+            continue
+        hits += 1
+        floor = min(eps0, 0.5 * corner(qbar, T, dt, fW, fF, np.zeros(6))[0])
+        rho_c = corner(qbar, T, dt, fW, fF, np.where(neg, prop, 0.0))[0]
+        assert abs(rho_c - floor) <= 1e-12 * (abs(qbar[0]) + dt / T * np.abs(fW[:, 0]).sum())
+    assert hits >= 50
+    corners = np.array([[(c >> k) & 1 for k in range(6)] for c in range(64)], dtype=float)
+    hits = 0
+    for (T, dt, qbar, fW, fF) in _cells6(300, 47, "pressure"):
+        q_lxf = corner(qbar, T, dt, fW, fF, np.zeros(6))
+        if not (q_lxf[0] > 0 and _pressure3(q_lxf) > 0):
+            continue
+        prop, bad = orc.flux_limit_cell3(G, eps0, T, dt, qbar, fW, fF)
+        floor = min(eps0, 0.5 * _pressure3(q_lxf))
+        qc = np.array([corner(qbar, T, dt, fW, fF, c * prop) for c in corners])
+        pmin = _pressure3(qc).min()
+        tol = 1e-11 * (abs(qbar[4]) + dt / T * np.abs(fW[:, 4]).sum())
+        assert pmin >= floor - tol
+        if 0.0 < prop.min() < 1.0:
+            hits += 1
+            assert abs(pmin - floor) <= tol
+    assert hits >= 30
+
+
+def _lift_2d(Q2, deg, orc):
+    """2D quadrilateral modes (rho, mx, my, E) -> 3D modes with no z
+    dependence and no z momentum."""
+    A2 = np.array([[0, 0], [1, 0], [0, 1], [1, 1], [2, 0], [0, 2], [3, 0], [2, 1], [1, 2], [0, 3]])[:Q2.shape[2]]
+    abc = orc.mode_exponents3(deg)
+    Q3 = np.zeros((Q2.shape[0], 5, len(abc)))
+    for l2, (a, b) in enumerate(A2):
+        l3 = int(np.where((abc[:, 0] == a) & (abc[:, 1] == b) & (abc[:, 2] == 0))[0][0])
+        Q3[:, [0, 1, 2, 4], l3] = Q2[:, :, l2]
+    return Q3
+
+
+@pytest.mark.parametrize("deg", [1, 2, 3])
+def test_z_invariant_problem_is_the_2d_step(orc, deg):
+    """One periodic cell in z, no z velocity, random data with the moment and
+    shock limiters acting: every step equals the 2D oracle's, mode for mode
+    (the 3D quadrature only adds exact sums along z)."""
+    nx, ny = 7, 5
+    h = 1.0 / 7
+    # cubic cells: the shock limiter's alpha uses the side of the cell in both
+    s2 = orc.Solver(orc.Mesh.cartesian(nx, ny, (0.0, 1.0, 0.0, ny * h), (2, 1, 0, 0)), deg, gamma=G, alpha0=50.0)
+    s3 = orc.Solver3(orc.Mesh3(nx, ny, 1, (0.0, 1.0, 0.0, ny * h, 0.0, h), (2, 1, 0, 0, 0, 0)), deg, gamma=G,
+                     alpha0=50.0)
+    Q2 = synth.random_modal_state(nx * ny, s2.ML, seed=40 + deg, amp=0.25, rho_range=(0.05, 2.0), p_range=(0.02, 2.0))
+    Q3 = _lift_2d(Q2, deg, orc)
+    acted = 0
+    for k in range(4):
+        d2 = s2.step(Q2, dt=2e-3)
+        d3 = s3.step(Q3, dt=2e-3)
+        assert d2["n_edge"] == 0 and d3["n_face"] == 0      # no flux limiting (see the module notes)
+        acted += d2["n_mom"] + d2["n_sc"]
+        assert d3["n_mom"] == d2["n_mom"] and d3["n_sc"] == d2["n_sc"]
+        L2 = _lift_2d(Q2, deg, orc)
+        assert np.allclose(Q3, L2, rtol=1e-12, atol=1e-12 * np.abs(L2).max()), k
+    assert acted > 0
+
+
+def test_free_stream_conservation_and_walls(orc):
+    # a uniform state is kept on a periodic mesh
+    s = orc.Solver3(orc.Mesh3(4, 3, 5), 2, gamma=G)
+    Q = s.project_fn(lambda x, y, z: (1.3 + 0 * x, 0.4 + 0 * x, -0.2 + 0 * x, 0.7 + 0 * x, 0.9 + 0 * x))
+    Q0 = Q.copy()
+    for _ in range(3):
+        s.step(Q, cfl=0.3)
+    assert np.allclose(Q, Q0, atol=1e-13)
+    # random data with every limiter acting: totals conserved, states positive
+    m = orc.Mesh3(5, 4, 3)
+    s = orc.Solver3(m, 2, gamma=G, alpha0=50.0)
+    Q = synth.random_modal_state3(m.N, s.ML, seed=11, amp=0.3, rho_range=(0.02, 2.0), p_range=(0.01, 2.0))
+    vol = m.geometry()[0]
+    tot0 = (vol[:, None] * Q[:, :, 0]).sum(axis=0)
+    acted = 0
+    for _ in range(6):
+        d = s.step(Q, cfl=0.4)
+        assert d["status"] == 0 and d["min_rho"] > 0 and d["min_p"] > 0
+        acted += d["n_mom"] + d["n_face"] + d["n_sc"]
+    tot = (vol[:, None] * Q[:, :, 0]).sum(axis=0)
+    assert np.allclose(tot, tot0, rtol=1e-13, atol=1e-13) and acted > 0
+    # reflective walls on every side: mass and energy conserved, rest stays at rest
+    m = orc.Mesh3(4, 4, 4, bc=(1,) * 6)
+    s = orc.Solver3(m, 2, gamma=G)
+    Q = s.project_fn(lambda x, y, z: (1.0 + 0.3 * np.exp(-20 * ((x - .5) ** 2 + (y - .5) ** 2 + (z - .5) ** 2)),
+                                      0 * x, 0 * x, 0 * x, 1.0 + 0 * x))
+    vol = m.geometry()[0]
+    t0 = (vol[:, None] * Q[:, :, 0]).sum(axis=0)
+    for _ in range(5):
+        s.step(Q, cfl=0.3)
+    t1 = (vol[:, None] * Q[:, :, 0]).sum(axis=0)
+    assert abs(t1[0] - t0[0]) < 1e-13 and abs(t1[4] - t0[4]) < 1e-12
+    rest = orc.Solver3(m, 2, gamma=G)
+    Qr = rest.project_fn(lambda x, y, z: (1.0 + 0 * x, 0 * x, 0 * x, 0 * x, 1.0 + 0 * x))
+    Qr0 = Qr.copy()
+    rest.step(Qr, cfl=0.3)
+    assert np.allclose(Qr, Qr0, atol=1e-14)
+
+
+def test_smooth_advection_third_order(orc):
+    """rho = 1 + 0.2 sin 2 pi (x + y + z), u = (1, 0.5, 0.25), p = 1 on the
+    periodic unit cube to t = 0.04 (CFL 0.2, the last step shortened): the L2
+    error of the density falls at third order."""
+    U = np.array([1.0, 0.5, 0.25])
+    ex = lambda x, y, z, t: 1 + 0.2 * np.sin(2 * np.pi * ((x - U[0] * t) + (y - U[1] * t) + (z - U[2] * t)))  # noqa: E731
+    T = 0.04
+    errs, ns = [], (6, 9, 12)
+    for n in ns:
+        m = orc.Mesh3(n, n, n)
+        s = orc.Solver3(m, 2, gamma=G)
+        Q = s.project_fn(lambda x, y, z: (ex(x, y, z, 0.0), U[0] + 0 * x, U[1] + 0 * x, U[2] + 0 * x, 1.0 + 0 * x))
+        t = 0.0
+        while True:
+            Qc = Q.copy()
+            d = s.step(Qc, cfl=0.2)
+            if t + d["dt"] >= T:
+                s.step(Q, dt=T - t)
+                break
+            Q[...] = Qc
+            t += d["dt"]
+        xyz = s.projection_points(); w = s.projection_weights(); vol = m.geometry()[0]
+        q = s.eval_projection_points(Q)[..., 0]
+        errs.append(np.sqrt(np.sum(vol[:, None] * w[None, :] * (q - ex(xyz[..., 0], xyz[..., 1], xyz[..., 2], T)) ** 2)))
+    orders = [np.log(a / b) / np.log(nb / na) for a, b, na, nb in zip(errs[:-1], errs[1:], ns[:-1], ns[1:])]
+    assert min(orders) >= 2.75, (errs, orders)
