@@ -454,6 +454,64 @@ lxw_status lxw_moment_limit_noalloc(int kind, int degree, int n_elements, double
                                     double* Q_dev, double* theta_dev, double* s_dev, unsigned int* status_dev,
                                     void* stream);
 
+/* ------------------------------------------------------------------ */
+/* 3D Cartesian meshes (hexahedra), FP64: the same step on box cells with  */
+/* six faces (the extension the end of Sec. 3.3 says carries over         */
+/* directly; the 3D Euler equations of Sec. 1.1 with a third flux H).      */
+/* State Q[N][5][ML] (rho, rho u, rho v, rho w, E), ML = 4 (P1) or 10      */
+/* (P2); cell (ix, iy, iz) is element (iz ny + iy) nx + ix; modes           */
+/* L_a(xi) L_b(eta) L_c(zeta), L_n = sqrt(2n+1) P_n, a + b + c <= degree,  */
+/* ordered by total degree, then a descending, then b descending (the     */
+/* cell average is mode 0).  Faces and sides are ordered x-, x+, y-, y+,   */
+/* z-, z+.  Readings beyond the 2D step: dt = cfl * hmin / s with hmin =    */
+/* 3 |K| / |dK| (half the cell side, as in 2D); the shock limiter's alpha  */
+/* = alpha0 * (|K|^(1/3))^1.5; the flux limiter gives every face with a     */
+/* negative density difference the same Lambda and takes mu over the 63    */
+/* corners of the box of the six proposals.                                */
+/* ------------------------------------------------------------------ */
+typedef struct lxw_solver3 lxw_solver3;
+
+typedef struct {
+  double s, dt;               /* global wave speed and time step of the step       */
+  double min_rho, min_p;      /* minimum cell-average density / pressure after it  */
+  double mass, momx, momy, momz, energy;   /* sum_i |K_i| Q^(1)_i after the step   */
+  double n_mom;               /* cells with moment-limiter theta < 1                */
+  double n_face;              /* faces with flux-limiter theta < 1                  */
+  double n_sc;                /* cells with shock-limiter theta < 1                 */
+  int status;                 /* LXW_ST_* bits of the step                          */
+  int reserved;
+} lxw_diag3;
+
+/* nx x ny x nz cells of box = (x0, x1, y0, y1, z0, z1); bc[6] per side:
+ * LXW_BC_PERIODIC (paired on both sides of an axis), LXW_BC_REFLECT or
+ * LXW_BC_TRANSPARENT.  degree 1 or 2.  Options: gamma, eps0, alpha0,
+ * shock_limiter, llf_global, block_threads; precision must be
+ * LXW_PREC_FP64, moment_exact 0 and ck_order 3 (or 0).  Allocates the
+ * workspace (about (60 NF + 90) doubles per cell, NF = (degree + 1)^2).
+ * Errors: LXW_ERR_ARG, LXW_ERR_NOMEM, LXW_ERR_CUDA. */
+lxw_status lxw3_solver_create(int nx, int ny, int nz, const double box[6], const int bc[6], int degree,
+                              const lxw_options* opt, void* stream, lxw_solver3** out);
+void lxw3_solver_destroy(lxw_solver3* s);
+/* cells, modes per variable, projection points per cell (nullable outputs) */
+lxw_status lxw3_solver_info(const lxw_solver3* s, int* n_elements, int* n_modes, int* n_proj_points);
+/* physical coordinates xyz_host[N][NPJ][3] of the projection points */
+lxw_status lxw3_projection_points(const lxw_solver3* s, double* xyz_host);
+/* Q_dev[N][5][ML] = L2 projection of prim_dev[N][NPJ][5] = (rho, u, v, w, p) */
+lxw_status lxw3_project(lxw_solver3* s, const double* prim_dev, double* Q_dev);
+/* One step in place (dt > 0 fixes dt, else dt = cfl * hmin / s); fills
+ * diag_host (nullable), theta_face_dev[N][6] (nullable); synchronises.
+ * Returns LXW_ERR_NONPOSITIVE / LXW_ERR_CFL / LXW_ERR_NAN from the step's
+ * status bits (the step itself completes). */
+lxw_status lxw3_step(lxw_solver3* s, double* Q_dev, double dt, double cfl, lxw_diag3* diag_host,
+                     double* theta_face_dev);
+/* nsteps CFL steps: the first nsteps - 1 replay one captured CUDA graph (no
+ * host synchronisation), the last runs as lxw3_step and reports. */
+lxw_status lxw3_run(lxw_solver3* s, double* Q_dev, int nsteps, double cfl, lxw_diag3* diag_host);
+/* one step timed per phase: ms[5] = moment, ck, face, update, shock */
+lxw_status lxw3_profile_step(lxw_solver3* s, double* Q_dev, double cfl, float* ms);
+/* kernel launches of one step without diagnostics */
+int lxw3_step_launches(const lxw_solver3* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "lxw_internal.h"
+#include "lxw_internal3d.h"
 
 namespace lxw {
 void decode_diag(const double* raw, double out[9]);
@@ -221,6 +222,8 @@ void projection_reference_points(int kind, int deg, std::vector<double>& xi, std
 }  // namespace
 
 void lxw::set_last_error(const char* msg) { g_err = msg; }
+void lxw::host_gauss_legendre(int n, double* x, double* w) { gauss_legendre(n, x, w); }
+void lxw::host_legendre_norm(int n, double x, double& v, double& d) { legendre_norm(n, x, v, d); }
 
 void lxw::make_deriv_tables(const Tables& t, DerivTables& d) {
   std::memset(&d, 0, sizeof(d));

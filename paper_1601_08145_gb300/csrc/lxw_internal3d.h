@@ -1,0 +1,74 @@
+// lxw_internal3d.h -- shared declarations of the 3D Cartesian (hexahedral)
+// FP64 form: tables, device views, launchers.  Not part of the public ABI.
+#pragma once
+
+#include "lxw_internal.h"
+
+namespace lxw {
+
+// Degrees 1 and 2: at most 10 modes, 3 Gauss points per direction.
+constexpr int k3MaxML = 10;
+constexpr int k3MaxN = 3;
+constexpr int k3MaxQ = k3MaxN * k3MaxN * k3MaxN;   // interior points
+constexpr int k3MaxF = k3MaxN * k3MaxN;            // points per face
+constexpr int k3MaxPts = k3MaxQ + 6 * k3MaxF;      // limiter points: interior, then faces
+constexpr int k3MaxProj = 125;                     // projection points ((deg + 3)^3)
+
+// Reference-cube tables of one degree.  Points: the interior tensor Gauss
+// points (xi fastest), then face k's points at NQ + k NF + t n + u, with u
+// along the first and t along the second tangential axis (x, y, z order),
+// so that the two cells of a face meet its points in the same order.
+struct Tables3 {
+  double qw[k3MaxQ];                   // interior weights, sum 1
+  double fw[k3MaxF];                   // face weights, sum 1
+  double phi[k3MaxPts][k3MaxML];       // basis at every point
+  double dref[3][k3MaxQ][k3MaxML];     // d phi / d(xi, eta, zeta) at the interior points
+  double W[3][k3MaxQ][k3MaxML];        // qw_k sum_m phi_m(x_k) D_d[m][l], D_d[m][l] = (1/8) Int d_d phi_m phi_l
+};
+
+// Uniform box cells: one spacing per axis.
+struct Mesh3 {
+  int N, nx, ny, nz;
+  double h[3], vol, hmin;              // hmin = 3 |K| / |dK|
+  const int* nbr;                      // [6][N]: neighbour across face k, or -1 - bc
+};
+
+struct Diag3Block {
+  double sum[5];
+  unsigned long long minr, minp;       // order-preserving bits of min rho, min p
+  unsigned long long nmom, nface, nsc;
+};
+
+struct Work3 {
+  double* trace;                       // [6][NF][10][N]: q (5), n_out . F_T (5), n scaled by the face area
+  double* flux;                        // [6][10][N]: outward f^LxW (5), f^LxF (5)
+  double* prop;                        // [6][N]: flux-limiter proposals
+  unsigned long long* smax;            // bits of the global wave speed (non-negative double)
+  unsigned int* status;                // LXW_ST_* bits of the step
+  Diag3Block* diag;
+};
+
+struct Args3 {
+  double dt_in, cfl, gamma, eps0, alpha0;
+  int shock_limiter, llf_global, want_diag;
+  double* theta_face;                  // [N][6] or null
+};
+
+// Tables of one degree into the device's constant bank (synchronous).
+int upload_tables3(int deg, const Tables3& t);
+// One step: reset, moment, ck, face, update, shock (if on), diag (if asked).
+// events (nullable): recorded before each phase and after the last; upto:
+// phases to run (1 moment .. 5 shock).
+int launch_step3(int deg, const Mesh3& m, const Work3& w, double* Q, const Args3& a, void* stream, int block,
+                 void** events, int upto);
+int step3_launch_count(int want_diag, int shock_limiter);
+// Q[N][5][ML] = L2 projection of prim[N][NPJ][5] = (rho, u, v, w, p) with the
+// projection weights jw[NPJ] and basis jphi[NPJ][ML] (device arrays).
+int launch_project3(int deg, int N, int NPJ, double gamma, const double* jw, const double* jphi, const double* prim,
+                    double* Q, void* stream);
+
+// Host quadrature helpers shared with the 2D tables (lxw_host.cpp).
+void host_gauss_legendre(int n, double* x, double* w);
+void host_legendre_norm(int n, double x, double& v, double& d);
+
+}  // namespace lxw

@@ -1,0 +1,783 @@
+// lxw_kernels3d.cu -- sm_103a kernels of one LxW-DG step on 3D Cartesian
+// meshes (hexahedra), FP64, the extension the paper says carries over
+// directly (end of Sec. 3.3; the 3D Euler equations of Sec. 1.1 with the
+// third flux H).
+//
+// One thread owns one cell, as in the 2D FP64 form; state Q[N][5][ML]
+// (rho, rho u, rho v, rho w, E), modes ordered by total degree, then the x
+// exponent descending, then the y exponent descending.  Phases (kernel
+// boundaries carry the grid-wide dependencies):
+//   k3_moment  Sec. 3.1 moment limiter + max |u| + c -> atomicMax
+//   k3_ck      Sec. 2.2-2.3 CK flux (q_t, q_tt carried as modes through the
+//              weighted differentiation tables), volume integral, traces
+//   k3_face    Sec. 3.3 Step 3 on six faces (LLF with the local speed,
+//              f^LxW, f^LxF, face integral) and Steps 4-5 (Lambda, 63
+//              corners, mu) per cell
+//   k3_update  Step 6: theta = min of both proposals, averages
+//   k3_shock   Sec. 4.1 on (rho, u, v, w, p) with the six face neighbours
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "lxw_internal3d.h"
+
+namespace lxw {
+namespace {
+
+__constant__ Tables3 c_tab3[2];   // degree 1, degree 2
+
+__device__ __forceinline__ double speed_of3(double g, const double q[5]) {
+  if (!(q[0] > 0.0)) return 0.0;
+  const double ri = 1.0 / q[0];
+  const double u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
+  const double k2 = u * u + v * v + w * w;
+  const double p = (g - 1.0) * (q[4] - 0.5 * q[0] * k2);
+  return sqrt(k2) + (p > 0.0 ? sqrt(g * p * ri) : 0.0);
+}
+
+// The local Lax-Friedrichs speed of a trace with explicitly rounded
+// operations: both cells of a face evaluate it on the same two traces and
+// must get the same value.
+__device__ __forceinline__ double lf_speed3(double g, const double q[5]) {
+  if (!(q[0] > 0.0)) return 0.0;
+  const double ri = __drcp_rn(q[0]);
+  const double u = __dmul_rn(q[1], ri), v = __dmul_rn(q[2], ri), w = __dmul_rn(q[3], ri);
+  const double k2 = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
+  const double p = __dmul_rn(g - 1.0, __dsub_rn(q[4], __dmul_rn(0.5, __dmul_rn(q[0], k2))));
+  const double c = p > 0.0 ? __dsqrt_rn(__dmul_rn(__dmul_rn(g, p), ri)) : 0.0;
+  return __dadd_rn(__dsqrt_rn(k2), c);
+}
+
+__device__ __forceinline__ void block_max3(double v, unsigned long long* dst) {
+  // v >= 0: its bits order like the values
+  __shared__ unsigned long long sm[32];
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long t = __shfl_down_sync(0xffffffffu, b, o);
+    b = t > b ? t : b;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sm[warp] = b;
+  __syncthreads();
+  if (warp == 0) {
+    b = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long t = __shfl_down_sync(0xffffffffu, b, o);
+      b = t > b ? t : b;
+    }
+    if (lane == 0) atomicMax(dst, b);
+  }
+}
+
+__device__ __forceinline__ double step_dt3(const Work3& w, const Mesh3& m, const Args3& a) {
+  const double s = __longlong_as_double((long long)*w.smax);
+  return a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin / s;
+}
+
+// ---------------------------------------------------------------- flux
+// Point state with its primitives.
+struct P3 {
+  double q[5];
+  double ri, u[3], p;
+};
+__device__ __forceinline__ P3 make_p3(double g1, const double q[5]) {
+  P3 s;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) s.q[v] = q[v];
+  s.ri = 1.0 / q[0];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) s.u[d] = q[1 + d] * s.ri;
+  s.p = g1 * (q[4] - 0.5 * (q[1] * s.u[0] + q[2] * s.u[1] + q[3] * s.u[2]));
+  return s;
+}
+
+// F_d(q), d = 0, 1, 2
+__device__ __forceinline__ void flux3(const P3& s, double F[3][5]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[d][0] = s.q[1 + d];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) F[d][1 + e] = s.q[1 + e] * s.u[d] + (e == d ? s.p : 0.0);
+    F[d][4] = (s.q[4] + s.p) * s.u[d];
+  }
+}
+
+// F'(q) w; also the primitive increments du (velocity) and dp along w
+__device__ __forceinline__ void flux3_d1(double g1, const P3& s, const double w[5], double F[3][5], double du[3],
+                                         double& dp) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) du[d] = (w[1 + d] - s.u[d] * w[0]) * s.ri;
+  const double k2 = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
+  dp = g1 * (w[4] - (s.u[0] * w[1] + s.u[1] * w[2] + s.u[2] * w[3]) + 0.5 * k2 * w[0]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[d][0] = w[1 + d];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) F[d][1 + e] = w[1 + e] * s.u[d] + s.q[1 + e] * du[d] + (e == d ? dp : 0.0);
+    F[d][4] = (w[4] + dp) * s.u[d] + (s.q[4] + s.p) * du[d];
+  }
+}
+
+// F''(q)(w, w) from the increments of flux3_d1: along q + t w the density
+// and momentum are linear, so u'' = -2 w_rho u' / rho and
+// p'' = -(g-1)(m' . u' + m . u'' / 2)
+__device__ __forceinline__ void flux3_d2(double g1, const P3& s, const double w[5], const double du[3], double dp,
+                                         double F[3][5]) {
+  double d2u[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) d2u[d] = -2.0 * w[0] * du[d] * s.ri;
+  const double d2p = -g1 * ((w[1] * du[0] + w[2] * du[1] + w[3] * du[2]) +
+                            0.5 * (s.q[1] * d2u[0] + s.q[2] * d2u[1] + s.q[3] * d2u[2]));
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F[d][0] = 0.0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) F[d][1 + e] = 2.0 * w[1 + e] * du[d] + s.q[1 + e] * d2u[d] + (e == d ? d2p : 0.0);
+    F[d][4] = d2p * s.u[d] + 2.0 * (w[4] + dp) * du[d] + (s.q[4] + s.p) * d2u[d];
+  }
+}
+
+// ------------------------------------------------------------ k3_reset
+__global__ void k3_reset(Work3 w, int want_diag) {
+  if (threadIdx.x == 0) {
+    *w.smax = 0ull;
+    *w.status = 0u;
+  }
+  if (want_diag && threadIdx.x < 5) w.diag->sum[threadIdx.x] = 0.0;
+  if (want_diag && threadIdx.x == 0) {
+    w.diag->minr = w.diag->minp = ~0ull;
+    w.diag->nmom = w.diag->nface = w.diag->nsc = 0ull;
+  }
+}
+
+// ------------------------------------------------------------ k3_moment
+// Sec. 3.1 Steps 0-2 (Lemma 1's secant), then |u| + c of the limited state at
+// every point and of the average, block max -> atomicMax.
+template <int DEG, int ML, int N1>
+__global__ void __launch_bounds__(128) k3_moment(const Mesh3 m, const Work3 w, double* __restrict__ Q, const Args3 a) {
+  constexpr int NQ = N1 * N1 * N1, NF = N1 * N1, NPT = NQ + 6 * NF;
+  const Tables3& t = c_tab3[DEG - 1];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double smax = 0.0;
+  if (i < m.N) {
+    const double g = a.gamma, g1 = g - 1.0;
+    double* Qi = Q + (size_t)i * 5 * ML;
+    double c[5][ML];
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
+    const double pb = c[0][0] > 0.0
+                          ? g1 * (c[4][0] - 0.5 * (c[1][0] * c[1][0] + c[2][0] * c[2][0] + c[3][0] * c[3][0]) / c[0][0])
+                          : -1.0;
+    double th = 1.0;
+    if (!(c[0][0] > 0.0) || !(pb > 0.0)) {
+      // Step 0: a non-positive average: flatten the cell and report it
+      atomicOr(w.status, (unsigned)LXW_ST_NONPOSITIVE);
+      th = 0.0;
+    } else {
+      // Step 1: density
+      const double er = fmin(a.eps0, 0.5 * c[0][0]);
+      double thr = 1.0;
+#pragma unroll 1
+      for (int p = 0; p < NPT; ++p) {
+        double d = 0.0;
+#pragma unroll
+        for (int l = 1; l < ML; ++l) d = fma(c[0][l], t.phi[p][l], d);
+        const double rm = c[0][0] + d;
+        if (rm < er) thr = fmin(thr, (c[0][0] - er) / (c[0][0] - rm));
+      }
+      // Step 2: pressure of the density-limited state, secant through (0, pbar)
+      const double ep = fmin(a.eps0, 0.5 * pb);
+      th = thr;
+#pragma unroll 1
+      for (int p = 0; p < NPT; ++p) {
+        double q[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          double d = 0.0;
+#pragma unroll
+          for (int l = 1; l < ML; ++l) d = fma(c[v][l], t.phi[p][l], d);
+          q[v] = c[v][0] + thr * d;
+        }
+        const double pt = g1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+        if (pt < ep) th = fmin(th, thr * (pb - ep) / (pb - pt));
+      }
+      th = fmax(th, 0.0);
+    }
+    if (th < 1.0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+#pragma unroll
+        for (int l = 1; l < ML; ++l) {
+          c[v][l] *= th;
+          Qi[v * ML + l] = c[v][l];
+        }
+      if (a.want_diag) atomicAdd(&w.diag->nmom, 1ull);
+    }
+    // wave speed over the limited state
+    double qa[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qa[v] = c[v][0];
+    smax = speed_of3(g, qa);
+#pragma unroll 1
+    for (int p = 0; p < NPT; ++p) {
+      double q[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 0; l < ML; ++l) acc = fma(c[v][l], t.phi[p][l], acc);
+        q[v] = acc;
+      }
+      smax = fmax(smax, speed_of3(g, q));
+    }
+  }
+  block_max3(smax, w.smax);
+}
+
+// ------------------------------------------------------------ k3_ck
+// Sec. 2.2-2.3: q_t = -div F^h and q_tt = -div F_t^h lie in the modal space
+// (degree deg - 1), so they are carried as modal coefficients Qt, Qtt,
+// accumulated at the interior points with the weighted differentiation
+// tables (the same values as projecting the flux and differentiating the
+// expansion); F_t = F'(q) q_t, F_tt = F''(q)(q_t, q_t) + F'(q) q_tt, F_T =
+// F + dt/2 F_t + dt^2/6 F_tt at every point; the volume integral is added to
+// the higher moments in place, the face points store q and n_out . F_T.
+template <int DEG, int ML, int N1>
+__global__ void __launch_bounds__(128) k3_ck(const Mesh3 m, const Work3 w, double* __restrict__ Q, const Args3 a) {
+  constexpr int NQ = N1 * N1 * N1, NF = N1 * N1, NPT = NQ + 6 * NF;
+  const Tables3& t = c_tab3[DEG - 1];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int N = m.N;
+  const double g1 = a.gamma - 1.0;
+  const double dt = step_dt3(w, m, a);
+  const double c1 = 0.5 * dt, c2 = dt * dt / 6.0;
+  const double sd[3] = {2.0 / m.h[0], 2.0 / m.h[1], 2.0 / m.h[2]};
+  double* Qi = Q + (size_t)i * 5 * ML;
+  double c[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
+  // pass 1: Qt
+  double Qt[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Qt[v][l] = 0.0;
+#pragma unroll 1
+  for (int k = 0; k < NQ; ++k) {
+    double q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double acc = 0.0;
+#pragma unroll
+      for (int l = 0; l < ML; ++l) acc = fma(c[v][l], t.phi[k][l], acc);
+      q[v] = acc;
+    }
+    const P3 s = make_p3(g1, q);
+    double F[3][5];
+    flux3(s, F);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double f0 = sd[0] * F[0][v], f1 = sd[1] * F[1][v], f2 = sd[2] * F[2][v];
+#pragma unroll
+      for (int l = 0; l < ML; ++l)
+        Qt[v][l] -= f0 * t.W[0][k][l] + f1 * t.W[1][k][l] + f2 * t.W[2][k][l];
+    }
+  }
+  // pass 2: Qtt
+  double Qtt[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Qtt[v][l] = 0.0;
+#pragma unroll 1
+  for (int k = 0; k < NQ; ++k) {
+    double q[5], qt[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double acc = 0.0, d1 = 0.0;
+#pragma unroll
+      for (int l = 0; l < ML; ++l) {
+        acc = fma(c[v][l], t.phi[k][l], acc);
+        d1 = fma(Qt[v][l], t.phi[k][l], d1);
+      }
+      q[v] = acc; qt[v] = d1;
+    }
+    const P3 s = make_p3(g1, q);
+    double F1[3][5], du[3], dp;
+    flux3_d1(g1, s, qt, F1, du, dp);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double f0 = sd[0] * F1[0][v], f1 = sd[1] * F1[1][v], f2 = sd[2] * F1[2][v];
+#pragma unroll
+      for (int l = 0; l < ML; ++l)
+        Qtt[v][l] -= f0 * t.W[0][k][l] + f1 * t.W[1][k][l] + f2 * t.W[2][k][l];
+    }
+  }
+  // pass 3: F_T everywhere; volume integral at interior points, traces at face points
+  double Vv[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Vv[v][l] = 0.0;
+#pragma unroll 1
+  for (int p = 0; p < NPT; ++p) {
+    double q[5], qt[5], qtt[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double acc = 0.0, d1 = 0.0, d2 = 0.0;
+#pragma unroll
+      for (int l = 0; l < ML; ++l) {
+        const double ph = t.phi[p][l];
+        acc = fma(c[v][l], ph, acc);
+        d1 = fma(Qt[v][l], ph, d1);
+        d2 = fma(Qtt[v][l], ph, d2);
+      }
+      q[v] = acc; qt[v] = d1; qtt[v] = d2;
+    }
+    const P3 s = make_p3(g1, q);
+    double F[3][5], FT[3][5];
+    flux3(s, F);
+    {
+      double F1[3][5], du[3], dp;
+      flux3_d1(g1, s, qt, F1, du, dp);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) FT[d][v] = F[d][v] + c1 * F1[d][v];
+      flux3_d2(g1, s, qt, du, dp, F1);
+      double F3[3][5], eu[3], ep;
+      flux3_d1(g1, s, qtt, F3, eu, ep);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) FT[d][v] += c2 * (F1[d][v] + F3[d][v]);
+    }
+    if (p < NQ) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double f0 = t.qw[p] * sd[0] * FT[0][v], f1 = t.qw[p] * sd[1] * FT[1][v],
+                     f2 = t.qw[p] * sd[2] * FT[2][v];
+#pragma unroll
+        for (int l = 1; l < ML; ++l)
+          Vv[v][l] = fma(f0, t.dref[0][p][l], fma(f1, t.dref[1][p][l], fma(f2, t.dref[2][p][l], Vv[v][l])));
+      }
+    } else {
+      const int k = (p - NQ) / NF, pe = (p - NQ) - k * NF, d = k >> 1;
+      const double an = (k & 1 ? 1.0 : -1.0) * m.vol / m.h[d];   // outward normal times the face area
+      double* tr = w.trace + ((size_t)(k * NF + pe) * 10) * N + i;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        tr[(size_t)v * N] = q[v];
+        tr[(size_t)(5 + v) * N] = an * FT[d][v];
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 1; l < ML; ++l) Qi[v * ML + l] = c[v][l] + dt * Vv[v][l];
+}
+
+// ------------------------------------------------------------ k3_face
+// Sec. 3.3 Step 3 on the six faces, seen from each cell: both cells of a
+// face take its points in the same order and the same explicitly rounded
+// operations on negated operands, so their LLF values, f^LxW and f^LxF are
+// exact negatives.  Face integral of the higher moments; Steps 4-5: Gamma,
+// the density Lambda shared by the negative faces, the Lax-Friedrichs
+// state, mu over the 63 corners of the box of proposals.
+template <int DEG, int ML, int N1>
+__global__ void __launch_bounds__(128) k3_face(const Mesh3 m, const Work3 w, double* __restrict__ Q, const Args3 a) {
+  constexpr int NQ = N1 * N1 * N1, NF = N1 * N1;
+  const Tables3& t = c_tab3[DEG - 1];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int N = m.N;
+  const double g = a.gamma, g1 = g - 1.0;
+  const double s = __longlong_as_double((long long)*w.smax);
+  const double dt = step_dt3(w, m, a);
+  double* Qi = Q + (size_t)i * 5 * ML;
+  double qb[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qb[v] = Qi[v * ML];
+  const P3 sb = make_p3(g1, qb);
+  double Fb[3][5];
+  flux3(sb, Fb);
+  double Ei[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Ei[v][l] = 0.0;
+  double fW[6][5], fF[6][5];
+#pragma unroll 1
+  for (int k = 0; k < 6; ++k) {
+    const int j = m.nbr[k * N + i], d = k >> 1, kj = k ^ 1;
+    const double an = (k & 1 ? 1.0 : -1.0) * m.vol / m.h[d];
+    const double area = fabs(an);
+    const double hs = 0.5 * s * area;
+    // neighbour (or exterior) average: reflection flips the normal momentum
+    double qn[5];
+    if (j >= 0) {
+      const double* Qj = Q + (size_t)j * 5 * ML;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qn[v] = Qj[v * ML];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qn[v] = qb[v];
+      if (-1 - j == LXW_BC_REFLECT) qn[1 + d] = -qn[1 + d];
+    }
+    {
+      const P3 sn = make_p3(g1, qn);
+      double Fn[3][5];
+      flux3(sn, Fn);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double ai = __dmul_rn(an, Fb[d][v]), ak = __dmul_rn(an, Fn[d][v]);
+        fF[k][v] = __fma_rn(-hs, __dsub_rn(qn[v], qb[v]), __dmul_rn(0.5, __dadd_rn(ai, ak)));
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fW[k][v] = 0.0;
+#pragma unroll 1
+    for (int p = 0; p < NF; ++p) {
+      const double* tr = w.trace + ((size_t)(k * NF + p) * 10) * N + i;
+      double qi[5], Fi[5], qx[5], Fx[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { qi[v] = tr[(size_t)v * N]; Fi[v] = tr[(size_t)(5 + v) * N]; }
+      if (j >= 0) {
+        const double* tj = w.trace + ((size_t)(kj * NF + p) * 10) * N + j;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) { qx[v] = tj[(size_t)v * N]; Fx[v] = -tj[(size_t)(5 + v) * N]; }
+      } else if (-1 - j == LXW_BC_REFLECT) {
+        // exterior R q, and n . F_T(R q) = -R (n . F_T(q)) (the Euler flux's mirror symmetry)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) { qx[v] = qi[v]; Fx[v] = -Fi[v]; }
+        qx[1 + d] = -qi[1 + d];
+        Fx[1 + d] = Fi[1 + d];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) { qx[v] = qi[v]; Fx[v] = Fi[v]; }
+      }
+      // dissipation speed: the local speed of the two traces, at most s
+      const double hp = a.llf_global ? hs : 0.5 * fmin(s, fmax(lf_speed3(g, qi), lf_speed3(g, qx))) * area;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double fs = __fma_rn(-hp, __dsub_rn(qx[v], qi[v]), __dmul_rn(0.5, __dadd_rn(Fi[v], Fx[v])));
+        fW[k][v] = __fma_rn(t.fw[p], fs, fW[k][v]);
+        const double hw = t.fw[p] * fs;
+#pragma unroll
+        for (int l = 1; l < ML; ++l) Ei[v][l] = fma(hw, t.phi[NQ + k * NF + p][l], Ei[v][l]);
+      }
+    }
+  }
+  const double dta = dt / m.vol;
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 1; l < ML; ++l) Qi[v * ML + l] -= dta * Ei[v][l];
+
+  // Steps 4-5
+  double Gam0 = m.vol / dt * qb[0];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Gam0 -= fF[k][0];
+  if (Gam0 < 0.0) atomicOr(w.status, (unsigned)LXW_ST_CFL);
+  double neg = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double df = fF[k][0] - fW[k][0];
+    if (df < 0.0) neg += df;
+  }
+  double ql[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc += fF[k][v];
+    ql[v] = qb[v] - dta * acc;
+  }
+  const double er = fmax(fmin(a.eps0, 0.5 * ql[0]), 0.0);
+  double lneg = 1.0;
+  if (neg < 0.0) lneg = fmin(1.0, fmax(0.0, (Gam0 - m.vol / dt * er) / (-neg)));
+  double lam[6], dq[6][5];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    lam[k] = (fF[k][0] - fW[k][0]) < 0.0 ? lneg : 1.0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dq[k][v] = dta * lam[k] * (fF[k][v] - fW[k][v]);
+  }
+  const double pl =
+      ql[0] > 0.0 ? g1 * (ql[4] - 0.5 * (ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3]) / ql[0]) : -1.0;
+  double mmin[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) mmin[k] = 1.0;
+  if (!(ql[0] > 0.0) || !(pl > 0.0)) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) mmin[k] = 0.0;
+  } else {
+    const double kap = fmin(a.eps0, 0.5 * pl) / g1;
+    const double h0 = ql[0] * ql[4] - 0.5 * (ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3]) - kap * ql[0];
+#pragma unroll 1
+    for (int cm = 1; cm < 64; ++cm) {
+      double dd[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if ((cm >> k) & 1)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) dd[v] += dq[k][v];
+      // h(mu) = rho E - |m|^2 / 2 - kappa rho along ql + mu dd
+      const double h1 = ql[0] * dd[4] + dd[0] * ql[4] - (ql[1] * dd[1] + ql[2] * dd[2] + ql[3] * dd[3]) - kap * dd[0];
+      const double h2 = dd[0] * dd[4] - 0.5 * (dd[1] * dd[1] + dd[2] * dd[2] + dd[3] * dd[3]);
+      double mu = 1.0;
+      if (!(ql[0] + dd[0] > 0.0) || h0 + h1 + h2 < 0.0) {
+        const double disc = fmax(h1 * h1 - 4.0 * h0 * h2, 0.0);
+        const double den = -h1 + sqrt(disc);
+        mu = den > 0.0 ? fmin(1.0, fmax(0.0, 2.0 * h0 / den)) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if ((cm >> k) & 1) mmin[k] = fmin(mmin[k], mu);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    w.prop[k * N + i] = lam[k] * mmin[k];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      w.flux[(size_t)(k * 10 + v) * N + i] = fW[k][v];
+      w.flux[(size_t)(k * 10 + 5 + v) * N + i] = fF[k][v];
+    }
+  }
+}
+
+// ------------------------------------------------------------ k3_update
+// Sec. 3.3 Step 6: theta of a face = min of the two cells' proposals;
+// blended update of the averages.
+template <int ML>
+__global__ void __launch_bounds__(128) k3_update(const Mesh3 m, const Work3 w, double* __restrict__ Q, const Args3 a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int N = m.N;
+  const double dt = step_dt3(w, m, a);
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int j = m.nbr[k * N + i];
+    double th = w.prop[k * N + i];
+    if (j >= 0) th = fmin(th, w.prop[(k ^ 1) * N + j]);
+    if (a.theta_face) a.theta_face[(size_t)i * 6 + k] = th;
+    // count each face once: from its + side, or from the cell of a boundary face
+    if (a.want_diag && th < 1.0 && (j < 0 || (k & 1))) atomicAdd(&w.diag->nface, 1ull);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double fw = w.flux[(size_t)(k * 10 + v) * N + i], ff = w.flux[(size_t)(k * 10 + 5 + v) * N + i];
+      acc[v] += th * fw + (1.0 - th) * ff;
+    }
+  }
+  double* Qi = Q + (size_t)i * 5 * ML;
+  const double dta = dt / m.vol;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Qi[v * ML] -= dta * acc[v];
+}
+
+// ------------------------------------------------------------ k3_shock
+// Sec. 4.1 on (rho, u, v, w, p): M = max(w_i + alpha, max_j w_j), m =
+// min(w_i - alpha, min_j w_j) over the six face neighbours (a wall's
+// exterior: the mirrored average), theta = min(1, (M - w_i)/(max_pts w -
+// w_i), (w_i - m)/(w_i - min_pts w)) over the primitives, alpha = alpha0
+// dx^1.5 with dx = |K|^(1/3).
+template <int DEG, int ML, int N1>
+__global__ void __launch_bounds__(128) k3_shock(const Mesh3 m, const Work3 w, double* __restrict__ Q, const Args3 a) {
+  constexpr int NQ = N1 * N1 * N1, NF = N1 * N1, NPT = NQ + 6 * NF;
+  const Tables3& t = c_tab3[DEG - 1];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int N = m.N;
+  const double g1 = a.gamma - 1.0;
+  double* Qi = Q + (size_t)i * 5 * ML;
+  double c[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
+  auto prim = [&](const double q[5], double wv[5]) {
+    const double ri = 1.0 / q[0];
+    wv[0] = q[0]; wv[1] = q[1] * ri; wv[2] = q[2] * ri; wv[3] = q[3] * ri;
+    wv[4] = g1 * (q[4] - 0.5 * (q[1] * wv[1] + q[2] * wv[2] + q[3] * wv[3]));
+  };
+  double th = 1.0;
+  if (!(c[0][0] > 0.0)) {
+    th = 0.0;
+  } else {
+    double qb[5], wb[5], Mx[5], Mn[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qb[v] = c[v][0];
+    prim(qb, wb);
+    const double al = a.alpha0 * pow(cbrt(m.vol), 1.5);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { Mx[v] = wb[v] + al; Mn[v] = wb[v] - al; }
+#pragma unroll 1
+    for (int k = 0; k < 6; ++k) {
+      const int j = m.nbr[k * N + i];
+      double qn[5], wn[5];
+      if (j >= 0) {
+        const double* Qj = Q + (size_t)j * 5 * ML;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qn[v] = Qj[v * ML];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qn[v] = qb[v];
+        if (-1 - j == LXW_BC_REFLECT) qn[1 + (k >> 1)] = -qn[1 + (k >> 1)];
+      }
+      if (!(qn[0] > 0.0)) continue;
+      prim(qn, wn);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { Mx[v] = fmax(Mx[v], wn[v]); Mn[v] = fmin(Mn[v], wn[v]); }
+    }
+    double hx[5], hn[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { hx[v] = -1e300; hn[v] = 1e300; }
+    bool bad = false;
+#pragma unroll 1
+    for (int p = 0; p < NPT; ++p) {
+      double q[5], wp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 0; l < ML; ++l) acc = fma(c[v][l], t.phi[p][l], acc);
+        q[v] = acc;
+      }
+      if (!(q[0] > 0.0)) { bad = true; break; }
+      prim(q, wp);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { hx[v] = fmax(hx[v], wp[v]); hn[v] = fmin(hn[v], wp[v]); }
+    }
+    if (bad) {
+      th = 0.0;
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        if (hx[v] > wb[v]) th = fmin(th, (Mx[v] - wb[v]) / (hx[v] - wb[v]));
+        if (hn[v] < wb[v]) th = fmin(th, (wb[v] - Mn[v]) / (wb[v] - hn[v]));
+      }
+      th = fmax(th, 0.0);
+    }
+  }
+  if (th < 1.0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int l = 1; l < ML; ++l) Qi[v * ML + l] = th * c[v][l];
+    if (a.want_diag) atomicAdd(&w.diag->nsc, 1ull);
+  }
+}
+
+// ------------------------------------------------------------ k3_diag
+template <int ML>
+__global__ void __launch_bounds__(256) k3_diag(const Mesh3 m, const Work3 w, const double* __restrict__ Q, double gamma) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const double* Qi = Q + (size_t)i * 5 * ML;
+  double q[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    q[v] = Qi[v * ML];
+    atomicAdd(&w.diag->sum[v], m.vol * q[v]);
+    if (!isfinite(q[v])) atomicOr(w.status, (unsigned)LXW_ST_NAN);
+  }
+  const double p = (gamma - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+  auto ob = [](double x) {   // order-preserving bits
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+  };
+  atomicMin(&w.diag->minr, ob(q[0]));
+  atomicMin(&w.diag->minp, ob(p));
+}
+
+// ------------------------------------------------------------ k3_project
+template <int ML>
+__global__ void k3_project(int N, int NPJ, double gamma, const double* __restrict__ jw, const double* __restrict__ jphi,
+                           const double* __restrict__ prim, double* __restrict__ Q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double acc[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) acc[v][l] = 0.0;
+  for (int p = 0; p < NPJ; ++p) {
+    const double* wv = prim + ((size_t)i * NPJ + p) * 5;
+    const double r = wv[0], u = wv[1], v = wv[2], ww = wv[3];
+    const double q[5] = {r, r * u, r * v, r * ww, wv[4] / (gamma - 1.0) + 0.5 * r * (u * u + v * v + ww * ww)};
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int l = 0; l < ML; ++l) acc[c][l] = fma(jw[p] * q[c], jphi[p * ML + l], acc[c][l]);
+  }
+  double* Qi = Q + (size_t)i * 5 * ML;
+#pragma unroll
+  for (int c = 0; c < 5; ++c)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Qi[c * ML + l] = acc[c][l];
+}
+
+template <int DEG, int ML, int N1>
+int step3_impl(const Mesh3& m, const Work3& w, double* Q, const Args3& a, cudaStream_t st, int block, void** events,
+               int upto) {
+  const int grid = (m.N + block - 1) / block;
+  int ne = 0;
+  auto mark = [&]() { if (events) cudaEventRecord((cudaEvent_t)events[ne++], st); };
+  auto ok = [&]() { return cudaGetLastError() == cudaSuccess ? 0 : -1; };
+  k3_reset<<<1, 32, 0, st>>>(w, a.want_diag);
+  mark();
+  k3_moment<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  mark();
+  if (upto < 2) return ok();
+  k3_ck<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  mark();
+  if (upto < 3) return ok();
+  k3_face<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  mark();
+  if (upto < 4) return ok();
+  k3_update<ML><<<grid, block, 0, st>>>(m, w, Q, a);
+  mark();
+  if (upto < 5) return ok();
+  if (a.shock_limiter) k3_shock<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  mark();
+  if (a.want_diag) k3_diag<ML><<<(m.N + 255) / 256, 256, 0, st>>>(m, w, Q, a.gamma);
+  return ok();
+}
+
+}  // namespace
+
+int upload_tables3(int deg, const Tables3& t) {
+  if (deg < 1 || deg > 2) return -1;
+  return cudaMemcpyToSymbol(c_tab3, &t, sizeof(Tables3), sizeof(Tables3) * (deg - 1)) == cudaSuccess ? 0 : -1;
+}
+
+int launch_step3(int deg, const Mesh3& m, const Work3& w, double* Q, const Args3& a, void* stream, int block,
+                 void** events, int upto) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (deg == 1) return step3_impl<1, 4, 2>(m, w, Q, a, st, block, events, upto);
+  if (deg == 2) return step3_impl<2, 10, 3>(m, w, Q, a, st, block, events, upto);
+  return -2;
+}
+
+int step3_launch_count(int want_diag, int shock_limiter) { return 5 + (shock_limiter ? 1 : 0) + (want_diag ? 1 : 0); }
+
+int launch_project3(int deg, int N, int NPJ, double gamma, const double* jw, const double* jphi, const double* prim,
+                    double* Q, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int grid = (N + 127) / 128;
+  if (deg == 1) k3_project<4><<<grid, 128, 0, st>>>(N, NPJ, gamma, jw, jphi, prim, Q);
+  else if (deg == 2) k3_project<10><<<grid, 128, 0, st>>>(N, NPJ, gamma, jw, jphi, prim, Q);
+  else return -2;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace lxw

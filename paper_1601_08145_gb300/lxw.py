@@ -35,6 +35,8 @@ EXPORTS = [
     "lxw_step_gate", "lxw_profile_phases", "lxw_basis_eval", "lxw_mesh_cartesian_masked",
     "lxw_solver_set_inflow", "lxw_mlp_set_envelope", "lxw_mlp_get_envelope", "lxw_run_host_state",
     "lxw_solver_set_gate_wait_test", "lxw_run_to", "lxw_solver_get_options",
+    "lxw3_solver_create", "lxw3_solver_destroy", "lxw3_solver_info", "lxw3_projection_points",
+    "lxw3_project", "lxw3_step", "lxw3_run", "lxw3_profile_step", "lxw3_step_launches",
 ]
 
 
@@ -133,6 +135,17 @@ def lib():
     L.lxw_state_pack.argtypes = [_vp, _vp, _vp]
     L.lxw_state_unpack.argtypes = [_vp, _vp, _vp]
     L.lxw_moment_limit_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp]
+    L.lxw3_solver_create.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _ip, C.c_int, C.POINTER(Options), _vp,
+                                     C.POINTER(_vp)]
+    L.lxw3_solver_destroy.argtypes = [_vp]
+    L.lxw3_solver_destroy.restype = None
+    L.lxw3_solver_info.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.lxw3_projection_points.argtypes = [_vp, _dp]
+    L.lxw3_project.argtypes = [_vp, _vp, _vp]
+    L.lxw3_step.argtypes = [_vp, _vp, C.c_double, C.c_double, _vp, _vp]
+    L.lxw3_run.argtypes = [_vp, _vp, C.c_int, C.c_double, _vp]
+    L.lxw3_profile_step.argtypes = [_vp, _vp, C.c_double, C.POINTER(C.c_float)]
+    L.lxw3_step_launches.argtypes = [_vp]
     _lib = L
     return L
 
@@ -570,3 +583,82 @@ def lxw_step_gate(solver, state, cfl, features=False):
     F = torch.empty((solver.N, MLP_IN), dtype=torch.float32, device="cuda") if features else None
     _check(lib().lxw_step_gate(solver.h, _ptr(state, solver.state_shape, "state"), cfl, _fptr(g), _fptr(F)))
     return (g, F) if features else g
+
+
+# ---------------------------------------------------------------- 3D Cartesian (FP64)
+class Diag3(C.Structure):
+    _fields_ = [("s", C.c_double), ("dt", C.c_double), ("min_rho", C.c_double), ("min_p", C.c_double),
+                ("mass", C.c_double), ("momx", C.c_double), ("momy", C.c_double), ("momz", C.c_double),
+                ("energy", C.c_double), ("n_mom", C.c_double), ("n_face", C.c_double), ("n_sc", C.c_double),
+                ("status", C.c_int), ("reserved", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+PHASES3 = ("moment", "ck", "face", "update", "shock")
+
+
+class Solver3:
+    def __init__(self, handle, n3):
+        self.h = handle
+        self.nx, self.ny, self.nz = n3
+        N, ML, nproj = (C.c_int() for _ in range(3))
+        _check(lib().lxw3_solver_info(handle, C.byref(N), C.byref(ML), C.byref(nproj)))
+        self.N, self.ML, self.nproj = N.value, ML.value, nproj.value
+
+    @property
+    def state_shape(self):
+        return (self.N, 5, self.ML)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.lxw3_solver_destroy(self.h)
+            self.h = None
+
+
+def lxw3_solver_create(nx, ny, nz, box, bc, degree, options=None, stream=None):
+    """3D Cartesian FP64 solver: box = (x0, x1, y0, y1, z0, z1), bc per side (x-, x+, y-, y+, z-, z+)."""
+    h = _vp()
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    c = np.ascontiguousarray(bc, dtype=np.int32)
+    _check(lib().lxw3_solver_create(nx, ny, nz, b.ctypes.data_as(_dp), c.ctypes.data_as(_ip), degree,
+                                    C.byref(options) if options is not None else None, _stream_handle(stream),
+                                    C.byref(h)))
+    return Solver3(h, (nx, ny, nz))
+
+
+def lxw3_projection_points(solver):
+    xyz = np.zeros((solver.N, solver.nproj, 3))
+    _check(lib().lxw3_projection_points(solver.h, xyz.ctypes.data_as(_dp)))
+    return xyz
+
+
+def lxw3_project(solver, prim, Q):
+    _check(lib().lxw3_project(solver.h, _ptr(prim, (solver.N, solver.nproj, 5), "prim"),
+                              _ptr(Q, solver.state_shape, "Q")))
+
+
+def lxw3_step(solver, Q, dt=0.0, cfl=0.1, diag=False, theta_face=None):
+    d = Diag3()
+    st = _check(lib().lxw3_step(solver.h, _ptr(Q, solver.state_shape, "Q"), dt, cfl, C.byref(d),
+                                _ptr(theta_face, (solver.N, 6), "theta_face")),
+                allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN))
+    return _diag_result(st, d) if diag else None
+
+
+def lxw3_run(solver, Q, nsteps, cfl, diag=False):
+    d = Diag3()
+    st = _check(lib().lxw3_run(solver.h, _ptr(Q, solver.state_shape, "Q"), nsteps, cfl, C.byref(d)),
+                allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN))
+    return _diag_result(st, d) if diag else None
+
+
+def lxw3_profile_step(solver, Q, cfl):
+    ms = (C.c_float * 5)()
+    _check(lib().lxw3_profile_step(solver.h, _ptr(Q, solver.state_shape, "Q"), cfl, ms))
+    return {PHASES3[k]: float(ms[k]) for k in range(5)}
+
+
+def lxw3_step_launches(solver):
+    return lib().lxw3_step_launches(solver.h)

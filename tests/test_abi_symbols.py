@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "lxw.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = set(re.findall(r"\b(lxw_[a-z_0-9]+)\s*\(", src))
+    names = set(re.findall(r"\b(lxw3?_[a-z_0-9]+)\s*\(", src))
     return sorted(names)
 
 
@@ -103,3 +103,18 @@ def test_masked_mesh_and_boundary_codes_host_side(libpath):
     with pytest.raises(lxw.LxwError) as e:
         lxw.lxw_mesh_triangles(xy, tv, np.full((len(tv), 3), 7, np.int32))
     assert e.value.code == lxw.ERR_ARG
+
+
+def test_3d_argument_errors_without_gpu(libpath):
+    """The 3D solver validates its arguments on the host, before any CUDA call."""
+    from paper_1601_08145_gb300 import lxw
+    box = (0.0, 1.0, 0.0, 1.0, 0.0, 1.0)
+    bad = [dict(nx=0), dict(degree=3), dict(bc=(0, 1, 0, 0, 0, 0)), dict(bc=(4,) * 6), dict(box=(0, 1, 0, 1, 1, 1)),
+           dict(options=lxw.lxw_options_default(precision=lxw.PREC_MIXED)),
+           dict(options=lxw.lxw_options_default(ck_order=4)), dict(options=lxw.lxw_options_default(block_threads=48))]
+    for b in bad:
+        kw = dict(nx=3, degree=2, bc=(0,) * 6, box=box, options=None)
+        kw.update(b)
+        with pytest.raises(lxw.LxwError) as e:
+            lxw.lxw3_solver_create(kw["nx"], 3, 3, kw["box"], kw["bc"], kw["degree"], kw["options"])
+        assert e.value.code == lxw.ERR_ARG, b
