@@ -325,7 +325,18 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import oracle as O
-    sols = [(WORKLOADS[p],) + oracle_solver(WORKLOADS[p]) for p in parts_of(args.workload)]
+    if args.workload == "blast3d":
+        # the 3D oracle on a 48^3 sample of the blast (its work arrays, ~15 KB
+        # per cell, would take 13 GB of host memory at 96^3)
+        b = BLAST3D
+        box = (-b["half_width"], b["half_width"]) * 3
+        so = O.Solver3(O.Mesh3(48, 48, 48, box, (1,) * 6), b["deg"])
+        Q = so.project_fn(synth.ic_blast3d(48, b["half_width"]))
+        sols = [(b, so, Q)]
+        nv = 5
+    else:
+        sols = [(WORKLOADS[p],) + oracle_solver(WORKLOADS[p]) for p in parts_of(args.workload)]
+        nv = 4
     for _ in range(args.warmup):
         for w, s, Q in sols:
             s.step(Q, cfl=w["cfl"])
@@ -334,12 +345,13 @@ def run_reference(args):
         for w, s, Q in sols:
             s.step(Q, cfl=w["cfl"])
     dt = time.perf_counter() - t0
-    dof = sum(s.N * 4 * s.ML for _, s, _ in sols)
+    dof = sum(s.N * nv * s.ML for _, s, _ in sols)
     val = dof * args.steps / dt
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": desc_of(args.workload), "elements": sum(s.N for _, s, _ in sols), "degree": 2,
+           "config": {"workload": BLAST3D["desc"] if args.workload == "blast3d" else desc_of(args.workload),
+                      "elements": sum(s.N for _, s, _ in sols), "degree": 2,
                       "form": "FP64 CPU oracle"},
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                             "sample": f"{args.steps} full steps of every part after {args.warmup} warm-up steps"},
@@ -409,6 +421,93 @@ def run_ensemble(args):
            "batching_speedup": per_ms / (total_ms / args.steps),
            "gpu_launches": args.steps * L.lxw_step_launches(b),
            "clocks": clk}
+    print(json.dumps(out))
+
+
+BLAST3D = dict(n=96, deg=2, cfl=0.1, half_width=1.1,
+               desc="3D blast: 96^3 = 884,736 Cartesian P2 cells of [-1.1,1.1]^3, point energy 0.979264 in the "
+                    "8 centre cells, reflective walls (FP64 form)")
+
+
+def ck3_flops_per_element(deg):
+    """Algorithmic FP64 flop of k3_ck per cell (an FMA counts 2): with n =
+    deg + 1, NQ = n^3 interior and NPT = NQ + 6 n^2 points, ML modes, 5
+    variables.  Pass 1: q at the interior points (5 ML FMA), the flux (~40),
+    the three weighted-table sums (15 ML FMA + 15).  Pass 2: q and q_t
+    (10 ML FMA), F'(q) q_t (~70), three table sums (15 ML FMA + 15).  Pass
+    3 at every point: q, q_t, q_tt (15 ML FMA), F, F' q_t, F'' (q_t, q_t),
+    F' q_tt and F_T (~320); the volume sums at the interior points (15 (ML-1)
+    FMA + 15)."""
+    n = deg + 1
+    NQ, NPT = n ** 3, n ** 3 + 6 * n * n
+    ML = (deg + 1) * (deg + 2) * (deg + 3) // 6
+    p1 = NQ * (2 * 5 * ML + 40 + 2 * 15 * ML + 15)
+    p2 = NQ * (2 * 10 * ML + 70 + 2 * 15 * ML + 15)
+    p3 = NPT * (2 * 15 * ML + 320) + NQ * (2 * 15 * (ML - 1) + 15)
+    return p1 + p2 + p3
+
+
+def run_blast3d(args):
+    """The 3D Cartesian FP64 form on the 3D point-energy blast: K graph-
+    replayed steps bracketed by CUDA events (the state, 354 MB, exceeds the
+    L2), per-phase times from a traced step, the oracle on a sample."""
+    import torch
+    from paper_1601_08145_gb300 import build, lxw as L
+    build.build()
+    b = BLAST3D
+    n, hw = b["n"], b["half_width"]
+    box = (-hw, hw) * 3
+    stream = torch.cuda.current_stream()
+    s = L.lxw3_solver_create(n, n, n, box, (1,) * 6, b["deg"], L.lxw_options_default(), stream=stream)
+    ic = synth.ic_blast3d(n, hw)
+    xyz = L.lxw3_projection_points(s)
+    prim = torch.from_numpy(np.stack(np.broadcast_arrays(*ic(xyz[..., 0], xyz[..., 1], xyz[..., 2])), axis=-1).copy())
+    del xyz
+    Q = torch.zeros(s.state_shape, dtype=torch.float64, device="cuda")
+    L.lxw3_project(s, prim.cuda(), Q)
+    del prim
+    L.lxw3_run(s, Q, max(args.warmup, 3), b["cfl"])
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start(); time.sleep(0.5)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    d = L.lxw3_run(s, Q, args.steps, b["cfl"], diag=True)
+    ev1.record(); torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    phases = [L.lxw3_profile_step(s, Q, b["cfl"]) for _ in range(3)]
+    ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+    dof = s.N * 5 * s.ML
+    flops = ck3_flops_per_element(b["deg"]) * s.N
+    probes = fma_probes()
+    peak = 1.25
+    roof = {"kernel": "k3_ck", "bound": "alu", "pipe": "fp64", "achieved": flops / (ph["ck"] / 1e3) / 1e12,
+            "peak": peak, "unit": "TFLOP/s", "peak_source": "nominal GB300 FP64 rate (recipe table)",
+            "peak_measured_fma_probe": probes.get("fp64"), "algorithmic_flops_per_launch": flops,
+            "launch_ms": ph["ck"], "traffic": None}
+    roof["frac"] = roof["achieved"] / peak
+    out = {"metric": METRIC, "value": dof * args.steps / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": b["desc"], "elements": s.N, "degree": b["deg"], "cfl": b["cfl"],
+                      "l2": "state (354 MB) larger than the L2", "timing": "graph-replayed steps, CUDA events"},
+           "phases_ms": ph, "roofline": roof, "gpu_launches": args.steps * L.lxw3_step_launches(s) + 1,
+           "clocks": clk, "positivity_last_step": {"min_rho": d["min_rho"], "min_p": d["min_p"]},
+           "status_last_step": d["status"]}
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        m = 48   # the oracle holds ~15 KB of work arrays per cell: a 48^3 sample of the same blast
+        so = O.Solver3(O.Mesh3(m, m, m, box, (1,) * 6), b["deg"])
+        Qo = so.project_fn(synth.ic_blast3d(m, hw))
+        so.step(Qo, cfl=b["cfl"])
+        t0 = time.time()
+        k = 30
+        for _ in range(k):
+            so.step(Qo, cfl=b["cfl"])
+        dtc = time.time() - t0
+        out["cpu_baseline"] = {"value": so.N * 5 * so.ML * k / dtc, "unit": UNIT, "cores": O.lib().orc_num_threads(),
+                               "kind": "oracle", "sample": "%d steps of the same blast on %d^3 cells, %.1f s" % (k, m, dtc)}
     print(json.dumps(out))
 
 
@@ -620,7 +719,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config5", choices=sorted(WORKLOADS) + sorted(CONFIGS) + ["ensemble"])
+    ap.add_argument("--workload", default="config5", choices=sorted(WORKLOADS) + sorted(CONFIGS) + ["ensemble", "blast3d"])
     ap.add_argument("--tau", type=float, default=0.01, help="learned gate: skip where theta_hat >= 1 - tau")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work list of the mixed forms")
@@ -632,6 +731,8 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "blast3d":
+        return run_blast3d(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -678,25 +678,46 @@ __global__ void __launch_bounds__(128) k3_shock(const Mesh3 m, const Work3 w, do
 }
 
 // ------------------------------------------------------------ k3_diag
+// Totals |K| Q^(1) and minimum density / pressure of the averages; warp
+// reductions first, one atomic per warp and quantity.
 template <int ML>
 __global__ void __launch_bounds__(256) k3_diag(const Mesh3 m, const Work3 w, const double* __restrict__ Q, double gamma) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.N) return;
-  const double* Qi = Q + (size_t)i * 5 * ML;
-  double q[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    q[v] = Qi[v * ML];
-    atomicAdd(&w.diag->sum[v], m.vol * q[v]);
-    if (!isfinite(q[v])) atomicOr(w.status, (unsigned)LXW_ST_NAN);
-  }
-  const double p = (gamma - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+  const bool on = i < m.N;
   auto ob = [](double x) {   // order-preserving bits
     unsigned long long b = (unsigned long long)__double_as_longlong(x);
     return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
   };
-  atomicMin(&w.diag->minr, ob(q[0]));
-  atomicMin(&w.diag->minp, ob(p));
+  double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  unsigned long long br = ~0ull, bp = ~0ull;
+  bool nan = false;
+  if (on) {
+    const double* Qi = Q + (size_t)i * 5 * ML;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      q[v] = Qi[v * ML];
+      nan = nan || !isfinite(q[v]);
+    }
+    const double p = (gamma - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+    br = ob(q[0]);
+    bp = ob(p);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] *= m.vol;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] += __shfl_down_sync(0xffffffffu, q[v], o);
+    const unsigned long long r = __shfl_down_sync(0xffffffffu, br, o), pp = __shfl_down_sync(0xffffffffu, bp, o);
+    br = r < br ? r : br;
+    bp = pp < bp ? pp : bp;
+  }
+  if (__any_sync(0xffffffffu, nan) && (threadIdx.x & 31) == 0) atomicOr(w.status, (unsigned)LXW_ST_NAN);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) atomicAdd(&w.diag->sum[v], q[v]);
+    atomicMin(&w.diag->minr, br);
+    atomicMin(&w.diag->minp, bp);
+  }
 }
 
 // ------------------------------------------------------------ k3_project

@@ -118,6 +118,20 @@ def ic_blast(n: int, half_width: float = 1.1, gamma: float = GAMMA, e_total: flo
     return f
 
 
+def ic_blast3d(n: int, half_width: float = 1.1, gamma: float = GAMMA, e_total: float = 0.979264):
+    """The 3D point-energy blast on an n^3 grid of [-w,w]^3 (n even): the 8
+    cells touching the origin share e_total; elsewhere p = 1e-12, rho = 1,
+    at rest.  Returns f(x, y, z) -> (rho, u, v, w, p)."""
+    h = 2.0 * half_width / n
+    p_in = (gamma - 1.0) * (e_total / 8.0) / (h * h * h)
+
+    def f(x, y, z):
+        inside = (np.abs(x) < h) & (np.abs(y) < h) & (np.abs(z) < h)
+        zero = np.zeros_like(x)
+        return np.ones_like(x), zero, zero, zero, np.where(inside, p_in, 1e-12)
+    return f
+
+
 def ic_quadrants(seed: int):
     """Four-quadrant Riemann data on [0,1]^2 drawn from a per-problem seed:
     rho ~ U[0.1,2], p ~ U[0.01,2], u, v ~ U[-1,1] in each quadrant."""
