@@ -12,6 +12,14 @@
  *    Taylor coefficients of F along q + t w + t^2 b / 2 (series arithmetic
  *    of the flux formula), not from hand-derived Jacobians.
  *  - the moment limiter's pressure step is the secant of Lemma 1 only.
+ *  - q_t = -div F^h and q_tt = -div F_t^h lie in the modal space (degree
+ *    deg - 1): they are evaluated at the interior points, projected onto the
+ *    modes with the interior rule and evaluated from the modes elsewhere.
+ *  - tetrahedra: the interior rule has deg + 2 collapsed Gauss points per
+ *    direction (exact to degree 2 deg + 1: the mass matrix is exact), the
+ *    triangle faces deg + 1 (exact to degree 2 deg, as the 2D edges); a
+ *    face's points are generated from its vertices in the order of their
+ *    (periodically identified) ids, so both cells meet them in one order.
  */
 #include "lxw_oracle3d.h"
 #include "lxw_oracle.h"
@@ -22,8 +30,8 @@
 #define NV3 5
 #define MAXML3 20                 /* modes of degree 3 */
 #define MAXN3 4                   /* points per direction (degree 3) */
-#define MAXQ3 (MAXN3 * MAXN3 * MAXN3)
-#define MAXF3 (MAXN3 * MAXN3)
+#define MAXQ3 125                 /* interior points: hexahedra (deg+1)^3, tetrahedra (deg+2)^3 */
+#define MAXF3 (MAXN3 * MAXN3)     /* points per face */
 #define MAXPTS3 (MAXQ3 + 6 * MAXF3)
 #define MAXNJ3 6                  /* projection points per direction */
 #define MAXPJ3 (MAXNJ3 * MAXNJ3 * MAXNJ3)
@@ -149,106 +157,308 @@ static double wave_speed3(double g, const double* q) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Cartesian mesh: box cells, six faces each                            */
+/* Tetrahedra: reference T0 = {r, s, t >= 0, r + s + t <= 1}.  Rules    */
+/* by the collapsed (Duffy) map r = u, s = v (1 - u), t = w (1 - u)     */
+/* (1 - v) with Gauss points in u, v, w on [0, 1]; with n points per    */
+/* direction they integrate total degree 2n - 3 exactly.  Triangle      */
+/* faces: r = u, s = v (1 - u), total degree 2n - 2.  Weights sum to 1  */
+/* (the rule of (1/|T0|) Int).  The basis is the Gram-Schmidt           */
+/* orthonormalisation (under (1/|T0|) Int) of the monomials r^a s^b t^c  */
+/* in the mode order of the hexahedra.                                  */
 /* ------------------------------------------------------------------ */
+static int tet_rule(int n, double* r, double* s, double* t, double* w) {
+  double g[8], gw[8];
+  orc_gauss_legendre(n, g, gw);
+  int k = 0;
+  double tot = 0.0;
+  for (int c = 0; c < n; ++c)
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        double u = 0.5 * (g[a] + 1.0), v = 0.5 * (g[b] + 1.0), x = 0.5 * (g[c] + 1.0);
+        r[k] = u; s[k] = v * (1.0 - u); t[k] = x * (1.0 - u) * (1.0 - v);
+        w[k] = 0.125 * gw[a] * gw[b] * gw[c] * (1.0 - u) * (1.0 - u) * (1.0 - v);
+        tot += w[k];
+        ++k;
+      }
+  for (int i = 0; i < k; ++i) w[i] /= tot;
+  return k;
+}
+
+static int tri_rule(int n, double* a, double* b, double* w) {
+  double g[8], gw[8];
+  orc_gauss_legendre(n, g, gw);
+  int k = 0;
+  double tot = 0.0;
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) {
+      double u = 0.5 * (g[i] + 1.0), v = 0.5 * (g[j] + 1.0);
+      a[k] = u; b[k] = v * (1.0 - u);
+      w[k] = 0.25 * gw[i] * gw[j] * (1.0 - u);
+      tot += w[k];
+      ++k;
+    }
+  for (int i = 0; i < k; ++i) w[i] /= tot;
+  return k;
+}
+
+/* Gram-Schmidt coefficients: phi_l = sum_j C[l][j] r^a_j s^b_j t^c_j */
+static void tet_basis_coeffs(int deg, double C[MAXML3][MAXML3]) {
+  int ML = orc3_num_modes(deg), abc[3 * MAXML3];
+  orc3_mode_exponents(deg, abc);
+  double r[512], s[512], t[512], w[512];
+  int nq = tet_rule(deg + 2, r, s, t, w);   /* exact to degree 2 deg + 1 >= 2 deg */
+  static double M[512][MAXML3];
+  for (int q = 0; q < nq; ++q)
+    for (int j = 0; j < ML; ++j) M[q][j] = pow(r[q], abc[3 * j]) * pow(s[q], abc[3 * j + 1]) * pow(t[q], abc[3 * j + 2]);
+  long double Cl[MAXML3][MAXML3];
+  for (int l = 0; l < ML; ++l) {
+    for (int j = 0; j < ML; ++j) Cl[l][j] = (j == l) ? 1.0L : 0.0L;
+    for (int pass = 0; pass < 2; ++pass)   /* twice, for orthogonality to rounding */
+      for (int m = 0; m < l; ++m) {
+        long double ip = 0.0L;
+        for (int q = 0; q < nq; ++q) {
+          long double a = 0.0L, b = 0.0L;
+          for (int j = 0; j < ML; ++j) { a += Cl[l][j] * M[q][j]; b += Cl[m][j] * M[q][j]; }
+          ip += (long double)w[q] * a * b;
+        }
+        for (int j = 0; j < ML; ++j) Cl[l][j] -= ip * Cl[m][j];
+      }
+    long double nn = 0.0L;
+    for (int q = 0; q < nq; ++q) {
+      long double a = 0.0L;
+      for (int j = 0; j < ML; ++j) a += Cl[l][j] * M[q][j];
+      nn += (long double)w[q] * a * a;
+    }
+    for (int j = 0; j < ML; ++j) Cl[l][j] /= sqrtl(nn);
+  }
+  for (int l = 0; l < ML; ++l)
+    for (int j = 0; j < ML; ++j) C[l][j] = (double)Cl[l][j];
+}
+
+int orc3_tet_basis_eval(int deg, int npts, const double* r, const double* s, const double* t, double* phi,
+                        double* dr, double* ds, double* dt) {
+  int ML = orc3_num_modes(deg), abc[3 * MAXML3];
+  orc3_mode_exponents(deg, abc);
+  double C[MAXML3][MAXML3];
+  tet_basis_coeffs(deg, C);
+  for (int p = 0; p < npts; ++p) {
+    double m[MAXML3], mr[MAXML3], ms[MAXML3], mt[MAXML3];
+    for (int j = 0; j < ML; ++j) {
+      int a = abc[3 * j], b = abc[3 * j + 1], c = abc[3 * j + 2];
+      double pr = pow(r[p], a), ps = pow(s[p], b), pt = pow(t[p], c);
+      m[j] = pr * ps * pt;
+      mr[j] = a ? a * pow(r[p], a - 1) * ps * pt : 0.0;
+      ms[j] = b ? b * pr * pow(s[p], b - 1) * pt : 0.0;
+      mt[j] = c ? c * pr * ps * pow(t[p], c - 1) : 0.0;
+    }
+    for (int l = 0; l < ML; ++l) {
+      double v = 0, x = 0, y = 0, z = 0;
+      for (int j = 0; j < ML; ++j) { v += C[l][j] * m[j]; x += C[l][j] * mr[j]; y += C[l][j] * ms[j]; z += C[l][j] * mt[j]; }
+      if (phi) phi[p * ML + l] = v;
+      if (dr) dr[p * ML + l] = x;
+      if (ds) ds[p * ML + l] = y;
+      if (dt) dt[p * ML + l] = z;
+    }
+  }
+  return ML;
+}
+
+/* ------------------------------------------------------------------ */
+/* Meshes: per-element geometry for both kinds                          */
+/* ------------------------------------------------------------------ */
+enum { KIND3_HEX = 0, KIND3_TET = 1 };
+
 struct orc3_mesh {
-  int nx, ny, nz, N;
-  double box[6], h[3];
-  int bc[6];
-  int* nbr;      /* [N][6]: neighbour, or -1 - bc on a boundary side */
+  int kind, E, N;
+  int nx, ny, nz;       /* hexahedra */
+  double *vol, *org, *Jm, *Ji;   /* [N], [N][3], [N][9] dx_a/dr_b, [N][9] dr_a/dx_b */
+  double* nrm;          /* [N][E][3] outward normal scaled by the face area */
+  int *nbr, *nbk;       /* [N][E]: neighbour (or -1 - bc) and its local face */
+  int* canon;           /* tetrahedra [N][4][3]: the face's local vertices in id order */
   int nfaces;
-  int *f_i, *f_k, *f_j;   /* face: owner i, its local face k, neighbour j (or -1 - bc) */
-  int* face_of;  /* [N][6] face index */
-  double* eps;   /* [N][6] +1 owner side, -1 neighbour side */
+  int *f_i, *f_k, *f_j; /* face: owner i, its local face k, neighbour j (or -1 - bc) */
+  int* face_of;         /* [N][E] */
+  double* eps;          /* [N][E] +1 owner side, -1 neighbour side */
   double hmin;
 };
 
+static orc3_mesh* mesh3_alloc(int kind, int N) {
+  orc3_mesh* m = calloc(1, sizeof(orc3_mesh));
+  m->kind = kind; m->E = kind == KIND3_HEX ? 6 : 4; m->N = N;
+  int E = m->E;
+  m->vol = malloc(sizeof(double) * N); m->org = malloc(sizeof(double) * 3 * N);
+  m->Jm = malloc(sizeof(double) * 9 * N); m->Ji = malloc(sizeof(double) * 9 * N);
+  m->nrm = malloc(sizeof(double) * 3 * E * N);
+  m->nbr = malloc(sizeof(int) * E * N); m->nbk = malloc(sizeof(int) * E * N);
+  m->f_i = malloc(sizeof(int) * E * N); m->f_k = malloc(sizeof(int) * E * N); m->f_j = malloc(sizeof(int) * E * N);
+  m->face_of = malloc(sizeof(int) * E * N); m->eps = malloc(sizeof(double) * E * N);
+  return m;
+}
+
+/* faces: owned by the cell of lower index (or the lower local face when a
+ * cell meets itself across a period); boundary faces by their cell */
+static void mesh3_faces(orc3_mesh* m) {
+  int E = m->E, nf = 0;
+  for (int i = 0; i < m->N; ++i)
+    for (int k = 0; k < E; ++k) {
+      int j = m->nbr[E * i + k], kj = m->nbk[E * i + k];
+      if (j < 0 || i < j || (i == j && k < kj)) {
+        m->f_i[nf] = i; m->f_k[nf] = k; m->f_j[nf] = j;
+        m->face_of[E * i + k] = nf; m->eps[E * i + k] = 1.0;
+        ++nf;
+      }
+    }
+  for (int i = 0; i < m->N; ++i)
+    for (int k = 0; k < E; ++k) {
+      int j = m->nbr[E * i + k], kj = m->nbk[E * i + k];
+      if (!(j < 0 || i < j || (i == j && k < kj))) {
+        m->face_of[E * i + k] = m->face_of[E * j + kj];
+        m->eps[E * i + k] = -1.0;
+      }
+    }
+  m->nfaces = nf;
+  m->hmin = 1e300;
+  for (int i = 0; i < m->N; ++i) {
+    double surf = 0.0;
+    for (int k = 0; k < E; ++k) {
+      const double* n = m->nrm + 3 * (E * i + k);
+      surf += sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    }
+    double hm = 3.0 * m->vol[i] / surf;
+    if (hm < m->hmin) m->hmin = hm;
+  }
+}
+
 orc3_mesh* orc3_mesh_cartesian(int nx, int ny, int nz, const double* box, const int* bc) {
   if (nx < 1 || ny < 1 || nz < 1) return NULL;
-  orc3_mesh* m = calloc(1, sizeof(orc3_mesh));
-  m->nx = nx; m->ny = ny; m->nz = nz; m->N = nx * ny * nz;
-  memcpy(m->box, box, sizeof(double) * 6);
-  memcpy(m->bc, bc, sizeof(int) * 6);
-  m->h[0] = (box[1] - box[0]) / nx; m->h[1] = (box[3] - box[2]) / ny; m->h[2] = (box[5] - box[4]) / nz;
-  int N = m->N, n3[3] = {nx, ny, nz};
-  m->nbr = malloc(sizeof(int) * 6 * N);
+  int N = nx * ny * nz, n3[3] = {nx, ny, nz};
+  orc3_mesh* m = mesh3_alloc(KIND3_HEX, N);
+  m->nx = nx; m->ny = ny; m->nz = nz;
+  double h[3] = {(box[1] - box[0]) / nx, (box[3] - box[2]) / ny, (box[5] - box[4]) / nz};
   for (int iz = 0; iz < nz; ++iz)
     for (int iy = 0; iy < ny; ++iy)
       for (int ix = 0; ix < nx; ++ix) {
         int i = (iz * ny + iy) * nx + ix, c[3] = {ix, iy, iz};
+        m->vol[i] = h[0] * h[1] * h[2];
+        for (int d = 0; d < 3; ++d) m->org[3 * i + d] = box[2 * d] + (c[d] + 0.5) * h[d];
+        for (int a = 0; a < 9; ++a) { m->Jm[9 * i + a] = 0.0; m->Ji[9 * i + a] = 0.0; }
+        for (int d = 0; d < 3; ++d) { m->Jm[9 * i + 4 * d] = 0.5 * h[d]; m->Ji[9 * i + 4 * d] = 2.0 / h[d]; }
         for (int k = 0; k < 6; ++k) {
-          int d = k / 2, step = k % 2 ? 1 : -1;
-          int cc[3] = {c[0], c[1], c[2]};
-          cc[d] += step;
-          int side = k;   /* the domain side this face lies on when cc leaves the box */
+          int d = k / 2, cc[3] = {c[0], c[1], c[2]};
+          double* n = m->nrm + 3 * (6 * i + k);
+          n[0] = n[1] = n[2] = 0.0;
+          n[d] = (k % 2 ? 1.0 : -1.0) * m->vol[i] / h[d];
+          m->nbk[6 * i + k] = k ^ 1;
+          cc[d] += k % 2 ? 1 : -1;
           if (cc[d] < 0 || cc[d] >= n3[d]) {
-            if (bc[side] == B3_PERIODIC) cc[d] = (cc[d] + n3[d]) % n3[d];
-            else { m->nbr[6 * i + k] = -1 - bc[side]; continue; }
+            if (bc[k] == B3_PERIODIC) cc[d] = (cc[d] + n3[d]) % n3[d];
+            else { m->nbr[6 * i + k] = -1 - bc[k]; continue; }
           }
           m->nbr[6 * i + k] = (cc[2] * ny + cc[1]) * nx + cc[0];
         }
       }
-  /* faces: every + face of a cell, and the - faces on non-periodic boundaries */
-  m->f_i = malloc(sizeof(int) * 6 * N); m->f_k = malloc(sizeof(int) * 6 * N); m->f_j = malloc(sizeof(int) * 6 * N);
-  m->face_of = malloc(sizeof(int) * 6 * N);
-  m->eps = malloc(sizeof(double) * 6 * N);
-  int nf = 0;
-  for (int i = 0; i < N; ++i)
-    for (int k = 0; k < 6; ++k) {
-      int j = m->nbr[6 * i + k];
-      if (k % 2 == 1 || j < 0) {
-        m->f_i[nf] = i; m->f_k[nf] = k; m->f_j[nf] = j;
-        m->face_of[6 * i + k] = nf; m->eps[6 * i + k] = 1.0;
-        ++nf;
-      }
+  mesh3_faces(m);
+  return m;
+}
+
+static int cmp3(const void* a, const void* b) {
+  const long long* x = a; const long long* y = b;
+  for (int c = 0; c < 3; ++c) if (x[c] != y[c]) return x[c] < y[c] ? -1 : 1;
+  return 0;
+}
+
+orc3_mesh* orc3_mesh_tets(int nv, const double* xyz, int nt, const int* tets, const int* vid, const int* fbc) {
+  if (nt < 1 || nv < 4) return NULL;
+  orc3_mesh* m = mesh3_alloc(KIND3_TET, nt);
+  m->canon = malloc(sizeof(int) * 12 * nt);
+  /* records (sorted ids of face, cell * 4 + face) for matching */
+  long long* rec = malloc(sizeof(long long) * 4 * 4 * nt);
+  for (int i = 0; i < nt; ++i) {
+    const int* v = tets + 4 * i;
+    for (int a = 0; a < 4; ++a)
+      if (v[a] < 0 || v[a] >= nv) { free(rec); orc3_mesh_free(m); return NULL; }
+    const double *x0 = xyz + 3 * v[0];
+    double* J = m->Jm + 9 * i;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) J[3 * a + b] = xyz[3 * v[b + 1] + a] - x0[a];
+    double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) + J[2] * (J[3] * J[7] - J[4] * J[6]);
+    if (!(det > 0.0)) { free(rec); orc3_mesh_free(m); return NULL; }
+    m->vol[i] = det / 6.0;
+    double* K = m->Ji + 9 * i;   /* inverse by cofactors */
+    K[0] = (J[4] * J[8] - J[5] * J[7]) / det; K[1] = (J[2] * J[7] - J[1] * J[8]) / det; K[2] = (J[1] * J[5] - J[2] * J[4]) / det;
+    K[3] = (J[5] * J[6] - J[3] * J[8]) / det; K[4] = (J[0] * J[8] - J[2] * J[6]) / det; K[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+    K[6] = (J[3] * J[7] - J[4] * J[6]) / det; K[7] = (J[1] * J[6] - J[0] * J[7]) / det; K[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+    for (int d = 0; d < 3; ++d) m->org[3 * i + d] = x0[d];
+    for (int k = 0; k < 4; ++k) {
+      int lv[3], c = 0;
+      for (int a = 0; a < 4; ++a) if (a != k) lv[c++] = a;
+      /* canonical order: ascending vertex id */
+      for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b)
+          if (vid[v[lv[b]]] < vid[v[lv[a]]]) { int t = lv[a]; lv[a] = lv[b]; lv[b] = t; }
+      for (int a = 0; a < 3; ++a) m->canon[12 * i + 3 * k + a] = lv[a];
+      const double *pa = xyz + 3 * v[lv[0]], *pb = xyz + 3 * v[lv[1]], *pc = xyz + 3 * v[lv[2]], *po = xyz + 3 * v[k];
+      double e1[3], e2[3], n[3];
+      for (int d = 0; d < 3; ++d) { e1[d] = pb[d] - pa[d]; e2[d] = pc[d] - pa[d]; }
+      n[0] = 0.5 * (e1[1] * e2[2] - e1[2] * e2[1]);
+      n[1] = 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]);
+      n[2] = 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
+      double side = n[0] * (po[0] - pa[0]) + n[1] * (po[1] - pa[1]) + n[2] * (po[2] - pa[2]);
+      double sg = side > 0.0 ? -1.0 : 1.0;
+      for (int d = 0; d < 3; ++d) m->nrm[3 * (4 * i + k) + d] = sg * n[d];
+      long long* r = rec + 4 * (4 * i + k);
+      r[0] = vid[v[lv[0]]]; r[1] = vid[v[lv[1]]]; r[2] = vid[v[lv[2]]]; r[3] = 4 * i + k;
     }
-  for (int i = 0; i < N; ++i)
-    for (int k = 0; k < 6; k += 2) {
-      int j = m->nbr[6 * i + k];
-      if (j >= 0) {   /* the - face of i is the + face of j */
-        m->face_of[6 * i + k] = m->face_of[6 * j + k + 1];
-        m->eps[6 * i + k] = -1.0;
-      }
+  }
+  qsort(rec, (size_t)4 * nt, sizeof(long long) * 4, cmp3);
+  for (int i = 0; i < 4 * nt; ++i) { int c = (int)rec[4 * i + 3]; m->nbr[c] = -1 - B3_TRANSPARENT; m->nbk[c] = -1; }
+  for (int i = 0; i < 4 * nt;) {
+    int j = i + 1;
+    while (j < 4 * nt && cmp3(rec + 4 * i, rec + 4 * j) == 0) ++j;
+    if (j - i == 2) {
+      int a = (int)rec[4 * i + 3], b = (int)rec[4 * i + 7];
+      m->nbr[a] = b / 4; m->nbk[a] = b % 4;
+      m->nbr[b] = a / 4; m->nbk[b] = a % 4;
+    } else if (j - i == 1) {
+      int a = (int)rec[4 * i + 3];
+      m->nbr[a] = -1 - (fbc ? fbc[a] : B3_TRANSPARENT);
+    } else {
+      free(rec); orc3_mesh_free(m); return NULL;   /* a face shared by more than two cells */
     }
-  m->nfaces = nf;
-  double vol = m->h[0] * m->h[1] * m->h[2];
-  double surf = 2.0 * (m->h[0] * m->h[1] + m->h[1] * m->h[2] + m->h[0] * m->h[2]);
-  m->hmin = 3.0 * vol / surf;
+    i = j;
+  }
+  free(rec);
+  mesh3_faces(m);
   return m;
 }
 
 void orc3_mesh_free(orc3_mesh* m) {
   if (!m) return;
-  free(m->nbr); free(m->f_i); free(m->f_k); free(m->f_j); free(m->face_of); free(m->eps);
+  free(m->vol); free(m->org); free(m->Jm); free(m->Ji); free(m->nrm); free(m->nbr); free(m->nbk);
+  free(m->canon); free(m->f_i); free(m->f_k); free(m->f_j); free(m->face_of); free(m->eps);
   free(m);
 }
 
 int orc3_mesh_num_elements(const orc3_mesh* m) { return m->N; }
+int orc3_mesh_faces_per_element(const orc3_mesh* m) { return m->E; }
 
-static void cell_origin(const orc3_mesh* m, int i, double* o) {
-  int ix = i % m->nx, iy = (i / m->nx) % m->ny, iz = i / (m->nx * m->ny);
-  o[0] = m->box[0] + (ix + 0.5) * m->h[0];
-  o[1] = m->box[2] + (iy + 0.5) * m->h[1];
-  o[2] = m->box[4] + (iz + 0.5) * m->h[2];
+/* reference -> physical: x = org + Jm r */
+static void to_phys(const orc3_mesh* m, int i, const double* r, double* x) {
+  const double *o = m->org + 3 * i, *J = m->Jm + 9 * i;
+  for (int a = 0; a < 3; ++a) x[a] = o[a] + J[3 * a] * r[0] + J[3 * a + 1] * r[1] + J[3 * a + 2] * r[2];
 }
 
 void orc3_mesh_geometry(const orc3_mesh* m, double* vol, double* cx, double* cy, double* cz) {
   for (int i = 0; i < m->N; ++i) {
-    double o[3];
-    cell_origin(m, i, o);
-    if (vol) vol[i] = m->h[0] * m->h[1] * m->h[2];
-    if (cx) cx[i] = o[0];
-    if (cy) cy[i] = o[1];
-    if (cz) cz[i] = o[2];
+    double rc[3], x[3];
+    if (m->kind == KIND3_HEX) { rc[0] = rc[1] = rc[2] = 0.0; }
+    else { rc[0] = rc[1] = rc[2] = 0.25; }
+    to_phys(m, i, rc, x);
+    if (vol) vol[i] = m->vol[i];
+    if (cx) cx[i] = x[0];
+    if (cy) cy[i] = x[1];
+    if (cz) cz[i] = x[2];
   }
-}
-
-/* outward normal of face k scaled by the face area */
-static void face_normal(const orc3_mesh* m, int k, double* n) {
-  int d = k / 2;
-  double area = m->h[0] * m->h[1] * m->h[2] / m->h[d];
-  n[0] = n[1] = n[2] = 0.0;
-  n[d] = k % 2 ? area : -area;
 }
 
 /* ------------------------------------------------------------------ */
@@ -256,94 +466,132 @@ static void face_normal(const orc3_mesh* m, int k, double* n) {
 /* ------------------------------------------------------------------ */
 struct orc3_solver {
   const orc3_mesh* m;
-  int deg, ML, n, NQ, NF, NPT, NPJ;
+  int kind, deg, ML, E, NQ, NF, NPT, NPJ;
   double gamma, eps0, alpha0;
   int shock_limiter, llf_global;
-  double qw[MAXQ3], fw2[MAXF3];                     /* interior / face weights, each summing to 1 */
-  double px[MAXPTS3], py[MAXPTS3], pz[MAXPTS3];     /* reference points */
-  double phi[MAXPTS3][MAXML3], dxi[MAXPTS3][MAXML3], deta[MAXPTS3][MAXML3], dzeta[MAXPTS3][MAXML3];
+  double qw[MAXQ3], fw2[MAXF3];                        /* interior / face weights, each summing to 1 */
+  double px[MAXPTS3], py[MAXPTS3], pz[MAXPTS3];        /* reference points (tetrahedra: interior only) */
+  double phi[MAXPTS3][MAXML3];                         /* basis there */
+  double dref[MAXQ3][3][MAXML3];                       /* reference gradient at the interior points */
+  double* fphi;   /* tetrahedra: [N][4][NF][ML] basis at each cell's face points (canonical order) */
+  double* fref;   /* tetrahedra: [N][4][NF][3] their reference coordinates */
   double jx[MAXPJ3], jy[MAXPJ3], jz[MAXPJ3], jw[MAXPJ3], jphi[MAXPJ3][MAXML3];
-  double *V, *tq, *tqt, *tqtt, *tF;   /* V[N][ML][5]; traces [N][6][NF][5], tF [N][6][NF][3][5] */
+  double *V, *tq, *tqt, *tqtt, *tF;   /* V[N][ML][5]; traces [N][E][NF][5], tF [N][E][NF][3][5] */
   double *fstar, *flxw, *flxf;        /* per face: [nf][NF][5], [nf][5], [nf][5] */
-  double* prop;                       /* [N][6] */
+  double* prop;                       /* [N][E] */
   double last_dt;
 };
+
+static const double TREF3[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
 
 orc3_solver* orc3_solver_new(const orc3_mesh* m, int deg, double gamma) {
   if (deg < 1 || deg > 3) return NULL;
   orc3_solver* s = calloc(1, sizeof(orc3_solver));
-  s->m = m; s->deg = deg; s->gamma = gamma;
+  s->m = m; s->kind = m->kind; s->deg = deg; s->gamma = gamma; s->E = m->E;
   s->eps0 = 1e-12; s->alpha0 = 500.0; s->shock_limiter = 1;
   s->ML = orc3_num_modes(deg);
-  int n = deg + 1;
-  s->n = n;
+  int n = deg + 1, E = m->E;
   double g[8], gw[8];
   orc_gauss_legendre(n, g, gw);
-  s->NQ = n * n * n; s->NF = n * n;
-  for (int c = 0; c < n; ++c)
-    for (int b = 0; b < n; ++b)
-      for (int a = 0; a < n; ++a) {
-        int k = (c * n + b) * n + a;
-        s->px[k] = g[a]; s->py[k] = g[b]; s->pz[k] = g[c];
-        s->qw[k] = gw[a] * gw[b] * gw[c] / 8.0;
-      }
-  for (int t = 0; t < n; ++t)
-    for (int u = 0; u < n; ++u) s->fw2[t * n + u] = gw[u] * gw[t] / 4.0;
-  for (int k = 0; k < 6; ++k) {
-    int d = k / 2, d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;   /* tangential directions, x-y-z order */
-    double side = k % 2 ? 1.0 : -1.0;
-    for (int t = 0; t < n; ++t)
-      for (int u = 0; u < n; ++u) {
-        int idx = s->NQ + k * s->NF + t * n + u;
-        double r[3];
-        r[d] = side; r[d1] = g[u]; r[d2] = g[t];
-        s->px[idx] = r[0]; s->py[idx] = r[1]; s->pz[idx] = r[2];
-      }
-  }
-  s->NPT = s->NQ + 6 * s->NF;
-  /* the projection rule has more points than the limiter set */
   const size_t cap = (size_t)(MAXPJ3 > MAXPTS3 ? MAXPJ3 : MAXPTS3) * MAXML3;
   double *ph = malloc(sizeof(double) * cap), *dx = malloc(sizeof(double) * cap);
   double *dy = malloc(sizeof(double) * cap), *dz = malloc(sizeof(double) * cap);
-  orc3_basis_eval(deg, s->NPT, s->px, s->py, s->pz, ph, dx, dy, dz);
-  for (int p = 0; p < s->NPT; ++p)
+  if (s->kind == KIND3_HEX) {
+    s->NQ = n * n * n; s->NF = n * n;
+    for (int c = 0; c < n; ++c)
+      for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+          int k = (c * n + b) * n + a;
+          s->px[k] = g[a]; s->py[k] = g[b]; s->pz[k] = g[c];
+          s->qw[k] = gw[a] * gw[b] * gw[c] / 8.0;
+        }
+    for (int t = 0; t < n; ++t)
+      for (int u = 0; u < n; ++u) s->fw2[t * n + u] = gw[u] * gw[t] / 4.0;
+    for (int k = 0; k < 6; ++k) {
+      int d = k / 2, d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;   /* tangential directions, x-y-z order */
+      double side = k % 2 ? 1.0 : -1.0;
+      for (int t = 0; t < n; ++t)
+        for (int u = 0; u < n; ++u) {
+          int idx = s->NQ + k * s->NF + t * n + u;
+          double r[3];
+          r[d] = side; r[d1] = g[u]; r[d2] = g[t];
+          s->px[idx] = r[0]; s->py[idx] = r[1]; s->pz[idx] = r[2];
+        }
+    }
+    s->NPT = s->NQ + 6 * s->NF;
+    orc3_basis_eval(deg, s->NPT, s->px, s->py, s->pz, ph, dx, dy, dz);
+  } else {
+    s->NQ = tet_rule(deg + 2, s->px, s->py, s->pz, s->qw);
+    double fa[MAXF3], fb[MAXF3];
+    s->NF = tri_rule(n, fa, fb, s->fw2);
+    s->NPT = s->NQ + 4 * s->NF;
+    orc3_tet_basis_eval(deg, s->NQ, s->px, s->py, s->pz, ph, dx, dy, dz);
+    /* face points of every cell, from its face's vertices in id order */
+    size_t N = (size_t)m->N, NF = (size_t)s->NF, ML = (size_t)s->ML;
+    s->fref = malloc(sizeof(double) * N * 4 * NF * 3);
+    s->fphi = malloc(sizeof(double) * N * 4 * NF * ML);
+    for (size_t i = 0; i < N; ++i)
+      for (int k = 0; k < 4; ++k) {
+        const int* cv = m->canon + 12 * i + 3 * k;
+        double rr[MAXF3], rs[MAXF3], rt[MAXF3];
+        for (size_t p = 0; p < NF; ++p) {
+          double l1 = fa[p], l2 = fb[p], l0 = 1.0 - l1 - l2;
+          double r[3];
+          for (int d = 0; d < 3; ++d) r[d] = l0 * TREF3[cv[0]][d] + l1 * TREF3[cv[1]][d] + l2 * TREF3[cv[2]][d];
+          rr[p] = r[0]; rs[p] = r[1]; rt[p] = r[2];
+          for (int d = 0; d < 3; ++d) s->fref[((i * 4 + k) * NF + p) * 3 + d] = r[d];
+        }
+        double fp[MAXF3 * MAXML3];
+        orc3_tet_basis_eval(deg, (int)NF, rr, rs, rt, fp, NULL, NULL, NULL);
+        memcpy(s->fphi + (i * 4 + k) * NF * ML, fp, sizeof(double) * NF * ML);
+      }
+  }
+  int nint = s->kind == KIND3_HEX ? s->NPT : s->NQ;
+  for (int p = 0; p < nint; ++p)
+    for (int l = 0; l < s->ML; ++l) s->phi[p][l] = ph[p * s->ML + l];
+  for (int p = 0; p < s->NQ; ++p)
     for (int l = 0; l < s->ML; ++l) {
-      s->phi[p][l] = ph[p * s->ML + l];
-      s->dxi[p][l] = dx[p * s->ML + l];
-      s->deta[p][l] = dy[p * s->ML + l];
-      s->dzeta[p][l] = dz[p * s->ML + l];
+      s->dref[p][0][l] = dx[p * s->ML + l];
+      s->dref[p][1][l] = dy[p * s->ML + l];
+      s->dref[p][2][l] = dz[p * s->ML + l];
     }
   /* projection rule: deg + 3 points per direction */
   int nj = deg + 3;
-  double gj[8], gjw[8];
-  orc_gauss_legendre(nj, gj, gjw);
-  s->NPJ = nj * nj * nj;
-  for (int c = 0; c < nj; ++c)
-    for (int b = 0; b < nj; ++b)
-      for (int a = 0; a < nj; ++a) {
-        int k = (c * nj + b) * nj + a;
-        s->jx[k] = gj[a]; s->jy[k] = gj[b]; s->jz[k] = gj[c];
-        s->jw[k] = gjw[a] * gjw[b] * gjw[c] / 8.0;
-      }
-  orc3_basis_eval(deg, s->NPJ, s->jx, s->jy, s->jz, ph, NULL, NULL, NULL);
+  if (s->kind == KIND3_HEX) {
+    double gj[8], gjw[8];
+    orc_gauss_legendre(nj, gj, gjw);
+    s->NPJ = nj * nj * nj;
+    for (int c = 0; c < nj; ++c)
+      for (int b = 0; b < nj; ++b)
+        for (int a = 0; a < nj; ++a) {
+          int k = (c * nj + b) * nj + a;
+          s->jx[k] = gj[a]; s->jy[k] = gj[b]; s->jz[k] = gj[c];
+          s->jw[k] = gjw[a] * gjw[b] * gjw[c] / 8.0;
+        }
+    orc3_basis_eval(deg, s->NPJ, s->jx, s->jy, s->jz, ph, NULL, NULL, NULL);
+  } else {
+    s->NPJ = tet_rule(nj, s->jx, s->jy, s->jz, s->jw);
+    orc3_tet_basis_eval(deg, s->NPJ, s->jx, s->jy, s->jz, ph, NULL, NULL, NULL);
+  }
   for (int p = 0; p < s->NPJ; ++p)
     for (int l = 0; l < s->ML; ++l) s->jphi[p][l] = ph[p * s->ML + l];
   free(ph); free(dx); free(dy); free(dz);
   size_t N = (size_t)m->N, NF = (size_t)s->NF, nf = (size_t)m->nfaces;
   s->V = malloc(sizeof(double) * N * s->ML * NV3);
-  s->tq = malloc(sizeof(double) * N * 6 * NF * NV3);
-  s->tqt = malloc(sizeof(double) * N * 6 * NF * NV3);
-  s->tqtt = malloc(sizeof(double) * N * 6 * NF * NV3);
-  s->tF = malloc(sizeof(double) * N * 6 * NF * 3 * NV3);
+  s->tq = malloc(sizeof(double) * N * E * NF * NV3);
+  s->tqt = malloc(sizeof(double) * N * E * NF * NV3);
+  s->tqtt = malloc(sizeof(double) * N * E * NF * NV3);
+  s->tF = malloc(sizeof(double) * N * E * NF * 3 * NV3);
   s->fstar = malloc(sizeof(double) * nf * NF * NV3);
   s->flxw = malloc(sizeof(double) * nf * NV3);
   s->flxf = malloc(sizeof(double) * nf * NV3);
-  s->prop = malloc(sizeof(double) * N * 6);
+  s->prop = malloc(sizeof(double) * N * E);
   return s;
 }
 
 void orc3_solver_free(orc3_solver* s) {
   if (!s) return;
+  free(s->fphi); free(s->fref);
   free(s->V); free(s->tq); free(s->tqt); free(s->tqtt); free(s->tF);
   free(s->fstar); free(s->flxw); free(s->flxf); free(s->prop);
   free(s);
@@ -357,18 +605,27 @@ int orc3_solver_num_modes(const orc3_solver* s) { return s->ML; }
 int orc3_solver_num_points(const orc3_solver* s) { return s->NPT; }
 int orc3_projection_num_points(const orc3_solver* s) { return s->NPJ; }
 
+/* basis at point p of cell i: interior points (and the hexahedra's face
+ * points) from the shared table, the tetrahedra's face points per cell */
+static const double* phi_at(const orc3_solver* s, int i, int p) {
+  if (p < s->NQ || s->kind == KIND3_HEX) return s->phi[p];
+  int k = (p - s->NQ) / s->NF, pe = (p - s->NQ) % s->NF;
+  return s->fphi + (((size_t)i * 4 + k) * s->NF + pe) * s->ML;
+}
+
+static void ref_at(const orc3_solver* s, int i, int p, double* r) {
+  if (p < s->NQ || s->kind == KIND3_HEX) { r[0] = s->px[p]; r[1] = s->py[p]; r[2] = s->pz[p]; return; }
+  int k = (p - s->NQ) / s->NF, pe = (p - s->NQ) % s->NF;
+  const double* f = s->fref + (((size_t)i * 4 + k) * s->NF + pe) * 3;
+  r[0] = f[0]; r[1] = f[1]; r[2] = f[2];
+}
+
 void orc3_projection_points(const orc3_solver* s, double* xyz) {
-  const orc3_mesh* m = s->m;
-  for (int i = 0; i < m->N; ++i) {
-    double o[3];
-    cell_origin(m, i, o);
+  for (int i = 0; i < s->m->N; ++i)
     for (int p = 0; p < s->NPJ; ++p) {
-      double* r = xyz + ((size_t)i * s->NPJ + p) * 3;
-      r[0] = o[0] + 0.5 * m->h[0] * s->jx[p];
-      r[1] = o[1] + 0.5 * m->h[1] * s->jy[p];
-      r[2] = o[2] + 0.5 * m->h[2] * s->jz[p];
+      double r[3] = {s->jx[p], s->jy[p], s->jz[p]};
+      to_phys(s->m, i, r, xyz + ((size_t)i * s->NPJ + p) * 3);
     }
-  }
 }
 
 void orc3_projection_weights(const orc3_solver* s, double* w) {
@@ -406,29 +663,24 @@ void orc3_eval_projection_points(const orc3_solver* s, const double* Q, double* 
 }
 
 void orc3_limiter_points(const orc3_solver* s, double* xyz) {
-  const orc3_mesh* m = s->m;
-  for (int i = 0; i < m->N; ++i) {
-    double o[3];
-    cell_origin(m, i, o);
+  for (int i = 0; i < s->m->N; ++i)
     for (int p = 0; p < s->NPT; ++p) {
-      double* r = xyz + ((size_t)i * s->NPT + p) * 3;
-      r[0] = o[0] + 0.5 * m->h[0] * s->px[p];
-      r[1] = o[1] + 0.5 * m->h[1] * s->py[p];
-      r[2] = o[2] + 0.5 * m->h[2] * s->pz[p];
+      double r[3];
+      ref_at(s, i, p, r);
+      to_phys(s->m, i, r, xyz + ((size_t)i * s->NPT + p) * 3);
     }
-  }
 }
 
 void orc3_eval_limiter_points(const orc3_solver* s, const double* Q, double* q) {
   for (int i = 0; i < s->m->N; ++i)
     for (int p = 0; p < s->NPT; ++p)
-      eval_point3(s, Q + (size_t)i * NV3 * s->ML, s->phi[p], q + ((size_t)i * s->NPT + p) * 5);
+      eval_point3(s, Q + (size_t)i * NV3 * s->ML, phi_at(s, i, p), q + ((size_t)i * s->NPT + p) * 5);
 }
 
 /* ------------------------------------------------------------------ */
 /* Sec. 3.1: moment limiter (Steps 0-2) on one element                 */
 /* ------------------------------------------------------------------ */
-static double moment_limit3(const orc3_solver* s, double* Qi, int* status) {
+static double moment_limit3(const orc3_solver* s, int i, double* Qi, int* status) {
   int ML = s->ML;
   double g = s->gamma;
   double qbar[5];
@@ -442,12 +694,14 @@ static double moment_limit3(const orc3_solver* s, double* Qi, int* status) {
     return 0.0;
   }
   double dev[MAXPTS3][5];
-  for (int p = 0; p < s->NPT; ++p)
+  for (int p = 0; p < s->NPT; ++p) {
+    const double* ph = phi_at(s, i, p);
     for (int v = 0; v < NV3; ++v) {
       double a = 0.0;
-      for (int l = 1; l < ML; ++l) a += Qi[v * ML + l] * s->phi[p][l];
+      for (int l = 1; l < ML; ++l) a += Qi[v * ML + l] * ph[l];
       dev[p][v] = a;
     }
+  }
   /* Step 1: largest theta_rho keeping every point density at eps_rho or above */
   double eps_r = fmin(s->eps0, 0.5 * qbar[0]);
   double th_r = 1.0;
@@ -483,7 +737,7 @@ double orc3_moment_limit(const orc3_solver* s, double* Q, double* theta, int* st
 #pragma omp parallel for reduction(| : st) reduction(min : mn) schedule(static)
   for (int i = 0; i < s->m->N; ++i) {
     int sti = 0;
-    double t = moment_limit3(s, Q + (size_t)i * NV3 * s->ML, &sti);
+    double t = moment_limit3(s, i, Q + (size_t)i * NV3 * s->ML, &sti);
     if (theta) theta[i] = t;
     st |= sti;
     if (t < mn) mn = t;
@@ -503,7 +757,7 @@ double orc3_wave_speed(const orc3_solver* s, const double* Q) {
     if (a > smax) smax = a;
     for (int p = 0; p < s->NPT; ++p) {
       double q[5];
-      eval_point3(s, Qi, s->phi[p], q);
+      eval_point3(s, Qi, phi_at(s, i, p), q);
       double b = wave_speed3(s->gamma, q);
       if (b > smax) smax = b;
     }
@@ -513,92 +767,95 @@ double orc3_wave_speed(const orc3_solver* s, const double* Q) {
 
 /* ------------------------------------------------------------------ */
 /* Sec. 2.2-2.3: CK time-averaged flux on one element.  Project F onto  */
-/* the basis (interior rule), q_t = -div F^h, F_t = F'(q) q_t; project,  */
-/* q_tt = -div F_t^h, F_tt = F''(q)(q_t, q_t) + F'(q) q_tt;              */
-/* F_T = F + dt/2 F_t + dt^2/6 F_tt; volume integral Int grad phi . F_T. */
+/* the basis (interior rule); q_t = -div F^h at the interior points,     */
+/* projected onto the modes (it lies in the space) and evaluated at     */
+/* every point; F_t = F'(q) q_t, projected; q_tt = -div F_t^h likewise;  */
+/* F_tt = F''(q)(q_t, q_t) + F'(q) q_tt; F_T = F + dt/2 F_t + dt^2/6     */
+/* F_tt; volume integral Int grad phi . F_T.                             */
 /* ------------------------------------------------------------------ */
 typedef double pt5[5];
 typedef double pt35[3][5];
 
-static void ck3(const orc3_solver* s, const double* Qi, double dt, pt5* q, pt5* qt, pt5* qtt, pt35* FT,
-                double (*V)[5]) {
-  const orc3_mesh* m = s->m;
-  int ML = s->ML, NQ = s->NQ, NPT = s->NPT;
-  double g = s->gamma;
-  double sc[3] = {2.0 / m->h[0], 2.0 / m->h[1], 2.0 / m->h[2]};
-  double vol = m->h[0] * m->h[1] * m->h[2];
-  /* physical gradients of the basis: grad phi = (2/hx d/dxi, 2/hy d/deta, 2/hz d/dzeta) */
-  double (*gb)[3][MAXML3] = malloc(sizeof(double) * MAXPTS3 * 3 * MAXML3);
-  for (int p = 0; p < NPT; ++p)
-    for (int l = 0; l < ML; ++l) {
-      gb[p][0][l] = sc[0] * s->dxi[p][l];
-      gb[p][1][l] = sc[1] * s->deta[p][l];
-      gb[p][2][l] = sc[2] * s->dzeta[p][l];
-    }
-  pt35* F = malloc(sizeof(pt35) * MAXPTS3);
-  pt35* Ft = malloc(sizeof(pt35) * MAXPTS3);
-  pt35* Ftt = malloc(sizeof(pt35) * MAXPTS3);
-  for (int p = 0; p < NPT; ++p) {
-    eval_point3(s, Qi, s->phi[p], q[p]);
-    orc3_flux(g, q[p], &F[p][0][0]);
-  }
-  /* Galerkin expansion of F (the three directions) */
+/* modes of -div of the projection of a flux field given at the interior points */
+static void neg_div_modes(const orc3_solver* s, const double* Ji, pt35* Fk, double (*out)[5]) {
+  int ML = s->ML, NQ = s->NQ;
   double Fh[MAXML3][3][5];
   for (int l = 0; l < ML; ++l)
     for (int d = 0; d < 3; ++d)
       for (int v = 0; v < NV3; ++v) {
         double a = 0.0;
-        for (int k = 0; k < NQ; ++k) a += s->qw[k] * F[k][d][v] * s->phi[k][l];
+        for (int k = 0; k < NQ; ++k) a += s->qw[k] * Fk[k][d][v] * s->phi[k][l];
         Fh[l][d][v] = a;
       }
-  /* q_t = -div F^h and F_t = F'(q) q_t at every point */
+  for (int l = 0; l < ML; ++l)
+    for (int v = 0; v < NV3; ++v) out[l][v] = 0.0;
+  for (int k = 0; k < NQ; ++k) {
+    /* physical gradient: d phi / d x_d = sum_a (d r_a / d x_d) d phi / d r_a */
+    double div[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m < ML; ++m)
+      for (int d = 0; d < 3; ++d) {
+        double gd = Ji[0 * 3 + d] * s->dref[k][0][m] + Ji[1 * 3 + d] * s->dref[k][1][m] + Ji[2 * 3 + d] * s->dref[k][2][m];
+        for (int v = 0; v < NV3; ++v) div[v] += Fh[m][d][v] * gd;
+      }
+    for (int l = 0; l < ML; ++l)
+      for (int v = 0; v < NV3; ++v) out[l][v] -= s->qw[k] * div[v] * s->phi[k][l];
+  }
+}
+
+static void ck3(const orc3_solver* s, int i, const double* Qi, double dt, pt5* q, pt5* qt, pt5* qtt, pt35* FT,
+                double (*V)[5]) {
+  const orc3_mesh* m = s->m;
+  int ML = s->ML, NQ = s->NQ, NPT = s->NPT;
+  double g = s->gamma;
+  const double* Ji = m->Ji + 9 * i;
+  pt35* F = malloc(sizeof(pt35) * MAXPTS3);
+  pt35* Ft = malloc(sizeof(pt35) * MAXPTS3);
   for (int p = 0; p < NPT; ++p) {
+    eval_point3(s, Qi, phi_at(s, i, p), q[p]);
+    orc3_flux(g, q[p], &F[p][0][0]);
+  }
+  double Qt[MAXML3][5], Qtt[MAXML3][5];
+  neg_div_modes(s, Ji, F, Qt);
+  for (int p = 0; p < NPT; ++p) {
+    const double* ph = phi_at(s, i, p);
     for (int v = 0; v < NV3; ++v) {
       double a = 0.0;
-      for (int l = 0; l < ML; ++l)
-        for (int d = 0; d < 3; ++d) a += Fh[l][d][v] * gb[p][d][l];
-      qt[p][v] = -a;
+      for (int l = 0; l < ML; ++l) a += Qt[l][v] * ph[l];
+      qt[p][v] = a;
     }
     double qs[2][5], Fs[2][3][5];
     for (int v = 0; v < NV3; ++v) { qs[0][v] = q[p][v]; qs[1][v] = qt[p][v]; }
     orc3_flux_series(g, 1, &qs[0][0], &Fs[0][0][0]);
     memcpy(Ft[p], Fs[1], sizeof(pt35));
   }
-  double Fth[MAXML3][3][5];
-  for (int l = 0; l < ML; ++l)
-    for (int d = 0; d < 3; ++d)
-      for (int v = 0; v < NV3; ++v) {
-        double a = 0.0;
-        for (int k = 0; k < NQ; ++k) a += s->qw[k] * Ft[k][d][v] * s->phi[k][l];
-        Fth[l][d][v] = a;
-      }
-  /* q_tt = -div F_t^h; F_tt = twice the t^2 coefficient of F(q + t q_t + t^2 q_tt / 2) */
+  neg_div_modes(s, Ji, Ft, Qtt);
   for (int p = 0; p < NPT; ++p) {
+    const double* ph = phi_at(s, i, p);
     for (int v = 0; v < NV3; ++v) {
       double a = 0.0;
-      for (int l = 0; l < ML; ++l)
-        for (int d = 0; d < 3; ++d) a += Fth[l][d][v] * gb[p][d][l];
-      qtt[p][v] = -a;
+      for (int l = 0; l < ML; ++l) a += Qtt[l][v] * ph[l];
+      qtt[p][v] = a;
     }
+    /* F_tt = twice the t^2 coefficient of F(q + t q_t + t^2 q_tt / 2) */
     double qs[3][5], Fs[3][3][5];
     for (int v = 0; v < NV3; ++v) { qs[0][v] = q[p][v]; qs[1][v] = qt[p][v]; qs[2][v] = 0.5 * qtt[p][v]; }
     orc3_flux_series(g, 2, &qs[0][0], &Fs[0][0][0]);
     for (int d = 0; d < 3; ++d)
-      for (int v = 0; v < NV3; ++v) Ftt[p][d][v] = 2.0 * Fs[2][d][v];
-  }
-  for (int p = 0; p < NPT; ++p)
-    for (int d = 0; d < 3; ++d)
       for (int v = 0; v < NV3; ++v)
-        FT[p][d][v] = F[p][d][v] + dt / 2.0 * Ft[p][d][v] + dt * dt / 6.0 * Ftt[p][d][v];
+        FT[p][d][v] = F[p][d][v] + dt / 2.0 * Ft[p][d][v] + dt * dt / 6.0 * 2.0 * Fs[2][d][v];
+  }
   /* interior integral of grad phi_l . F_T over the cell */
   for (int l = 0; l < ML; ++l)
     for (int v = 0; v < NV3; ++v) {
       double a = 0.0;
       for (int k = 0; k < NQ; ++k)
-        for (int d = 0; d < 3; ++d) a += s->qw[k] * gb[k][d][l] * FT[k][d][v];
-      V[l][v] = vol * a;
+        for (int d = 0; d < 3; ++d) {
+          double gd = Ji[0 * 3 + d] * s->dref[k][0][l] + Ji[1 * 3 + d] * s->dref[k][1][l] + Ji[2 * 3 + d] * s->dref[k][2][l];
+          a += s->qw[k] * gd * FT[k][d][v];
+        }
+      V[l][v] = m->vol[i] * a;
     }
-  free(gb); free(F); free(Ft); free(Ftt);
+  free(F); free(Ft);
 }
 
 void orc3_ck_element(const orc3_solver* s, const double* Q, int i, double dt, double* q, double* qt,
@@ -608,7 +865,7 @@ void orc3_ck_element(const orc3_solver* s, const double* Q, int i, double dt, do
   pt5* c = malloc(sizeof(pt5) * MAXPTS3);
   pt35* f = malloc(sizeof(pt35) * MAXPTS3);
   double vv[MAXML3][5];
-  ck3(s, Q + (size_t)i * NV3 * s->ML, dt, a, b, c, f, vv);
+  ck3(s, i, Q + (size_t)i * NV3 * s->ML, dt, a, b, c, f, vv);
   for (int p = 0; p < s->NPT; ++p)
     for (int v = 0; v < NV3; ++v) {
       if (q) q[p * 5 + v] = a[p][v];
@@ -623,13 +880,14 @@ void orc3_ck_element(const orc3_solver* s, const double* Q, int i, double dt, do
   free(a); free(b); free(c); free(f);
 }
 
-/* ------------------------------------------------------------------ */
-/* Sec. 2.4 on a face of axis d: reflective flips the normal momentum,  */
-/* transparent copies; the same map applies to q, q_t and q_tt.          */
-/* ------------------------------------------------------------------ */
-static void boundary_state3(int bc, int d, const double* qin, double* qout) {
+/* Sec. 2.4 on a face of unit normal nh: reflective mirrors the momentum,
+ * transparent copies; the same map applies to q, q_t and q_tt. */
+static void boundary_state3(int bc, const double* nh, const double* qin, double* qout) {
   for (int v = 0; v < NV3; ++v) qout[v] = qin[v];
-  if (bc == B3_REFLECT) qout[1 + d] = -qin[1 + d];
+  if (bc == B3_REFLECT) {
+    double mn = qin[1] * nh[0] + qin[2] * nh[1] + qin[3] * nh[2];
+    for (int d = 0; d < 3; ++d) qout[1 + d] = qin[1 + d] - 2.0 * mn * nh[d];
+  }
 }
 
 /* F_T at one point from q, q_t, q_tt (boundary states) */
@@ -724,6 +982,7 @@ int orc3_flux_limit_cell(double g, double eps0, int E, double T, double dt, cons
   return Gam[0] < 0.0;
 }
 
+
 /* ------------------------------------------------------------------ */
 /* Sec. 4.1: shock limiter on (rho, u, v, w, p) (reading G14 in 3D)     */
 /* ------------------------------------------------------------------ */
@@ -731,9 +990,16 @@ static void primitive3(double g, const double* q, double* w) {
   w[0] = q[0]; w[1] = q[1] / q[0]; w[2] = q[2] / q[0]; w[3] = q[3] / q[0]; w[4] = pressure3(g, q);
 }
 
+static void unit_normal(const orc3_mesh* m, int i, int k, double* nh, double* ln) {
+  const double* n = m->nrm + 3 * ((size_t)m->E * i + k);
+  double l = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  for (int d = 0; d < 3; ++d) nh[d] = n[d] / l;
+  if (ln) *ln = l;
+}
+
 static double shock_theta3(const orc3_solver* s, const double* Q, int i) {
   const orc3_mesh* m = s->m;
-  int ML = s->ML;
+  int ML = s->ML, E = m->E;
   double g = s->gamma;
   const double* Qi = Q + (size_t)i * NV3 * ML;
   double qbar[5];
@@ -741,16 +1007,18 @@ static double shock_theta3(const orc3_solver* s, const double* Q, int i) {
   if (!(qbar[0] > 0.0)) return 0.0;
   double wbar[5];
   primitive3(g, qbar, wbar);
-  double alpha = s->alpha0 * pow(cbrt(m->h[0] * m->h[1] * m->h[2]), 1.5);
+  double alpha = s->alpha0 * pow(cbrt(m->vol[i]), 1.5);
   double Mx[5], Mn[5];
   for (int c = 0; c < 5; ++c) { Mx[c] = wbar[c] + alpha; Mn[c] = wbar[c] - alpha; }
-  for (int k = 0; k < 6; ++k) {
-    int j = m->nbr[6 * i + k];
+  for (int k = 0; k < E; ++k) {
+    int j = m->nbr[E * i + k];
     double qj[5];
     if (j >= 0) {
       for (int v = 0; v < NV3; ++v) qj[v] = Q[(size_t)j * NV3 * ML + v * ML];
     } else {
-      boundary_state3(-1 - j, k / 2, qbar, qj);
+      double nh[3];
+      unit_normal(m, i, k, nh, NULL);
+      boundary_state3(-1 - j, nh, qbar, qj);
     }
     if (!(qj[0] > 0.0)) continue;
     double wj[5];
@@ -764,7 +1032,7 @@ static double shock_theta3(const orc3_solver* s, const double* Q, int i) {
   for (int c = 0; c < 5; ++c) { hmax[c] = -1e300; hmin[c] = 1e300; }
   for (int p = 0; p < s->NPT; ++p) {
     double q[5], w[5];
-    eval_point3(s, Qi, s->phi[p], q);
+    eval_point3(s, Qi, phi_at(s, i, p), q);
     if (!(q[0] > 0.0)) return 0.0;
     primitive3(g, q, w);
     for (int c = 0; c < 5; ++c) {
@@ -796,15 +1064,14 @@ void orc3_shock_limit(const orc3_solver* s, double* Q, double* theta) {
 }
 
 /* ------------------------------------------------------------------ */
-/* One time step: Sec. 3.3 Steps 1-6 on six faces, then the shock      */
+/* One time step: Sec. 3.3 Steps 1-6 on the faces, then the shock       */
 /* limiter (outline Step 5).                                            */
 /* ------------------------------------------------------------------ */
 int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag, double* theta_mom,
               double* theta_sc, double* theta_face) {
   const orc3_mesh* m = s->m;
-  int N = m->N, ML = s->ML, NF = s->NF, NQ = s->NQ, nf = m->nfaces;
+  int N = m->N, ML = s->ML, NF = s->NF, NQ = s->NQ, nf = m->nfaces, E = m->E;
   double g = s->gamma;
-  double vol = m->h[0] * m->h[1] * m->h[2];
   int status = 0;
 
   /* Step 1: moment limiter */
@@ -814,7 +1081,7 @@ int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag,
 #pragma omp parallel for reduction(| : st) reduction(+ : nmom) schedule(static)
     for (int i = 0; i < N; ++i) {
       int sti = 0;
-      double t = moment_limit3(s, Q + (size_t)i * NV3 * ML, &sti);
+      double t = moment_limit3(s, i, Q + (size_t)i * NV3 * ML, &sti);
       if (theta_mom) theta_mom[i] = t;
       if (t < 1.0) ++nmom;
       st |= sti;
@@ -833,12 +1100,12 @@ int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag,
     pt5* qtt = malloc(sizeof(pt5) * MAXPTS3);
     pt35* FT = malloc(sizeof(pt35) * MAXPTS3);
     double V[MAXML3][5];
-    ck3(s, Q + (size_t)i * NV3 * ML, dt, q, qt, qtt, FT, V);
+    ck3(s, i, Q + (size_t)i * NV3 * ML, dt, q, qt, qtt, FT, V);
     for (int l = 0; l < ML; ++l)
       for (int v = 0; v < NV3; ++v) s->V[((size_t)i * ML + l) * NV3 + v] = V[l][v];
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < E; ++k)
       for (int p = 0; p < NF; ++p) {
-        size_t t = (((size_t)i * 6 + k) * NF + p) * NV3;
+        size_t t = (((size_t)i * E + k) * NF + p) * NV3;
         int src = NQ + k * NF + p;
         for (int v = 0; v < NV3; ++v) {
           s->tq[t + v] = q[src][v]; s->tqt[t + v] = qt[src][v]; s->tqtt[t + v] = qtt[src][v];
@@ -852,26 +1119,26 @@ int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag,
 #pragma omp parallel for schedule(static)
   for (int f = 0; f < nf; ++f) {
     int i = m->f_i[f], ki = m->f_k[f], j = m->f_j[f];
-    int d = ki / 2, kj = ki ^ 1;   /* the neighbour's matching face */
-    double n[3];
-    face_normal(m, ki, n);   /* outward for i, scaled by the face area */
-    double ln = fabs(n[d]);
+    int kj = j >= 0 ? m->nbk[E * i + ki] : -1;
+    const double* n = m->nrm + 3 * ((size_t)E * i + ki);   /* outward for i, scaled by the face area */
+    double nh[3], ln;
+    unit_normal(m, i, ki, nh, &ln);
     double fw[5] = {0, 0, 0, 0, 0};
     for (int p = 0; p < NF; ++p) {
-      size_t ti = (((size_t)i * 6 + ki) * NF + p) * NV3;
+      size_t ti = (((size_t)i * E + ki) * NF + p) * NV3;
       const double* qm = s->tq + ti;
       const double* Fm = s->tF + ti * 3;
       double qp[5], Fp[15];
       if (j >= 0) {
         /* both cells see the face's points in the same order */
-        size_t tj = (((size_t)j * 6 + kj) * NF + p) * NV3;
+        size_t tj = (((size_t)j * E + kj) * NF + p) * NV3;
         for (int v = 0; v < NV3; ++v) qp[v] = s->tq[tj + v];
         for (int c = 0; c < 15; ++c) Fp[c] = s->tF[tj * 3 + c];
       } else {
         double qtp[5], qttp[5];
-        boundary_state3(-1 - j, d, qm, qp);
-        boundary_state3(-1 - j, d, s->tqt + ti, qtp);
-        boundary_state3(-1 - j, d, s->tqtt + ti, qttp);
+        boundary_state3(-1 - j, nh, qm, qp);
+        boundary_state3(-1 - j, nh, s->tqt + ti, qtp);
+        boundary_state3(-1 - j, nh, s->tqtt + ti, qttp);
         ft_point3(g, dt, qp, qtp, qttp, Fp);
       }
       double sp = sw;
@@ -883,7 +1150,9 @@ int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag,
       double* fs = s->fstar + ((size_t)f * NF + p) * NV3;
       for (int v = 0; v < NV3; ++v) {
         /* Eq. LLF times the face area */
-        fs[v] = 0.5 * n[d] * (Fp[d * 5 + v] + Fm[d * 5 + v]) - 0.5 * sp * ln * (qp[v] - qm[v]);
+        double fn = 0.0;
+        for (int d = 0; d < 3; ++d) fn += n[d] * (Fp[d * 5 + v] + Fm[d * 5 + v]);
+        fs[v] = 0.5 * fn - 0.5 * sp * ln * (qp[v] - qm[v]);
         fw[v] += s->fw2[p] * fs[v];
       }
     }
@@ -893,14 +1162,16 @@ int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag,
     if (j >= 0) {
       for (int v = 0; v < NV3; ++v) qj[v] = Q[(size_t)j * NV3 * ML + v * ML];
     } else {
-      boundary_state3(-1 - j, d, qi, qj);
+      boundary_state3(-1 - j, nh, qi, qj);
     }
     double Fi[15], Fj[15];
     orc3_flux(g, qi, Fi);
     orc3_flux(g, qj, Fj);
     for (int v = 0; v < NV3; ++v) {
+      double fn = 0.0;
+      for (int d = 0; d < 3; ++d) fn += n[d] * (Fj[d * 5 + v] + Fi[d * 5 + v]);
       s->flxw[(size_t)f * NV3 + v] = fw[v];
-      s->flxf[(size_t)f * NV3 + v] = 0.5 * n[d] * (Fj[d * 5 + v] + Fi[d * 5 + v]) - 0.5 * ln * sw * (qj[v] - qi[v]);
+      s->flxf[(size_t)f * NV3 + v] = 0.5 * fn - 0.5 * ln * sw * (qj[v] - qi[v]);
     }
   }
 
@@ -910,15 +1181,15 @@ int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag,
   for (int i = 0; i < N; ++i) {
     double qbar[5], fW[6][5], fF[6][5];
     for (int v = 0; v < NV3; ++v) qbar[v] = Q[(size_t)i * NV3 * ML + v * ML];
-    for (int k = 0; k < 6; ++k) {
-      int f = m->face_of[6 * i + k];
-      double ek = m->eps[6 * i + k];
+    for (int k = 0; k < E; ++k) {
+      int f = m->face_of[E * i + k];
+      double ek = m->eps[E * i + k];
       for (int v = 0; v < NV3; ++v) {
         fW[k][v] = ek * s->flxw[(size_t)f * NV3 + v];
         fF[k][v] = ek * s->flxf[(size_t)f * NV3 + v];
       }
     }
-    if (orc3_flux_limit_cell(g, s->eps0, 6, vol, dt, qbar, &fW[0][0], &fF[0][0], s->prop + (size_t)i * 6))
+    if (orc3_flux_limit_cell(g, s->eps0, E, m->vol[i], dt, qbar, &fW[0][0], &fF[0][0], s->prop + (size_t)i * E))
       cfl_bad = 1;
   }
   if (cfl_bad) status |= ST3_CFL;
@@ -930,25 +1201,26 @@ int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag,
   for (int i = 0; i < N; ++i) {
     const double* Qi = Q + (size_t)i * NV3 * ML;
     double* Qo = Qn + (size_t)i * NV3 * ML;
+    double vol = m->vol[i];
     double Eint[MAXML3][5];
     for (int l = 0; l < ML; ++l) for (int v = 0; v < NV3; ++v) Eint[l][v] = 0.0;
     double avg_upd[5] = {0, 0, 0, 0, 0};
-    for (int k = 0; k < 6; ++k) {
-      int f = m->face_of[6 * i + k];
-      double ek = m->eps[6 * i + k];
-      int j = m->nbr[6 * i + k];
-      double th = s->prop[(size_t)i * 6 + k];
-      if (j >= 0) { double o = s->prop[(size_t)j * 6 + (k ^ 1)]; if (o < th) th = o; }
-      if (theta_face) theta_face[(size_t)i * 6 + k] = th;
+    for (int k = 0; k < E; ++k) {
+      int f = m->face_of[E * i + k];
+      double ek = m->eps[E * i + k];
+      int j = m->nbr[E * i + k];
+      double th = s->prop[(size_t)i * E + k];
+      if (j >= 0) { double o = s->prop[(size_t)j * E + m->nbk[E * i + k]]; if (o < th) th = o; }
+      if (theta_face) theta_face[(size_t)i * E + k] = th;
       if (th < 1.0 && ek > 0) ++nface_lim;
       for (int v = 0; v < NV3; ++v)
         avg_upd[v] += ek * (th * s->flxw[(size_t)f * NV3 + v] + (1.0 - th) * s->flxf[(size_t)f * NV3 + v]);
       /* face integral of phi_l F*.n over this face */
       for (int p = 0; p < NF; ++p) {
         const double* fs = s->fstar + ((size_t)f * NF + p) * NV3;
-        int pt = NQ + k * NF + p;
+        const double* ph = phi_at(s, i, NQ + k * NF + p);
         for (int l = 0; l < ML; ++l)
-          for (int v = 0; v < NV3; ++v) Eint[l][v] += s->fw2[p] * s->phi[pt][l] * ek * fs[v];
+          for (int v = 0; v < NV3; ++v) Eint[l][v] += s->fw2[p] * ph[l] * ek * fs[v];
       }
     }
     for (int v = 0; v < NV3; ++v) {
@@ -980,7 +1252,7 @@ int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag,
       double pb = pressure3(g, qb);
       if (qb[0] < mr) mr = qb[0];
       if (pb < mp) mp = pb;
-      for (int v = 0; v < NV3; ++v) tot[v] += vol * qb[v];
+      for (int v = 0; v < NV3; ++v) tot[v] += m->vol[i] * qb[v];
       for (int v = 0; v < NV3; ++v) if (!isfinite(qb[v])) status |= ST3_NAN;
     }
     for (int c = 0; c < ORC3_DIAG_LEN; ++c) diag[c] = 0.0;
@@ -994,13 +1266,14 @@ int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag,
 
 double orc3_last_fluxes(const orc3_solver* s, double* fw, double* ff) {
   const orc3_mesh* m = s->m;
+  int E = m->E;
   for (int i = 0; i < m->N; ++i)
-    for (int k = 0; k < 6; ++k) {
-      int f = m->face_of[6 * i + k];
-      double ek = m->eps[6 * i + k];
+    for (int k = 0; k < E; ++k) {
+      int f = m->face_of[E * i + k];
+      double ek = m->eps[E * i + k];
       for (int v = 0; v < NV3; ++v) {
-        fw[((size_t)i * 6 + k) * NV3 + v] = ek * s->flxw[(size_t)f * NV3 + v];
-        ff[((size_t)i * 6 + k) * NV3 + v] = ek * s->flxf[(size_t)f * NV3 + v];
+        fw[((size_t)i * E + k) * NV3 + v] = ek * s->flxw[(size_t)f * NV3 + v];
+        ff[((size_t)i * E + k) * NV3 + v] = ek * s->flxf[(size_t)f * NV3 + v];
       }
     }
   return s->last_dt;

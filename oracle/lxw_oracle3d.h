@@ -1,7 +1,7 @@
 /*
  * lxw_oracle3d.h -- plain FP64 CPU oracle of the same positivity-preserving
- * Lax-Wendroff DG time step on 3D Cartesian meshes (hexahedra), the
- * extension the paper states carries over directly (end of Sec. 3.3; the
+ * Lax-Wendroff DG time step on 3D meshes of hexahedra (Cartesian) and
+ * tetrahedra, the extension the paper states carries over directly (end of Sec. 3.3; the
  * 3D Euler equations of Sec. 1.1 with a third flux H).
  *
  * TEST INFRASTRUCTURE ONLY.  Like the 2D oracle it shares no code, header,
@@ -14,13 +14,14 @@
  *   Sec. 2.3  weak form, Eq. LLF with the local speed of the two traces
  *             (reading L0; the global s with llf_global)
  *   Sec. 2.4  reflective / transparent / periodic sides
- *   Sec. 3.2-3.3  flux limiter with six faces: Lambda from the density
- *             (Step 4), mu over the 63 corners of the box (Step 5)
- *   Sec. 4.1  shock limiter on (rho, u, v, w, p) with the six face neighbours
+ *   Sec. 3.2-3.3  flux limiter with E faces (6 on a hexahedron, 4 on a
+ *             tetrahedron): Lambda from the density (Step 4), mu over the
+ *             2^E - 1 corners of the box (Step 5)
+ *   Sec. 4.1  shock limiter on (rho, u, v, w, p) with the E face neighbours
  *
  * Conventions, shared with the GPU library by documentation only:
  *   state Q[N][5][ML], variables (rho, rho u, rho v, rho w, E);
- *   cell (ix, iy, iz) is element (iz * ny + iy) * nx + ix;
+ *   hexahedra: cell (ix, iy, iz) is element (iz * ny + iy) * nx + ix;
  *   faces k = 0..5: x-, x+, y-, y+, z-, z+; bc[6] per domain side in that
  *   order (0 periodic, 1 reflective, 2 transparent);
  *   modes (a, b, c) with a + b + c <= deg, ordered by total degree, then a
@@ -30,6 +31,14 @@
  *   (deg+1)^2 Gauss points at NQ + k * NF + (s + n t), s and t the two
  *   tangential directions in x, y, z order, each ascending -- so the two
  *   cells of a face see its points in the same order.
+ * Tetrahedra: the reference cell T0 = {r, s, t >= 0, r + s + t <= 1}, mapped
+ *   affinely from the cell's vertices 0..3; the basis is the Gram-Schmidt
+ *   orthonormalisation (under (1/|T0|) Int, in the mode order above) of the
+ *   monomials r^a s^b t^c; interior points a collapsed (Duffy) Gauss rule
+ *   with deg + 2 points per direction, face points a collapsed triangle rule
+ *   with deg + 1 per direction, placed from the face's three vertices taken
+ *   in ascending vertex-id order, so again both cells see the same points in
+ *   the same order.
  */
 #ifndef LXW_ORACLE3D_H
 #define LXW_ORACLE3D_H
@@ -62,6 +71,18 @@ void orc3_flux(double gamma, const double* q, double* F);
 void orc3_flux_series(double gamma, int K, const double* qs, double* Fs);
 
 orc3_mesh* orc3_mesh_cartesian(int nx, int ny, int nz, const double* box, const int* bc);
+/* Tetrahedra: vertex positions xyz[nv][3], cells tets[nt][4] (positively
+ * oriented), vertex ids vid[nv] that identify periodic images (faces match
+ * by their sorted ids), fbc[nt][4] boundary codes of the faces opposite each
+ * vertex (used on unmatched faces; NULL = transparent).  Face k of a cell
+ * is the one opposite its vertex k; its points come from its vertices in
+ * ascending id order.  NULL on bad input. */
+orc3_mesh* orc3_mesh_tets(int nv, const double* xyz, int nt, const int* tets, const int* vid, const int* fbc);
+int orc3_mesh_faces_per_element(const orc3_mesh* m);
+/* the tetrahedral basis (Gram-Schmidt of the monomials on the reference
+ * tetrahedron, orthonormal under (1/|T0|) Int) and its gradient */
+int orc3_tet_basis_eval(int deg, int npts, const double* r, const double* s, const double* t, double* phi,
+                        double* dr, double* ds, double* dt);
 void orc3_mesh_free(orc3_mesh* m);
 int orc3_mesh_num_elements(const orc3_mesh* m);
 /* per element: volume and centroid */
@@ -98,11 +119,11 @@ double orc3_mu_solve(double gamma, double eps0, const double* ql, const double* 
 /* Sec. 4.1 on every element; theta[N] nullable */
 void orc3_shock_limit(const orc3_solver* s, double* Q, double* theta);
 /* one step; dt_in > 0 fixes dt, else dt = cfl * hmin / s.  diag[ORC3_DIAG_LEN],
- * theta_mom[N], theta_sc[N], theta_face[N][6] nullable.  Returns status bits
+ * theta_mom[N], theta_sc[N], theta_face[N][E] nullable.  Returns status bits
  * (1 non-positive input average, 2 Gamma^rho < 0, 4 NaN). */
 int orc3_step(orc3_solver* s, double* Q, double dt_in, double cfl, double* diag, double* theta_mom,
               double* theta_sc, double* theta_face);
-/* f^LxW and f^LxF of the last step per element face, outward: [N][6][5]; returns dt */
+/* f^LxW and f^LxF of the last step per element face, outward: [N][E][5]; returns dt */
 double orc3_last_fluxes(const orc3_solver* s, double* fw, double* ff);
 
 #ifdef __cplusplus

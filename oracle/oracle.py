@@ -112,6 +112,10 @@ def _configure(L):
         L.orc3_flux_series.argtypes = [C.c_double, C.c_int, _dp, _dp]
         L.orc3_mesh_cartesian.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _ip]
         L.orc3_mesh_cartesian.restype = C.c_void_p
+        L.orc3_mesh_tets.argtypes = [C.c_int, _dp, C.c_int, _ip, _ip, _ip]
+        L.orc3_mesh_tets.restype = C.c_void_p
+        L.orc3_mesh_faces_per_element.argtypes = [C.c_void_p]
+        L.orc3_tet_basis_eval.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc3_mesh_free.argtypes = [C.c_void_p]
         L.orc3_mesh_num_elements.argtypes = [C.c_void_p]
         L.orc3_mesh_geometry.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
@@ -405,11 +409,14 @@ def mode_exponents3(deg):
     return abc.reshape(n, 3)
 
 
-def basis_eval3(deg, xi, eta, zeta):
+def basis_eval3(deg, xi, eta, zeta, tet=False):
+    """Hexahedral (tensor Legendre on [-1,1]^3) or tetrahedral basis and its
+    reference gradient: [phi, d/dxi, d/deta, d/dzeta], each [npts][ML]."""
     xi, eta, zeta = (np.ascontiguousarray(a, dtype=np.float64) for a in (xi, eta, zeta))
     n = (deg + 1) * (deg + 2) * (deg + 3) // 6
     out = [np.zeros((len(xi), n)) for _ in range(4)]
-    lib().orc3_basis_eval(deg, len(xi), _d(xi), _d(eta), _d(zeta), *[_d(o) for o in out])
+    f = lib().orc3_tet_basis_eval if tet else lib().orc3_basis_eval
+    f(deg, len(xi), _d(xi), _d(eta), _d(zeta), *[_d(o) for o in out])
     return out
 
 
@@ -437,14 +444,32 @@ def flux_limit_cell3(gamma, eps0, vol, dt, qbar, fW, fF):
 
 class Mesh3:
     """Cartesian nx x ny x nz mesh of box = (x0, x1, y0, y1, z0, z1); bc per
-    side (x-, x+, y-, y+, z-, z+): 0 periodic, 1 reflective, 2 transparent."""
+    side (x-, x+, y-, y+, z-, z+): 0 periodic, 1 reflective, 2 transparent.
+    Mesh3.tets(...) builds a tetrahedral mesh instead."""
 
-    def __init__(self, nx, ny, nz, box=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0), bc=(0,) * 6):
-        b = np.ascontiguousarray(box, dtype=np.float64)
-        c = np.ascontiguousarray(bc, dtype=np.int32)
-        self.ptr = lib().orc3_mesh_cartesian(nx, ny, nz, _d(b), _i(c))
+    def __init__(self, nx, ny, nz, box=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0), bc=(0,) * 6, _ptr=None):
+        if _ptr is None:
+            b = np.ascontiguousarray(box, dtype=np.float64)
+            c = np.ascontiguousarray(bc, dtype=np.int32)
+            _ptr = lib().orc3_mesh_cartesian(nx, ny, nz, _d(b), _i(c))
+        if not _ptr:
+            raise ValueError("oracle mesh construction failed")
+        self.ptr = _ptr
         self.nx, self.ny, self.nz = nx, ny, nz
         self.N = lib().orc3_mesh_num_elements(self.ptr)
+        self.E = lib().orc3_mesh_faces_per_element(self.ptr)
+
+    @classmethod
+    def tets(cls, xyz, tets, vid=None, fbc=None):
+        """Tetrahedra xyz[nv][3], tets[nt][4], periodic vertex ids vid[nv]
+        (None: the vertex index), boundary codes fbc[nt][4] of the faces
+        opposite each vertex (None: transparent)."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        vid = np.ascontiguousarray(np.arange(len(xyz)) if vid is None else vid, dtype=np.int32)
+        fb = None if fbc is None else np.ascontiguousarray(fbc, dtype=np.int32)
+        ptr = lib().orc3_mesh_tets(len(xyz), _d(xyz), len(tets), _i(tets), _i(vid), _i(fb))
+        return cls(0, 0, 0, _ptr=ptr)
 
     def __del__(self):
         if getattr(self, "ptr", None) and _lib is not None:
@@ -539,7 +564,8 @@ class Solver3:
         return th
 
     def last_fluxes(self):
-        fw = np.zeros((self.N, 6, 5)); ff = np.zeros((self.N, 6, 5))
+        E = self.mesh.E
+        fw = np.zeros((self.N, E, 5)); ff = np.zeros((self.N, E, 5))
         dt = lib().orc3_last_fluxes(self.ptr, _d(fw), _d(ff))
         return fw, ff, dt
 
@@ -548,7 +574,7 @@ class Solver3:
         diag = np.zeros(16)
         tm = ts = tf = None
         if want_theta:
-            tm = np.zeros(self.N); ts = np.zeros(self.N); tf = np.zeros((self.N, 6))
+            tm = np.zeros(self.N); ts = np.zeros(self.N); tf = np.zeros((self.N, self.mesh.E))
         lib().orc3_step(self.ptr, _d(Q), dt, cfl, _d(diag), _d(tm), _d(ts), _d(tf))
         d = {k: diag[i] for i, k in enumerate(DIAG3_KEYS)}
         d["status"] = int(d["status"])

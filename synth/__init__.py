@@ -132,6 +132,59 @@ def ic_blast3d(n: int, half_width: float = 1.1, gamma: float = GAMMA, e_total: f
     return f
 
 
+def tet_mesh(n: int, box=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0), periodic: bool = False, jitter: float = 0.0,
+             seed: int = 0):
+    """Tetrahedra of an n^3 grid of boxes, each box cut into six along its
+    main diagonal (Kuhn's subdivision: v0 = the low corner, then one unit
+    step along each axis in the order of a permutation), so neighbouring
+    boxes share their faces' triangles.  Returns (xyz[nv][3], tets[nt][4],
+    vid[nv]): vertex positions, positively oriented tetrahedra (indices into
+    xyz) and a vertex id that identifies periodic images (equal to the vertex
+    index when periodic is False; with periodic=True the grid index is taken
+    modulo n on every axis, so the two cells of a face across the period
+    share its vertex ids).  jitter moves interior vertices by up to jitter
+    times the spacing (U[-1,1] per coordinate, from the seed); periodic
+    meshes are not jittered."""
+    m = n + 1
+    ax = [np.linspace(box[2 * d], box[2 * d + 1], m) for d in range(3)]
+    I, J, K = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    idx = lambda i, j, k: (k * m + j) * m + i   # noqa: E731
+    xyz = np.zeros((m ** 3, 3))
+    xyz[idx(I, J, K).ravel(), 0] = ax[0][I.ravel()]
+    xyz[idx(I, J, K).ravel(), 1] = ax[1][J.ravel()]
+    xyz[idx(I, J, K).ravel(), 2] = ax[2][K.ravel()]
+    if jitter > 0.0 and not periodic:
+        h = np.array([(box[2 * d + 1] - box[2 * d]) / n for d in range(3)])
+        r = uniform01(seed, 3 * m ** 3).reshape(m ** 3, 3) * 2.0 - 1.0
+        inner = ((I > 0) & (I < n) & (J > 0) & (J < n) & (K > 0) & (K < n)).ravel()
+        ii = idx(I, J, K).ravel()[inner]
+        xyz[ii] += jitter * h * r[ii]
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                for pm in perms:
+                    c = [i, j, k]
+                    vs = [idx(*c)]
+                    for a in pm:
+                        c[a] += 1
+                        vs.append(idx(*c))
+                    tets.append(vs)
+    tets = np.array(tets, dtype=np.int32)
+    p = xyz[tets]
+    vol = np.einsum("ij,ij->i", np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), p[:, 3] - p[:, 0])
+    neg = vol < 0
+    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    if periodic:
+        vid = idx(I % n, J % n, K % n).ravel()
+        vid_of = np.empty(m ** 3, dtype=np.int32)
+        vid_of[idx(I, J, K).ravel()] = vid
+    else:
+        vid_of = np.arange(m ** 3, dtype=np.int32)
+    return xyz, tets, vid_of
+
+
 def ic_quadrants(seed: int):
     """Four-quadrant Riemann data on [0,1]^2 drawn from a per-problem seed:
     rho ~ U[0.1,2], p ~ U[0.01,2], u, v ~ U[-1,1] in each quadrant."""
