@@ -15,9 +15,10 @@
  *  - q_t = -div F^h and q_tt = -div F_t^h lie in the modal space (degree
  *    deg - 1): they are evaluated at the interior points, projected onto the
  *    modes with the interior rule and evaluated from the modes elsewhere.
- *  - tetrahedra: the interior rule has deg + 2 collapsed Gauss points per
- *    direction (exact to degree 2 deg + 1: the mass matrix is exact), the
- *    triangle faces deg + 1 (exact to degree 2 deg, as the 2D edges); a
+ *  - tetrahedra: the interior and face rules are conical products of
+ *    Gauss-Jacobi rules with deg + 1 points per direction, exact to degree
+ *    2 deg + 1 like the hexahedra's tensor rules (the mass matrix is
+ *    exact); a
  *    face's points are generated from its vertices in the order of their
  *    (periodically identified) ids, so both cells meet them in one order.
  */
@@ -30,7 +31,7 @@
 #define NV3 5
 #define MAXML3 20                 /* modes of degree 3 */
 #define MAXN3 4                   /* points per direction (degree 3) */
-#define MAXQ3 125                 /* interior points: hexahedra (deg+1)^3, tetrahedra (deg+2)^3 */
+#define MAXQ3 64                  /* interior points: (deg+1)^3 */
 #define MAXF3 (MAXN3 * MAXN3)     /* points per face */
 #define MAXPTS3 (MAXQ3 + 6 * MAXF3)
 #define MAXNJ3 6                  /* projection points per direction */
@@ -158,25 +159,81 @@ static double wave_speed3(double g, const double* q) {
 
 /* ------------------------------------------------------------------ */
 /* Tetrahedra: reference T0 = {r, s, t >= 0, r + s + t <= 1}.  Rules    */
-/* by the collapsed (Duffy) map r = u, s = v (1 - u), t = w (1 - u)     */
-/* (1 - v) with Gauss points in u, v, w on [0, 1]; with n points per    */
-/* direction they integrate total degree 2n - 3 exactly.  Triangle      */
-/* faces: r = u, s = v (1 - u), total degree 2n - 2.  Weights sum to 1  */
-/* (the rule of (1/|T0|) Int).  The basis is the Gram-Schmidt           */
+/* by the collapsed map r = u, s = v (1 - u), t = w (1 - u) (1 - v)     */
+/* (Stroud's conical product): the map's Jacobian (1 - u)^2 (1 - v) is  */
+/* taken into the weight functions of Gauss rules in u and v, so n      */
+/* points per direction integrate total degree 2n - 1 exactly.          */
+/* Triangle faces: r = u, s = v (1 - u), weight (1 - u) in u.  Weights  */
+/* sum to 1 (the rule of (1/|T0|) Int).  The basis is the Gram-Schmidt  */
 /* orthonormalisation (under (1/|T0|) Int) of the monomials r^a s^b t^c  */
 /* in the mode order of the hexahedra.                                  */
 /* ------------------------------------------------------------------ */
+
+/* Jacobi polynomial P_n^(alpha, 0)(x) and its derivative by the three-term
+ * recurrence in n (its derivative by differentiating the recurrence). */
+static void jacobi_p(int n, double al, double x, double* p, double* dp) {
+  double p0 = 1.0, d0 = 0.0;
+  if (n == 0) { *p = p0; *dp = d0; return; }
+  double p1 = 0.5 * ((al + 2.0) * x + al), d1 = 0.5 * (al + 2.0);
+  for (int k = 2; k <= n; ++k) {
+    double sk = 2.0 * k + al;
+    double A = (sk - 1.0) * sk * (sk - 2.0), B = (sk - 1.0) * al * al;
+    double C = 2.0 * (k + al - 1.0) * (k - 1.0) * sk, D = 2.0 * k * (k + al) * (sk - 2.0);
+    double p2 = ((A * x + B) * p1 - C * p0) / D;
+    double d2 = ((A * x + B) * d1 + A * p1 - C * d0) / D;
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+  }
+  *p = p1; *dp = d1;
+}
+
+/* n-point Gauss rule on [0, 1] for the weight (1 - u)^al: the nodes are the
+ * roots of P_n^(al, 0) mapped from [-1, 1], found one after another by
+ * Newton's method with the roots already found divided out (Maehly); each
+ * weight integrates its node's Lagrange polynomial against the weight
+ * function exactly (Gauss-Legendre with n + 2 points).  Unnormalised. */
+static void gauss_jacobi01(int n, double al, double* u, double* w) {
+  double x[8];
+  for (int j = 0; j < n; ++j) {
+    double z = -cos(3.14159265358979323846 * (j + 0.75) / (n + 0.5));
+    if (j > 0 && z <= x[j - 1]) z = x[j - 1] + 1e-3;
+    for (int it = 0; it < 200; ++it) {
+      double p, dp, sdef = 0.0;
+      jacobi_p(n, al, z, &p, &dp);
+      for (int i = 0; i < j; ++i) sdef += 1.0 / (z - x[i]);
+      double dz = p / (dp - p * sdef);
+      z -= dz;
+      if (fabs(dz) < 1e-17) break;
+    }
+    x[j] = z;
+  }
+  double g[10], gw[10];
+  orc_gauss_legendre(n + 2, g, gw);
+  for (int j = 0; j < n; ++j) {
+    double acc = 0.0;
+    for (int q = 0; q < n + 2; ++q) {
+      double l = pow(1.0 - g[q], al);
+      for (int i = 0; i < n; ++i)
+        if (i != j) l *= (g[q] - x[i]) / (x[j] - x[i]);
+      acc += gw[q] * l;
+    }
+    u[j] = 0.5 * (x[j] + 1.0);
+    w[j] = acc;
+  }
+}
+
 static int tet_rule(int n, double* r, double* s, double* t, double* w) {
-  double g[8], gw[8];
-  orc_gauss_legendre(n, g, gw);
+  double ua[8], uw[8], va[8], vw[8], wa[8], ww[8];
+  gauss_jacobi01(n, 2.0, ua, uw);
+  gauss_jacobi01(n, 1.0, va, vw);
+  gauss_jacobi01(n, 0.0, wa, ww);
   int k = 0;
   double tot = 0.0;
   for (int c = 0; c < n; ++c)
     for (int b = 0; b < n; ++b)
       for (int a = 0; a < n; ++a) {
-        double u = 0.5 * (g[a] + 1.0), v = 0.5 * (g[b] + 1.0), x = 0.5 * (g[c] + 1.0);
+        double u = ua[a], v = va[b], x = wa[c];
         r[k] = u; s[k] = v * (1.0 - u); t[k] = x * (1.0 - u) * (1.0 - v);
-        w[k] = 0.125 * gw[a] * gw[b] * gw[c] * (1.0 - u) * (1.0 - u) * (1.0 - v);
+        w[k] = uw[a] * vw[b] * ww[c];
         tot += w[k];
         ++k;
       }
@@ -185,15 +242,15 @@ static int tet_rule(int n, double* r, double* s, double* t, double* w) {
 }
 
 static int tri_rule(int n, double* a, double* b, double* w) {
-  double g[8], gw[8];
-  orc_gauss_legendre(n, g, gw);
+  double ua[8], uw[8], va[8], vw[8];
+  gauss_jacobi01(n, 1.0, ua, uw);
+  gauss_jacobi01(n, 0.0, va, vw);
   int k = 0;
   double tot = 0.0;
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) {
-      double u = 0.5 * (g[i] + 1.0), v = 0.5 * (g[j] + 1.0);
-      a[k] = u; b[k] = v * (1.0 - u);
-      w[k] = 0.25 * gw[i] * gw[j] * (1.0 - u);
+      a[k] = ua[i]; b[k] = va[j] * (1.0 - ua[i]);
+      w[k] = uw[i] * vw[j];
       tot += w[k];
       ++k;
     }
@@ -206,7 +263,7 @@ static void tet_basis_coeffs(int deg, double C[MAXML3][MAXML3]) {
   int ML = orc3_num_modes(deg), abc[3 * MAXML3];
   orc3_mode_exponents(deg, abc);
   double r[512], s[512], t[512], w[512];
-  int nq = tet_rule(deg + 2, r, s, t, w);   /* exact to degree 2 deg + 1 >= 2 deg */
+  int nq = tet_rule(deg + 1, r, s, t, w);   /* exact to degree 2 deg + 1 >= 2 deg */
   static double M[512][MAXML3];
   for (int q = 0; q < nq; ++q)
     for (int j = 0; j < ML; ++j) M[q][j] = pow(r[q], abc[3 * j]) * pow(s[q], abc[3 * j + 1]) * pow(t[q], abc[3 * j + 2]);
@@ -521,7 +578,7 @@ orc3_solver* orc3_solver_new(const orc3_mesh* m, int deg, double gamma) {
     s->NPT = s->NQ + 6 * s->NF;
     orc3_basis_eval(deg, s->NPT, s->px, s->py, s->pz, ph, dx, dy, dz);
   } else {
-    s->NQ = tet_rule(deg + 2, s->px, s->py, s->pz, s->qw);
+    s->NQ = tet_rule(n, s->px, s->py, s->pz, s->qw);
     double fa[MAXF3], fb[MAXF3];
     s->NF = tri_rule(n, fa, fb, s->fw2);
     s->NPT = s->NQ + 4 * s->NF;

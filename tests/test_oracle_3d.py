@@ -452,3 +452,23 @@ def test_tet_smooth_advection_third_order(orc):
         errs.append(np.sqrt(np.sum(vol[:, None] * w[None, :] * (q - ex(xyz[..., 0], xyz[..., 1], xyz[..., 2], T)) ** 2)))
     orders = [np.log(a / b) / np.log(nb / na) for a, b, na, nb in zip(errs[:-1], errs[1:], ns[:-1], ns[1:])]
     assert min(orders) >= 2.5, (errs, orders)
+
+
+def test_tet_rule_exact_to_its_degree(orc):
+    """The collapsed Gauss-Jacobi rules (here the projection rule, deg + 3
+    points per direction) integrate every monomial of total degree up to
+    2 (deg + 3) - 1 exactly over the reference tetrahedron: 6 a! b! c! /
+    (a + b + c + 3)! under (1/|T0|) Int."""
+    import math
+    xyz = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    m = orc.Mesh3.tets(xyz, np.array([[0, 1, 2, 3]], dtype=np.int32), np.arange(4, dtype=np.int32), None)
+    for deg in (1, 2, 3):
+        s = orc.Solver3(m, deg)
+        P, w = s.projection_points()[0], s.projection_weights()
+        assert s.nproj == (deg + 3) ** 3 and w.min() > 0
+        top = 2 * (deg + 3) - 1
+        for a in range(top + 1):
+            for b in range(top + 1 - a):
+                for c in range(top + 1 - a - b):
+                    ex = 6.0 * math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(a + b + c + 3)
+                    assert abs((w * P[:, 0] ** a * P[:, 1] ** b * P[:, 2] ** c).sum() - ex) < 1e-15, (deg, a, b, c)
