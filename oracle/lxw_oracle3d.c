@@ -188,7 +188,8 @@ static void jacobi_p(int n, double al, double x, double* p, double* dp) {
 
 /* n-point Gauss rule on [0, 1] for the weight (1 - u)^al: the nodes are the
  * roots of P_n^(al, 0) mapped from [-1, 1], found one after another by
- * Newton's method with the roots already found divided out (Maehly); each
+ * Newton's method with the roots already found divided out (Maehly) and
+ * sorted ascending; each
  * weight integrates its node's Lagrange polynomial against the weight
  * function exactly (Gauss-Legendre with n + 2 points).  Unnormalised. */
 static void gauss_jacobi01(int n, double al, double* u, double* w) {
@@ -206,6 +207,8 @@ static void gauss_jacobi01(int n, double al, double* u, double* w) {
     }
     x[j] = z;
   }
+  for (int j = 1; j < n; ++j)   /* ascending (deflation may find the roots out of order) */
+    for (int i = j; i > 0 && x[i] < x[i - 1]; --i) { double t = x[i]; x[i] = x[i - 1]; x[i - 1] = t; }
   double g[10], gw[10];
   orc_gauss_legendre(n + 2, g, gw);
   for (int j = 0; j < n; ++j) {

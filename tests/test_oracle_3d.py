@@ -472,3 +472,20 @@ def test_tet_rule_exact_to_its_degree(orc):
                 for c in range(top + 1 - a - b):
                     ex = 6.0 * math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(a + b + c + 3)
                     assert abs((w * P[:, 0] ** a * P[:, 1] ** b * P[:, 2] ** c).sum() - ex) < 1e-15, (deg, a, b, c)
+
+
+def test_tet_rule_points_ordered(orc):
+    """The collapsed rules list their points with the first collapsed
+    coordinate fastest and each one-dimensional node set ascending (the
+    order both sides document), here on the projection rule of every degree."""
+    xyz = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    m = orc.Mesh3.tets(xyz, np.array([[0, 1, 2, 3]], dtype=np.int32), np.arange(4, dtype=np.int32), None)
+    for deg in (1, 2, 3):
+        s = orc.Solver3(m, deg)
+        n = deg + 3
+        P = s.projection_points()[0].reshape(n, n, n, 3)
+        u = P[0, 0, :, 0]
+        v = P[0, :, 0, 1] / (1 - u[0])
+        assert np.all(np.diff(u) > 0) and np.all(np.diff(v) > 0)
+        w = P[:, 0, 0, 2] / ((1 - u[0]) * (1 - v[0]))
+        assert np.all(np.diff(w) > 0)
