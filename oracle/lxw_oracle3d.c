@@ -295,12 +295,11 @@ static void tet_basis_coeffs(int deg, double C[MAXML3][MAXML3]) {
     for (int j = 0; j < ML; ++j) C[l][j] = (double)Cl[l][j];
 }
 
-int orc3_tet_basis_eval(int deg, int npts, const double* r, const double* s, const double* t, double* phi,
-                        double* dr, double* ds, double* dt) {
+/* the basis of coefficients C at npts points */
+static void tet_basis_apply(int deg, double C[MAXML3][MAXML3], int npts, const double* r, const double* s,
+                            const double* t, double* phi, double* dr, double* ds, double* dt) {
   int ML = orc3_num_modes(deg), abc[3 * MAXML3];
   orc3_mode_exponents(deg, abc);
-  double C[MAXML3][MAXML3];
-  tet_basis_coeffs(deg, C);
   for (int p = 0; p < npts; ++p) {
     double m[MAXML3], mr[MAXML3], ms[MAXML3], mt[MAXML3];
     for (int j = 0; j < ML; ++j) {
@@ -320,7 +319,14 @@ int orc3_tet_basis_eval(int deg, int npts, const double* r, const double* s, con
       if (dt) dt[p * ML + l] = z;
     }
   }
-  return ML;
+}
+
+int orc3_tet_basis_eval(int deg, int npts, const double* r, const double* s, const double* t, double* phi,
+                        double* dr, double* ds, double* dt) {
+  double C[MAXML3][MAXML3];
+  tet_basis_coeffs(deg, C);
+  tet_basis_apply(deg, C, npts, r, s, t, phi, dr, ds, dt);
+  return orc3_num_modes(deg);
 }
 
 /* ------------------------------------------------------------------ */
@@ -551,6 +557,7 @@ orc3_solver* orc3_solver_new(const orc3_mesh* m, int deg, double gamma) {
   s->eps0 = 1e-12; s->alpha0 = 500.0; s->shock_limiter = 1;
   s->ML = orc3_num_modes(deg);
   int n = deg + 1, E = m->E;
+  double Ct[MAXML3][MAXML3];   /* tetrahedra: basis coefficients */
   double g[8], gw[8];
   orc_gauss_legendre(n, g, gw);
   const size_t cap = (size_t)(MAXPJ3 > MAXPTS3 ? MAXPJ3 : MAXPTS3) * MAXML3;
@@ -581,11 +588,12 @@ orc3_solver* orc3_solver_new(const orc3_mesh* m, int deg, double gamma) {
     s->NPT = s->NQ + 6 * s->NF;
     orc3_basis_eval(deg, s->NPT, s->px, s->py, s->pz, ph, dx, dy, dz);
   } else {
+    tet_basis_coeffs(deg, Ct);   /* once per solver: the Gram-Schmidt runs in long double */
     s->NQ = tet_rule(n, s->px, s->py, s->pz, s->qw);
     double fa[MAXF3], fb[MAXF3];
     s->NF = tri_rule(n, fa, fb, s->fw2);
     s->NPT = s->NQ + 4 * s->NF;
-    orc3_tet_basis_eval(deg, s->NQ, s->px, s->py, s->pz, ph, dx, dy, dz);
+    tet_basis_apply(deg, Ct, s->NQ, s->px, s->py, s->pz, ph, dx, dy, dz);
     /* face points of every cell, from its face's vertices in id order */
     size_t N = (size_t)m->N, NF = (size_t)s->NF, ML = (size_t)s->ML;
     s->fref = malloc(sizeof(double) * N * 4 * NF * 3);
@@ -602,7 +610,7 @@ orc3_solver* orc3_solver_new(const orc3_mesh* m, int deg, double gamma) {
           for (int d = 0; d < 3; ++d) s->fref[((i * 4 + k) * NF + p) * 3 + d] = r[d];
         }
         double fp[MAXF3 * MAXML3];
-        orc3_tet_basis_eval(deg, (int)NF, rr, rs, rt, fp, NULL, NULL, NULL);
+        tet_basis_apply(deg, Ct, (int)NF, rr, rs, rt, fp, NULL, NULL, NULL);
         memcpy(s->fphi + (i * 4 + k) * NF * ML, fp, sizeof(double) * NF * ML);
       }
   }
@@ -631,7 +639,7 @@ orc3_solver* orc3_solver_new(const orc3_mesh* m, int deg, double gamma) {
     orc3_basis_eval(deg, s->NPJ, s->jx, s->jy, s->jz, ph, NULL, NULL, NULL);
   } else {
     s->NPJ = tet_rule(nj, s->jx, s->jy, s->jz, s->jw);
-    orc3_tet_basis_eval(deg, s->NPJ, s->jx, s->jy, s->jz, ph, NULL, NULL, NULL);
+    tet_basis_apply(deg, Ct, s->NPJ, s->jx, s->jy, s->jz, ph, NULL, NULL, NULL);
   }
   for (int p = 0; p < s->NPJ; ++p)
     for (int l = 0; l < s->ML; ++l) s->jphi[p][l] = ph[p * s->ML + l];

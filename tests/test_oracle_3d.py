@@ -427,9 +427,10 @@ def test_tet_smooth_advection_third_order(orc):
     """The smooth 3D advection of the hexahedral pin on periodic tetrahedral
     meshes (6 n^3 cells) to t = 0.03.  On simplices the proven L2 rate of DG
     for advection is k + 1/2 (Johnson and Pitkaranta), and this scheme
-    measures 2.57-2.64 at P2 here (1.5 at P1, 3.4-3.6 at P3; the 2D
-    triangles behave alike): the pin is that rate, and the exactness pin
-    above covers consistency."""
+    measures 2.57-2.64 at P2 on these coarse meshes (1.5 at P1, 3.4-3.6 at
+    P3; the 2D jittered triangles give 2.57 from 8 to 16 and 2.96 from 16
+    to 32): the pin is that rate, and the exactness pin above covers
+    consistency."""
     U = np.array([1.0, 0.5, 0.25])
     ex = lambda x, y, z, t: 1 + 0.2 * np.sin(2 * np.pi * ((x - U[0] * t) + (y - U[1] * t) + (z - U[2] * t)))  # noqa: E731
     T = 0.03
