@@ -334,6 +334,15 @@ def run_reference(args):
         Q = so.project_fn(synth.ic_blast3d(48, b["half_width"]))
         sols = [(b, so, Q)]
         nv = 5
+    elif args.workload == "blast3t":
+        # the same blast on a 24^3-box sample of the tetrahedral mesh
+        b = BLAST3T
+        box = (-b["half_width"], b["half_width"]) * 3
+        xo, to, vo = synth.tet_mesh(24, box=box)
+        so = O.Solver3(O.Mesh3.tets(xo, to, vo, np.full((len(to), 4), 1, dtype=np.int32)), b["deg"])
+        Q = so.project_fn(synth.ic_blast3d(24, b["half_width"]))
+        sols = [(b, so, Q)]
+        nv = 5
     else:
         sols = [(WORKLOADS[p],) + oracle_solver(WORKLOADS[p]) for p in parts_of(args.workload)]
         nv = 4
@@ -350,7 +359,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": BLAST3D["desc"] if args.workload == "blast3d" else desc_of(args.workload),
+           "config": {"workload": {"blast3d": BLAST3D["desc"], "blast3t": BLAST3T["desc"]}.get(args.workload)
+                      or desc_of(args.workload),
                       "elements": sum(s.N for _, s, _ in sols), "degree": 2,
                       "form": "FP64 CPU oracle"},
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
@@ -429,6 +439,26 @@ BLAST3D = dict(n=96, deg=2, cfl=0.1, half_width=1.1,
                     "8 centre cells, reflective walls (FP64 form)")
 
 
+BLAST3T = dict(n=48, deg=2, cfl=0.1, half_width=1.1,
+               desc="3D blast on tetrahedra: 48^3 boxes of [-1.1,1.1]^3 cut into 6 Kuhn tetrahedra = 663,552 P2 "
+                    "cells, point energy 0.979264 in the 48 cells around the origin, reflective walls (FP64 form)")
+
+
+def ck3t_flops_per_element(deg):
+    """Algorithmic FP64 flop of k3t_ck per tetrahedron (an FMA counts 2), the
+    hexahedral count with NPT = NQ + 4 n^2 points and, at each interior
+    point of every pass, the contravariant flux G_a = sum_d Ji[a][d] F_d (45
+    FMA) in place of the three axis scalings; at a face point an_k . F_T (15
+    FMA)."""
+    n = deg + 1
+    NQ, NF = n ** 3, n * n
+    ML = (deg + 1) * (deg + 2) * (deg + 3) // 6
+    p1 = NQ * (2 * 5 * ML + 40 + 90 + 2 * 15 * ML)
+    p2 = NQ * (2 * 10 * ML + 70 + 90 + 2 * 15 * ML)
+    p3 = NQ * (2 * 15 * ML + 320 + 90 + 2 * 15 * (ML - 1)) + 4 * NF * (2 * 15 * ML + 320 + 30)
+    return p1 + p2 + p3
+
+
 def ck3_flops_per_element(deg):
     """Algorithmic FP64 flop of k3_ck per cell (an FMA counts 2): with n =
     deg + 1, NQ = n^3 interior and NPT = NQ + 6 n^2 points, ML modes, 5
@@ -448,17 +478,27 @@ def ck3_flops_per_element(deg):
 
 
 def run_blast3d(args):
-    """The 3D Cartesian FP64 form on the 3D point-energy blast: K graph-
-    replayed steps bracketed by CUDA events (the state, 354 MB, exceeds the
-    L2), per-phase times from a traced step, the oracle on a sample."""
+    """The 3D FP64 form on the 3D point-energy blast (Cartesian hexahedra, or
+    with --workload blast3t the same blast on Kuhn tetrahedra): K graph-
+    replayed steps bracketed by CUDA events (the state, 265-354 MB, exceeds
+    the L2), per-phase times from a traced step, the oracle on a sample."""
     import torch
     from paper_1601_08145_gb300 import build, lxw as L
     build.build()
-    b = BLAST3D
+    tet = args.workload == "blast3t"
+    b = BLAST3T if tet else BLAST3D
+    if args.n3:   # a smaller mesh of the same blast (profiling captures)
+        b = dict(b, n=args.n3, desc=b["desc"] + " -- run here at %d per axis" % args.n3)
     n, hw = b["n"], b["half_width"]
     box = (-hw, hw) * 3
     stream = torch.cuda.current_stream()
-    s = L.lxw3_solver_create(n, n, n, box, (1,) * 6, b["deg"], L.lxw_options_default(), stream=stream)
+    if tet:
+        xyz, tets, vid = synth.tet_mesh(n, box=box)
+        s = L.lxw3_solver_create_tets(xyz, tets, vid, b["deg"], face_bc=np.full((len(tets), 4), 1, dtype=np.int32),
+                                      options=L.lxw_options_default(), stream=stream)
+        del xyz, tets, vid
+    else:
+        s = L.lxw3_solver_create(n, n, n, box, (1,) * 6, b["deg"], L.lxw_options_default(), stream=stream)
     ic = synth.ic_blast3d(n, hw)
     xyz = L.lxw3_projection_points(s)
     prim = torch.from_numpy(np.stack(np.broadcast_arrays(*ic(xyz[..., 0], xyz[..., 1], xyz[..., 2])), axis=-1).copy())
@@ -479,10 +519,10 @@ def run_blast3d(args):
     phases = [L.lxw3_profile_step(s, Q, b["cfl"]) for _ in range(3)]
     ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
     dof = s.N * 5 * s.ML
-    flops = ck3_flops_per_element(b["deg"]) * s.N
+    flops = (ck3t_flops_per_element if tet else ck3_flops_per_element)(b["deg"]) * s.N
     probes = fma_probes()
     peak = 1.25
-    roof = {"kernel": "k3_ck", "bound": "alu", "pipe": "fp64", "achieved": flops / (ph["ck"] / 1e3) / 1e12,
+    roof = {"kernel": "k3t_ck" if tet else "k3_ck", "bound": "alu", "pipe": "fp64", "achieved": flops / (ph["ck"] / 1e3) / 1e12,
             "peak": peak, "unit": "TFLOP/s", "peak_source": "nominal GB300 FP64 rate (recipe table)",
             "peak_measured_fma_probe": probes.get("fp64"), "algorithmic_flops_per_launch": flops,
             "launch_ms": ph["ck"], "traffic": None}
@@ -491,14 +531,19 @@ def run_blast3d(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": b["desc"], "elements": s.N, "degree": b["deg"], "cfl": b["cfl"],
-                      "l2": "state (354 MB) larger than the L2", "timing": "graph-replayed steps, CUDA events"},
+                      "l2": "state (%d MB) larger than the L2" % (s.N * 5 * s.ML * 8 // 10 ** 6), "timing": "graph-replayed steps, CUDA events"},
            "phases_ms": ph, "roofline": roof, "gpu_launches": args.steps * L.lxw3_step_launches(s) + 1,
            "clocks": clk, "positivity_last_step": {"min_rho": d["min_rho"], "min_p": d["min_p"]},
            "status_last_step": d["status"]}
     if not args.no_cpu_baseline:
         from oracle import oracle as O
-        m = 48   # the oracle holds ~15 KB of work arrays per cell: a 48^3 sample of the same blast
-        so = O.Solver3(O.Mesh3(m, m, m, box, (1,) * 6), b["deg"])
+        if tet:   # a 24^3-box sample (82,944 cells) of the same blast
+            m = 24
+            xo, to, vo = synth.tet_mesh(m, box=box)
+            so = O.Solver3(O.Mesh3.tets(xo, to, vo, np.full((len(to), 4), 1, dtype=np.int32)), b["deg"])
+        else:     # the oracle holds ~15 KB of work arrays per cell: a 48^3 sample of the same blast
+            m = 48
+            so = O.Solver3(O.Mesh3(m, m, m, box, (1,) * 6), b["deg"])
         Qo = so.project_fn(synth.ic_blast3d(m, hw))
         so.step(Qo, cfl=b["cfl"])
         t0 = time.time()
@@ -507,7 +552,7 @@ def run_blast3d(args):
             so.step(Qo, cfl=b["cfl"])
         dtc = time.time() - t0
         out["cpu_baseline"] = {"value": so.N * 5 * so.ML * k / dtc, "unit": UNIT, "cores": O.lib().orc_num_threads(),
-                               "kind": "oracle", "sample": "%d steps of the same blast on %d^3 cells, %.1f s" % (k, m, dtc)}
+                               "kind": "oracle", "sample": "%d steps of the same blast on %d cells (%d^3 boxes), %.1f s" % (k, so.N, m, dtc)}
     print(json.dumps(out))
 
 
@@ -719,9 +764,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config5", choices=sorted(WORKLOADS) + sorted(CONFIGS) + ["ensemble", "blast3d"])
+    ap.add_argument("--workload", default="config5", choices=sorted(WORKLOADS) + sorted(CONFIGS) + ["ensemble", "blast3d", "blast3t"])
     ap.add_argument("--tau", type=float, default=0.01, help="learned gate: skip where theta_hat >= 1 - tau")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n3", type=int, default=0, help="blast3d / blast3t: cells (boxes) per axis instead of the default")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work list of the mixed forms")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 100,352-triangle secondary line")
     ap.add_argument("--form", default="all", choices=["all", "learned", "mixed", "fp64"],
@@ -731,7 +777,7 @@ def main():
         return run_reference(args)
     if args.workload == "ensemble":
         return run_ensemble(args)
-    if args.workload == "blast3d":
+    if args.workload in ("blast3d", "blast3t"):
         return run_blast3d(args)
 
     import torch

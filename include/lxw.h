@@ -499,7 +499,8 @@ lxw_status lxw3_projection_points(const lxw_solver3* s, double* xyz_host);
 /* Q_dev[N][5][ML] = L2 projection of prim_dev[N][NPJ][5] = (rho, u, v, w, p) */
 lxw_status lxw3_project(lxw_solver3* s, const double* prim_dev, double* Q_dev);
 /* One step in place (dt > 0 fixes dt, else dt = cfl * hmin / s); fills
- * diag_host (nullable), theta_face_dev[N][6] (nullable); synchronises.
+ * diag_host (nullable), theta_face_dev[N][E] (nullable; E = 6 on
+ * hexahedra, 4 on tetrahedra); synchronises.
  * Returns LXW_ERR_NONPOSITIVE / LXW_ERR_CFL / LXW_ERR_NAN from the step's
  * status bits (the step itself completes). */
 lxw_status lxw3_step(lxw_solver3* s, double* Q_dev, double dt, double cfl, lxw_diag3* diag_host,
@@ -511,6 +512,43 @@ lxw_status lxw3_run(lxw_solver3* s, double* Q_dev, int nsteps, double cfl, lxw_d
 lxw_status lxw3_profile_step(lxw_solver3* s, double* Q_dev, double cfl, float* ms);
 /* kernel launches of one step without diagnostics */
 int lxw3_step_launches(const lxw_solver3* s);
+
+/* Tetrahedral meshes, FP64: the same step on unstructured cells with four
+ * faces, through the same solver type and the lxw3_step / lxw3_run /
+ * lxw3_project / lxw3_profile_step calls above (theta_face_dev is then
+ * [N][4]).  Each cell is the affine image of the reference tetrahedron
+ * T0 = {r, s, t >= 0, r + s + t <= 1} taking T0's vertices (0,0,0),
+ * (1,0,0), (0,1,0), (0,0,1) to the cell's vertices 0..3 in the order given.
+ * Modes: the orthonormal basis (under (1/|K|) Int) obtained by Gram-Schmidt
+ * from the monomials r^a s^b t^c in the mode order of the hexahedra (mode 0
+ * = 1, the cell average).  Interior quadrature: a conical product of
+ * Gauss-Jacobi rules with degree + 1 points per direction; face k (opposite
+ * vertex k): a collapsed triangle rule with (degree + 1)^2 points placed from
+ * the face's vertices in ascending vertex-id order, so both cells of a face
+ * meet the same points in the same order.  Both rules integrate total
+ * degree 2 degree + 1 exactly.
+ *   xyz[n_vertices][3] (host): vertex positions;
+ *   tets[n_tets][4] (host): vertex indices, positively oriented (the
+ *     determinant of (x1 - x0, x2 - x0, x3 - x0) is positive);
+ *   vid[n_vertices] (host): vertex ids; two faces with the same three ids
+ *     are glued (periodic images carry equal ids; give vid[v] = v for an
+ *     ordinary mesh).  A cell's four ids must differ;
+ *   face_bc[n_tets][4] (host, nullable = all transparent): the code of face
+ *     k of each cell, read only where no other cell has its ids:
+ *     LXW_BC_REFLECT or LXW_BC_TRANSPARENT.
+ * dt = cfl * hmin / s with hmin = min 3 |K| / |dK| over the cells; the shock
+ * limiter's alpha = alpha0 * (|K|^(1/3))^1.5 per cell; the flux limiter's mu
+ * runs over the 15 corners of the box of four proposals.  The host arrays
+ * are read during the call only.  Allocates about (40 NF + 90) doubles per
+ * cell of workspace plus 22 doubles and 5 ints of geometry.  Errors:
+ * LXW_ERR_ARG (null pointer, sizes, degree, index out of range, repeated id
+ * in a cell, non-positive orientation, a face shared by more than two
+ * cells, a bad boundary code), LXW_ERR_NOMEM, LXW_ERR_CUDA. */
+lxw_status lxw3_solver_create_tets(int n_vertices, const double* xyz, int n_tets, const int* tets, const int* vid,
+                                   const int* face_bc, int degree, const lxw_options* opt, void* stream,
+                                   lxw_solver3** out);
+/* faces per element: 6 (hexahedra) or 4 (tetrahedra); 0 for NULL */
+int lxw3_faces_per_element(const lxw_solver3* s);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "liblxw.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lxw_kernels.cu", "lxw_kernels_mx.cu", "lxw_host.cpp", "lxw_mlp.cu", "lxw_kernels3d.cu",
-           "lxw_host3d.cpp"]
+           "lxw_kernels3t.cu", "lxw_host3d.cpp"]
 FAST_FP32 = {"lxw_kernels_mx.cu"}
 
 

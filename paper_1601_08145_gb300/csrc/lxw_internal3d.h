@@ -1,5 +1,6 @@
-// lxw_internal3d.h -- shared declarations of the 3D Cartesian (hexahedral)
-// FP64 form: tables, device views, launchers.  Not part of the public ABI.
+// lxw_internal3d.h -- shared declarations of the 3D FP64 forms on hexahedra
+// (Cartesian boxes) and tetrahedra: tables, device views, launchers.  Not
+// part of the public ABI.
 #pragma once
 
 #include "lxw_internal.h"
@@ -40,9 +41,9 @@ struct Diag3Block {
 };
 
 struct Work3 {
-  double* trace;                       // [6][NF][10][N]: q (5), n_out . F_T (5), n scaled by the face area
-  double* flux;                        // [6][10][N]: outward f^LxW (5), f^LxF (5)
-  double* prop;                        // [6][N]: flux-limiter proposals
+  double* trace;                       // [E][NF][10][N]: q (5), n_out . F_T (5), n scaled by the face area
+  double* flux;                        // [E][10][N]: outward f^LxW (5), f^LxF (5)
+  double* prop;                        // [E][N]: flux-limiter proposals
   unsigned long long* smax;            // bits of the global wave speed (non-negative double)
   unsigned int* status;                // LXW_ST_* bits of the step
   Diag3Block* diag;
@@ -51,7 +52,7 @@ struct Work3 {
 struct Args3 {
   double dt_in, cfl, gamma, eps0, alpha0;
   int shock_limiter, llf_global, want_diag;
-  double* theta_face;                  // [N][6] or null
+  double* theta_face;                  // [N][E] or null
 };
 
 // Tables of one degree into the device's constant bank (synchronous).
@@ -66,6 +67,40 @@ int step3_launch_count(int want_diag, int shock_limiter);
 // projection weights jw[NPJ] and basis jphi[NPJ][ML] (device arrays).
 int launch_project3(int deg, int N, int NPJ, double gamma, const double* jw, const double* jphi, const double* prim,
                     double* Q, void* stream);
+
+// ---------------------------------------------------------------- tetrahedra
+// Reference cell T0 = {r, s, t >= 0, r + s + t <= 1}, affine map from the
+// cell's vertices 0..3.  Interior points: a conical product of Gauss-Jacobi
+// rules, (deg + 1)^3 points; face k (opposite vertex k): a collapsed
+// triangle rule with (deg + 1)^2 points placed from the face's vertices in
+// ascending vertex-id order, so both cells of a face meet its points in one
+// order.  Face k's vertices appear in one of 6 orders ("perm").
+constexpr int k3tPerms = 6;
+
+struct Tables3T {
+  double qw[k3MaxQ];                   // interior weights, sum 1
+  double fw[k3MaxF];                   // face weights, sum 1
+  double phi[k3MaxQ][k3MaxML];         // basis at the interior points
+  double dref[3][k3MaxQ][k3MaxML];     // d phi / d(r, s, t) there
+  double W[3][k3MaxQ][k3MaxML];        // qw_k sum_m phi_m(x_k) D_a[m][l], D_a[m][l] = (1/|T0|) Int d_a phi_m phi_l
+};
+
+// Per-cell geometry, structure of arrays.
+constexpr int k3tGeo = 22;             // Ji (9), vol, an (4 x 3)
+struct Mesh3T {
+  int N;
+  double hmin;                         // min 3 |K| / |dK|
+  const double* geo;                   // [22][N]: Ji[a][d] = d r_a / d x_d (row-major), |K|, outward
+                                       //   normals scaled by the face area (face k: 10 + 3k ..)
+  const int* nbr;                      // [4][N]: neighbour across face k, or -1 - bc
+  const int* code;                     // [N]: bits 3k..3k+2 perm of face k, bits 12+2k..12+2k+1 the
+                                       //   neighbour's local face
+  const double* fphi;                  // [4][6][NF][ML]: basis at the face points (device, read-only)
+};
+
+int upload_tables3t(int deg, const Tables3T& t);
+int launch_step3t(int deg, const Mesh3T& m, const Work3& w, double* Q, const Args3& a, void* stream, int block,
+                  void** events, int upto);
 
 // Host quadrature helpers shared with the 2D tables (lxw_host.cpp).
 void host_gauss_legendre(int n, double* x, double* w);

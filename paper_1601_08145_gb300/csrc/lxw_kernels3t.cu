@@ -1,0 +1,739 @@
+// lxw_kernels3t.cu -- sm_103a kernels of one LxW-DG step on tetrahedral
+// meshes, FP64: the unstructured 3D extension (end of Sec. 3.3; the 3D Euler
+// equations of Sec. 1.1).
+//
+// One thread owns one cell, as in the hexahedral form; state Q[N][5][ML].
+// Each cell is the affine image of the reference tetrahedron T0; its
+// geometry (the inverse Jacobian, the volume and the four outward normals
+// scaled by the face areas) is read per cell from a structure of arrays.
+// The interior tables live in constant memory (all threads of a warp read
+// the same point); the face tables depend on the order in which a face's
+// vertices appear in the cell (6 orders per face) and are read from global
+// memory through the read-only cache.  Phases as in the hexahedral form:
+//   k3t_moment  Sec. 3.1 moment limiter + max |u| + c -> atomicMax
+//   k3t_ck      Sec. 2.2-2.3 CK flux: q_t, q_tt carried as modes through the
+//               weighted differentiation tables applied to the contravariant
+//               flux G_a = sum_d (d r_a / d x_d) F_d; volume integral; traces
+//   k3t_face    Sec. 3.3 Step 3 on four faces and Steps 4-5 (Lambda, 15
+//               corners, mu)
+//   k3t_update  Step 6
+//   k3t_shock   Sec. 4.1 with the four face neighbours
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "lxw_internal3d.h"
+
+namespace lxw {
+namespace {
+
+__constant__ Tables3T c_tab3t[2];   // degree 1, degree 2
+
+#include "lxw_flux3.cuh"
+
+__device__ __forceinline__ double step_dt3t(const Work3& w, const Mesh3T& m, const Args3& a) {
+  const double s = __longlong_as_double((long long)*w.smax);
+  return a.dt_in > 0.0 ? a.dt_in : a.cfl * m.hmin / s;
+}
+
+__device__ __forceinline__ double geo(const Mesh3T& m, int e, int i) { return m.geo[(size_t)e * m.N + i]; }
+
+// basis values at limiter point p of a cell: interior points from the
+// constant bank, face points from the table of the face's vertex order
+template <int ML, int NQ, int NF>
+__device__ __forceinline__ void load_phi(const Tables3T& t, const Mesh3T& m, int code, int p, double ph[ML]) {
+  if (p < NQ) {
+#pragma unroll
+    for (int l = 0; l < ML; ++l) ph[l] = t.phi[p][l];
+  } else {
+    const int k = (p - NQ) / NF, pe = p - NQ - k * NF;
+    const double* f = m.fphi + (size_t)((k * k3tPerms + ((code >> (3 * k)) & 7)) * NF + pe) * ML;
+#pragma unroll
+    for (int l = 0; l < ML; ++l) ph[l] = __ldg(f + l);
+  }
+}
+
+// momentum mirror in the plane of unit normal nh (a reflective wall)
+__device__ __forceinline__ void mirror3(const double nh[3], double q[5]) {
+  const double mn = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) q[1 + d] -= 2.0 * mn * nh[d];
+}
+
+// an . F[.][v] with sign-symmetric rounding: both cells of a face use
+// exactly negated normals and must get exactly negated products
+__device__ __forceinline__ double ndot(const double an[3], const double F[3][5], int v) {
+  return __fma_rn(an[2], F[2][v], __fma_rn(an[1], F[1][v], __dmul_rn(an[0], F[0][v])));
+}
+
+__device__ __forceinline__ double face_area(const double an[3]) {
+  return __dsqrt_rn(__fma_rn(an[2], an[2], __fma_rn(an[1], an[1], __dmul_rn(an[0], an[0]))));
+}
+
+// ------------------------------------------------------------ k3t_reset
+__global__ void k3t_reset(Work3 w, int want_diag) {
+  if (threadIdx.x == 0) {
+    *w.smax = 0ull;
+    *w.status = 0u;
+  }
+  if (want_diag && threadIdx.x < 5) w.diag->sum[threadIdx.x] = 0.0;
+  if (want_diag && threadIdx.x == 0) {
+    w.diag->minr = w.diag->minp = ~0ull;
+    w.diag->nmom = w.diag->nface = w.diag->nsc = 0ull;
+  }
+}
+
+// ------------------------------------------------------------ k3t_moment
+// Sec. 3.1 Steps 0-2 (Lemma 1's secant) over the interior and face points,
+// then |u| + c of the limited state, block max -> atomicMax.
+template <int DEG, int ML, int N1>
+__global__ void __launch_bounds__(128) k3t_moment(const Mesh3T m, const Work3 w, double* __restrict__ Q,
+                                                  const Args3 a) {
+  constexpr int NQ = N1 * N1 * N1, NF = N1 * N1, NPT = NQ + 4 * NF;
+  const Tables3T& t = c_tab3t[DEG - 1];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double smax = 0.0;
+  if (i < m.N) {
+    const double g = a.gamma, g1 = g - 1.0;
+    const int code = m.code[i];
+    double* Qi = Q + (size_t)i * 5 * ML;
+    double c[5][ML];
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
+    const double pb = c[0][0] > 0.0
+                          ? g1 * (c[4][0] - 0.5 * (c[1][0] * c[1][0] + c[2][0] * c[2][0] + c[3][0] * c[3][0]) / c[0][0])
+                          : -1.0;
+    double th = 1.0;
+    if (!(c[0][0] > 0.0) || !(pb > 0.0)) {
+      atomicOr(w.status, (unsigned)LXW_ST_NONPOSITIVE);
+      th = 0.0;
+    } else {
+      const double er = fmin(a.eps0, 0.5 * c[0][0]);
+      double thr = 1.0;
+#pragma unroll 1
+      for (int p = 0; p < NPT; ++p) {
+        double ph[ML];
+        load_phi<ML, NQ, NF>(t, m, code, p, ph);
+        double d = 0.0;
+#pragma unroll
+        for (int l = 1; l < ML; ++l) d = fma(c[0][l], ph[l], d);
+        const double rm = c[0][0] + d;
+        if (rm < er) thr = fmin(thr, (c[0][0] - er) / (c[0][0] - rm));
+      }
+      const double ep = fmin(a.eps0, 0.5 * pb);
+      th = thr;
+#pragma unroll 1
+      for (int p = 0; p < NPT; ++p) {
+        double ph[ML];
+        load_phi<ML, NQ, NF>(t, m, code, p, ph);
+        double q[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          double d = 0.0;
+#pragma unroll
+          for (int l = 1; l < ML; ++l) d = fma(c[v][l], ph[l], d);
+          q[v] = c[v][0] + thr * d;
+        }
+        const double pt = g1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+        if (pt < ep) th = fmin(th, thr * (pb - ep) / (pb - pt));
+      }
+      th = fmax(th, 0.0);
+    }
+    if (th < 1.0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+#pragma unroll
+        for (int l = 1; l < ML; ++l) {
+          c[v][l] *= th;
+          Qi[v * ML + l] = c[v][l];
+        }
+      if (a.want_diag) atomicAdd(&w.diag->nmom, 1ull);
+    }
+    double qa[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qa[v] = c[v][0];
+    smax = speed_of3(g, qa);
+#pragma unroll 1
+    for (int p = 0; p < NPT; ++p) {
+      double ph[ML];
+      load_phi<ML, NQ, NF>(t, m, code, p, ph);
+      double q[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 0; l < ML; ++l) acc = fma(c[v][l], ph[l], acc);
+        q[v] = acc;
+      }
+      smax = fmax(smax, speed_of3(g, q));
+    }
+  }
+  block_max3(smax, w.smax);
+}
+
+// contravariant flux G_a[v] = sum_d Ji[a][d] F_d[v]
+__device__ __forceinline__ void contra3(const double Ji[9], const double F[3][5], double G[3][5]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) G[a][v] = Ji[3 * a] * F[0][v] + Ji[3 * a + 1] * F[1][v] + Ji[3 * a + 2] * F[2][v];
+}
+
+// q and F_T = F + dt/2 F_t + dt^2/6 F_tt at a point from the basis values
+template <int ML>
+__device__ __forceinline__ void ft_point3t(double g1, double c1, double c2, const double ph[ML], const double c[5][ML],
+                                           const double Qt[5][ML], const double Qtt[5][ML], double q[5],
+                                           double FT[3][5]) {
+  double qt[5], qtt[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    double acc = 0.0, d1 = 0.0, d2 = 0.0;
+#pragma unroll
+    for (int l = 0; l < ML; ++l) {
+      acc = fma(c[v][l], ph[l], acc);
+      d1 = fma(Qt[v][l], ph[l], d1);
+      d2 = fma(Qtt[v][l], ph[l], d2);
+    }
+    q[v] = acc; qt[v] = d1; qtt[v] = d2;
+  }
+  const P3 s = make_p3(g1, q);
+  double F[3][5];
+  flux3(s, F);
+  double F1[3][5], du[3], dp;
+  flux3_d1(g1, s, qt, F1, du, dp);
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) FT[d][v] = F[d][v] + c1 * F1[d][v];
+  flux3_d2(g1, s, qt, du, dp, F1);
+  double F3[3][5], eu[3], ep;
+  flux3_d1(g1, s, qtt, F3, eu, ep);
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) FT[d][v] += c2 * (F1[d][v] + F3[d][v]);
+}
+
+// ------------------------------------------------------------ k3t_ck
+// Sec. 2.2-2.3 on one cell: Qt = -(projection of div F^h), Qtt likewise
+// with F_t, both through W_a applied to G_a; F_T at the interior points
+// feeds the volume integral (1/|K|) Int F_T . grad phi_l = sum_k qw_k G_a
+// d_a phi_l, the face points store q and an_k . F_T in the trace array.
+template <int DEG, int ML, int N1>
+__global__ void __launch_bounds__(128) k3t_ck(const Mesh3T m, const Work3 w, double* __restrict__ Q, const Args3 a) {
+  constexpr int NQ = N1 * N1 * N1, NF = N1 * N1;
+  const Tables3T& t = c_tab3t[DEG - 1];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int N = m.N;
+  const double g1 = a.gamma - 1.0;
+  const double dt = step_dt3t(w, m, a);
+  const double c1 = 0.5 * dt, c2 = dt * dt / 6.0;
+  double Ji[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) Ji[e] = geo(m, e, i);
+  double* Qi = Q + (size_t)i * 5 * ML;
+  double c[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
+  // pass 1: Qt
+  double Qt[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Qt[v][l] = 0.0;
+#pragma unroll 1
+  for (int k = 0; k < NQ; ++k) {
+    double q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double acc = 0.0;
+#pragma unroll
+      for (int l = 0; l < ML; ++l) acc = fma(c[v][l], t.phi[k][l], acc);
+      q[v] = acc;
+    }
+    const P3 s = make_p3(g1, q);
+    double F[3][5], G[3][5];
+    flux3(s, F);
+    contra3(Ji, F, G);
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int l = 0; l < ML; ++l) Qt[v][l] -= G[0][v] * t.W[0][k][l] + G[1][v] * t.W[1][k][l] + G[2][v] * t.W[2][k][l];
+  }
+  // pass 2: Qtt
+  double Qtt[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Qtt[v][l] = 0.0;
+#pragma unroll 1
+  for (int k = 0; k < NQ; ++k) {
+    double q[5], qt[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double acc = 0.0, d1 = 0.0;
+#pragma unroll
+      for (int l = 0; l < ML; ++l) {
+        acc = fma(c[v][l], t.phi[k][l], acc);
+        d1 = fma(Qt[v][l], t.phi[k][l], d1);
+      }
+      q[v] = acc; qt[v] = d1;
+    }
+    const P3 s = make_p3(g1, q);
+    double F1[3][5], G[3][5], du[3], dp;
+    flux3_d1(g1, s, qt, F1, du, dp);
+    contra3(Ji, F1, G);
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int l = 0; l < ML; ++l)
+        Qtt[v][l] -= G[0][v] * t.W[0][k][l] + G[1][v] * t.W[1][k][l] + G[2][v] * t.W[2][k][l];
+  }
+  // pass 3a: F_T at the interior points -> volume integral of the higher moments
+  double Vv[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Vv[v][l] = 0.0;
+#pragma unroll 1
+  for (int p = 0; p < NQ; ++p) {
+    double ph[ML], q[5], FT[3][5], G[3][5];
+#pragma unroll
+    for (int l = 0; l < ML; ++l) ph[l] = t.phi[p][l];
+    ft_point3t<ML>(g1, c1, c2, ph, c, Qt, Qtt, q, FT);
+    contra3(Ji, FT, G);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double f0 = t.qw[p] * G[0][v], f1 = t.qw[p] * G[1][v], f2 = t.qw[p] * G[2][v];
+#pragma unroll
+      for (int l = 1; l < ML; ++l)
+        Vv[v][l] = fma(f0, t.dref[0][p][l], fma(f1, t.dref[1][p][l], fma(f2, t.dref[2][p][l], Vv[v][l])));
+    }
+  }
+  // pass 3b: traces at the face points, in the face's canonical point order
+  const int code = m.code[i];
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {
+    const double an[3] = {geo(m, 10 + 3 * k, i), geo(m, 11 + 3 * k, i), geo(m, 12 + 3 * k, i)};
+    const double* fk = m.fphi + (size_t)((k * k3tPerms + ((code >> (3 * k)) & 7)) * NF) * ML;
+#pragma unroll 1
+    for (int p = 0; p < NF; ++p) {
+      double ph[ML], q[5], FT[3][5];
+#pragma unroll
+      for (int l = 0; l < ML; ++l) ph[l] = __ldg(fk + p * ML + l);
+      ft_point3t<ML>(g1, c1, c2, ph, c, Qt, Qtt, q, FT);
+      double* tr = w.trace + ((size_t)(k * NF + p) * 10) * N + i;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        tr[(size_t)v * N] = q[v];
+        tr[(size_t)(5 + v) * N] = ndot(an, FT, v);
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 1; l < ML; ++l) Qi[v * ML + l] = c[v][l] + dt * Vv[v][l];
+}
+
+// ------------------------------------------------------------ k3t_face
+// Sec. 3.3 Step 3 on the four faces, seen from each cell: both cells of a
+// face take its points in the same order, exactly negated normals and the
+// same sign-symmetric rounded operations, so their LLF values, f^LxW and
+// f^LxF are exact negatives.  Face integral of the higher moments; Steps
+// 4-5: Gamma, the density Lambda shared by the negative faces, the
+// Lax-Friedrichs state, mu over the 15 corners of the box of proposals.
+template <int DEG, int ML, int N1>
+__global__ void __launch_bounds__(128) k3t_face(const Mesh3T m, const Work3 w, double* __restrict__ Q,
+                                                const Args3 a) {
+  constexpr int NF = N1 * N1;
+  const Tables3T& t = c_tab3t[DEG - 1];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int N = m.N;
+  const double g = a.gamma, g1 = g - 1.0;
+  const double s = __longlong_as_double((long long)*w.smax);
+  const double dt = step_dt3t(w, m, a);
+  const double vol = geo(m, 9, i);
+  const int code = m.code[i];
+  double* Qi = Q + (size_t)i * 5 * ML;
+  double qb[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qb[v] = Qi[v * ML];
+  const P3 sb = make_p3(g1, qb);
+  double Fb[3][5];
+  flux3(sb, Fb);
+  double Ei[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) Ei[v][l] = 0.0;
+  double fW[4][5], fF[4][5];
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {
+    const int j = m.nbr[k * N + i], kj = (code >> (12 + 2 * k)) & 3;
+    const double an[3] = {geo(m, 10 + 3 * k, i), geo(m, 11 + 3 * k, i), geo(m, 12 + 3 * k, i)};
+    const double area = face_area(an);
+    const double nh[3] = {an[0] / area, an[1] / area, an[2] / area};
+    const bool wall = j < 0 && -1 - j == LXW_BC_REFLECT;
+    const double hs = 0.5 * s * area;
+    double qn[5];
+    if (j >= 0) {
+      const double* Qj = Q + (size_t)j * 5 * ML;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qn[v] = Qj[v * ML];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qn[v] = qb[v];
+      if (wall) mirror3(nh, qn);
+    }
+    {
+      const P3 sn = make_p3(g1, qn);
+      double Fn[3][5];
+      flux3(sn, Fn);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double ai = ndot(an, Fb, v), ak = ndot(an, Fn, v);
+        fF[k][v] = __fma_rn(-hs, __dsub_rn(qn[v], qb[v]), __dmul_rn(0.5, __dadd_rn(ai, ak)));
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fW[k][v] = 0.0;
+    const double* fk = m.fphi + (size_t)((k * k3tPerms + ((code >> (3 * k)) & 7)) * NF) * ML;
+#pragma unroll 1
+    for (int p = 0; p < NF; ++p) {
+      const double* tr = w.trace + ((size_t)(k * NF + p) * 10) * N + i;
+      double qi[5], Fi[5], qx[5], Fx[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { qi[v] = tr[(size_t)v * N]; Fi[v] = tr[(size_t)(5 + v) * N]; }
+      if (j >= 0) {
+        const double* tj = w.trace + ((size_t)(kj * NF + p) * 10) * N + j;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) { qx[v] = tj[(size_t)v * N]; Fx[v] = -tj[(size_t)(5 + v) * N]; }
+      } else if (wall) {
+        // exterior R q, and n . F_T(R q) = -R (n . F_T(q)) (the Euler flux's mirror symmetry)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) { qx[v] = qi[v]; Fx[v] = Fi[v]; }
+        mirror3(nh, qx);
+        mirror3(nh, Fx);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Fx[v] = -Fx[v];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) { qx[v] = qi[v]; Fx[v] = Fi[v]; }
+      }
+      const double hp = a.llf_global ? hs : 0.5 * fmin(s, fmax(lf_speed3(g, qi), lf_speed3(g, qx))) * area;
+      double ph[ML];
+#pragma unroll
+      for (int l = 1; l < ML; ++l) ph[l] = __ldg(fk + p * ML + l);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double fs = __fma_rn(-hp, __dsub_rn(qx[v], qi[v]), __dmul_rn(0.5, __dadd_rn(Fi[v], Fx[v])));
+        fW[k][v] = __fma_rn(t.fw[p], fs, fW[k][v]);
+        const double hw = t.fw[p] * fs;
+#pragma unroll
+        for (int l = 1; l < ML; ++l) Ei[v][l] = fma(hw, ph[l], Ei[v][l]);
+      }
+    }
+  }
+  const double dta = dt / vol;
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 1; l < ML; ++l) Qi[v * ML + l] -= dta * Ei[v][l];
+
+  // Steps 4-5
+  double Gam0 = vol / dt * qb[0];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Gam0 -= fF[k][0];
+  if (Gam0 < 0.0) atomicOr(w.status, (unsigned)LXW_ST_CFL);
+  double neg = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double df = fF[k][0] - fW[k][0];
+    if (df < 0.0) neg += df;
+  }
+  double ql[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc += fF[k][v];
+    ql[v] = qb[v] - dta * acc;
+  }
+  const double er = fmax(fmin(a.eps0, 0.5 * ql[0]), 0.0);
+  double lneg = 1.0;
+  if (neg < 0.0) lneg = fmin(1.0, fmax(0.0, (Gam0 - vol / dt * er) / (-neg)));
+  double lam[4], dq[4][5];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    lam[k] = (fF[k][0] - fW[k][0]) < 0.0 ? lneg : 1.0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dq[k][v] = dta * lam[k] * (fF[k][v] - fW[k][v]);
+  }
+  const double pl =
+      ql[0] > 0.0 ? g1 * (ql[4] - 0.5 * (ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3]) / ql[0]) : -1.0;
+  double mmin[4] = {1.0, 1.0, 1.0, 1.0};
+  if (!(ql[0] > 0.0) || !(pl > 0.0)) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mmin[k] = 0.0;
+  } else {
+    const double kap = fmin(a.eps0, 0.5 * pl) / g1;
+    const double h0 = ql[0] * ql[4] - 0.5 * (ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3]) - kap * ql[0];
+#pragma unroll 1
+    for (int cm = 1; cm < 16; ++cm) {
+      double dd[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if ((cm >> k) & 1)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) dd[v] += dq[k][v];
+      // h(mu) = rho E - |m|^2 / 2 - kappa rho along ql + mu dd
+      const double h1 = ql[0] * dd[4] + dd[0] * ql[4] - (ql[1] * dd[1] + ql[2] * dd[2] + ql[3] * dd[3]) - kap * dd[0];
+      const double h2 = dd[0] * dd[4] - 0.5 * (dd[1] * dd[1] + dd[2] * dd[2] + dd[3] * dd[3]);
+      double mu = 1.0;
+      if (!(ql[0] + dd[0] > 0.0) || h0 + h1 + h2 < 0.0) {
+        const double disc = fmax(h1 * h1 - 4.0 * h0 * h2, 0.0);
+        const double den = -h1 + sqrt(disc);
+        mu = den > 0.0 ? fmin(1.0, fmax(0.0, 2.0 * h0 / den)) : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if ((cm >> k) & 1) mmin[k] = fmin(mmin[k], mu);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w.prop[k * N + i] = lam[k] * mmin[k];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      w.flux[(size_t)(k * 10 + v) * N + i] = fW[k][v];
+      w.flux[(size_t)(k * 10 + 5 + v) * N + i] = fF[k][v];
+    }
+  }
+}
+
+// ------------------------------------------------------------ k3t_update
+// Sec. 3.3 Step 6: theta of a face = min of the two cells' proposals;
+// blended update of the averages.
+template <int ML>
+__global__ void __launch_bounds__(128) k3t_update(const Mesh3T m, const Work3 w, double* __restrict__ Q,
+                                                  const Args3 a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int N = m.N;
+  const double dt = step_dt3t(w, m, a);
+  const int code = m.code[i];
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int j = m.nbr[k * N + i], kj = (code >> (12 + 2 * k)) & 3;
+    double th = w.prop[k * N + i];
+    if (j >= 0) th = fmin(th, w.prop[kj * N + j]);
+    if (a.theta_face) a.theta_face[(size_t)i * 4 + k] = th;
+    // count each face once: from the lower cell (lower local face when a
+    // cell meets itself across a period), or from the cell of a boundary face
+    if (a.want_diag && th < 1.0 && (j < 0 || i < j || (i == j && k < kj))) atomicAdd(&w.diag->nface, 1ull);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double fw = w.flux[(size_t)(k * 10 + v) * N + i], ff = w.flux[(size_t)(k * 10 + 5 + v) * N + i];
+      acc[v] += th * fw + (1.0 - th) * ff;
+    }
+  }
+  double* Qi = Q + (size_t)i * 5 * ML;
+  const double dta = dt / geo(m, 9, i);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Qi[v * ML] -= dta * acc[v];
+}
+
+// ------------------------------------------------------------ k3t_shock
+// Sec. 4.1 on (rho, u, v, w, p) with the four face neighbours (a wall's
+// exterior: the mirrored average), alpha = alpha0 dx^1.5 with dx = |K|^(1/3).
+template <int DEG, int ML, int N1>
+__global__ void __launch_bounds__(128) k3t_shock(const Mesh3T m, const Work3 w, double* __restrict__ Q,
+                                                 const Args3 a) {
+  constexpr int NQ = N1 * N1 * N1, NF = N1 * N1, NPT = NQ + 4 * NF;
+  const Tables3T& t = c_tab3t[DEG - 1];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int N = m.N;
+  const double g1 = a.gamma - 1.0;
+  double* Qi = Q + (size_t)i * 5 * ML;
+  double c[5][ML];
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
+  auto prim = [&](const double q[5], double wv[5]) {
+    const double ri = 1.0 / q[0];
+    wv[0] = q[0]; wv[1] = q[1] * ri; wv[2] = q[2] * ri; wv[3] = q[3] * ri;
+    wv[4] = g1 * (q[4] - 0.5 * (q[1] * wv[1] + q[2] * wv[2] + q[3] * wv[3]));
+  };
+  double th = 1.0;
+  if (!(c[0][0] > 0.0)) {
+    th = 0.0;
+  } else {
+    const int code = m.code[i];
+    double qb[5], wb[5], Mx[5], Mn[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qb[v] = c[v][0];
+    prim(qb, wb);
+    const double al = a.alpha0 * pow(cbrt(geo(m, 9, i)), 1.5);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { Mx[v] = wb[v] + al; Mn[v] = wb[v] - al; }
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      const int j = m.nbr[k * N + i];
+      double qn[5], wn[5];
+      if (j >= 0) {
+        const double* Qj = Q + (size_t)j * 5 * ML;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qn[v] = Qj[v * ML];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qn[v] = qb[v];
+        if (-1 - j == LXW_BC_REFLECT) {
+          const double an[3] = {geo(m, 10 + 3 * k, i), geo(m, 11 + 3 * k, i), geo(m, 12 + 3 * k, i)};
+          const double area = face_area(an);
+          const double nh[3] = {an[0] / area, an[1] / area, an[2] / area};
+          mirror3(nh, qn);
+        }
+      }
+      if (!(qn[0] > 0.0)) continue;
+      prim(qn, wn);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { Mx[v] = fmax(Mx[v], wn[v]); Mn[v] = fmin(Mn[v], wn[v]); }
+    }
+    double hx[5], hn[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { hx[v] = -1e300; hn[v] = 1e300; }
+    bool bad = false;
+#pragma unroll 1
+    for (int p = 0; p < NPT; ++p) {
+      double ph[ML], q[5], wp[5];
+      load_phi<ML, NQ, NF>(t, m, code, p, ph);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 0; l < ML; ++l) acc = fma(c[v][l], ph[l], acc);
+        q[v] = acc;
+      }
+      if (!(q[0] > 0.0)) { bad = true; break; }
+      prim(q, wp);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) { hx[v] = fmax(hx[v], wp[v]); hn[v] = fmin(hn[v], wp[v]); }
+    }
+    if (bad) {
+      th = 0.0;
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        if (hx[v] > wb[v]) th = fmin(th, (Mx[v] - wb[v]) / (hx[v] - wb[v]));
+        if (hn[v] < wb[v]) th = fmin(th, (wb[v] - Mn[v]) / (wb[v] - hn[v]));
+      }
+      th = fmax(th, 0.0);
+    }
+  }
+  if (th < 1.0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int l = 1; l < ML; ++l) Qi[v * ML + l] = th * c[v][l];
+    if (a.want_diag) atomicAdd(&w.diag->nsc, 1ull);
+  }
+}
+
+// ------------------------------------------------------------ k3t_diag
+// Totals |K| Q^(1) and minimum density / pressure of the averages.
+template <int ML>
+__global__ void __launch_bounds__(256) k3t_diag(const Mesh3T m, const Work3 w, const double* __restrict__ Q,
+                                                double gamma) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool on = i < m.N;
+  auto ob = [](double x) {   // order-preserving bits
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+  };
+  double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  unsigned long long br = ~0ull, bp = ~0ull;
+  bool nan = false;
+  if (on) {
+    const double* Qi = Q + (size_t)i * 5 * ML;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      q[v] = Qi[v * ML];
+      nan = nan || !isfinite(q[v]);
+    }
+    const double p = (gamma - 1.0) * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+    br = ob(q[0]);
+    bp = ob(p);
+    const double vol = geo(m, 9, i);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] *= vol;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] += __shfl_down_sync(0xffffffffu, q[v], o);
+    const unsigned long long r = __shfl_down_sync(0xffffffffu, br, o), pp = __shfl_down_sync(0xffffffffu, bp, o);
+    br = r < br ? r : br;
+    bp = pp < bp ? pp : bp;
+  }
+  if (__any_sync(0xffffffffu, nan) && (threadIdx.x & 31) == 0) atomicOr(w.status, (unsigned)LXW_ST_NAN);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) atomicAdd(&w.diag->sum[v], q[v]);
+    atomicMin(&w.diag->minr, br);
+    atomicMin(&w.diag->minp, bp);
+  }
+}
+
+template <int DEG, int ML, int N1>
+int step3t_impl(const Mesh3T& m, const Work3& w, double* Q, const Args3& a, cudaStream_t st, int block, void** events,
+                int upto) {
+  const int grid = (m.N + block - 1) / block;
+  int ne = 0;
+  auto mark = [&]() { if (events) cudaEventRecord((cudaEvent_t)events[ne++], st); };
+  auto ok = [&]() { return cudaGetLastError() == cudaSuccess ? 0 : -1; };
+  k3t_reset<<<1, 32, 0, st>>>(w, a.want_diag);
+  mark();
+  k3t_moment<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  mark();
+  if (upto < 2) return ok();
+  k3t_ck<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  mark();
+  if (upto < 3) return ok();
+  k3t_face<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  mark();
+  if (upto < 4) return ok();
+  k3t_update<ML><<<grid, block, 0, st>>>(m, w, Q, a);
+  mark();
+  if (upto < 5) return ok();
+  if (a.shock_limiter) k3t_shock<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  mark();
+  if (a.want_diag) k3t_diag<ML><<<(m.N + 255) / 256, 256, 0, st>>>(m, w, Q, a.gamma);
+  return ok();
+}
+
+}  // namespace
+
+int upload_tables3t(int deg, const Tables3T& t) {
+  if (deg < 1 || deg > 2) return -1;
+  return cudaMemcpyToSymbol(c_tab3t, &t, sizeof(Tables3T), sizeof(Tables3T) * (deg - 1)) == cudaSuccess ? 0 : -1;
+}
+
+int launch_step3t(int deg, const Mesh3T& m, const Work3& w, double* Q, const Args3& a, void* stream, int block,
+                  void** events, int upto) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (deg == 1) return step3t_impl<1, 4, 2>(m, w, Q, a, st, block, events, upto);
+  if (deg == 2) return step3t_impl<2, 10, 3>(m, w, Q, a, st, block, events, upto);
+  return -2;
+}
+
+}  // namespace lxw

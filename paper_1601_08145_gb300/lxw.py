@@ -37,6 +37,7 @@ EXPORTS = [
     "lxw_solver_set_gate_wait_test", "lxw_run_to", "lxw_solver_get_options",
     "lxw3_solver_create", "lxw3_solver_destroy", "lxw3_solver_info", "lxw3_projection_points",
     "lxw3_project", "lxw3_step", "lxw3_run", "lxw3_profile_step", "lxw3_step_launches",
+    "lxw3_solver_create_tets", "lxw3_faces_per_element",
 ]
 
 
@@ -146,6 +147,9 @@ def lib():
     L.lxw3_run.argtypes = [_vp, _vp, C.c_int, C.c_double, _vp]
     L.lxw3_profile_step.argtypes = [_vp, _vp, C.c_double, C.POINTER(C.c_float)]
     L.lxw3_step_launches.argtypes = [_vp]
+    L.lxw3_solver_create_tets.argtypes = [C.c_int, _dp, C.c_int, _ip, _ip, _ip, C.c_int, C.POINTER(Options), _vp,
+                                          C.POINTER(_vp)]
+    L.lxw3_faces_per_element.argtypes = [_vp]
     _lib = L
     return L
 
@@ -600,12 +604,13 @@ PHASES3 = ("moment", "ck", "face", "update", "shock")
 
 
 class Solver3:
-    def __init__(self, handle, n3):
+    def __init__(self, handle, n3=None):
         self.h = handle
-        self.nx, self.ny, self.nz = n3
+        self.nx, self.ny, self.nz = n3 if n3 is not None else (None, None, None)
         N, ML, nproj = (C.c_int() for _ in range(3))
         _check(lib().lxw3_solver_info(handle, C.byref(N), C.byref(ML), C.byref(nproj)))
         self.N, self.ML, self.nproj = N.value, ML.value, nproj.value
+        self.E = lib().lxw3_faces_per_element(handle)
 
     @property
     def state_shape(self):
@@ -628,6 +633,28 @@ def lxw3_solver_create(nx, ny, nz, box, bc, degree, options=None, stream=None):
     return Solver3(h, (nx, ny, nz))
 
 
+def lxw3_solver_create_tets(xyz, tets, vid, degree, face_bc=None, options=None, stream=None):
+    """3D tetrahedral FP64 solver from host arrays: vertex positions xyz[nv][3],
+    positively oriented cells tets[nt][4], vertex ids vid[nv] (equal ids glue
+    periodic faces), face_bc[nt][4] codes of unmatched faces (None: transparent)."""
+    h = _vp()
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    v = np.ascontiguousarray(vid, dtype=np.int32).reshape(-1)
+    if v.shape[0] != x.shape[0]:
+        raise ValueError("vid needs one id per vertex")
+    fb = None
+    if face_bc is not None:
+        fb = np.ascontiguousarray(face_bc, dtype=np.int32).reshape(-1, 4)
+        if fb.shape[0] != t.shape[0]:
+            raise ValueError("face_bc needs four codes per cell")
+    _check(lib().lxw3_solver_create_tets(x.shape[0], x.ctypes.data_as(_dp), t.shape[0], t.ctypes.data_as(_ip),
+                                         v.ctypes.data_as(_ip), fb.ctypes.data_as(_ip) if fb is not None else None,
+                                         degree, C.byref(options) if options is not None else None,
+                                         _stream_handle(stream), C.byref(h)))
+    return Solver3(h)
+
+
 def lxw3_projection_points(solver):
     xyz = np.zeros((solver.N, solver.nproj, 3))
     _check(lib().lxw3_projection_points(solver.h, xyz.ctypes.data_as(_dp)))
@@ -642,7 +669,7 @@ def lxw3_project(solver, prim, Q):
 def lxw3_step(solver, Q, dt=0.0, cfl=0.1, diag=False, theta_face=None):
     d = Diag3()
     st = _check(lib().lxw3_step(solver.h, _ptr(Q, solver.state_shape, "Q"), dt, cfl, C.byref(d),
-                                _ptr(theta_face, (solver.N, 6), "theta_face")),
+                                _ptr(theta_face, (solver.N, solver.E), "theta_face")),
                 allow=(ERR_NONPOSITIVE, ERR_CFL, ERR_NAN))
     return _diag_result(st, d) if diag else None
 

@@ -160,18 +160,17 @@ def tet_mesh(n: int, box=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0), periodic: bool = False,
         ii = idx(I, J, K).ravel()[inner]
         xyz[ii] += jitter * h * r[ii]
     perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
-    tets = []
-    for k in range(n):
-        for j in range(n):
-            for i in range(n):
-                for pm in perms:
-                    c = [i, j, k]
-                    vs = [idx(*c)]
-                    for a in pm:
-                        c[a] += 1
-                        vs.append(idx(*c))
-                    tets.append(vs)
-    tets = np.array(tets, dtype=np.int32)
+    # boxes in (k, j, i) order with i fastest, six cells per box in the order of perms
+    Kb, Jb, Ib = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    base = np.stack([Ib.ravel(), Jb.ravel(), Kb.ravel()], axis=1)
+    tets = np.empty((n ** 3, 6, 4), dtype=np.int64)
+    for q, pm in enumerate(perms):
+        c = base.copy()
+        tets[:, q, 0] = idx(c[:, 0], c[:, 1], c[:, 2])
+        for s_, a in enumerate(pm):
+            c[:, a] += 1
+            tets[:, q, s_ + 1] = idx(c[:, 0], c[:, 1], c[:, 2])
+    tets = tets.reshape(-1, 4).astype(np.int32)
     p = xyz[tets]
     vol = np.einsum("ij,ij->i", np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), p[:, 3] - p[:, 0])
     neg = vol < 0

@@ -118,3 +118,29 @@ def test_3d_argument_errors_without_gpu(libpath):
         with pytest.raises(lxw.LxwError) as e:
             lxw.lxw3_solver_create(kw["nx"], 3, 3, kw["box"], kw["bc"], kw["degree"], kw["options"])
         assert e.value.code == lxw.ERR_ARG, b
+
+
+def test_tet_argument_errors_without_gpu(libpath):
+    """The tetrahedral solver validates its mesh on the host, before any
+    CUDA call: indices, repeated ids, orientation, over-shared faces and the
+    boundary codes of unmatched faces."""
+    from paper_1601_08145_gb300 import lxw
+    import synth
+    xyz, tets, vid = synth.tet_mesh(2, jitter=0.1, seed=1)
+    flipped = tets.copy()
+    flipped[0, [1, 2]] = flipped[0, [2, 1]]
+    out_of_range = tets.copy()
+    out_of_range[3, 2] = len(xyz)
+    repeated = vid.copy()
+    repeated[tets[0, 1]] = vid[tets[0, 0]]
+    tripled = np.concatenate([tets, tets[:1]])
+    bad = [dict(degree=3), dict(tets=flipped), dict(tets=out_of_range), dict(vid=repeated), dict(tets=tripled),
+           dict(face_bc=np.zeros((len(tets), 4), dtype=np.int32)),
+           dict(options=lxw.lxw_options_default(precision=lxw.PREC_MIXED))]
+    for b in bad:
+        kw = dict(xyz=xyz, tets=tets, vid=vid, degree=2, face_bc=None, options=None)
+        kw.update(b)
+        with pytest.raises(lxw.LxwError) as e:
+            lxw.lxw3_solver_create_tets(kw["xyz"], kw["tets"], kw["vid"], kw["degree"], face_bc=kw["face_bc"],
+                                        options=kw["options"])
+        assert e.value.code == lxw.ERR_ARG, b
