@@ -478,10 +478,12 @@ def ck3_flops_per_element(deg):
 
 
 def run_blast3d(args):
-    """The 3D FP64 form on the 3D point-energy blast (Cartesian hexahedra, or
-    with --workload blast3t the same blast on Kuhn tetrahedra): K graph-
-    replayed steps bracketed by CUDA events (the state, 265-354 MB, exceeds
-    the L2), per-phase times from a traced step, the oracle on a sample."""
+    """The 3D forms on the 3D point-energy blast (Cartesian hexahedra, or with
+    --workload blast3t the same blast on Kuhn tetrahedra): the mixed form
+    (the line's value) and the FP64 form, each K graph-replayed steps from the
+    same projected state bracketed by CUDA events (the state, 265-354 MB,
+    exceeds the L2), per-phase times from traced steps, the oracle on a
+    sample.  --form mixed / fp64 times one form only."""
     import torch
     from paper_1601_08145_gb300 import build, lxw as L
     build.build()
@@ -494,47 +496,76 @@ def run_blast3d(args):
     stream = torch.cuda.current_stream()
     if tet:
         xyz, tets, vid = synth.tet_mesh(n, box=box)
-        s = L.lxw3_solver_create_tets(xyz, tets, vid, b["deg"], face_bc=np.full((len(tets), 4), 1, dtype=np.int32),
-                                      options=L.lxw_options_default(), stream=stream)
-        del xyz, tets, vid
+        walls = np.full((len(tets), 4), 1, dtype=np.int32)
+        make = lambda o: L.lxw3_solver_create_tets(xyz, tets, vid, b["deg"], face_bc=walls, options=o,  # noqa: E731
+                                                   stream=stream)
     else:
-        s = L.lxw3_solver_create(n, n, n, box, (1,) * 6, b["deg"], L.lxw_options_default(), stream=stream)
+        make = lambda o: L.lxw3_solver_create(n, n, n, box, (1,) * 6, b["deg"], o, stream=stream)  # noqa: E731
+    forms = {"mixed": L.PREC_MIXED, "fp64": L.PREC_FP64}
+    if args.form in forms:
+        forms = {args.form: forms[args.form]}
     ic = synth.ic_blast3d(n, hw)
-    xyz = L.lxw3_projection_points(s)
-    prim = torch.from_numpy(np.stack(np.broadcast_arrays(*ic(xyz[..., 0], xyz[..., 1], xyz[..., 2])), axis=-1).copy())
-    del xyz
-    Q = torch.zeros(s.state_shape, dtype=torch.float64, device="cuda")
-    L.lxw3_project(s, prim.cuda(), Q)
-    del prim
-    L.lxw3_run(s, Q, max(args.warmup, 3), b["cfl"])
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-    clocks.start(); time.sleep(0.5)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    d = L.lxw3_run(s, Q, args.steps, b["cfl"], diag=True)
-    ev1.record(); torch.cuda.synchronize()
-    clk = clocks.stop()
-    total_ms = ev0.elapsed_time(ev1)
-    phases = [L.lxw3_profile_step(s, Q, b["cfl"]) for _ in range(3)]
-    ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
-    dof = s.N * 5 * s.ML
-    flops = (ck3t_flops_per_element if tet else ck3_flops_per_element)(b["deg"]) * s.N
+    Q0 = None
+    res = {}
     probes = fma_probes()
-    peak = 1.25
-    roof = {"kernel": "k3t_ck" if tet else "k3_ck", "bound": "alu", "pipe": "fp64", "achieved": flops / (ph["ck"] / 1e3) / 1e12,
-            "peak": peak, "unit": "TFLOP/s", "peak_source": "nominal GB300 FP64 rate (recipe table)",
-            "peak_measured_fma_probe": probes.get("fp64"), "algorithmic_flops_per_launch": flops,
-            "launch_ms": ph["ck"], "traffic": None}
-    roof["frac"] = roof["achieved"] / peak
-    out = {"metric": METRIC, "value": dof * args.steps / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": b["desc"], "elements": s.N, "degree": b["deg"], "cfl": b["cfl"],
-                      "l2": "state (%d MB) larger than the L2" % (s.N * 5 * s.ML * 8 // 10 ** 6), "timing": "graph-replayed steps, CUDA events"},
-           "phases_ms": ph, "roofline": roof, "gpu_launches": args.steps * L.lxw3_step_launches(s) + 1,
-           "clocks": clk, "positivity_last_step": {"min_rho": d["min_rho"], "min_p": d["min_p"]},
-           "status_last_step": d["status"]}
+    flop_cell = (ck3t_flops_per_element if tet else ck3_flops_per_element)(b["deg"])
+    for name, prec in forms.items():
+        s = make(L.lxw_options_default(precision=prec))
+        if Q0 is None:
+            xyz3 = L.lxw3_projection_points(s)
+            prim = torch.from_numpy(np.stack(np.broadcast_arrays(*ic(xyz3[..., 0], xyz3[..., 1], xyz3[..., 2])),
+                                             axis=-1).copy())
+            del xyz3
+            Q0 = torch.zeros(s.state_shape, dtype=torch.float64, device="cuda")
+            L.lxw3_project(s, prim.cuda(), Q0)
+            del prim
+        Q = Q0.clone()
+        L.lxw3_run(s, Q, max(args.warmup, 3), b["cfl"])
+        clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+        clocks.start(); time.sleep(0.5)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        d = L.lxw3_run(s, Q, args.steps, b["cfl"], diag=True)
+        ev1.record(); torch.cuda.synchronize()
+        clk = clocks.stop()
+        total_ms = ev0.elapsed_time(ev1)
+        phases = [L.lxw3_profile_step(s, Q, b["cfl"]) for _ in range(3)]
+        ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+        flops = flop_cell * s.N
+        fp32 = name == "mixed"
+        peak = FP32_PEAK_TFLOPS if fp32 else 1.25
+        roof = {"kernel": ("k3t_ck" if tet else "k3_ck") + ("<float>" if fp32 else "<double>"), "bound": "alu",
+                "pipe": "fp32" if fp32 else "fp64", "achieved": flops / (ph["ck"] / 1e3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s",
+                "peak_source": ("152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if fp32
+                                else "nominal GB300 FP64 rate (recipe table)"),
+                "peak_measured_fma_probe": probes.get("fp32" if fp32 else "fp64"),
+                "algorithmic_flops_per_launch": flops, "launch_ms": ph["ck"], "traffic": None}
+        roof["frac"] = roof["achieved"] / peak
+        res[name] = {"value": s.N * 5 * s.ML * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                     "phases_ms": ph, "roofline": roof, "clocks": clk, "launches": args.steps * L.lxw3_step_launches(s) + 1,
+                     "positivity_last_step": {"min_rho": d["min_rho"], "min_p": d["min_p"]}, "status_last_step": d["status"],
+                     "elements": s.N, "dof": s.N * 5 * s.ML}
+        del s
+    head = "mixed" if "mixed" in res else "fp64"
+    r = res[head]
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if head == "mixed" else "f64", "data": "synthetic",
+           "config": {"workload": b["desc"], "elements": r["elements"], "degree": b["deg"], "cfl": b["cfl"],
+                      "form": {"mixed": "mixed (FP32 CK kernel, FP64 state and limiters)", "fp64": "FP64"}[head],
+                      "l2": "state (%d MB) larger than the L2" % (r["dof"] * 8 // 10 ** 6),
+                      "timing": "graph-replayed steps, CUDA events"},
+           "phases_ms": r["phases_ms"], "roofline": r["roofline"],
+           "gpu_launches": sum(x["launches"] for x in res.values()),
+           "clocks": r["clocks"], "positivity_last_step": r["positivity_last_step"],
+           "status_last_step": r["status_last_step"]}
+    if len(res) > 1:
+        out["fp64_form"] = {k: res["fp64"][k] for k in ("value", "ms_per_step", "phases_ms", "roofline",
+                                                        "positivity_last_step", "status_last_step")}
+        out["mixed_vs_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
     if not args.no_cpu_baseline:
         from oracle import oracle as O
         if tet:   # a 24^3-box sample (82,944 cells) of the same blast

@@ -485,8 +485,13 @@ typedef struct {
 /* nx x ny x nz cells of box = (x0, x1, y0, y1, z0, z1); bc[6] per side:
  * LXW_BC_PERIODIC (paired on both sides of an axis), LXW_BC_REFLECT or
  * LXW_BC_TRANSPARENT.  degree 1 or 2.  Options: gamma, eps0, alpha0,
- * shock_limiter, llf_global, block_threads; precision must be
- * LXW_PREC_FP64, moment_exact 0 and ck_order 3 (or 0).  Allocates the
+ * shock_limiter, llf_global, block_threads, precision; moment_exact 0 and
+ * ck_order 3 (or 0).  precision LXW_PREC_FP64: every operation in FP64;
+ * LXW_PREC_MIXED: the Cauchy-Kovalevskaya kernel (point values, flux
+ * derivatives, q_t and q_tt, the volume integral, the traces) in FP32,
+ * while the state, the cell averages, the face fluxes, the moment, flux and
+ * shock limiters and every positivity decision stay FP64 (the state keeps
+ * its FP64 layout; the volume term is added to it in FP64).  Allocates the
  * workspace (about (60 NF + 90) doubles per cell, NF = (degree + 1)^2).
  * Errors: LXW_ERR_ARG, LXW_ERR_NOMEM, LXW_ERR_CUDA. */
 lxw_status lxw3_solver_create(int nx, int ny, int nz, const double box[6], const int bc[6], int degree,

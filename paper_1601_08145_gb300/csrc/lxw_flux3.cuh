@@ -14,17 +14,54 @@ __device__ __forceinline__ double speed_of3(double g, const double q[5]) {
   return sqrt(k2) + (p > 0.0 ? sqrt(g * p * ri) : 0.0);
 }
 
+// fma / min / max in the argument's own precision (an unqualified fma on
+// floats may resolve to the double function and run on the FP64 pipe).
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fminT(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float fminT(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double fmaxT(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float fmaxT(float a, float b) { return fmaxf(a, b); }
+
+// A value the compiler must keep (in a register, or spilled) rather than
+// recompute at each use: under register pressure it otherwise re-derives
+// FP32 constants from FP64 sources (divisions, conversions) on the FP64 pipe.
+__device__ __forceinline__ float opaque(float x) {
+  asm volatile("" : "+f"(x));
+  return x;
+}
+__device__ __forceinline__ double opaque(double x) {
+  asm volatile("" : "+d"(x));
+  return x;
+}
+
+// Explicitly rounded arithmetic in either precision: sign-symmetric, so
+// operations on negated operands give exactly negated results.
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_sqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float rn_sqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double rn_rcp(double a) { return __drcp_rn(a); }
+__device__ __forceinline__ float rn_rcp(float a) { return __frcp_rn(a); }
+
 // The local Lax-Friedrichs speed of a trace with explicitly rounded
 // operations: both cells of a face evaluate it on the same two traces and
 // must get the same value.
-__device__ __forceinline__ double lf_speed3(double g, const double q[5]) {
-  if (!(q[0] > 0.0)) return 0.0;
-  const double ri = __drcp_rn(q[0]);
-  const double u = __dmul_rn(q[1], ri), v = __dmul_rn(q[2], ri), w = __dmul_rn(q[3], ri);
-  const double k2 = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
-  const double p = __dmul_rn(g - 1.0, __dsub_rn(q[4], __dmul_rn(0.5, __dmul_rn(q[0], k2))));
-  const double c = p > 0.0 ? __dsqrt_rn(__dmul_rn(__dmul_rn(g, p), ri)) : 0.0;
-  return __dadd_rn(__dsqrt_rn(k2), c);
+template <typename T>
+__device__ __forceinline__ T lf_speed3(T g, const T q[5]) {
+  if (!(q[0] > T(0))) return T(0);
+  const T ri = rn_rcp(q[0]);
+  const T u = rn_mul(q[1], ri), v = rn_mul(q[2], ri), w = rn_mul(q[3], ri);
+  const T k2 = rn_add(rn_add(rn_mul(u, u), rn_mul(v, v)), rn_mul(w, w));
+  const T p = rn_mul(g - T(1), rn_sub(q[4], rn_mul(T(0.5), rn_mul(q[0], k2))));
+  const T c = p > T(0) ? rn_sqrt(rn_mul(rn_mul(g, p), ri)) : T(0);
+  return rn_add(rn_sqrt(k2), c);
 }
 
 __device__ __forceinline__ void block_max3(double v, unsigned long long* dst) {
@@ -49,45 +86,52 @@ __device__ __forceinline__ void block_max3(double v, unsigned long long* dst) {
 }
 
 // ---------------------------------------------------------------- flux
+// Templated on the arithmetic type: double for the FP64 forms, float for the
+// FP32 Cauchy-Kovalevskaya kernels of the mixed forms.
 // Point state with its primitives.
-struct P3 {
-  double q[5];
-  double ri, u[3], p;
+template <typename T>
+struct P3T {
+  T q[5];
+  T ri, u[3], p;
 };
-__device__ __forceinline__ P3 make_p3(double g1, const double q[5]) {
-  P3 s;
+using P3 = P3T<double>;
+
+template <typename T>
+__device__ __forceinline__ P3T<T> make_p3(T g1, const T q[5]) {
+  P3T<T> s;
 #pragma unroll
   for (int v = 0; v < 5; ++v) s.q[v] = q[v];
-  s.ri = 1.0 / q[0];
+  s.ri = T(1) / q[0];
 #pragma unroll
   for (int d = 0; d < 3; ++d) s.u[d] = q[1 + d] * s.ri;
-  s.p = g1 * (q[4] - 0.5 * (q[1] * s.u[0] + q[2] * s.u[1] + q[3] * s.u[2]));
+  s.p = g1 * (q[4] - T(0.5) * (q[1] * s.u[0] + q[2] * s.u[1] + q[3] * s.u[2]));
   return s;
 }
 
 // F_d(q), d = 0, 1, 2
-__device__ __forceinline__ void flux3(const P3& s, double F[3][5]) {
+template <typename T>
+__device__ __forceinline__ void flux3(const P3T<T>& s, T F[3][5]) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     F[d][0] = s.q[1 + d];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) F[d][1 + e] = s.q[1 + e] * s.u[d] + (e == d ? s.p : 0.0);
+    for (int e = 0; e < 3; ++e) F[d][1 + e] = s.q[1 + e] * s.u[d] + (e == d ? s.p : T(0));
     F[d][4] = (s.q[4] + s.p) * s.u[d];
   }
 }
 
 // F'(q) w; also the primitive increments du (velocity) and dp along w
-__device__ __forceinline__ void flux3_d1(double g1, const P3& s, const double w[5], double F[3][5], double du[3],
-                                         double& dp) {
+template <typename T>
+__device__ __forceinline__ void flux3_d1(T g1, const P3T<T>& s, const T w[5], T F[3][5], T du[3], T& dp) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) du[d] = (w[1 + d] - s.u[d] * w[0]) * s.ri;
-  const double k2 = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
-  dp = g1 * (w[4] - (s.u[0] * w[1] + s.u[1] * w[2] + s.u[2] * w[3]) + 0.5 * k2 * w[0]);
+  const T k2 = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
+  dp = g1 * (w[4] - (s.u[0] * w[1] + s.u[1] * w[2] + s.u[2] * w[3]) + T(0.5) * k2 * w[0]);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     F[d][0] = w[1 + d];
 #pragma unroll
-    for (int e = 0; e < 3; ++e) F[d][1 + e] = w[1 + e] * s.u[d] + s.q[1 + e] * du[d] + (e == d ? dp : 0.0);
+    for (int e = 0; e < 3; ++e) F[d][1 + e] = w[1 + e] * s.u[d] + s.q[1 + e] * du[d] + (e == d ? dp : T(0));
     F[d][4] = (w[4] + dp) * s.u[d] + (s.q[4] + s.p) * du[d];
   }
 }
@@ -95,19 +139,209 @@ __device__ __forceinline__ void flux3_d1(double g1, const P3& s, const double w[
 // F''(q)(w, w) from the increments of flux3_d1: along q + t w the density
 // and momentum are linear, so u'' = -2 w_rho u' / rho and
 // p'' = -(g-1)(m' . u' + m . u'' / 2)
-__device__ __forceinline__ void flux3_d2(double g1, const P3& s, const double w[5], const double du[3], double dp,
-                                         double F[3][5]) {
-  double d2u[3];
+template <typename T>
+__device__ __forceinline__ void flux3_d2(T g1, const P3T<T>& s, const T w[5], const T du[3], T dp, T F[3][5]) {
+  T d2u[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) d2u[d] = -2.0 * w[0] * du[d] * s.ri;
-  const double d2p = -g1 * ((w[1] * du[0] + w[2] * du[1] + w[3] * du[2]) +
-                            0.5 * (s.q[1] * d2u[0] + s.q[2] * d2u[1] + s.q[3] * d2u[2]));
+  for (int d = 0; d < 3; ++d) d2u[d] = T(-2) * w[0] * du[d] * s.ri;
+  const T d2p = -g1 * ((w[1] * du[0] + w[2] * du[1] + w[3] * du[2]) +
+                       T(0.5) * (s.q[1] * d2u[0] + s.q[2] * d2u[1] + s.q[3] * d2u[2]));
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    F[d][0] = 0.0;
+    F[d][0] = T(0);
 #pragma unroll
-    for (int e = 0; e < 3; ++e) F[d][1 + e] = 2.0 * w[1 + e] * du[d] + s.q[1 + e] * d2u[d] + (e == d ? d2p : 0.0);
-    F[d][4] = d2p * s.u[d] + 2.0 * (w[4] + dp) * du[d] + (s.q[4] + s.p) * d2u[d];
+    for (int e = 0; e < 3; ++e) F[d][1 + e] = T(2) * w[1 + e] * du[d] + s.q[1 + e] * d2u[d] + (e == d ? d2p : T(0));
+    F[d][4] = d2p * s.u[d] + T(2) * (w[4] + dp) * du[d] + (s.q[4] + s.p) * d2u[d];
   }
 }
 
+// ---------------------------------------------------------------- moment limiter
+// Sec. 3.1 Steps 0-2 (Lemma 1's secant) on one cell's coefficients c[5][ML]
+// (scaled in place when limited); load(p, ph) gives the basis values at
+// limiter point p.  Returns theta (0 for a non-positive average, nonpos set)
+// and smax = max |u| + c of the limited state over its average and points.
+// One pass over the points yields the density minimum, the pressure
+// proposal for an unlimited density and the wave speed, which is all a cell
+// that is not limited needs; a limited cell takes the pressure pass with its
+// density theta and a wave-speed pass over the scaled state.
+template <int ML, int NPT, class Load>
+__device__ __forceinline__ double moment_cell3(double c[5][ML], double g, double eps0, const Load& load, double& smax,
+                                               bool& nonpos) {
+  const double g1 = g - 1.0;
+  const double pb = c[0][0] > 0.0
+                        ? g1 * (c[4][0] - 0.5 * (c[1][0] * c[1][0] + c[2][0] * c[2][0] + c[3][0] * c[3][0]) / c[0][0])
+                        : -1.0;
+  double qa[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) qa[v] = c[v][0];
+  nonpos = !(c[0][0] > 0.0) || !(pb > 0.0);
+  if (nonpos) {   // Step 0: flatten the cell
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+#pragma unroll
+      for (int l = 1; l < ML; ++l) c[v][l] = 0.0;
+    smax = speed_of3(g, qa);
+    return 0.0;
+  }
+  const double er = fmin(eps0, 0.5 * c[0][0]), ep = fmin(eps0, 0.5 * pb);
+  double thr = 1.0, th = 1.0, sm = speed_of3(g, qa);
+#pragma unroll 1
+  for (int p = 0; p < NPT; ++p) {
+    double ph[ML];
+    load(p, ph);
+    double q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double d = 0.0;
+#pragma unroll
+      for (int l = 1; l < ML; ++l) d = fma(c[v][l], ph[l], d);
+      q[v] = c[v][0] + d;
+    }
+    if (q[0] < er) thr = fmin(thr, (c[0][0] - er) / (c[0][0] - q[0]));
+    const double pt = g1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+    if (pt < ep) th = fmin(th, (pb - ep) / (pb - pt));
+    sm = fmax(sm, speed_of3(g, q));
+  }
+  if (thr < 1.0) {   // Step 2 again on the density-limited state
+    th = thr;
+#pragma unroll 1
+    for (int p = 0; p < NPT; ++p) {
+      double ph[ML];
+      load(p, ph);
+      double q[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double d = 0.0;
+#pragma unroll
+        for (int l = 1; l < ML; ++l) d = fma(c[v][l], ph[l], d);
+        q[v] = c[v][0] + thr * d;
+      }
+      const double pt = g1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
+      if (pt < ep) th = fmin(th, thr * (pb - ep) / (pb - pt));
+    }
+  }
+  th = fmax(th, 0.0);
+  if (!(th < 1.0)) {
+    smax = sm;
+    return th;
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v)
+#pragma unroll
+    for (int l = 1; l < ML; ++l) c[v][l] *= th;
+  sm = speed_of3(g, qa);
+#pragma unroll 1
+  for (int p = 0; p < NPT; ++p) {
+    double ph[ML];
+    load(p, ph);
+    double q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double acc = 0.0;
+#pragma unroll
+      for (int l = 0; l < ML; ++l) acc = fma(c[v][l], ph[l], acc);
+      q[v] = acc;
+    }
+    sm = fmax(sm, speed_of3(g, q));
+  }
+  smax = sm;
+  return th;
+}
+
+// ---------------------------------------------------------------- FP32 screens
+// The mixed forms screen the moment and shock limiters in FP32.  With S_v =
+// |c_v0| + sum_l |c_vl| max_p |phi_l(p)|, the FP32 value of variable v at any
+// limiter point is within ~ML 2^-24 S_v of the exact one; kScreenTol = 1e-5
+// leaves a margin of more than 10x.  A cell whose FP32 values clear the
+// limiter's thresholds by that bound at every point is provably not limited
+// in FP64 either; every other cell takes the FP64 path, so the decisions
+// equal the FP64 form's.
+constexpr float kScreenTol = 1e-5f;
+
+template <int ML>
+__device__ __forceinline__ void screen_state3(const double c[5][ML], const float* phimax, float cf[5][ML],
+                                              float S[5]) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    float sv = 0.0f;
+#pragma unroll
+    for (int l = 0; l < ML; ++l) {
+      cf[v][l] = opaque((float)c[v][l]);
+      sv = fmaf(fabsf(cf[v][l]), phimax[l], sv);
+    }
+    S[v] = sv;
+  }
+}
+
+// Sec. 3.1 screen: true when every point has rho > er and p > ep by more than
+// the bound (theta = 1); smax is then the FP32 wave speed over the points.
+template <int ML, int NPT, class LoadF>
+__device__ __forceinline__ bool moment_screen3(const float cf[5][ML], const float S[5], float g, float er, float ep,
+                                               const LoadF& loadf, float& smax) {
+  const float g1 = g - 1.0f;
+  float sm = 0.0f;
+#pragma unroll 1
+  for (int p = 0; p < NPT; ++p) {
+    float ph[ML];
+    loadf(p, ph);
+    float q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      float acc = cf[v][0];
+#pragma unroll
+      for (int l = 1; l < ML; ++l) acc = fmaf(cf[v][l], ph[l], acc);
+      q[v] = acc;
+    }
+    if (!(q[0] > er * (1.0f + kScreenTol) + kScreenTol * S[0])) return false;
+    const float ri = 1.0f / q[0];
+    const float u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
+    const float k2 = u * u + v * v + w * w;
+    const float pp = g1 * (q[4] - 0.5f * q[0] * k2);
+    const float B = S[4] + fabsf(u) * S[1] + fabsf(v) * S[2] + fabsf(w) * S[3] + 0.5f * k2 * S[0];
+    if (!(pp > ep * (1.0f + kScreenTol) + kScreenTol * g1 * B)) return false;
+    sm = fmaxf(sm, sqrtf(k2) + sqrtf(g * pp * ri));
+  }
+  smax = sm;
+  return true;
+}
+
+// Sec. 4.1 screen: true when every point's primitives lie inside [Mn, Mx]
+// by more than their bounds (theta = 1).  Mx, Mn are the FP64 bounds.
+template <int ML, int NPT, class LoadF>
+__device__ __forceinline__ bool shock_screen3(const float cf[5][ML], const float S[5], float g, const double Mx[5],
+                                              const double Mn[5], const LoadF& loadf) {
+  const float g1 = g - 1.0f;
+  float hi[5], lo[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    hi[v] = (float)Mx[v] - kScreenTol * fabsf((float)Mx[v]);
+    lo[v] = (float)Mn[v] + kScreenTol * fabsf((float)Mn[v]);
+  }
+#pragma unroll 1
+  for (int p = 0; p < NPT; ++p) {
+    float ph[ML];
+    loadf(p, ph);
+    float q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      float acc = cf[v][0];
+#pragma unroll
+      for (int l = 1; l < ML; ++l) acc = fmaf(cf[v][l], ph[l], acc);
+      q[v] = acc;
+    }
+    const float e0 = kScreenTol * S[0];
+    if (!(q[0] > 2.0f * e0)) return false;
+    const float ri = 1.0f / q[0];
+    const float u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
+    const float k2 = u * u + v * v + w * w;
+    const float pp = g1 * (q[4] - 0.5f * q[0] * k2);
+    const float wv[5] = {q[0], u, v, w, pp};
+    const float ev[5] = {e0, kScreenTol * (S[1] + fabsf(u) * S[0]) * ri, kScreenTol * (S[2] + fabsf(v) * S[0]) * ri,
+                         kScreenTol * (S[3] + fabsf(w) * S[0]) * ri,
+                         kScreenTol * g1 * (S[4] + fabsf(u) * S[1] + fabsf(v) * S[2] + fabsf(w) * S[3] + 0.5f * k2 * S[0])};
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      if (!(wv[c] + ev[c] <= hi[c] && wv[c] - ev[c] >= lo[c])) return false;
+  }
+  return true;
+}

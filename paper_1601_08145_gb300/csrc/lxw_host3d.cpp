@@ -123,6 +123,8 @@ void make_tables3(int deg, Tables3& t, std::vector<double>& pj, std::vector<doub
       for (int ax = 0; ax < 3; ++ax)
         for (int l = 0; l < ML; ++l) t.dref[ax][p][l] = grad[ax * ML + l];
   }
+  for (int p = 0; p < NPT; ++p)
+    for (int l = 0; l < ML; ++l) t.phimax[l] = std::max(t.phimax[l], std::fabs(t.phi[p][l]));
   // D_d[m][l] = (1/8) Int d_d phi_m phi_l (exact with n points per direction),
   // W_d[k][l] = qw_k sum_m phi_m(x_k) D_d[m][l]
   for (int ax = 0; ax < 3; ++ax) {
@@ -162,7 +164,8 @@ lxw_status options3(const lxw_options* optp, const char* who, lxw_options& opt) 
   if (optp) opt = *optp; else lxw_options_default(&opt);
   const std::string w(who);
   if (!(opt.gamma > 1.0)) return fail3(LXW_ERR_ARG, w + ": gamma must exceed 1");
-  if (opt.precision != LXW_PREC_FP64) return fail3(LXW_ERR_ARG, w + ": the 3D form is FP64 only");
+  if (opt.precision != LXW_PREC_FP64 && opt.precision != LXW_PREC_MIXED)
+    return fail3(LXW_ERR_ARG, w + ": the 3D forms are FP64 or mixed (FP32 Cauchy-Kovalevskaya kernel)");
   if (opt.moment_exact || (opt.ck_order != 0 && opt.ck_order != 3))
     return fail3(LXW_ERR_ARG, w + ": moment_exact and ck_order 4 are 2D options");
   if (opt.block_threads <= 0) opt.block_threads = 128;
@@ -325,6 +328,7 @@ Args3 make_args3(const lxw_solver3* s, double dt, double cfl, int want_diag, dou
   a.dt_in = dt; a.cfl = cfl; a.gamma = s->opt.gamma; a.eps0 = s->opt.eps0; a.alpha0 = s->opt.alpha0;
   a.shock_limiter = s->opt.shock_limiter; a.llf_global = s->opt.llf_global; a.want_diag = want_diag;
   a.theta_face = theta_face;
+  a.ck_fp32 = s->opt.precision == LXW_PREC_MIXED;
   return a;
 }
 
@@ -618,6 +622,9 @@ void make_tables3t(int deg, Tables3T& t, std::vector<double>& fphi, std::vector<
       }
     }
   }
+  for (int k = 0; k < NQ; ++k)
+    for (int l = 0; l < ML; ++l) t.phimax[l] = std::max(t.phimax[l], std::fabs(t.phi[k][l]));
+  for (size_t e = 0; e < fphi.size(); ++e) t.phimax[e % ML] = std::max(t.phimax[e % ML], std::fabs(fphi[e]));
   // projection rule: deg + 3 points per direction
   std::vector<double> jp, jwt;
   tet_rule_host(deg + 3, jp, jwt);
@@ -766,6 +773,8 @@ lxw_status lxw3_solver_create_tets(int n_vertices, const double* xyz, int n_tets
   int* dnbr = (int*)dalloc(sizeof(int) * hnbr.size());
   int* dcode = (int*)dalloc(sizeof(int) * N);
   double* dfphi = (double*)dalloc(sizeof(double) * fphi.size());
+  float* dfphif = (float*)dalloc(sizeof(float) * fphi.size());
+  std::vector<float> fphif(fphi.begin(), fphi.end());
   s->dw.trace = (double*)dalloc(sizeof(double) * 4 * s->NF * 10 * N);
   s->dw.flux = (double*)dalloc(sizeof(double) * 40 * N);
   s->dw.prop = (double*)dalloc(sizeof(double) * 4 * N);
@@ -774,7 +783,7 @@ lxw_status lxw3_solver_create_tets(int n_vertices, const double* xyz, int n_tets
   s->dw.diag = (Diag3Block*)dalloc(sizeof(Diag3Block));
   s->jw = (double*)dalloc(sizeof(double) * jw.size());
   s->jphi = (double*)dalloc(sizeof(double) * jphi.size());
-  if (!dgeo || !dnbr || !dcode || !dfphi || !s->dw.trace || !s->dw.flux || !s->dw.prop || !s->dw.smax ||
+  if (!dgeo || !dnbr || !dcode || !dfphi || !dfphif || !s->dw.trace || !s->dw.flux || !s->dw.prop || !s->dw.smax ||
       !s->dw.status || !s->dw.diag || !s->jw || !s->jphi) {
     delete s;
     return fail3(LXW_ERR_NOMEM, std::string(who) + ": device allocation failed");
@@ -783,6 +792,7 @@ lxw_status lxw3_solver_create_tets(int n_vertices, const double* xyz, int n_tets
   if (e == cudaSuccess) e = cudaMemcpy(dnbr, hnbr.data(), sizeof(int) * hnbr.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dcode, code.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dfphi, fphi.data(), sizeof(double) * fphi.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dfphif, fphif.data(), sizeof(float) * fphif.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->jw, jw.data(), sizeof(double) * jw.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->jphi, jphi.data(), sizeof(double) * jphi.size(), cudaMemcpyHostToDevice);
   for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreate(&s->ev[k]);
@@ -797,6 +807,7 @@ lxw_status lxw3_solver_create_tets(int n_vertices, const double* xyz, int n_tets
   s->tm.nbr = dnbr;
   s->tm.code = dcode;
   s->tm.fphi = dfphi;
+  s->tm.fphif = dfphif;
   *out = s;
   return LXW_OK;
 }

@@ -19,13 +19,17 @@ constexpr int k3MaxProj = 125;                     // projection points ((deg + 
 // points (xi fastest), then face k's points at NQ + k NF + t n + u, with u
 // along the first and t along the second tangential axis (x, y, z order),
 // so that the two cells of a face meet its points in the same order.
-struct Tables3 {
-  double qw[k3MaxQ];                   // interior weights, sum 1
-  double fw[k3MaxF];                   // face weights, sum 1
-  double phi[k3MaxPts][k3MaxML];       // basis at every point
-  double dref[3][k3MaxQ][k3MaxML];     // d phi / d(xi, eta, zeta) at the interior points
-  double W[3][k3MaxQ][k3MaxML];        // qw_k sum_m phi_m(x_k) D_d[m][l], D_d[m][l] = (1/8) Int d_d phi_m phi_l
+template <typename T>
+struct Tables3Of {
+  T qw[k3MaxQ];                        // interior weights, sum 1
+  T fw[k3MaxF];                        // face weights, sum 1
+  T phi[k3MaxPts][k3MaxML];            // basis at every point
+  T dref[3][k3MaxQ][k3MaxML];          // d phi / d(xi, eta, zeta) at the interior points
+  T W[3][k3MaxQ][k3MaxML];             // qw_k sum_m phi_m(x_k) D_d[m][l], D_d[m][l] = (1/8) Int d_d phi_m phi_l
+  T phimax[k3MaxML];                   // max over the limiter points of |phi_l| (the FP32 screens' bound)
 };
+using Tables3 = Tables3Of<double>;     // FP64 forms
+using Tables3F = Tables3Of<float>;     // the FP32 CK kernel of the mixed forms
 
 // Uniform box cells: one spacing per axis.
 struct Mesh3 {
@@ -52,10 +56,13 @@ struct Work3 {
 struct Args3 {
   double dt_in, cfl, gamma, eps0, alpha0;
   int shock_limiter, llf_global, want_diag;
+  int ck_fp32;                         // mixed form: FP32 CK and face point loops, FP32 screens in the
+                                       // moment and shock limiters (state, decisions in FP64)
   double* theta_face;                  // [N][E] or null
 };
 
-// Tables of one degree into the device's constant bank (synchronous).
+// Tables of one degree into the device's constant bank, with their FP32
+// copy (synchronous).
 int upload_tables3(int deg, const Tables3& t);
 // One step: reset, moment, ck, face, update, shock (if on), diag (if asked).
 // events (nullable): recorded before each phase and after the last; upto:
@@ -77,13 +84,17 @@ int launch_project3(int deg, int N, int NPJ, double gamma, const double* jw, con
 // order.  Face k's vertices appear in one of 6 orders ("perm").
 constexpr int k3tPerms = 6;
 
-struct Tables3T {
-  double qw[k3MaxQ];                   // interior weights, sum 1
-  double fw[k3MaxF];                   // face weights, sum 1
-  double phi[k3MaxQ][k3MaxML];         // basis at the interior points
-  double dref[3][k3MaxQ][k3MaxML];     // d phi / d(r, s, t) there
-  double W[3][k3MaxQ][k3MaxML];        // qw_k sum_m phi_m(x_k) D_a[m][l], D_a[m][l] = (1/|T0|) Int d_a phi_m phi_l
+template <typename T>
+struct Tables3TOf {
+  T qw[k3MaxQ];                        // interior weights, sum 1
+  T fw[k3MaxF];                        // face weights, sum 1
+  T phi[k3MaxQ][k3MaxML];              // basis at the interior points
+  T dref[3][k3MaxQ][k3MaxML];          // d phi / d(r, s, t) there
+  T W[3][k3MaxQ][k3MaxML];             // qw_k sum_m phi_m(x_k) D_a[m][l], D_a[m][l] = (1/|T0|) Int d_a phi_m phi_l
+  T phimax[k3MaxML];                   // max over the interior and every face table of |phi_l|
 };
+using Tables3T = Tables3TOf<double>;
+using Tables3TF = Tables3TOf<float>;
 
 // Per-cell geometry, structure of arrays.
 constexpr int k3tGeo = 22;             // Ji (9), vol, an (4 x 3)
@@ -96,6 +107,7 @@ struct Mesh3T {
   const int* code;                     // [N]: bits 3k..3k+2 perm of face k, bits 12+2k..12+2k+1 the
                                        //   neighbour's local face
   const double* fphi;                  // [4][6][NF][ML]: basis at the face points (device, read-only)
+  const float* fphif;                  // the same in FP32 (mixed forms)
 };
 
 int upload_tables3t(int deg, const Tables3T& t);

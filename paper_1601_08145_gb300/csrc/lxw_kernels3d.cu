@@ -25,9 +25,18 @@
 namespace lxw {
 namespace {
 
-__constant__ Tables3 c_tab3[2];   // degree 1, degree 2
+__constant__ Tables3 c_tab3[2];    // degree 1, degree 2
+__constant__ Tables3F c_tab3f[2];  // their FP32 copies (the mixed form's CK kernel)
 
 #include "lxw_flux3.cuh"
+
+template <typename T>
+__device__ __forceinline__ const Tables3Of<T>& tab3(int deg);
+template <>
+__device__ __forceinline__ const Tables3Of<double>& tab3<double>(int deg) { return c_tab3[deg - 1]; }
+template <>
+__device__ __forceinline__ const Tables3Of<float>& tab3<float>(int deg) { return c_tab3f[deg - 1]; }
+
 
 __device__ __forceinline__ double step_dt3(const Work3& w, const Mesh3& m, const Args3& a) {
   const double s = __longlong_as_double((long long)*w.smax);
@@ -57,77 +66,46 @@ __global__ void __launch_bounds__(128) k3_moment(const Mesh3 m, const Work3 w, d
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double smax = 0.0;
   if (i < m.N) {
-    const double g = a.gamma, g1 = g - 1.0;
     double* Qi = Q + (size_t)i * 5 * ML;
     double c[5][ML];
 #pragma unroll
     for (int v = 0; v < 5; ++v)
 #pragma unroll
       for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
-    const double pb = c[0][0] > 0.0
-                          ? g1 * (c[4][0] - 0.5 * (c[1][0] * c[1][0] + c[2][0] * c[2][0] + c[3][0] * c[3][0]) / c[0][0])
-                          : -1.0;
-    double th = 1.0;
-    if (!(c[0][0] > 0.0) || !(pb > 0.0)) {
-      // Step 0: a non-positive average: flatten the cell and report it
-      atomicOr(w.status, (unsigned)LXW_ST_NONPOSITIVE);
-      th = 0.0;
-    } else {
-      // Step 1: density
-      const double er = fmin(a.eps0, 0.5 * c[0][0]);
-      double thr = 1.0;
-#pragma unroll 1
-      for (int p = 0; p < NPT; ++p) {
-        double d = 0.0;
+    auto load = [&](int p, double ph[ML]) {
 #pragma unroll
-        for (int l = 1; l < ML; ++l) d = fma(c[0][l], t.phi[p][l], d);
-        const double rm = c[0][0] + d;
-        if (rm < er) thr = fmin(thr, (c[0][0] - er) / (c[0][0] - rm));
-      }
-      // Step 2: pressure of the density-limited state, secant through (0, pbar)
-      const double ep = fmin(a.eps0, 0.5 * pb);
-      th = thr;
-#pragma unroll 1
-      for (int p = 0; p < NPT; ++p) {
-        double q[5];
+      for (int l = 0; l < ML; ++l) ph[l] = t.phi[p][l];
+    };
+    bool screened = false;
+    if (a.ck_fp32 && c[0][0] > 0.0) {   // mixed form: the FP32 screen clears unlimited cells
+      const double pb = (a.gamma - 1.0) * (c[4][0] - 0.5 * (c[1][0] * c[1][0] + c[2][0] * c[2][0] + c[3][0] * c[3][0]) / c[0][0]);
+      if (pb > 0.0) {
+        const Tables3Of<float>& tf = tab3<float>(DEG);
+        float cf[5][ML], S[5], smf;
+        screen_state3<ML>(c, tf.phimax, cf, S);
+        auto loadf = [&](int p, float ph[ML]) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          double d = 0.0;
+          for (int l = 0; l < ML; ++l) ph[l] = tf.phi[p][l];
+        };
+        if (moment_screen3<ML, NPT>(cf, S, (float)a.gamma, (float)fmin(a.eps0, 0.5 * c[0][0]), (float)fmin(a.eps0, 0.5 * pb),
+                                    loadf, smf)) {
+          double qa[5];
 #pragma unroll
-          for (int l = 1; l < ML; ++l) d = fma(c[v][l], t.phi[p][l], d);
-          q[v] = c[v][0] + thr * d;
+          for (int v = 0; v < 5; ++v) qa[v] = c[v][0];
+          smax = fmax((double)smf, speed_of3(a.gamma, qa));
+          screened = true;
         }
-        const double pt = g1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
-        if (pt < ep) th = fmin(th, thr * (pb - ep) / (pb - pt));
       }
-      th = fmax(th, 0.0);
     }
+    bool nonpos = false;
+    const double th = screened ? 1.0 : moment_cell3<ML, NPT>(c, a.gamma, a.eps0, load, smax, nonpos);
+    if (nonpos) atomicOr(w.status, (unsigned)LXW_ST_NONPOSITIVE);
     if (th < 1.0) {
 #pragma unroll
       for (int v = 0; v < 5; ++v)
 #pragma unroll
-        for (int l = 1; l < ML; ++l) {
-          c[v][l] *= th;
-          Qi[v * ML + l] = c[v][l];
-        }
+        for (int l = 1; l < ML; ++l) Qi[v * ML + l] = c[v][l];
       if (a.want_diag) atomicAdd(&w.diag->nmom, 1ull);
-    }
-    // wave speed over the limited state
-    double qa[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) qa[v] = c[v][0];
-    smax = speed_of3(g, qa);
-#pragma unroll 1
-    for (int p = 0; p < NPT; ++p) {
-      double q[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        double acc = 0.0;
-#pragma unroll
-        for (int l = 0; l < ML; ++l) acc = fma(c[v][l], t.phi[p][l], acc);
-        q[v] = acc;
-      }
-      smax = fmax(smax, speed_of3(g, q));
     }
   }
   block_max3(smax, w.smax);
@@ -141,114 +119,128 @@ __global__ void __launch_bounds__(128) k3_moment(const Mesh3 m, const Work3 w, d
 // expansion); F_t = F'(q) q_t, F_tt = F''(q)(q_t, q_t) + F'(q) q_tt, F_T =
 // F + dt/2 F_t + dt^2/6 F_tt at every point; the volume integral is added to
 // the higher moments in place, the face points store q and n_out . F_T.
-template <int DEG, int ML, int N1>
+// T = double: the FP64 form; T = float: the mixed form's FP32 kernel (the
+// state stays FP64 and the volume term is added to it in FP64; the traces
+// are stored in T, the face kernel of the same form reads them in T).
+template <typename T, int DEG, int ML, int N1>
 __global__ void __launch_bounds__(128) k3_ck(const Mesh3 m, const Work3 w, double* __restrict__ Q, const Args3 a) {
   constexpr int NQ = N1 * N1 * N1, NF = N1 * N1, NPT = NQ + 6 * NF;
-  const Tables3& t = c_tab3[DEG - 1];
+  constexpr bool F64 = sizeof(T) == 8;
+  const Tables3Of<T>& t = tab3<T>(DEG);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.N) return;
   const int N = m.N;
-  const double g1 = a.gamma - 1.0;
-  const double dt = step_dt3(w, m, a);
-  const double c1 = 0.5 * dt, c2 = dt * dt / 6.0;
-  const double sd[3] = {2.0 / m.h[0], 2.0 / m.h[1], 2.0 / m.h[2]};
+  const T g1 = opaque(T(a.gamma - 1.0));
+  const double dtd = step_dt3(w, m, a);
+  const T dt = T(dtd);
+  const T c1 = opaque(T(0.5 * dtd)), c2 = opaque(T(dtd * dtd / 6.0));
+  const T sd[3] = {opaque(T(2.0 / m.h[0])), opaque(T(2.0 / m.h[1])), opaque(T(2.0 / m.h[2]))};
+  const T avh[3] = {opaque(T(m.vol / m.h[0])), opaque(T(m.vol / m.h[1])), opaque(T(m.vol / m.h[2]))};
   double* Qi = Q + (size_t)i * 5 * ML;
-  double c[5][ML];
+  // FP32 form: read the coefficients once (a volatile view) and pin the
+  // converted values, so that the compiler keeps (or spills) them instead of
+  // reloading or re-converting the FP64 state at every use (conversions run
+  // on the FP64 pipe)
+  T c[5][ML];
+  const volatile double* Qv = Qi;
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
+    for (int l = 0; l < ML; ++l) {
+      if constexpr (F64) c[v][l] = Qi[v * ML + l];
+      else c[v][l] = opaque(T(Qv[v * ML + l]));
+    }
   // pass 1: Qt
-  double Qt[5][ML];
+  T Qt[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) Qt[v][l] = 0.0;
+    for (int l = 0; l < ML; ++l) Qt[v][l] = T(0);
 #pragma unroll 1
   for (int k = 0; k < NQ; ++k) {
-    double q[5];
+    T q[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double acc = 0.0;
+      T acc = T(0);
 #pragma unroll
-      for (int l = 0; l < ML; ++l) acc = fma(c[v][l], t.phi[k][l], acc);
+      for (int l = 0; l < ML; ++l) acc = fmaT(c[v][l], t.phi[k][l], acc);
       q[v] = acc;
     }
-    const P3 s = make_p3(g1, q);
-    double F[3][5];
-    flux3(s, F);
+    const P3T<T> s = make_p3<T>(g1, q);
+    T F[3][5];
+    flux3<T>(s, F);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const double f0 = sd[0] * F[0][v], f1 = sd[1] * F[1][v], f2 = sd[2] * F[2][v];
+      const T f0 = sd[0] * F[0][v], f1 = sd[1] * F[1][v], f2 = sd[2] * F[2][v];
 #pragma unroll
       for (int l = 0; l < ML; ++l)
         Qt[v][l] -= f0 * t.W[0][k][l] + f1 * t.W[1][k][l] + f2 * t.W[2][k][l];
     }
   }
   // pass 2: Qtt
-  double Qtt[5][ML];
+  T Qtt[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) Qtt[v][l] = 0.0;
+    for (int l = 0; l < ML; ++l) Qtt[v][l] = T(0);
 #pragma unroll 1
   for (int k = 0; k < NQ; ++k) {
-    double q[5], qt[5];
+    T q[5], qt[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double acc = 0.0, d1 = 0.0;
+      T acc = T(0), d1 = T(0);
 #pragma unroll
       for (int l = 0; l < ML; ++l) {
-        acc = fma(c[v][l], t.phi[k][l], acc);
-        d1 = fma(Qt[v][l], t.phi[k][l], d1);
+        acc = fmaT(c[v][l], t.phi[k][l], acc);
+        d1 = fmaT(Qt[v][l], t.phi[k][l], d1);
       }
       q[v] = acc; qt[v] = d1;
     }
-    const P3 s = make_p3(g1, q);
-    double F1[3][5], du[3], dp;
-    flux3_d1(g1, s, qt, F1, du, dp);
+    const P3T<T> s = make_p3<T>(g1, q);
+    T F1[3][5], du[3], dp;
+    flux3_d1<T>(g1, s, qt, F1, du, dp);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const double f0 = sd[0] * F1[0][v], f1 = sd[1] * F1[1][v], f2 = sd[2] * F1[2][v];
+      const T f0 = sd[0] * F1[0][v], f1 = sd[1] * F1[1][v], f2 = sd[2] * F1[2][v];
 #pragma unroll
       for (int l = 0; l < ML; ++l)
         Qtt[v][l] -= f0 * t.W[0][k][l] + f1 * t.W[1][k][l] + f2 * t.W[2][k][l];
     }
   }
   // pass 3: F_T everywhere; volume integral at interior points, traces at face points
-  double Vv[5][ML];
+  T Vv[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) Vv[v][l] = 0.0;
+    for (int l = 0; l < ML; ++l) Vv[v][l] = T(0);
 #pragma unroll 1
   for (int p = 0; p < NPT; ++p) {
-    double q[5], qt[5], qtt[5];
+    T q[5], qt[5], qtt[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double acc = 0.0, d1 = 0.0, d2 = 0.0;
+      T acc = T(0), d1 = T(0), d2 = T(0);
 #pragma unroll
       for (int l = 0; l < ML; ++l) {
-        const double ph = t.phi[p][l];
-        acc = fma(c[v][l], ph, acc);
-        d1 = fma(Qt[v][l], ph, d1);
-        d2 = fma(Qtt[v][l], ph, d2);
+        const T ph = t.phi[p][l];
+        acc = fmaT(c[v][l], ph, acc);
+        d1 = fmaT(Qt[v][l], ph, d1);
+        d2 = fmaT(Qtt[v][l], ph, d2);
       }
       q[v] = acc; qt[v] = d1; qtt[v] = d2;
     }
-    const P3 s = make_p3(g1, q);
-    double F[3][5], FT[3][5];
-    flux3(s, F);
+    const P3T<T> s = make_p3<T>(g1, q);
+    T F[3][5], FT[3][5];
+    flux3<T>(s, F);
     {
-      double F1[3][5], du[3], dp;
-      flux3_d1(g1, s, qt, F1, du, dp);
+      T F1[3][5], du[3], dp;
+      flux3_d1<T>(g1, s, qt, F1, du, dp);
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int v = 0; v < 5; ++v) FT[d][v] = F[d][v] + c1 * F1[d][v];
-      flux3_d2(g1, s, qt, du, dp, F1);
-      double F3[3][5], eu[3], ep;
-      flux3_d1(g1, s, qtt, F3, eu, ep);
+      flux3_d2<T>(g1, s, qt, du, dp, F1);
+      T F3[3][5], eu[3], ep;
+      flux3_d1<T>(g1, s, qtt, F3, eu, ep);
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
@@ -257,27 +249,29 @@ __global__ void __launch_bounds__(128) k3_ck(const Mesh3 m, const Work3 w, doubl
     if (p < NQ) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double f0 = t.qw[p] * sd[0] * FT[0][v], f1 = t.qw[p] * sd[1] * FT[1][v],
-                     f2 = t.qw[p] * sd[2] * FT[2][v];
+        const T f0 = t.qw[p] * sd[0] * FT[0][v], f1 = t.qw[p] * sd[1] * FT[1][v], f2 = t.qw[p] * sd[2] * FT[2][v];
 #pragma unroll
         for (int l = 1; l < ML; ++l)
-          Vv[v][l] = fma(f0, t.dref[0][p][l], fma(f1, t.dref[1][p][l], fma(f2, t.dref[2][p][l], Vv[v][l])));
+          Vv[v][l] = fmaT(f0, t.dref[0][p][l], fmaT(f1, t.dref[1][p][l], fmaT(f2, t.dref[2][p][l], Vv[v][l])));
       }
     } else {
       const int k = (p - NQ) / NF, pe = (p - NQ) - k * NF, d = k >> 1;
-      const double an = (k & 1 ? 1.0 : -1.0) * m.vol / m.h[d];   // outward normal times the face area
-      double* tr = w.trace + ((size_t)(k * NF + pe) * 10) * N + i;
+      const T an = (k & 1) ? avh[d] : -avh[d];   // outward normal times the face area
+      T* tr = reinterpret_cast<T*>(w.trace) + ((size_t)(k * NF + pe) * 10) * N + i;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         tr[(size_t)v * N] = q[v];
-        tr[(size_t)(5 + v) * N] = an * FT[d][v];
+        tr[(size_t)(5 + v) * N] = rn_mul(an, FT[d][v]);
       }
     }
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 1; l < ML; ++l) Qi[v * ML + l] = c[v][l] + dt * Vv[v][l];
+    for (int l = 1; l < ML; ++l) {
+      if constexpr (F64) Qi[v * ML + l] = c[v][l] + dt * Vv[v][l];
+      else Qi[v * ML + l] += dtd * double(Vv[v][l]);
+    }
 }
 
 // ------------------------------------------------------------ k3_face
@@ -287,16 +281,21 @@ __global__ void __launch_bounds__(128) k3_ck(const Mesh3 m, const Work3 w, doubl
 // exact negatives.  Face integral of the higher moments; Steps 4-5: Gamma,
 // the density Lambda shared by the negative faces, the Lax-Friedrichs
 // state, mu over the 63 corners of the box of proposals.
-template <int DEG, int ML, int N1>
+// T is the arithmetic of the point loop (the traces, the LLF values, f^LxW
+// and the face integral: FP32 in the mixed form); the averages, f^LxF and
+// Steps 4-5 are FP64 in both forms.
+template <typename T, int DEG, int ML, int N1>
 __global__ void __launch_bounds__(128) k3_face(const Mesh3 m, const Work3 w, double* __restrict__ Q, const Args3 a) {
   constexpr int NQ = N1 * N1 * N1, NF = N1 * N1;
-  const Tables3& t = c_tab3[DEG - 1];
+  const Tables3Of<T>& t = tab3<T>(DEG);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.N) return;
   const int N = m.N;
   const double g = a.gamma, g1 = g - 1.0;
+  const T gT = T(g);
   const double s = __longlong_as_double((long long)*w.smax);
   const double dt = step_dt3(w, m, a);
+  const T* trb = reinterpret_cast<const T*>(w.trace);
   double* Qi = Q + (size_t)i * 5 * ML;
   double qb[5];
 #pragma unroll
@@ -304,11 +303,11 @@ __global__ void __launch_bounds__(128) k3_face(const Mesh3 m, const Work3 w, dou
   const P3 sb = make_p3(g1, qb);
   double Fb[3][5];
   flux3(sb, Fb);
-  double Ei[5][ML];
+  T Ei[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) Ei[v][l] = 0.0;
+    for (int l = 0; l < ML; ++l) Ei[v][l] = T(0);
   double fW[6][5], fF[6][5];
 #pragma unroll 1
   for (int k = 0; k < 6; ++k) {
@@ -337,16 +336,16 @@ __global__ void __launch_bounds__(128) k3_face(const Mesh3 m, const Work3 w, dou
         fF[k][v] = __fma_rn(-hs, __dsub_rn(qn[v], qb[v]), __dmul_rn(0.5, __dadd_rn(ai, ak)));
       }
     }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) fW[k][v] = 0.0;
+    T fWk[5] = {T(0), T(0), T(0), T(0), T(0)};
+    const T hsT = T(hs), sT = T(s), areaT = T(area);
 #pragma unroll 1
     for (int p = 0; p < NF; ++p) {
-      const double* tr = w.trace + ((size_t)(k * NF + p) * 10) * N + i;
-      double qi[5], Fi[5], qx[5], Fx[5];
+      const T* tr = trb + ((size_t)(k * NF + p) * 10) * N + i;
+      T qi[5], Fi[5], qx[5], Fx[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) { qi[v] = tr[(size_t)v * N]; Fi[v] = tr[(size_t)(5 + v) * N]; }
       if (j >= 0) {
-        const double* tj = w.trace + ((size_t)(kj * NF + p) * 10) * N + j;
+        const T* tj = trb + ((size_t)(kj * NF + p) * 10) * N + j;
 #pragma unroll
         for (int v = 0; v < 5; ++v) { qx[v] = tj[(size_t)v * N]; Fx[v] = -tj[(size_t)(5 + v) * N]; }
       } else if (-1 - j == LXW_BC_REFLECT) {
@@ -360,22 +359,24 @@ __global__ void __launch_bounds__(128) k3_face(const Mesh3 m, const Work3 w, dou
         for (int v = 0; v < 5; ++v) { qx[v] = qi[v]; Fx[v] = Fi[v]; }
       }
       // dissipation speed: the local speed of the two traces, at most s
-      const double hp = a.llf_global ? hs : 0.5 * fmin(s, fmax(lf_speed3(g, qi), lf_speed3(g, qx))) * area;
+      const T hp = a.llf_global ? hsT : T(0.5) * fminT(sT, fmaxT(lf_speed3<T>(gT, qi), lf_speed3<T>(gT, qx))) * areaT;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double fs = __fma_rn(-hp, __dsub_rn(qx[v], qi[v]), __dmul_rn(0.5, __dadd_rn(Fi[v], Fx[v])));
-        fW[k][v] = __fma_rn(t.fw[p], fs, fW[k][v]);
-        const double hw = t.fw[p] * fs;
+        const T fs = rn_fma(-hp, rn_sub(qx[v], qi[v]), rn_mul(T(0.5), rn_add(Fi[v], Fx[v])));
+        fWk[v] = rn_fma(t.fw[p], fs, fWk[v]);
+        const T hw = t.fw[p] * fs;
 #pragma unroll
-        for (int l = 1; l < ML; ++l) Ei[v][l] = fma(hw, t.phi[NQ + k * NF + p][l], Ei[v][l]);
+        for (int l = 1; l < ML; ++l) Ei[v][l] = fmaT(hw, t.phi[NQ + k * NF + p][l], Ei[v][l]);
       }
     }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fW[k][v] = double(fWk[v]);
   }
   const double dta = dt / m.vol;
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 1; l < ML; ++l) Qi[v * ML + l] -= dta * Ei[v][l];
+    for (int l = 1; l < ML; ++l) Qi[v * ML + l] -= dta * double(Ei[v][l]);
 
   // Steps 4-5
   double Gam0 = m.vol / dt * qb[0];
@@ -417,8 +418,23 @@ __global__ void __launch_bounds__(128) k3_face(const Mesh3 m, const Work3 w, dou
   } else {
     const double kap = fmin(a.eps0, 0.5 * pl) / g1;
     const double h0 = ql[0] * ql[4] - 0.5 * (ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3]) - kap * ql[0];
+    // every corner ql + dd has |dd_v| <= D_v = sum_k |dq_kv|, so h(ql + dd) >= h0
+    // - (|rho| D_E + |E - kappa| D_rho + |m| . D_m) - (D_rho D_E + |D_m|^2 / 2):
+    // when that bound (and rho - D_rho) clears zero by more than the rounding,
+    // every corner is positive and every mu is 1 without the corner loop
+    double D[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) D[v] += fabs(dq[k][v]);
+    const double lin = fabs(ql[0]) * D[4] + fabs(ql[4] - kap) * D[0] + fabs(ql[1]) * D[1] + fabs(ql[2]) * D[2] +
+                       fabs(ql[3]) * D[3];
+    const double quad = D[0] * D[4] + 0.5 * (D[1] * D[1] + D[2] * D[2] + D[3] * D[3]);
+    const double scale = fabs(ql[0] * ql[4]) + 0.5 * (ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3]) +
+                         fabs(kap * ql[0]) + lin + quad;
+    const bool all_pos = ql[0] - D[0] > 1e-12 * ql[0] && h0 - lin - quad > 1e-12 * scale;
 #pragma unroll 1
-    for (int cm = 1; cm < 64; ++cm) {
+    for (int cm = all_pos ? 64 : 1; cm < 64; ++cm) {
       double dd[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int k = 0; k < 6; ++k)
@@ -533,6 +549,16 @@ __global__ void __launch_bounds__(128) k3_shock(const Mesh3 m, const Work3 w, do
       prim(qn, wn);
 #pragma unroll
       for (int v = 0; v < 5; ++v) { Mx[v] = fmax(Mx[v], wn[v]); Mn[v] = fmin(Mn[v], wn[v]); }
+    }
+    if (a.ck_fp32) {   // mixed form: the FP32 screen clears cells well inside the bounds
+      const Tables3Of<float>& tf = tab3<float>(DEG);
+      float cf[5][ML], S[5];
+      screen_state3<ML>(c, tf.phimax, cf, S);
+      auto loadf = [&](int p, float ph[ML]) {
+#pragma unroll
+        for (int l = 0; l < ML; ++l) ph[l] = tf.phi[p][l];
+      };
+      if (shock_screen3<ML, NPT>(cf, S, (float)a.gamma, Mx, Mn, loadf)) return;
     }
     double hx[5], hn[5];
 #pragma unroll
@@ -655,10 +681,12 @@ int step3_impl(const Mesh3& m, const Work3& w, double* Q, const Args3& a, cudaSt
   k3_moment<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
   mark();
   if (upto < 2) return ok();
-  k3_ck<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  if (a.ck_fp32) k3_ck<float, DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  else k3_ck<double, DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
   mark();
   if (upto < 3) return ok();
-  k3_face<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  if (a.ck_fp32) k3_face<float, DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  else k3_face<double, DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
   mark();
   if (upto < 4) return ok();
   k3_update<ML><<<grid, block, 0, st>>>(m, w, Q, a);
@@ -674,7 +702,13 @@ int step3_impl(const Mesh3& m, const Work3& w, double* Q, const Args3& a, cudaSt
 
 int upload_tables3(int deg, const Tables3& t) {
   if (deg < 1 || deg > 2) return -1;
-  return cudaMemcpyToSymbol(c_tab3, &t, sizeof(Tables3), sizeof(Tables3) * (deg - 1)) == cudaSuccess ? 0 : -1;
+  Tables3F f;
+  const double* src = &t.qw[0];
+  float* dst = &f.qw[0];
+  static_assert(sizeof(Tables3) == 2 * sizeof(Tables3F), "tables hold doubles only");
+  for (size_t k = 0; k < sizeof(Tables3) / sizeof(double); ++k) dst[k] = (float)src[k];
+  if (cudaMemcpyToSymbol(c_tab3, &t, sizeof(Tables3), sizeof(Tables3) * (deg - 1)) != cudaSuccess) return -1;
+  return cudaMemcpyToSymbol(c_tab3f, &f, sizeof(Tables3F), sizeof(Tables3F) * (deg - 1)) == cudaSuccess ? 0 : -1;
 }
 
 int launch_step3(int deg, const Mesh3& m, const Work3& w, double* Q, const Args3& a, void* stream, int block,

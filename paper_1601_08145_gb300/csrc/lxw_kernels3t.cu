@@ -28,9 +28,38 @@
 namespace lxw {
 namespace {
 
-__constant__ Tables3T c_tab3t[2];   // degree 1, degree 2
+__constant__ Tables3T c_tab3t[2];    // degree 1, degree 2
+__constant__ Tables3TF c_tab3tf[2];  // their FP32 copies (the mixed form's CK kernel)
 
 #include "lxw_flux3.cuh"
+
+template <typename T>
+__device__ __forceinline__ const Tables3TOf<T>& tab3t(int deg);
+template <>
+__device__ __forceinline__ const Tables3TOf<double>& tab3t<double>(int deg) { return c_tab3t[deg - 1]; }
+template <>
+__device__ __forceinline__ const Tables3TOf<float>& tab3t<float>(int deg) { return c_tab3tf[deg - 1]; }
+
+template <typename T>
+__device__ __forceinline__ const T* face_tables(const Mesh3T& m);
+template <>
+__device__ __forceinline__ const double* face_tables<double>(const Mesh3T& m) { return m.fphi; }
+template <>
+__device__ __forceinline__ const float* face_tables<float>(const Mesh3T& m) { return m.fphif; }
+
+// FP32 basis values at limiter point p (the mixed forms' screens)
+template <int ML, int NQ, int NF>
+__device__ __forceinline__ void load_phif(const Tables3TF& t, const Mesh3T& m, int code, int p, float ph[ML]) {
+  if (p < NQ) {
+#pragma unroll
+    for (int l = 0; l < ML; ++l) ph[l] = t.phi[p][l];
+  } else {
+    const int k = (p - NQ) / NF, pe = p - NQ - k * NF;
+    const float* f = m.fphif + (size_t)((k * k3tPerms + ((code >> (3 * k)) & 7)) * NF + pe) * ML;
+#pragma unroll
+    for (int l = 0; l < ML; ++l) ph[l] = __ldg(f + l);
+  }
+}
 
 __device__ __forceinline__ double step_dt3t(const Work3& w, const Mesh3T& m, const Args3& a) {
   const double s = __longlong_as_double((long long)*w.smax);
@@ -55,16 +84,18 @@ __device__ __forceinline__ void load_phi(const Tables3T& t, const Mesh3T& m, int
 }
 
 // momentum mirror in the plane of unit normal nh (a reflective wall)
-__device__ __forceinline__ void mirror3(const double nh[3], double q[5]) {
-  const double mn = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
+template <typename T>
+__device__ __forceinline__ void mirror3(const T nh[3], T q[5]) {
+  const T mn = q[1] * nh[0] + q[2] * nh[1] + q[3] * nh[2];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) q[1 + d] -= 2.0 * mn * nh[d];
+  for (int d = 0; d < 3; ++d) q[1 + d] -= T(2) * mn * nh[d];
 }
 
 // an . F[.][v] with sign-symmetric rounding: both cells of a face use
 // exactly negated normals and must get exactly negated products
-__device__ __forceinline__ double ndot(const double an[3], const double F[3][5], int v) {
-  return __fma_rn(an[2], F[2][v], __fma_rn(an[1], F[1][v], __dmul_rn(an[0], F[0][v])));
+template <typename T>
+__device__ __forceinline__ T ndot(const T an[3], const T F[3][5], int v) {
+  return rn_fma(an[2], F[2][v], rn_fma(an[1], F[1][v], rn_mul(an[0], F[0][v])));
 }
 
 __device__ __forceinline__ double face_area(const double an[3]) {
@@ -95,87 +126,49 @@ __global__ void __launch_bounds__(128) k3t_moment(const Mesh3T m, const Work3 w,
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double smax = 0.0;
   if (i < m.N) {
-    const double g = a.gamma, g1 = g - 1.0;
-    const int code = m.code[i];
     double* Qi = Q + (size_t)i * 5 * ML;
     double c[5][ML];
 #pragma unroll
     for (int v = 0; v < 5; ++v)
 #pragma unroll
       for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
-    const double pb = c[0][0] > 0.0
-                          ? g1 * (c[4][0] - 0.5 * (c[1][0] * c[1][0] + c[2][0] * c[2][0] + c[3][0] * c[3][0]) / c[0][0])
-                          : -1.0;
-    double th = 1.0;
-    if (!(c[0][0] > 0.0) || !(pb > 0.0)) {
-      atomicOr(w.status, (unsigned)LXW_ST_NONPOSITIVE);
-      th = 0.0;
-    } else {
-      const double er = fmin(a.eps0, 0.5 * c[0][0]);
-      double thr = 1.0;
-#pragma unroll 1
-      for (int p = 0; p < NPT; ++p) {
-        double ph[ML];
-        load_phi<ML, NQ, NF>(t, m, code, p, ph);
-        double d = 0.0;
+    const int code = m.code[i];
+    auto load = [&](int p, double ph[ML]) { load_phi<ML, NQ, NF>(t, m, code, p, ph); };
+    bool screened = false;
+    if (a.ck_fp32 && c[0][0] > 0.0) {   // mixed form: the FP32 screen clears unlimited cells
+      const double pb = (a.gamma - 1.0) * (c[4][0] - 0.5 * (c[1][0] * c[1][0] + c[2][0] * c[2][0] + c[3][0] * c[3][0]) / c[0][0]);
+      if (pb > 0.0) {
+        const Tables3TF& tf = tab3t<float>(DEG);
+        float cf[5][ML], S[5], smf;
+        screen_state3<ML>(c, tf.phimax, cf, S);
+        auto loadf = [&](int p, float ph[ML]) { load_phif<ML, NQ, NF>(tf, m, code, p, ph); };
+        if (moment_screen3<ML, NPT>(cf, S, (float)a.gamma, (float)fmin(a.eps0, 0.5 * c[0][0]), (float)fmin(a.eps0, 0.5 * pb),
+                                    loadf, smf)) {
+          double qa[5];
 #pragma unroll
-        for (int l = 1; l < ML; ++l) d = fma(c[0][l], ph[l], d);
-        const double rm = c[0][0] + d;
-        if (rm < er) thr = fmin(thr, (c[0][0] - er) / (c[0][0] - rm));
-      }
-      const double ep = fmin(a.eps0, 0.5 * pb);
-      th = thr;
-#pragma unroll 1
-      for (int p = 0; p < NPT; ++p) {
-        double ph[ML];
-        load_phi<ML, NQ, NF>(t, m, code, p, ph);
-        double q[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          double d = 0.0;
-#pragma unroll
-          for (int l = 1; l < ML; ++l) d = fma(c[v][l], ph[l], d);
-          q[v] = c[v][0] + thr * d;
+          for (int v = 0; v < 5; ++v) qa[v] = c[v][0];
+          smax = fmax((double)smf, speed_of3(a.gamma, qa));
+          screened = true;
         }
-        const double pt = g1 * (q[4] - 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0]);
-        if (pt < ep) th = fmin(th, thr * (pb - ep) / (pb - pt));
       }
-      th = fmax(th, 0.0);
     }
+    bool nonpos = false;
+    const double th = screened ? 1.0 : moment_cell3<ML, NPT>(c, a.gamma, a.eps0, load, smax, nonpos);
+    if (nonpos) atomicOr(w.status, (unsigned)LXW_ST_NONPOSITIVE);
     if (th < 1.0) {
 #pragma unroll
       for (int v = 0; v < 5; ++v)
 #pragma unroll
-        for (int l = 1; l < ML; ++l) {
-          c[v][l] *= th;
-          Qi[v * ML + l] = c[v][l];
-        }
+        for (int l = 1; l < ML; ++l) Qi[v * ML + l] = c[v][l];
       if (a.want_diag) atomicAdd(&w.diag->nmom, 1ull);
-    }
-    double qa[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) qa[v] = c[v][0];
-    smax = speed_of3(g, qa);
-#pragma unroll 1
-    for (int p = 0; p < NPT; ++p) {
-      double ph[ML];
-      load_phi<ML, NQ, NF>(t, m, code, p, ph);
-      double q[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        double acc = 0.0;
-#pragma unroll
-        for (int l = 0; l < ML; ++l) acc = fma(c[v][l], ph[l], acc);
-        q[v] = acc;
-      }
-      smax = fmax(smax, speed_of3(g, q));
     }
   }
   block_max3(smax, w.smax);
 }
 
 // contravariant flux G_a[v] = sum_d Ji[a][d] F_d[v]
-__device__ __forceinline__ void contra3(const double Ji[9], const double F[3][5], double G[3][5]) {
+template <typename T>
+__device__ __forceinline__ void contra3(const T Ji[9], const T F[3][5], T G[3][5]) {
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -183,34 +176,33 @@ __device__ __forceinline__ void contra3(const double Ji[9], const double F[3][5]
 }
 
 // q and F_T = F + dt/2 F_t + dt^2/6 F_tt at a point from the basis values
-template <int ML>
-__device__ __forceinline__ void ft_point3t(double g1, double c1, double c2, const double ph[ML], const double c[5][ML],
-                                           const double Qt[5][ML], const double Qtt[5][ML], double q[5],
-                                           double FT[3][5]) {
-  double qt[5], qtt[5];
+template <typename T, int ML>
+__device__ __forceinline__ void ft_point3t(T g1, T c1, T c2, const T ph[ML], const T c[5][ML], const T Qt[5][ML],
+                                           const T Qtt[5][ML], T q[5], T FT[3][5]) {
+  T qt[5], qtt[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    double acc = 0.0, d1 = 0.0, d2 = 0.0;
+    T acc = T(0), d1 = T(0), d2 = T(0);
 #pragma unroll
     for (int l = 0; l < ML; ++l) {
-      acc = fma(c[v][l], ph[l], acc);
-      d1 = fma(Qt[v][l], ph[l], d1);
-      d2 = fma(Qtt[v][l], ph[l], d2);
+      acc = fmaT(c[v][l], ph[l], acc);
+      d1 = fmaT(Qt[v][l], ph[l], d1);
+      d2 = fmaT(Qtt[v][l], ph[l], d2);
     }
     q[v] = acc; qt[v] = d1; qtt[v] = d2;
   }
-  const P3 s = make_p3(g1, q);
-  double F[3][5];
-  flux3(s, F);
-  double F1[3][5], du[3], dp;
-  flux3_d1(g1, s, qt, F1, du, dp);
+  const P3T<T> s = make_p3<T>(g1, q);
+  T F[3][5];
+  flux3<T>(s, F);
+  T F1[3][5], du[3], dp;
+  flux3_d1<T>(g1, s, qt, F1, du, dp);
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
     for (int v = 0; v < 5; ++v) FT[d][v] = F[d][v] + c1 * F1[d][v];
-  flux3_d2(g1, s, qt, du, dp, F1);
-  double F3[3][5], eu[3], ep;
-  flux3_d1(g1, s, qtt, F3, eu, ep);
+  flux3_d2<T>(g1, s, qt, du, dp, F1);
+  T F3[3][5], eu[3], ep;
+  flux3_d1<T>(g1, s, qtt, F3, eu, ep);
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
@@ -222,73 +214,86 @@ __device__ __forceinline__ void ft_point3t(double g1, double c1, double c2, cons
 // with F_t, both through W_a applied to G_a; F_T at the interior points
 // feeds the volume integral (1/|K|) Int F_T . grad phi_l = sum_k qw_k G_a
 // d_a phi_l, the face points store q and an_k . F_T in the trace array.
-template <int DEG, int ML, int N1>
+// T = double: the FP64 form; T = float: the mixed form's FP32 kernel (state
+// and volume update in FP64; the traces are stored in T, and the face
+// kernel of the same form reads them in T).
+template <typename T, int DEG, int ML, int N1>
 __global__ void __launch_bounds__(128) k3t_ck(const Mesh3T m, const Work3 w, double* __restrict__ Q, const Args3 a) {
   constexpr int NQ = N1 * N1 * N1, NF = N1 * N1;
-  const Tables3T& t = c_tab3t[DEG - 1];
+  constexpr bool F64 = sizeof(T) == 8;
+  const Tables3TOf<T>& t = tab3t<T>(DEG);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.N) return;
   const int N = m.N;
-  const double g1 = a.gamma - 1.0;
-  const double dt = step_dt3t(w, m, a);
-  const double c1 = 0.5 * dt, c2 = dt * dt / 6.0;
-  double Ji[9];
+  const T g1 = opaque(T(a.gamma - 1.0));
+  const double dtd = step_dt3t(w, m, a);
+  const T dt = T(dtd);
+  const T c1 = opaque(T(0.5 * dtd)), c2 = opaque(T(dtd * dtd / 6.0));
+  T Ji[9];
 #pragma unroll
-  for (int e = 0; e < 9; ++e) Ji[e] = geo(m, e, i);
+  for (int e = 0; e < 9; ++e) Ji[e] = opaque(T(geo(m, e, i)));
   double* Qi = Q + (size_t)i * 5 * ML;
-  double c[5][ML];
+  // FP32 form: read the coefficients once (a volatile view) and pin the
+  // converted values, so that the compiler keeps (or spills) them instead of
+  // reloading or re-converting the FP64 state at every use (conversions run
+  // on the FP64 pipe)
+  T c[5][ML];
+  const volatile double* Qv = Qi;
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
+    for (int l = 0; l < ML; ++l) {
+      if constexpr (F64) c[v][l] = Qi[v * ML + l];
+      else c[v][l] = opaque(T(Qv[v * ML + l]));
+    }
   // pass 1: Qt
-  double Qt[5][ML];
+  T Qt[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) Qt[v][l] = 0.0;
+    for (int l = 0; l < ML; ++l) Qt[v][l] = T(0);
 #pragma unroll 1
   for (int k = 0; k < NQ; ++k) {
-    double q[5];
+    T q[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double acc = 0.0;
+      T acc = T(0);
 #pragma unroll
-      for (int l = 0; l < ML; ++l) acc = fma(c[v][l], t.phi[k][l], acc);
+      for (int l = 0; l < ML; ++l) acc = fmaT(c[v][l], t.phi[k][l], acc);
       q[v] = acc;
     }
-    const P3 s = make_p3(g1, q);
-    double F[3][5], G[3][5];
-    flux3(s, F);
-    contra3(Ji, F, G);
+    const P3T<T> s = make_p3<T>(g1, q);
+    T F[3][5], G[3][5];
+    flux3<T>(s, F);
+    contra3<T>(Ji, F, G);
 #pragma unroll
     for (int v = 0; v < 5; ++v)
 #pragma unroll
       for (int l = 0; l < ML; ++l) Qt[v][l] -= G[0][v] * t.W[0][k][l] + G[1][v] * t.W[1][k][l] + G[2][v] * t.W[2][k][l];
   }
   // pass 2: Qtt
-  double Qtt[5][ML];
+  T Qtt[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) Qtt[v][l] = 0.0;
+    for (int l = 0; l < ML; ++l) Qtt[v][l] = T(0);
 #pragma unroll 1
   for (int k = 0; k < NQ; ++k) {
-    double q[5], qt[5];
+    T q[5], qt[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double acc = 0.0, d1 = 0.0;
+      T acc = T(0), d1 = T(0);
 #pragma unroll
       for (int l = 0; l < ML; ++l) {
-        acc = fma(c[v][l], t.phi[k][l], acc);
-        d1 = fma(Qt[v][l], t.phi[k][l], d1);
+        acc = fmaT(c[v][l], t.phi[k][l], acc);
+        d1 = fmaT(Qt[v][l], t.phi[k][l], d1);
       }
       q[v] = acc; qt[v] = d1;
     }
-    const P3 s = make_p3(g1, q);
-    double F1[3][5], G[3][5], du[3], dp;
-    flux3_d1(g1, s, qt, F1, du, dp);
-    contra3(Ji, F1, G);
+    const P3T<T> s = make_p3<T>(g1, q);
+    T F1[3][5], G[3][5], du[3], dp;
+    flux3_d1<T>(g1, s, qt, F1, du, dp);
+    contra3<T>(Ji, F1, G);
 #pragma unroll
     for (int v = 0; v < 5; ++v)
 #pragma unroll
@@ -296,50 +301,54 @@ __global__ void __launch_bounds__(128) k3t_ck(const Mesh3T m, const Work3 w, dou
         Qtt[v][l] -= G[0][v] * t.W[0][k][l] + G[1][v] * t.W[1][k][l] + G[2][v] * t.W[2][k][l];
   }
   // pass 3a: F_T at the interior points -> volume integral of the higher moments
-  double Vv[5][ML];
+  T Vv[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) Vv[v][l] = 0.0;
+    for (int l = 0; l < ML; ++l) Vv[v][l] = T(0);
 #pragma unroll 1
   for (int p = 0; p < NQ; ++p) {
-    double ph[ML], q[5], FT[3][5], G[3][5];
+    T ph[ML], q[5], FT[3][5], G[3][5];
 #pragma unroll
     for (int l = 0; l < ML; ++l) ph[l] = t.phi[p][l];
-    ft_point3t<ML>(g1, c1, c2, ph, c, Qt, Qtt, q, FT);
-    contra3(Ji, FT, G);
+    ft_point3t<T, ML>(g1, c1, c2, ph, c, Qt, Qtt, q, FT);
+    contra3<T>(Ji, FT, G);
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const double f0 = t.qw[p] * G[0][v], f1 = t.qw[p] * G[1][v], f2 = t.qw[p] * G[2][v];
+      const T f0 = t.qw[p] * G[0][v], f1 = t.qw[p] * G[1][v], f2 = t.qw[p] * G[2][v];
 #pragma unroll
       for (int l = 1; l < ML; ++l)
-        Vv[v][l] = fma(f0, t.dref[0][p][l], fma(f1, t.dref[1][p][l], fma(f2, t.dref[2][p][l], Vv[v][l])));
+        Vv[v][l] = fmaT(f0, t.dref[0][p][l], fmaT(f1, t.dref[1][p][l], fmaT(f2, t.dref[2][p][l], Vv[v][l])));
     }
   }
   // pass 3b: traces at the face points, in the face's canonical point order
   const int code = m.code[i];
+  const T* ftab = face_tables<T>(m);
 #pragma unroll 1
   for (int k = 0; k < 4; ++k) {
-    const double an[3] = {geo(m, 10 + 3 * k, i), geo(m, 11 + 3 * k, i), geo(m, 12 + 3 * k, i)};
-    const double* fk = m.fphi + (size_t)((k * k3tPerms + ((code >> (3 * k)) & 7)) * NF) * ML;
+    const T an[3] = {T(geo(m, 10 + 3 * k, i)), T(geo(m, 11 + 3 * k, i)), T(geo(m, 12 + 3 * k, i))};
+    const T* fk = ftab + (size_t)((k * k3tPerms + ((code >> (3 * k)) & 7)) * NF) * ML;
 #pragma unroll 1
     for (int p = 0; p < NF; ++p) {
-      double ph[ML], q[5], FT[3][5];
+      T ph[ML], q[5], FT[3][5];
 #pragma unroll
       for (int l = 0; l < ML; ++l) ph[l] = __ldg(fk + p * ML + l);
-      ft_point3t<ML>(g1, c1, c2, ph, c, Qt, Qtt, q, FT);
-      double* tr = w.trace + ((size_t)(k * NF + p) * 10) * N + i;
+      ft_point3t<T, ML>(g1, c1, c2, ph, c, Qt, Qtt, q, FT);
+      T* tr = reinterpret_cast<T*>(w.trace) + ((size_t)(k * NF + p) * 10) * N + i;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         tr[(size_t)v * N] = q[v];
-        tr[(size_t)(5 + v) * N] = ndot(an, FT, v);
+        tr[(size_t)(5 + v) * N] = ndot<T>(an, FT, v);
       }
     }
   }
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 1; l < ML; ++l) Qi[v * ML + l] = c[v][l] + dt * Vv[v][l];
+    for (int l = 1; l < ML; ++l) {
+      if constexpr (F64) Qi[v * ML + l] = c[v][l] + dt * Vv[v][l];
+      else Qi[v * ML + l] += dtd * double(Vv[v][l]);
+    }
 }
 
 // ------------------------------------------------------------ k3t_face
@@ -349,19 +358,24 @@ __global__ void __launch_bounds__(128) k3t_ck(const Mesh3T m, const Work3 w, dou
 // f^LxF are exact negatives.  Face integral of the higher moments; Steps
 // 4-5: Gamma, the density Lambda shared by the negative faces, the
 // Lax-Friedrichs state, mu over the 15 corners of the box of proposals.
-template <int DEG, int ML, int N1>
+// T is the arithmetic of the point loop (FP32 in the mixed form); the
+// averages, f^LxF and Steps 4-5 are FP64 in both forms.
+template <typename T, int DEG, int ML, int N1>
 __global__ void __launch_bounds__(128) k3t_face(const Mesh3T m, const Work3 w, double* __restrict__ Q,
                                                 const Args3 a) {
   constexpr int NF = N1 * N1;
-  const Tables3T& t = c_tab3t[DEG - 1];
+  const Tables3TOf<T>& t = tab3t<T>(DEG);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.N) return;
   const int N = m.N;
   const double g = a.gamma, g1 = g - 1.0;
+  const T gT = T(g);
   const double s = __longlong_as_double((long long)*w.smax);
   const double dt = step_dt3t(w, m, a);
   const double vol = geo(m, 9, i);
   const int code = m.code[i];
+  const T* trb = reinterpret_cast<const T*>(w.trace);
+  const T* ftab = face_tables<T>(m);
   double* Qi = Q + (size_t)i * 5 * ML;
   double qb[5];
 #pragma unroll
@@ -369,11 +383,11 @@ __global__ void __launch_bounds__(128) k3t_face(const Mesh3T m, const Work3 w, d
   const P3 sb = make_p3(g1, qb);
   double Fb[3][5];
   flux3(sb, Fb);
-  double Ei[5][ML];
+  T Ei[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 0; l < ML; ++l) Ei[v][l] = 0.0;
+    for (int l = 0; l < ML; ++l) Ei[v][l] = T(0);
   double fW[4][5], fF[4][5];
 #pragma unroll 1
   for (int k = 0; k < 4; ++k) {
@@ -391,7 +405,7 @@ __global__ void __launch_bounds__(128) k3t_face(const Mesh3T m, const Work3 w, d
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) qn[v] = qb[v];
-      if (wall) mirror3(nh, qn);
+      if (wall) mirror3<double>(nh, qn);
     }
     {
       const P3 sn = make_p3(g1, qn);
@@ -399,54 +413,57 @@ __global__ void __launch_bounds__(128) k3t_face(const Mesh3T m, const Work3 w, d
       flux3(sn, Fn);
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double ai = ndot(an, Fb, v), ak = ndot(an, Fn, v);
+        const double ai = ndot<double>(an, Fb, v), ak = ndot<double>(an, Fn, v);
         fF[k][v] = __fma_rn(-hs, __dsub_rn(qn[v], qb[v]), __dmul_rn(0.5, __dadd_rn(ai, ak)));
       }
     }
-#pragma unroll
-    for (int v = 0; v < 5; ++v) fW[k][v] = 0.0;
-    const double* fk = m.fphi + (size_t)((k * k3tPerms + ((code >> (3 * k)) & 7)) * NF) * ML;
+    T fWk[5] = {T(0), T(0), T(0), T(0), T(0)};
+    const T hsT = T(hs), sT = T(s), areaT = T(area);
+    const T nhT[3] = {T(nh[0]), T(nh[1]), T(nh[2])};
+    const T* fk = ftab + (size_t)((k * k3tPerms + ((code >> (3 * k)) & 7)) * NF) * ML;
 #pragma unroll 1
     for (int p = 0; p < NF; ++p) {
-      const double* tr = w.trace + ((size_t)(k * NF + p) * 10) * N + i;
-      double qi[5], Fi[5], qx[5], Fx[5];
+      const T* tr = trb + ((size_t)(k * NF + p) * 10) * N + i;
+      T qi[5], Fi[5], qx[5], Fx[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) { qi[v] = tr[(size_t)v * N]; Fi[v] = tr[(size_t)(5 + v) * N]; }
       if (j >= 0) {
-        const double* tj = w.trace + ((size_t)(kj * NF + p) * 10) * N + j;
+        const T* tj = trb + ((size_t)(kj * NF + p) * 10) * N + j;
 #pragma unroll
         for (int v = 0; v < 5; ++v) { qx[v] = tj[(size_t)v * N]; Fx[v] = -tj[(size_t)(5 + v) * N]; }
       } else if (wall) {
         // exterior R q, and n . F_T(R q) = -R (n . F_T(q)) (the Euler flux's mirror symmetry)
 #pragma unroll
         for (int v = 0; v < 5; ++v) { qx[v] = qi[v]; Fx[v] = Fi[v]; }
-        mirror3(nh, qx);
-        mirror3(nh, Fx);
+        mirror3<T>(nhT, qx);
+        mirror3<T>(nhT, Fx);
 #pragma unroll
         for (int v = 0; v < 5; ++v) Fx[v] = -Fx[v];
       } else {
 #pragma unroll
         for (int v = 0; v < 5; ++v) { qx[v] = qi[v]; Fx[v] = Fi[v]; }
       }
-      const double hp = a.llf_global ? hs : 0.5 * fmin(s, fmax(lf_speed3(g, qi), lf_speed3(g, qx))) * area;
-      double ph[ML];
+      const T hp = a.llf_global ? hsT : T(0.5) * fminT(sT, fmaxT(lf_speed3<T>(gT, qi), lf_speed3<T>(gT, qx))) * areaT;
+      T ph[ML];
 #pragma unroll
       for (int l = 1; l < ML; ++l) ph[l] = __ldg(fk + p * ML + l);
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double fs = __fma_rn(-hp, __dsub_rn(qx[v], qi[v]), __dmul_rn(0.5, __dadd_rn(Fi[v], Fx[v])));
-        fW[k][v] = __fma_rn(t.fw[p], fs, fW[k][v]);
-        const double hw = t.fw[p] * fs;
+        const T fs = rn_fma(-hp, rn_sub(qx[v], qi[v]), rn_mul(T(0.5), rn_add(Fi[v], Fx[v])));
+        fWk[v] = rn_fma(t.fw[p], fs, fWk[v]);
+        const T hw = t.fw[p] * fs;
 #pragma unroll
-        for (int l = 1; l < ML; ++l) Ei[v][l] = fma(hw, ph[l], Ei[v][l]);
+        for (int l = 1; l < ML; ++l) Ei[v][l] = fmaT(hw, ph[l], Ei[v][l]);
       }
     }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) fW[k][v] = double(fWk[v]);
   }
   const double dta = dt / vol;
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
-    for (int l = 1; l < ML; ++l) Qi[v * ML + l] -= dta * Ei[v][l];
+    for (int l = 1; l < ML; ++l) Qi[v * ML + l] -= dta * double(Ei[v][l]);
 
   // Steps 4-5
   double Gam0 = vol / dt * qb[0];
@@ -486,8 +503,23 @@ __global__ void __launch_bounds__(128) k3t_face(const Mesh3T m, const Work3 w, d
   } else {
     const double kap = fmin(a.eps0, 0.5 * pl) / g1;
     const double h0 = ql[0] * ql[4] - 0.5 * (ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3]) - kap * ql[0];
+    // every corner ql + dd has |dd_v| <= D_v = sum_k |dq_kv|, so h(ql + dd) >= h0
+    // - (|rho| D_E + |E - kappa| D_rho + |m| . D_m) - (D_rho D_E + |D_m|^2 / 2):
+    // when that bound (and rho - D_rho) clears zero by more than the rounding,
+    // every corner is positive and every mu is 1 without the corner loop
+    double D[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) D[v] += fabs(dq[k][v]);
+    const double lin = fabs(ql[0]) * D[4] + fabs(ql[4] - kap) * D[0] + fabs(ql[1]) * D[1] + fabs(ql[2]) * D[2] +
+                       fabs(ql[3]) * D[3];
+    const double quad = D[0] * D[4] + 0.5 * (D[1] * D[1] + D[2] * D[2] + D[3] * D[3]);
+    const double scale = fabs(ql[0] * ql[4]) + 0.5 * (ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3]) +
+                         fabs(kap * ql[0]) + lin + quad;
+    const bool all_pos = ql[0] - D[0] > 1e-12 * ql[0] && h0 - lin - quad > 1e-12 * scale;
 #pragma unroll 1
-    for (int cm = 1; cm < 16; ++cm) {
+    for (int cm = all_pos ? 16 : 1; cm < 16; ++cm) {
       double dd[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int k = 0; k < 4; ++k)
@@ -602,13 +634,20 @@ __global__ void __launch_bounds__(128) k3t_shock(const Mesh3T m, const Work3 w, 
           const double an[3] = {geo(m, 10 + 3 * k, i), geo(m, 11 + 3 * k, i), geo(m, 12 + 3 * k, i)};
           const double area = face_area(an);
           const double nh[3] = {an[0] / area, an[1] / area, an[2] / area};
-          mirror3(nh, qn);
+          mirror3<double>(nh, qn);
         }
       }
       if (!(qn[0] > 0.0)) continue;
       prim(qn, wn);
 #pragma unroll
       for (int v = 0; v < 5; ++v) { Mx[v] = fmax(Mx[v], wn[v]); Mn[v] = fmin(Mn[v], wn[v]); }
+    }
+    if (a.ck_fp32) {   // mixed form: the FP32 screen clears cells well inside the bounds
+      const Tables3TF& tf = tab3t<float>(DEG);
+      float cf[5][ML], S[5];
+      screen_state3<ML>(c, tf.phimax, cf, S);
+      auto loadf = [&](int p, float ph[ML]) { load_phif<ML, NQ, NF>(tf, m, code, p, ph); };
+      if (shock_screen3<ML, NPT>(cf, S, (float)a.gamma, Mx, Mn, loadf)) return;
     }
     double hx[5], hn[5];
 #pragma unroll
@@ -706,10 +745,12 @@ int step3t_impl(const Mesh3T& m, const Work3& w, double* Q, const Args3& a, cuda
   k3t_moment<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
   mark();
   if (upto < 2) return ok();
-  k3t_ck<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  if (a.ck_fp32) k3t_ck<float, DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  else k3t_ck<double, DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
   mark();
   if (upto < 3) return ok();
-  k3t_face<DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  if (a.ck_fp32) k3t_face<float, DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
+  else k3t_face<double, DEG, ML, N1><<<grid, block, 0, st>>>(m, w, Q, a);
   mark();
   if (upto < 4) return ok();
   k3t_update<ML><<<grid, block, 0, st>>>(m, w, Q, a);
@@ -725,7 +766,13 @@ int step3t_impl(const Mesh3T& m, const Work3& w, double* Q, const Args3& a, cuda
 
 int upload_tables3t(int deg, const Tables3T& t) {
   if (deg < 1 || deg > 2) return -1;
-  return cudaMemcpyToSymbol(c_tab3t, &t, sizeof(Tables3T), sizeof(Tables3T) * (deg - 1)) == cudaSuccess ? 0 : -1;
+  Tables3TF f;
+  const double* src = &t.qw[0];
+  float* dst = &f.qw[0];
+  static_assert(sizeof(Tables3T) == 2 * sizeof(Tables3TF), "tables hold doubles only");
+  for (size_t k = 0; k < sizeof(Tables3T) / sizeof(double); ++k) dst[k] = (float)src[k];
+  if (cudaMemcpyToSymbol(c_tab3t, &t, sizeof(Tables3T), sizeof(Tables3T) * (deg - 1)) != cudaSuccess) return -1;
+  return cudaMemcpyToSymbol(c_tab3tf, &f, sizeof(Tables3TF), sizeof(Tables3TF) * (deg - 1)) == cudaSuccess ? 0 : -1;
 }
 
 int launch_step3t(int deg, const Mesh3T& m, const Work3& w, double* Q, const Args3& a, void* stream, int block,

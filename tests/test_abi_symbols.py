@@ -110,7 +110,7 @@ def test_3d_argument_errors_without_gpu(libpath):
     from paper_1601_08145_gb300 import lxw
     box = (0.0, 1.0, 0.0, 1.0, 0.0, 1.0)
     bad = [dict(nx=0), dict(degree=3), dict(bc=(0, 1, 0, 0, 0, 0)), dict(bc=(4,) * 6), dict(box=(0, 1, 0, 1, 1, 1)),
-           dict(options=lxw.lxw_options_default(precision=lxw.PREC_MIXED)),
+           dict(options=lxw.lxw_options_default(precision=7)),
            dict(options=lxw.lxw_options_default(ck_order=4)), dict(options=lxw.lxw_options_default(block_threads=48))]
     for b in bad:
         kw = dict(nx=3, degree=2, bc=(0,) * 6, box=box, options=None)
@@ -136,7 +136,7 @@ def test_tet_argument_errors_without_gpu(libpath):
     tripled = np.concatenate([tets, tets[:1]])
     bad = [dict(degree=3), dict(tets=flipped), dict(tets=out_of_range), dict(vid=repeated), dict(tets=tripled),
            dict(face_bc=np.zeros((len(tets), 4), dtype=np.int32)),
-           dict(options=lxw.lxw_options_default(precision=lxw.PREC_MIXED))]
+           dict(options=lxw.lxw_options_default(precision=7))]
     for b in bad:
         kw = dict(xyz=xyz, tets=tets, vid=vid, degree=2, face_bc=None, options=None)
         kw.update(b)
