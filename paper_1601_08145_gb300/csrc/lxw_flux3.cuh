@@ -305,18 +305,57 @@ __device__ __forceinline__ bool moment_screen3(const float cf[5][ML], const floa
   return true;
 }
 
-// Sec. 4.1 screen: true when every point's primitives lie inside [Mn, Mx]
-// by more than their bounds (theta = 1).  Mx, Mn are the FP64 bounds.
-template <int ML, int NPT, class LoadF>
-__device__ __forceinline__ bool shock_screen3(const float cf[5][ML], const float S[5], float g, const double Mx[5],
-                                              const double Mn[5], const LoadF& loadf) {
+// FP32 primitives (rho, u, v, w, p) of a state q with first-order bounds on
+// their rounding, given bounds Sv on the error scale of each component
+__device__ __forceinline__ void prim_bounds3(float g1, const float q[5], const float Sv[5], float wv[5], float ev[5]) {
+  const float ri = 1.0f / q[0];
+  const float u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
+  const float k2 = u * u + v * v + w * w;
+  wv[0] = q[0]; wv[1] = u; wv[2] = v; wv[3] = w; wv[4] = g1 * (q[4] - 0.5f * q[0] * k2);
+  ev[0] = kScreenTol * Sv[0];
+  ev[1] = kScreenTol * (Sv[1] + fabsf(u) * Sv[0]) * ri;
+  ev[2] = kScreenTol * (Sv[2] + fabsf(v) * Sv[0]) * ri;
+  ev[3] = kScreenTol * (Sv[3] + fabsf(w) * Sv[0]) * ri;
+  ev[4] = kScreenTol * g1 * (Sv[4] + fabsf(u) * Sv[1] + fabsf(v) * Sv[2] + fabsf(w) * Sv[3] + 0.5f * k2 * Sv[0]);
+}
+
+// Sec. 4.1 bounds for the screen, in FP32: a lower bound hi on M = max(w_i +
+// alpha, max_j w_j) and an upper bound lo on m = min(w_i - alpha, min_j w_j)
+// from the cell average qb and the neighbour (or mirrored) averages given by
+// nbr(k, qn) (false: no such neighbour, or a non-positive density)
+template <int E, class Nbr>
+__device__ __forceinline__ bool shock_bounds3(float g, float alpha, const float qb[5], const Nbr& nbr, float hi[5],
+                                              float lo[5]) {
   const float g1 = g - 1.0f;
-  float hi[5], lo[5];
+  float Sb[5], wb[5], eb[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    hi[v] = (float)Mx[v] - kScreenTol * fabsf((float)Mx[v]);
-    lo[v] = (float)Mn[v] + kScreenTol * fabsf((float)Mn[v]);
+  for (int v = 0; v < 5; ++v) Sb[v] = fabsf(qb[v]);
+  if (!(qb[0] > 0.0f)) return false;
+  prim_bounds3(g1, qb, Sb, wb, eb);
+  const float al = alpha * (1.0f - kScreenTol);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { hi[v] = wb[v] + al - eb[v]; lo[v] = wb[v] - al + eb[v]; }
+#pragma unroll 1
+  for (int k = 0; k < E; ++k) {
+    float qn[5];
+    if (!nbr(k, qn) || !(qn[0] > 0.0f)) continue;
+    float Sn[5], wn[5], en[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Sn[v] = fabsf(qn[v]);
+    prim_bounds3(g1, qn, Sn, wn, en);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { hi[v] = fmaxf(hi[v], wn[v] - en[v]); lo[v] = fminf(lo[v], wn[v] + en[v]); }
   }
+  return true;
+}
+
+// Sec. 4.1 screen: true when every point's primitives lie inside [lo, hi]
+// (FP32 bounds inside the exact [m, M]) by more than their rounding bounds
+// (theta = 1).
+template <int ML, int NPT, class LoadF>
+__device__ __forceinline__ bool shock_screen3(const float cf[5][ML], const float S[5], float g, const float hi[5],
+                                              const float lo[5], const LoadF& loadf) {
+  const float g1 = g - 1.0f;
 #pragma unroll 1
   for (int p = 0; p < NPT; ++p) {
     float ph[ML];
@@ -329,16 +368,9 @@ __device__ __forceinline__ bool shock_screen3(const float cf[5][ML], const float
       for (int l = 1; l < ML; ++l) acc = fmaf(cf[v][l], ph[l], acc);
       q[v] = acc;
     }
-    const float e0 = kScreenTol * S[0];
-    if (!(q[0] > 2.0f * e0)) return false;
-    const float ri = 1.0f / q[0];
-    const float u = q[1] * ri, v = q[2] * ri, w = q[3] * ri;
-    const float k2 = u * u + v * v + w * w;
-    const float pp = g1 * (q[4] - 0.5f * q[0] * k2);
-    const float wv[5] = {q[0], u, v, w, pp};
-    const float ev[5] = {e0, kScreenTol * (S[1] + fabsf(u) * S[0]) * ri, kScreenTol * (S[2] + fabsf(v) * S[0]) * ri,
-                         kScreenTol * (S[3] + fabsf(w) * S[0]) * ri,
-                         kScreenTol * g1 * (S[4] + fabsf(u) * S[1] + fabsf(v) * S[2] + fabsf(w) * S[3] + 0.5f * k2 * S[0])};
+    if (!(q[0] > 2.0f * kScreenTol * S[0])) return false;
+    float wv[5], ev[5];
+    prim_bounds3(g1, q, S, wv, ev);
 #pragma unroll
     for (int c = 0; c < 5; ++c)
       if (!(wv[c] + ev[c] <= hi[c] && wv[c] - ev[c] >= lo[c])) return false;

@@ -525,6 +525,34 @@ __global__ void __launch_bounds__(128) k3_shock(const Mesh3 m, const Work3 w, do
   if (!(c[0][0] > 0.0)) {
     th = 0.0;
   } else {
+    if (a.ck_fp32) {   // mixed form: FP32 bounds and points clear cells well inside [m, M]
+      const Tables3Of<float>& tf = tab3<float>(DEG);
+      float cf[5][ML], S[5], qbf[5], hi[5], lo[5];
+      screen_state3<ML>(c, tf.phimax, cf, S);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qbf[v] = cf[v][0];
+      auto nbrf = [&](int k, float qn[5]) -> bool {
+        const int j = m.nbr[k * N + i];
+        if (j >= 0) {
+          const double* Qj = Q + (size_t)j * 5 * ML;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) qn[v] = (float)Qj[v * ML];
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) qn[v] = qbf[v];
+          if (-1 - j == LXW_BC_REFLECT) qn[1 + (k >> 1)] = -qn[1 + (k >> 1)];
+        }
+        return true;
+      };
+      auto loadf = [&](int p, float ph[ML]) {
+#pragma unroll
+        for (int l = 0; l < ML; ++l) ph[l] = tf.phi[p][l];
+      };
+      const float alf = (float)a.alpha0 * powf(cbrtf((float)m.vol), 1.5f);
+      if (shock_bounds3<6>((float)a.gamma, alf, qbf, nbrf, hi, lo) &&
+          shock_screen3<ML, NPT>(cf, S, (float)a.gamma, hi, lo, loadf))
+        return;
+    }
     double qb[5], wb[5], Mx[5], Mn[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qb[v] = c[v][0];
@@ -549,16 +577,6 @@ __global__ void __launch_bounds__(128) k3_shock(const Mesh3 m, const Work3 w, do
       prim(qn, wn);
 #pragma unroll
       for (int v = 0; v < 5; ++v) { Mx[v] = fmax(Mx[v], wn[v]); Mn[v] = fmin(Mn[v], wn[v]); }
-    }
-    if (a.ck_fp32) {   // mixed form: the FP32 screen clears cells well inside the bounds
-      const Tables3Of<float>& tf = tab3<float>(DEG);
-      float cf[5][ML], S[5];
-      screen_state3<ML>(c, tf.phimax, cf, S);
-      auto loadf = [&](int p, float ph[ML]) {
-#pragma unroll
-        for (int l = 0; l < ML; ++l) ph[l] = tf.phi[p][l];
-      };
-      if (shock_screen3<ML, NPT>(cf, S, (float)a.gamma, Mx, Mn, loadf)) return;
     }
     double hx[5], hn[5];
 #pragma unroll

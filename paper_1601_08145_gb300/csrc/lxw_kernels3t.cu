@@ -612,6 +612,36 @@ __global__ void __launch_bounds__(128) k3t_shock(const Mesh3T m, const Work3 w, 
     th = 0.0;
   } else {
     const int code = m.code[i];
+    if (a.ck_fp32) {   // mixed form: FP32 bounds and points clear cells well inside [m, M]
+      const Tables3TF& tf = tab3t<float>(DEG);
+      float cf[5][ML], S[5], qbf[5], hi[5], lo[5];
+      screen_state3<ML>(c, tf.phimax, cf, S);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qbf[v] = cf[v][0];
+      auto nbrf = [&](int k, float qn[5]) -> bool {
+        const int j = m.nbr[k * N + i];
+        if (j >= 0) {
+          const double* Qj = Q + (size_t)j * 5 * ML;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) qn[v] = (float)Qj[v * ML];
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) qn[v] = qbf[v];
+          if (-1 - j == LXW_BC_REFLECT) {
+            const double an[3] = {geo(m, 10 + 3 * k, i), geo(m, 11 + 3 * k, i), geo(m, 12 + 3 * k, i)};
+            const double area = face_area(an);
+            const float nh[3] = {(float)(an[0] / area), (float)(an[1] / area), (float)(an[2] / area)};
+            mirror3<float>(nh, qn);
+          }
+        }
+        return true;
+      };
+      auto loadf = [&](int p, float ph[ML]) { load_phif<ML, NQ, NF>(tf, m, code, p, ph); };
+      const float alf = (float)a.alpha0 * powf(cbrtf((float)geo(m, 9, i)), 1.5f);
+      if (shock_bounds3<4>((float)a.gamma, alf, qbf, nbrf, hi, lo) &&
+          shock_screen3<ML, NPT>(cf, S, (float)a.gamma, hi, lo, loadf))
+        return;
+    }
     double qb[5], wb[5], Mx[5], Mn[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qb[v] = c[v][0];
@@ -641,13 +671,6 @@ __global__ void __launch_bounds__(128) k3t_shock(const Mesh3T m, const Work3 w, 
       prim(qn, wn);
 #pragma unroll
       for (int v = 0; v < 5; ++v) { Mx[v] = fmax(Mx[v], wn[v]); Mn[v] = fmin(Mn[v], wn[v]); }
-    }
-    if (a.ck_fp32) {   // mixed form: the FP32 screen clears cells well inside the bounds
-      const Tables3TF& tf = tab3t<float>(DEG);
-      float cf[5][ML], S[5];
-      screen_state3<ML>(c, tf.phimax, cf, S);
-      auto loadf = [&](int p, float ph[ML]) { load_phif<ML, NQ, NF>(tf, m, code, p, ph); };
-      if (shock_screen3<ML, NPT>(cf, S, (float)a.gamma, Mx, Mn, loadf)) return;
     }
     double hx[5], hn[5];
 #pragma unroll
