@@ -219,12 +219,13 @@ lxw_status lxw3_solver_create(int nx, int ny, int nz, const double box[6], const
   s->dw.trace = (double*)dalloc(sizeof(double) * 6 * s->NF * 10 * N);
   s->dw.flux = (double*)dalloc(sizeof(double) * 60 * N);
   s->dw.prop = (double*)dalloc(sizeof(double) * 6 * N);
+  s->dw.fbar = (double*)dalloc(sizeof(double) * 15 * N);
   s->dw.smax = (unsigned long long*)dalloc(sizeof(unsigned long long));
   s->dw.status = (unsigned int*)dalloc(sizeof(unsigned int));
   s->dw.diag = (Diag3Block*)dalloc(sizeof(Diag3Block));
   s->jw = (double*)dalloc(sizeof(double) * jw.size());
   s->jphi = (double*)dalloc(sizeof(double) * jphi.size());
-  if (!nbr || !s->dw.trace || !s->dw.flux || !s->dw.prop || !s->dw.smax || !s->dw.status || !s->dw.diag || !s->jw ||
+  if (!nbr || !s->dw.trace || !s->dw.flux || !s->dw.prop || !s->dw.fbar || !s->dw.smax || !s->dw.status || !s->dw.diag || !s->jw ||
       !s->jphi) {
     delete s;
     return fail3(LXW_ERR_NOMEM, "lxw3_solver_create: device allocation failed");
@@ -778,12 +779,13 @@ lxw_status lxw3_solver_create_tets(int n_vertices, const double* xyz, int n_tets
   s->dw.trace = (double*)dalloc(sizeof(double) * 4 * s->NF * 10 * N);
   s->dw.flux = (double*)dalloc(sizeof(double) * 40 * N);
   s->dw.prop = (double*)dalloc(sizeof(double) * 4 * N);
+  s->dw.fbar = (double*)dalloc(sizeof(double) * 15 * N);
   s->dw.smax = (unsigned long long*)dalloc(sizeof(unsigned long long));
   s->dw.status = (unsigned int*)dalloc(sizeof(unsigned int));
   s->dw.diag = (Diag3Block*)dalloc(sizeof(Diag3Block));
   s->jw = (double*)dalloc(sizeof(double) * jw.size());
   s->jphi = (double*)dalloc(sizeof(double) * jphi.size());
-  if (!dgeo || !dnbr || !dcode || !dfphi || !dfphif || !s->dw.trace || !s->dw.flux || !s->dw.prop || !s->dw.smax ||
+  if (!dgeo || !dnbr || !dcode || !dfphi || !dfphif || !s->dw.trace || !s->dw.flux || !s->dw.prop || !s->dw.fbar || !s->dw.smax ||
       !s->dw.status || !s->dw.diag || !s->jw || !s->jphi) {
     delete s;
     return fail3(LXW_ERR_NOMEM, std::string(who) + ": device allocation failed");

@@ -48,6 +48,7 @@ struct Work3 {
   double* trace;                       // [E][NF][10][N]: q (5), n_out . F_T (5), n scaled by the face area
   double* flux;                        // [E][10][N]: outward f^LxW (5), f^LxF (5)
   double* prop;                        // [E][N]: flux-limiter proposals
+  double* fbar;                        // [3][5][N]: Euler flux of each cell's average (moment kernel)
   unsigned long long* smax;            // bits of the global wave speed (non-negative double)
   unsigned int* status;                // LXW_ST_* bits of the step
   Diag3Block* diag;

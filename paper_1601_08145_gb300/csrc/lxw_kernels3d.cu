@@ -72,6 +72,18 @@ __global__ void __launch_bounds__(128) k3_moment(const Mesh3 m, const Work3 w, d
     for (int v = 0; v < 5; ++v)
 #pragma unroll
       for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
+    {   // the Euler flux of the average, read by the face kernel for this cell and its neighbours
+      double qa[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qa[v] = c[v][0];
+      const P3 sa = make_p3(a.gamma - 1.0, qa);
+      double Fa[3][5];
+      flux3(sa, Fa);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) w.fbar[(size_t)(d * 5 + v) * m.N + i] = Fa[d][v];
+    }
     auto load = [&](int p, double ph[ML]) {
 #pragma unroll
       for (int l = 0; l < ML; ++l) ph[l] = t.phi[p][l];
@@ -300,9 +312,6 @@ __global__ void __launch_bounds__(128) k3_face(const Mesh3 m, const Work3 w, dou
   double qb[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) qb[v] = Qi[v * ML];
-  const P3 sb = make_p3(g1, qb);
-  double Fb[3][5];
-  flux3(sb, Fb);
   T Ei[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
@@ -327,12 +336,27 @@ __global__ void __launch_bounds__(128) k3_face(const Mesh3 m, const Work3 w, dou
       if (-1 - j == LXW_BC_REFLECT) qn[1 + d] = -qn[1 + d];
     }
     {
-      const P3 sn = make_p3(g1, qn);
-      double Fn[3][5];
-      flux3(sn, Fn);
+      // the averages' fluxes along axis d: this cell's and an interior neighbour's
+      // from the moment kernel, a wall's mirrored state computed here
+      double Fbd[5], Fnd[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fbd[v] = w.fbar[(size_t)(d * 5 + v) * N + i];
+      if (j >= 0) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Fnd[v] = w.fbar[(size_t)(d * 5 + v) * N + j];
+      } else if (-1 - j == LXW_BC_REFLECT) {
+        const P3 sn = make_p3(g1, qn);
+        double Fn[3][5];
+        flux3(sn, Fn);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Fnd[v] = Fn[d][v];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Fnd[v] = Fbd[v];
+      }
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double ai = __dmul_rn(an, Fb[d][v]), ak = __dmul_rn(an, Fn[d][v]);
+        const double ai = __dmul_rn(an, Fbd[v]), ak = __dmul_rn(an, Fnd[v]);
         fF[k][v] = __fma_rn(-hs, __dsub_rn(qn[v], qb[v]), __dmul_rn(0.5, __dadd_rn(ai, ak)));
       }
     }

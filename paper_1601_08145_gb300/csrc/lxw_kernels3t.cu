@@ -132,6 +132,18 @@ __global__ void __launch_bounds__(128) k3t_moment(const Mesh3T m, const Work3 w,
     for (int v = 0; v < 5; ++v)
 #pragma unroll
       for (int l = 0; l < ML; ++l) c[v][l] = Qi[v * ML + l];
+    {   // the Euler flux of the average, read by the face kernel for this cell and its neighbours
+      double qa[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qa[v] = c[v][0];
+      const P3 sa = make_p3(a.gamma - 1.0, qa);
+      double Fa[3][5];
+      flux3(sa, Fa);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) w.fbar[(size_t)(d * 5 + v) * m.N + i] = Fa[d][v];
+    }
     const int code = m.code[i];
     auto load = [&](int p, double ph[ML]) { load_phi<ML, NQ, NF>(t, m, code, p, ph); };
     bool screened = false;
@@ -380,9 +392,11 @@ __global__ void __launch_bounds__(128) k3t_face(const Mesh3T m, const Work3 w, d
   double qb[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) qb[v] = Qi[v * ML];
-  const P3 sb = make_p3(g1, qb);
-  double Fb[3][5];
-  flux3(sb, Fb);
+  double Fb[3][5];   // the average's flux, from the moment kernel
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Fb[d][v] = w.fbar[(size_t)(d * 5 + v) * N + i];
   T Ei[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
@@ -408,9 +422,22 @@ __global__ void __launch_bounds__(128) k3t_face(const Mesh3T m, const Work3 w, d
       if (wall) mirror3<double>(nh, qn);
     }
     {
-      const P3 sn = make_p3(g1, qn);
+      // a neighbour's average flux from the moment kernel, a wall's mirrored state here
       double Fn[3][5];
-      flux3(sn, Fn);
+      if (j >= 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Fn[d][v] = w.fbar[(size_t)(d * 5 + v) * N + j];
+      } else if (wall) {
+        const P3 sn = make_p3(g1, qn);
+        flux3(sn, Fn);
+      } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Fn[d][v] = Fb[d][v];
+      }
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double ai = ndot<double>(an, Fb, v), ak = ndot<double>(an, Fn, v);
