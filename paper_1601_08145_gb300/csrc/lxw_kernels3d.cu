@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(128) k3_ck(const Mesh3 m, const Work3 w, doubl
 // and the face integral: FP32 in the mixed form); the averages, f^LxF and
 // Steps 4-5 are FP64 in both forms.
 template <typename T, int DEG, int ML, int N1>
-__global__ void __launch_bounds__(128) k3_face(const Mesh3 m, const Work3 w, double* __restrict__ Q, const Args3 a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k3_face(const Mesh3 m, const Work3 w, double* __restrict__ Q, const Args3 a) {
   constexpr int NQ = N1 * N1 * N1, NF = N1 * N1;
   const Tables3Of<T>& t = tab3<T>(DEG);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

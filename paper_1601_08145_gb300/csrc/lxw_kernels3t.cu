@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(128) k3t_ck(const Mesh3T m, const Work3 w, dou
 // T is the arithmetic of the point loop (FP32 in the mixed form); the
 // averages, f^LxF and Steps 4-5 are FP64 in both forms.
 template <typename T, int DEG, int ML, int N1>
-__global__ void __launch_bounds__(128) k3t_face(const Mesh3T m, const Work3 w, double* __restrict__ Q,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k3t_face(const Mesh3T m, const Work3 w, double* __restrict__ Q,
                                                 const Args3 a) {
   constexpr int NF = N1 * N1;
   const Tables3TOf<T>& t = tab3t<T>(DEG);
