@@ -133,7 +133,7 @@ def ic_blast3d(n: int, half_width: float = 1.1, gamma: float = GAMMA, e_total: f
 
 
 def tet_mesh(n: int, box=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0), periodic: bool = False, jitter: float = 0.0,
-             seed: int = 0):
+             seed: int = 0, permute: bool = False):
     """Tetrahedra of an n^3 grid of boxes, each box cut into six along its
     main diagonal (Kuhn's subdivision: v0 = the low corner, then one unit
     step along each axis in the order of a permutation), so neighbouring
@@ -144,7 +144,10 @@ def tet_mesh(n: int, box=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0), periodic: bool = False,
     modulo n on every axis, so the two cells of a face across the period
     share its vertex ids).  jitter moves interior vertices by up to jitter
     times the spacing (U[-1,1] per coordinate, from the seed); periodic
-    meshes are not jittered."""
+    meshes are not jittered.  permute renumbers each cell's four vertices by
+    one of the 12 even permutations (drawn from seed + 1), which keeps the
+    orientation positive, so that neighbouring cells list a shared face's
+    vertices in unrelated orders."""
     m = n + 1
     ax = [np.linspace(box[2 * d], box[2 * d + 1], m) for d in range(3)]
     I, J, K = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
@@ -175,6 +178,11 @@ def tet_mesh(n: int, box=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0), periodic: bool = False,
     vol = np.einsum("ij,ij->i", np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0]), p[:, 3] - p[:, 0])
     neg = vol < 0
     tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
+    if permute:
+        even = np.array([p for p in __import__("itertools").permutations(range(4))
+                         if sum(p[a] > p[b] for a in range(4) for b in range(a + 1, 4)) % 2 == 0])
+        pick = (uniform01(seed + 1, len(tets)) * len(even)).astype(np.int64)
+        tets = np.take_along_axis(tets, even[pick], axis=1).astype(np.int32)
     if periodic:
         vid = idx(I % n, J % n, K % n).ravel()
         vid_of = np.empty(m ** 3, dtype=np.int32)
