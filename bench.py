@@ -445,35 +445,37 @@ BLAST3T = dict(n=48, deg=2, cfl=0.1, half_width=1.1,
 
 
 def ck3t_flops_per_element(deg):
-    """Algorithmic FP64 flop of k3t_ck per tetrahedron (an FMA counts 2), the
+    """Algorithmic flop of k3t_ck per tetrahedron (an FMA counts 2), the
     hexahedral count with NPT = NQ + 4 n^2 points and, at each interior
     point of every pass, the contravariant flux G_a = sum_d Ji[a][d] F_d (45
-    FMA) in place of the three axis scalings; at a face point an_k . F_T (15
-    FMA)."""
+    FMA) in place of the three axis scalings; a face point evaluates q, q_t,
+    q_tt and only the normal component an_k . F_T (the normal flux and its
+    derivatives, ~200)."""
     n = deg + 1
     NQ, NF = n ** 3, n * n
     ML = (deg + 1) * (deg + 2) * (deg + 3) // 6
     p1 = NQ * (2 * 5 * ML + 40 + 90 + 2 * 15 * ML)
     p2 = NQ * (2 * 10 * ML + 70 + 90 + 2 * 15 * ML)
-    p3 = NQ * (2 * 15 * ML + 320 + 90 + 2 * 15 * (ML - 1)) + 4 * NF * (2 * 15 * ML + 320 + 30)
+    p3 = NQ * (2 * 15 * ML + 320 + 90 + 2 * 15 * (ML - 1)) + 4 * NF * (2 * 15 * ML + 200)
     return p1 + p2 + p3
 
 
 def ck3_flops_per_element(deg):
     """Algorithmic FP64 flop of k3_ck per cell (an FMA counts 2): with n =
-    deg + 1, NQ = n^3 interior and NPT = NQ + 6 n^2 points, ML modes, 5
-    variables.  Pass 1: q at the interior points (5 ML FMA), the flux (~40),
-    the three weighted-table sums (15 ML FMA + 15).  Pass 2: q and q_t
-    (10 ML FMA), F'(q) q_t (~70), three table sums (15 ML FMA + 15).  Pass
-    3 at every point: q, q_t, q_tt (15 ML FMA), F, F' q_t, F'' (q_t, q_t),
-    F' q_tt and F_T (~320); the volume sums at the interior points (15 (ML-1)
-    FMA + 15)."""
+    deg + 1, NQ = n^3 interior and 6 n^2 face points, ML modes, 5 variables.
+    Pass 1: q at the interior points (5 ML FMA), the flux (~40), the three
+    weighted-table sums (15 ML FMA + 15).  Pass 2: q and q_t (10 ML FMA),
+    F'(q) q_t (~70), three table sums (15 ML FMA + 15).  Pass 3 at the
+    interior points: q, q_t, q_tt (15 ML FMA), F, F' q_t, F'' (q_t, q_t),
+    F' q_tt and F_T (~320), the volume sums (15 (ML-1) FMA + 15); at the face
+    points: q, q_t, q_tt and only the normal component of F_T (the normal
+    flux and its derivatives, ~200)."""
     n = deg + 1
-    NQ, NPT = n ** 3, n ** 3 + 6 * n * n
+    NQ, NF = n ** 3, n * n
     ML = (deg + 1) * (deg + 2) * (deg + 3) // 6
     p1 = NQ * (2 * 5 * ML + 40 + 2 * 15 * ML + 15)
     p2 = NQ * (2 * 10 * ML + 70 + 2 * 15 * ML + 15)
-    p3 = NPT * (2 * 15 * ML + 320) + NQ * (2 * 15 * (ML - 1) + 15)
+    p3 = NQ * (2 * 15 * ML + 320) + 6 * NF * (2 * 15 * ML + 200) + NQ * (2 * 15 * (ML - 1) + 15)
     return p1 + p2 + p3
 
 

@@ -377,3 +377,74 @@ __device__ __forceinline__ bool shock_screen3(const float cf[5][ML], const float
   }
   return true;
 }
+
+// ---------------------------------------------------------------- normal flux
+// n . F and its derivatives along n, for the face points, where only the
+// normal component of F_T is needed: n . F(q) = (m . n, m (u . n) + p n,
+// (E + p) u . n); the first and second derivatives follow flux3_d1 and
+// flux3_d2 dotted with n.
+template <typename T>
+__device__ __forceinline__ void fluxn3(const P3T<T>& s, const T n[3], T F[5]) {
+  const T un = s.u[0] * n[0] + s.u[1] * n[1] + s.u[2] * n[2];
+  F[0] = s.q[1] * n[0] + s.q[2] * n[1] + s.q[3] * n[2];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) F[1 + e] = s.q[1 + e] * un + s.p * n[e];
+  F[4] = (s.q[4] + s.p) * un;
+}
+
+template <typename T>
+__device__ __forceinline__ void fluxn3_d1(T g1, const P3T<T>& s, const T n[3], const T w[5], T F[5], T du[3], T& dp) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) du[d] = (w[1 + d] - s.u[d] * w[0]) * s.ri;
+  const T k2 = s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2];
+  dp = g1 * (w[4] - (s.u[0] * w[1] + s.u[1] * w[2] + s.u[2] * w[3]) + T(0.5) * k2 * w[0]);
+  const T un = s.u[0] * n[0] + s.u[1] * n[1] + s.u[2] * n[2];
+  const T dun = du[0] * n[0] + du[1] * n[1] + du[2] * n[2];
+  F[0] = w[1] * n[0] + w[2] * n[1] + w[3] * n[2];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) F[1 + e] = w[1 + e] * un + s.q[1 + e] * dun + dp * n[e];
+  F[4] = (w[4] + dp) * un + (s.q[4] + s.p) * dun;
+}
+
+template <typename T>
+__device__ __forceinline__ void fluxn3_d2(T g1, const P3T<T>& s, const T n[3], const T w[5], const T du[3], T dp,
+                                          T F[5]) {
+  T d2u[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) d2u[d] = T(-2) * w[0] * du[d] * s.ri;
+  const T d2p = -g1 * ((w[1] * du[0] + w[2] * du[1] + w[3] * du[2]) +
+                       T(0.5) * (s.q[1] * d2u[0] + s.q[2] * d2u[1] + s.q[3] * d2u[2]));
+  const T un = s.u[0] * n[0] + s.u[1] * n[1] + s.u[2] * n[2];
+  const T dun = du[0] * n[0] + du[1] * n[1] + du[2] * n[2];
+  const T d2un = d2u[0] * n[0] + d2u[1] * n[1] + d2u[2] * n[2];
+  F[0] = T(0);
+#pragma unroll
+  for (int e = 0; e < 3; ++e) F[1 + e] = T(2) * w[1 + e] * dun + s.q[1 + e] * d2un + d2p * n[e];
+  F[4] = d2p * un + T(2) * (w[4] + dp) * dun + (s.q[4] + s.p) * d2un;
+}
+
+// q and n . F_T = n . (F + dt/2 F_t + dt^2/6 F_tt) at a point from the basis values
+template <typename T, int ML>
+__device__ __forceinline__ void ftn_point3(T g1, T c1, T c2, const T n[3], const T ph[ML], const T c[5][ML],
+                                           const T Qt[5][ML], const T Qtt[5][ML], T q[5], T FTn[5]) {
+  T qt[5], qtt[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    T acc = T(0), d1 = T(0), d2 = T(0);
+#pragma unroll
+    for (int l = 0; l < ML; ++l) {
+      acc = fmaT(c[v][l], ph[l], acc);
+      d1 = fmaT(Qt[v][l], ph[l], d1);
+      d2 = fmaT(Qtt[v][l], ph[l], d2);
+    }
+    q[v] = acc; qt[v] = d1; qtt[v] = d2;
+  }
+  const P3T<T> s = make_p3<T>(g1, q);
+  T F[5], F1[5], F2[5], F3[5], du[3], dp, eu[3], ep;
+  fluxn3<T>(s, n, F);
+  fluxn3_d1<T>(g1, s, n, qt, F1, du, dp);
+  fluxn3_d2<T>(g1, s, n, qt, du, dp, F2);
+  fluxn3_d1<T>(g1, s, n, qtt, F3, eu, ep);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) FTn[v] = F[v] + c1 * F1[v] + c2 * (F2[v] + F3[v]);
+}

@@ -219,14 +219,14 @@ __global__ void __launch_bounds__(128) k3_ck(const Mesh3 m, const Work3 w, doubl
         Qtt[v][l] -= f0 * t.W[0][k][l] + f1 * t.W[1][k][l] + f2 * t.W[2][k][l];
     }
   }
-  // pass 3: F_T everywhere; volume integral at interior points, traces at face points
+  // pass 3a: F_T at the interior points -> volume integral of the higher moments
   T Vv[5][ML];
 #pragma unroll
   for (int v = 0; v < 5; ++v)
 #pragma unroll
     for (int l = 0; l < ML; ++l) Vv[v][l] = T(0);
 #pragma unroll 1
-  for (int p = 0; p < NPT; ++p) {
+  for (int p = 0; p < NQ; ++p) {
     T q[5], qt[5], qtt[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -258,23 +258,29 @@ __global__ void __launch_bounds__(128) k3_ck(const Mesh3 m, const Work3 w, doubl
 #pragma unroll
         for (int v = 0; v < 5; ++v) FT[d][v] += c2 * (F1[d][v] + F3[d][v]);
     }
-    if (p < NQ) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const T f0 = t.qw[p] * sd[0] * FT[0][v], f1 = t.qw[p] * sd[1] * FT[1][v], f2 = t.qw[p] * sd[2] * FT[2][v];
+    for (int v = 0; v < 5; ++v) {
+      const T f0 = t.qw[p] * sd[0] * FT[0][v], f1 = t.qw[p] * sd[1] * FT[1][v], f2 = t.qw[p] * sd[2] * FT[2][v];
 #pragma unroll
-        for (int l = 1; l < ML; ++l)
-          Vv[v][l] = fmaT(f0, t.dref[0][p][l], fmaT(f1, t.dref[1][p][l], fmaT(f2, t.dref[2][p][l], Vv[v][l])));
-      }
-    } else {
-      const int k = (p - NQ) / NF, pe = (p - NQ) - k * NF, d = k >> 1;
-      const T an = (k & 1) ? avh[d] : -avh[d];   // outward normal times the face area
-      T* tr = reinterpret_cast<T*>(w.trace) + ((size_t)(k * NF + pe) * 10) * N + i;
+      for (int l = 1; l < ML; ++l)
+        Vv[v][l] = fmaT(f0, t.dref[0][p][l], fmaT(f1, t.dref[1][p][l], fmaT(f2, t.dref[2][p][l], Vv[v][l])));
+    }
+  }
+  // pass 3b: q and n_out . F_T (n scaled by the face area) at the face points
+#pragma unroll 1
+  for (int p = NQ; p < NPT; ++p) {
+    const int k = (p - NQ) / NF, pe = (p - NQ) - k * NF, d = k >> 1;
+    T nv[3] = {T(0), T(0), T(0)};
+    nv[d] = (k & 1) ? avh[d] : -avh[d];   // outward normal times the face area
+    T ph[ML], q[5], FTn[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        tr[(size_t)v * N] = q[v];
-        tr[(size_t)(5 + v) * N] = rn_mul(an, FT[d][v]);
-      }
+    for (int l = 0; l < ML; ++l) ph[l] = t.phi[p][l];
+    ftn_point3<T, ML>(g1, c1, c2, nv, ph, c, Qt, Qtt, q, FTn);
+    T* tr = reinterpret_cast<T*>(w.trace) + ((size_t)(k * NF + pe) * 10) * N + i;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      tr[(size_t)v * N] = q[v];
+      tr[(size_t)(5 + v) * N] = FTn[v];
     }
   }
 #pragma unroll

@@ -342,15 +342,15 @@ __global__ void __launch_bounds__(128) k3t_ck(const Mesh3T m, const Work3 w, dou
     const T* fk = ftab + (size_t)((k * k3tPerms + ((code >> (3 * k)) & 7)) * NF) * ML;
 #pragma unroll 1
     for (int p = 0; p < NF; ++p) {
-      T ph[ML], q[5], FT[3][5];
+      T ph[ML], q[5], FTn[5];
 #pragma unroll
       for (int l = 0; l < ML; ++l) ph[l] = __ldg(fk + p * ML + l);
-      ft_point3t<T, ML>(g1, c1, c2, ph, c, Qt, Qtt, q, FT);
+      ftn_point3<T, ML>(g1, c1, c2, an, ph, c, Qt, Qtt, q, FTn);   // an . F_T directly
       T* tr = reinterpret_cast<T*>(w.trace) + ((size_t)(k * NF + p) * 10) * N + i;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         tr[(size_t)v * N] = q[v];
-        tr[(size_t)(5 + v) * N] = ndot<T>(an, FT, v);
+        tr[(size_t)(5 + v) * N] = FTn[v];
       }
     }
   }
