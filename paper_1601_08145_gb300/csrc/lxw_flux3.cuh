@@ -1,8 +1,10 @@
-// lxw_flux3.cuh -- device helpers of the 3D FP64 forms (hexahedra and
-// tetrahedra): the Euler flux in three directions, its first and second
-// directional derivatives (the Cauchy-Kovalevskaya terms of Sec. 2.2), the
-// wave speed and the local Lax-Friedrichs speed.  Included inside each
-// kernel file's anonymous namespace.
+// lxw_flux3.cuh -- device helpers of the 3D forms (hexahedra and
+// tetrahedra, FP64 and mixed): the Euler flux in three directions and along
+// a normal, its first and second directional derivatives (the
+// Cauchy-Kovalevskaya terms of Sec. 2.2), the wave speed and the local
+// Lax-Friedrichs speed, the moment limiter of Sec. 3.1, and the FP32 screens
+// of the mixed forms.  Included inside each kernel file's anonymous
+// namespace.
 #pragma once
 
 __device__ __forceinline__ double speed_of3(double g, const double q[5]) {

@@ -1,7 +1,10 @@
 // lxw_kernels3d.cu -- sm_103a kernels of one LxW-DG step on 3D Cartesian
-// meshes (hexahedra), FP64, the extension the paper says carries over
-// directly (end of Sec. 3.3; the 3D Euler equations of Sec. 1.1 with the
-// third flux H).
+// meshes (hexahedra), the extension the paper says carries over directly
+// (end of Sec. 3.3; the 3D Euler equations of Sec. 1.1 with the third flux
+// H).  Two forms: FP64 throughout, and mixed (Args3::ck_fp32): the CK kernel
+// and the face point loop in FP32, FP32 screens in the moment and shock
+// limiters, the state, averages, f^LxF, Steps 4-5 and every limiter
+// decision in FP64.
 //
 // One thread owns one cell, as in the 2D FP64 form; state Q[N][5][ML]
 // (rho, rho u, rho v, rho w, E), modes ordered by total degree, then the x

@@ -1,6 +1,7 @@
 // lxw_kernels3t.cu -- sm_103a kernels of one LxW-DG step on tetrahedral
-// meshes, FP64: the unstructured 3D extension (end of Sec. 3.3; the 3D Euler
-// equations of Sec. 1.1).
+// meshes: the unstructured 3D extension (end of Sec. 3.3; the 3D Euler
+// equations of Sec. 1.1), in the FP64 and the mixed form of the hexahedral
+// kernels.
 //
 // One thread owns one cell, as in the hexahedral form; state Q[N][5][ML].
 // Each cell is the affine image of the reference tetrahedron T0; its
