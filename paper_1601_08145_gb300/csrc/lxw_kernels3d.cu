@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(128) k3_ck(const Mesh3 m, const Work3 w, doubl
       const T f0 = sd[0] * F[0][v], f1 = sd[1] * F[1][v], f2 = sd[2] * F[2][v];
 #pragma unroll
       for (int l = 0; l < ML; ++l)
-        Qt[v][l] -= f0 * t.W[0][k][l] + f1 * t.W[1][k][l] + f2 * t.W[2][k][l];
+        Qt[v][l] = fmaT(-f2, t.W[2][k][l], fmaT(-f1, t.W[1][k][l], fmaT(-f0, t.W[0][k][l], Qt[v][l])));
     }
   }
   // pass 2: Qtt
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(128) k3_ck(const Mesh3 m, const Work3 w, doubl
       const T f0 = sd[0] * F1[0][v], f1 = sd[1] * F1[1][v], f2 = sd[2] * F1[2][v];
 #pragma unroll
       for (int l = 0; l < ML; ++l)
-        Qtt[v][l] -= f0 * t.W[0][k][l] + f1 * t.W[1][k][l] + f2 * t.W[2][k][l];
+        Qtt[v][l] = fmaT(-f2, t.W[2][k][l], fmaT(-f1, t.W[1][k][l], fmaT(-f0, t.W[0][k][l], Qtt[v][l])));
     }
   }
   // pass 3a: F_T at the interior points -> volume integral of the higher moments

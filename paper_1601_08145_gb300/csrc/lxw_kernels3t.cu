@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(128) k3t_ck(const Mesh3T m, const Work3 w, dou
 #pragma unroll
     for (int v = 0; v < 5; ++v)
 #pragma unroll
-      for (int l = 0; l < ML; ++l) Qt[v][l] -= G[0][v] * t.W[0][k][l] + G[1][v] * t.W[1][k][l] + G[2][v] * t.W[2][k][l];
+      for (int l = 0; l < ML; ++l)
+        Qt[v][l] = fmaT(-G[2][v], t.W[2][k][l], fmaT(-G[1][v], t.W[1][k][l], fmaT(-G[0][v], t.W[0][k][l], Qt[v][l])));
   }
   // pass 2: Qtt
   T Qtt[5][ML];
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(128) k3t_ck(const Mesh3T m, const Work3 w, dou
     for (int v = 0; v < 5; ++v)
 #pragma unroll
       for (int l = 0; l < ML; ++l)
-        Qtt[v][l] -= G[0][v] * t.W[0][k][l] + G[1][v] * t.W[1][k][l] + G[2][v] * t.W[2][k][l];
+        Qtt[v][l] = fmaT(-G[2][v], t.W[2][k][l], fmaT(-G[1][v], t.W[1][k][l], fmaT(-G[0][v], t.W[0][k][l], Qtt[v][l])));
   }
   // pass 3a: F_T at the interior points -> volume integral of the higher moments
   T Vv[5][ML];
