@@ -444,6 +444,26 @@ BLAST3T = dict(n=48, deg=2, cfl=0.1, half_width=1.1,
                     "cells, point energy 0.979264 in the 48 cells around the origin, reflective walls (FP64 form)")
 
 
+# DRAM bytes (read + write) of one launch of the mixed forms' FP32 CK kernel from an ncu
+# capture of the same blast on a smaller mesh (--n3 32 / 64), scaled by the cells (the
+# kernel's traffic is per cell: the state read and written back, the FP32 traces), valid
+# while the source the kernel is built from is unchanged
+CK3_TRAFFIC = {
+    "blast3t": {"bytes": 125_647_104 + 302_418_688, "captured_elements": 196_608, "source": "ba7a2b5ffd0472fd"},
+    "blast3d": {"bytes": 154_067_712 + 615_788_544, "captured_elements": 262_144, "source": "e01c9701d787f53b"},
+}
+
+
+def ck3_source_hash(tet):
+    """Hash of the 3D helpers and of the kernel file up to its face kernel."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1601_08145_gb300", "csrc")
+    tu, marker = (("lxw_kernels3t.cu", b"// ------------------------------------------------------------ k3t_face") if tet
+                  else ("lxw_kernels3d.cu", b"// ------------------------------------------------------------ k3_face"))
+    text = open(os.path.join(csrc, tu), "rb").read()
+    return hashlib.sha256(open(os.path.join(csrc, "lxw_flux3.cuh"), "rb").read() + text[:text.index(marker)]).hexdigest()[:16]
+
+
 def ck3t_flops_per_element(deg):
     """Algorithmic flop of k3t_ck per tetrahedron (an FMA counts 2), the
     hexahedral count with NPT = NQ + 4 n^2 points and, at each interior
@@ -544,6 +564,12 @@ def run_blast3d(args):
                                 else "nominal GB300 FP64 rate (recipe table)"),
                 "peak_measured_fma_probe": probes.get("fp32" if fp32 else "fp64"),
                 "algorithmic_flops_per_launch": flops, "launch_ms": ph["ck"], "traffic": None}
+        rec = CK3_TRAFFIC.get(args.workload)
+        if fp32 and rec is not None and rec["source"] == ck3_source_hash(tet):
+            roof["traffic"] = rec["bytes"] * s.N / rec["captured_elements"]
+            roof["traffic_source"] = "ncu dram__bytes_read+write at %d cells, scaled by the cells" % rec["captured_elements"]
+            roof["algorithmic_bytes_per_launch"] = s.N * (5 * s.ML * 8 + 5 * (s.ML - 1) * 8 + (4 if tet else 6) * (
+                (b["deg"] + 1) ** 2) * 10 * 4)
         roof["frac"] = roof["achieved"] / peak
         res[name] = {"value": s.N * 5 * s.ML * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
                      "phases_ms": ph, "roofline": roof, "clocks": clk, "launches": args.steps * L.lxw3_step_launches(s) + 1,
