@@ -545,7 +545,7 @@ int lxw3_step_launches(const lxw_solver3* s);
  * limiter's alpha = alpha0 * (|K|^(1/3))^1.5 per cell; the flux limiter's mu
  * runs over the 15 corners of the box of four proposals.  The host arrays
  * are read during the call only.  Allocates about (40 NF + 90) doubles per
- * cell of workspace plus 22 doubles and 5 ints of geometry.  Errors:
+ * cell of workspace plus 26 doubles and 5 ints of geometry.  Errors:
  * LXW_ERR_ARG (null pointer, sizes, degree, index out of range, repeated id
  * in a cell, non-positive orientation, a face shared by more than two
  * cells, a bad boundary code), LXW_ERR_NOMEM, LXW_ERR_CUDA. */

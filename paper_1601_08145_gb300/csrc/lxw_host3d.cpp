@@ -716,6 +716,7 @@ lxw_status lxw3_solver_create_tets(int n_vertices, const double* xyz, int n_tets
   };
   auto put_normal = [&](size_t i, int k, const double an[3], double sg) {
     for (int d = 0; d < 3; ++d) hgeo[(size_t)(10 + 3 * k + d) * N + i] = sg * an[d];
+    hgeo[(size_t)(22 + k) * N + i] = std::sqrt(an[0] * an[0] + an[1] * an[1] + an[2] * an[2]);
   };
   for (size_t r = 0; r < rec.size();) {
     size_t e = r + 1;
@@ -743,11 +744,7 @@ lxw_status lxw3_solver_create_tets(int n_vertices, const double* xyz, int n_tets
   double hmin = 1e300;
   for (size_t i = 0; i < N; ++i) {
     double surf = 0.0;
-    for (int k = 0; k < 4; ++k) {
-      double a2 = 0.0;
-      for (int d = 0; d < 3; ++d) { const double x = hgeo[(size_t)(10 + 3 * k + d) * N + i]; a2 += x * x; }
-      surf += std::sqrt(a2);
-    }
+    for (int k = 0; k < 4; ++k) surf += hgeo[(size_t)(22 + k) * N + i];
     hmin = std::min(hmin, 3.0 * hgeo[9 * N + i] / surf);
   }
   lxw_solver3* s = new (std::nothrow) lxw_solver3;

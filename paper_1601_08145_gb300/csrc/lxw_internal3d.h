@@ -98,12 +98,13 @@ using Tables3T = Tables3TOf<double>;
 using Tables3TF = Tables3TOf<float>;
 
 // Per-cell geometry, structure of arrays.
-constexpr int k3tGeo = 22;             // Ji (9), vol, an (4 x 3)
+constexpr int k3tGeo = 26;             // Ji (9), vol, an (4 x 3), face areas (4)
 struct Mesh3T {
   int N;
   double hmin;                         // min 3 |K| / |dK|
-  const double* geo;                   // [22][N]: Ji[a][d] = d r_a / d x_d (row-major), |K|, outward
-                                       //   normals scaled by the face area (face k: 10 + 3k ..)
+  const double* geo;                   // [26][N]: Ji[a][d] = d r_a / d x_d (row-major), |K|, outward
+                                       //   normals scaled by the face area (face k: 10 + 3k ..), the
+                                       //   face areas (face k: 22 + k; one value for both cells)
   const int* nbr;                      // [4][N]: neighbour across face k, or -1 - bc
   const int* code;                     // [N]: bits 3k..3k+2 perm of face k, bits 12+2k..12+2k+1 the
                                        //   neighbour's local face

@@ -99,9 +99,8 @@ __device__ __forceinline__ T ndot(const T an[3], const T F[3][5], int v) {
   return rn_fma(an[2], F[2][v], rn_fma(an[1], F[1][v], rn_mul(an[0], F[0][v])));
 }
 
-__device__ __forceinline__ double face_area(const double an[3]) {
-  return __dsqrt_rn(__fma_rn(an[2], an[2], __fma_rn(an[1], an[1], __dmul_rn(an[0], an[0]))));
-}
+// the area of face k of cell i (stored once per face for both of its cells)
+__device__ __forceinline__ double face_area(const Mesh3T& m, int k, int i) { return m.geo[(size_t)(22 + k) * m.N + i]; }
 
 // ------------------------------------------------------------ k3t_reset
 __global__ void k3t_reset(Work3 w, int want_diag) {
@@ -409,9 +408,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k3t_face(const Me
   for (int k = 0; k < 4; ++k) {
     const int j = m.nbr[k * N + i], kj = (code >> (12 + 2 * k)) & 3;
     const double an[3] = {geo(m, 10 + 3 * k, i), geo(m, 11 + 3 * k, i), geo(m, 12 + 3 * k, i)};
-    const double area = face_area(an);
-    const double nh[3] = {an[0] / area, an[1] / area, an[2] / area};
+    const double area = face_area(m, k, i);
     const bool wall = j < 0 && -1 - j == LXW_BC_REFLECT;
+    double nh[3] = {0.0, 0.0, 0.0};   // the unit normal, needed on walls only
+    if (wall) { nh[0] = an[0] / area; nh[1] = an[1] / area; nh[2] = an[2] / area; }
     const double hs = 0.5 * s * area;
     double qn[5];
     if (j >= 0) {
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(128) k3t_shock(const Mesh3T m, const Work3 w, 
           for (int v = 0; v < 5; ++v) qn[v] = qbf[v];
           if (-1 - j == LXW_BC_REFLECT) {
             const double an[3] = {geo(m, 10 + 3 * k, i), geo(m, 11 + 3 * k, i), geo(m, 12 + 3 * k, i)};
-            const double area = face_area(an);
+            const double area = face_area(m, k, i);
             const float nh[3] = {(float)(an[0] / area), (float)(an[1] / area), (float)(an[2] / area)};
             mirror3<float>(nh, qn);
           }
@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(128) k3t_shock(const Mesh3T m, const Work3 w, 
         for (int v = 0; v < 5; ++v) qn[v] = qb[v];
         if (-1 - j == LXW_BC_REFLECT) {
           const double an[3] = {geo(m, 10 + 3 * k, i), geo(m, 11 + 3 * k, i), geo(m, 12 + 3 * k, i)};
-          const double area = face_area(an);
+          const double area = face_area(m, k, i);
           const double nh[3] = {an[0] / area, an[1] / area, an[2] / area};
           mirror3<double>(nh, qn);
         }
