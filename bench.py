@@ -449,7 +449,7 @@ BLAST3T = dict(n=48, deg=2, cfl=0.1, half_width=1.1,
 # kernel's traffic is per cell: the state read and written back, the FP32 traces), valid
 # while the source the kernel is built from is unchanged
 CK3_TRAFFIC = {
-    "blast3t": {"bytes": 125_647_104 + 302_418_688, "captured_elements": 196_608, "source": "ba7a2b5ffd0472fd"},
+    "blast3t": {"bytes": 125_647_104 + 302_418_688, "captured_elements": 196_608, "source": "45533b02a27e26d1"},
     "blast3d": {"bytes": 154_067_712 + 615_788_544, "captured_elements": 262_144, "source": "e01c9701d787f53b"},
 }
 
