@@ -106,3 +106,84 @@ def test_planted_mistakes_fail_the_pins(name):
     with tempfile.TemporaryDirectory() as tmp:
         with orc.use_library(_build(tmp, name)):
             assert pin_failures(orc) != [], name
+
+
+# ---------------------------------------------------------------- hexahedra
+HEX_MUTANTS = {
+    # neighbour index with the y and z strides confused
+    "neighbour_strides": ("m->nbr[6 * i + k] = (cc[2] * ny + cc[1]) * nx + cc[0];",
+                          "m->nbr[6 * i + k] = (cc[1] * nz + cc[2]) * nx + cc[0];"),
+    # face normals pointing inward
+    "normal_inward": ("n[d] = (k % 2 ? 1.0 : -1.0) * m->vol[i] / h[d];", "n[d] = (k % 2 ? -1.0 : 1.0) * m->vol[i] / h[d];"),
+    # the reference-to-physical derivative without its factor 2
+    "jacobian_half": ("m->Ji[9 * i + 4 * d] = 2.0 / h[d];", "m->Ji[9 * i + 4 * d] = 1.0 / h[d];"),
+    # Legendre polynomials without their normalisation (the basis no longer orthonormal)
+    "legendre_unnormalised": ("v[k] = sqrt(2.0 * k + 1.0) * p[k];", "v[k] = p[k];"),
+    # the periodic wrap one cell off
+    "periodic_wrap_off": ("if (bc[k] == B3_PERIODIC) cc[d] = (cc[d] + n3[d]) % n3[d];",
+                          "if (bc[k] == B3_PERIODIC) cc[d] = (cc[d] + n3[d] + 1) % n3[d];"),
+}
+
+
+def _build_hex(tmp, name):
+    src = open(SRC3).read()
+    if name is not None:
+        old, new = HEX_MUTANTS[name]
+        assert src.count(old) == 1, name
+        src = src.replace(old, new)
+    path = os.path.join(tmp, "mut3d.c")
+    open(path, "w").write(src)
+    lib = os.path.join(tmp, "liborc_hex_%s.so" % (name or "base"))
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=gnu11", "-I", ODIR, "-o", lib,
+                    SRC2, path, "-lm"], check=True, capture_output=True)
+    return lib
+
+
+def hex_pin_failures(orc):
+    """The hexahedral pins of the short set that fail on the loaded oracle:
+    the exact step of an advected quadratic on non-cubic cells with ny != nz,
+    free stream, conservation of all five totals on a periodic mesh."""
+    fails = []
+    U = np.array([0.7, -0.4, 0.3]); P = 1.1
+    rho0 = lambda x, y, z: 1.0 + 0.3 * x - 0.2 * y + 0.1 * z + 0.4 * x * x + 0.1 * x * y - 0.3 * y * z + 0.2 * z * z  # noqa: E731
+    try:
+        m = orc.Mesh3(3, 2, 4, (0.0, 0.9, 0.0, 0.6, 0.0, 0.7), (2,) * 6)
+        s = orc.Solver3(m, 2, gamma=G, shock_limiter=False)
+        ic = lambda t: (lambda x, y, z: (rho0(x - U[0] * t, y - U[1] * t, z - U[2] * t), U[0] + 0 * x,  # noqa: E731
+                                         U[1] + 0 * x, U[2] + 0 * x, P + 0 * x))
+        Q = s.project_fn(ic(0.0))
+        s.step(Q, dt=0.02)
+        if not np.abs(Q - s.project_fn(ic(0.02))).max() < 5e-14:
+            fails.append("exact_quadratic")
+        Q = s.project_fn(lambda x, y, z: (1.3 + 0 * x, 0.4 + 0 * x, -0.2 + 0 * x, 0.7 + 0 * x, 0.9 + 0 * x))
+        Q0 = Q.copy()
+        s.step(Q, cfl=0.3)
+        if not np.allclose(Q, Q0, atol=1e-13):
+            fails.append("free_stream")
+        m = orc.Mesh3(4, 3, 5, (0.0, 1.0, 0.0, 0.8, 0.0, 1.2), (0,) * 6)
+        s = orc.Solver3(m, 2, gamma=G, alpha0=50.0)
+        Q = synth.random_modal_state3(m.N, s.ML, seed=21, amp=0.3, rho_range=(0.02, 2.0), p_range=(0.01, 2.0))
+        vol = m.geometry()[0]
+        t0 = (vol[:, None] * Q[:, :, 0]).sum(axis=0)
+        d = s.step(Q, cfl=0.3)
+        t1 = (vol[:, None] * Q[:, :, 0]).sum(axis=0)
+        if d["status"] != 0 or not np.allclose(t1, t0, rtol=1e-13, atol=1e-13):
+            fails.append("conservation")
+    except Exception as e:
+        fails.append("error: %s" % str(e)[:60])
+    return fails
+
+
+def test_unchanged_source_passes_hex():
+    from oracle import oracle as orc
+    with tempfile.TemporaryDirectory() as tmp:
+        with orc.use_library(_build_hex(tmp, None)):
+            assert hex_pin_failures(orc) == []
+
+
+@pytest.mark.parametrize("name", sorted(HEX_MUTANTS))
+def test_planted_hex_mistakes_fail_the_pins(name):
+    from oracle import oracle as orc
+    with tempfile.TemporaryDirectory() as tmp:
+        with orc.use_library(_build_hex(tmp, name)):
+            assert hex_pin_failures(orc) != [], name
