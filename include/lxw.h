@@ -455,9 +455,10 @@ lxw_status lxw_moment_limit_noalloc(int kind, int degree, int n_elements, double
                                     void* stream);
 
 /* ------------------------------------------------------------------ */
-/* 3D Cartesian meshes (hexahedra), FP64: the same step on box cells with  */
-/* six faces (the extension the end of Sec. 3.3 says carries over         */
-/* directly; the 3D Euler equations of Sec. 1.1 with a third flux H).      */
+/* 3D Cartesian meshes (hexahedra): the same step on box cells with six    */
+/* faces (the extension the end of Sec. 3.3 says carries over directly;   */
+/* the 3D Euler equations of Sec. 1.1 with a third flux H), in FP64 or in */
+/* the mixed form (options.precision; see lxw3_solver_create).            */
 /* State Q[N][5][ML] (rho, rho u, rho v, rho w, E), ML = 4 (P1) or 10      */
 /* (P2); cell (ix, iy, iz) is element (iz ny + iy) nx + ix; modes           */
 /* L_a(xi) L_b(eta) L_c(zeta), L_n = sqrt(2n+1) P_n, a + b + c <= degree,  */
